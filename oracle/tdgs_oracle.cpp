@@ -1,0 +1,208 @@
+// CPU oracle for the 3DGS tile depth sort -- TEST INFRASTRUCTURE ONLY.
+//
+// Only the test suite, the smoke check and the benchmark's CPU-baseline leg
+// may load this library.  It shares no code, header or constant with the
+// CUDA path: it is the plain, slow definition of each step, written from the
+// paper's statement of the pipeline (Sec. II-A "Duplication with Tiles" and
+// "Sorting"; Table III lists which buffers feed PrefixSum and
+// DuplicateWithTile; Table VI names the stages Scan, Duplicate with tiles,
+// Sorting and Identify Range).  Every function runs on one host thread.
+//
+// Readings where the paper is silent (the exact rectangle rule, validity of
+// depths, tile numbering, the key layout, tie order, empty tiles) are stated
+// beside the code that applies them.
+//
+// Status codes (same numbering as the library's public header, restated
+// here on purpose so nothing is shared):
+//   0 ok, 1 invalid argument, 3 pair-count overflow.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+constexpr int kOk = 0;
+constexpr int kInvalid = 1;
+constexpr int kOverflow = 3;
+
+struct G2 {       // one projected Gaussian (Table IV, Group 1: xy, depth, radius)
+  float x, y, depth;
+  int32_t radius;
+};
+static_assert(sizeof(G2) == 16, "record is 16 bytes");
+
+struct Rect {
+  int32_t x0, y0, x1, y1;  // tiles [x0,x1) x [y0,y1)
+};
+
+// Tile rectangle of a Gaussian's 3-sigma box (Sec. II-A: the AABB of the
+// projected ellipse is intersected with the 16x16 tile grid).  Reading: the
+// box is [x - r, x + r] in pixels; the first touched column is
+// floor((x - r) / 16) and the end column is floor((x + r + 15) / 16), each
+// evaluated in float32 in exactly this order, then clamped to [0, grid].
+// Division by 16 is written as multiplication by 1/16, which is exact.
+// `volatile` keeps every intermediate a rounded float32 (no contraction,
+// no excess precision).
+Rect tile_rect(const G2& g, int32_t gx, int32_t gy) {
+  volatile float r = static_cast<float>(g.radius);
+  volatile float sx0 = g.x - r;
+  volatile float sx1 = g.x + r;
+  sx1 = sx1 + 15.0f;
+  volatile float sy0 = g.y - r;
+  volatile float sy1 = g.y + r;
+  sy1 = sy1 + 15.0f;
+  float fx0 = std::floor(sx0 * 0.0625f);
+  float fx1 = std::floor(sx1 * 0.0625f);
+  float fy0 = std::floor(sy0 * 0.0625f);
+  float fy1 = std::floor(sy1 * 0.0625f);
+  auto clampf = [](float v, float hi) { return v < 0.0f ? 0.0f : (v > hi ? hi : v); };
+  Rect q;
+  q.x0 = static_cast<int32_t>(clampf(fx0, static_cast<float>(gx)));
+  q.x1 = static_cast<int32_t>(clampf(fx1, static_cast<float>(gx)));
+  q.y0 = static_cast<int32_t>(clampf(fy0, static_cast<float>(gy)));
+  q.y1 = static_cast<int32_t>(clampf(fy1, static_cast<float>(gy)));
+  return q;
+}
+
+bool rect_empty(const Rect& q) { return q.x1 <= q.x0 || q.y1 <= q.y0; }
+
+// Reading of validity: radius <= 0 means culled (no tiles, nothing checked).
+// A Gaussian with radius > 0 must have a finite mean; one whose rectangle is
+// non-empty must have a finite depth > +0.0, because the key carries the raw
+// float bits of the depth and only positive finite floats keep their order
+// when compared as unsigned integers.
+bool depth_ok(float d) { return std::isfinite(d) && d > 0.0f; }
+
+uint32_t grid_dim(uint32_t px) { return (px + 15u) / 16u; }
+
+uint32_t bits_of(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return u;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Step 1, tile count: counts[i] = number of 16x16 tiles the i-th Gaussian's
+// rectangle covers (0 when culled or off-screen).  Returns 1 on an invalid
+// Gaussian (its count is written as 0 and the scan continues).
+int oracle_count_tiles(const G2* g, uint32_t n, uint32_t width, uint32_t height,
+                       uint32_t* counts) {
+  if (width == 0 || height == 0) return kInvalid;
+  const int32_t gx = static_cast<int32_t>(grid_dim(width));
+  const int32_t gy = static_cast<int32_t>(grid_dim(height));
+  int status = kOk;
+  for (uint32_t i = 0; i < n; ++i) {
+    counts[i] = 0;
+    if (g[i].radius <= 0) continue;
+    if (!std::isfinite(g[i].x) || !std::isfinite(g[i].y)) {
+      status = kInvalid;
+      continue;
+    }
+    Rect q = tile_rect(g[i], gx, gy);
+    if (rect_empty(q)) continue;
+    if (!depth_ok(g[i].depth)) {
+      status = kInvalid;
+      continue;
+    }
+    counts[i] = static_cast<uint32_t>(q.x1 - q.x0) * static_cast<uint32_t>(q.y1 - q.y0);
+  }
+  return status;
+}
+
+// Step 2, PrefixSum (Table III): offsets[i] = sum of counts[j] for j < i,
+// accumulated in 64 bits; *total = the full sum.  A total above 2^32 - 1
+// cannot index uint32 offsets and returns the overflow status.
+int oracle_scan(const uint32_t* counts, uint32_t n, uint32_t* offsets, uint64_t* total) {
+  uint64_t run = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    offsets[i] = static_cast<uint32_t>(run);
+    run += counts[i];
+  }
+  *total = run;
+  return run > 0xFFFFFFFFull ? kOverflow : kOk;
+}
+
+// Step 3, DuplicateWithTile (Sec. II-A): each Gaussian i writes one pair per
+// covered tile, rows (ty) outer and columns (tx) inner, starting at
+// offsets[i].  Key = (tile id << 32) | raw bits of the float32 depth, with
+// tile id = ty * gx + tx (row-major); value = i.  m is the capacity of keys
+// and values; a pair that would land at or beyond it is an invalid argument.
+int oracle_duplicate(const G2* g, const uint32_t* offsets, uint32_t n, uint32_t width,
+                     uint32_t height, uint64_t* keys, uint32_t* values, uint32_t m) {
+  if (width == 0 || height == 0) return kInvalid;
+  const int32_t gx = static_cast<int32_t>(grid_dim(width));
+  const int32_t gy = static_cast<int32_t>(grid_dim(height));
+  for (uint32_t i = 0; i < n; ++i) {
+    if (g[i].radius <= 0) continue;
+    if (!std::isfinite(g[i].x) || !std::isfinite(g[i].y)) return kInvalid;
+    Rect q = tile_rect(g[i], gx, gy);
+    if (rect_empty(q)) continue;
+    if (!depth_ok(g[i].depth)) return kInvalid;
+    uint64_t k = offsets[i];
+    const uint64_t dbits = bits_of(g[i].depth);
+    for (int32_t ty = q.y0; ty < q.y1; ++ty)
+      for (int32_t tx = q.x0; tx < q.x1; ++tx) {
+        const uint64_t tile = static_cast<uint64_t>(ty) * static_cast<uint64_t>(gx) +
+                              static_cast<uint64_t>(tx);
+        if (k >= m) return kInvalid;
+        keys[k] = (tile << 32) | dbits;
+        values[k] = i;
+        ++k;
+      }
+  }
+  return kOk;
+}
+
+// Step 4, Sorting (Sec. II-A: by tile, then by depth within the tile): a
+// stable ascending sort of the pairs by the whole 64-bit key.  Equal keys
+// keep their input order.
+int oracle_sort_pairs(uint64_t* keys, uint32_t* values, uint32_t m) {
+  std::vector<uint32_t> idx(m);
+  for (uint32_t k = 0; k < m; ++k) idx[k] = k;
+  std::stable_sort(idx.begin(), idx.end(),
+                   [keys](uint32_t a, uint32_t b) { return keys[a] < keys[b]; });
+  std::vector<uint64_t> k2(m);
+  std::vector<uint32_t> v2(m);
+  for (uint32_t k = 0; k < m; ++k) {
+    k2[k] = keys[idx[k]];
+    v2[k] = values[idx[k]];
+  }
+  std::copy(k2.begin(), k2.end(), keys);
+  std::copy(v2.begin(), v2.end(), values);
+  return kOk;
+}
+
+// Step 5, Identify Range (Sec. IV-B): ranges[2t], ranges[2t+1] = first and
+// one-past-last position of tile t in the sorted list, found by one linear
+// pass over the sorted keys.  Reading: a tile with no pairs keeps {0, 0}.
+// A key whose tile id is >= num_tiles is an invalid argument.
+int oracle_tile_ranges(const uint64_t* sorted_keys, uint32_t m, uint32_t num_tiles,
+                       uint32_t* ranges) {
+  for (uint32_t t = 0; t < num_tiles; ++t) ranges[2 * t] = ranges[2 * t + 1] = 0;
+  if (m == 0) return kOk;
+  uint64_t prev = 0;
+  for (uint32_t k = 0; k < m; ++k) {
+    const uint64_t t = sorted_keys[k] >> 32;
+    if (t >= num_tiles) return kInvalid;
+    if (k == 0 || t != prev) {
+      ranges[2 * t] = k;
+      if (k > 0) ranges[2 * prev + 1] = k;
+    }
+    prev = t;
+  }
+  ranges[2 * prev + 1] = m;
+  return kOk;
+}
+
+// Number of tiles and tile bits of an image (helpers for callers).
+uint32_t oracle_num_tiles(uint32_t width, uint32_t height) {
+  return grid_dim(width) * grid_dim(height);
+}
+
+}  // extern "C"

@@ -1,0 +1,248 @@
+"""Seeded synthetic inputs for the 3DGS tile depth sort.
+
+This module only draws random numbers and arranges them into the projected
+Gaussian records that the sort step consumes (Sec. II-A, "Duplication with
+Tiles": a 2D mean, a view depth and a pixel radius per Gaussian; Table IV
+packs exactly these four values into one record).  It holds none of the
+sorting method's arithmetic: no tile rectangles, no keys, no scans.  Both
+the CUDA path and the CPU oracle are fed from here, so neither depends on
+the other for its inputs.
+
+The paper evaluates on trained scenes (Tanks and Temples, DeepBlending,
+Synthetic-NeRF) that are not available; the workloads below are seeded
+stand-ins with the sizes and value distributions of those frames:
+
+* ``frame_small``  - 10,000 Gaussians, 256x256, uniform means.
+* ``frame_scene``  - 1,000,000 Gaussians, 1280x720, 70 % clustered means.
+* ``frame_large``  - 3,000,000 Gaussians, 1920x1080, 85 % clustered means,
+  5 % of depths quantised to a 1/8 grid (many exact key ties).
+* ``multiview``    - one 500,000-Gaussian 3D scene seen by 64 pinhole
+  cameras (the projection happens here, as part of input generation).
+* ``request_trace``- a Poisson stream of frames of mixed size/resolution.
+
+All draws use ``numpy.random.default_rng(seed)`` in float64 and are rounded
+to float32 at the end; radius = ceil(3 * sigma) computed in float64.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# One projected Gaussian: 2D mean (px), view depth, integer pixel radius.
+GAUSSIAN2D = np.dtype(
+    [("x", "<f4"), ("y", "<f4"), ("depth", "<f4"), ("radius", "<i4")], align=True
+)
+assert GAUSSIAN2D.itemsize == 16
+
+TILE = 16  # screen tiles are 16x16 pixels (Sec. II-A)
+
+
+@dataclasses.dataclass
+class Frame:
+    """One view to sort: image size and its projected Gaussians."""
+
+    width: int
+    height: int
+    gaussians: np.ndarray  # GAUSSIAN2D records
+    name: str = ""
+
+    @property
+    def n(self) -> int:
+        return int(self.gaussians.shape[0])
+
+    @property
+    def grid(self) -> tuple[int, int]:
+        return (self.width + TILE - 1) // TILE, (self.height + TILE - 1) // TILE
+
+    @property
+    def num_tiles(self) -> int:
+        gx, gy = self.grid
+        return gx * gy
+
+    @property
+    def tile_bits(self) -> int:
+        t = self.num_tiles
+        return 0 if t <= 1 else int(t - 1).bit_length()
+
+
+def records(x, y, depth, radius) -> np.ndarray:
+    """Pack four equal-length arrays into GAUSSIAN2D records."""
+    n = len(x)
+    g = np.empty(n, dtype=GAUSSIAN2D)
+    g["x"] = np.asarray(x, dtype=np.float64).astype(np.float32)
+    g["y"] = np.asarray(y, dtype=np.float64).astype(np.float32)
+    g["depth"] = np.asarray(depth, dtype=np.float64).astype(np.float32)
+    g["radius"] = np.asarray(radius, dtype=np.int64).astype(np.int32)
+    return g
+
+
+def _radius(sigma: np.ndarray) -> np.ndarray:
+    return np.ceil(3.0 * sigma).astype(np.int64)
+
+
+def _means(rng, n, width, height, cluster_frac, n_centres, centre_sd):
+    n_cl = int(round(cluster_frac * n))
+    centres = rng.uniform((0.0, 0.0), (width, height), size=(n_centres, 2))
+    which = rng.integers(0, n_centres, size=n_cl)
+    clustered = centres[which] + rng.normal(0.0, centre_sd, size=(n_cl, 2))
+    uniform = rng.uniform((0.0, 0.0), (width, height), size=(n - n_cl, 2))
+    pts = np.concatenate([clustered, uniform], axis=0)
+    return pts[rng.permutation(n)]
+
+
+def frame_small(seed: int = 0, n: int = 10_000, width: int = 256, height: int = 256) -> Frame:
+    """10k Gaussians on 256x256: uniform means, sigma ~ lognormal(ln 3, 0.6)
+    clipped to [1, 64], depth ~ U[0.2, 50]."""
+    rng = np.random.default_rng(seed)
+    xy = rng.uniform((0.0, 0.0), (width, height), size=(n, 2))
+    sigma = np.clip(rng.lognormal(math.log(3.0), 0.6, size=n), 1.0, 64.0)
+    depth = rng.uniform(0.2, 50.0, size=n)
+    return Frame(width, height, records(xy[:, 0], xy[:, 1], depth, _radius(sigma)),
+                 f"small-{n}-{width}x{height}-s{seed}")
+
+
+def frame_scene(seed: int = 0, n: int = 1_000_000, width: int = 1280, height: int = 720) -> Frame:
+    """Scene-scale frame: 70 % of means around 32 centres (sd 60 px), 30 %
+    uniform; sigma ~ lognormal(ln 4, 0.8) clipped to [1, 256];
+    depth ~ lognormal(ln 5, 0.7).  Means are not clipped to the image."""
+    rng = np.random.default_rng(seed)
+    xy = _means(rng, n, width, height, 0.70, 32, 60.0)
+    sigma = np.clip(rng.lognormal(math.log(4.0), 0.8, size=n), 1.0, 256.0)
+    depth = rng.lognormal(math.log(5.0), 0.7, size=n)
+    return Frame(width, height, records(xy[:, 0], xy[:, 1], depth, _radius(sigma)),
+                 f"scene-{n}-{width}x{height}-s{seed}")
+
+
+def frame_large(seed: int = 0, n: int = 3_000_000, width: int = 1920, height: int = 1080) -> Frame:
+    """Large frame: 85 % of means around 128 centres (sd 40 px);
+    sigma ~ lognormal(ln 3, 1.0) clipped to [1, 512];
+    depth ~ lognormal(ln 8, 0.9), then 5 % of the Gaussians (chosen by the
+    RNG) get depth round(d*8)/8, which is exact in binary and creates many
+    equal keys, so stability is exercised."""
+    rng = np.random.default_rng(seed)
+    xy = _means(rng, n, width, height, 0.85, 128, 40.0)
+    sigma = np.clip(rng.lognormal(math.log(3.0), 1.0, size=n), 1.0, 512.0)
+    depth = rng.lognormal(math.log(8.0), 0.9, size=n)
+    q = rng.random(n) < 0.05
+    depth[q] = np.maximum(np.round(depth[q] * 8.0) / 8.0, 0.125)
+    return Frame(width, height, records(xy[:, 0], xy[:, 1], depth, _radius(sigma)),
+                 f"large-{n}-{width}x{height}-s{seed}")
+
+
+def frame_random(seed: int, n: int, width: int, height: int, *, max_sigma: float = 64.0,
+                 offscreen: float = 0.1, culled: float = 0.05, depth_ties: float = 0.0) -> Frame:
+    """Small mixed frames for parity sweeps: some means off-screen, some
+    Gaussians culled (radius 0), optional depth ties."""
+    rng = np.random.default_rng(seed)
+    margin = 2.0 * max_sigma
+    x = rng.uniform(-margin * offscreen * 4, width + margin * offscreen * 4, size=n)
+    y = rng.uniform(-margin * offscreen * 4, height + margin * offscreen * 4, size=n)
+    sigma = np.clip(rng.lognormal(math.log(3.0), 0.9, size=n), 1.0, max_sigma)
+    r = _radius(sigma)
+    r[rng.random(n) < culled] = 0
+    depth = rng.lognormal(math.log(6.0), 0.8, size=n)
+    if depth_ties > 0:
+        t = rng.random(n) < depth_ties
+        depth[t] = np.maximum(np.round(depth[t] * 2.0) / 2.0, 0.5)
+    return Frame(width, height, records(x, y, depth, r), f"random-{n}-{width}x{height}-s{seed}")
+
+
+# ---------------------------------------------------------------- multi-view
+@dataclasses.dataclass
+class MultiView:
+    """A 3D scene seen by several cameras; each view is a Frame whose
+    records index the scene's Gaussian array."""
+
+    views: list[Frame]
+    scale0: float
+    seed: int
+
+
+def _fibonacci_sphere(k: int) -> np.ndarray:
+    i = np.arange(k, dtype=np.float64) + 0.5
+    phi = np.arccos(1.0 - 2.0 * i / k)
+    theta = math.pi * (1.0 + 5.0 ** 0.5) * i
+    return np.stack([np.cos(theta) * np.sin(phi), np.cos(phi), np.sin(theta) * np.sin(phi)], 1)
+
+
+def multiview(seed: int = 0, n: int = 500_000, views: int = 64, width: int = 1280,
+              height: int = 720, scale0: float = 0.03, cam_radius: float = 15.0) -> MultiView:
+    """One scene, many cameras.  Means ~ U[0,1)^3 * 10 - 5; isotropic scale
+    s ~ lognormal(ln scale0, 0.5); cameras on a Fibonacci lattice of a
+    sphere of radius ``cam_radius`` looking at the origin plus a jitter
+    drawn uniformly from a ball of radius 4, up = +y.  Pinhole with
+    fx = fy = 1108.5, principal point at the image centre.  Per view:
+    depth = view-space z, radius 0 (culled) where z <= 0.2, otherwise
+    r = ceil(3 * fx * s / z) and the mean is projected."""
+    rng = np.random.default_rng(seed)
+    mean3 = rng.random((n, 3)) * 10.0 - 5.0
+    scale = rng.lognormal(math.log(scale0), 0.5, size=n)
+    eye = _fibonacci_sphere(views) * cam_radius
+    u = rng.normal(size=(views, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    jitter = u * (4.0 * rng.random(views) ** (1.0 / 3.0))[:, None]
+    fx = fy = 1108.5
+    cx, cy = width / 2.0, height / 2.0
+    out = []
+    for v in range(views):
+        fwd = jitter[v] - eye[v]
+        fwd /= np.linalg.norm(fwd)
+        up = np.array([0.0, 1.0, 0.0])
+        right = np.cross(fwd, up)
+        if np.linalg.norm(right) < 1e-6:
+            right = np.array([1.0, 0.0, 0.0])
+        right /= np.linalg.norm(right)
+        down = np.cross(fwd, right)
+        rel = mean3 - eye[v]
+        xc = rel @ right
+        yc = rel @ down
+        zc = rel @ fwd
+        ok = zc > 0.2
+        zs = np.where(ok, zc, 1.0)
+        px = fx * xc / zs + cx
+        py = fy * yc / zs + cy
+        r = np.where(ok, np.ceil(3.0 * fx * scale / zs), 0).astype(np.int64)
+        depth = np.where(ok, zc, 1.0)
+        out.append(Frame(width, height, records(px, py, depth, r), f"view{v}"))
+    return MultiView(out, scale0, seed)
+
+
+# ------------------------------------------------------------ request trace
+RESOLUTIONS = ((640, 360), (1280, 720), (1920, 1080))
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival_s: float
+    n: int
+    width: int
+    height: int
+    seed: int
+
+    def frame(self) -> Frame:
+        """Frame of this request, drawn like the scene-scale frame."""
+        return frame_scene(self.seed, self.n, self.width, self.height)
+
+
+def request_trace(seed: int = 0, count: int = 2000, rate_hz: float = 200.0,
+                  n_lo: int = 100_000, n_hi: int = 3_000_000) -> list[Request]:
+    """Poisson arrivals at ``rate_hz``; N log-uniform in [n_lo, n_hi];
+    resolution uniform over 640x360, 1280x720, 1920x1080; per-request
+    seed 1000 + id."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate_hz, size=count)
+    t = np.cumsum(gaps) - gaps[0]
+    ns = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=count)).astype(np.int64)
+    res = rng.integers(0, len(RESOLUTIONS), size=count)
+    return [Request(i, float(t[i]), int(ns[i]), *RESOLUTIONS[int(res[i])], 1000 + i)
+            for i in range(count)]
+
+
+CONFIGS = {
+    "small": frame_small,
+    "scene": frame_scene,
+    "large": frame_large,
+}

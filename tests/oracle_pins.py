@@ -1,0 +1,307 @@
+"""Checks that pin the CPU oracle to facts fixed outside of it.
+
+None of these retypes the oracle's formulas.  Each check compares the
+oracle with something independent:
+
+* a hand-worked frame (``tests/golden/hand_frame_40x36.json``);
+* a brute-force tile-overlap test written as exact comparisons of the
+  rounded box edges against every tile's pixel boundary (no floor, no
+  clamp, no division);
+* Python's arbitrary-precision running sum for the scan;
+* Python's ``sorted`` (documented stable) for the sort, plus an O(m^2)
+  insertion sort on tiny inputs;
+* invariants (permutation, order, stability, partition of the ranges).
+
+The checks take an ``Oracle`` object so the same checks can also be run
+against deliberately broken builds of the oracle (see
+``test_oracle_mutants.py``) to show that each plausible mistake fails at
+least one of them.
+"""
+from __future__ import annotations
+
+import json
+import os
+import struct
+
+import numpy as np
+
+from paper_2511_16298_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_frame_40x36.json")
+
+
+def f32_bits(v: float) -> int:
+    return struct.unpack("<I", struct.pack("<f", v))[0]
+
+
+# ------------------------------------------------------------ brute force
+def brute_cover(x, y, r, width, height):
+    """Tiles (ty, tx) whose 16x16 pixel square meets the Gaussian's box.
+
+    The box edges are the float32-rounded values s1 = x - r and
+    s2 = (x + r) + 15 (same for y).  Column tx is covered iff its right
+    pixel boundary 16*tx + 16 lies in (s1, s2].  Every comparison is exact
+    (float32 values against small integers)."""
+    gx, gy = -(-width // 16), -(-height // 16)
+    if r <= 0:
+        return []
+    rf = np.float32(r)
+    xf, yf = np.float32(x), np.float32(y)
+    sx1 = float(np.float32(xf - rf))
+    sx2 = float(np.float32(np.float32(xf + rf) + np.float32(15.0)))
+    sy1 = float(np.float32(yf - rf))
+    sy2 = float(np.float32(np.float32(yf + rf) + np.float32(15.0)))
+    cols = [tx for tx in range(gx) if 16 * tx + 16 > sx1 and 16 * tx + 16 <= sx2]
+    rows = [ty for ty in range(gy) if 16 * ty + 16 > sy1 and 16 * ty + 16 <= sy2]
+    return [(ty, tx) for ty in rows for tx in cols]
+
+
+def brute_frame(g, width, height):
+    """Brute-force pairs in emission order: Gaussian, then row, then column."""
+    gx = -(-width // 16)
+    pairs = []
+    counts = []
+    for i, rec in enumerate(g):
+        cov = brute_cover(float(rec["x"]), float(rec["y"]), int(rec["radius"]), width, height)
+        counts.append(len(cov))
+        for ty, tx in cov:
+            pairs.append(((ty * gx + tx) << 32 | f32_bits(float(rec["depth"])), i))
+    return counts, pairs
+
+
+def tiny_frame(seed: int):
+    """Tiny frame with many edge positions: means on and next to tile
+    boundaries (+-1 ulp), off-screen means, culled and large radii."""
+    rng = np.random.default_rng(seed)
+    width = int(rng.integers(1, 65))
+    height = int(rng.integers(1, 65))
+    n = int(rng.integers(1, 51))
+    kind = rng.integers(0, 3, size=(n, 2))
+    base = rng.integers(-3, 6, size=(n, 2)) * 16.0 + rng.choice([0.0, 0.5, 15.0, 15.5], size=(n, 2))
+    xy = np.where(kind == 0, rng.uniform(-40, 100, size=(n, 2)), base)
+    xy = xy.astype(np.float32)
+    bump = rng.choice([-1, 0, 1], size=(n, 2))
+    xy = np.where(kind == 2, np.nextafter(xy, np.where(bump > 0, np.inf, -np.inf)).astype(np.float32), xy)
+    r = rng.choice([0, 1, 2, 3, 7, 8, 9, 15, 16, 17, 31, 40, 100], size=n)
+    depth = rng.uniform(0.1, 20.0, size=n)
+    g = synth.records(xy[:, 0], xy[:, 1], depth, r)
+    return g, width, height
+
+
+# ----------------------------------------------------------------- checks
+def check_golden(O):
+    d = json.load(open(GOLDEN))
+    gs = d["gaussians"]
+    g = synth.records([q["x"] for q in gs], [q["y"] for q in gs], [q["depth"] for q in gs],
+                      [q["radius"] for q in gs])
+    W, H = d["width"], d["height"]
+    st, counts = O.count_tiles(g, W, H)
+    assert st == 0 and counts.tolist() == d["counts"], counts
+    st, offsets, m = O.scan(counts)
+    assert st == 0 and offsets.tolist() == d["offsets"] and m == d["m"]
+    st, keys, values = O.duplicate(g, offsets, m, W, H)
+    assert st == 0
+    exp_keys = [t << 32 | f32_bits(z) for t, z in zip(d["unsorted_tiles"], d["unsorted_depths"])]
+    assert keys.tolist() == exp_keys and values.tolist() == d["unsorted_values"]
+    st, sk, sv = O.sort_pairs(keys, values)
+    exp_sorted = [t << 32 | f32_bits(z) for t, z in zip(d["sorted_tiles"], d["sorted_depths"])]
+    assert st == 0 and sk.tolist() == exp_sorted and sv.tolist() == d["sorted_values"]
+    st, ranges = O.tile_ranges(sk, len(d["ranges"]))
+    assert st == 0 and ranges.tolist() == d["ranges"]
+    for k, v in d["float32_bits"].items():
+        assert f32_bits(float(k)) == int(v, 16)
+
+
+def check_count_and_duplicate_bruteforce(O, seeds=range(40)):
+    for seed in seeds:
+        g, W, H = tiny_frame(seed)
+        counts_bf, pairs_bf = brute_frame(g, W, H)
+        st, counts = O.count_tiles(g, W, H)
+        assert st == 0, (seed, st)
+        assert counts.tolist() == counts_bf, (seed, W, H)
+        st, offsets, m = O.scan(counts)
+        assert st == 0 and m == len(pairs_bf)
+        st, keys, values = O.duplicate(g, offsets, m, W, H)
+        assert st == 0
+        assert list(zip(keys.tolist(), values.tolist())) == pairs_bf, (seed, W, H)
+
+
+def check_special_cases(O):
+    W, H = 256, 128  # 16 x 8 tiles
+    T = 128
+    cases = [
+        # (x, y, r, expected count)
+        (8.5, 8.5, 1, 1),          # stays inside one tile
+        (-100.0, 50.0, 5, 0),      # fully left of the screen
+        (50.0, 500.0, 5, 0),       # fully below the screen
+        (128.0, 64.0, 1000, T),    # radius covering the screen
+        (0.0, 0.0, 1, 1),          # corner: box [-1,1] -> tile 0 only
+        (16.0, 16.0, 1, 4),        # box [15,17] straddles 2x2 tiles
+        (255.9, 127.9, 1, 1),      # last tile
+        (10.0, 10.0, 0, 0),        # culled
+        (10.0, 10.0, -3, 0),       # negative radius: culled
+    ]
+    g = synth.records([c[0] for c in cases], [c[1] for c in cases], [1.0] * len(cases),
+                      [c[2] for c in cases])
+    st, counts = O.count_tiles(g, W, H)
+    assert st == 0 and counts.tolist() == [c[3] for c in cases], counts
+    # one tile image: every visible Gaussian hits tile 0
+    g1 = synth.records([3.0, 20.0], [3.0, 3.0], [1.0, 2.0], [2, 1])
+    st, c1 = O.count_tiles(g1, 16, 16)
+    assert st == 0 and c1.tolist() == [1, 0]
+    # n = 0
+    st, c0 = O.count_tiles(g[:0], W, H)
+    assert st == 0 and len(c0) == 0
+    st, r0 = O.tile_ranges(np.zeros(0, np.uint64), 5)
+    assert st == 0 and (r0 == 0).all()
+
+
+def check_validity(O):
+    W, H = 64, 64
+    bad = [
+        (10.0, 10.0, float("nan"), 3),
+        (10.0, 10.0, float("inf"), 3),
+        (10.0, 10.0, -1.0, 3),
+        (10.0, 10.0, 0.0, 3),
+        (10.0, 10.0, -0.0, 3),
+        (float("nan"), 10.0, 1.0, 3),
+        (10.0, float("inf"), 1.0, 3),
+    ]
+    for x, y, z, r in bad:
+        g = synth.records([5.0, x], [5.0, y], [1.0, z], [2, r])
+        st, _ = O.count_tiles(g, W, H)
+        assert st == 1, (x, y, z)
+    ok = [
+        (10.0, 10.0, float("nan"), 0),      # culled: not checked
+        (-500.0, 10.0, -1.0, 3),             # off-screen: depth not checked
+        (10.0, 10.0, 1e-45, 3),              # smallest subnormal is > 0
+        (float("nan"), 10.0, 1.0, 0),        # culled NaN mean
+    ]
+    for x, y, z, r in ok:
+        g = synth.records([x], [y], [z], [r])
+        st, _ = O.count_tiles(g, W, H)
+        assert st == 0, (x, y, z, r)
+    st, _ = O.count_tiles(synth.records([1.0], [1.0], [1.0], [1]), 0, 16)
+    assert st == 1
+
+
+def check_scan(O):
+    rng = np.random.default_rng(7)
+    for n in (0, 1, 2, 31, 1000, 4097):
+        c = rng.integers(0, 3000, size=n).astype(np.uint32)
+        st, off, total = O.scan(c)
+        run = 0
+        exp = []
+        for v in c.tolist():
+            exp.append(run)
+            run += v
+        assert st == 0 and off.tolist() == exp and total == run
+    st, _, total = O.scan(np.array([2**31, 2**31 - 1], dtype=np.uint32))
+    assert st == 0 and total == 2**32 - 1
+    st, _, total = O.scan(np.array([2**31, 2**31], dtype=np.uint32))
+    assert st == 3 and total == 2**32
+
+
+def check_sort(O):
+    rng = np.random.default_rng(11)
+    for m, nkeys, wide in ((0, 1, False), (1, 1, False), (2, 1, False), (17, 3, False),
+                           (300, 20, False), (5000, 50, True), (20000, 2000, True)):
+        if wide:
+            pool = rng.integers(0, 2**63, size=nkeys, dtype=np.uint64) * np.uint64(2) \
+                + rng.integers(0, 2, size=nkeys, dtype=np.uint64)
+        else:
+            pool = rng.integers(0, 1 << 40, size=nkeys, dtype=np.uint64)
+        keys = pool[rng.integers(0, nkeys, size=m)] if m else np.zeros(0, np.uint64)
+        values = rng.permutation(m).astype(np.uint32)
+        st, sk, sv = O.sort_pairs(keys, values)
+        assert st == 0
+        kl, vl = keys.tolist(), values.tolist()
+        order = sorted(range(m), key=lambda k: kl[k])  # Python's sort is stable
+        assert sk.tolist() == [kl[k] for k in order]
+        assert sv.tolist() == [vl[k] for k in order]
+        # invariants
+        assert sorted(zip(sk.tolist(), sv.tolist())) == sorted(zip(kl, vl))
+        assert all(a <= b for a, b in zip(sk.tolist(), sk.tolist()[1:]))
+    # O(m^2) insertion sort on a tiny case with ties
+    keys = np.array([5, 3, 5, 1, 3, 3, 9, 0, 5], dtype=np.uint64)
+    values = np.arange(9, dtype=np.uint32)[::-1].copy()
+    pairs = list(zip(keys.tolist(), values.tolist()))
+    out = []
+    for p in pairs:
+        j = len(out)
+        while j > 0 and out[j - 1][0] > p[0]:
+            j -= 1
+        out.insert(j, p)
+    st, sk, sv = O.sort_pairs(keys, values)
+    assert list(zip(sk.tolist(), sv.tolist())) == out
+
+
+def check_frame_invariants(O, frames):
+    """Full pipeline on frames: permutation of the duplicated pairs, keys
+    non-decreasing, equal keys with increasing values (the lemma: equal
+    keys come from distinct Gaussians emitted in index order), ranges
+    partition [0, m) in tile order and match per-tile brute-force counts."""
+    for fr in frames:
+        d = O.sort_frame(fr.gaussians, fr.width, fr.height)
+        assert d["status"] == 0
+        k, v = d["keys"].astype(np.uint64), d["values"].astype(np.int64)
+        m = d["m"]
+        assert len(k) == m
+        assert np.all(k[1:] >= k[:-1])
+        tie = k[1:] == k[:-1]
+        assert np.all(v[1:][tie] > v[:-1][tie])
+        uk, uv = d["unsorted_keys"], d["unsorted_values"]
+        a = np.lexsort((uv, uk))
+        assert np.array_equal(uk[a], k) and np.array_equal(uv[a].astype(np.int64), v)
+        T = fr.num_tiles
+        r = d["ranges"].astype(np.int64)
+        tiles = (k >> np.uint64(32)).astype(np.int64)
+        per_tile = np.bincount(tiles, minlength=T) if m else np.zeros(T, np.int64)
+        assert (r[:, 1] - r[:, 0] == per_tile).all()
+        assert (r[per_tile == 0] == 0).all()
+        nz = np.nonzero(per_tile)[0]
+        if len(nz):
+            assert r[nz[0], 0] == 0 and r[nz[-1], 1] == m
+            assert (r[nz[1:], 0] == r[nz[:-1], 1]).all()
+            for t in nz[:: max(1, len(nz) // 50)]:
+                assert (tiles[r[t, 0]:r[t, 1]] == t).all()
+
+
+def check_float_order(samples: int = 10_000_000):
+    """For positive finite float32 a, b: a < b iff bits(a) < bits(b).  This
+    is the premise that lets the key carry raw depth bits."""
+    rng = np.random.default_rng(3)
+    u = rng.integers(1, 0x7F800000, size=(samples, 2), dtype=np.uint32)
+    f = u.view(np.float32)
+    assert np.all(np.isfinite(f)) and np.all(f > 0)
+    assert np.array_equal(f[:, 0] < f[:, 1], u[:, 0] < u[:, 1])
+    edge = np.array([1e-45, 1.17549435e-38, 1.1754942e-38, 1.0, np.nextafter(np.float32(1), 2),
+                     3.4028235e38, np.nextafter(np.float32(3.4028235e38), 0)], dtype=np.float32)
+    eb = edge.view(np.uint32)
+    for i in range(len(edge)):
+        for j in range(len(edge)):
+            assert (edge[i] < edge[j]) == (eb[i] < eb[j])
+
+
+ALL_CHECKS = (check_golden, check_count_and_duplicate_bruteforce, check_special_cases,
+              check_validity, check_scan, check_sort)
+
+
+def run_all(O) -> list[str]:
+    """Names of the checks that fail for oracle ``O``."""
+    failed = []
+    for check in ALL_CHECKS:
+        try:
+            if check is check_count_and_duplicate_bruteforce:
+                check(O, seeds=range(60))
+            else:
+                check(O)
+        except AssertionError:
+            failed.append(check.__name__)
+    return failed
+
+
+if __name__ == "__main__":  # run every check against the library named on the command line
+    import sys
+    from oracle import oracle as _O
+    print(json.dumps(run_all(_O.Oracle(_O.load(sys.argv[1])))))
