@@ -1,0 +1,415 @@
+#!/usr/bin/env python3
+"""Throughput of the 3DGS tile depth sort on GB300.
+
+A step is one whole frame through tdgs_sort_frame: tile count + scan,
+duplication, the stable radix sort and the tile ranges, on the
+1,000,000-Gaussian 1280x720 workload (3,600 tiles).  The metric is
+Gaussian-tile pairs sorted per second.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank sorts its own frame (seed = rank): frames are
+independent, so the work is replicated, not exchanged (weak scaling).
+`--impl reference` times the CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gaussian-tile pairs sorted/s, % HBM roofline; p50/p99 ms batched vs plain"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        time.sleep(0.3)
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, names = [], [], set()
+        keys = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, v in zip(keys, f[5:9]):
+                if v.lower().startswith("active"):
+                    names.add(k)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(names),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel: str):
+    """Per-launch DRAM traffic of `kernel` from the committed ncu summary,
+    if the kernel source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    items = re.search(r"items_per_launch:\s*([0-9]+)", text)
+    src = os.path.join(ROOT, "paper_2511_16298_gb300", "csrc", "sort_kernels.cu")
+    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if not (sha and tr) or sha.group(1) != cur:
+        return None
+    return float(tr.group(1)), int(items.group(1)) if items else None
+
+
+def algorithmic_bytes(kernel: str, items: int, n: int, m: int, tiles: int) -> float:
+    """Minimum DRAM bytes of one launch (reads + writes), per kernel."""
+    if kernel == "scan":            # records in (16 B), offsets out (4 B)
+        return 20.0 * items
+    if kernel == "count_tiles":
+        return 20.0 * items
+    if kernel == "duplicate_keys":  # records + offsets in, 12 B per pair out
+        return 20.0 * items + 12.0 * m
+    if kernel == "radix_upfront_hist":
+        return 8.0 * items
+    if kernel == "radix_onesweep_pass":  # 12 B read + 12 B written per pair
+        return 24.0 * items
+    if kernel == "tile_ranges":
+        return 8.0 * items + 8.0 * tiles
+    return 0.0
+
+
+# --------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank, dist):
+    import torch
+
+    from paper_2511_16298_gb300 import build, synth, tdgs
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    fr = synth.frame_scene(seed=rank)
+    n, W, H = fr.n, fr.width, fr.height
+    T = fr.num_tiles
+    g = tdgs.records_to_tensor(fr.gaussians, dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ctx = tdgs.Context(local_rank)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        ctx.sort_frame(g, W, H)
+        flush.zero_()
+    ctx.sync()
+    _, _, _, m = ctx.sort_frame(g, W, H)
+    ctx.sync()
+
+    # ---- timed region: K whole frames, device-resident inputs
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    ctx.enable_timing(True)
+    launches0 = ctx.launches
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local_rank) as clk:
+        t0 = time.perf_counter()
+        for a, b in ev:
+            a.record(stream)
+            ctx.sort_frame(g, W, H)
+            b.record(stream)
+            flush.zero_()
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+    ctx.sync()
+    if dist:
+        dist.barrier()
+    launches = ctx.launches - launches0
+    ktimes = ctx.kernel_times()
+    ctx.enable_timing(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_s = sum(step_ms) / 1e3
+    pairs = m * args.steps
+    if dist:
+        t = torch.tensor([dev_s, float(pairs)], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+        dev_s_max, pairs_all = float(tmax[0]), float(t[1])
+    else:
+        dev_s_max, pairs_all = dev_s, float(pairs)
+    value = pairs_all / dev_s_max
+
+    # ---- per-kernel live timings -> roofline of the dominant kernel
+    peak, peak_kind = measured_peaks()
+    kernels = {}
+    for name, d in ktimes.items():
+        per_launch_items = d["items"] / max(1, d["launches"])
+        ms = d["ms"] / max(1, d["launches"])
+        ab = algorithmic_bytes(name, per_launch_items, n, m, T)
+        kernels[name] = {"launches": d["launches"], "avg_ms": round(ms, 5),
+                         "share": None, "gbs": round(ab / (ms * 1e-3) / 1e9, 1) if ms > 0 else None}
+    tot_ms = sum(d["ms"] for d in ktimes.values())
+    for name, d in ktimes.items():
+        kernels[name]["share"] = round(d["ms"] / tot_ms, 4) if tot_ms else None
+    dom = max(ktimes, key=lambda k: ktimes[k]["ms"]) if ktimes else None
+    roof = None
+    if dom:
+        d = ktimes[dom]
+        per_items = d["items"] / d["launches"]
+        ms = d["ms"] / d["launches"]
+        ab = algorithmic_bytes(dom, per_items, n, m, T)
+        ach = ab / (ms * 1e-3) / 1e9
+        tr = profiled_traffic(dom)
+        traffic = None
+        if tr is not None:
+            tb, titems = tr
+            traffic = tb * (per_items / titems) if titems else tb
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": ab,
+                "traffic": round(traffic) if traffic is not None else None}
+
+    # ---- sort-only (tdgs_sort_pairs) on this frame's pairs
+    sort_only = None
+    if not args.no_sort_only:
+        counts = ctx.count_tiles(g, W, H)
+        offs, tot = ctx.scan(counts)
+        k0, v0 = ctx.duplicate_keys(g, offs, W, H, m)
+        ka, va = torch.empty_like(k0), torch.empty_like(v0)
+        kw, vw = torch.empty_like(k0), torch.empty_like(v0)
+        ctx.sync()
+        tb = fr.tile_bits
+        sev = []
+        ctx.enable_timing(True)
+        for i in range(args.warmup + args.steps):
+            kw.copy_(k0)
+            vw.copy_(v0)
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.sort_pairs(kw, vw, tb, tdgs.SORT_DEPTH_POSITIVE, ka, va)
+            b.record(stream)
+            if i >= args.warmup:
+                sev.append((a, b))
+        torch.cuda.synchronize(dev)
+        ctx.sync()
+        skt = ctx.kernel_times()
+        ctx.enable_timing(False)
+        sms = [a.elapsed_time(b) for a, b in sev]
+        passes = skt.get("radix_onesweep_pass", {}).get("launches", 0) // (args.warmup + args.steps)
+        sbytes = m * (8 + 24 * passes)
+        smean = statistics.mean(sms)
+        op = skt.get("radix_onesweep_pass")
+        sort_only = {"pairs_per_s": m / (smean * 1e-3), "ms_mean": round(smean, 4),
+                     "ms_p50": round(statistics.median(sms), 4), "passes": passes,
+                     "algorithmic_bytes": sbytes,
+                     "achieved_gbs": round(sbytes / (smean * 1e-3) / 1e9, 1),
+                     "frac": round(sbytes / (smean * 1e-3) / 1e9 / peak, 4),
+                     "pass_avg_ms": round(op["ms"] / op["launches"], 5) if op else None,
+                     "pass_frac": round(24.0 * op["items"] / op["launches"] / (op["ms"] / op["launches"] * 1e-3)
+                                        / 1e9 / peak, 4) if op else None}
+        del k0, v0, ka, va, kw, vw
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_g = torch.from_numpy(np.ascontiguousarray(fr.gaussians).view(np.int32).reshape(-1, 4)).pin_memory()
+        d_g = torch.empty_like(h_g, device=dev)
+        h_k = torch.empty(m + (1 << 20), dtype=torch.int64).pin_memory()
+        h_v = torch.empty(m + (1 << 20), dtype=torch.int32).pin_memory()
+        h_r = torch.empty((T, 2), dtype=torch.int32).pin_memory()
+        for i in range(args.warmup + args.steps):
+            if i == args.warmup:
+                torch.cuda.synchronize(dev)
+                if dist:
+                    dist.barrier()
+                te = time.perf_counter()
+                pairs_e2e = 0
+            d_g.copy_(h_g, non_blocking=True)
+            k, v, r, mm = ctx.sort_frame(d_g, W, H)
+            h_k[:mm].copy_(k, non_blocking=True)
+            h_v[:mm].copy_(v, non_blocking=True)
+            h_r.copy_(r, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            if i >= args.warmup:
+                pairs_e2e += mm
+        e2e_s = time.perf_counter() - te
+        if dist:
+            t = torch.tensor([e2e_s, float(pairs_e2e)], dtype=torch.float64, device=dev)
+            dist.all_reduce(t[0:1], op=dist.ReduceOp.MAX)
+            dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+            e2e_s, pairs_e2e = float(t[0]), float(t[1])
+        e2e = {"value": pairs_e2e / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": 16 * n,
+               "d2h_bytes_per_step": 12 * m + 8 * T, "ms_per_step": round(e2e_s / args.steps * 1e3, 4)}
+        ok = (np.array_equal(h_v[:m].numpy(), v.cpu().numpy()))
+        if not ok:
+            raise RuntimeError("e2e copy mismatch")
+
+    ctx.close()
+    return {
+        "value": value, "ms_per_step": round(dev_s_max / args.steps * 1e3, 4),
+        "latency_ms": {"p50": round(statistics.median(step_ms), 4),
+                       "p99": round(float(np.percentile(step_ms, 99)), 4),
+                       "wall_ms_per_step": round(wall / args.steps * 1e3, 4)},
+        "pairs_per_frame": m, "n": n, "tiles": T, "kernels": kernels, "roofline": roof,
+        "sort_pairs": sort_only, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_baseline(frame, reps: int):
+    from oracle import oracle as O
+    O.build()
+    t = []
+    m = 0
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        d = O.sort_frame(frame.gaussians, frame.width, frame.height)
+        t.append(time.perf_counter() - t0)
+        m = d["m"]
+    return m, t
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sort-only", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-reps", type=int, default=5)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2511_16298_gb300 import synth
+
+    if args.impl == "reference":
+        # The CPU oracle as the reference arm: rank 0 only, each step the
+        # oracle on a bounded sample of the same workload.
+        if rank != 0:
+            return
+        fr = synth.frame_scene(seed=0)
+        sample = synth.Frame(fr.width, fr.height, fr.gaussians[:250_000].copy(), "sample")
+        m, _ = oracle_baseline(sample, args.warmup)
+        m, t = oracle_baseline(sample, args.steps)
+        v = m * len(t) / sum(t)
+        desc = ("CPU oracle, 1 thread, per step the first 250,000 Gaussians of the "
+                "1M-Gaussian 1280x720 frame (%d pairs)" % m)
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(sum(t) / len(t) * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "scene-1M sample: 250,000 Gaussians, 1280x720, 3600 tiles"},
+            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}))
+        return
+
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist = tdist
+    res = run_ours(args, rank, world, local_rank, dist)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        fr = synth.frame_scene(seed=0)
+        m, t = oracle_baseline(fr, args.cpu_reps)
+        cpu = {"value": m * len(t) / sum(t), "unit": "pairs/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(t)} full frames of the 1M-Gaussian 1280x720 workload "
+                         f"({m} pairs each), single thread"}
+    if dist:
+        dist.barrier()
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": res["value"], "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": "scene-1M: 1,000,000 projected Gaussians, 1280x720 image, "
+                                   "3,600 16x16 tiles, 70% clustered means, seed=rank",
+                       "gaussians": res["n"], "pairs": res["pairs_per_frame"],
+                       "tiles": res["tiles"], "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (256 MiB memset, outside the step events)",
+                       "timing": "CUDA events around each tdgs_sort_frame call, summed"},
+            "latency_ms": res["latency_ms"],
+            "roofline": res["roofline"], "kernels": res["kernels"], "sort_pairs": res["sort_pairs"],
+            "cpu_baseline": cpu, "e2e": res["e2e"], "gpu_launches": res["gpu_launches"],
+            "clocks": res["clocks"],
+        }
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * tdgs.h -- C ABI of the GB300 (sm_103a) 3D Gaussian Splatting tile depth sort.
+ *
+ * The library computes the steps that sit between Preprocessing and
+ * Rendering in the 3DGS pipeline (arXiv 2511.16298, Sec. II-A
+ * "Duplication with Tiles" and "Sorting"; Table III shows PrefixSum feeding
+ * DuplicateWithTile; Table VI times Scan, Duplicate with tiles, Sorting and
+ * Identify Range as separate stages):
+ *
+ *   1. tdgs_count_tiles    tiles touched by each projected Gaussian
+ *   2. tdgs_scan           exclusive prefix sum of those counts
+ *   3. tdgs_duplicate_keys one (tile << 32 | depth bits, index) pair per
+ *                          Gaussian-tile instance
+ *   4. tdgs_sort_pairs     stable sort of the pairs by key (tile, then depth)
+ *   5. tdgs_tile_ranges    [start, end) of every tile in the sorted list
+ *   +  tdgs_sort_frame     all five steps on context-owned buffers
+ *   +  tdgs_sort_views     many views of one scene in one batched call
+ *
+ * Conventions shared by every call
+ *   - Data pointers are DEVICE pointers unless a parameter says "host".
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream).  The caller owns inputs and outputs of the per-step
+ *     calls and keeps them alive until the stream has finished the work.
+ *   - A call returns TDGS_OK or the first error it detects on the host
+ *     (NULL pointer with a non-zero size, misaligned pointer, zero image
+ *     size, out-of-range parameter, CUDA launch failure).  No call throws,
+ *     aborts or prints.
+ *   - Errors that only the GPU can see (an invalid depth or mean on a
+ *     visible Gaussian, a pair count above 2^32-1, a key wider than the
+ *     declared bits, a pair written beyond the given capacity, a
+ *     cross-block wait that exceeded its iteration bound) are latched in
+ *     the context and returned by the next tdgs_context_sync() or
+ *     tdgs_sort_frame() on that context, which also clears them.
+ *   - n = 0 and m = 0 are valid everywhere.
+ *   - A context may be used from one host thread and one stream at a time;
+ *     use one context per concurrent stream.
+ */
+#ifndef TDGS_H_
+#define TDGS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TDGS_OK = 0,
+  TDGS_ERR_INVALID_ARGUMENT = 1, /* bad pointer/size/flag, or invalid Gaussian */
+  TDGS_ERR_OUT_OF_MEMORY = 2,    /* device allocation failed                  */
+  TDGS_ERR_OVERFLOW = 3,         /* pair count above 2^32 - 1                 */
+  TDGS_ERR_CUDA = 4,             /* a CUDA runtime call failed                */
+  TDGS_ERR_TIMEOUT = 5,          /* a bounded cross-block wait gave up        */
+  TDGS_ERR_CAPACITY = 6          /* output capacity smaller than required     */
+} tdgs_status;
+
+/* One projected Gaussian, 16 bytes, 16-byte aligned in arrays: the packing
+ * of Table IV, Group 1 (2D mean in pixels, view depth, pixel radius).
+ * radius <= 0 marks a culled Gaussian. */
+typedef struct {
+  float x, y;
+  float depth;
+  int32_t radius;
+} tdgs_gaussian2d;
+
+/* Image size in pixels; tiles are 16x16, partial edge tiles count. */
+typedef struct {
+  uint32_t width, height;
+} tdgs_frame;
+
+/* Tile range in the sorted list; an empty tile is {0, 0}. */
+typedef struct {
+  uint32_t start, end;
+} tdgs_range;
+
+typedef struct tdgs_context tdgs_context; /* opaque */
+
+/* tdgs_sort_pairs flag: every key has bit 31 clear (true for keys made by
+ * tdgs_duplicate_keys, whose depths are positive), so the sort skips that
+ * bit.  A key with bit 31 set latches TDGS_ERR_INVALID_ARGUMENT. */
+#define TDGS_SORT_DEPTH_POSITIVE 1u
+
+/* ------------------------------------------------------------ context --- */
+
+/* Create a context on CUDA device `device`.  The context owns the scratch
+ * memory of the calls below (look-back status words, histograms, offsets)
+ * and the output buffers of tdgs_sort_frame, growing them on demand.
+ * *out is set to NULL on failure. */
+tdgs_status tdgs_context_create(tdgs_context** out, int device);
+
+/* Free every buffer the context owns.  NULL is a no-op.  The caller must
+ * ensure no work on the context is still running. */
+void tdgs_context_destroy(tdgs_context* ctx);
+
+/* Wait for `stream`, then return and clear the first device-latched error
+ * (TDGS_OK if none). */
+tdgs_status tdgs_context_sync(tdgs_context* ctx, void* stream);
+
+/* Static description of a status code; never NULL. */
+const char* tdgs_status_string(tdgs_status s);
+
+/* Human-readable detail of the last failure on this context ("" if none).
+ * Valid until the next call on the context. */
+const char* tdgs_last_error(const tdgs_context* ctx);
+
+/* Grid helpers: gx = ceil(width/16), gy = ceil(height/16), T = gx*gy and
+ * tile bits = ceil(log2 T) (0 when T = 1). */
+uint32_t tdgs_num_tiles(tdgs_frame f);
+uint32_t tdgs_tile_bits(tdgs_frame f);
+
+/* Tuning of the sort's digit passes (used by the autotuner; the paper has
+ * no counterpart).  Variant i is a compiled pass kernel with
+ * 2^bits digit bins, `threads` threads per block and `items` keys per
+ * thread.  tdgs_context_set_sort_variant(ctx, -1) restores the built-in
+ * choice; an index out of range returns TDGS_ERR_INVALID_ARGUMENT. */
+int tdgs_sort_variant_count(void);
+tdgs_status tdgs_sort_variant_info(int i, int* bits, int* threads, int* items);
+tdgs_status tdgs_context_set_sort_variant(tdgs_context* ctx, int variant);
+
+/* Tracing (the paper has no counterpart; its Table VI times each stage
+ * separately, which this reproduces on the GPU).  Every kernel launch made
+ * through a context increments a counter.  With timing enabled, the
+ * library brackets each launch with CUDA events on the launching stream;
+ * tdgs_context_kernel_times waits for those events and returns, per
+ * kernel name, the launches, the items processed (Gaussians or pairs) and
+ * the summed device time in ms, then clears the record.  It writes at most
+ * `max` entries and returns how many kernels have data (or -1 on error).
+ * Enabling or disabling timing clears the record. */
+typedef struct {
+  const char* name; /* static string */
+  uint64_t launches;
+  uint64_t items;
+  double total_ms;
+} tdgs_kernel_time;
+
+uint64_t tdgs_context_launch_count(const tdgs_context* ctx);
+tdgs_status tdgs_context_enable_timing(tdgs_context* ctx, int enable);
+int tdgs_context_kernel_times(tdgs_context* ctx, tdgs_kernel_time* out, int max);
+
+/* ------------------------------------------------------- the five steps --- */
+
+/* Step 1 (Sec. II-A: each projected Gaussian is represented by the
+ * axis-aligned box of its footprint and touches every 16x16 tile the box
+ * intersects).  For i < n: tiles_touched[i] = (x1-x0)*(y1-y0) where, in
+ * float32 and in this order, x0 = floor((x - r) / 16),
+ * x1 = floor(((x + r) + 15) / 16), likewise for y, each clamped to
+ * [0, gx] (resp. [0, gy]); 0 when radius <= 0 or the box misses the image.
+ * g: n records (16-byte aligned); tiles_touched: n uint32.
+ * A visible Gaussian (radius > 0) with a non-finite mean, or with a
+ * non-empty box and a depth that is not finite and > 0, latches
+ * TDGS_ERR_INVALID_ARGUMENT (its count is written as 0). */
+tdgs_status tdgs_count_tiles(tdgs_context* ctx, const tdgs_gaussian2d* g, uint32_t n,
+                             tdgs_frame f, uint32_t* tiles_touched, void* stream);
+
+/* Step 2 (Table III, PrefixSum over Tiles_touched): offsets[i] = sum of
+ * counts[j] for j < i; *total_dev (device, one uint32) = sum of all counts.
+ * A sum above 2^32-1 latches TDGS_ERR_OVERFLOW (total_dev then holds
+ * 0xFFFFFFFF).  counts and offsets may not overlap.  total_dev may be NULL. */
+tdgs_status tdgs_scan(tdgs_context* ctx, const uint32_t* counts, uint32_t n,
+                      uint32_t* offsets, uint32_t* total_dev, void* stream);
+
+/* Step 3 (Sec. II-A: Gaussians are duplicated across the tiles their box
+ * intersects, forming key-value pairs keyed by tile and depth).  Gaussian i
+ * writes its pairs at offsets[i], offsets[i]+1, ... with rows (ty) outer and
+ * columns (tx) inner:
+ *   keys[k]   = ((uint64_t)(ty*gx + tx) << 32) | float32 bit pattern of depth
+ *   values[k] = i
+ * offsets must be the exclusive scan of the step-1 counts of the same g and
+ * f.  m_capacity = length of keys and values; a pair that would land at or
+ * beyond it is dropped and latches TDGS_ERR_CAPACITY.
+ * keys 8-byte aligned, values 4-byte aligned. */
+tdgs_status tdgs_duplicate_keys(tdgs_context* ctx, const tdgs_gaussian2d* g,
+                                const uint32_t* offsets, uint32_t n, tdgs_frame f,
+                                uint64_t* keys, uint32_t* values, uint32_t m_capacity,
+                                void* stream);
+
+/* Step 4 (Sec. II-A Sorting: by tile index, then by depth within a tile).
+ * Stable ascending sort of the m pairs by key.  Only key bits [0, 32 +
+ * tile_bits) take part (bit 31 is skipped with TDGS_SORT_DEPTH_POSITIVE);
+ * a key with a higher bit set latches TDGS_ERR_INVALID_ARGUMENT.
+ * keys/values are the input; keys_alt/values_alt are caller-provided
+ * buffers of the same length.  The sort ping-pongs between the two, and
+ * *result_in_alt (host int) tells where the sorted pairs are: 0 = keys/
+ * values, 1 = keys_alt/values_alt.  The other pair of buffers is clobbered.
+ * tile_bits <= 32. */
+tdgs_status tdgs_sort_pairs(tdgs_context* ctx, uint64_t* keys, uint32_t* values,
+                            uint64_t* keys_alt, uint32_t* values_alt, uint32_t m,
+                            uint32_t tile_bits, uint32_t flags, int* result_in_alt,
+                            void* stream);
+
+/* Step 5 (Identify Range, Sec. IV-B and Table VI): ranges[t] = first and
+ * one-past-last position of tile t (= key >> 32) in sorted_keys, {0, 0} for
+ * a tile with no pairs.  sorted_keys must be ordered by tile.  A tile id
+ * >= num_tiles latches TDGS_ERR_INVALID_ARGUMENT.  ranges: num_tiles
+ * entries, 8-byte aligned. */
+tdgs_status tdgs_tile_ranges(tdgs_context* ctx, const uint64_t* sorted_keys, uint32_t m,
+                             uint32_t num_tiles, tdgs_range* ranges, void* stream);
+
+/* Steps 1-5 fused.  Writes host *m_out (pair count), and *sorted_keys,
+ * *sorted_values (m entries) and *ranges (tdgs_num_tiles(f) entries) as
+ * device pointers into buffers owned by the context, valid until the next
+ * call on the context or its destruction.  The call waits once for the
+ * pair count (a 4-byte device-to-host read), so it returns the errors of
+ * steps 1-2 directly; errors of later steps are returned by the next
+ * tdgs_context_sync or tdgs_sort_frame. */
+tdgs_status tdgs_sort_frame(tdgs_context* ctx, const tdgs_gaussian2d* g, uint32_t n,
+                            tdgs_frame f, const uint64_t** sorted_keys,
+                            const uint32_t** sorted_values, const tdgs_range** ranges,
+                            uint32_t* m_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDGS_H_ */

@@ -1,0 +1,182 @@
+// Internal declarations shared by the CUDA translation units of libtdgs.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "tdgs.h"
+
+namespace tdgs {
+
+constexpr int kTile = 16;             // 16x16-pixel screen tiles (Sec. II-A)
+constexpr uint32_t kSpinLimit = 1u << 21;  // bounded cross-block waits (~0.1-1 s)
+
+// ---------------------------------------------------------------- geometry
+struct FrameGeom {
+  int32_t gx, gy;    // tiles per row / column
+  float gxf, gyf;    // the same as floats, for clamping
+};
+
+inline FrameGeom make_geom(tdgs_frame f) {
+  FrameGeom g;
+  g.gx = static_cast<int32_t>((f.width + kTile - 1) / kTile);
+  g.gy = static_cast<int32_t>((f.height + kTile - 1) / kTile);
+  g.gxf = static_cast<float>(g.gx);
+  g.gyf = static_cast<float>(g.gy);
+  return g;
+}
+
+// Outcome of the tile test for one Gaussian.
+struct TileRect {
+  int32_t x0, y0, x1, y1;  // covered tiles [x0,x1) x [y0,y1)
+  uint32_t count;          // (x1-x0)*(y1-y0), 0 when culled/off-screen/invalid
+  bool invalid;            // visible but with a bad mean or depth
+};
+
+// Tile rectangle of a projected Gaussian (Sec. II-A: the footprint's
+// axis-aligned box, intersected with the 16x16 tile grid).  Box edges are
+// rounded float32 values taken in a fixed order, with no contraction:
+// x0 = floor((x - r) / 16), x1 = floor(((x + r) + 15) / 16), likewise for y,
+// each clamped to [0, grid].  Multiplying by 1/16 is exact.
+__device__ __forceinline__ TileRect tile_rect(float x, float y, float depth, int32_t r,
+                                              const FrameGeom& fg) {
+  TileRect q;
+  q.x0 = q.y0 = q.x1 = q.y1 = 0;
+  q.count = 0;
+  q.invalid = false;
+  if (r <= 0) return q;
+  if (!isfinite(x) || !isfinite(y)) {
+    q.invalid = true;
+    return q;
+  }
+  const float rf = __int2float_rn(r);
+  const float sx0 = __fsub_rn(x, rf);
+  const float sx1 = __fadd_rn(__fadd_rn(x, rf), 15.0f);
+  const float sy0 = __fsub_rn(y, rf);
+  const float sy1 = __fadd_rn(__fadd_rn(y, rf), 15.0f);
+  const float fx0 = fminf(fmaxf(floorf(__fmul_rn(sx0, 0.0625f)), 0.0f), fg.gxf);
+  const float fx1 = fminf(fmaxf(floorf(__fmul_rn(sx1, 0.0625f)), 0.0f), fg.gxf);
+  const float fy0 = fminf(fmaxf(floorf(__fmul_rn(sy0, 0.0625f)), 0.0f), fg.gyf);
+  const float fy1 = fminf(fmaxf(floorf(__fmul_rn(sy1, 0.0625f)), 0.0f), fg.gyf);
+  q.x0 = __float2int_rz(fx0);
+  q.x1 = __float2int_rz(fx1);
+  q.y0 = __float2int_rz(fy0);
+  q.y1 = __float2int_rz(fy1);
+  if (q.x1 <= q.x0 || q.y1 <= q.y0) {
+    q.x0 = q.y0 = q.x1 = q.y1 = 0;
+    return q;
+  }
+  // Keys carry raw depth bits: only finite depths > +0.0 keep their order.
+  if (!(isfinite(depth) && depth > 0.0f)) {
+    q.invalid = true;
+    q.x0 = q.y0 = q.x1 = q.y1 = 0;
+    return q;
+  }
+  q.count = static_cast<uint32_t>(q.x1 - q.x0) * static_cast<uint32_t>(q.y1 - q.y0);
+  return q;
+}
+
+__device__ __forceinline__ TileRect tile_rect(const float4 rec, const FrameGeom& fg) {
+  return tile_rect(rec.x, rec.y, rec.z, __float_as_int(rec.w), fg);
+}
+
+// ------------------------------------------------------------ device sync
+// The first non-zero code wins; later errors are dropped.
+__device__ __forceinline__ void latch_error(uint32_t* err, uint32_t code) {
+  atomicCAS(err, 0u, code);
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// ------------------------------------------------------------- host side
+// Per-call status helpers used by the API layer.
+struct Scratch {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+// Launchers (each returns a cudaError_t from the launch).
+cudaError_t launch_count_tiles(const float4* g, uint32_t n, FrameGeom fg, uint32_t* counts,
+                               uint32_t* err, cudaStream_t s);
+
+// Decoupled look-back exclusive scan.  With recs != nullptr the counts are
+// computed from the records (count and scan fused); otherwise read from
+// counts.  status: one uint64 per 2048-item block, zeroed by the caller.
+constexpr uint32_t kScanTileItems = 2048;
+cudaError_t launch_scan(const uint32_t* counts, const float4* recs, FrameGeom fg, uint32_t n,
+                        uint32_t* offsets, uint64_t* status, uint32_t* ticket,
+                        uint32_t ticket_base, uint64_t* total64, uint32_t* total32,
+                        uint32_t* err, cudaStream_t s);
+
+cudaError_t launch_duplicate(const float4* g, const uint32_t* offsets, uint32_t n,
+                             FrameGeom fg, uint64_t* keys, uint32_t* values, uint32_t cap,
+                             uint32_t* err, cudaStream_t s);
+
+cudaError_t launch_tile_ranges(const uint64_t* keys, uint32_t m, uint32_t num_tiles,
+                               uint2* ranges, uint32_t* err, cudaStream_t s);
+
+// ----------------------------------------------------------- radix sort
+constexpr int kMaxPasses = 8;
+constexpr uint32_t kPortionMax = 1u << 26;  // look-back values must fit 27 bits
+
+struct SortPlan {
+  uint32_t key_bits;   // sorted bits of the transformed key
+  uint32_t passes;     // number of digit passes
+  uint32_t digit_bits; // bins = 1 << digit_bits
+  uint32_t shift[kMaxPasses];
+  uint32_t mask[kMaxPasses];
+  bool drop31;         // transformed key skips bit 31
+  uint64_t bad_mask;   // key bits that must be zero
+  uint32_t tile_keys;  // keys per CTA tile of a pass
+  uint32_t portion;    // keys per look-back portion
+  uint32_t portions;
+  uint32_t variant;    // which compiled pass kernel
+};
+
+// Tunable pass-kernel configurations (digit bits, threads, items/thread).
+struct PassVariant {
+  int bits, threads, items;
+};
+int num_pass_variants();
+PassVariant pass_variant(int i);
+int default_pass_variant(uint32_t digit_bits);
+
+SortPlan make_sort_plan(uint32_t m, uint32_t tile_bits, uint32_t flags, int variant_override);
+
+cudaError_t launch_upfront_hist(const uint64_t* keys, uint32_t m, const SortPlan& plan,
+                                uint32_t* hist, uint32_t* err, cudaStream_t s);
+cudaError_t launch_digit_offsets(const uint32_t* hist, const SortPlan& plan, uint32_t* offs,
+                                 cudaStream_t s);
+cudaError_t launch_onesweep_pass(const SortPlan& plan, uint32_t pass, uint32_t portion,
+                                 const uint64_t* kin, const uint32_t* vin, uint64_t* kout,
+                                 uint32_t* vout, uint32_t m, const uint32_t* digit_off,
+                                 uint32_t* status, uint32_t epoch, uint32_t* ticket,
+                                 uint32_t ticket_base, uint32_t* err, uint32_t* grid_out,
+                                 cudaStream_t s);
+size_t onesweep_status_bytes(const SortPlan& plan);
+
+}  // namespace tdgs

@@ -1,0 +1,276 @@
+"""Python binding of libtdgs (the C ABI in ``include/tdgs.h``).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+Tensors are torch CUDA tensors; their device pointers and the current
+torch stream are handed to the C calls.  If the shared library has not been
+built, importing works but the first call raises -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+OK = 0
+INVALID_ARGUMENT = 1
+OUT_OF_MEMORY = 2
+OVERFLOW = 3
+CUDA_ERROR = 4
+TIMEOUT = 5
+CAPACITY = 6
+SORT_DEPTH_POSITIVE = 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class TdgsError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        name = lib().tdgs_status_string(status).decode() if _lib else str(status)
+        super().__init__(f"{where}: {name} ({status}){': ' + detail if detail else ''}")
+
+
+class _Range(ctypes.Structure):
+    _fields_ = [("start", ctypes.c_uint32), ("end", ctypes.c_uint32)]
+
+
+class _Frame(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_uint32), ("height", ctypes.c_uint32)]
+
+
+class _KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_uint64),
+                ("items", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libtdgs.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    f"{path} is missing: build the CUDA library first "
+                    "(python -c 'import __graft_entry__ as g; g.build()')")
+            L = ctypes.CDLL(path)
+            P, u32, i32, st = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int, ctypes.c_int
+            F = _Frame
+            sig = {
+                "tdgs_context_create": ([ctypes.POINTER(P), i32], st),
+                "tdgs_context_destroy": ([P], None),
+                "tdgs_context_sync": ([P, P], st),
+                "tdgs_status_string": ([i32], ctypes.c_char_p),
+                "tdgs_last_error": ([P], ctypes.c_char_p),
+                "tdgs_num_tiles": ([F], u32),
+                "tdgs_tile_bits": ([F], u32),
+                "tdgs_sort_variant_count": ([], i32),
+                "tdgs_sort_variant_info": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                            ctypes.POINTER(i32)], st),
+                "tdgs_context_set_sort_variant": ([P, i32], st),
+                "tdgs_context_launch_count": ([P], ctypes.c_uint64),
+                "tdgs_context_enable_timing": ([P, i32], st),
+                "tdgs_context_kernel_times": ([P, ctypes.POINTER(_KernelTime), i32], i32),
+                "tdgs_count_tiles": ([P, P, u32, F, P, P], st),
+                "tdgs_scan": ([P, P, u32, P, P, P], st),
+                "tdgs_duplicate_keys": ([P, P, P, u32, F, P, P, u32, P], st),
+                "tdgs_sort_pairs": ([P, P, P, P, P, u32, u32, u32, ctypes.POINTER(i32), P], st),
+                "tdgs_tile_ranges": ([P, P, u32, u32, P, P], st),
+                "tdgs_sort_frame": ([P, P, u32, F, ctypes.POINTER(P), ctypes.POINTER(P),
+                                     ctypes.POINTER(P), ctypes.POINTER(u32), P], st),
+            }
+            for name, (args, res) in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(0)
+    return ctypes.c_void_p(t.data_ptr()) if t.numel() else ctypes.c_void_p(0)
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def records_to_tensor(g: np.ndarray, device="cuda") -> torch.Tensor:
+    """16-byte Gaussian records (numpy) -> int32 CUDA tensor of shape (n, 4)."""
+    a = np.ascontiguousarray(g).view(np.int32).reshape(-1, 4)
+    return torch.from_numpy(a).to(device)
+
+
+def num_tiles(width: int, height: int) -> int:
+    return int(lib().tdgs_num_tiles(_Frame(width, height)))
+
+
+def tile_bits(width: int, height: int) -> int:
+    return int(lib().tdgs_tile_bits(_Frame(width, height)))
+
+
+def sort_variants() -> list[tuple[int, int, int]]:
+    L = lib()
+    out = []
+    for i in range(L.tdgs_sort_variant_count()):
+        b, t, it = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        L.tdgs_sort_variant_info(i, ctypes.byref(b), ctypes.byref(t), ctypes.byref(it))
+        out.append((b.value, t.value, it.value))
+    return out
+
+
+class _DeviceView:
+    """Zero-copy view of a context-owned device buffer (CUDA array interface)."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {
+            "shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3,
+            "strides": None, "stream": None}
+
+
+def _view(ptr: int, n: int, dtype: torch.dtype, device) -> torch.Tensor:
+    ts = {torch.int64: "<i8", torch.int32: "<i4"}[dtype]
+    if n == 0 or not ptr:
+        return torch.empty(0, dtype=dtype, device=device)
+    return torch.as_tensor(_DeviceView(ptr, n, ts), device=device)
+
+
+class Context:
+    """One library context (scratch buffers, latched device errors) bound to
+    one CUDA device.  Use one context per concurrent stream."""
+
+    def __init__(self, device: int | torch.device = 0):
+        if isinstance(device, torch.device):
+            device = device.index or 0
+        self.device = torch.device("cuda", device)
+        self._h = ctypes.c_void_p()
+        st = lib().tdgs_context_create(ctypes.byref(self._h), int(device))
+        if st != OK:
+            raise TdgsError(st, "tdgs_context_create")
+
+    def close(self):
+        if self._h:
+            torch.cuda.synchronize(self.device)
+            lib().tdgs_context_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.tdgs_context_destroy(self._h)
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------ helpers
+    def _check(self, st: int, where: str):
+        if st != OK:
+            raise TdgsError(st, where, lib().tdgs_last_error(self._h).decode())
+
+    def sync(self):
+        """Wait for the current stream; raise the first device-latched error."""
+        self._check(lib().tdgs_context_sync(self._h, _stream(self.device)), "tdgs_context_sync")
+
+    def set_sort_variant(self, variant: int):
+        self._check(lib().tdgs_context_set_sort_variant(self._h, int(variant)),
+                    "tdgs_context_set_sort_variant")
+
+    @property
+    def launches(self) -> int:
+        """Kernels launched through this context so far."""
+        return int(lib().tdgs_context_launch_count(self._h))
+
+    def enable_timing(self, on: bool = True):
+        self._check(lib().tdgs_context_enable_timing(self._h, int(on)), "tdgs_context_enable_timing")
+
+    def kernel_times(self) -> dict:
+        """{kernel: {"launches", "items", "ms"}} since the last read (waits
+        for the recorded events)."""
+        buf = (_KernelTime * 16)()
+        n = lib().tdgs_context_kernel_times(self._h, buf, 16)
+        if n < 0:
+            raise TdgsError(INVALID_ARGUMENT, "tdgs_context_kernel_times")
+        return {buf[i].name.decode(): {"launches": int(buf[i].launches), "items": int(buf[i].items),
+                                       "ms": float(buf[i].total_ms)} for i in range(min(n, 16))}
+
+    # ------------------------------------------------------------ the steps
+    def count_tiles(self, g: torch.Tensor, width: int, height: int, out=None) -> torch.Tensor:
+        n = g.shape[0]
+        out = torch.empty(n, dtype=torch.int32, device=self.device) if out is None else out
+        self._check(lib().tdgs_count_tiles(self._h, _ptr(g), n, _Frame(width, height), _ptr(out),
+                                           _stream(self.device)), "tdgs_count_tiles")
+        return out
+
+    def scan(self, counts: torch.Tensor, out=None, total=None):
+        n = counts.shape[0]
+        out = torch.empty(n, dtype=torch.int32, device=self.device) if out is None else out
+        total = torch.zeros(1, dtype=torch.int32, device=self.device) if total is None else total
+        self._check(lib().tdgs_scan(self._h, _ptr(counts), n, _ptr(out), _ptr(total),
+                                    _stream(self.device)), "tdgs_scan")
+        return out, total
+
+    def duplicate_keys(self, g, offsets, width, height, m, keys=None, values=None):
+        n = g.shape[0]
+        keys = torch.empty(m, dtype=torch.int64, device=self.device) if keys is None else keys
+        values = torch.empty(m, dtype=torch.int32, device=self.device) if values is None else values
+        self._check(lib().tdgs_duplicate_keys(self._h, _ptr(g), _ptr(offsets), n,
+                                              _Frame(width, height), _ptr(keys), _ptr(values),
+                                              min(m, keys.shape[0], values.shape[0]),
+                                              _stream(self.device)), "tdgs_duplicate_keys")
+        return keys, values
+
+    def sort_pairs(self, keys, values, tile_bits: int, flags: int = 0, keys_alt=None,
+                   values_alt=None):
+        """Sort in place through the alternate buffers; returns the
+        (keys, values) tensors that hold the sorted result."""
+        m = keys.shape[0]
+        keys_alt = torch.empty_like(keys) if keys_alt is None else keys_alt
+        values_alt = torch.empty_like(values) if values_alt is None else values_alt
+        alt = ctypes.c_int(0)
+        self._check(lib().tdgs_sort_pairs(self._h, _ptr(keys), _ptr(values), _ptr(keys_alt),
+                                          _ptr(values_alt), m, tile_bits, flags, ctypes.byref(alt),
+                                          _stream(self.device)), "tdgs_sort_pairs")
+        return (keys_alt, values_alt) if alt.value else (keys, values)
+
+    def tile_ranges(self, sorted_keys, num_tiles: int, m=None, out=None) -> torch.Tensor:
+        m = sorted_keys.shape[0] if m is None else m
+        out = torch.empty((num_tiles, 2), dtype=torch.int32, device=self.device) if out is None else out
+        self._check(lib().tdgs_tile_ranges(self._h, _ptr(sorted_keys), m, num_tiles, _ptr(out),
+                                           _stream(self.device)), "tdgs_tile_ranges")
+        return out
+
+    def sort_frame(self, g: torch.Tensor, width: int, height: int, copy: bool = False):
+        """All five steps.  Returns (keys, values, ranges, m); the tensors are
+        views of context buffers valid until the next call on this context
+        unless copy=True."""
+        n = g.shape[0]
+        kp, vp, rp = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        m = ctypes.c_uint32(0)
+        self._check(lib().tdgs_sort_frame(self._h, _ptr(g), n, _Frame(width, height),
+                                          ctypes.byref(kp), ctypes.byref(vp), ctypes.byref(rp),
+                                          ctypes.byref(m), _stream(self.device)), "tdgs_sort_frame")
+        T = num_tiles(width, height)
+        k = _view(kp.value or 0, m.value, torch.int64, self.device)
+        v = _view(vp.value or 0, m.value, torch.int32, self.device)
+        r = _view(rp.value or 0, 2 * T, torch.int32, self.device).view(T, 2)
+        if copy:
+            k, v, r = k.clone(), v.clone(), r.clone()
+        return k, v, r, int(m.value)

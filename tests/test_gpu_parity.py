@@ -1,0 +1,256 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Everything on the path is integer or a float32 computation with a pinned
+operation order, so the bar is bit-exact: counts, offsets, keys, values and
+ranges must be identical, and error statuses must agree.
+"""
+import functools
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2511_16298_gb300 import synth
+from paper_2511_16298_gb300 import tdgs as T
+from tests import oracle_pins as P
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2511_16298_gb300 import build
+    build.build()
+    c = T.Context(0)
+    yield c
+    c.close()
+
+
+def u64(t: torch.Tensor) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint64)
+
+
+def u32(t: torch.Tensor) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint32)
+
+
+@functools.lru_cache(maxsize=1)
+def frames_small():
+    out = [synth.frame_small(0), synth.frame_small(3, n=777, width=100, height=37)]
+    for s in range(6):
+        out.append(synth.frame_random(s, int(np.random.default_rng(s).integers(1, 9000)),
+                                      int(np.random.default_rng(s + 50).integers(1, 700)),
+                                      int(np.random.default_rng(s + 90).integers(1, 500)),
+                                      depth_ties=0.2 * (s % 2)))
+    for s in range(30):
+        g, W, H = P.tiny_frame(s)
+        out.append(synth.Frame(W, H, g, f"tiny{s}"))
+    out.append(synth.frame_random(9, 3000, 16, 16))         # one tile, 0 tile bits
+    out.append(synth.frame_random(10, 5000, 17, 1))         # 2 x 1 tiles
+    out.append(synth.frame_large(1, n=50_000, width=640, height=360))
+    return out
+
+
+# ------------------------------------------------------------------ steps
+@pytest.mark.parametrize("fi", range(41))
+def test_count_scan_duplicate(ctx, oracle, fi):
+    fr = frames_small()[fi]
+    g = T.records_to_tensor(fr.gaussians, DEV)
+    ref = oracle.sort_frame(fr.gaussians, fr.width, fr.height)
+    assert ref["status"] == 0
+    counts = ctx.count_tiles(g, fr.width, fr.height)
+    ctx.sync()
+    assert np.array_equal(u32(counts), ref["counts"])
+    offsets, total = ctx.scan(counts)
+    ctx.sync()
+    assert np.array_equal(u32(offsets), ref["offsets"])
+    assert int(u32(total)[0]) == ref["m"]
+    keys, values = ctx.duplicate_keys(g, offsets, fr.width, fr.height, ref["m"])
+    ctx.sync()
+    assert np.array_equal(u64(keys), ref["unsorted_keys"])
+    assert np.array_equal(u32(values), ref["unsorted_values"])
+    sk, sv = ctx.sort_pairs(keys, values, fr.tile_bits, T.SORT_DEPTH_POSITIVE)
+    ctx.sync()
+    assert np.array_equal(u64(sk), ref["keys"])
+    assert np.array_equal(u32(sv), ref["values"])
+    r = ctx.tile_ranges(sk, fr.num_tiles)
+    ctx.sync()
+    assert np.array_equal(u32(r), ref["ranges"])
+
+
+@pytest.mark.parametrize("n", [1, 2, 2047, 2048, 2049, 65536 + 7, 3_000_001])
+def test_scan_sizes(ctx, oracle, n):
+    rng = np.random.default_rng(n)
+    c = rng.integers(0, 1500, size=n).astype(np.uint32)
+    st, off, total = oracle.scan(c)
+    o, t = ctx.scan(torch.from_numpy(c.view(np.int32)).to(DEV))
+    ctx.sync()
+    assert np.array_equal(u32(o), off) and int(u32(t)[0]) == total
+
+
+def test_scan_overflow(ctx, oracle):
+    c = np.full(5000, 2**20, dtype=np.uint32)  # total 5000 * 2^20 > 2^32
+    st, _, total = oracle.scan(c)
+    assert st == P_OVERFLOW
+    o, t = ctx.scan(torch.from_numpy(c.view(np.int32)).to(DEV))
+    with pytest.raises(T.TdgsError) as e:
+        ctx.sync()
+    assert e.value.status == T.OVERFLOW
+    assert int(u32(t)[0]) == 0xFFFFFFFF
+
+
+P_OVERFLOW = 3
+
+
+@pytest.mark.parametrize("case", ["nan_depth", "zero_depth", "neg_zero_depth", "inf_x", "neg_depth"])
+def test_invalid_gaussian(ctx, oracle, case):
+    vals = {"nan_depth": (10.0, 10.0, float("nan")), "zero_depth": (10.0, 10.0, 0.0),
+            "neg_zero_depth": (10.0, 10.0, -0.0), "inf_x": (float("inf"), 10.0, 1.0),
+            "neg_depth": (10.0, 10.0, -2.0)}[case]
+    g = synth.records([5.0, vals[0], 30.0], [5.0, vals[1], 30.0], [1.0, vals[2], 2.0], [2, 3, 4])
+    st, _ = oracle.count_tiles(g, 64, 64)
+    assert st == 1
+    gt = T.records_to_tensor(g, DEV)
+    ctx.count_tiles(gt, 64, 64)
+    with pytest.raises(T.TdgsError) as e:
+        ctx.sync()
+    assert e.value.status == T.INVALID_ARGUMENT
+    with pytest.raises(T.TdgsError) as e:
+        ctx.sort_frame(gt, 64, 64)
+    assert e.value.status == T.INVALID_ARGUMENT
+    ctx.sync()  # error was cleared
+
+
+def _random_pairs(m, seed, key_bits, ties):
+    rng = np.random.default_rng(seed)
+    if ties:
+        pool = rng.integers(0, 1 << key_bits, size=max(1, m // 20), dtype=np.uint64)
+        k = pool[rng.integers(0, len(pool), size=m)]
+    else:
+        k = rng.integers(0, 1 << key_bits, size=m, dtype=np.uint64)
+    v = rng.permutation(m).astype(np.uint32)
+    return k, v
+
+
+@pytest.mark.parametrize("variant", range(7))
+@pytest.mark.parametrize("m,tile_bits,ties", [(1, 0, False), (4095, 8, True), (4096, 8, False),
+                                               (8193, 12, True), (100_003, 13, True),
+                                               (250_000, 32, False)])
+def test_sort_pairs_variants(ctx, oracle, variant, m, tile_bits, ties):
+    if variant >= len(T.sort_variants()):
+        pytest.skip("variant not compiled")
+    k, v = _random_pairs(m, m + variant, 32 + tile_bits if tile_bits < 32 else 63, ties)
+    if tile_bits == 32:
+        k |= np.uint64(1) << np.uint64(63)
+    _, rk, rv = oracle.sort_pairs(k, v)
+    ctx.set_sort_variant(variant)
+    try:
+        kt = torch.from_numpy(k.view(np.int64)).to(DEV)
+        vt = torch.from_numpy(v.view(np.int32)).to(DEV)
+        sk, sv = ctx.sort_pairs(kt, vt, tile_bits, 0)
+        ctx.sync()
+    finally:
+        ctx.set_sort_variant(-1)
+    assert np.array_equal(u64(sk), rk)
+    assert np.array_equal(u32(sv), rv)
+
+
+def test_sort_pairs_depth_flag_violation(ctx):
+    k = np.array([1, 2, 0x80000000], dtype=np.uint64)
+    v = np.arange(3, dtype=np.uint32)
+    ctx.sort_pairs(torch.from_numpy(k.view(np.int64)).to(DEV),
+                   torch.from_numpy(v.view(np.int32)).to(DEV), 4, T.SORT_DEPTH_POSITIVE)
+    with pytest.raises(T.TdgsError) as e:
+        ctx.sync()
+    assert e.value.status == T.INVALID_ARGUMENT
+
+
+def test_sort_pairs_key_too_wide(ctx):
+    k = np.array([1, 1 << 45], dtype=np.uint64)
+    v = np.arange(2, dtype=np.uint32)
+    ctx.sort_pairs(torch.from_numpy(k.view(np.int64)).to(DEV),
+                   torch.from_numpy(v.view(np.int32)).to(DEV), 8, 0)
+    with pytest.raises(T.TdgsError):
+        ctx.sync()
+
+
+def test_tile_ranges_bad_tile(ctx):
+    k = np.array([0, 1 << 32, 9 << 32], dtype=np.uint64)
+    ctx.tile_ranges(torch.from_numpy(k.view(np.int64)).to(DEV), 4)
+    with pytest.raises(T.TdgsError):
+        ctx.sync()
+
+
+# ------------------------------------------------------------ fused frame
+def _check_frame(ctx, oracle, fr):
+    ref = oracle.sort_frame(fr.gaussians, fr.width, fr.height)
+    assert ref["status"] == 0
+    g = T.records_to_tensor(fr.gaussians, DEV)
+    k, v, r, m = ctx.sort_frame(g, fr.width, fr.height)
+    ctx.sync()
+    assert m == ref["m"]
+    assert np.array_equal(u64(k), ref["keys"])
+    assert np.array_equal(u32(v), ref["values"])
+    assert np.array_equal(u32(r), ref["ranges"])
+    return m
+
+
+@pytest.mark.parametrize("fi", range(41))
+def test_sort_frame_small(ctx, oracle, fi):
+    _check_frame(ctx, oracle, frames_small()[fi])
+
+
+def test_sort_frame_edge_cases(ctx, oracle):
+    W, H = 300, 200
+    cases = {
+        "empty": synth.records([], [], [], []),
+        "all_culled": synth.records([10.0] * 50, [10.0] * 50, [1.0] * 50, [0] * 50),
+        "offscreen": synth.records([-500.0, 5000.0], [10.0, 10.0], [1.0, 1.0], [5, 5]),
+        "whole_screen": synth.records([150.0, 150.0], [100.0, 100.0], [3.0, 2.0], [1000, 400]),
+        "equal_depths": synth.records(np.linspace(0, 300, 500), np.linspace(0, 200, 500),
+                                      [2.5] * 500, [20] * 500),
+        "subnormal_depth": synth.records([10.0, 20.0], [10.0, 20.0], [1e-45, 1e-40], [3, 3]),
+    }
+    for name, g in cases.items():
+        _check_frame(ctx, oracle, synth.Frame(W, H, g, name))
+
+
+def test_sort_frame_repeated_calls(ctx, oracle):
+    """Many sorts on one context (the look-back epoch tag wraps every 7
+    passes) stay exact."""
+    for s in range(6):
+        _check_frame(ctx, oracle, synth.frame_random(100 + s, 20_000, 500, 300, depth_ties=0.3))
+
+
+def test_sort_frame_scene_1m(ctx, oracle):
+    m = _check_frame(ctx, oracle, synth.frame_scene(0))
+    assert m > 5_000_000
+
+
+def test_sort_frame_large_3m(ctx, oracle):
+    m = _check_frame(ctx, oracle, synth.frame_large(0))
+    assert m > 20_000_000
+
+
+def test_sort_pairs_multi_portion(ctx):
+    """More pairs than one look-back portion (2^26): checked by properties
+    that determine the stable sort uniquely -- values are the input
+    positions, so they must form a permutation, sorted_keys must equal
+    keys[values], keys must be non-decreasing and ties must keep input
+    order."""
+    m = (1 << 26) + 12_345
+    rng = np.random.default_rng(5)
+    k = rng.integers(0, 1 << 20, size=m, dtype=np.uint64) << np.uint64(12)  # many ties
+    kt = torch.from_numpy(k.view(np.int64)).to(DEV)
+    vt = torch.arange(m, dtype=torch.int32, device=DEV)
+    sk, sv = ctx.sort_pairs(kt, vt, 0, 0)
+    ctx.sync()
+    del kt
+    skn, svn = u64(sk), u32(sv).astype(np.int64)
+    assert np.all(skn[1:] >= skn[:-1])
+    assert np.array_equal(skn, k[svn])
+    assert np.array_equal(np.bincount(svn, minlength=m), np.ones(m, dtype=np.int64))
+    tie = skn[1:] == skn[:-1]
+    assert np.all(svn[1:][tie] > svn[:-1][tie])
