@@ -183,7 +183,8 @@ tdgs_status tdgs_duplicate_keys(tdgs_context* ctx, const tdgs_gaussian2d* g,
  * buffers of the same length.  The sort ping-pongs between the two, and
  * *result_in_alt (host int) tells where the sorted pairs are: 0 = keys/
  * values, 1 = keys_alt/values_alt.  The other pair of buffers is clobbered.
- * tile_bits <= 32. */
+ * tile_bits <= 32.  Keys changed by someone else while the sort runs can
+ * send a pair outside [0, m); it is dropped and TDGS_ERR_CAPACITY latched. */
 tdgs_status tdgs_sort_pairs(tdgs_context* ctx, uint64_t* keys, uint32_t* values,
                             uint64_t* keys_alt, uint32_t* values_alt, uint32_t m,
                             uint32_t tile_bits, uint32_t flags, int* result_in_alt,

@@ -229,9 +229,11 @@ tdgs_status do_sort(tdgs_context* ctx, uint64_t* keys, uint32_t* values, uint64_
   if (m == 0) return TDGS_OK;
   const SortPlan plan = make_sort_plan(m, tile_bits, flags, ctx->variant_override);
   const uint32_t bins = 1u << pass_variant(static_cast<int>(plan.variant)).bits;
-  const size_t hbytes = static_cast<size_t>(plan.portions) * plan.passes * bins * 4;
+  // hist[pass][bin]; offs[pass][bin] plus two bins-long chain buffers that
+  // carry digit offsets from one portion to the next.
+  const size_t hbytes = static_cast<size_t>(plan.passes) * bins * 4;
   tdgs_status st = ensure(ctx, ctx->hist, hbytes, s);
-  if (st == TDGS_OK) st = ensure(ctx, ctx->offs, hbytes, s);
+  if (st == TDGS_OK) st = ensure(ctx, ctx->offs, hbytes + 2 * bins * 4, s);
   bool grown = false;
   if (st == TDGS_OK) st = ensure(ctx, ctx->sort_status, onesweep_status_bytes(plan), s, &grown);
   if (st != TDGS_OK) return st;
@@ -256,12 +258,14 @@ tdgs_status do_sort(tdgs_context* ctx, uint64_t* keys, uint32_t* values, uint64_
       uint32_t epoch = 0, grid = 0;
       st = next_epoch(ctx, s, &epoch);
       if (st != TDGS_OK) return st;
-      const uint32_t* doff =
-          static_cast<uint32_t*>(ctx->offs.p) + (static_cast<size_t>(q) * plan.passes + p) * bins;
+      uint32_t* chain = static_cast<uint32_t*>(ctx->offs.p) + static_cast<size_t>(plan.passes) * bins;
+      const uint32_t* doff = q == 0 ? static_cast<uint32_t*>(ctx->offs.p) + static_cast<size_t>(p) * bins
+                                    : chain + ((q - 1) & 1u) * bins;
+      uint32_t* next = q + 1 < plan.portions ? chain + (q & 1u) * bins : nullptr;
       const uint64_t pbeg = static_cast<uint64_t>(q) * plan.portion;
       const uint64_t pitems = std::min<uint64_t>(plan.portion, m - pbeg);
       TDGS_TRACED(ctx, kKOnesweep, pitems, s,
-                  launch_onesweep_pass(plan, p, q, kin, vin, kout, vout, m, doff,
+                  launch_onesweep_pass(plan, p, q, kin, vin, kout, vout, m, doff, next,
                                        static_cast<uint32_t*>(ctx->sort_status.p), epoch,
                                        ctx->d_tickets + 1, ctx->ticket_base[1], err_word(ctx),
                                        &grid, s));

@@ -63,9 +63,9 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp
 
 // ------------------------------------------------------ upfront histogram
 // grid = (blocks per portion, portions).  Histograms of every pass's digit
-// are counted with shared-memory atomics and added to the global
-// per-portion histograms.  Also checks that no key sets a bit outside the
-// sorted range.
+// over all keys are counted with shared-memory atomics and added to the
+// global histograms hist[pass][bin].  Also checks that no key sets a bit
+// outside the sorted range.
 __global__ void __launch_bounds__(512)
     k_upfront_hist(const uint64_t* __restrict__ keys, uint32_t m, uint32_t portion,
                    uint32_t passes, uint32_t bins, DigitShifts ds, int drop31, uint64_t bad_mask,
@@ -102,40 +102,30 @@ __global__ void __launch_bounds__(512)
       if (p < passes) atomicAdd(&sh[p * bins + ((e >> ds.shift[p]) & ds.mask[p])], 1u);
   }
   __syncthreads();
-  uint32_t* gh = hist + static_cast<size_t>(q) * passes * bins;
   for (uint32_t j = t; j < passes * bins; j += blockDim.x)
-    if (sh[j]) atomicAdd(gh + j, sh[j]);
+    if (sh[j]) atomicAdd(hist + j, sh[j]);
   if (__any_sync(0xffffffffu, bad) && lane_id() == 0) latch_error(err, TDGS_ERR_INVALID_ARGUMENT);
 }
 
 // ---------------------------------------------------------- digit offsets
-// One block per pass: offs[q][p][b] = (number of keys, over all portions,
-// whose digit p is < b) + (keys with digit b in portions before q).
+// One block per pass: offs[p][b] = number of keys whose digit p is < b,
+// i.e. where the keys with digit b start after pass p.
 __global__ void __launch_bounds__(1024)
-    k_digit_offsets(const uint32_t* __restrict__ hist, uint32_t portions, uint32_t passes,
-                    uint32_t bins, uint32_t* __restrict__ offs) {
+    k_digit_offsets(const uint32_t* __restrict__ hist, uint32_t bins, uint32_t* __restrict__ offs) {
   __shared__ uint32_t s_warp[32];
-  const uint32_t p = blockIdx.x;
+  const size_t p = blockIdx.x;
   const uint32_t per = (bins + 1023) / 1024;  // 1 or 2
   uint32_t tot[2] = {0, 0};
   uint32_t sum = 0;
   for (uint32_t i = 0; i < per; ++i) {
     const uint32_t b = threadIdx.x * per + i;
-    if (b < bins)
-      for (uint32_t q = 0; q < portions; ++q) tot[i] += hist[(static_cast<size_t>(q) * passes + p) * bins + b];
+    if (b < bins) tot[i] = hist[p * bins + b];
     sum += tot[i];
   }
   uint32_t run = block_excl_scan<32>(sum, s_warp);
   for (uint32_t i = 0; i < per; ++i) {
     const uint32_t b = threadIdx.x * per + i;
-    if (b < bins) {
-      uint32_t r = run;
-      for (uint32_t q = 0; q < portions; ++q) {
-        const size_t at = (static_cast<size_t>(q) * passes + p) * bins + b;
-        offs[at] = r;
-        r += hist[at];
-      }
-    }
+    if (b < bins) offs[p * bins + b] = run;
     run += tot[i];
   }
 }
@@ -163,8 +153,9 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1))
     k_onesweep(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t total,
                uint32_t begin, uint32_t count, uint32_t shift, uint32_t mask, int drop31,
-               const uint32_t* __restrict__ digit_off, uint32_t* status, uint32_t epoch,
-               uint32_t* ticket, uint32_t ticket_base, uint32_t* err) {
+               const uint32_t* __restrict__ digit_off, uint32_t* __restrict__ next_off,
+               uint32_t* status, uint32_t epoch, uint32_t* ticket, uint32_t ticket_base,
+               uint32_t* err) {
   constexpr int kBins = 1 << kBits;
   constexpr int kWarps = kThreads / 32;
   constexpr int kTileKeys = kThreads * kItems;
@@ -319,6 +310,15 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1))
                      kFlagPre | (epoch << kEpochShift) | ((excl[i] + tot[i]) & kCountMask));
       }
     }
+    // The last tile of a portion hands the running digit offsets to the
+    // next portion of the same pass (launched after this one).
+    if (next_off && tile == gridDim.x - 1) {
+#pragma unroll
+      for (int i = 0; i < kBpt; ++i) {
+        const uint32_t b = t + i * kThreads;
+        if (b < static_cast<uint32_t>(kBins)) next_off[b] = __ldg(digit_off + b) + excl[i] + tot[i];
+      }
+    }
   }
   __syncthreads();
 
@@ -371,14 +371,14 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1))
     const uint32_t p = i * kThreads + t;
     if (p < valid && dst[i] < total) vout[dst[i]] = xv[p];
   }
-  if (out_of_range) latch_error(err, TDGS_ERR_TIMEOUT);
+  if (out_of_range) latch_error(err, TDGS_ERR_CAPACITY);
 }
 
 // ------------------------------------------------------------ variants
 namespace {
 using PassFn = void (*)(const uint64_t*, const uint32_t*, uint64_t*, uint32_t*, uint32_t, uint32_t,
-                        uint32_t, uint32_t, uint32_t, int, const uint32_t*, uint32_t*, uint32_t,
-                        uint32_t*, uint32_t, uint32_t*);
+                        uint32_t, uint32_t, uint32_t, int, const uint32_t*, uint32_t*, uint32_t*,
+                        uint32_t, uint32_t*, uint32_t, uint32_t*);
 
 template <int B, int T, int I>
 constexpr size_t pass_smem() {
@@ -475,16 +475,16 @@ cudaError_t launch_digit_offsets(const uint32_t* hist, const SortPlan& plan, uin
                                  cudaStream_t s) {
   if (plan.portions == 0) return cudaSuccess;
   const uint32_t bins = 1u << kVariants[plan.variant].v.bits;
-  k_digit_offsets<<<plan.passes, 1024, 0, s>>>(hist, plan.portions, plan.passes, bins, offs);
+  k_digit_offsets<<<plan.passes, 1024, 0, s>>>(hist, bins, offs);
   return cudaGetLastError();
 }
 
 cudaError_t launch_onesweep_pass(const SortPlan& plan, uint32_t pass, uint32_t portion,
                                  const uint64_t* kin, const uint32_t* vin, uint64_t* kout,
                                  uint32_t* vout, uint32_t m, const uint32_t* digit_off,
-                                 uint32_t* status, uint32_t epoch, uint32_t* ticket,
-                                 uint32_t ticket_base, uint32_t* err, uint32_t* grid_out,
-                                 cudaStream_t s) {
+                                 uint32_t* next_off, uint32_t* status, uint32_t epoch,
+                                 uint32_t* ticket, uint32_t ticket_base, uint32_t* err,
+                                 uint32_t* grid_out, cudaStream_t s) {
   const VariantEntry& e = kVariants[plan.variant];
   if (!g_smem_set[plan.variant]) {
     cudaError_t ce = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -500,7 +500,8 @@ cudaError_t launch_onesweep_pass(const SortPlan& plan, uint32_t pass, uint32_t p
   if (grid == 0) return cudaSuccess;
   e.fn<<<grid, e.v.threads, e.smem, s>>>(kin, vin, kout, vout, m, static_cast<uint32_t>(beg), count,
                                          plan.shift[pass], plan.mask[pass], plan.drop31 ? 1 : 0,
-                                         digit_off, status, epoch, ticket, ticket_base, err);
+                                         digit_off, next_off, status, epoch, ticket, ticket_base,
+                                         err);
   return cudaGetLastError();
 }
 

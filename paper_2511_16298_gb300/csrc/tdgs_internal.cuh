@@ -174,9 +174,9 @@ cudaError_t launch_digit_offsets(const uint32_t* hist, const SortPlan& plan, uin
 cudaError_t launch_onesweep_pass(const SortPlan& plan, uint32_t pass, uint32_t portion,
                                  const uint64_t* kin, const uint32_t* vin, uint64_t* kout,
                                  uint32_t* vout, uint32_t m, const uint32_t* digit_off,
-                                 uint32_t* status, uint32_t epoch, uint32_t* ticket,
-                                 uint32_t ticket_base, uint32_t* err, uint32_t* grid_out,
-                                 cudaStream_t s);
+                                 uint32_t* next_off, uint32_t* status, uint32_t epoch,
+                                 uint32_t* ticket, uint32_t ticket_base, uint32_t* err,
+                                 uint32_t* grid_out, cudaStream_t s);
 size_t onesweep_status_bytes(const SortPlan& plan);
 
 }  // namespace tdgs
