@@ -129,9 +129,7 @@ def algorithmic_bytes(kernel: str, items: int, n: int, m: int, tiles: int) -> fl
         return 20.0 * items
     if kernel == "duplicate_keys":  # records + offsets in, 12 B per pair out
         return 20.0 * items + 12.0 * m
-    if kernel == "radix_upfront_hist":
-        return 8.0 * items
-    if kernel == "radix_onesweep_pass":  # 12 B read + 12 B written per pair
+    if kernel == "radix_pass":  # 12 B read + 12 B written per pair
         return 24.0 * items
     if kernel == "tile_ranges":
         return 8.0 * items + 8.0 * tiles
@@ -255,10 +253,10 @@ def run_ours(args, rank, world, local_rank, dist):
         skt = ctx.kernel_times()
         ctx.enable_timing(False)
         sms = [a.elapsed_time(b) for a, b in sev]
-        passes = skt.get("radix_onesweep_pass", {}).get("launches", 0) // (args.warmup + args.steps)
+        passes = skt.get("radix_pass", {}).get("launches", 0) // (args.warmup + args.steps)
         sbytes = m * (8 + 24 * passes)
         smean = statistics.mean(sms)
-        op = skt.get("radix_onesweep_pass")
+        op = skt.get("radix_pass")
         sort_only = {"pairs_per_s": m / (smean * 1e-3), "ms_mean": round(smean, 4),
                      "ms_p50": round(statistics.median(sms), 4), "passes": passes,
                      "algorithmic_bytes": sbytes,

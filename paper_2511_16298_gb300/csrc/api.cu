@@ -30,11 +30,12 @@ struct Buffer {
 };
 
 enum KernelId {
-  kKCount, kKScan, kKDuplicate, kKRanges, kKUpfront, kKDigitOffsets, kKOnesweep, kKNum
+  kKCount, kKScan, kKDuplicate, kKRanges, kKRadixPass,
+  kKFrameCount, kKDepthSort, kKDupDepth, kKTilePass, kKRangesDiff, kKNum
 };
 const char* const kKernelNames[kKNum] = {
-    "count_tiles",         "scan",          "duplicate_keys",       "tile_ranges",
-    "radix_upfront_hist",  "radix_offsets", "radix_onesweep_pass"};
+    "count_tiles",  "scan",       "duplicate_keys",     "tile_ranges",    "radix_pass",
+    "frame_count",  "depth_sort", "duplicate_by_depth", "tile_sort_pass", "ranges_from_diff"};
 
 struct PendingTime {
   int id;
@@ -48,12 +49,11 @@ struct tdgs_context {
   int device = 0;
   DevStatus* d_status = nullptr;
   DevStatus* h_status = nullptr;  // pinned
-  uint32_t* d_tickets = nullptr;  // [0] scan tiles, [1] sort pass tiles
+  uint32_t* d_tickets = nullptr;  // [0] scan tiles, [2..3] radix grid barrier
   uint32_t ticket_base[2] = {0, 0};
-  Buffer scan_status, hist, offs, sort_status;
-  size_t sort_status_dirty = 0;
-  uint32_t epoch = 0;
-  Buffer f_offsets, f_keys[2], f_values[2], f_ranges;
+  Buffer scan_status, sort_scratch;
+  // fused-frame buffers
+  Buffer f_counts, f_dkey[2], f_dval[2], f_soff, f_diff, f_stream[2], f_keys, f_values, f_ranges;
   int variant_override = -1;
   std::string last_error;
   // tracing
@@ -194,28 +194,15 @@ tdgs_status traced(tdgs_context* ctx, KernelId id, uint64_t items, cudaStream_t 
     if (_st != TDGS_OK) return _st;                                              \
   } while (0)
 
-// Look-back epoch for the next sort pass launch (1..7).  When the tag wraps,
-// every status word written since the last clear is zeroed so no stale word
-// can carry the reused tag.
-tdgs_status next_epoch(tdgs_context* ctx, cudaStream_t s, uint32_t* epoch) {
-  ctx->epoch = ctx->epoch % 7 + 1;
-  if (ctx->epoch == 1 && ctx->sort_status_dirty) {
-    TDGS_CUDA(ctx, cudaMemsetAsync(ctx->sort_status.p, 0, ctx->sort_status_dirty, s));
-    ctx->sort_status_dirty = 0;
-  }
-  *epoch = ctx->epoch;
-  return TDGS_OK;
-}
-
-tdgs_status do_scan(tdgs_context* ctx, const uint32_t* counts, const float4* recs, FrameGeom fg,
-                    uint32_t n, uint32_t* offsets, uint64_t* total64, uint32_t* total32,
-                    cudaStream_t s) {
+tdgs_status do_scan(tdgs_context* ctx, const uint32_t* counts, const float4* recs,
+                    const uint32_t* gather, FrameGeom fg, uint32_t n, uint32_t* offsets,
+                    uint64_t* total64, uint32_t* total32, cudaStream_t s) {
   const uint32_t tiles = (n + kScanTileItems - 1) / kScanTileItems;
   tdgs_status st = ensure(ctx, ctx->scan_status, static_cast<size_t>(tiles) * 8, s);
   if (st != TDGS_OK) return st;
   TDGS_CUDA(ctx, cudaMemsetAsync(ctx->scan_status.p, 0, static_cast<size_t>(tiles) * 8, s));
   TDGS_TRACED(ctx, kKScan, n, s,
-              launch_scan(counts, recs, fg, n, offsets,
+              launch_scan(counts, recs, gather, fg, n, offsets,
                           static_cast<uint64_t*>(ctx->scan_status.p), ctx->d_tickets + 0,
                           ctx->ticket_base[0], total64, total32, err_word(ctx), s));
   ctx->ticket_base[0] += tiles;
@@ -228,50 +215,18 @@ tdgs_status do_sort(tdgs_context* ctx, uint64_t* keys, uint32_t* values, uint64_
   *result_in_alt = 0;
   if (m == 0) return TDGS_OK;
   const SortPlan plan = make_sort_plan(m, tile_bits, flags, ctx->variant_override);
-  const uint32_t bins = 1u << pass_variant(static_cast<int>(plan.variant)).bits;
-  // hist[pass][bin]; offs[pass][bin] plus two bins-long chain buffers that
-  // carry digit offsets from one portion to the next.
-  const size_t hbytes = static_cast<size_t>(plan.passes) * bins * 4;
-  tdgs_status st = ensure(ctx, ctx->hist, hbytes, s);
-  if (st == TDGS_OK) st = ensure(ctx, ctx->offs, hbytes + 2 * bins * 4, s);
-  bool grown = false;
-  if (st == TDGS_OK) st = ensure(ctx, ctx->sort_status, onesweep_status_bytes(plan), s, &grown);
+  if (plan.grid == 0) return fail(ctx, TDGS_ERR_CUDA, "device query for the sort plan failed");
+  tdgs_status st = ensure(ctx, ctx->sort_scratch, radix_scratch_words(plan) * 4, s);
   if (st != TDGS_OK) return st;
-  if (grown) {
-    TDGS_CUDA(ctx, cudaMemsetAsync(ctx->sort_status.p, 0, ctx->sort_status.bytes, s));
-    ctx->sort_status_dirty = 0;
-    ctx->epoch = 0;
-  }
-  TDGS_CUDA(ctx, cudaMemsetAsync(ctx->hist.p, 0, hbytes, s));
-  TDGS_TRACED(ctx, kKUpfront, m, s,
-              launch_upfront_hist(keys, m, plan, static_cast<uint32_t*>(ctx->hist.p),
-                                  err_word(ctx), s));
-  TDGS_TRACED(ctx, kKDigitOffsets, plan.passes, s,
-              launch_digit_offsets(static_cast<uint32_t*>(ctx->hist.p), plan,
-                                   static_cast<uint32_t*>(ctx->offs.p), s));
   uint64_t* kin = keys;
   uint32_t* vin = values;
   uint64_t* kout = keys_alt;
   uint32_t* vout = values_alt;
   for (uint32_t p = 0; p < plan.passes; ++p) {
-    for (uint32_t q = 0; q < plan.portions; ++q) {
-      uint32_t epoch = 0, grid = 0;
-      st = next_epoch(ctx, s, &epoch);
-      if (st != TDGS_OK) return st;
-      uint32_t* chain = static_cast<uint32_t*>(ctx->offs.p) + static_cast<size_t>(plan.passes) * bins;
-      const uint32_t* doff = q == 0 ? static_cast<uint32_t*>(ctx->offs.p) + static_cast<size_t>(p) * bins
-                                    : chain + ((q - 1) & 1u) * bins;
-      uint32_t* next = q + 1 < plan.portions ? chain + (q & 1u) * bins : nullptr;
-      const uint64_t pbeg = static_cast<uint64_t>(q) * plan.portion;
-      const uint64_t pitems = std::min<uint64_t>(plan.portion, m - pbeg);
-      TDGS_TRACED(ctx, kKOnesweep, pitems, s,
-                  launch_onesweep_pass(plan, p, q, kin, vin, kout, vout, m, doff, next,
-                                       static_cast<uint32_t*>(ctx->sort_status.p), epoch,
-                                       ctx->d_tickets + 1, ctx->ticket_base[1], err_word(ctx),
-                                       &grid, s));
-      ctx->ticket_base[1] += grid;
-      ctx->sort_status_dirty = std::max(ctx->sort_status_dirty, static_cast<size_t>(grid) * bins * 4);
-    }
+    TDGS_TRACED(ctx, kKRadixPass, m, s,
+                launch_radix_pass(plan, p, kin, vin, kout, vout, m,
+                                  static_cast<uint32_t*>(ctx->sort_scratch.p), ctx->d_tickets + 2,
+                                  err_word(ctx), s));
     std::swap(kin, kout);
     std::swap(vin, vout);
   }
@@ -406,9 +361,10 @@ void tdgs_context_destroy(tdgs_context* ctx) {
   DeviceGuard g(ctx->device);
   drain_timings(ctx);
   for (cudaEvent_t e : ctx->free_events) cudaEventDestroy(e);
-  Buffer* bufs[] = {&ctx->scan_status, &ctx->hist,      &ctx->offs,        &ctx->sort_status,
-                    &ctx->f_offsets,   &ctx->f_keys[0], &ctx->f_keys[1],   &ctx->f_values[0],
-                    &ctx->f_values[1], &ctx->f_ranges};
+  Buffer* bufs[] = {&ctx->scan_status, &ctx->sort_scratch, &ctx->f_counts,    &ctx->f_dkey[0],
+                    &ctx->f_dkey[1],    &ctx->f_dval[0],     &ctx->f_dval[1],    &ctx->f_soff,
+                    &ctx->f_diff,       &ctx->f_stream[0],   &ctx->f_stream[1],  &ctx->f_keys,
+                    &ctx->f_values,     &ctx->f_ranges};
   for (Buffer* b : bufs)
     if (b->p) cudaFree(b->p);
   if (ctx->d_status) cudaFree(ctx->d_status);
@@ -451,7 +407,7 @@ tdgs_status tdgs_scan(tdgs_context* ctx, const uint32_t* counts, uint32_t n, uin
   if (!counts || !offsets) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "null pointer");
   if (!aligned(counts, 4) || !aligned(offsets, 4) || (total_dev && !aligned(total_dev, 4)))
     return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "misaligned pointer");
-  return do_scan(ctx, counts, nullptr, FrameGeom{}, n, offsets, nullptr, total_dev, s);
+  return do_scan(ctx, counts, nullptr, nullptr, FrameGeom{}, n, offsets, nullptr, total_dev, s);
 }
 
 tdgs_status tdgs_duplicate_keys(tdgs_context* ctx, const tdgs_gaussian2d* g,
@@ -509,6 +465,18 @@ tdgs_status tdgs_tile_ranges(tdgs_context* ctx, const uint64_t* sorted_keys, uin
   return TDGS_OK;
 }
 
+// Fused frame, depth first.  Steps (all on `stream`):
+//   1. frame_count: tile counts, depth keys, per-CTA tile difference grids
+//   2. depth_sort: the N Gaussians by (depth bits, index)  -> depth order
+//   3. scan of the counts in depth order -> pair offsets, pair count M
+//   4. (host) read M and the error word; size the pair buffers
+//   5. duplicate_by_depth: element (tile << rbits | depth position) per pair
+//   6. tile_sort_pass x1-2: stable passes on the tile bits; the last one
+//      writes the final keys (tile << 32 | depth bits) and indices
+//   7. ranges_from_diff: per-tile counts from the difference grids, scanned
+// The result equals the stable sort of the 64-bit keys of steps 1-4 of the
+// per-step calls: ties of the 64-bit key are pairs of distinct Gaussians in
+// the same tile with equal depth, which both orders put in index order.
 tdgs_status tdgs_sort_frame(tdgs_context* ctx, const tdgs_gaussian2d* g, uint32_t n,
                             tdgs_frame f, const uint64_t** sorted_keys,
                             const uint32_t** sorted_values, const tdgs_range** ranges,
@@ -523,16 +491,51 @@ tdgs_status tdgs_sort_frame(tdgs_context* ctx, const tdgs_gaussian2d* g, uint32_
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const FrameGeom fg = make_geom(f);
   const uint32_t T = tdgs_num_tiles(f);
-  tdgs_status st = ensure(ctx, ctx->f_offsets, static_cast<size_t>(n) * 4 + 4, s);
+  const uint32_t tb = tdgs_tile_bits(f);
+  const float4* rec = reinterpret_cast<const float4*>(g);
+  uint32_t rbits = 0;
+  while (rbits < 32 && (1ull << rbits) < n) ++rbits;
+  const bool wide = tb + rbits > 32 || rbits >= 32;
+  const uint64_t cells = static_cast<uint64_t>(fg.gx + 1) * (fg.gy + 1);
+  const bool use_diff = cells <= kMaxDiffCells;
+  const uint32_t count_grid = use_diff ? 152u * 2u : 152u * 8u;
+
+  tdgs_status st = TDGS_OK;
+  const size_t n4 = static_cast<size_t>(n) * 4 + 16;
+  for (Buffer* b : {&ctx->f_counts, &ctx->f_dkey[0], &ctx->f_dkey[1], &ctx->f_dval[0],
+                    &ctx->f_dval[1], &ctx->f_soff})
+    if (st == TDGS_OK) st = ensure(ctx, *b, n4, s);
+  if (st == TDGS_OK && use_diff) st = ensure(ctx, ctx->f_diff, (count_grid + 1) * cells * 4, s);
+  if (st == TDGS_OK) st = ensure(ctx, ctx->f_ranges, static_cast<size_t>(T) * 8, s);
+  const uint32_t dgrid = depth_sort_grid(n ? n : 1);
+  if (dgrid == 0) return fail(ctx, TDGS_ERR_CUDA, "device query for the depth sort failed");
+  if (st == TDGS_OK) st = ensure(ctx, ctx->sort_scratch, depth_sort_scratch_words(dgrid) * 4, s);
   if (st != TDGS_OK) return st;
-  // Steps 1+2 fused: counts are computed from the records inside the scan.
+  uint32_t* counts = static_cast<uint32_t*>(ctx->f_counts.p);
+  uint32_t* dk[2] = {static_cast<uint32_t*>(ctx->f_dkey[0].p), static_cast<uint32_t*>(ctx->f_dkey[1].p)};
+  uint32_t* dv[2] = {static_cast<uint32_t*>(ctx->f_dval[0].p), static_cast<uint32_t*>(ctx->f_dval[1].p)};
+  uint32_t* soff = static_cast<uint32_t*>(ctx->f_soff.p);
+  int32_t* diff = use_diff ? static_cast<int32_t*>(ctx->f_diff.p) : nullptr;
+  uint32_t* scratch = static_cast<uint32_t*>(ctx->sort_scratch.p);
+  uint32_t* bar = ctx->d_tickets + 2;
+
+  // 1-3
+  TDGS_TRACED(ctx, kKFrameCount, n, s,
+              launch_frame_count(rec, n, fg, counts, dk[0], dv[0], diff, count_grid, err_word(ctx), s));
+  for (uint32_t p = 0; p < kDepthPasses; ++p) {
+    TDGS_TRACED(ctx, kKDepthSort, n, s,
+                launch_depth_pass(dgrid, p, dk[p & 1], dv[p & 1], dk[(p + 1) & 1], dv[(p + 1) & 1], n,
+                                  scratch, bar, err_word(ctx), s));
+  }
+  const uint32_t* sdepth = dk[kDepthPasses & 1];
+  const uint32_t* sorder = dv[kDepthPasses & 1];
   if (n) {
-    st = do_scan(ctx, nullptr, reinterpret_cast<const float4*>(g), fg, n,
-                 static_cast<uint32_t*>(ctx->f_offsets.p), &ctx->d_status->total, nullptr, s);
+    st = do_scan(ctx, counts, nullptr, sorder, fg, n, soff, &ctx->d_status->total, nullptr, s);
     if (st != TDGS_OK) return st;
   } else {
     TDGS_CUDA(ctx, cudaMemsetAsync(&ctx->d_status->total, 0, 8, s));
   }
+  // 4
   TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(DevStatus),
                                  cudaMemcpyDeviceToHost, s));
   TDGS_CUDA(ctx, cudaStreamSynchronize(s));
@@ -544,30 +547,54 @@ tdgs_status tdgs_sort_frame(tdgs_context* ctx, const tdgs_gaussian2d* g, uint32_
   const uint64_t total = ctx->h_status->total;
   if (total > 0xffffffffull) return fail(ctx, TDGS_ERR_OVERFLOW, "pair count above 2^32-1");
   const uint32_t m = static_cast<uint32_t>(total);
-  for (int b = 0; b < 2 && st == TDGS_OK; ++b) {
-    st = ensure(ctx, ctx->f_keys[b], static_cast<size_t>(m) * 8 + 8, s);
-    if (st == TDGS_OK) st = ensure(ctx, ctx->f_values[b], static_cast<size_t>(m) * 4 + 4, s);
+  const size_t esz = wide ? 8 : 4;
+  for (int b = 0; b < 2 && st == TDGS_OK; ++b)
+    st = ensure(ctx, ctx->f_stream[b], static_cast<size_t>(m) * esz + 16, s);
+  if (st == TDGS_OK) st = ensure(ctx, ctx->f_keys, static_cast<size_t>(m) * 8 + 16, s);
+  if (st == TDGS_OK) st = ensure(ctx, ctx->f_values, static_cast<size_t>(m) * 4 + 16, s);
+  // 5-6
+  const uint32_t npass = tb <= 8 ? 1u : 2u;
+  const uint32_t w0 = npass == 1 ? tb : (tb + 1) / 2;
+  const uint32_t sgrid = stream_grid(wide, npass == 1, m ? m : 1);
+  const uint32_t sgrid_x = stream_grid(wide, true, m ? m : 1);
+  if (sgrid == 0 || sgrid_x == 0) return fail(ctx, TDGS_ERR_CUDA, "device query for the tile sort failed");
+  if (st == TDGS_OK)
+    st = ensure(ctx, ctx->sort_scratch,
+                std::max(stream_scratch_words(wide, false, sgrid), stream_scratch_words(wide, true, sgrid_x)) * 4,
+                s);
+  if (st != TDGS_OK) return st;
+  scratch = static_cast<uint32_t*>(ctx->sort_scratch.p);
+  void* s0 = ctx->f_stream[0].p;
+  void* s1 = ctx->f_stream[1].p;
+  uint64_t* okeys = static_cast<uint64_t*>(ctx->f_keys.p);
+  uint32_t* ovals = static_cast<uint32_t*>(ctx->f_values.p);
+  TDGS_TRACED(ctx, kKDupDepth, m ? n : 0, s,
+              launch_dup_depth(rec, sorder, soff, n, fg, rbits, s0, wide, m, err_word(ctx), s));
+  if (npass == 1) {
+    TDGS_TRACED(ctx, kKTilePass, m, s,
+                launch_stream_pass(wide, true, sgrid_x, s0, okeys, ovals, m, rbits, tb, rbits, sdepth,
+                                   sorder, scratch, bar, err_word(ctx), s));
+  } else {
+    TDGS_TRACED(ctx, kKTilePass, m, s,
+                launch_stream_pass(wide, false, sgrid, s0, s1, nullptr, m, rbits, w0, rbits, sdepth,
+                                   sorder, scratch, bar, err_word(ctx), s));
+    TDGS_TRACED(ctx, kKTilePass, m, s,
+                launch_stream_pass(wide, true, sgrid_x, s1, okeys, ovals, m, rbits + w0, tb - w0, rbits,
+                                   sdepth, sorder, scratch, bar, err_word(ctx), s));
   }
-  if (st == TDGS_OK) st = ensure(ctx, ctx->f_ranges, static_cast<size_t>(T) * 8, s);
-  if (st != TDGS_OK) return st;
-  uint64_t* k0 = static_cast<uint64_t*>(ctx->f_keys[0].p);
-  uint64_t* k1 = static_cast<uint64_t*>(ctx->f_keys[1].p);
-  uint32_t* v0 = static_cast<uint32_t*>(ctx->f_values[0].p);
-  uint32_t* v1 = static_cast<uint32_t*>(ctx->f_values[1].p);
-  TDGS_TRACED(ctx, kKDuplicate, m ? n : 0, s,
-              launch_duplicate(reinterpret_cast<const float4*>(g),
-                               static_cast<uint32_t*>(ctx->f_offsets.p), n, fg, k0, v0, m,
-                               err_word(ctx), s));
-  int alt = 0;
-  st = do_sort(ctx, k0, v0, k1, v1, m, tdgs_tile_bits(f), TDGS_SORT_DEPTH_POSITIVE, &alt, s);
-  if (st != TDGS_OK) return st;
-  const uint64_t* sk = alt ? k1 : k0;
-  TDGS_CUDA(ctx, cudaMemsetAsync(ctx->f_ranges.p, 0, static_cast<size_t>(T) * 8, s));
-  TDGS_TRACED(ctx, kKRanges, m, s,
-              launch_tile_ranges(sk, m, T, static_cast<uint2*>(ctx->f_ranges.p), err_word(ctx), s));
-  *sorted_keys = sk;
-  *sorted_values = alt ? v1 : v0;
-  *ranges = static_cast<const tdgs_range*>(ctx->f_ranges.p);
+  // 7
+  uint2* rg = static_cast<uint2*>(ctx->f_ranges.p);
+  if (use_diff && n) {
+    TDGS_TRACED(ctx, kKRangesDiff, T, s,
+                launch_ranges_from_diff(diff, count_grid, fg, diff + count_grid * cells, rg,
+                                        err_word(ctx), s));
+  } else {
+    TDGS_CUDA(ctx, cudaMemsetAsync(rg, 0, static_cast<size_t>(T) * 8, s));
+    TDGS_TRACED(ctx, kKRanges, m, s, launch_tile_ranges(okeys, m, T, rg, err_word(ctx), s));
+  }
+  *sorted_keys = okeys;
+  *sorted_values = ovals;
+  *ranges = reinterpret_cast<const tdgs_range*>(rg);
   *m_out = m;
   return TDGS_OK;
 }

@@ -1,0 +1,63 @@
+// Radix passes of the depth-first frame path: the depth sort of the N
+// Gaussians and the stable passes over the packed (tile, depth rank)
+// stream, the last of which expands to the final keys and indices.
+#include "radix.cuh"
+
+namespace tdgs {
+
+namespace {
+using radix::make_kernel;
+const radix::Kernel& depth_kernel() {
+  static const radix::Kernel k = make_kernel<uint32_t, true, false, 11, 256, 16>();
+  return k;
+}
+const radix::Kernel& stream_kernel(bool wide, bool expand) {
+  static const radix::Kernel k[4] = {
+      make_kernel<uint32_t, false, false, 8, 256, 16>(),
+      make_kernel<uint32_t, false, true, 8, 256, 16>(),
+      make_kernel<uint64_t, false, false, 8, 256, 16>(),
+      make_kernel<uint64_t, false, true, 8, 256, 16>(),
+  };
+  return k[(wide ? 2 : 0) + (expand ? 1 : 0)];
+}
+}  // namespace
+
+uint32_t depth_sort_grid(uint32_t n) { return radix::grid_for(depth_kernel(), n); }
+size_t depth_sort_scratch_words(uint32_t grid) { return radix::scratch_words(depth_kernel(), grid); }
+
+cudaError_t launch_depth_pass(uint32_t grid, uint32_t pass, const uint32_t* kin, const uint32_t* vin,
+                              uint32_t* kout, uint32_t* vout, uint32_t n, uint32_t* scratch,
+                              uint32_t* bar, uint32_t* err, cudaStream_t s) {
+  radix::PassArgs a{};
+  a.m = n;
+  a.shift = pass * 11;
+  a.mask = pass * 11 + 11 <= 32 ? 0x7ffu : (1u << (32 - pass * 11)) - 1;
+  a.bar = bar;
+  a.err = err;
+  return radix::launch(depth_kernel(), grid, kin, vin, kout, vout, a, scratch, s);
+}
+
+uint32_t stream_grid(bool wide, bool expand, uint32_t m) {
+  return radix::grid_for(stream_kernel(wide, expand), m);
+}
+size_t stream_scratch_words(bool wide, bool expand, uint32_t grid) {
+  return radix::scratch_words(stream_kernel(wide, expand), grid);
+}
+
+cudaError_t launch_stream_pass(bool wide, bool expand, uint32_t grid, const void* kin, void* kout,
+                               uint32_t* vout, uint32_t m, uint32_t shift, uint32_t width,
+                               uint32_t rbits, const uint32_t* sdepth, const uint32_t* sorder,
+                               uint32_t* scratch, uint32_t* bar, uint32_t* err, cudaStream_t s) {
+  radix::PassArgs a{};
+  a.m = m;
+  a.shift = shift;
+  a.mask = width >= 32 ? 0xffffffffu : (1u << width) - 1;
+  a.rbits = rbits;
+  a.sdepth = sdepth;
+  a.sorder = sorder;
+  a.bar = bar;
+  a.err = err;
+  return radix::launch(stream_kernel(wide, expand), grid, kin, nullptr, kout, vout, a, scratch, s);
+}
+
+}  // namespace tdgs

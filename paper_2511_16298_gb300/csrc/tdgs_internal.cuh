@@ -127,10 +127,10 @@ cudaError_t launch_count_tiles(const float4* g, uint32_t n, FrameGeom fg, uint32
 // computed from the records (count and scan fused); otherwise read from
 // counts.  status: one uint64 per 2048-item block, zeroed by the caller.
 constexpr uint32_t kScanTileItems = 2048;
-cudaError_t launch_scan(const uint32_t* counts, const float4* recs, FrameGeom fg, uint32_t n,
-                        uint32_t* offsets, uint64_t* status, uint32_t* ticket,
-                        uint32_t ticket_base, uint64_t* total64, uint32_t* total32,
-                        uint32_t* err, cudaStream_t s);
+cudaError_t launch_scan(const uint32_t* counts, const float4* recs, const uint32_t* gather,
+                        FrameGeom fg, uint32_t n, uint32_t* offsets, uint64_t* status,
+                        uint32_t* ticket, uint32_t ticket_base, uint64_t* total64,
+                        uint32_t* total32, uint32_t* err, cudaStream_t s);
 
 cudaError_t launch_duplicate(const float4* g, const uint32_t* offsets, uint32_t n,
                              FrameGeom fg, uint64_t* keys, uint32_t* values, uint32_t cap,
@@ -139,22 +139,56 @@ cudaError_t launch_duplicate(const float4* g, const uint32_t* offsets, uint32_t 
 cudaError_t launch_tile_ranges(const uint64_t* keys, uint32_t m, uint32_t num_tiles,
                                uint2* ranges, uint32_t* err, cudaStream_t s);
 
+// ---- depth-first frame path
+// Largest difference grid (gx+1)*(gy+1) handled in shared memory; larger
+// images take the tile ranges from the sorted keys instead.
+constexpr uint32_t kMaxDiffCells = 48 * 1024;
+cudaError_t launch_frame_count(const float4* g, uint32_t n, FrameGeom fg, uint32_t* counts,
+                               uint32_t* dkey, uint32_t* dval, int32_t* diff_part,
+                               uint32_t grid, uint32_t* err, cudaStream_t s);
+cudaError_t launch_dup_depth(const float4* g, const uint32_t* sorder, const uint32_t* soff,
+                             uint32_t n, FrameGeom fg, uint32_t rbits, void* out, bool wide,
+                             uint32_t cap, uint32_t* err, cudaStream_t s);
+// diff: (gx+1)*(gy+1) words of scratch for the summed grid.
+cudaError_t launch_ranges_from_diff(const int32_t* diff_part, uint32_t parts, FrameGeom fg,
+                                    int32_t* diff, uint2* ranges, uint32_t* err, cudaStream_t s);
+
+// Radix passes of the frame path (radix_frame.cu).
+struct FramePassPlan {
+  uint32_t grid;
+  uint32_t bits;   // digit bits of the kernel
+};
+// Depth sort of the N Gaussians: (uint32 depth key, uint32 index), 32 bits.
+uint32_t depth_sort_grid(uint32_t n);
+size_t depth_sort_scratch_words(uint32_t grid);
+cudaError_t launch_depth_pass(uint32_t grid, uint32_t pass, const uint32_t* kin, const uint32_t* vin,
+                              uint32_t* kout, uint32_t* vout, uint32_t n, uint32_t* scratch,
+                              uint32_t* bar, uint32_t* err, cudaStream_t s);
+constexpr uint32_t kDepthPasses = 3;  // 11 + 11 + 10 bits
+// Stable pass over the packed stream on tile bits [shift, shift + width).
+// expand: write the final (tile << 32 | depth bits) keys and indices.
+uint32_t stream_grid(bool wide, bool expand, uint32_t m);
+size_t stream_scratch_words(bool wide, bool expand, uint32_t grid);
+cudaError_t launch_stream_pass(bool wide, bool expand, uint32_t grid, const void* kin, void* kout,
+                               uint32_t* vout, uint32_t m, uint32_t shift, uint32_t width,
+                               uint32_t rbits, const uint32_t* sdepth, const uint32_t* sorder,
+                               uint32_t* scratch, uint32_t* bar, uint32_t* err, cudaStream_t s);
+
 // ----------------------------------------------------------- radix sort
 constexpr int kMaxPasses = 8;
-constexpr uint32_t kPortionMax = 1u << 26;  // look-back values must fit 27 bits
 
 struct SortPlan {
   uint32_t key_bits;   // sorted bits of the transformed key
   uint32_t passes;     // number of digit passes
-  uint32_t digit_bits; // bins = 1 << digit_bits
+  uint32_t digit_bits; // digit width of every pass but possibly the last
   uint32_t shift[kMaxPasses];
   uint32_t mask[kMaxPasses];
   bool drop31;         // transformed key skips bit 31
   uint64_t bad_mask;   // key bits that must be zero
-  uint32_t tile_keys;  // keys per CTA tile of a pass
-  uint32_t portion;    // keys per look-back portion
-  uint32_t portions;
   uint32_t variant;    // which compiled pass kernel
+  uint32_t bins;       // digit bins of that kernel
+  uint32_t tile_keys;  // keys per shared-memory tile of a chunk
+  uint32_t grid;       // resident CTAs = chunks (0 if the device query failed)
 };
 
 // Tunable pass-kernel configurations (digit bits, threads, items/thread).
@@ -165,18 +199,13 @@ int num_pass_variants();
 PassVariant pass_variant(int i);
 int default_pass_variant(uint32_t digit_bits);
 
+// Plans a sort of m keys on the current device.
 SortPlan make_sort_plan(uint32_t m, uint32_t tile_bits, uint32_t flags, int variant_override);
-
-cudaError_t launch_upfront_hist(const uint64_t* keys, uint32_t m, const SortPlan& plan,
-                                uint32_t* hist, uint32_t* err, cudaStream_t s);
-cudaError_t launch_digit_offsets(const uint32_t* hist, const SortPlan& plan, uint32_t* offs,
-                                 cudaStream_t s);
-cudaError_t launch_onesweep_pass(const SortPlan& plan, uint32_t pass, uint32_t portion,
-                                 const uint64_t* kin, const uint32_t* vin, uint64_t* kout,
-                                 uint32_t* vout, uint32_t m, const uint32_t* digit_off,
-                                 uint32_t* next_off, uint32_t* status, uint32_t epoch,
-                                 uint32_t* ticket, uint32_t ticket_base, uint32_t* err,
-                                 uint32_t* grid_out, cudaStream_t s);
-size_t onesweep_status_bytes(const SortPlan& plan);
+// uint32 words of scratch one pass needs (chunk histograms, prefixes, totals).
+size_t radix_scratch_words(const SortPlan& plan);
+// One digit pass (cooperative launch).  bar: two zero-initialised words.
+cudaError_t launch_radix_pass(const SortPlan& plan, uint32_t pass, const uint64_t* kin,
+                              const uint32_t* vin, uint64_t* kout, uint32_t* vout, uint32_t m,
+                              uint32_t* scratch, uint32_t* bar, uint32_t* err, cudaStream_t s);
 
 }  // namespace tdgs

@@ -217,6 +217,22 @@ def test_sort_frame_edge_cases(ctx, oracle):
         _check_frame(ctx, oracle, synth.Frame(W, H, g, name))
 
 
+def test_sort_frame_huge_image(ctx, oracle):
+    """A 4096x3200 image has more tile-grid cells than the shared-memory
+    difference grid holds, so the ranges come from the sorted keys."""
+    _check_frame(ctx, oracle, synth.frame_random(21, 30_000, 4096, 3200, max_sigma=200.0))
+
+
+def test_sort_frame_single_gaussian(ctx, oracle):
+    _check_frame(ctx, oracle, synth.Frame(100, 100, synth.records([50.0], [50.0], [3.0], [40]), "one"))
+
+
+def test_sort_frame_wide_elements(ctx, oracle):
+    """Tile bits + depth-rank bits above 32 use 64-bit stream elements."""
+    fr = synth.frame_random(22, 300_000, 4000, 4000, max_sigma=30.0)  # 250x250 tiles, 16+19 bits
+    _check_frame(ctx, oracle, fr)
+
+
 def test_sort_frame_repeated_calls(ctx, oracle):
     """Many sorts on one context (the look-back epoch tag wraps every 7
     passes) stay exact."""
@@ -234,8 +250,8 @@ def test_sort_frame_large_3m(ctx, oracle):
     assert m > 20_000_000
 
 
-def test_sort_pairs_multi_portion(ctx):
-    """More pairs than one look-back portion (2^26): checked by properties
+def test_sort_pairs_over_2p26(ctx):
+    """More than 2^26 pairs (digit counts beyond 26 bits): checked by properties
     that determine the stable sort uniquely -- values are the input
     positions, so they must form a permutation, sorted_keys must equal
     keys[values], keys must be non-decreasing and ties must keep input
