@@ -133,6 +133,17 @@ def algorithmic_bytes(kernel: str, items: int, n: int, m: int, tiles: int) -> fl
         return 24.0 * items
     if kernel == "tile_ranges":
         return 8.0 * items + 8.0 * tiles
+    # fused frame (items: Gaussians, or pairs for the tile passes)
+    if kernel == "frame_count":      # records in; counts, depth key, index out
+        return 28.0 * items
+    if kernel == "depth_sort":       # (u32 key, u32 index) in and out
+        return 16.0 * items
+    if kernel == "duplicate_by_depth":  # order, offsets, records in; 4 B per pair out
+        return 24.0 * items + 4.0 * m
+    if kernel == "tile_sort_pass":   # 4 B element in; 4 B out, or 12 B for the expanding pass
+        return 16.0 * items
+    if kernel == "ranges_from_diff":
+        return 8.0 * items
     return 0.0
 
 

@@ -38,7 +38,8 @@ uint32_t grid_for(const Kernel& k, uint32_t m) {
   if (resident == 0) return 0;
   const uint64_t tile = static_cast<uint64_t>(k.threads) * k.items;
   const uint32_t need = static_cast<uint32_t>((static_cast<uint64_t>(m) + tile - 1) / tile);
-  const uint32_t g = need < resident ? need : resident;
+  uint32_t g = need < resident ? need : resident;
+  if (g > kMaxGrid) g = kMaxGrid;
   return g ? g : 1;
 }
 

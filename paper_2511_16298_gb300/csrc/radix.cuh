@@ -30,6 +30,7 @@ namespace tdgs {
 namespace radix {
 
 constexpr uint32_t kNoDigit = 0xffffffffu;
+constexpr uint32_t kMaxGrid = 512;  // chunks per pass (the column scan holds 16 per lane)
 
 __device__ __forceinline__ uint64_t policy_evict_last() {
   uint64_t p;
@@ -203,11 +204,10 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
         const uint64_t i = i0 + u * 32 + lane;
-        bad |= (static_cast<uint64_t>(k8[u]) & a.bad_mask) != 0;
-        const uint32_t d = i < end ? digit_of<K>(k8[u], a.shift, a.mask, d31) : kNoDigit;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (d != kNoDigit && lane == static_cast<uint32_t>(__ffs(peers) - 1))
-          atomicAdd(&lstart[d], static_cast<uint32_t>(__popc(peers)));
+        if (i < end) {
+          bad |= (static_cast<uint64_t>(k8[u]) & a.bad_mask) != 0;
+          atomicAdd(&lstart[digit_of<K>(k8[u], a.shift, a.mask, d31)], 1u);
+        }
       }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) latch_error(a.err, TDGS_ERR_INVALID_ARGUMENT);
@@ -217,21 +217,33 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
   grid_barrier(a.bar, a.err);
 
   // ---- phase 2: column scans over chunks, one warp per digit
+  // Lane l holds chunks l*kCol .. l*kCol+kCol-1 of one digit column; all
+  // loads are issued before the scan so the column costs one L2 round trip.
+  constexpr uint32_t kCol = kMaxGrid / 32;
   for (uint32_t b = c * kWarps + warp; b < static_cast<uint32_t>(kBins); b += G * kWarps) {
-    uint32_t run = 0;
-    for (uint32_t c0 = 0; c0 < G; c0 += 32) {
-      const uint32_t cc = c0 + lane;
-      const uint32_t h = cc < G ? __ldcg(a.H + static_cast<size_t>(cc) * kBins + b) : 0;
-      uint32_t x = h;
+    uint32_t h[kCol];
 #pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t o = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= static_cast<uint32_t>(d)) x += o;
-      }
-      if (cc < G) a.P[static_cast<size_t>(cc) * kBins + b] = run + x - h;
-      run += __shfl_sync(0xffffffffu, x, 31);
+    for (uint32_t q = 0; q < kCol; ++q) {
+      const uint32_t cc = lane * kCol + q;
+      h[q] = cc < G ? __ldcg(a.H + static_cast<size_t>(cc) * kBins + b) : 0u;
     }
-    if (lane == 0) a.tot[b] = run;
+    uint32_t sum = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < kCol; ++q) sum += h[q];
+    uint32_t x = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t o = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= static_cast<uint32_t>(d)) x += o;
+    }
+    uint32_t run = x - sum;
+#pragma unroll
+    for (uint32_t q = 0; q < kCol; ++q) {
+      const uint32_t cc = lane * kCol + q;
+      if (cc < G) a.P[static_cast<size_t>(cc) * kBins + b] = run;
+      run += h[q];
+    }
+    if (lane == 31) a.tot[b] = x;
   }
   grid_barrier(a.bar, a.err);
   {
@@ -278,7 +290,19 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
     for (int j = 0; j < kItems; ++j) {
       const uint32_t idx = wbase + j * 32 + lane;
       const uint32_t d = idx < valid ? digit_of<K>(k[j], a.shift, a.mask, d31) : kNoDigit;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      uint32_t peers;
+      if constexpr (kBits <= 8) {
+        // lanes with equal digits: AND of one ballot per digit bit
+        peers = __ballot_sync(0xffffffffu, d != kNoDigit);
+        if (d == kNoDigit) peers = ~peers;
+#pragma unroll
+        for (int bit = 0; bit < kBits; ++bit) {
+          const uint32_t bal = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+          peers &= ((d >> bit) & 1u) ? bal : ~bal;
+        }
+      } else {
+        peers = __match_any_sync(0xffffffffu, d);
+      }
       const uint32_t leader = __ffs(peers) - 1;
       uint32_t before = 0;
       if (lane == leader && d != kNoDigit) before = my_wh[d];
@@ -333,7 +357,12 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
         r[j] += lstart[d] + my_wh[d];
       }
     }
-    __syncthreads();  // wh is overwritten by the exchange below
+    __syncthreads();  // wh is overwritten by the exchange below; lstart becomes the offset
+#pragma unroll
+    for (int i = 0; i < kBpt; ++i) {
+      const uint32_t b = t + i * kThreads;
+      if (b < kBins) lstart[b] = base[b] - lstart[b];
+    }
 #pragma unroll
     for (int j = 0; j < kItems; ++j)
       if (wbase + j * 32 + lane < valid) xk[r[j]] = k[j];
@@ -349,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
       if (p < valid) {
         const K key = xk[p];
         const uint32_t d = digit_of<K>(key, a.shift, a.mask, d31);
-        dst[i] = base[d] + p - lstart[d];
+        dst[i] = lstart[d] + p;
         if (dst[i] < m) {
           if constexpr (kExpand) {
             const uint32_t rk = static_cast<uint32_t>(key & ((static_cast<K>(1) << a.rbits) - 1));
