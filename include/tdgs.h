@@ -210,6 +210,54 @@ tdgs_status tdgs_sort_frame(tdgs_context* ctx, const tdgs_gaussian2d* g, uint32_
                             const uint32_t** sorted_values, const tdgs_range** ranges,
                             uint32_t* m_out, void* stream);
 
+/* ------------------------------------------------------ several views --- */
+
+/* One view of a batch: its projected Gaussians (device, 16-byte aligned)
+ * and its image size. */
+typedef struct {
+  const tdgs_gaussian2d* g;
+  uint32_t n;
+  tdgs_frame f;
+} tdgs_view;
+
+/* Sorted result of one view: pointers into context-owned device buffers
+ * (valid until the next call on the context), its pair count and tiles.
+ * Keys carry the view's LOCAL tile id; values are indices into the view's
+ * own Gaussian array; ranges index the view's own list. */
+typedef struct {
+  const uint64_t* keys;
+  const uint32_t* values;
+  const tdgs_range* ranges;
+  uint32_t m;
+  uint32_t num_tiles;
+} tdgs_view_result;
+
+/* Steps 1-5 for up to 256 views with one set of passes (the batched form of
+ * the Sorting step, Sec. II-A, over several cameras): each view's result is
+ * byte-identical to tdgs_sort_frame on that view alone.  Waits once for the
+ * pair count; results[num_views] (host) is filled. */
+tdgs_status tdgs_sort_views(tdgs_context* ctx, const tdgs_view* views, uint32_t num_views,
+                            tdgs_view_result* results, void* stream);
+
+/* Allocate everything a batch of this shape needs (same view count, total
+ * Gaussians and total tiles) for up to pair_capacity pairs.  Waits. */
+tdgs_status tdgs_reserve_views(tdgs_context* ctx, const tdgs_view* views, uint32_t num_views,
+                               uint64_t pair_capacity, void* stream);
+
+/* The same work as tdgs_sort_views without any host wait or allocation, so
+ * it can be captured in a CUDA graph and replayed: kernels read the pair
+ * count from device memory.  Requires tdgs_reserve_views with the same
+ * shape.  A batch with more pairs than the reserved capacity latches
+ * TDGS_ERR_CAPACITY (reserve more and run again).  The view table is read
+ * from a host staging buffer the context owns, refreshed by each call. */
+tdgs_status tdgs_sort_views_async(tdgs_context* ctx, const tdgs_view* views, uint32_t num_views,
+                                  void* stream);
+
+/* After tdgs_sort_views_async: wait for `stream`, return the first latched
+ * error, else fill results[num_views]. */
+tdgs_status tdgs_views_results(tdgs_context* ctx, tdgs_view_result* results, uint32_t num_views,
+                               void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,8 +21,25 @@ namespace {
 struct DevStatus {
   uint64_t total;
   uint32_t err;
-  uint32_t pad;
+  uint32_t site;  // which kernel latched err (ErrorSite)
 };
+
+const char* site_name(uint32_t site) {
+  switch (site) {
+    case kSiteCount: return "tile count";
+    case kSiteScan: return "scan";
+    case kSiteScanTimeout: return "scan look-back wait";
+    case kSiteDuplicate: return "duplicate_keys";
+    case kSiteRanges: return "tile_ranges";
+    case kSiteRadixKeys: return "radix pass key check";
+    case kSiteRadixRange: return "radix pass destination out of range";
+    case kSiteRadixCapacity: return "radix pass count above reserved capacity";
+    case kSiteBarrier: return "radix pass grid barrier wait";
+    case kSiteViewsCount: return "frame count";
+    case kSiteViewsDup: return "duplicate by depth";
+  }
+  return "device";
+}
 
 struct Buffer {
   void* p = nullptr;
@@ -31,11 +48,23 @@ struct Buffer {
 
 enum KernelId {
   kKCount, kKScan, kKDuplicate, kKRanges, kKRadixPass,
-  kKFrameCount, kKDepthSort, kKDupDepth, kKTilePass, kKRangesDiff, kKNum
+  kKFrameCount, kKDepthSort, kKDupDepth, kKTilePass, kKRangesFinal, kKPairBegin, kKNum
 };
 const char* const kKernelNames[kKNum] = {
     "count_tiles",  "scan",       "duplicate_keys",     "tile_ranges",    "radix_pass",
-    "frame_count",  "depth_sort", "duplicate_by_depth", "tile_sort_pass", "ranges_from_diff"};
+    "frame_count",  "depth_sort", "duplicate_by_depth", "tile_sort_pass", "ranges_final",
+    "view_pair_begin"};
+
+// View table as stored in device memory (SoA, fixed maximum size).
+struct ViewBlob {
+  const float4* g[kMaxViews];
+  uint64_t vtot[kMaxViews];
+  FrameGeom geom[kMaxViews];
+  uint32_t rec_begin[kMaxViews + 1];
+  uint32_t tile_begin[kMaxViews + 1];
+  uint32_t pbeg[kMaxViews + 1];
+  uint32_t nt[kMaxViews];
+};
 
 struct PendingTime {
   int id;
@@ -52,8 +81,13 @@ struct tdgs_context {
   uint32_t* d_tickets = nullptr;  // [0] scan tiles, [2..3] radix grid barrier
   uint32_t ticket_base[2] = {0, 0};
   Buffer scan_status, sort_scratch;
-  // fused-frame buffers
-  Buffer f_counts, f_dkey[2], f_dval[2], f_soff, f_diff, f_stream[2], f_keys, f_values, f_ranges;
+  // fused-frame / multi-view buffers
+  Buffer f_counts, f_dkey[2], f_dval[2], f_soff, f_rminmax, f_stream[2], f_keys, f_values, f_ranges;
+  ViewBlob* d_views = nullptr;  // device view table
+  ViewBlob* h_views = nullptr;  // pinned staging of the table
+  uint32_t nv = 0, n_all = 0, t_all = 0;
+  uint64_t capacity = 0;        // pair capacity reserved for the asynchronous path
+  bool reserved = false;
   int variant_override = -1;
   std::string last_error;
   // tracing
@@ -201,11 +235,11 @@ tdgs_status do_scan(tdgs_context* ctx, const uint32_t* counts, const float4* rec
   tdgs_status st = ensure(ctx, ctx->scan_status, static_cast<size_t>(tiles) * 8, s);
   if (st != TDGS_OK) return st;
   TDGS_CUDA(ctx, cudaMemsetAsync(ctx->scan_status.p, 0, static_cast<size_t>(tiles) * 8, s));
+  TDGS_CUDA(ctx, cudaMemsetAsync(ctx->d_tickets + 0, 0, 4, s));
   TDGS_TRACED(ctx, kKScan, n, s,
               launch_scan(counts, recs, gather, fg, n, offsets,
-                          static_cast<uint64_t*>(ctx->scan_status.p), ctx->d_tickets + 0,
-                          ctx->ticket_base[0], total64, total32, err_word(ctx), s));
-  ctx->ticket_base[0] += tiles;
+                          static_cast<uint64_t*>(ctx->scan_status.p), ctx->d_tickets + 0, 0u,
+                          total64, total32, err_word(ctx), s));
   return TDGS_OK;
 }
 
@@ -235,14 +269,15 @@ tdgs_status do_sort(tdgs_context* ctx, uint64_t* keys, uint32_t* values, uint64_
 }
 
 tdgs_status read_and_clear_error(tdgs_context* ctx, cudaStream_t s) {
-  TDGS_CUDA(ctx, cudaMemcpyAsync(&ctx->h_status->err, &ctx->d_status->err, 4,
+  TDGS_CUDA(ctx, cudaMemcpyAsync(&ctx->h_status->err, &ctx->d_status->err, 8,
                                  cudaMemcpyDeviceToHost, s));
   TDGS_CUDA(ctx, cudaStreamSynchronize(s));
   const uint32_t e = ctx->h_status->err;
   if (e != 0) {
-    TDGS_CUDA(ctx, cudaMemsetAsync(&ctx->d_status->err, 0, 4, s));
+    TDGS_CUDA(ctx, cudaMemsetAsync(&ctx->d_status->err, 0, 8, s));
     TDGS_CUDA(ctx, cudaStreamSynchronize(s));
-    return fail(ctx, static_cast<tdgs_status>(e), "error latched on the device");
+    return fail(ctx, static_cast<tdgs_status>(e),
+                std::string("error latched on the device by ") + site_name(ctx->h_status->site));
   }
   return TDGS_OK;
 }
@@ -312,6 +347,8 @@ tdgs_status tdgs_context_create(tdgs_context** out, int device) {
   if (cudaMalloc(&ctx->d_status, sizeof(DevStatus)) != cudaSuccess ||
       cudaMalloc(&ctx->d_tickets, 4 * sizeof(uint32_t)) != cudaSuccess ||
       cudaMallocHost(&ctx->h_status, sizeof(DevStatus)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_views, sizeof(ViewBlob)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_views, sizeof(ViewBlob)) != cudaSuccess ||
       cudaMemset(ctx->d_status, 0, sizeof(DevStatus)) != cudaSuccess ||
       cudaMemset(ctx->d_tickets, 0, 4 * sizeof(uint32_t)) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {
@@ -363,8 +400,10 @@ void tdgs_context_destroy(tdgs_context* ctx) {
   for (cudaEvent_t e : ctx->free_events) cudaEventDestroy(e);
   Buffer* bufs[] = {&ctx->scan_status, &ctx->sort_scratch, &ctx->f_counts,    &ctx->f_dkey[0],
                     &ctx->f_dkey[1],    &ctx->f_dval[0],     &ctx->f_dval[1],    &ctx->f_soff,
-                    &ctx->f_diff,       &ctx->f_stream[0],   &ctx->f_stream[1],  &ctx->f_keys,
+                    &ctx->f_rminmax,    &ctx->f_stream[0],   &ctx->f_stream[1],  &ctx->f_keys,
                     &ctx->f_values,     &ctx->f_ranges};
+  if (ctx->d_views) cudaFree(ctx->d_views);
+  if (ctx->h_views) cudaFreeHost(ctx->h_views);
   for (Buffer* b : bufs)
     if (b->p) cudaFree(b->p);
   if (ctx->d_status) cudaFree(ctx->d_status);
@@ -465,18 +504,236 @@ tdgs_status tdgs_tile_ranges(tdgs_context* ctx, const uint64_t* sorted_keys, uin
   return TDGS_OK;
 }
 
-// Fused frame, depth first.  Steps (all on `stream`):
-//   1. frame_count: tile counts, depth keys, per-CTA tile difference grids
-//   2. depth_sort: the N Gaussians by (depth bits, index)  -> depth order
-//   3. scan of the counts in depth order -> pair offsets, pair count M
-//   4. (host) read M and the error word; size the pair buffers
-//   5. duplicate_by_depth: element (tile << rbits | depth position) per pair
-//   6. tile_sort_pass x1-2: stable passes on the tile bits; the last one
-//      writes the final keys (tile << 32 | depth bits) and indices
-//   7. ranges_from_diff: per-tile counts from the difference grids, scanned
-// The result equals the stable sort of the 64-bit keys of steps 1-4 of the
-// per-step calls: ties of the 64-bit key are pairs of distinct Gaussians in
-// the same tile with equal depth, which both orders put in index order.
+}  // extern "C"
+
+namespace {
+
+uint32_t bits_for(uint64_t count) {  // smallest b with count <= 2^b
+  uint32_t b = 0;
+  while (b < 64 && (1ull << b) < count) ++b;
+  return b;
+}
+
+// Validate the views, fill the pinned staging table and the totals.
+tdgs_status stage_views(tdgs_context* ctx, const tdgs_view* views, uint32_t nv) {
+  if (nv == 0 || nv > kMaxViews) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "view count out of range");
+  if (!views) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "null views");
+  ViewBlob* h = ctx->h_views;
+  uint64_t n_all = 0, t_all = 0;
+  for (uint32_t v = 0; v < nv; ++v) {
+    const tdgs_view& w = views[v];
+    if (w.f.width == 0 || w.f.height == 0) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "empty image");
+    if (w.n && !w.g) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "null pointer");
+    if (!aligned(w.g, 16)) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "misaligned pointer");
+    h->g[v] = reinterpret_cast<const float4*>(w.g);
+    h->geom[v] = make_geom(w.f);
+    h->rec_begin[v] = static_cast<uint32_t>(n_all);
+    h->tile_begin[v] = static_cast<uint32_t>(t_all);
+    h->nt[v] = tdgs_num_tiles(w.f);
+    h->vtot[v] = 0;
+    n_all += w.n;
+    t_all += h->nt[v];
+  }
+  if (n_all > 0xffffffffull || t_all > 0xffffffffull)
+    return fail(ctx, TDGS_ERR_OVERFLOW, "too many Gaussians or tiles in one batch");
+  h->rec_begin[nv] = static_cast<uint32_t>(n_all);
+  h->tile_begin[nv] = static_cast<uint32_t>(t_all);
+  ctx->nv = nv;
+  ctx->n_all = static_cast<uint32_t>(n_all);
+  ctx->t_all = static_cast<uint32_t>(t_all);
+  return TDGS_OK;
+}
+
+ViewTable device_table(tdgs_context* ctx) {
+  ViewBlob* d = ctx->d_views;
+  ViewTable vt;
+  vt.g = d->g;
+  vt.rec_begin = d->rec_begin;
+  vt.tile_begin = d->tile_begin;
+  vt.geom = d->geom;
+  vt.vtot = d->vtot;
+  vt.pbeg = d->pbeg;
+  vt.nv = ctx->nv;
+  return vt;
+}
+
+struct Shape {
+  uint32_t rbits, tbits;
+  bool wide;
+  uint32_t npass, w0;
+};
+
+Shape shape_of(const tdgs_context* ctx) {
+  Shape sh;
+  sh.rbits = bits_for(ctx->n_all);
+  sh.tbits = bits_for(ctx->t_all);
+  sh.wide = sh.tbits + sh.rbits > 32 || sh.rbits >= 32;
+  sh.npass = sh.tbits <= 8 ? 1u : (sh.tbits + 7) / 8;   // digits of at most 8 bits
+  sh.w0 = (sh.tbits + sh.npass - 1) / std::max(1u, sh.npass);
+  return sh;
+}
+
+// Buffers that depend only on the record and tile counts.
+tdgs_status ensure_record_buffers(tdgs_context* ctx, cudaStream_t s) {
+  const size_t n4 = static_cast<size_t>(ctx->n_all) * 4 + 16;
+  tdgs_status st = TDGS_OK;
+  for (Buffer* b : {&ctx->f_counts, &ctx->f_dkey[0], &ctx->f_dkey[1], &ctx->f_dval[0],
+                    &ctx->f_dval[1], &ctx->f_soff})
+    if (st == TDGS_OK) st = ensure(ctx, *b, n4, s);
+  if (st == TDGS_OK) st = ensure(ctx, ctx->f_rminmax, static_cast<size_t>(ctx->t_all) * 8 + 16, s);
+  if (st == TDGS_OK) st = ensure(ctx, ctx->f_ranges, static_cast<size_t>(ctx->t_all) * 8 + 16, s);
+  const uint32_t n_all = ctx->n_all;
+  const uint32_t tiles = (n_all + kScanTileItems - 1) / kScanTileItems;
+  if (st == TDGS_OK) st = ensure(ctx, ctx->scan_status, static_cast<size_t>(tiles) * 8 + 8, s);
+  const uint32_t dgrid = depth_sort_grid(n_all ? n_all : 1);
+  if (dgrid == 0) return fail(ctx, TDGS_ERR_CUDA, "device query for the depth sort failed");
+  if (st == TDGS_OK) st = ensure(ctx, ctx->sort_scratch, depth_sort_scratch_words(dgrid) * 4, s);
+  return st;
+}
+
+// Buffers that depend on the pair count (or capacity) m.
+tdgs_status ensure_pair_buffers(tdgs_context* ctx, uint64_t m, cudaStream_t s) {
+  const Shape sh = shape_of(ctx);
+  const size_t esz = sh.wide ? 8 : 4;
+  tdgs_status st = TDGS_OK;
+  for (int b = 0; b < 2 && st == TDGS_OK; ++b) st = ensure(ctx, ctx->f_stream[b], m * esz + 16, s);
+  if (st == TDGS_OK) st = ensure(ctx, ctx->f_keys, m * 8 + 16, s);
+  if (st == TDGS_OK) st = ensure(ctx, ctx->f_values, m * 4 + 16, s);
+  const uint32_t mm = static_cast<uint32_t>(m ? m : 1);
+  const uint32_t g0 = stream_grid(sh.wide, false, mm), g1 = stream_grid(sh.wide, true, mm);
+  if (g0 == 0 || g1 == 0) return fail(ctx, TDGS_ERR_CUDA, "device query for the tile sort failed");
+  if (st == TDGS_OK)
+    st = ensure(ctx, ctx->sort_scratch,
+                std::max(stream_scratch_words(sh.wide, false, g0), stream_scratch_words(sh.wide, true, g1)) * 4,
+                s);
+  return st;
+}
+
+// Steps before the pair count is known: view table upload, counts, depth
+// sort, scan in depth order (total -> d_status->total).
+tdgs_status run_front(tdgs_context* ctx, cudaStream_t s) {
+  const ViewTable vt = device_table(ctx);
+  const uint32_t n_all = ctx->n_all;
+  TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->d_views, ctx->h_views, sizeof(ViewBlob), cudaMemcpyHostToDevice, s));
+  uint32_t* counts = static_cast<uint32_t*>(ctx->f_counts.p);
+  uint32_t* dk[2] = {static_cast<uint32_t*>(ctx->f_dkey[0].p), static_cast<uint32_t*>(ctx->f_dkey[1].p)};
+  uint32_t* dv[2] = {static_cast<uint32_t*>(ctx->f_dval[0].p), static_cast<uint32_t*>(ctx->f_dval[1].p)};
+  TDGS_TRACED(ctx, kKFrameCount, n_all, s, launch_views_count(vt, n_all, counts, dk[0], dv[0], err_word(ctx), s));
+  TDGS_TRACED(ctx, kKPairBegin, 1, s, launch_views_pair_begin(vt, s));
+  const uint32_t dgrid = depth_sort_grid(n_all ? n_all : 1);
+  for (uint32_t p = 0; p < kDepthPasses; ++p) {
+    TDGS_TRACED(ctx, kKDepthSort, n_all, s,
+                launch_depth_pass(dgrid, p, dk[p & 1], dv[p & 1], dk[(p + 1) & 1], dv[(p + 1) & 1],
+                                  n_all, static_cast<uint32_t*>(ctx->sort_scratch.p), ctx->d_tickets + 2,
+                                  err_word(ctx), s));
+  }
+  if (n_all) {
+    tdgs_status st = do_scan(ctx, counts, nullptr, dv[kDepthPasses & 1], FrameGeom{}, n_all,
+                             static_cast<uint32_t*>(ctx->f_soff.p), &ctx->d_status->total, nullptr, s);
+    if (st != TDGS_OK) return st;
+  } else {
+    TDGS_CUDA(ctx, cudaMemsetAsync(&ctx->d_status->total, 0, 8, s));
+  }
+  return TDGS_OK;
+}
+
+// Steps after: duplication, tile passes, ranges.  m = exact pair count, or
+// the reserved capacity with m_dev pointing at the device count.
+tdgs_status run_back(tdgs_context* ctx, uint32_t m, const uint64_t* m_dev, cudaStream_t s) {
+  const ViewTable vt = device_table(ctx);
+  const Shape sh = shape_of(ctx);
+  const uint32_t n_all = ctx->n_all;
+  const uint32_t* sdepth = static_cast<uint32_t*>(ctx->f_dkey[kDepthPasses & 1].p);
+  const uint32_t* sorder = static_cast<uint32_t*>(ctx->f_dval[kDepthPasses & 1].p);
+  uint32_t* scratch = static_cast<uint32_t*>(ctx->sort_scratch.p);
+  uint32_t* bar = ctx->d_tickets + 2;
+  void* st[2] = {ctx->f_stream[0].p, ctx->f_stream[1].p};
+  uint32_t* rmin = static_cast<uint32_t*>(ctx->f_rminmax.p);
+  uint32_t* rmax = rmin + ctx->t_all;
+  TDGS_TRACED(ctx, kKDupDepth, m ? n_all : 0, s,
+              launch_views_dup(vt, sorder, static_cast<uint32_t*>(ctx->f_soff.p), n_all, sh.rbits, st[0],
+                               sh.wide, m, err_word(ctx), s));
+  TDGS_CUDA(ctx, cudaMemsetAsync(rmin, 0xff, static_cast<size_t>(ctx->t_all) * 4, s));
+  TDGS_CUDA(ctx, cudaMemsetAsync(rmax, 0, static_cast<size_t>(ctx->t_all) * 4, s));
+  const uint32_t mm = m ? m : 1;
+  uint32_t shift = sh.rbits;
+  for (uint32_t p = 0; p < sh.npass; ++p) {
+    const bool last = p + 1 == sh.npass;
+    const uint32_t width = last ? sh.tbits - (shift - sh.rbits) : sh.w0;
+    StreamPass sp{};
+    sp.wide = sh.wide;
+    sp.expand = last;
+    sp.grid = stream_grid(sh.wide, last, mm);
+    sp.kin = st[p & 1];
+    sp.kout = last ? ctx->f_keys.p : st[(p + 1) & 1];
+    sp.vout = last ? static_cast<uint32_t*>(ctx->f_values.p) : nullptr;
+    sp.m = m;
+    sp.m_dev = m_dev;
+    sp.shift = shift;
+    sp.width = width;
+    sp.rbits = sh.rbits;
+    sp.sdepth = sdepth;
+    sp.sorder = sorder;
+    sp.views = &vt;
+    sp.rmin = last ? rmin : nullptr;
+    sp.rmax = last ? rmax : nullptr;
+    TDGS_TRACED(ctx, kKTilePass, m, s, launch_stream_pass(sp, scratch, bar, err_word(ctx), s));
+    shift += width;
+  }
+  TDGS_TRACED(ctx, kKRangesFinal, ctx->t_all, s,
+              launch_views_ranges(vt, rmin, rmax, ctx->t_all, static_cast<uint2*>(ctx->f_ranges.p), s));
+  return TDGS_OK;
+}
+
+// Exact mode: one host wait for the pair count (and the per-view counts).
+tdgs_status sort_views_exact(tdgs_context* ctx, cudaStream_t s, uint32_t* m_out) {
+  tdgs_status st = ensure_record_buffers(ctx, s);
+  if (st != TDGS_OK) return st;
+  st = run_front(ctx, s);
+  if (st != TDGS_OK) return st;
+  TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  TDGS_CUDA(ctx, cudaStreamSynchronize(s));
+  if (ctx->h_status->err) {
+    const tdgs_status e = static_cast<tdgs_status>(ctx->h_status->err);
+    TDGS_CUDA(ctx, cudaMemsetAsync(&ctx->d_status->err, 0, 8, s));
+    return fail(ctx, e, std::string("error latched on the device by ") + site_name(ctx->h_status->site));
+  }
+  const uint64_t total = ctx->h_status->total;
+  if (total > 0xffffffffull) return fail(ctx, TDGS_ERR_OVERFLOW, "pair count above 2^32-1");
+  const uint32_t m = static_cast<uint32_t>(total);
+  st = ensure_pair_buffers(ctx, m, s);
+  if (st != TDGS_OK) return st;
+  st = run_back(ctx, m, nullptr, s);
+  if (st != TDGS_OK) return st;
+  *m_out = m;
+  return TDGS_OK;
+}
+
+// Per-view results, read after the work on `s` is complete.
+tdgs_status fill_results(tdgs_context* ctx, tdgs_view_result* results, uint32_t nv, cudaStream_t s) {
+  tdgs_status st = read_and_clear_error(ctx, s);
+  if (st != TDGS_OK) return st;
+  TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_views->pbeg, ctx->d_views->pbeg, sizeof(uint32_t) * (nv + 1),
+                                 cudaMemcpyDeviceToHost, s));
+  TDGS_CUDA(ctx, cudaStreamSynchronize(s));
+  const uint64_t* k = static_cast<const uint64_t*>(ctx->f_keys.p);
+  const uint32_t* v = static_cast<const uint32_t*>(ctx->f_values.p);
+  const tdgs_range* r = static_cast<const tdgs_range*>(ctx->f_ranges.p);
+  for (uint32_t i = 0; i < nv; ++i) {
+    const uint32_t b = ctx->h_views->pbeg[i], e = ctx->h_views->pbeg[i + 1];
+    results[i].keys = k + b;
+    results[i].values = v + b;
+    results[i].ranges = r + ctx->h_views->tile_begin[i];
+    results[i].m = e - b;
+    results[i].num_tiles = ctx->h_views->nt[i];
+  }
+  return TDGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 tdgs_status tdgs_sort_frame(tdgs_context* ctx, const tdgs_gaussian2d* g, uint32_t n,
                             tdgs_frame f, const uint64_t** sorted_keys,
                             const uint32_t** sorted_values, const tdgs_range** ranges,
@@ -484,119 +741,74 @@ tdgs_status tdgs_sort_frame(tdgs_context* ctx, const tdgs_gaussian2d* g, uint32_
   if (!ctx || !sorted_keys || !sorted_values || !ranges || !m_out)
     return TDGS_ERR_INVALID_ARGUMENT;
   *m_out = 0;
-  if (f.width == 0 || f.height == 0) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "empty image");
-  if (n && !g) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "null pointer");
-  if (!aligned(g, 16)) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "misaligned pointer");
   DeviceGuard dg(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const FrameGeom fg = make_geom(f);
-  const uint32_t T = tdgs_num_tiles(f);
-  const uint32_t tb = tdgs_tile_bits(f);
-  const float4* rec = reinterpret_cast<const float4*>(g);
-  uint32_t rbits = 0;
-  while (rbits < 32 && (1ull << rbits) < n) ++rbits;
-  const bool wide = tb + rbits > 32 || rbits >= 32;
-  const uint64_t cells = static_cast<uint64_t>(fg.gx + 1) * (fg.gy + 1);
-  const bool use_diff = cells <= kMaxDiffCells;
-  const uint32_t count_grid = use_diff ? 152u * 2u : 152u * 8u;
-
-  tdgs_status st = TDGS_OK;
-  const size_t n4 = static_cast<size_t>(n) * 4 + 16;
-  for (Buffer* b : {&ctx->f_counts, &ctx->f_dkey[0], &ctx->f_dkey[1], &ctx->f_dval[0],
-                    &ctx->f_dval[1], &ctx->f_soff})
-    if (st == TDGS_OK) st = ensure(ctx, *b, n4, s);
-  if (st == TDGS_OK && use_diff) st = ensure(ctx, ctx->f_diff, (count_grid + 1) * cells * 4, s);
-  if (st == TDGS_OK) st = ensure(ctx, ctx->f_ranges, static_cast<size_t>(T) * 8, s);
-  const uint32_t dgrid = depth_sort_grid(n ? n : 1);
-  if (dgrid == 0) return fail(ctx, TDGS_ERR_CUDA, "device query for the depth sort failed");
-  if (st == TDGS_OK) st = ensure(ctx, ctx->sort_scratch, depth_sort_scratch_words(dgrid) * 4, s);
+  tdgs_view view{g, n, f};
+  tdgs_status st = stage_views(ctx, &view, 1);
   if (st != TDGS_OK) return st;
-  uint32_t* counts = static_cast<uint32_t*>(ctx->f_counts.p);
-  uint32_t* dk[2] = {static_cast<uint32_t*>(ctx->f_dkey[0].p), static_cast<uint32_t*>(ctx->f_dkey[1].p)};
-  uint32_t* dv[2] = {static_cast<uint32_t*>(ctx->f_dval[0].p), static_cast<uint32_t*>(ctx->f_dval[1].p)};
-  uint32_t* soff = static_cast<uint32_t*>(ctx->f_soff.p);
-  int32_t* diff = use_diff ? static_cast<int32_t*>(ctx->f_diff.p) : nullptr;
-  uint32_t* scratch = static_cast<uint32_t*>(ctx->sort_scratch.p);
-  uint32_t* bar = ctx->d_tickets + 2;
-
-  // 1-3
-  TDGS_TRACED(ctx, kKFrameCount, n, s,
-              launch_frame_count(rec, n, fg, counts, dk[0], dv[0], diff, count_grid, err_word(ctx), s));
-  for (uint32_t p = 0; p < kDepthPasses; ++p) {
-    TDGS_TRACED(ctx, kKDepthSort, n, s,
-                launch_depth_pass(dgrid, p, dk[p & 1], dv[p & 1], dk[(p + 1) & 1], dv[(p + 1) & 1], n,
-                                  scratch, bar, err_word(ctx), s));
-  }
-  const uint32_t* sdepth = dk[kDepthPasses & 1];
-  const uint32_t* sorder = dv[kDepthPasses & 1];
-  if (n) {
-    st = do_scan(ctx, counts, nullptr, sorder, fg, n, soff, &ctx->d_status->total, nullptr, s);
-    if (st != TDGS_OK) return st;
-  } else {
-    TDGS_CUDA(ctx, cudaMemsetAsync(&ctx->d_status->total, 0, 8, s));
-  }
-  // 4
-  TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(DevStatus),
-                                 cudaMemcpyDeviceToHost, s));
-  TDGS_CUDA(ctx, cudaStreamSynchronize(s));
-  if (ctx->h_status->err) {
-    const tdgs_status e = static_cast<tdgs_status>(ctx->h_status->err);
-    TDGS_CUDA(ctx, cudaMemsetAsync(&ctx->d_status->err, 0, 4, s));
-    return fail(ctx, e, "error latched on the device");
-  }
-  const uint64_t total = ctx->h_status->total;
-  if (total > 0xffffffffull) return fail(ctx, TDGS_ERR_OVERFLOW, "pair count above 2^32-1");
-  const uint32_t m = static_cast<uint32_t>(total);
-  const size_t esz = wide ? 8 : 4;
-  for (int b = 0; b < 2 && st == TDGS_OK; ++b)
-    st = ensure(ctx, ctx->f_stream[b], static_cast<size_t>(m) * esz + 16, s);
-  if (st == TDGS_OK) st = ensure(ctx, ctx->f_keys, static_cast<size_t>(m) * 8 + 16, s);
-  if (st == TDGS_OK) st = ensure(ctx, ctx->f_values, static_cast<size_t>(m) * 4 + 16, s);
-  // 5-6
-  const uint32_t npass = tb <= 8 ? 1u : 2u;
-  const uint32_t w0 = npass == 1 ? tb : (tb + 1) / 2;
-  const uint32_t sgrid = stream_grid(wide, npass == 1, m ? m : 1);
-  const uint32_t sgrid_x = stream_grid(wide, true, m ? m : 1);
-  if (sgrid == 0 || sgrid_x == 0) return fail(ctx, TDGS_ERR_CUDA, "device query for the tile sort failed");
-  if (st == TDGS_OK)
-    st = ensure(ctx, ctx->sort_scratch,
-                std::max(stream_scratch_words(wide, false, sgrid), stream_scratch_words(wide, true, sgrid_x)) * 4,
-                s);
+  ctx->reserved = false;
+  uint32_t m = 0;
+  st = sort_views_exact(ctx, s, &m);
   if (st != TDGS_OK) return st;
-  scratch = static_cast<uint32_t*>(ctx->sort_scratch.p);
-  void* s0 = ctx->f_stream[0].p;
-  void* s1 = ctx->f_stream[1].p;
-  uint64_t* okeys = static_cast<uint64_t*>(ctx->f_keys.p);
-  uint32_t* ovals = static_cast<uint32_t*>(ctx->f_values.p);
-  TDGS_TRACED(ctx, kKDupDepth, m ? n : 0, s,
-              launch_dup_depth(rec, sorder, soff, n, fg, rbits, s0, wide, m, err_word(ctx), s));
-  if (npass == 1) {
-    TDGS_TRACED(ctx, kKTilePass, m, s,
-                launch_stream_pass(wide, true, sgrid_x, s0, okeys, ovals, m, rbits, tb, rbits, sdepth,
-                                   sorder, scratch, bar, err_word(ctx), s));
-  } else {
-    TDGS_TRACED(ctx, kKTilePass, m, s,
-                launch_stream_pass(wide, false, sgrid, s0, s1, nullptr, m, rbits, w0, rbits, sdepth,
-                                   sorder, scratch, bar, err_word(ctx), s));
-    TDGS_TRACED(ctx, kKTilePass, m, s,
-                launch_stream_pass(wide, true, sgrid_x, s1, okeys, ovals, m, rbits + w0, tb - w0, rbits,
-                                   sdepth, sorder, scratch, bar, err_word(ctx), s));
-  }
-  // 7
-  uint2* rg = static_cast<uint2*>(ctx->f_ranges.p);
-  if (use_diff && n) {
-    TDGS_TRACED(ctx, kKRangesDiff, T, s,
-                launch_ranges_from_diff(diff, count_grid, fg, diff + count_grid * cells, rg,
-                                        err_word(ctx), s));
-  } else {
-    TDGS_CUDA(ctx, cudaMemsetAsync(rg, 0, static_cast<size_t>(T) * 8, s));
-    TDGS_TRACED(ctx, kKRanges, m, s, launch_tile_ranges(okeys, m, T, rg, err_word(ctx), s));
-  }
-  *sorted_keys = okeys;
-  *sorted_values = ovals;
-  *ranges = reinterpret_cast<const tdgs_range*>(rg);
+  *sorted_keys = static_cast<const uint64_t*>(ctx->f_keys.p);
+  *sorted_values = static_cast<const uint32_t*>(ctx->f_values.p);
+  *ranges = static_cast<const tdgs_range*>(ctx->f_ranges.p);
   *m_out = m;
   return TDGS_OK;
+}
+
+tdgs_status tdgs_sort_views(tdgs_context* ctx, const tdgs_view* views, uint32_t num_views,
+                            tdgs_view_result* results, void* stream) {
+  if (!ctx || !results) return TDGS_ERR_INVALID_ARGUMENT;
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  tdgs_status st = stage_views(ctx, views, num_views);
+  if (st != TDGS_OK) return st;
+  ctx->reserved = false;
+  uint32_t m = 0;
+  st = sort_views_exact(ctx, s, &m);
+  if (st != TDGS_OK) return st;
+  return fill_results(ctx, results, num_views, s);
+}
+
+tdgs_status tdgs_reserve_views(tdgs_context* ctx, const tdgs_view* views, uint32_t num_views,
+                               uint64_t pair_capacity, void* stream) {
+  if (!ctx) return TDGS_ERR_INVALID_ARGUMENT;
+  if (pair_capacity > 0xffffffffull) return fail(ctx, TDGS_ERR_OVERFLOW, "capacity above 2^32-1");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  tdgs_status st = stage_views(ctx, views, num_views);
+  if (st == TDGS_OK) st = ensure_record_buffers(ctx, s);
+  if (st == TDGS_OK) st = ensure_pair_buffers(ctx, pair_capacity, s);
+  if (st != TDGS_OK) return st;
+  TDGS_CUDA(ctx, cudaStreamSynchronize(s));
+  ctx->capacity = pair_capacity;
+  ctx->reserved = true;
+  return TDGS_OK;
+}
+
+tdgs_status tdgs_sort_views_async(tdgs_context* ctx, const tdgs_view* views, uint32_t num_views,
+                                  void* stream) {
+  if (!ctx) return TDGS_ERR_INVALID_ARGUMENT;
+  if (!ctx->reserved) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "call tdgs_reserve_views first");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint32_t n_prev = ctx->n_all, t_prev = ctx->t_all, nv_prev = ctx->nv;
+  tdgs_status st = stage_views(ctx, views, num_views);
+  if (st != TDGS_OK) return st;
+  if (ctx->n_all != n_prev || ctx->t_all != t_prev || ctx->nv != nv_prev)
+    return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "views differ in shape from the reservation");
+  st = run_front(ctx, s);
+  if (st != TDGS_OK) return st;
+  return run_back(ctx, static_cast<uint32_t>(ctx->capacity), &ctx->d_status->total, s);
+}
+
+tdgs_status tdgs_views_results(tdgs_context* ctx, tdgs_view_result* results, uint32_t num_views,
+                               void* stream) {
+  if (!ctx || !results || num_views != ctx->nv) return TDGS_ERR_INVALID_ARGUMENT;
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return fill_results(ctx, results, num_views, s);
 }
 
 }  // extern "C"

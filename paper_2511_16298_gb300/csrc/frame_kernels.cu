@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(256) k_count_tiles(const float4* __restrict__ 
     bad |= q.invalid;
     counts[i] = q.count;
   }
-  if (__any_sync(0xffffffffu, bad) && lane_id() == 0) latch_error(err, TDGS_ERR_INVALID_ARGUMENT);
+  if (__any_sync(0xffffffffu, bad) && lane_id() == 0) latch_error(err, TDGS_ERR_INVALID_ARGUMENT, kSiteCount);
 }
 
 cudaError_t launch_count_tiles(const float4* g, uint32_t n, FrameGeom fg, uint32_t* counts,
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kScanThreads)
     s_items[spad(p)] = v;
   }
   if (kFromRecords && __any_sync(0xffffffffu, bad) && lane == 0)
-    latch_error(err, TDGS_ERR_INVALID_ARGUMENT);
+    latch_error(err, TDGS_ERR_INVALID_ARGUMENT, kSiteScan);
   __syncthreads();
   uint32_t mine[kScanItems];
   uint64_t tsum = 0;
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kScanThreads)
           }
         }
         if (spins > kSpinLimit) {
-          if (lane == 0) latch_error(err, TDGS_ERR_TIMEOUT);
+          if (lane == 0) latch_error(err, TDGS_ERR_TIMEOUT, kSiteScanTimeout);
           break;
         }
         const uint32_t pmask = __ballot_sync(0xffffffffu, (s >> 62) == 2);
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kScanThreads)
   __syncthreads();
   const uint64_t tile_excl = s_excl;
   const uint64_t incl_end = tile_excl + agg;
-  if (incl_end > 0xffffffffull && t == 0) latch_error(err, TDGS_ERR_OVERFLOW);
+  if (incl_end > 0xffffffffull && t == 0) latch_error(err, TDGS_ERR_OVERFLOW, kSiteScan);
   uint64_t run = tile_excl + texcl;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
@@ -264,8 +264,8 @@ __global__ void __launch_bounds__(256)
       }
     }
   }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) latch_error(err, TDGS_ERR_INVALID_ARGUMENT);
-  if (__any_sync(0xffffffffu, over) && lane == 0) latch_error(err, TDGS_ERR_CAPACITY);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) latch_error(err, TDGS_ERR_INVALID_ARGUMENT, kSiteDuplicate);
+  if (__any_sync(0xffffffffu, over) && lane == 0) latch_error(err, TDGS_ERR_CAPACITY, kSiteDuplicate);
 }
 
 cudaError_t launch_duplicate(const float4* g, const uint32_t* offsets, uint32_t n,
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(256) k_tile_ranges(const uint64_t* __restrict_
     if (t != prev) ranges[t].x = k;
     if (t != next) ranges[t].y = k + 1;
   }
-  if (__any_sync(0xffffffffu, bad) && lane_id() == 0) latch_error(err, TDGS_ERR_INVALID_ARGUMENT);
+  if (__any_sync(0xffffffffu, bad) && lane_id() == 0) latch_error(err, TDGS_ERR_INVALID_ARGUMENT, kSiteRanges);
 }
 
 cudaError_t launch_tile_ranges(const uint64_t* keys, uint32_t m, uint32_t num_tiles,
@@ -307,249 +307,6 @@ cudaError_t launch_tile_ranges(const uint64_t* keys, uint32_t m, uint32_t num_ti
   const uint32_t blocks = (m + 255) / 256;
   const uint32_t grid = blocks < 152u * 16u ? blocks : 152u * 16u;
   k_tile_ranges<<<grid, 256, 0, s>>>(keys, m, num_tiles, ranges, err);
-  return cudaGetLastError();
-}
-
-// ====================================================== depth-first frame
-// The fused frame sorts the N Gaussians by depth first and emits every
-// Gaussian's pairs in depth order; a stable sort on the tile bits alone
-// then yields the order by (tile, depth, index) that the stable 64-bit key
-// sort defines (equal keys come from distinct Gaussians in index order).
-
-// Per Gaussian: tile count, the depth sort key (raw depth bits for a
-// visible Gaussian, all ones otherwise so culled ones sort last) and its
-// index; per CTA: a 2D difference grid of the tile rectangles, written to
-// diff_part[blockIdx.x][(gy+1)*(gx+1)] (rect [x0,x1)x[y0,y1) adds +1 at
-// (y0,x0) and (y1,x1), -1 at (y0,x1) and (y1,x0)).  diff_part may be null.
-__global__ void __launch_bounds__(256)
-    k_frame_count(const float4* __restrict__ g, uint32_t n, FrameGeom fg,
-                  uint32_t* __restrict__ counts, uint32_t* __restrict__ dkey,
-                  uint32_t* __restrict__ dval, int32_t* __restrict__ diff_part, uint32_t* err) {
-  extern __shared__ int32_t sdiff[];
-  const uint32_t gw = static_cast<uint32_t>(fg.gx) + 1;
-  const uint32_t E = gw * (static_cast<uint32_t>(fg.gy) + 1);
-  if (diff_part) {
-    for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) sdiff[e] = 0;
-    __syncthreads();
-  }
-  bool bad = false;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const float4 rec = __ldg(g + i);
-    const TileRect q = tile_rect(rec, fg);
-    bad |= q.invalid;
-    counts[i] = q.count;
-    dkey[i] = q.count ? __float_as_uint(rec.z) : 0xffffffffu;
-    dval[i] = i;
-    if (diff_part && q.count) {
-      atomicAdd(&sdiff[q.y0 * gw + q.x0], 1);
-      atomicAdd(&sdiff[q.y0 * gw + q.x1], -1);
-      atomicAdd(&sdiff[q.y1 * gw + q.x0], -1);
-      atomicAdd(&sdiff[q.y1 * gw + q.x1], 1);
-    }
-  }
-  if (__any_sync(0xffffffffu, bad) && lane_id() == 0) latch_error(err, TDGS_ERR_INVALID_ARGUMENT);
-  if (diff_part) {
-    __syncthreads();
-    int32_t* out = diff_part + static_cast<size_t>(blockIdx.x) * E;
-    for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) out[e] = sdiff[e];
-  }
-}
-
-cudaError_t launch_frame_count(const float4* g, uint32_t n, FrameGeom fg, uint32_t* counts,
-                               uint32_t* dkey, uint32_t* dval, int32_t* diff_part,
-                               uint32_t grid, uint32_t* err, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  const size_t E = static_cast<size_t>(fg.gx + 1) * (fg.gy + 1);
-  const size_t smem = diff_part ? E * 4 : 0;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_frame_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-  }
-  k_frame_count<<<grid, 256, smem, s>>>(g, n, fg, counts, dkey, dval, diff_part, err);
-  return cudaGetLastError();
-}
-
-// Duplicate in depth order: position j of the depth order is Gaussian
-// g = sorder[j]; its pairs start at soff[j] and each is the packed element
-// (tile << rbits) | j.  Same warp-cooperative expansion as k_duplicate.
-template <typename K>
-__global__ void __launch_bounds__(256)
-    k_dup_depth(const float4* __restrict__ g, const uint32_t* __restrict__ sorder,
-                const uint32_t* __restrict__ soff, uint32_t n, FrameGeom fg, uint32_t rbits,
-                K* __restrict__ out, uint32_t cap, uint32_t* err) {
-  const uint32_t lane = lane_id();
-  const uint32_t warps_total = (gridDim.x * blockDim.x) >> 5;
-  bool over = false;
-  for (uint32_t wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-       static_cast<uint64_t>(wg) * 32u < n; wg += warps_total) {
-    const uint32_t j = wg * 32u + lane;
-    TileRect q;
-    uint64_t start = 0;
-    const uint32_t gi = j < n ? __ldg(sorder + j) : 0xffffffffu;
-    if (gi < n) {  // a depth order that is not a permutation of [0, n) is never followed
-      q = tile_rect(__ldg(g + gi), fg);
-      start = __ldg(soff + j);
-    } else {
-      q.x0 = q.y0 = q.x1 = q.y1 = 0;
-      q.count = 0;
-    }
-    const uint64_t end = start + q.count;
-    uint64_t end_max = end;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-      const uint64_t o = __shfl_xor_sync(0xffffffffu, end_max, d);
-      end_max = o > end_max ? o : end_max;
-    }
-    if (j >= n) start = end_max;
-    const uint64_t begin = __shfl_sync(0xffffffffu, start, 0);
-    const int32_t w = q.x1 - q.x0;
-    for (uint64_t c = begin; c < end_max; c += 32) {
-      const uint64_t p = c + lane;
-      uint32_t lo = 0;
-#pragma unroll
-      for (uint32_t step = 16; step > 0; step >>= 1) {
-        const uint64_t sc = __shfl_sync(0xffffffffu, start, lo + step);
-        if (sc <= p) lo += step;
-      }
-      const uint64_t s0 = __shfl_sync(0xffffffffu, start, lo);
-      const int32_t ow = __shfl_sync(0xffffffffu, w, lo);
-      const int32_t ox0 = __shfl_sync(0xffffffffu, q.x0, lo);
-      const int32_t oy0 = __shfl_sync(0xffffffffu, q.y0, lo);
-      if (p < end_max && ow > 0) {
-        const uint32_t jj = static_cast<uint32_t>(p - s0);
-        const uint32_t ry = jj / static_cast<uint32_t>(ow);
-        const uint32_t rx = jj - ry * static_cast<uint32_t>(ow);
-        const uint64_t tile = static_cast<uint64_t>(oy0 + ry) * static_cast<uint64_t>(fg.gx) +
-                              static_cast<uint64_t>(ox0 + rx);
-        if (p < cap) out[p] = static_cast<K>((tile << rbits) | (wg * 32u + lo));
-        else over = true;
-      }
-    }
-  }
-  if (__any_sync(0xffffffffu, over) && lane == 0) latch_error(err, TDGS_ERR_CAPACITY);
-}
-
-cudaError_t launch_dup_depth(const float4* g, const uint32_t* sorder, const uint32_t* soff,
-                             uint32_t n, FrameGeom fg, uint32_t rbits, void* out, bool wide,
-                             uint32_t cap, uint32_t* err, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  const uint32_t warps = (n + 31) / 32;
-  const uint32_t blocks = (warps + 7) / 8;
-  const uint32_t grid = blocks < 152u * 32u ? blocks : 152u * 32u;
-  if (wide)
-    k_dup_depth<uint64_t><<<grid, 256, 0, s>>>(g, sorder, soff, n, fg, rbits,
-                                               static_cast<uint64_t*>(out), cap, err);
-  else
-    k_dup_depth<uint32_t><<<grid, 256, 0, s>>>(g, sorder, soff, n, fg, rbits,
-                                               static_cast<uint32_t*>(out), cap, err);
-  return cudaGetLastError();
-}
-
-// Sum of the per-CTA difference grids: block (x, y) adds parts
-// [y*parts/gridDim.y, (y+1)*parts/gridDim.y) of cells [256x, 256x+256) into
-// diff (zeroed beforehand).
-__global__ void __launch_bounds__(256)
-    k_diff_reduce(const int32_t* __restrict__ diff_part, uint32_t parts, uint32_t E,
-                  int32_t* __restrict__ diff) {
-  const uint32_t e = blockIdx.x * 256 + threadIdx.x;
-  if (e >= E) return;
-  const uint32_t c0 = blockIdx.y * parts / gridDim.y, c1 = (blockIdx.y + 1) * parts / gridDim.y;
-  int32_t acc = 0;
-#pragma unroll 8
-  for (uint32_t c = c0; c < c1; ++c) acc += __ldg(diff_part + static_cast<size_t>(c) * E + e);
-  if (acc) atomicAdd(diff + e, acc);
-}
-
-// Tile ranges from the summed difference grid: 2D prefix sum (per-tile pair
-// counts), then an exclusive scan of the counts in tile order.  One block;
-// the grid lives in shared memory (E <= kMaxDiffCells).
-__global__ void __launch_bounds__(1024)
-    k_ranges_from_diff(const int32_t* __restrict__ diff, FrameGeom fg, uint2* __restrict__ ranges,
-                       uint32_t* err) {
-  extern __shared__ int32_t cell[];
-  __shared__ uint32_t s_warp[32];
-  const uint32_t gx = fg.gx, gy = fg.gy, gw = gx + 1;
-  const uint32_t E = gw * (gy + 1);
-  for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) cell[e] = __ldg(diff + e);
-  __syncthreads();
-  for (uint32_t y = threadIdx.x; y <= gy; y += blockDim.x) {  // prefix along rows
-    int32_t run = 0;
-    for (uint32_t x = 0; x <= gx; ++x) {
-      run += cell[y * gw + x];
-      cell[y * gw + x] = run;
-    }
-  }
-  __syncthreads();
-  for (uint32_t x = threadIdx.x; x <= gx; x += blockDim.x) {  // then along columns
-    int32_t run = 0;
-    for (uint32_t y = 0; y <= gy; ++y) {
-      run += cell[y * gw + x];
-      cell[y * gw + x] = run;
-    }
-  }
-  __syncthreads();
-  // cell[ty*gw + tx] is now the pair count of tile (ty, tx); scan in tile order.
-  const uint32_t T = gx * gy;
-  const uint32_t per = (T + blockDim.x - 1) / blockDim.x;
-  const uint32_t t0 = threadIdx.x * per;
-  uint32_t sum = 0;
-  bool bad = false;
-  for (uint32_t k = 0; k < per; ++k) {
-    const uint32_t t = t0 + k;
-    if (t < T) {
-      const int32_t v = cell[(t / gx) * gw + (t % gx)];
-      bad |= v < 0;
-      sum += static_cast<uint32_t>(v);
-    }
-  }
-  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  uint32_t x = sum;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t o = __shfl_up_sync(0xffffffffu, x, d);
-    if (lane >= static_cast<uint32_t>(d)) x += o;
-  }
-  if (lane == 31) s_warp[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t w = lane < (blockDim.x >> 5) ? s_warp[lane] : 0;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t o = __shfl_up_sync(0xffffffffu, w, d);
-      if (lane >= static_cast<uint32_t>(d)) w += o;
-    }
-    s_warp[lane] = w;
-  }
-  __syncthreads();
-  uint32_t run = x - sum + (warp ? s_warp[warp - 1] : 0);
-  for (uint32_t k = 0; k < per; ++k) {
-    const uint32_t t = t0 + k;
-    if (t < T) {
-      const uint32_t v = static_cast<uint32_t>(cell[(t / gx) * gw + (t % gx)]);
-      ranges[t] = v ? make_uint2(run, run + v) : make_uint2(0u, 0u);
-      run += v;
-    }
-  }
-  if (bad && lane == 0) latch_error(err, TDGS_ERR_INVALID_ARGUMENT);
-}
-
-cudaError_t launch_ranges_from_diff(const int32_t* diff_part, uint32_t parts, FrameGeom fg,
-                                    int32_t* diff, uint2* ranges, uint32_t* err, cudaStream_t s) {
-  const size_t E = static_cast<size_t>(fg.gx + 1) * (fg.gy + 1);
-  cudaError_t ce = cudaMemsetAsync(diff, 0, E * 4, s);
-  if (ce != cudaSuccess) return ce;
-  const uint32_t ry = parts < 32 ? parts : 32;
-  k_diff_reduce<<<dim3(static_cast<uint32_t>((E + 255) / 256), ry), 256, 0, s>>>(
-      diff_part, parts, static_cast<uint32_t>(E), diff);
-  const size_t smem = E * 4;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_ranges_from_diff,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-  }
-  k_ranges_from_diff<<<1, 1024, smem, s>>>(diff, fg, ranges, err);
   return cudaGetLastError();
 }
 

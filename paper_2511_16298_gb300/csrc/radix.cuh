@@ -79,7 +79,7 @@ __device__ __forceinline__ void grid_barrier(uint32_t* bar, uint32_t* err) {
       uint32_t spins = 0;
       while (ld_acquire32(bar + 1) == gen) {
         if (++spins > kSpinLimit) {
-          latch_error(err, TDGS_ERR_TIMEOUT);
+          latch_error(err, TDGS_ERR_TIMEOUT, kSiteBarrier);
           break;
         }
         __nanosleep(64);
@@ -138,10 +138,16 @@ struct PassArgs {
   uint32_t* tot;         // [bins] digit totals
   uint32_t* bar;         // grid barrier words
   uint32_t* err;
-  // expansion (frame path, last pass): element = (tile << rbits) | rank
+  // expansion (frame path, last pass): element = (global tile << rbits) | rank
   uint32_t rbits;
-  const uint32_t* sdepth;  // depth bits by rank
-  const uint32_t* sorder;  // Gaussian index by rank
+  const uint32_t* sdepth;      // depth bits by rank
+  const uint32_t* sorder;      // global record index by rank
+  const uint32_t* vrec_begin;  // [nv+1] first record of each view
+  const uint32_t* vtile_begin; // [nv+1] first global tile of each view
+  uint32_t nv;
+  uint32_t* rmin;              // per global tile: first sorted position (atomicMin)
+  uint32_t* rmax;              // per global tile: one past the last (atomicMax)
+  const uint64_t* m_dev;       // optional device element count, capped at m
 };
 
 template <typename K, bool kVals, bool kExpand, int kBits, int kThreads, int kItems>
@@ -173,12 +179,19 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
   uint32_t* base = reinterpret_cast<uint32_t*>(smem + S::kUBytes);  // running output base
   uint32_t* lstart = base + kBins;                                   // tile-local digit start
   __shared__ uint32_t s_warp[kWarps];
+  __shared__ uint32_t s_vrec[kExpand ? kMaxViews + 1 : 1];
+  __shared__ uint32_t s_vtile[kExpand ? kMaxViews + 1 : 1];
 
   const uint32_t t = threadIdx.x;
   const uint32_t lane = lane_id();
   const uint32_t warp = t >> 5;
   const bool d31 = a.drop31 != 0;
-  const uint32_t m = a.m;
+  uint32_t m = a.m;
+  if (a.m_dev) {
+    const uint64_t md = *a.m_dev;
+    if (md > a.m && t == 0 && blockIdx.x == 0) latch_error(a.err, TDGS_ERR_CAPACITY, kSiteRadixCapacity);
+    m = md < a.m ? static_cast<uint32_t>(md) : a.m;
+  }
   const uint32_t G = gridDim.x;
   const uint32_t c = blockIdx.x;
   // chunks are multiples of 4 keys so that every chunk starts 16-byte aligned
@@ -187,6 +200,12 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
   const uint32_t beg = static_cast<uint32_t>(b64 < m ? b64 : m);
   const uint32_t end = static_cast<uint32_t>(e64 < m ? e64 : m);
 
+  if constexpr (kExpand) {
+    for (uint32_t v = t; v <= a.nv; v += kThreads) {
+      s_vrec[v] = a.vrec_begin[v];
+      s_vtile[v] = a.vtile_begin[v];
+    }
+  }
   // ---- phase 1: chunk histogram (lstart doubles as the counter array)
   for (uint32_t b = t; b < kBins; b += kThreads) lstart[b] = 0;
   __syncthreads();
@@ -210,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
         }
       }
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) latch_error(a.err, TDGS_ERR_INVALID_ARGUMENT);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) latch_error(a.err, TDGS_ERR_INVALID_ARGUMENT, kSiteRadixKeys);
   }
   __syncthreads();
   for (uint32_t b = t; b < kBins; b += kThreads) a.H[static_cast<size_t>(c) * kBins + b] = lstart[b];
@@ -382,9 +401,17 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
         if (dst[i] < m) {
           if constexpr (kExpand) {
             const uint32_t rk = static_cast<uint32_t>(key & ((static_cast<K>(1) << a.rbits) - 1));
-            const uint64_t tile = static_cast<uint64_t>(key >> a.rbits);
-            static_cast<uint64_t*>(kout_raw)[dst[i]] = (tile << 32) | __ldg(a.sdepth + rk);
-            vout[dst[i]] = __ldg(a.sorder + rk);
+            const uint64_t gt = static_cast<uint64_t>(key >> a.rbits);
+            const uint32_t gi = __ldg(a.sorder + rk);
+            const uint32_t v = a.nv == 1 ? 0u : find_view(s_vrec, a.nv, gi);
+            static_cast<uint64_t*>(kout_raw)[dst[i]] = ((gt - s_vtile[v]) << 32) | __ldg(a.sdepth + rk);
+            vout[dst[i]] = gi - s_vrec[v];
+            if (a.rmin) {  // first / last element of a tile run in this tile's exchange
+              if (p == 0 || static_cast<uint64_t>(xk[p - 1] >> a.rbits) != gt)
+                atomicMin(a.rmin + gt, dst[i]);
+              if (p + 1 == valid || static_cast<uint64_t>(xk[p + 1] >> a.rbits) != gt)
+                atomicMax(a.rmax + gt, dst[i] + 1);
+            }
           } else {
             static_cast<K*>(kout_raw)[dst[i]] = key;
           }
@@ -413,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
     }
     __syncthreads();
   }
-  if (out_of_range) latch_error(a.err, TDGS_ERR_CAPACITY);
+  if (out_of_range) latch_error(a.err, TDGS_ERR_CAPACITY, kSiteRadixRange);
 }
 
 // --------------------------------------------------------------- host side

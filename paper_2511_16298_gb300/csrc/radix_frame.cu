@@ -44,20 +44,27 @@ size_t stream_scratch_words(bool wide, bool expand, uint32_t grid) {
   return radix::scratch_words(stream_kernel(wide, expand), grid);
 }
 
-cudaError_t launch_stream_pass(bool wide, bool expand, uint32_t grid, const void* kin, void* kout,
-                               uint32_t* vout, uint32_t m, uint32_t shift, uint32_t width,
-                               uint32_t rbits, const uint32_t* sdepth, const uint32_t* sorder,
-                               uint32_t* scratch, uint32_t* bar, uint32_t* err, cudaStream_t s) {
+cudaError_t launch_stream_pass(const StreamPass& sp, uint32_t* scratch, uint32_t* bar,
+                               uint32_t* err, cudaStream_t s) {
   radix::PassArgs a{};
-  a.m = m;
-  a.shift = shift;
-  a.mask = width >= 32 ? 0xffffffffu : (1u << width) - 1;
-  a.rbits = rbits;
-  a.sdepth = sdepth;
-  a.sorder = sorder;
+  a.m = sp.m;
+  a.m_dev = sp.m_dev;
+  a.shift = sp.shift;
+  a.mask = sp.width >= 32 ? 0xffffffffu : (1u << sp.width) - 1;
+  a.rbits = sp.rbits;
+  a.sdepth = sp.sdepth;
+  a.sorder = sp.sorder;
+  if (sp.expand && sp.views) {
+    a.vrec_begin = sp.views->rec_begin;
+    a.vtile_begin = sp.views->tile_begin;
+    a.nv = sp.views->nv;
+  }
+  a.rmin = sp.rmin;
+  a.rmax = sp.rmax;
   a.bar = bar;
   a.err = err;
-  return radix::launch(stream_kernel(wide, expand), grid, kin, nullptr, kout, vout, a, scratch, s);
+  return radix::launch(stream_kernel(sp.wide, sp.expand), sp.grid, sp.kin, nullptr, sp.kout, sp.vout,
+                       a, scratch, s);
 }
 
 }  // namespace tdgs

@@ -83,9 +83,14 @@ __device__ __forceinline__ TileRect tile_rect(const float4 rec, const FrameGeom&
 }
 
 // ------------------------------------------------------------ device sync
-// The first non-zero code wins; later errors are dropped.
-__device__ __forceinline__ void latch_error(uint32_t* err, uint32_t code) {
-  atomicCAS(err, 0u, code);
+// The first non-zero code wins; later errors are dropped.  err[1] records
+// which site latched it (kSite* below), for the host's error message.
+enum ErrorSite : uint32_t {
+  kSiteNone = 0, kSiteCount, kSiteScan, kSiteScanTimeout, kSiteDuplicate, kSiteRanges,
+  kSiteRadixKeys, kSiteRadixRange, kSiteRadixCapacity, kSiteBarrier, kSiteViewsCount, kSiteViewsDup
+};
+__device__ __forceinline__ void latch_error(uint32_t* err, uint32_t code, uint32_t site = kSiteNone) {
+  if (atomicCAS(err, 0u, code) == 0u) err[1] = site;
 }
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
@@ -139,25 +144,40 @@ cudaError_t launch_duplicate(const float4* g, const uint32_t* offsets, uint32_t 
 cudaError_t launch_tile_ranges(const uint64_t* keys, uint32_t m, uint32_t num_tiles,
                                uint2* ranges, uint32_t* err, cudaStream_t s);
 
-// ---- depth-first frame path
-// Largest difference grid (gx+1)*(gy+1) handled in shared memory; larger
-// images take the tile ranges from the sorted keys instead.
-constexpr uint32_t kMaxDiffCells = 48 * 1024;
-cudaError_t launch_frame_count(const float4* g, uint32_t n, FrameGeom fg, uint32_t* counts,
-                               uint32_t* dkey, uint32_t* dval, int32_t* diff_part,
-                               uint32_t grid, uint32_t* err, cudaStream_t s);
-cudaError_t launch_dup_depth(const float4* g, const uint32_t* sorder, const uint32_t* soff,
-                             uint32_t n, FrameGeom fg, uint32_t rbits, void* out, bool wide,
-                             uint32_t cap, uint32_t* err, cudaStream_t s);
-// diff: (gx+1)*(gy+1) words of scratch for the summed grid.
-cudaError_t launch_ranges_from_diff(const int32_t* diff_part, uint32_t parts, FrameGeom fg,
-                                    int32_t* diff, uint2* ranges, uint32_t* err, cudaStream_t s);
+// ---- depth-first frame path over a table of views (one view = one frame)
+constexpr uint32_t kMaxViews = 256;
+struct ViewTable {             // device arrays
+  const float4* const* g;      // [nv] records of each view
+  const uint32_t* rec_begin;   // [nv+1] global index of each view's first record
+  const uint32_t* tile_begin;  // [nv+1] global id of each view's first tile
+  const FrameGeom* geom;       // [nv]
+  uint64_t* vtot;              // [nv] pair count per view (accumulated, zeroed beforehand)
+  uint32_t* pbeg;              // [nv+1] first pair of each view in the sorted list
+  uint32_t nv;
+};
+
+// Largest v with begin[v] <= i (begin ascending, begin[0] = 0).
+__device__ __forceinline__ uint32_t find_view(const uint32_t* begin, uint32_t nv, uint32_t i) {
+  uint32_t lo = 0, hi = nv;  // answer in [lo, hi)
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (begin[mid] <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+cudaError_t launch_views_count(const ViewTable& vt, uint32_t n_all, uint32_t* counts,
+                               uint32_t* dkey, uint32_t* dval, uint32_t* err, cudaStream_t s);
+cudaError_t launch_views_pair_begin(const ViewTable& vt, cudaStream_t s);
+cudaError_t launch_views_dup(const ViewTable& vt, const uint32_t* sorder, const uint32_t* soff,
+                             uint32_t n_all, uint32_t rbits, void* out, bool wide, uint32_t cap,
+                             uint32_t* err, cudaStream_t s);
+// rmin/rmax: per global tile, first and one-past-last sorted position
+// (0xffffffff / 0 for an empty tile); writes local ranges per view.
+cudaError_t launch_views_ranges(const ViewTable& vt, const uint32_t* rmin, const uint32_t* rmax,
+                                uint32_t t_all, uint2* ranges, cudaStream_t s);
 
 // Radix passes of the frame path (radix_frame.cu).
-struct FramePassPlan {
-  uint32_t grid;
-  uint32_t bits;   // digit bits of the kernel
-};
 // Depth sort of the N Gaussians: (uint32 depth key, uint32 index), 32 bits.
 uint32_t depth_sort_grid(uint32_t n);
 size_t depth_sort_scratch_words(uint32_t grid);
@@ -166,13 +186,28 @@ cudaError_t launch_depth_pass(uint32_t grid, uint32_t pass, const uint32_t* kin,
                               uint32_t* bar, uint32_t* err, cudaStream_t s);
 constexpr uint32_t kDepthPasses = 3;  // 11 + 11 + 10 bits
 // Stable pass over the packed stream on tile bits [shift, shift + width).
-// expand: write the final (tile << 32 | depth bits) keys and indices.
+// expand: write the final (local tile << 32 | depth bits) keys and local
+// indices, and record each global tile's first/last sorted position.
+// m_dev (optional): device copy of the element count, capped at m.
+struct StreamPass {
+  bool wide, expand;
+  uint32_t grid;
+  const void* kin;
+  void* kout;
+  uint32_t* vout;
+  uint32_t m;
+  const uint64_t* m_dev;
+  uint32_t shift, width, rbits;
+  const uint32_t* sdepth;
+  const uint32_t* sorder;
+  const ViewTable* views;  // expand only
+  uint32_t* rmin;
+  uint32_t* rmax;
+};
 uint32_t stream_grid(bool wide, bool expand, uint32_t m);
 size_t stream_scratch_words(bool wide, bool expand, uint32_t grid);
-cudaError_t launch_stream_pass(bool wide, bool expand, uint32_t grid, const void* kin, void* kout,
-                               uint32_t* vout, uint32_t m, uint32_t shift, uint32_t width,
-                               uint32_t rbits, const uint32_t* sdepth, const uint32_t* sorder,
-                               uint32_t* scratch, uint32_t* bar, uint32_t* err, cudaStream_t s);
+cudaError_t launch_stream_pass(const StreamPass& sp, uint32_t* scratch, uint32_t* bar,
+                               uint32_t* err, cudaStream_t s);
 
 // ----------------------------------------------------------- radix sort
 constexpr int kMaxPasses = 8;

@@ -45,6 +45,15 @@ class _Frame(ctypes.Structure):
     _fields_ = [("width", ctypes.c_uint32), ("height", ctypes.c_uint32)]
 
 
+class _View(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_void_p), ("n", ctypes.c_uint32), ("f", _Frame)]
+
+
+class _ViewResult(ctypes.Structure):
+    _fields_ = [("keys", ctypes.c_void_p), ("values", ctypes.c_void_p), ("ranges", ctypes.c_void_p),
+                ("m", ctypes.c_uint32), ("num_tiles", ctypes.c_uint32)]
+
+
 class _KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_uint64),
                 ("items", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
@@ -89,6 +98,10 @@ def lib():
                 "tdgs_tile_ranges": ([P, P, u32, u32, P, P], st),
                 "tdgs_sort_frame": ([P, P, u32, F, ctypes.POINTER(P), ctypes.POINTER(P),
                                      ctypes.POINTER(P), ctypes.POINTER(u32), P], st),
+                "tdgs_sort_views": ([P, ctypes.POINTER(_View), u32, ctypes.POINTER(_ViewResult), P], st),
+                "tdgs_reserve_views": ([P, ctypes.POINTER(_View), u32, ctypes.c_uint64, P], st),
+                "tdgs_sort_views_async": ([P, ctypes.POINTER(_View), u32, P], st),
+                "tdgs_views_results": ([P, ctypes.POINTER(_ViewResult), u32, P], st),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -274,3 +287,52 @@ class Context:
         if copy:
             k, v, r = k.clone(), v.clone(), r.clone()
         return k, v, r, int(m.value)
+
+    # ------------------------------------------------------------ views
+    @staticmethod
+    def _views(views):
+        """views: list of (records tensor (n, 4), width, height)."""
+        arr = (_View * len(views))()
+        for i, (g, w, h) in enumerate(views):
+            arr[i].g = g.data_ptr() if g.numel() else None
+            arr[i].n = g.shape[0]
+            arr[i].f = _Frame(w, h)
+        return arr
+
+    def _results(self, res, n, copy):
+        out = []
+        for i in range(n):
+            r = res[i]
+            k = _view(r.keys or 0, r.m, torch.int64, self.device)
+            v = _view(r.values or 0, r.m, torch.int32, self.device)
+            rg = _view(r.ranges or 0, 2 * r.num_tiles, torch.int32, self.device).view(r.num_tiles, 2)
+            if copy:
+                k, v, rg = k.clone(), v.clone(), rg.clone()
+            out.append((k, v, rg, int(r.m)))
+        return out
+
+    def sort_views(self, views, copy: bool = False):
+        """All views in one batch; returns [(keys, values, ranges, m)] per
+        view (views of context buffers unless copy=True)."""
+        arr = self._views(views)
+        res = (_ViewResult * len(views))()
+        self._check(lib().tdgs_sort_views(self._h, arr, len(views), res, _stream(self.device)),
+                    "tdgs_sort_views")
+        return self._results(res, len(views), copy)
+
+    def reserve_views(self, views, pair_capacity: int):
+        arr = self._views(views)
+        self._check(lib().tdgs_reserve_views(self._h, arr, len(views), int(pair_capacity),
+                                             _stream(self.device)), "tdgs_reserve_views")
+
+    def sort_views_async(self, views):
+        """Graph-capturable batch (after reserve_views); read with views_results()."""
+        arr = self._views(views)
+        self._check(lib().tdgs_sort_views_async(self._h, arr, len(views), _stream(self.device)),
+                    "tdgs_sort_views_async")
+
+    def views_results(self, n: int, copy: bool = False):
+        res = (_ViewResult * n)()
+        self._check(lib().tdgs_views_results(self._h, res, n, _stream(self.device)), "tdgs_views_results")
+        return self._results(res, n, copy)
+
