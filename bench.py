@@ -325,6 +325,123 @@ def run_ours(args, rank, world, local_rank, dist):
     }
 
 
+# -------------------------------------------------------- batched views
+def run_batched(args, local_rank):
+    """64 cameras of one 500k-Gaussian scene: the plain per-view path (one
+    tdgs_sort_frame per view) against one multi-view batch, exact and
+    replayed from a captured CUDA graph."""
+    import torch
+
+    from paper_2511_16298_gb300 import synth, tdgs
+
+    dev = torch.device("cuda", local_rank)
+    mv = synth.multiview(seed=0)
+    gs = [tdgs.records_to_tensor(f.gaussians, dev) for f in mv.views]
+    views = [(g, f.width, f.height) for g, f in zip(gs, mv.views)]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ctx = tdgs.Context(local_rank)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        out = []
+        for i in range(reps + 2):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            if i >= 2:
+                out.append(a.elapsed_time(b))
+        return out
+
+    ms_view = []
+
+    def plain():
+        for g, f in zip(gs, mv.views):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.sort_frame(g, f.width, f.height)
+            b.record(stream)
+            ms_view.append((a, b))
+
+    reps = max(3, min(args.steps, 5))
+    t_plain = timed(plain, reps)
+    per_view = [a.elapsed_time(b) for a, b in ms_view[2 * len(gs):]]
+    res = ctx.sort_views(views)
+    m_total = sum(r[3] for r in res)
+    t_batch = timed(lambda: ctx.sort_views(views), reps)
+    ctx.reserve_views(views, int(m_total * 1.1) + 1024)
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            ctx.sort_views_async(views)
+    stream.wait_stream(side)
+    t_graph = timed(graph.replay, max(reps, args.steps))
+    res2 = ctx.views_results(len(views))
+    assert [r[3] for r in res2] == [r[3] for r in res]
+    ctx.close()
+
+    def summ(ts):
+        return {"pairs_per_s": m_total / (statistics.median(ts) * 1e-3), "p50_ms": round(statistics.median(ts), 4),
+                "p99_ms": round(float(np.percentile(ts, 99)), 4)}
+    ms = [r[3] for r in res]
+    return {"workload": "64 pinhole cameras (1280x720) of one 500,000-Gaussian scene, seed 0",
+            "views": len(gs), "pairs_total": m_total, "pairs_per_view_min": min(ms),
+            "pairs_per_view_max": max(ms), "plain_per_view_loop": summ(t_plain),
+            "plain_view_latency_ms": {"p50": round(statistics.median(per_view), 4),
+                                      "p99": round(float(np.percentile(per_view, 99)), 4)},
+            "batched": summ(t_batch), "batched_graph": summ(t_graph)}
+
+
+# ------------------------------------------------------- served requests
+def run_served(args, local_rank):
+    """Poisson request stream (200 req/s): frames of 100k-3M Gaussians at
+    640x360 / 1280x720 / 1920x1080, 40 GB HBM budget, replayed in wall
+    time, plain (one request per launch, one slot) against continuous
+    batching (two slots); then a closed-loop burst to saturate."""
+    import torch
+
+    from paper_2511_16298_gb300 import serve, synth
+
+    trace = synth.request_trace(seed=0, count=args.serve_requests)
+    frames = [r.frame() for r in trace]
+    host = [torch.from_numpy(np.ascontiguousarray(f.gaussians).view(np.int32).reshape(-1, 4)).pin_memory()
+            for f in frames]
+    out = {"workload": f"first {len(trace)} requests of a seed-0 Poisson trace at 200 req/s "
+                       "(N log-uniform in [1e5, 3e6]), 40 GB HBM budget"}
+    for name, batching, slots in (("plain", False, 1), ("batched", True, 2)):
+        for mode in ("trace", "burst"):
+            ex = serve.GpuExecutor(local_rank, slots=slots)
+            # warm the slots' buffers with the largest frame
+            big = int(np.argmax([f.n for f in frames]))
+            for sl in range(slots):
+                ex(sl, [serve.Request(-1, host[big], frames[big].n, frames[big].width,
+                                      frames[big].height, 0, time.perf_counter(), None)])
+            torch.cuda.synchronize()
+            with serve.Server(ex, slots=slots, hbm_budget=40 << 30, max_batch=16, batching=batching,
+                              policy=serve.narrow_batches if batching else None) as s:
+                t0 = time.perf_counter()
+                futs = []
+                for r, h, f in zip(trace, host, frames):
+                    if mode == "trace":
+                        dt = t0 + r.arrival_s - time.perf_counter()
+                        if dt > 0:
+                            time.sleep(dt)
+                    futs.append(s.submit(r.rid, h, f.n, f.width, f.height))
+                res = [fu.result(timeout=600) for fu in futs]
+                wall = time.perf_counter() - t0
+            ex.close()
+            lat = [r.latency_s * 1e3 for r in res]
+            pairs = sum(r.m for r in res)
+            out[f"{name}_{mode}"] = {"pairs_per_s": pairs / wall, "p50_ms": round(statistics.median(lat), 3),
+                                     "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                                     "mean_batch": round(statistics.mean(s.batches), 2), "wall_s": round(wall, 3)}
+    return out
+
+
 # ------------------------------------------------------------ CPU oracle
 def oracle_baseline(frame, reps: int):
     from oracle import oracle as O
@@ -349,6 +466,9 @@ def main():
     ap.add_argument("--no-sort-only", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-reps", type=int, default=5)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=48)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -388,6 +508,8 @@ def main():
         tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
         dist = tdist
     res = run_ours(args, rank, world, local_rank, dist)
+    batched = None if args.no_batched else run_batched(args, local_rank)
+    served = None if args.no_served else run_served(args, local_rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -413,7 +535,7 @@ def main():
             "latency_ms": res["latency_ms"],
             "roofline": res["roofline"], "kernels": res["kernels"], "sort_pairs": res["sort_pairs"],
             "cpu_baseline": cpu, "e2e": res["e2e"], "gpu_launches": res["gpu_launches"],
-            "clocks": res["clocks"],
+            "clocks": res["clocks"], "batched_views": batched, "served": served,
         }
         print(json.dumps(out))
     if dist:
