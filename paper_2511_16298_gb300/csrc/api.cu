@@ -37,6 +37,7 @@ const char* site_name(uint32_t site) {
     case kSiteBarrier: return "radix pass grid barrier wait";
     case kSiteViewsCount: return "frame count";
     case kSiteViewsDup: return "duplicate by depth";
+    case kSiteCopyWait: return "radix pass bulk-copy wait";
   }
   return "device";
 }

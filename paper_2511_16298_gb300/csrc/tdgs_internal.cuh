@@ -87,7 +87,8 @@ __device__ __forceinline__ TileRect tile_rect(const float4 rec, const FrameGeom&
 // which site latched it (kSite* below), for the host's error message.
 enum ErrorSite : uint32_t {
   kSiteNone = 0, kSiteCount, kSiteScan, kSiteScanTimeout, kSiteDuplicate, kSiteRanges,
-  kSiteRadixKeys, kSiteRadixRange, kSiteRadixCapacity, kSiteBarrier, kSiteViewsCount, kSiteViewsDup
+  kSiteRadixKeys, kSiteRadixRange, kSiteRadixCapacity, kSiteBarrier, kSiteViewsCount, kSiteViewsDup,
+  kSiteCopyWait
 };
 __device__ __forceinline__ void latch_error(uint32_t* err, uint32_t code, uint32_t site = kSiteNone) {
   if (atomicCAS(err, 0u, code) == 0u) err[1] = site;
