@@ -210,6 +210,32 @@ tdgs_status tdgs_sort_frame(tdgs_context* ctx, const tdgs_gaussian2d* g, uint32_
                             const uint32_t** sorted_values, const tdgs_range** ranges,
                             uint32_t* m_out, void* stream);
 
+/* ------------------------------------------------- scan without allocation */
+
+/* The exclusive scan of tdgs_scan (offsets, total, 64-bit overflow check)
+ * for callers that cannot allocate device memory: code running while a CUDA
+ * graph is captured, real-time loops that must never reach the device
+ * allocator, or plugins whose device memory belongs to a host application.
+ * The paper has no counterpart; it is a deployment convenience.
+ *
+ * It needs no context and allocates nothing (no cudaMalloc, cudaFree or
+ * allocating library call).  Its scratch -- look-back status words, the
+ * tile ticket and an error word -- is one fixed array of about 64 KB in
+ * the library's device memory, present on every GPU that loads the library
+ * until the process exits.  Limits and behaviour:
+ *   - n <= 16,777,216 counts; a larger n returns TDGS_ERR_INVALID_ARGUMENT.
+ *   - The first call on a device looks up the array's address on that
+ *     device (make that first call before any stream capture).
+ *   - Every call on a device shares the array: calls whose GPU work
+ *     overlaps (different streams, or threads without ordering) race and
+ *     give wrong results.  Order them on one stream.
+ *   - total_dev (may be NULL) receives the sum, 0xFFFFFFFF on overflow;
+ *     error_dev (may be NULL) receives 0 or the error the GPU detected
+ *     (TDGS_ERR_OVERFLOW, or TDGS_ERR_TIMEOUT from a bounded wait).
+ * counts, offsets, total_dev, error_dev: device pointers, 4-byte aligned. */
+tdgs_status tdgs_scan_noalloc(const uint32_t* counts, uint32_t n, uint32_t* offsets,
+                              uint32_t* total_dev, uint32_t* error_dev, void* stream);
+
 /* ------------------------------------------------------ several views --- */
 
 /* One view of a batch: its projected Gaussians (device, 16-byte aligned)

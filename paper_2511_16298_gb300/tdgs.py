@@ -98,6 +98,7 @@ def lib():
                 "tdgs_tile_ranges": ([P, P, u32, u32, P, P], st),
                 "tdgs_sort_frame": ([P, P, u32, F, ctypes.POINTER(P), ctypes.POINTER(P),
                                      ctypes.POINTER(P), ctypes.POINTER(u32), P], st),
+                "tdgs_scan_noalloc": ([P, u32, P, P, P, P], st),
                 "tdgs_sort_views": ([P, ctypes.POINTER(_View), u32, ctypes.POINTER(_ViewResult), P], st),
                 "tdgs_reserve_views": ([P, ctypes.POINTER(_View), u32, ctypes.c_uint64, P], st),
                 "tdgs_sort_views_async": ([P, ctypes.POINTER(_View), u32, P], st),
@@ -133,6 +134,20 @@ def num_tiles(width: int, height: int) -> int:
 
 def tile_bits(width: int, height: int) -> int:
     return int(lib().tdgs_tile_bits(_Frame(width, height)))
+
+
+def scan_noalloc(counts: torch.Tensor, offsets=None, total=None, error=None):
+    """tdgs_scan_noalloc on the current stream (no context, no allocation
+    inside the library); returns (offsets, total, error) device tensors."""
+    n = counts.shape[0]
+    dev = counts.device
+    offsets = torch.empty(n, dtype=torch.int32, device=dev) if offsets is None else offsets
+    total = torch.zeros(1, dtype=torch.int32, device=dev) if total is None else total
+    error = torch.zeros(1, dtype=torch.int32, device=dev) if error is None else error
+    st = lib().tdgs_scan_noalloc(_ptr(counts), n, _ptr(offsets), _ptr(total), _ptr(error), _stream(dev))
+    if st != OK:
+        raise TdgsError(st, "tdgs_scan_noalloc")
+    return offsets, total, error
 
 
 def sort_variants() -> list[tuple[int, int, int]]:
