@@ -118,6 +118,25 @@ int tdgs_sort_variant_count(void);
 tdgs_status tdgs_sort_variant_info(int i, int* bits, int* threads, int* items);
 tdgs_status tdgs_context_set_sort_variant(tdgs_context* ctx, int variant);
 
+/* Further tuning knobs of a context (value 0, or -1 for the sort variant,
+ * restores the built-in choice); out-of-range keys or values return
+ * TDGS_ERR_INVALID_ARGUMENT.
+ *   TDGS_TUNE_SORT_VARIANT     pass kernel of tdgs_sort_pairs (as above)
+ *   TDGS_TUNE_TILE_DIGIT_BITS  digit width 4..8 of the frame's tile passes
+ *   TDGS_TUNE_TILE_KERNEL      0: warp-ballot ranking, 1: per-thread
+ *                              counter table with bulk-copy staging
+ *                              (digits of at most 6 bits)
+ *   TDGS_TUNE_CTAS_PER_SM      CTAs per SM of the persistent radix grids
+ *                              (capped by occupancy) */
+enum {
+  TDGS_TUNE_SORT_VARIANT = 0,
+  TDGS_TUNE_TILE_DIGIT_BITS = 1,
+  TDGS_TUNE_TILE_KERNEL = 2,
+  TDGS_TUNE_CTAS_PER_SM = 3
+};
+tdgs_status tdgs_context_set_tuning(tdgs_context* ctx, int key, int value);
+tdgs_status tdgs_context_get_tuning(const tdgs_context* ctx, int key, int* value);
+
 /* Tracing (the paper has no counterpart; its Table VI times each stage
  * separately, which this reproduces on the GPU).  Every kernel launch made
  * through a context increments a counter.  With timing enabled, the

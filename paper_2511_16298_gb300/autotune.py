@@ -1,0 +1,120 @@
+"""Autotuner for the radix passes.
+
+Times candidate settings of a context's tuning knobs on a representative
+workload with CUDA events and keeps the fastest:
+
+* tdgs_sort_pairs: the pass kernel variant (digit width 8/10/11, threads,
+  keys per thread) and CTAs per SM of the persistent grid;
+* the fused frame / multi-view batch: tile-pass ranking kernel (warp
+  ballots or per-thread counter table), tile digit width (4..8) and CTAs
+  per SM.
+
+Results are stored as JSON keyed by workload shape (pair-count bucket and
+key bits, or Gaussians/tiles buckets), so a server can apply the table
+entry that matches each request.  Every setting yields identical results;
+only speed differs.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import statistics
+from typing import Callable
+
+import torch
+
+from . import tdgs
+
+L2_FLUSH = 256 << 20
+
+
+def _bucket(x: int) -> int:
+    return 0 if x <= 1 else int(math.ceil(math.log2(x)))
+
+
+def _time(fn: Callable[[], None], reps: int, flush: torch.Tensor, setup=None) -> float:
+    stream = torch.cuda.current_stream()
+    ts = []
+    for i in range(reps + 1):
+        if setup:
+            setup()
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i:
+            ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def tune_sort_pairs(ctx: tdgs.Context, keys: torch.Tensor, values: torch.Tensor, tile_bits: int,
+                    flags: int = tdgs.SORT_DEPTH_POSITIVE, reps: int = 3) -> dict:
+    """Best (sort_variant, ctas_per_sm) for sorting these pairs."""
+    kw, vw = torch.empty_like(keys), torch.empty_like(values)
+    ka, va = torch.empty_like(keys), torch.empty_like(values)
+    flush = torch.empty(L2_FLUSH, dtype=torch.uint8, device=keys.device)
+
+    def setup():
+        kw.copy_(keys)
+        vw.copy_(values)
+
+    trials = []
+    for v in range(len(tdgs.sort_variants())):
+        for cps in (0, 1, 2):
+            ctx.apply_tuning({"sort_variant": v, "ctas_per_sm": cps})
+            ms = _time(lambda: ctx.sort_pairs(kw, vw, tile_bits, flags, ka, va), reps, flush, setup)
+            trials.append(({"sort_variant": v, "ctas_per_sm": cps}, ms))
+    ctx.apply_tuning({"sort_variant": -1, "ctas_per_sm": 0})
+    ctx.sync()
+    best, ms = min(trials, key=lambda x: x[1])
+    return {"best": best, "ms": ms, "trials": [(t, round(m, 4)) for t, m in trials],
+            "key": f"pairs:m{_bucket(keys.shape[0])}:tb{tile_bits}:f{flags}"}
+
+
+def tune_views(ctx: tdgs.Context, views: list, reps: int = 3) -> dict:
+    """Best (tile_kernel, tile_digit_bits, ctas_per_sm) for a batch of
+    views [(records, width, height)] (one view = one frame)."""
+    flush = torch.empty(L2_FLUSH, dtype=torch.uint8, device=views[0][0].device)
+    trials = []
+    for kern, bits_list in ((0, (8, 6)), (1, (6, 5))):
+        for bits in bits_list:
+            for cps in (0, 2, 3):
+                knobs = {"tile_kernel": kern, "tile_digit_bits": bits, "ctas_per_sm": cps}
+                ctx.apply_tuning(knobs)
+                ms = _time(lambda: ctx.sort_views(views), reps, flush)
+                trials.append((knobs, ms))
+    ctx.apply_tuning({"tile_kernel": 0, "tile_digit_bits": 0, "ctas_per_sm": 0})
+    ctx.sync()
+    best, ms = min(trials, key=lambda x: x[1])
+    n = sum(int(v[0].shape[0]) for v in views)
+    t = sum(tdgs.num_tiles(v[1], v[2]) for v in views)
+    return {"best": best, "ms": ms, "trials": [(tt, round(m, 4)) for tt, m in trials],
+            "key": f"views:n{_bucket(n)}:t{_bucket(t)}:v{len(views)}"}
+
+
+class Table:
+    """JSON table of tuned knobs, keyed by workload shape."""
+
+    def __init__(self, path: str):
+        self.path = path
+        self.entries = json.load(open(path)) if os.path.exists(path) else {}
+
+    def record(self, result: dict):
+        self.entries[result["key"]] = {"knobs": result["best"], "ms": result["ms"]}
+
+    def save(self):
+        os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
+        json.dump(self.entries, open(self.path, "w"), indent=1, sort_keys=True)
+
+    def knobs_for_views(self, views) -> dict | None:
+        n = sum(int(v[0].shape[0]) for v in views)
+        t = sum(tdgs.num_tiles(v[1], v[2]) for v in views)
+        e = self.entries.get(f"views:n{_bucket(n)}:t{_bucket(t)}:v{len(views)}")
+        return e["knobs"] if e else None
+
+    def knobs_for_pairs(self, m: int, tile_bits: int, flags: int) -> dict | None:
+        e = self.entries.get(f"pairs:m{_bucket(m)}:tb{tile_bits}:f{flags}")
+        return e["knobs"] if e else None

@@ -89,7 +89,7 @@ struct tdgs_context {
   uint32_t nv = 0, n_all = 0, t_all = 0;
   uint64_t capacity = 0;        // pair capacity reserved for the asynchronous path
   bool reserved = false;
-  int variant_override = -1;
+  Tuning tuning;
   std::string last_error;
   // tracing
   uint64_t launches = 0;
@@ -249,7 +249,7 @@ tdgs_status do_sort(tdgs_context* ctx, uint64_t* keys, uint32_t* values, uint64_
                     int* result_in_alt, cudaStream_t s) {
   *result_in_alt = 0;
   if (m == 0) return TDGS_OK;
-  const SortPlan plan = make_sort_plan(m, tile_bits, flags, ctx->variant_override);
+  const SortPlan plan = make_sort_plan(m, tile_bits, flags, ctx->tuning);
   if (plan.grid == 0) return fail(ctx, TDGS_ERR_CUDA, "device query for the sort plan failed");
   tdgs_status st = ensure(ctx, ctx->sort_scratch, radix_scratch_words(plan) * 4, s);
   if (st != TDGS_OK) return st;
@@ -327,9 +327,43 @@ tdgs_status tdgs_sort_variant_info(int i, int* bits, int* threads, int* items) {
   return TDGS_OK;
 }
 
+tdgs_status tdgs_context_set_tuning(tdgs_context* ctx, int key, int value) {
+  if (!ctx) return TDGS_ERR_INVALID_ARGUMENT;
+  switch (key) {
+    case TDGS_TUNE_SORT_VARIANT:
+      if (value < -1 || value >= num_pass_variants()) return TDGS_ERR_INVALID_ARGUMENT;
+      ctx->tuning.sort_variant = value;
+      return TDGS_OK;
+    case TDGS_TUNE_TILE_DIGIT_BITS:
+      if (value != 0 && (value < 4 || value > 8)) return TDGS_ERR_INVALID_ARGUMENT;
+      ctx->tuning.tile_digit_bits = value;
+      return TDGS_OK;
+    case TDGS_TUNE_TILE_KERNEL:
+      if (value < 0 || value > 1) return TDGS_ERR_INVALID_ARGUMENT;
+      ctx->tuning.tile_kernel = value;
+      return TDGS_OK;
+    case TDGS_TUNE_CTAS_PER_SM:
+      if (value < 0 || value > 8) return TDGS_ERR_INVALID_ARGUMENT;
+      ctx->tuning.ctas_per_sm = value;
+      return TDGS_OK;
+  }
+  return TDGS_ERR_INVALID_ARGUMENT;
+}
+
+tdgs_status tdgs_context_get_tuning(const tdgs_context* ctx, int key, int* value) {
+  if (!ctx || !value) return TDGS_ERR_INVALID_ARGUMENT;
+  switch (key) {
+    case TDGS_TUNE_SORT_VARIANT: *value = ctx->tuning.sort_variant; return TDGS_OK;
+    case TDGS_TUNE_TILE_DIGIT_BITS: *value = ctx->tuning.tile_digit_bits; return TDGS_OK;
+    case TDGS_TUNE_TILE_KERNEL: *value = ctx->tuning.tile_kernel; return TDGS_OK;
+    case TDGS_TUNE_CTAS_PER_SM: *value = ctx->tuning.ctas_per_sm; return TDGS_OK;
+  }
+  return TDGS_ERR_INVALID_ARGUMENT;
+}
+
 tdgs_status tdgs_context_set_sort_variant(tdgs_context* ctx, int variant) {
   if (!ctx || variant < -1 || variant >= num_pass_variants()) return TDGS_ERR_INVALID_ARGUMENT;
-  ctx->variant_override = variant;
+  ctx->tuning.sort_variant = variant;
   return TDGS_OK;
 }
 
@@ -569,7 +603,11 @@ Shape shape_of(const tdgs_context* ctx) {
   sh.rbits = bits_for(ctx->n_all);
   sh.tbits = bits_for(ctx->t_all);
   sh.wide = sh.tbits + sh.rbits > 32 || sh.rbits >= 32;
-  sh.npass = sh.tbits <= 8 ? 1u : (sh.tbits + 7) / 8;   // digits of at most 8 bits
+  // digit width of the tile passes: at most 8 bits (ballot ranking) or 6
+  // (counter table), lower if tuned
+  uint32_t dmax = ctx->tuning.tile_digit_bits > 0 ? static_cast<uint32_t>(ctx->tuning.tile_digit_bits) : 8u;
+  if (ctx->tuning.tile_kernel == 1 && dmax > 6) dmax = 6;
+  sh.npass = sh.tbits <= dmax ? 1u : (sh.tbits + dmax - 1) / dmax;
   sh.w0 = (sh.tbits + sh.npass - 1) / std::max(1u, sh.npass);
   return sh;
 }
@@ -586,7 +624,7 @@ tdgs_status ensure_record_buffers(tdgs_context* ctx, cudaStream_t s) {
   const uint32_t n_all = ctx->n_all;
   const uint32_t tiles = (n_all + kScanTileItems - 1) / kScanTileItems;
   if (st == TDGS_OK) st = ensure(ctx, ctx->scan_status, static_cast<size_t>(tiles) * 8 + 8, s);
-  const uint32_t dgrid = depth_sort_grid(n_all ? n_all : 1);
+  const uint32_t dgrid = depth_sort_grid(n_all ? n_all : 1, ctx->tuning.ctas_per_sm);
   if (dgrid == 0) return fail(ctx, TDGS_ERR_CUDA, "device query for the depth sort failed");
   if (st == TDGS_OK) st = ensure(ctx, ctx->sort_scratch, depth_sort_scratch_words(dgrid) * 4, s);
   return st;
@@ -601,11 +639,13 @@ tdgs_status ensure_pair_buffers(tdgs_context* ctx, uint64_t m, cudaStream_t s) {
   if (st == TDGS_OK) st = ensure(ctx, ctx->f_keys, m * 8 + 16, s);
   if (st == TDGS_OK) st = ensure(ctx, ctx->f_values, m * 4 + 16, s);
   const uint32_t mm = static_cast<uint32_t>(m ? m : 1);
-  const uint32_t g0 = stream_grid(sh.wide, false, mm), g1 = stream_grid(sh.wide, true, mm);
+  const int kern = ctx->tuning.tile_kernel, cps = ctx->tuning.ctas_per_sm;
+  const uint32_t g0 = stream_grid(sh.wide, false, kern, mm, cps), g1 = stream_grid(sh.wide, true, kern, mm, cps);
   if (g0 == 0 || g1 == 0) return fail(ctx, TDGS_ERR_CUDA, "device query for the tile sort failed");
   if (st == TDGS_OK)
     st = ensure(ctx, ctx->sort_scratch,
-                std::max(stream_scratch_words(sh.wide, false, g0), stream_scratch_words(sh.wide, true, g1)) * 4,
+                std::max(stream_scratch_words(sh.wide, false, kern, g0),
+                         stream_scratch_words(sh.wide, true, kern, g1)) * 4,
                 s);
   return st;
 }
@@ -621,7 +661,7 @@ tdgs_status run_front(tdgs_context* ctx, cudaStream_t s) {
   uint32_t* dv[2] = {static_cast<uint32_t*>(ctx->f_dval[0].p), static_cast<uint32_t*>(ctx->f_dval[1].p)};
   TDGS_TRACED(ctx, kKFrameCount, n_all, s, launch_views_count(vt, n_all, counts, dk[0], dv[0], err_word(ctx), s));
   TDGS_TRACED(ctx, kKPairBegin, 1, s, launch_views_pair_begin(vt, s));
-  const uint32_t dgrid = depth_sort_grid(n_all ? n_all : 1);
+  const uint32_t dgrid = depth_sort_grid(n_all ? n_all : 1, ctx->tuning.ctas_per_sm);
   for (uint32_t p = 0; p < kDepthPasses; ++p) {
     TDGS_TRACED(ctx, kKDepthSort, n_all, s,
                 launch_depth_pass(dgrid, p, dk[p & 1], dv[p & 1], dk[(p + 1) & 1], dv[(p + 1) & 1],
@@ -664,7 +704,8 @@ tdgs_status run_back(tdgs_context* ctx, uint32_t m, const uint64_t* m_dev, cudaS
     StreamPass sp{};
     sp.wide = sh.wide;
     sp.expand = last;
-    sp.grid = stream_grid(sh.wide, last, mm);
+    sp.kernel = ctx->tuning.tile_kernel;
+    sp.grid = stream_grid(sh.wide, last, sp.kernel, mm, ctx->tuning.ctas_per_sm);
     sp.kin = st[p & 1];
     sp.kout = last ? ctx->f_keys.p : st[(p + 1) & 1];
     sp.vout = last ? static_cast<uint32_t*>(ctx->f_values.p) : nullptr;

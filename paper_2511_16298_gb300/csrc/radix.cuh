@@ -786,10 +786,10 @@ Kernel make_kernel() {
 
 // Resident CTAs of `k` on the current device (0 on failure); caches the
 // occupancy query per device and kernel.
-uint32_t resident_ctas(const Kernel& k);
+uint32_t resident_ctas(const Kernel& k, int ctas_per_sm = 0);
 
 // Grid for m keys: every CTA gets at least one tile, at most all resident.
-uint32_t grid_for(const Kernel& k, uint32_t m);
+uint32_t grid_for(const Kernel& k, uint32_t m, int ctas_per_sm = 0);
 
 // Scratch words a pass with this kernel and grid needs.
 inline size_t scratch_words(const Kernel& k, uint32_t grid) {

@@ -11,18 +11,22 @@ const radix::Kernel& depth_kernel() {
   static const radix::Kernel k = make_kernel<uint32_t, true, false, 11, 256, 16>();
   return k;
 }
-const radix::Kernel& stream_kernel(bool wide, bool expand) {
-  static const radix::Kernel k[4] = {
+const radix::Kernel& stream_kernel(bool wide, bool expand, int kernel) {
+  static const radix::Kernel k[8] = {
       make_kernel<uint32_t, false, false, 8, 256, 16>(),
       make_kernel<uint32_t, false, true, 8, 256, 16>(),
       make_kernel<uint64_t, false, false, 8, 256, 16>(),
       make_kernel<uint64_t, false, true, 8, 256, 16>(),
+      radix::make_ct_kernel<uint32_t, false>(),
+      radix::make_ct_kernel<uint32_t, true>(),
+      radix::make_ct_kernel<uint64_t, false>(),
+      radix::make_ct_kernel<uint64_t, true>(),
   };
-  return k[(wide ? 2 : 0) + (expand ? 1 : 0)];
+  return k[(kernel == 1 ? 4 : 0) + (wide ? 2 : 0) + (expand ? 1 : 0)];
 }
 }  // namespace
 
-uint32_t depth_sort_grid(uint32_t n) { return radix::grid_for(depth_kernel(), n); }
+uint32_t depth_sort_grid(uint32_t n, int ctas_per_sm) { return radix::grid_for(depth_kernel(), n, ctas_per_sm); }
 size_t depth_sort_scratch_words(uint32_t grid) { return radix::scratch_words(depth_kernel(), grid); }
 
 cudaError_t launch_depth_pass(uint32_t grid, uint32_t pass, const uint32_t* kin, const uint32_t* vin,
@@ -37,11 +41,11 @@ cudaError_t launch_depth_pass(uint32_t grid, uint32_t pass, const uint32_t* kin,
   return radix::launch(depth_kernel(), grid, kin, vin, kout, vout, a, scratch, s);
 }
 
-uint32_t stream_grid(bool wide, bool expand, uint32_t m) {
-  return radix::grid_for(stream_kernel(wide, expand), m);
+uint32_t stream_grid(bool wide, bool expand, int kernel, uint32_t m, int ctas_per_sm) {
+  return radix::grid_for(stream_kernel(wide, expand, kernel), m, ctas_per_sm);
 }
-size_t stream_scratch_words(bool wide, bool expand, uint32_t grid) {
-  return radix::scratch_words(stream_kernel(wide, expand), grid);
+size_t stream_scratch_words(bool wide, bool expand, int kernel, uint32_t grid) {
+  return radix::scratch_words(stream_kernel(wide, expand, kernel), grid);
 }
 
 cudaError_t launch_stream_pass(const StreamPass& sp, uint32_t* scratch, uint32_t* bar,
@@ -63,7 +67,7 @@ cudaError_t launch_stream_pass(const StreamPass& sp, uint32_t* scratch, uint32_t
   a.rmax = sp.rmax;
   a.bar = bar;
   a.err = err;
-  return radix::launch(stream_kernel(sp.wide, sp.expand), sp.grid, sp.kin, nullptr, sp.kout, sp.vout,
+  return radix::launch(stream_kernel(sp.wide, sp.expand, sp.kernel), sp.grid, sp.kin, nullptr, sp.kout, sp.vout,
                        a, scratch, s);
 }
 

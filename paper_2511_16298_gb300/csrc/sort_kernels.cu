@@ -35,7 +35,8 @@ int default_pass_variant(uint32_t digit_bits) {
   return 4;
 }
 
-SortPlan make_sort_plan(uint32_t m, uint32_t tile_bits, uint32_t flags, int variant_override) {
+SortPlan make_sort_plan(uint32_t m, uint32_t tile_bits, uint32_t flags, const Tuning& tu) {
+  const int variant_override = tu.sort_variant;
   SortPlan p{};
   p.drop31 = (flags & TDGS_SORT_DEPTH_POSITIVE) != 0;
   p.key_bits = 32 + tile_bits - (p.drop31 ? 1 : 0);
@@ -58,7 +59,7 @@ SortPlan make_sort_plan(uint32_t m, uint32_t tile_bits, uint32_t flags, int vari
   const radix::Kernel& k = variant_kernel(static_cast<int>(p.variant));
   p.tile_keys = static_cast<uint32_t>(k.threads * k.items);
   p.bins = 1u << k.bits;
-  p.grid = radix::grid_for(k, m);
+  p.grid = radix::grid_for(k, m, tu.ctas_per_sm);
   return p;
 }
 

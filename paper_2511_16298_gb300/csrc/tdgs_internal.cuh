@@ -180,7 +180,7 @@ cudaError_t launch_views_ranges(const ViewTable& vt, const uint32_t* rmin, const
 
 // Radix passes of the frame path (radix_frame.cu).
 // Depth sort of the N Gaussians: (uint32 depth key, uint32 index), 32 bits.
-uint32_t depth_sort_grid(uint32_t n);
+uint32_t depth_sort_grid(uint32_t n, int ctas_per_sm);
 size_t depth_sort_scratch_words(uint32_t grid);
 cudaError_t launch_depth_pass(uint32_t grid, uint32_t pass, const uint32_t* kin, const uint32_t* vin,
                               uint32_t* kout, uint32_t* vout, uint32_t n, uint32_t* scratch,
@@ -192,6 +192,7 @@ constexpr uint32_t kDepthPasses = 3;  // 11 + 11 + 10 bits
 // m_dev (optional): device copy of the element count, capped at m.
 struct StreamPass {
   bool wide, expand;
+  int kernel;              // Tuning::tile_kernel
   uint32_t grid;
   const void* kin;
   void* kout;
@@ -205,10 +206,19 @@ struct StreamPass {
   uint32_t* rmin;
   uint32_t* rmax;
 };
-uint32_t stream_grid(bool wide, bool expand, uint32_t m);
-size_t stream_scratch_words(bool wide, bool expand, uint32_t grid);
+uint32_t stream_grid(bool wide, bool expand, int kernel, uint32_t m, int ctas_per_sm);
+size_t stream_scratch_words(bool wide, bool expand, int kernel, uint32_t grid);
 cudaError_t launch_stream_pass(const StreamPass& sp, uint32_t* scratch, uint32_t* bar,
                                uint32_t* err, cudaStream_t s);
+
+// ---------------------------------------------------------------- tuning
+// Knobs picked by the autotuner (0 / -1 = built-in choice).
+struct Tuning {
+  int sort_variant = -1;     // tdgs_sort_pairs pass kernel
+  int tile_digit_bits = 0;   // frame tile passes: digit width 4..8 (0 = 8)
+  int tile_kernel = 0;       // frame tile passes: 0 ballot ranking, 1 counter table (<= 6-bit digits)
+  int ctas_per_sm = 0;       // persistent radix grids: CTAs per SM (0 = kernel default)
+};
 
 // ----------------------------------------------------------- radix sort
 constexpr int kMaxPasses = 8;
@@ -236,7 +246,7 @@ PassVariant pass_variant(int i);
 int default_pass_variant(uint32_t digit_bits);
 
 // Plans a sort of m keys on the current device.
-SortPlan make_sort_plan(uint32_t m, uint32_t tile_bits, uint32_t flags, int variant_override);
+SortPlan make_sort_plan(uint32_t m, uint32_t tile_bits, uint32_t flags, const Tuning& tu);
 // uint32 words of scratch one pass needs (chunk histograms, prefixes, totals).
 size_t radix_scratch_words(const SortPlan& plan);
 // One digit pass (cooperative launch).  bar: two zero-initialised words.

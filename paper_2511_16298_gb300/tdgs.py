@@ -25,6 +25,7 @@ CUDA_ERROR = 4
 TIMEOUT = 5
 CAPACITY = 6
 SORT_DEPTH_POSITIVE = 1
+TUNE_SORT_VARIANT, TUNE_TILE_DIGIT_BITS, TUNE_TILE_KERNEL, TUNE_CTAS_PER_SM = 0, 1, 2, 3
 
 _lock = threading.Lock()
 _lib = None
@@ -88,6 +89,8 @@ def lib():
                 "tdgs_sort_variant_info": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                             ctypes.POINTER(i32)], st),
                 "tdgs_context_set_sort_variant": ([P, i32], st),
+                "tdgs_context_set_tuning": ([P, i32, i32], st),
+                "tdgs_context_get_tuning": ([P, i32, ctypes.POINTER(i32)], st),
                 "tdgs_context_launch_count": ([P], ctypes.c_uint64),
                 "tdgs_context_enable_timing": ([P, i32], st),
                 "tdgs_context_kernel_times": ([P, ctypes.POINTER(_KernelTime), i32], i32),
@@ -220,6 +223,19 @@ class Context:
     def set_sort_variant(self, variant: int):
         self._check(lib().tdgs_context_set_sort_variant(self._h, int(variant)),
                     "tdgs_context_set_sort_variant")
+
+    def set_tuning(self, key: int, value: int):
+        self._check(lib().tdgs_context_set_tuning(self._h, int(key), int(value)), "tdgs_context_set_tuning")
+
+    def get_tuning(self, key: int) -> int:
+        v = ctypes.c_int(0)
+        self._check(lib().tdgs_context_get_tuning(self._h, int(key), ctypes.byref(v)), "tdgs_context_get_tuning")
+        return v.value
+
+    def apply_tuning(self, knobs: dict):
+        for k, v in knobs.items():
+            self.set_tuning({"sort_variant": TUNE_SORT_VARIANT, "tile_digit_bits": TUNE_TILE_DIGIT_BITS,
+                             "tile_kernel": TUNE_TILE_KERNEL, "ctas_per_sm": TUNE_CTAS_PER_SM}[k], v)
 
     @property
     def launches(self) -> int:
