@@ -104,46 +104,62 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def kernel_source_sha() -> str:
+    """Hash of the sources the radix passes are built from."""
+    h = hashlib.sha256()
+    for f in ("radix.cuh", "radix.cu", "radix_frame.cu", "sort_kernels.cu", "tdgs_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2511_16298_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def profiled_traffic(kernel: str):
     """Per-launch DRAM traffic of `kernel` from the committed ncu summary,
     if the kernel source is unchanged since the capture."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_scene_1m.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
     tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     items = re.search(r"items_per_launch:\s*([0-9]+)", text)
-    src = os.path.join(ROOT, "paper_2511_16298_gb300", "csrc", "sort_kernels.cu")
-    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    cur = kernel_source_sha()
     if not (sha and tr) or sha.group(1) != cur:
         return None
     return float(tr.group(1)), int(items.group(1)) if items else None
 
 
 def algorithmic_bytes(kernel: str, items: int, n: int, m: int, tiles: int) -> float:
-    """Minimum DRAM bytes of one launch (reads + writes), per kernel."""
-    if kernel == "scan":            # records in (16 B), offsets out (4 B)
+    """Minimum DRAM bytes of one launch (reads + writes), per kernel.
+    items = the units the launch processed (Gaussians, pairs or tiles, as
+    the library's tracer reports them); n, m, tiles = the frame's sizes.
+    The fused-frame figures assume the packed (tile, depth rank) element
+    fits 32 bits, which holds for every single-frame workload timed here."""
+    # the five separate steps
+    if kernel == "count_tiles":      # record in (16 B), count out (4 B)
         return 20.0 * items
-    if kernel == "count_tiles":
-        return 20.0 * items
-    if kernel == "duplicate_keys":  # records + offsets in, 12 B per pair out
+    if kernel == "scan":             # count in, offset out
+        return 8.0 * items
+    if kernel == "duplicate_keys":   # record + offset in per Gaussian, 12 B per pair out
         return 20.0 * items + 12.0 * m
-    if kernel == "radix_pass":  # 12 B read + 12 B written per pair
+    if kernel == "radix_pass":       # (u64 key, u32 value) in and out
         return 24.0 * items
-    if kernel == "tile_ranges":
+    if kernel == "tile_ranges":      # key in per pair, range out per tile
         return 8.0 * items + 8.0 * tiles
-    # fused frame (items: Gaussians, or pairs for the tile passes)
-    if kernel == "frame_count":      # records in; counts, depth key, index out
+    # fused frame
+    if kernel == "frame_count":      # record in; count, depth key, index out
         return 28.0 * items
     if kernel == "depth_sort":       # (u32 key, u32 index) in and out
         return 16.0 * items
-    if kernel == "duplicate_by_depth":  # order, offsets, records in; 4 B per pair out
+    if kernel == "scan_by_depth":    # index in, gathered count, offset out
+        return 12.0 * items
+    if kernel == "duplicate_by_depth":  # index, offset, record in; 4 B per pair out
         return 24.0 * items + 4.0 * m
-    if kernel == "tile_sort_pass":   # 4 B element in; 4 B out, or 12 B for the expanding pass
-        return 16.0 * items
-    if kernel == "ranges_from_diff":
+    if kernel == "tile_sort_pass":   # 4 B element in and out
         return 8.0 * items
+    if kernel == "tile_expand_pass":  # 4 B element in; u64 key + u32 value out; depth tables once
+        return 16.0 * items + 8.0 * n
+    if kernel == "ranges_final":     # run first/last in, range out, per tile
+        return 16.0 * items
     return 0.0
 
 

@@ -127,12 +127,16 @@ tdgs_status tdgs_context_set_sort_variant(tdgs_context* ctx, int variant);
  *                              counter table with bulk-copy staging
  *                              (digits of at most 6 bits)
  *   TDGS_TUNE_CTAS_PER_SM      CTAs per SM of the persistent radix grids
- *                              (capped by occupancy) */
+ *                              (capped by occupancy)
+ *   TDGS_TUNE_DEPTH_DIGIT_BITS digit width of the frame's depth sort: 8
+ *                              (4 passes, the built-in choice) or 11
+ *                              (3 passes) */
 enum {
   TDGS_TUNE_SORT_VARIANT = 0,
   TDGS_TUNE_TILE_DIGIT_BITS = 1,
   TDGS_TUNE_TILE_KERNEL = 2,
-  TDGS_TUNE_CTAS_PER_SM = 3
+  TDGS_TUNE_CTAS_PER_SM = 3,
+  TDGS_TUNE_DEPTH_DIGIT_BITS = 4
 };
 tdgs_status tdgs_context_set_tuning(tdgs_context* ctx, int key, int value);
 tdgs_status tdgs_context_get_tuning(const tdgs_context* ctx, int key, int* value);

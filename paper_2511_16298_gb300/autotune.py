@@ -82,11 +82,13 @@ def tune_views(ctx: tdgs.Context, views: list, reps: int = 3) -> dict:
     for kern, bits_list in ((0, (8, 6)), (1, (6, 5))):
         for bits in bits_list:
             for cps in (0, 2, 3):
-                knobs = {"tile_kernel": kern, "tile_digit_bits": bits, "ctas_per_sm": cps}
-                ctx.apply_tuning(knobs)
-                ms = _time(lambda: ctx.sort_views(views), reps, flush)
-                trials.append((knobs, ms))
-    ctx.apply_tuning({"tile_kernel": 0, "tile_digit_bits": 0, "ctas_per_sm": 0})
+                for dbits in (11, 8):
+                    knobs = {"tile_kernel": kern, "tile_digit_bits": bits, "ctas_per_sm": cps,
+                             "depth_digit_bits": dbits}
+                    ctx.apply_tuning(knobs)
+                    ms = _time(lambda: ctx.sort_views(views), reps, flush)
+                    trials.append((knobs, ms))
+    ctx.apply_tuning({"tile_kernel": 0, "tile_digit_bits": 0, "ctas_per_sm": 0, "depth_digit_bits": 0})
     ctx.sync()
     best, ms = min(trials, key=lambda x: x[1])
     n = sum(int(v[0].shape[0]) for v in views)

@@ -49,12 +49,13 @@ struct Buffer {
 
 enum KernelId {
   kKCount, kKScan, kKDuplicate, kKRanges, kKRadixPass,
-  kKFrameCount, kKDepthSort, kKDupDepth, kKTilePass, kKRangesFinal, kKPairBegin, kKNum
+  kKFrameCount, kKDepthSort, kKFrameScan, kKDupDepth, kKTilePass, kKTileExpand, kKRangesFinal,
+  kKPairBegin, kKNum
 };
 const char* const kKernelNames[kKNum] = {
     "count_tiles",  "scan",       "duplicate_keys",     "tile_ranges",    "radix_pass",
-    "frame_count",  "depth_sort", "duplicate_by_depth", "tile_sort_pass", "ranges_final",
-    "view_pair_begin"};
+    "frame_count",  "depth_sort", "scan_by_depth", "duplicate_by_depth", "tile_sort_pass",
+    "tile_expand_pass", "ranges_final", "view_pair_begin"};
 
 // View table as stored in device memory (SoA, fixed maximum size).
 struct ViewBlob {
@@ -229,7 +230,7 @@ tdgs_status traced(tdgs_context* ctx, KernelId id, uint64_t items, cudaStream_t 
     if (_st != TDGS_OK) return _st;                                              \
   } while (0)
 
-tdgs_status do_scan(tdgs_context* ctx, const uint32_t* counts, const float4* recs,
+tdgs_status do_scan(tdgs_context* ctx, KernelId id, const uint32_t* counts, const float4* recs,
                     const uint32_t* gather, FrameGeom fg, uint32_t n, uint32_t* offsets,
                     uint64_t* total64, uint32_t* total32, cudaStream_t s) {
   const uint32_t tiles = (n + kScanTileItems - 1) / kScanTileItems;
@@ -237,7 +238,7 @@ tdgs_status do_scan(tdgs_context* ctx, const uint32_t* counts, const float4* rec
   if (st != TDGS_OK) return st;
   TDGS_CUDA(ctx, cudaMemsetAsync(ctx->scan_status.p, 0, static_cast<size_t>(tiles) * 8, s));
   TDGS_CUDA(ctx, cudaMemsetAsync(ctx->d_tickets + 0, 0, 4, s));
-  TDGS_TRACED(ctx, kKScan, n, s,
+  TDGS_TRACED(ctx, id, n, s,
               launch_scan(counts, recs, gather, fg, n, offsets,
                           static_cast<uint64_t*>(ctx->scan_status.p), ctx->d_tickets + 0, 0u,
                           total64, total32, err_word(ctx), s));
@@ -346,6 +347,10 @@ tdgs_status tdgs_context_set_tuning(tdgs_context* ctx, int key, int value) {
       if (value < 0 || value > 8) return TDGS_ERR_INVALID_ARGUMENT;
       ctx->tuning.ctas_per_sm = value;
       return TDGS_OK;
+    case TDGS_TUNE_DEPTH_DIGIT_BITS:
+      if (value != 0 && value != 8 && value != 11) return TDGS_ERR_INVALID_ARGUMENT;
+      ctx->tuning.depth_digit_bits = value;
+      return TDGS_OK;
   }
   return TDGS_ERR_INVALID_ARGUMENT;
 }
@@ -357,6 +362,7 @@ tdgs_status tdgs_context_get_tuning(const tdgs_context* ctx, int key, int* value
     case TDGS_TUNE_TILE_DIGIT_BITS: *value = ctx->tuning.tile_digit_bits; return TDGS_OK;
     case TDGS_TUNE_TILE_KERNEL: *value = ctx->tuning.tile_kernel; return TDGS_OK;
     case TDGS_TUNE_CTAS_PER_SM: *value = ctx->tuning.ctas_per_sm; return TDGS_OK;
+    case TDGS_TUNE_DEPTH_DIGIT_BITS: *value = ctx->tuning.depth_digit_bits; return TDGS_OK;
   }
   return TDGS_ERR_INVALID_ARGUMENT;
 }
@@ -481,7 +487,7 @@ tdgs_status tdgs_scan(tdgs_context* ctx, const uint32_t* counts, uint32_t n, uin
   if (!counts || !offsets) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "null pointer");
   if (!aligned(counts, 4) || !aligned(offsets, 4) || (total_dev && !aligned(total_dev, 4)))
     return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "misaligned pointer");
-  return do_scan(ctx, counts, nullptr, nullptr, FrameGeom{}, n, offsets, nullptr, total_dev, s);
+  return do_scan(ctx, kKScan, counts, nullptr, nullptr, FrameGeom{}, n, offsets, nullptr, total_dev, s);
 }
 
 tdgs_status tdgs_duplicate_keys(tdgs_context* ctx, const tdgs_gaussian2d* g,
@@ -624,9 +630,10 @@ tdgs_status ensure_record_buffers(tdgs_context* ctx, cudaStream_t s) {
   const uint32_t n_all = ctx->n_all;
   const uint32_t tiles = (n_all + kScanTileItems - 1) / kScanTileItems;
   if (st == TDGS_OK) st = ensure(ctx, ctx->scan_status, static_cast<size_t>(tiles) * 8 + 8, s);
-  const uint32_t dgrid = depth_sort_grid(n_all ? n_all : 1, ctx->tuning.ctas_per_sm);
+  const int dbits = ctx->tuning.depth_digit_bits;
+  const uint32_t dgrid = depth_sort_grid(n_all ? n_all : 1, dbits, ctx->tuning.ctas_per_sm);
   if (dgrid == 0) return fail(ctx, TDGS_ERR_CUDA, "device query for the depth sort failed");
-  if (st == TDGS_OK) st = ensure(ctx, ctx->sort_scratch, depth_sort_scratch_words(dgrid) * 4, s);
+  if (st == TDGS_OK) st = ensure(ctx, ctx->sort_scratch, depth_sort_scratch_words(dbits, dgrid) * 4, s);
   return st;
 }
 
@@ -661,15 +668,17 @@ tdgs_status run_front(tdgs_context* ctx, cudaStream_t s) {
   uint32_t* dv[2] = {static_cast<uint32_t*>(ctx->f_dval[0].p), static_cast<uint32_t*>(ctx->f_dval[1].p)};
   TDGS_TRACED(ctx, kKFrameCount, n_all, s, launch_views_count(vt, n_all, counts, dk[0], dv[0], err_word(ctx), s));
   TDGS_TRACED(ctx, kKPairBegin, 1, s, launch_views_pair_begin(vt, s));
-  const uint32_t dgrid = depth_sort_grid(n_all ? n_all : 1, ctx->tuning.ctas_per_sm);
-  for (uint32_t p = 0; p < kDepthPasses; ++p) {
+  const int dbits = ctx->tuning.depth_digit_bits;
+  const uint32_t dpasses = depth_passes(dbits);
+  const uint32_t dgrid = depth_sort_grid(n_all ? n_all : 1, dbits, ctx->tuning.ctas_per_sm);
+  for (uint32_t p = 0; p < dpasses; ++p) {
     TDGS_TRACED(ctx, kKDepthSort, n_all, s,
-                launch_depth_pass(dgrid, p, dk[p & 1], dv[p & 1], dk[(p + 1) & 1], dv[(p + 1) & 1],
+                launch_depth_pass(dbits, dgrid, p, dk[p & 1], dv[p & 1], dk[(p + 1) & 1], dv[(p + 1) & 1],
                                   n_all, static_cast<uint32_t*>(ctx->sort_scratch.p), ctx->d_tickets + 2,
                                   err_word(ctx), s));
   }
   if (n_all) {
-    tdgs_status st = do_scan(ctx, counts, nullptr, dv[kDepthPasses & 1], FrameGeom{}, n_all,
+    tdgs_status st = do_scan(ctx, kKFrameScan, counts, nullptr, dv[dpasses & 1], FrameGeom{}, n_all,
                              static_cast<uint32_t*>(ctx->f_soff.p), &ctx->d_status->total, nullptr, s);
     if (st != TDGS_OK) return st;
   } else {
@@ -684,8 +693,9 @@ tdgs_status run_back(tdgs_context* ctx, uint32_t m, const uint64_t* m_dev, cudaS
   const ViewTable vt = device_table(ctx);
   const Shape sh = shape_of(ctx);
   const uint32_t n_all = ctx->n_all;
-  const uint32_t* sdepth = static_cast<uint32_t*>(ctx->f_dkey[kDepthPasses & 1].p);
-  const uint32_t* sorder = static_cast<uint32_t*>(ctx->f_dval[kDepthPasses & 1].p);
+  const uint32_t dpasses = depth_passes(ctx->tuning.depth_digit_bits);
+  const uint32_t* sdepth = static_cast<uint32_t*>(ctx->f_dkey[dpasses & 1].p);
+  const uint32_t* sorder = static_cast<uint32_t*>(ctx->f_dval[dpasses & 1].p);
   uint32_t* scratch = static_cast<uint32_t*>(ctx->sort_scratch.p);
   uint32_t* bar = ctx->d_tickets + 2;
   void* st[2] = {ctx->f_stream[0].p, ctx->f_stream[1].p};
@@ -719,7 +729,7 @@ tdgs_status run_back(tdgs_context* ctx, uint32_t m, const uint64_t* m_dev, cudaS
     sp.views = &vt;
     sp.rmin = last ? rmin : nullptr;
     sp.rmax = last ? rmax : nullptr;
-    TDGS_TRACED(ctx, kKTilePass, m, s, launch_stream_pass(sp, scratch, bar, err_word(ctx), s));
+    TDGS_TRACED(ctx, last ? kKTileExpand : kKTilePass, m, s, launch_stream_pass(sp, scratch, bar, err_word(ctx), s));
     shift += width;
   }
   TDGS_TRACED(ctx, kKRangesFinal, ctx->t_all, s,

@@ -326,6 +326,9 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
     }
   }
   chunk_bases<K, kBins, kThreads>(kin, a, beg, end, d31, base, lstart, s_warp);
+  // bins and bits this pass's digit actually uses (<= kBins, kBits)
+  const uint32_t nb = a.mask + 1 < static_cast<uint32_t>(kBins) ? a.mask + 1 : static_cast<uint32_t>(kBins);
+  const int nbits = 32 - __clz(nb - 1);
 
   // ---- phase 3: stable rank + scatter, tile by tile
   const uint64_t drop = policy_evict_first();
@@ -354,13 +357,16 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
       const uint32_t d = idx < valid ? digit_of<K>(k[j], a.shift, a.mask, d31) : kNoDigit;
       uint32_t peers;
       if constexpr (kBits <= 8) {
-        // lanes with equal digits: AND of one ballot per digit bit
+        // lanes with equal digits: AND of one ballot per digit bit (only
+        // the bits this pass's digit actually has)
         peers = __ballot_sync(0xffffffffu, d != kNoDigit);
         if (d == kNoDigit) peers = ~peers;
 #pragma unroll
         for (int bit = 0; bit < kBits; ++bit) {
-          const uint32_t bal = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
-          peers &= ((d >> bit) & 1u) ? bal : ~bal;
+          if (bit < nbits) {
+            const uint32_t bal = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+            peers &= ((d >> bit) & 1u) ? bal : ~bal;
+          }
         }
       } else {
         peers = __match_any_sync(0xffffffffu, d);
@@ -380,7 +386,7 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
     for (int i = 0; i < kBpt; ++i) {
       const uint32_t b = t + i * kThreads;
       cnt[i] = 0;
-      if (b < kBins) {
+      if (b < nb) {
         uint32_t run = 0;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) {

@@ -7,9 +7,10 @@ namespace tdgs {
 
 namespace {
 using radix::make_kernel;
-const radix::Kernel& depth_kernel() {
-  static const radix::Kernel k = make_kernel<uint32_t, true, false, 11, 256, 16>();
-  return k;
+const radix::Kernel& depth_kernel(int digit_bits) {
+  static const radix::Kernel k11 = make_kernel<uint32_t, true, false, 11, 256, 16>();
+  static const radix::Kernel k8 = make_kernel<uint32_t, true, false, 8, 256, 16>();
+  return digit_bits == 11 ? k11 : k8;
 }
 const radix::Kernel& stream_kernel(bool wide, bool expand, int kernel) {
   static const radix::Kernel k[8] = {
@@ -26,19 +27,24 @@ const radix::Kernel& stream_kernel(bool wide, bool expand, int kernel) {
 }
 }  // namespace
 
-uint32_t depth_sort_grid(uint32_t n, int ctas_per_sm) { return radix::grid_for(depth_kernel(), n, ctas_per_sm); }
-size_t depth_sort_scratch_words(uint32_t grid) { return radix::scratch_words(depth_kernel(), grid); }
+uint32_t depth_sort_grid(uint32_t n, int digit_bits, int ctas_per_sm) {
+  return radix::grid_for(depth_kernel(digit_bits), n, ctas_per_sm);
+}
+size_t depth_sort_scratch_words(int digit_bits, uint32_t grid) {
+  return radix::scratch_words(depth_kernel(digit_bits), grid);
+}
 
-cudaError_t launch_depth_pass(uint32_t grid, uint32_t pass, const uint32_t* kin, const uint32_t* vin,
-                              uint32_t* kout, uint32_t* vout, uint32_t n, uint32_t* scratch,
-                              uint32_t* bar, uint32_t* err, cudaStream_t s) {
+cudaError_t launch_depth_pass(int digit_bits, uint32_t grid, uint32_t pass, const uint32_t* kin,
+                              const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t n,
+                              uint32_t* scratch, uint32_t* bar, uint32_t* err, cudaStream_t s) {
+  const uint32_t w = digit_bits == 11 ? 11u : 8u;
   radix::PassArgs a{};
   a.m = n;
-  a.shift = pass * 11;
-  a.mask = pass * 11 + 11 <= 32 ? 0x7ffu : (1u << (32 - pass * 11)) - 1;
+  a.shift = pass * w;
+  a.mask = a.shift + w <= 32 ? (1u << w) - 1 : (1u << (32 - a.shift)) - 1;
   a.bar = bar;
   a.err = err;
-  return radix::launch(depth_kernel(), grid, kin, vin, kout, vout, a, scratch, s);
+  return radix::launch(depth_kernel(digit_bits), grid, kin, vin, kout, vout, a, scratch, s);
 }
 
 uint32_t stream_grid(bool wide, bool expand, int kernel, uint32_t m, int ctas_per_sm) {

@@ -180,12 +180,13 @@ cudaError_t launch_views_ranges(const ViewTable& vt, const uint32_t* rmin, const
 
 // Radix passes of the frame path (radix_frame.cu).
 // Depth sort of the N Gaussians: (uint32 depth key, uint32 index), 32 bits.
-uint32_t depth_sort_grid(uint32_t n, int ctas_per_sm);
-size_t depth_sort_scratch_words(uint32_t grid);
-cudaError_t launch_depth_pass(uint32_t grid, uint32_t pass, const uint32_t* kin, const uint32_t* vin,
-                              uint32_t* kout, uint32_t* vout, uint32_t n, uint32_t* scratch,
-                              uint32_t* bar, uint32_t* err, cudaStream_t s);
-constexpr uint32_t kDepthPasses = 3;  // 11 + 11 + 10 bits
+// digit_bits 11 (3 passes) or 8 (4 passes) over the 32 bits of the key.
+uint32_t depth_sort_grid(uint32_t n, int digit_bits, int ctas_per_sm);
+size_t depth_sort_scratch_words(int digit_bits, uint32_t grid);
+cudaError_t launch_depth_pass(int digit_bits, uint32_t grid, uint32_t pass, const uint32_t* kin,
+                              const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t n,
+                              uint32_t* scratch, uint32_t* bar, uint32_t* err, cudaStream_t s);
+inline uint32_t depth_passes(int digit_bits) { return digit_bits == 11 ? 3u : 4u; }
 // Stable pass over the packed stream on tile bits [shift, shift + width).
 // expand: write the final (local tile << 32 | depth bits) keys and local
 // indices, and record each global tile's first/last sorted position.
@@ -218,6 +219,7 @@ struct Tuning {
   int tile_digit_bits = 0;   // frame tile passes: digit width 4..8 (0 = 8)
   int tile_kernel = 0;       // frame tile passes: 0 ballot ranking, 1 counter table (<= 6-bit digits)
   int ctas_per_sm = 0;       // persistent radix grids: CTAs per SM (0 = kernel default)
+  int depth_digit_bits = 0;  // depth sort: 11 (3 passes, match.any) or 8 (4 passes, ballots); 0 = 8
 };
 
 // ----------------------------------------------------------- radix sort

@@ -24,7 +24,7 @@ def ctx():
     {"tile_kernel": 1, "tile_digit_bits": 6},
     {"tile_kernel": 1, "tile_digit_bits": 4, "ctas_per_sm": 1},
     {"tile_kernel": 0, "tile_digit_bits": 5, "ctas_per_sm": 3},
-    {"tile_kernel": 0, "tile_digit_bits": 8, "ctas_per_sm": 1},
+    {"tile_kernel": 0, "tile_digit_bits": 8, "ctas_per_sm": 1, "depth_digit_bits": 8},
 ])
 def test_frame_knobs_exact(ctx, oracle, knobs):
     frames = [synth.frame_small(0), synth.frame_large(2, n=60_000, width=1920, height=1080),
@@ -45,7 +45,7 @@ def test_frame_knobs_exact(ctx, oracle, knobs):
             ref = oracle.sort_frame(f.gaussians, f.width, f.height)
             assert np.array_equal(k.cpu().numpy().view(np.uint64), ref["keys"])
     finally:
-        ctx.apply_tuning({"tile_kernel": 0, "tile_digit_bits": 0, "ctas_per_sm": 0})
+        ctx.apply_tuning({"tile_kernel": 0, "tile_digit_bits": 0, "ctas_per_sm": 0, "depth_digit_bits": 0})
 
 
 def test_tuning_rejects_bad_values(ctx):
@@ -60,7 +60,7 @@ def test_autotuner_table(ctx, tmp_path):
     fr = synth.frame_small(1)
     g = T.records_to_tensor(fr.gaussians, DEV)
     res = autotune.tune_views(ctx, [(g, fr.width, fr.height)], reps=1)
-    assert res["ms"] > 0 and len(res["trials"]) == 12
+    assert res["ms"] > 0 and len(res["trials"]) == 24
     counts = ctx.count_tiles(g, fr.width, fr.height)
     offs, tot = ctx.scan(counts)
     k, v = ctx.duplicate_keys(g, offs, fr.width, fr.height, int(tot.item()))
