@@ -263,6 +263,7 @@ def run_ours(args, rank, world, local_rank, dist):
         kw, vw = torch.empty_like(k0), torch.empty_like(v0)
         ctx.sync()
         tb = fr.tile_bits
+        ctx.set_sort_variant(args.sort_variant)
         sev = []
         ctx.enable_timing(True)
         for i in range(args.warmup + args.steps):
@@ -279,6 +280,7 @@ def run_ours(args, rank, world, local_rank, dist):
         ctx.sync()
         skt = ctx.kernel_times()
         ctx.enable_timing(False)
+        ctx.set_sort_variant(-1)
         sms = [a.elapsed_time(b) for a, b in sev]
         passes = skt.get("radix_pass", {}).get("launches", 0) // (args.warmup + args.steps)
         sbytes = m * (8 + 24 * passes)
@@ -485,6 +487,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--sort-variant", type=int, default=-1,
+                    help="pass kernel of the sort-only section (-1: the library's choice)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

@@ -122,10 +122,8 @@ tdgs_status tdgs_context_set_sort_variant(tdgs_context* ctx, int variant);
  * restores the built-in choice); out-of-range keys or values return
  * TDGS_ERR_INVALID_ARGUMENT.
  *   TDGS_TUNE_SORT_VARIANT     pass kernel of tdgs_sort_pairs (as above)
- *   TDGS_TUNE_TILE_DIGIT_BITS  digit width 4..8 of the frame's tile passes
- *   TDGS_TUNE_TILE_KERNEL      0: warp-ballot ranking, 1: per-thread
- *                              counter table with bulk-copy staging
- *                              (digits of at most 6 bits)
+ *   TDGS_TUNE_TILE_DIGIT_BITS  widest digit (4..12) of the frame's passes
+ *                              over the tile bits (built-in: 8)
  *   TDGS_TUNE_CTAS_PER_SM      CTAs per SM of the persistent radix grids
  *                              (capped by occupancy)
  *   TDGS_TUNE_DEPTH_DIGIT_BITS digit width of the frame's depth sort: 8
@@ -134,7 +132,6 @@ tdgs_status tdgs_context_set_sort_variant(tdgs_context* ctx, int variant);
 enum {
   TDGS_TUNE_SORT_VARIANT = 0,
   TDGS_TUNE_TILE_DIGIT_BITS = 1,
-  TDGS_TUNE_TILE_KERNEL = 2,
   TDGS_TUNE_CTAS_PER_SM = 3,
   TDGS_TUNE_DEPTH_DIGIT_BITS = 4
 };

@@ -75,20 +75,18 @@ def tune_sort_pairs(ctx: tdgs.Context, keys: torch.Tensor, values: torch.Tensor,
 
 
 def tune_views(ctx: tdgs.Context, views: list, reps: int = 3) -> dict:
-    """Best (tile_kernel, tile_digit_bits, ctas_per_sm) for a batch of
+    """Best (tile_digit_bits, ctas_per_sm, depth_digit_bits) for a batch of
     views [(records, width, height)] (one view = one frame)."""
     flush = torch.empty(L2_FLUSH, dtype=torch.uint8, device=views[0][0].device)
     trials = []
-    for kern, bits_list in ((0, (8, 6)), (1, (6, 5))):
-        for bits in bits_list:
-            for cps in (0, 2, 3):
-                for dbits in (11, 8):
-                    knobs = {"tile_kernel": kern, "tile_digit_bits": bits, "ctas_per_sm": cps,
-                             "depth_digit_bits": dbits}
-                    ctx.apply_tuning(knobs)
-                    ms = _time(lambda: ctx.sort_views(views), reps, flush)
-                    trials.append((knobs, ms))
-    ctx.apply_tuning({"tile_kernel": 0, "tile_digit_bits": 0, "ctas_per_sm": 0, "depth_digit_bits": 0})
+    for bits in (12, 8, 6):
+        for cps in (0, 1, 2, 3):
+            for dbits in (11, 8):
+                knobs = {"tile_digit_bits": bits, "ctas_per_sm": cps, "depth_digit_bits": dbits}
+                ctx.apply_tuning(knobs)
+                ms = _time(lambda: ctx.sort_views(views), reps, flush)
+                trials.append((knobs, ms))
+    ctx.apply_tuning({"tile_digit_bits": 0, "ctas_per_sm": 0, "depth_digit_bits": 0})
     ctx.sync()
     best, ms = min(trials, key=lambda x: x[1])
     n = sum(int(v[0].shape[0]) for v in views)

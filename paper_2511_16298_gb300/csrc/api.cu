@@ -37,7 +37,6 @@ const char* site_name(uint32_t site) {
     case kSiteBarrier: return "radix pass grid barrier wait";
     case kSiteViewsCount: return "frame count";
     case kSiteViewsDup: return "duplicate by depth";
-    case kSiteCopyWait: return "radix pass bulk-copy wait";
   }
   return "device";
 }
@@ -336,12 +335,8 @@ tdgs_status tdgs_context_set_tuning(tdgs_context* ctx, int key, int value) {
       ctx->tuning.sort_variant = value;
       return TDGS_OK;
     case TDGS_TUNE_TILE_DIGIT_BITS:
-      if (value != 0 && (value < 4 || value > 8)) return TDGS_ERR_INVALID_ARGUMENT;
+      if (value != 0 && (value < 4 || value > 12)) return TDGS_ERR_INVALID_ARGUMENT;
       ctx->tuning.tile_digit_bits = value;
-      return TDGS_OK;
-    case TDGS_TUNE_TILE_KERNEL:
-      if (value < 0 || value > 1) return TDGS_ERR_INVALID_ARGUMENT;
-      ctx->tuning.tile_kernel = value;
       return TDGS_OK;
     case TDGS_TUNE_CTAS_PER_SM:
       if (value < 0 || value > 8) return TDGS_ERR_INVALID_ARGUMENT;
@@ -360,7 +355,6 @@ tdgs_status tdgs_context_get_tuning(const tdgs_context* ctx, int key, int* value
   switch (key) {
     case TDGS_TUNE_SORT_VARIANT: *value = ctx->tuning.sort_variant; return TDGS_OK;
     case TDGS_TUNE_TILE_DIGIT_BITS: *value = ctx->tuning.tile_digit_bits; return TDGS_OK;
-    case TDGS_TUNE_TILE_KERNEL: *value = ctx->tuning.tile_kernel; return TDGS_OK;
     case TDGS_TUNE_CTAS_PER_SM: *value = ctx->tuning.ctas_per_sm; return TDGS_OK;
     case TDGS_TUNE_DEPTH_DIGIT_BITS: *value = ctx->tuning.depth_digit_bits; return TDGS_OK;
   }
@@ -602,6 +596,7 @@ struct Shape {
   uint32_t rbits, tbits;
   bool wide;
   uint32_t npass, w0;
+  uint32_t kbits;  // compiled digit width of the tile passes
 };
 
 Shape shape_of(const tdgs_context* ctx) {
@@ -609,12 +604,14 @@ Shape shape_of(const tdgs_context* ctx) {
   sh.rbits = bits_for(ctx->n_all);
   sh.tbits = bits_for(ctx->t_all);
   sh.wide = sh.tbits + sh.rbits > 32 || sh.rbits >= 32;
-  // digit width of the tile passes: at most 8 bits (ballot ranking) or 6
-  // (counter table), lower if tuned
-  uint32_t dmax = ctx->tuning.tile_digit_bits > 0 ? static_cast<uint32_t>(ctx->tuning.tile_digit_bits) : 8u;
-  if (ctx->tuning.tile_kernel == 1 && dmax > 6) dmax = 6;
+  // digit width of the tile passes: at most 8 bits by default (12 if
+  // tuned: one pass, but its scatter writes runs of about one element per
+  // digit, which costs more than a second pass); the bits are split evenly
+  // over the passes
+  const uint32_t dmax = ctx->tuning.tile_digit_bits > 0 ? static_cast<uint32_t>(ctx->tuning.tile_digit_bits) : 8u;
   sh.npass = sh.tbits <= dmax ? 1u : (sh.tbits + dmax - 1) / dmax;
   sh.w0 = (sh.tbits + sh.npass - 1) / std::max(1u, sh.npass);
+  sh.kbits = stream_kernel_bits(sh.w0);
   return sh;
 }
 
@@ -646,13 +643,13 @@ tdgs_status ensure_pair_buffers(tdgs_context* ctx, uint64_t m, cudaStream_t s) {
   if (st == TDGS_OK) st = ensure(ctx, ctx->f_keys, m * 8 + 16, s);
   if (st == TDGS_OK) st = ensure(ctx, ctx->f_values, m * 4 + 16, s);
   const uint32_t mm = static_cast<uint32_t>(m ? m : 1);
-  const int kern = ctx->tuning.tile_kernel, cps = ctx->tuning.ctas_per_sm;
-  const uint32_t g0 = stream_grid(sh.wide, false, kern, mm, cps), g1 = stream_grid(sh.wide, true, kern, mm, cps);
+  const int cps = ctx->tuning.ctas_per_sm;
+  const uint32_t g0 = stream_grid(sh.wide, false, sh.kbits, mm, cps), g1 = stream_grid(sh.wide, true, sh.kbits, mm, cps);
   if (g0 == 0 || g1 == 0) return fail(ctx, TDGS_ERR_CUDA, "device query for the tile sort failed");
   if (st == TDGS_OK)
     st = ensure(ctx, ctx->sort_scratch,
-                std::max(stream_scratch_words(sh.wide, false, kern, g0),
-                         stream_scratch_words(sh.wide, true, kern, g1)) * 4,
+                std::max(stream_scratch_words(sh.wide, false, sh.kbits, g0),
+                         stream_scratch_words(sh.wide, true, sh.kbits, g1)) * 4,
                 s);
   return st;
 }
@@ -704,9 +701,19 @@ tdgs_status run_back(tdgs_context* ctx, uint32_t m, const uint64_t* m_dev, cudaS
   TDGS_TRACED(ctx, kKDupDepth, m ? n_all : 0, s,
               launch_views_dup(vt, sorder, static_cast<uint32_t*>(ctx->f_soff.p), n_all, sh.rbits, st[0],
                                sh.wide, m, err_word(ctx), s));
-  TDGS_CUDA(ctx, cudaMemsetAsync(rmin, 0xff, static_cast<size_t>(ctx->t_all) * 4, s));
-  TDGS_CUDA(ctx, cudaMemsetAsync(rmax, 0, static_cast<size_t>(ctx->t_all) * 4, s));
-  const uint32_t mm = m ? m : 1;
+  // One pass over the whole tile id writes the ranges from its digit
+  // totals; with several passes the last one records each tile's first and
+  // last position and a small kernel turns them into ranges.
+  const bool single = sh.npass == 1;
+  uint2* ranges = static_cast<uint2*>(ctx->f_ranges.p);
+  if (m == 0) {
+    TDGS_CUDA(ctx, cudaMemsetAsync(ranges, 0, static_cast<size_t>(ctx->t_all) * 8, s));
+    return TDGS_OK;
+  }
+  if (!single) {
+    TDGS_CUDA(ctx, cudaMemsetAsync(rmin, 0xff, static_cast<size_t>(ctx->t_all) * 4, s));
+    TDGS_CUDA(ctx, cudaMemsetAsync(rmax, 0, static_cast<size_t>(ctx->t_all) * 4, s));
+  }
   uint32_t shift = sh.rbits;
   for (uint32_t p = 0; p < sh.npass; ++p) {
     const bool last = p + 1 == sh.npass;
@@ -714,8 +721,8 @@ tdgs_status run_back(tdgs_context* ctx, uint32_t m, const uint64_t* m_dev, cudaS
     StreamPass sp{};
     sp.wide = sh.wide;
     sp.expand = last;
-    sp.kernel = ctx->tuning.tile_kernel;
-    sp.grid = stream_grid(sh.wide, last, sp.kernel, mm, ctx->tuning.ctas_per_sm);
+    sp.bits = sh.kbits;
+    sp.grid = stream_grid(sh.wide, last, sh.kbits, m, ctx->tuning.ctas_per_sm);
     sp.kin = st[p & 1];
     sp.kout = last ? ctx->f_keys.p : st[(p + 1) & 1];
     sp.vout = last ? static_cast<uint32_t*>(ctx->f_values.p) : nullptr;
@@ -727,13 +734,15 @@ tdgs_status run_back(tdgs_context* ctx, uint32_t m, const uint64_t* m_dev, cudaS
     sp.sdepth = sdepth;
     sp.sorder = sorder;
     sp.views = &vt;
-    sp.rmin = last ? rmin : nullptr;
-    sp.rmax = last ? rmax : nullptr;
+    sp.rmin = last && !single ? rmin : nullptr;
+    sp.rmax = last && !single ? rmax : nullptr;
+    sp.ranges = last && single ? ranges : nullptr;
+    sp.t_all = ctx->t_all;
     TDGS_TRACED(ctx, last ? kKTileExpand : kKTilePass, m, s, launch_stream_pass(sp, scratch, bar, err_word(ctx), s));
     shift += width;
   }
-  TDGS_TRACED(ctx, kKRangesFinal, ctx->t_all, s,
-              launch_views_ranges(vt, rmin, rmax, ctx->t_all, static_cast<uint2*>(ctx->f_ranges.p), s));
+  if (!single)
+    TDGS_TRACED(ctx, kKRangesFinal, ctx->t_all, s, launch_views_ranges(vt, rmin, rmax, ctx->t_all, ranges, s));
   return TDGS_OK;
 }
 

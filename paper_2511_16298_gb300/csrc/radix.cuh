@@ -4,19 +4,25 @@
 // One digit pass is one persistent, cooperatively launched kernel whose
 // grid is the number of CTAs resident on the GPU (a multiple of the SM
 // count).  CTA c owns one contiguous chunk of the input:
-//   phase 1  histogram of the chunk's digits (keys read with an L2
-//            evict-last policy so phase 3 finds most of them in L2);
+//   phase 1  histogram of the chunk's digits (16-byte loads with an L2
+//            evict-last policy, so phase 3 finds most keys in L2);
 //   barrier
 //   phase 2  one warp per digit scans the chunk histograms over chunks
 //            -> each chunk's exclusive prefix per digit, and digit totals;
 //   barrier
 //            every CTA scans the totals over digits; its running output
 //            base per digit = digit start + chunk prefix;
-//   phase 3  the chunk is processed tile by tile: warp-level match.any
-//            ranking into per-warp shared counters, exchange through shared
-//            memory into digit order, coalesced scatter at base + rank.
+//   phase 3  the chunk is processed tile by tile (kThreads x kItems keys):
+//            stable ranking inside each warp from one ballot per digit bit,
+//            per-warp digit counters in shared memory, a prefix over warps
+//            and digits, exchange through shared memory into digit order,
+//            coalesced scatter at base + rank.
 // Two bounded grid barriers replace a decoupled look-back, whose walk
 // depth grows with the number of resident tiles when digits are wide.
+//
+// Ranking uses ballots for every digit width: on this GPU one match.any
+// costs about as much as eight ballot rounds, so the ballot chain wins up
+// to 12-bit digits.
 //
 // Template knobs: key type K (uint32/uint64), whether a uint32 value
 // travels with the key, and "expand" (the last pass of the frame path: the
@@ -29,7 +35,6 @@
 namespace tdgs {
 namespace radix {
 
-constexpr uint32_t kNoDigit = 0xffffffffu;
 constexpr uint32_t kMaxGrid = 512;  // chunks per pass (the column scan holds 16 per lane)
 
 __device__ __forceinline__ uint64_t policy_evict_last() {
@@ -37,19 +42,10 @@ __device__ __forceinline__ uint64_t policy_evict_last() {
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
-__device__ __forceinline__ uint64_t policy_evict_first() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t ld_hint(const uint64_t* a, uint64_t pol) {
-  uint64_t v;
-  asm volatile("ld.global.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(a), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ uint32_t ld_hint(const uint32_t* a, uint64_t pol) {
-  uint32_t v;
-  asm volatile("ld.global.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+__device__ __forceinline__ uint4 ld_hint_v4(const void* a, uint64_t pol) {
+  uint4 v;
+  asm volatile("ld.global.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(a), "l"(pol));
   return v;
 }
 __device__ __forceinline__ uint32_t ld_acquire32(const uint32_t* p) {
@@ -116,6 +112,26 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp
   return r;
 }
 
+// Lanes of the warp whose digit equals this lane's, from one ballot per
+// digit bit: a lane keeps the ballot where its own bit is set and the
+// complement where it is clear.  Digits must be < 2^kBits.
+template <int kBits>
+__device__ __forceinline__ uint32_t equal_digit_lanes(uint32_t d) {
+  uint32_t peers = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < kBits; ++b) {
+    asm("{\n\t.reg .pred p;\n\t.reg .u32 t;\n\t"
+        "and.b32 t, %1, %2;\n\t"
+        "setp.ne.u32 p, t, 0;\n\t"
+        "vote.sync.ballot.b32 t, p, 0xffffffff;\n\t"
+        "@!p not.b32 t, t;\n\t"
+        "and.b32 %0, %0, t;\n\t}"
+        : "+r"(peers)
+        : "r"(d), "r"(1u << b));
+  }
+  return peers;
+}
+
 // Digit of a key.  With drop31 (64-bit keys only) bit 31 of every key is
 // known to be zero and is squeezed out: (tile bits : depth bits 30..0).
 template <typename K>
@@ -147,6 +163,11 @@ struct PassArgs {
   uint32_t nv;
   uint32_t* rmin;              // per global tile: first sorted position (atomicMin)
   uint32_t* rmax;              // per global tile: one past the last (atomicMax)
+  // single-pass expansion (the digit is the whole global tile id): ranges
+  // are written straight from the digit totals
+  uint2* ranges;               // [t_all] view-local [start, end), or null
+  const uint32_t* pbeg;        // [nv+1] first pair of each view
+  uint32_t t_all;
   const uint64_t* m_dev;       // optional device element count, capped at m
 };
 
@@ -156,15 +177,21 @@ struct PassShape {
   static constexpr int kWarps = kThreads / 32;
   static constexpr int kTileKeys = kThreads * kItems;
   static constexpr int kBpt = (kBins + kThreads - 1) / kThreads;
+  static constexpr int kCols = kBins / 2;  // counter words: two 16-bit digits each
+  static constexpr int kCpt = (kCols + kThreads - 1) / kThreads;
   static constexpr size_t kWhBytes = static_cast<size_t>(kWarps) * kBins * 2;
   static constexpr size_t kXBytes = static_cast<size_t>(kTileKeys) * sizeof(K);
   static constexpr size_t kUBytes = kWhBytes > kXBytes ? kWhBytes : kXBytes;
   static constexpr size_t kSmem = kUBytes + static_cast<size_t>(kBins) * 8;
-  static constexpr int kMinBlocks = kThreads >= 512 ? 1 : ((sizeof(K) == 4 && !kVals) ? 3 : 2);
+  static constexpr int kMinBlocks = kThreads >= 512 ? 1 : ((sizeof(K) == 4 && !kVals && kBits <= 8) ? 3 : 2);
+  static_assert(kBits >= 1 && kBits <= 12, "digits of 1..12 bits");
+  static_assert(kTileKeys <= 32768, "per-warp counters and their prefixes are 16-bit");
+  static_assert(kWhBytes % 16 == 0, "counters are cleared with 16-byte stores");
 };
 
 // Chunk of the input owned by this CTA (chunks are multiples of 4 keys so
-// every chunk starts 16-byte aligned); m may come from device memory.
+// every chunk starts 16-byte aligned when the array does); m may come from
+// device memory.
 struct Chunk {
   uint32_t m, beg, end;
 };
@@ -185,13 +212,21 @@ __device__ __forceinline__ Chunk chunk_of(const PassArgs& a) {
   return ch;
 }
 
+// Phase 1 body for one key.
+template <typename K>
+__device__ __forceinline__ void count_key(K k, const PassArgs& a, bool d31, uint32_t* hist, bool& bad) {
+  if constexpr (sizeof(K) == 8) bad |= (k & a.bad_mask) != 0;
+  atomicAdd(&hist[digit_of<K>(k, a.shift, a.mask, d31)], 1u);
+}
+
 // Phases 1-2: histogram of this chunk's digits, column scans over chunks
 // between two grid barriers, then base[b] = first output position of this
-// chunk's keys with digit b.  hist: kBins words of shared scratch.
+// chunk's keys with digit b.  hist: kBins words of shared scratch.  With
+// a.ranges set, the tile ranges are written from the digit totals.
 template <typename K, int kBins, int kThreads>
 __device__ __forceinline__ void chunk_bases(const K* __restrict__ kin, const PassArgs& a,
                                             uint32_t beg, uint32_t end, bool d31, uint32_t* base,
-                                            uint32_t* hist, uint32_t* s_warp) {
+                                            uint32_t* hist, uint32_t* s_warp, const uint32_t* s_vtile) {
   constexpr int kWarps = kThreads / 32;
   constexpr int kBpt = (kBins + kThreads - 1) / kThreads;
   const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
@@ -201,23 +236,32 @@ __device__ __forceinline__ void chunk_bases(const K* __restrict__ kin, const Pas
   {
     const uint64_t keep = policy_evict_last();
     bool bad = false;
-    constexpr int kU = 8;
-    for (uint64_t i0 = beg + warp * 32 * kU; i0 < end; i0 += kThreads * kU) {
-      K k8[kU];
+    const K* kc = kin + beg;
+    const uint32_t len = end - beg;
+    uint32_t done = 0;
+    if ((reinterpret_cast<uintptr_t>(kc) & 15u) == 0) {
+      constexpr uint32_t kPer = 16 / sizeof(K);  // keys per 16-byte vector
+      constexpr uint32_t kU = 4;                 // vectors in flight per thread
+      const uint32_t nvec = len / kPer;
+      for (uint32_t q0 = t; q0 < nvec; q0 += kThreads * kU) {
+        uint4 w[kU];
 #pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const uint64_t i = i0 + u * 32 + lane;
-        k8[u] = i < end ? ld_hint(kin + i, keep) : K(0);
-      }
+        for (uint32_t u = 0; u < kU; ++u) {
+          const uint32_t q = q0 + u * kThreads;
+          w[u] = q < nvec ? ld_hint_v4(kc + q * kPer, keep) : make_uint4(0, 0, 0, 0);
+        }
 #pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const uint64_t i = i0 + u * 32 + lane;
-        if (i < end) {
-          bad |= (static_cast<uint64_t>(k8[u]) & a.bad_mask) != 0;
-          atomicAdd(&hist[digit_of<K>(k8[u], a.shift, a.mask, d31)], 1u);
+        for (uint32_t u = 0; u < kU; ++u) {
+          if (q0 + u * kThreads < nvec) {
+            const K* e = reinterpret_cast<const K*>(&w[u]);
+#pragma unroll
+            for (uint32_t i = 0; i < kPer; ++i) count_key<K>(e[i], a, d31, hist, bad);
+          }
         }
       }
+      done = nvec * kPer;
     }
+    for (uint32_t i = done + t; i < len; i += kThreads) count_key<K>(kc[i], a, d31, hist, bad);
     if (__any_sync(0xffffffffu, bad) && lane == 0) latch_error(a.err, TDGS_ERR_INVALID_ARGUMENT, kSiteRadixKeys);
   }
   __syncthreads();
@@ -264,7 +308,19 @@ __device__ __forceinline__ void chunk_bases(const K* __restrict__ kin, const Pas
 #pragma unroll
   for (int i = 0; i < kBpt; ++i) {
     const uint32_t b = t * kBpt + i;
-    if (b < kBins) base[b] = run + __ldcg(a.P + static_cast<size_t>(c) * kBins + b);
+    if (b < kBins) {
+      base[b] = run + __ldcg(a.P + static_cast<size_t>(c) * kBins + b);
+      // every tile's range, spread over the CTAs; positions are relative
+      // to the view's first pair
+      if (a.ranges && b < a.t_all && b % G == c) {
+        uint2 rg = make_uint2(0u, 0u);
+        if (seg[i]) {
+          const uint32_t pb = a.pbeg[a.nv == 1 ? 0u : find_view(s_vtile, a.nv, b)];
+          rg = make_uint2(run - pb, run + seg[i] - pb);
+        }
+        a.ranges[b] = rg;
+      }
+    }
     run += seg[i];
   }
   __syncthreads();
@@ -272,26 +328,197 @@ __device__ __forceinline__ void chunk_bases(const K* __restrict__ kin, const Pas
 
 // Output of one key at its sorted position dst.  Plain passes store the
 // key; the expanding pass stores (local tile << 32 | depth bits) and the
-// view-local Gaussian index, and records the first/last position of each
-// global tile run seen in this tile's exchange buffer xk.
+// view-local Gaussian index, and (multi-pass tile sorts) records the
+// first/last position of each global tile run seen in this tile's exchange
+// buffer xk.
 template <typename K, bool kExpand>
 __device__ __forceinline__ void emit_key(const PassArgs& a, K key, uint32_t dst, const K* xk,
                                          uint32_t p, uint32_t valid, const uint32_t* s_vrec,
                                          const uint32_t* s_vtile, void* kout_raw, uint32_t* vout) {
   if constexpr (kExpand) {
     const uint32_t rk = static_cast<uint32_t>(key & ((static_cast<K>(1) << a.rbits) - 1));
-    const uint64_t gt = static_cast<uint64_t>(key >> a.rbits);
+    const uint32_t gt = static_cast<uint32_t>(key >> a.rbits);
     const uint32_t gi = __ldg(a.sorder + rk);
     const uint32_t v = a.nv == 1 ? 0u : find_view(s_vrec, a.nv, gi);
-    static_cast<uint64_t*>(kout_raw)[dst] = ((gt - s_vtile[v]) << 32) | __ldg(a.sdepth + rk);
+    static_cast<uint64_t*>(kout_raw)[dst] =
+        (static_cast<uint64_t>(gt - s_vtile[v]) << 32) | __ldg(a.sdepth + rk);
     vout[dst] = gi - s_vrec[v];
     if (a.rmin) {
-      if (p == 0 || static_cast<uint64_t>(xk[p - 1] >> a.rbits) != gt) atomicMin(a.rmin + gt, dst);
-      if (p + 1 == valid || static_cast<uint64_t>(xk[p + 1] >> a.rbits) != gt) atomicMax(a.rmax + gt, dst + 1);
+      if (p == 0 || static_cast<uint32_t>(xk[p - 1] >> a.rbits) != gt) atomicMin(a.rmin + gt, dst);
+      if (p + 1 == valid || static_cast<uint32_t>(xk[p + 1] >> a.rbits) != gt) atomicMax(a.rmax + gt, dst + 1);
     }
   } else {
     static_cast<K*>(kout_raw)[dst] = key;
   }
+}
+
+// Shared-memory layout of one pass CTA.
+template <typename K>
+struct Smem {
+  uint16_t* wh;     // [kWarps][kBins] per-warp digit counters while ranking
+  K* xk;            // key exchange afterwards (aliases wh)
+  uint32_t* xv;     // value exchange afterwards (aliases wh)
+  uint32_t* base;   // [kBins] running output base of this chunk per digit
+  uint32_t* lstart; // [kBins] tile-local digit start, then base - start
+};
+
+// Phase 3 for one tile of `valid` keys starting at kt (kFull: valid ==
+// kTileKeys, no bounds checks).  Returns false if a destination fell
+// outside [0, m).
+template <bool kFull, typename S, typename K, bool kVals, bool kExpand, int kBits, int kItems>
+__device__ __forceinline__ bool rank_and_scatter(const K* __restrict__ kt, const uint32_t* __restrict__ vt,
+                                                 uint32_t valid, uint32_t m, const PassArgs& a, bool d31,
+                                                 const Smem<K>& sm, uint32_t* s_warp,
+                                                 const uint32_t* s_vrec, const uint32_t* s_vtile,
+                                                 void* kout_raw, uint32_t* vout) {
+  constexpr int kBins = S::kBins;
+  constexpr int kWarps = S::kWarps;
+  constexpr int kThreads = kWarps * 32;
+  constexpr int kBpt = S::kBpt;
+  constexpr int kCols = S::kCols;
+  constexpr int kCpt = S::kCpt;
+  const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+  const uint32_t wbase = warp * 32 * kItems;
+  bool ok = true;
+
+  // clear the per-warp counters (16-byte stores)
+  {
+    uint4* z = reinterpret_cast<uint4*>(sm.wh);
+    constexpr uint32_t kVec = static_cast<uint32_t>(S::kWhBytes / 16);
+    for (uint32_t i = t; i < kVec; i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
+  }
+  K k[kItems];
+  uint32_t v[kVals ? kItems : 1];
+  uint32_t d[kItems];
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    const uint32_t idx = wbase + j * 32 + lane;
+    if (kFull || idx < valid) {
+      k[j] = __ldcs(kt + idx);
+      if constexpr (kVals) v[j] = __ldcs(vt + idx);
+    } else {
+      k[j] = K(0);
+      if constexpr (kVals) v[j] = 0u;
+    }
+    d[j] = digit_of<K>(k[j], a.shift, a.mask, d31);
+  }
+  __syncthreads();
+  // rank within the warp: every lane of an equal-digit group reads the
+  // warp's counter, the group's highest lane writes it back bumped
+  uint16_t* my_wh = sm.wh + warp * kBins;
+  uint32_t r[kItems];
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    uint32_t peers = equal_digit_lanes<kBits>(d[j]);
+    bool live = true;
+    if constexpr (!kFull) {
+      const uint32_t first = wbase + j * 32;
+      const uint32_t nlive = valid > first ? min(valid - first, 32u) : 0u;
+      live = lane < nlive;
+      peers &= nlive >= 32 ? 0xffffffffu : ((1u << nlive) - 1u);
+    }
+    const uint32_t before = my_wh[d[j]];
+    __syncwarp();
+    const uint32_t cnt = __popc(peers);
+    const uint32_t below = __popc(peers & lt);
+    if (live && below + 1 == cnt) my_wh[d[j]] = static_cast<uint16_t>(before + cnt);
+    __syncwarp();
+    r[j] = before + below;
+  }
+  __syncthreads();
+  // exclusive prefix over warps per digit (two digits per 32-bit word);
+  // tile count per digit into lstart
+  uint32_t cnt2[kCpt];
+  {
+    uint32_t* wh32 = reinterpret_cast<uint32_t*>(sm.wh);
+#pragma unroll
+    for (int i = 0; i < kCpt; ++i) {
+      const uint32_t c = t + i * kThreads;
+      cnt2[i] = 0;
+      if (c < static_cast<uint32_t>(kCols)) {
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+          const uint32_t x = wh32[w * kCols + c];
+          wh32[w * kCols + c] = run;
+          run += x;  // halves stay below 2^16: no carry between digits
+        }
+        cnt2[i] = run;
+        sm.lstart[2 * c] = run & 0xffffu;
+        sm.lstart[2 * c + 1] = run >> 16;
+      }
+    }
+  }
+  __syncthreads();
+  {
+    uint32_t seg[kBpt];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < kBpt; ++i) {
+      const uint32_t b = t * kBpt + i;
+      seg[i] = b < kBins ? sm.lstart[b] : 0;
+      sum += seg[i];
+    }
+    uint32_t run = block_excl_scan<kWarps>(sum, s_warp);
+#pragma unroll
+    for (int i = 0; i < kBpt; ++i) {
+      const uint32_t b = t * kBpt + i;
+      if (b < kBins) sm.lstart[b] = run;
+      run += seg[i];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) r[j] += sm.lstart[d[j]] + my_wh[d[j]];
+  __syncthreads();  // wh is overwritten by the exchange below; lstart becomes the offset
+#pragma unroll
+  for (int i = 0; i < kCpt; ++i) {
+    const uint32_t c = t + i * kThreads;
+    if (c < static_cast<uint32_t>(kCols)) {
+      const uint32_t b0 = 2 * c, b1 = 2 * c + 1;
+      sm.lstart[b0] = sm.base[b0] - sm.lstart[b0];
+      sm.lstart[b1] = sm.base[b1] - sm.lstart[b1];
+      sm.base[b0] += cnt2[i] & 0xffffu;
+      sm.base[b1] += cnt2[i] >> 16;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kItems; ++j)
+    if (kFull || wbase + j * 32 + lane < valid) sm.xk[r[j]] = k[j];
+  __syncthreads();
+  // Scatter in digit order.  A destination outside [0, m) can only come
+  // from a timed-out barrier or keys changed underneath the sort: it is
+  // dropped and reported instead of written.
+  uint32_t dst[kItems];
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const uint32_t p = i * kThreads + t;
+    dst[i] = 0xffffffffu;
+    if (kFull || p < valid) {
+      const K key = sm.xk[p];
+      dst[i] = sm.lstart[digit_of<K>(key, a.shift, a.mask, d31)] + p;
+      if (dst[i] < m) {
+        emit_key<K, kExpand>(a, key, dst[i], sm.xk, p, valid, s_vrec, s_vtile, kout_raw, vout);
+      } else {
+        ok = false;
+      }
+    }
+  }
+  if constexpr (kVals) {
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kItems; ++j)
+      if (kFull || wbase + j * 32 + lane < valid) sm.xv[r[j]] = v[j];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      const uint32_t p = i * kThreads + t;
+      if ((kFull || p < valid) && dst[i] < m) vout[dst[i]] = sm.xv[p];
+    }
+  }
+  __syncthreads();  // exchange buffers and offsets are reused by the next tile
+  return ok;
 }
 
 template <typename K, bool kVals, bool kExpand, int kBits, int kThreads, int kItems>
@@ -299,23 +526,19 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
     k_radix_pass(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
                  void* __restrict__ kout_raw, uint32_t* __restrict__ vout, PassArgs a) {
   using S = PassShape<K, kVals, kExpand, kBits, kThreads, kItems>;
-  constexpr int kBins = S::kBins;
-  constexpr int kWarps = S::kWarps;
-  constexpr int kTileKeys = S::kTileKeys;
-  constexpr int kBpt = S::kBpt;
+  constexpr uint32_t kTileKeys = S::kTileKeys;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint16_t* wh = reinterpret_cast<uint16_t*>(smem);  // [kWarps][kBins] while ranking
-  K* xk = reinterpret_cast<K*>(smem);                 // key exchange afterwards
-  uint32_t* xv = reinterpret_cast<uint32_t*>(smem);   // value exchange afterwards
-  uint32_t* base = reinterpret_cast<uint32_t*>(smem + S::kUBytes);  // running output base
-  uint32_t* lstart = base + kBins;                                   // tile-local digit start
-  __shared__ uint32_t s_warp[kWarps];
+  Smem<K> sm;
+  sm.wh = reinterpret_cast<uint16_t*>(smem);
+  sm.xk = reinterpret_cast<K*>(smem);
+  sm.xv = reinterpret_cast<uint32_t*>(smem);
+  sm.base = reinterpret_cast<uint32_t*>(smem + S::kUBytes);
+  sm.lstart = sm.base + S::kBins;
+  __shared__ uint32_t s_warp[S::kWarps];
   __shared__ uint32_t s_vrec[kExpand ? kMaxViews + 1 : 1];
   __shared__ uint32_t s_vtile[kExpand ? kMaxViews + 1 : 1];
 
   const uint32_t t = threadIdx.x;
-  const uint32_t lane = lane_id();
-  const uint32_t warp = t >> 5;
   const bool d31 = a.drop31 != 0;
   const Chunk ch = chunk_of(a);
   const uint32_t m = ch.m, beg = ch.beg, end = ch.end;
@@ -325,463 +548,33 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
       s_vtile[v] = a.vtile_begin[v];
     }
   }
-  chunk_bases<K, kBins, kThreads>(kin, a, beg, end, d31, base, lstart, s_warp);
-  // bins and bits this pass's digit actually uses (<= kBins, kBits)
-  const uint32_t nb = a.mask + 1 < static_cast<uint32_t>(kBins) ? a.mask + 1 : static_cast<uint32_t>(kBins);
-  const int nbits = 32 - __clz(nb - 1);
+  chunk_bases<K, S::kBins, kThreads>(kin, a, beg, end, d31, sm.base, sm.lstart, s_warp, s_vtile);
 
   // ---- phase 3: stable rank + scatter, tile by tile
-  const uint64_t drop = policy_evict_first();
-  bool out_of_range = false;
-  for (uint64_t tb64 = beg; tb64 < end; tb64 += kTileKeys) {
-    const uint32_t tb = static_cast<uint32_t>(tb64);
-    const uint32_t valid = min(static_cast<uint32_t>(kTileKeys), end - tb);
-    for (uint32_t i = t; i < kWarps * kBins / 2; i += kThreads) reinterpret_cast<uint32_t*>(wh)[i] = 0;
-    K k[kItems];
-    uint32_t v[kVals ? kItems : 1];
-    uint32_t r[kItems];
-    const uint32_t wbase = warp * 32 * kItems;
-#pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-      const uint32_t idx = wbase + j * 32 + lane;
-      k[j] = idx < valid ? ld_hint(kin + tb + idx, drop) : K(0);
-      if constexpr (kVals) v[j] = idx < valid ? ld_hint(vin + tb + idx, drop) : 0u;
-    }
-    __syncthreads();
-    // rank within the warp: the lowest lane of each equal-digit group reads
-    // and bumps the warp's counter of that digit
-    uint16_t* my_wh = wh + warp * kBins;
-#pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-      const uint32_t idx = wbase + j * 32 + lane;
-      const uint32_t d = idx < valid ? digit_of<K>(k[j], a.shift, a.mask, d31) : kNoDigit;
-      uint32_t peers;
-      if constexpr (kBits <= 8) {
-        // lanes with equal digits: AND of one ballot per digit bit (only
-        // the bits this pass's digit actually has)
-        peers = __ballot_sync(0xffffffffu, d != kNoDigit);
-        if (d == kNoDigit) peers = ~peers;
-#pragma unroll
-        for (int bit = 0; bit < kBits; ++bit) {
-          if (bit < nbits) {
-            const uint32_t bal = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
-            peers &= ((d >> bit) & 1u) ? bal : ~bal;
-          }
-        }
-      } else {
-        peers = __match_any_sync(0xffffffffu, d);
-      }
-      const uint32_t leader = __ffs(peers) - 1;
-      uint32_t before = 0;
-      if (lane == leader && d != kNoDigit) before = my_wh[d];
-      before = __shfl_sync(0xffffffffu, before, leader);
-      if (lane == leader && d != kNoDigit) my_wh[d] = static_cast<uint16_t>(before + __popc(peers));
-      r[j] = before + __popc(peers & lanemask_lt());
-      __syncwarp();
-    }
-    __syncthreads();
-    // exclusive prefix over warps per digit; tile count per digit
-    uint32_t cnt[kBpt];
-#pragma unroll
-    for (int i = 0; i < kBpt; ++i) {
-      const uint32_t b = t + i * kThreads;
-      cnt[i] = 0;
-      if (b < nb) {
-        uint32_t run = 0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-          const uint32_t x = wh[w * kBins + b];
-          wh[w * kBins + b] = static_cast<uint16_t>(run);
-          run += x;
-        }
-        cnt[i] = run;
-        lstart[b] = run;
-      }
-    }
-    __syncthreads();
-    {
-      uint32_t seg[kBpt];
-      uint32_t sum = 0;
-#pragma unroll
-      for (int i = 0; i < kBpt; ++i) {
-        const uint32_t b = t * kBpt + i;
-        seg[i] = b < kBins ? lstart[b] : 0;
-        sum += seg[i];
-      }
-      uint32_t run = block_excl_scan<kWarps>(sum, s_warp);
-#pragma unroll
-      for (int i = 0; i < kBpt; ++i) {
-        const uint32_t b = t * kBpt + i;
-        if (b < kBins) lstart[b] = run;
-        run += seg[i];
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-      const uint32_t idx = wbase + j * 32 + lane;
-      if (idx < valid) {
-        const uint32_t d = digit_of<K>(k[j], a.shift, a.mask, d31);
-        r[j] += lstart[d] + my_wh[d];
-      }
-    }
-    __syncthreads();  // wh is overwritten by the exchange below; lstart becomes the offset
-#pragma unroll
-    for (int i = 0; i < kBpt; ++i) {
-      const uint32_t b = t + i * kThreads;
-      if (b < kBins) lstart[b] = base[b] - lstart[b];
-    }
-#pragma unroll
-    for (int j = 0; j < kItems; ++j)
-      if (wbase + j * 32 + lane < valid) xk[r[j]] = k[j];
-    __syncthreads();
-    // Scatter in digit order.  A destination outside [0, m) can only come
-    // from a timed-out barrier or keys changed underneath the sort: it is
-    // dropped and reported instead of written.
-    uint32_t dst[kItems];
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-      const uint32_t p = i * kThreads + t;
-      dst[i] = 0xffffffffu;
-      if (p < valid) {
-        const K key = xk[p];
-        const uint32_t d = digit_of<K>(key, a.shift, a.mask, d31);
-        dst[i] = lstart[d] + p;
-        if (dst[i] < m) {
-          emit_key<K, kExpand>(a, key, dst[i], xk, p, valid, s_vrec, s_vtile, kout_raw, vout);
-        } else {
-          out_of_range = true;
-        }
-      }
-    }
-    if constexpr (kVals) {
-      __syncthreads();
-#pragma unroll
-      for (int j = 0; j < kItems; ++j)
-        if (wbase + j * 32 + lane < valid) xv[r[j]] = v[j];
-      __syncthreads();
-#pragma unroll
-      for (int i = 0; i < kItems; ++i) {
-        const uint32_t p = i * kThreads + t;
-        if (p < valid && dst[i] < m) vout[dst[i]] = xv[p];
-      }
-    }
-    __syncthreads();  // every scatter has read base[] before it moves on
-#pragma unroll
-    for (int i = 0; i < kBpt; ++i) {
-      const uint32_t b = t + i * kThreads;
-      if (b < kBins) base[b] += cnt[i];
-    }
-    __syncthreads();
-  }
-  if (out_of_range) latch_error(a.err, TDGS_ERR_CAPACITY, kSiteRadixRange);
-}
-
-// ------------------------------------------------- bulk copies (TMA)
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-// One thread: expect `bytes` on `bar`, then copy them global -> shared.
-// dst, src 16-byte aligned; bytes a multiple of 16.
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
-                                          uint64_t policy) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
-      ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
-      : "memory");
-}
-// Wait for phase `parity` of `bar`, bounded; returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t spin = 0; spin < kSpinLimit; ++spin) {
-    uint32_t ok;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-// ------------------------------------------------ counter-table ranking
-// Keys-only pass for digits of at most 6 bits (the tile passes of the fused
-// frame).  Thread t owns 16 consecutive keys of a 4096-key tile (blocked,
-// loaded as 16-byte vectors).  Ranking needs no cross-lane operation:
-//   1. every thread bumps its own column of a [64 digits][256 threads]
-//      counter table (the count before the bump is the key's rank among
-//      its own earlier keys with that digit);
-//   2. one exclusive scan over the table in digit-major, thread-minor order
-//      turns each counter into "keys of the tile with a smaller digit, plus
-//      keys with this digit in earlier threads";
-//   3. rank = scanned counter + own-column rank: the stable position of
-//      the key in the tile sorted by digit.
-// The table is padded (row stride 260 words, quarter-row stride 65) so the
-// bumps and the per-thread scan segments hit distinct banks.
-namespace ct {
-constexpr int kThreads = 256, kItems = 16, kBins = 64, kTileKeys = kThreads * kItems;
-constexpr int kRow = 260, kQuarter = 65;
-constexpr size_t kTableWords = static_cast<size_t>(kBins) * kRow;
-constexpr size_t kTableBytes = kTableWords * 4;       // 66,560 B
-constexpr int kRing = 4;                               // phase-1 copy blocks in flight
-constexpr uint32_t kBlockBytes = 16384;                // bytes per phase-1 block
-// layout: table | stage (one tile of keys) | base, off | 5 mbarriers
-template <typename K>
-__host__ __device__ constexpr size_t stage_bytes() { return static_cast<size_t>(kTileKeys) * sizeof(K); }
-template <typename K>
-__host__ __device__ constexpr size_t smem_bytes() { return kTableBytes + stage_bytes<K>() + kBins * 8 + 64; }
-__device__ __forceinline__ uint32_t cell(uint32_t d, uint32_t t) {
-  return d * kRow + (t >> 6) * kQuarter + (t & 63);
-}
-}  // namespace ct
-
-__device__ __forceinline__ uint4 ld_hint_v4(const void* a, uint64_t pol) {
-  uint4 v;
-  asm volatile("ld.global.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(a), "l"(pol));
-  return v;
-}
-
-// Keys are fetched with bulk copies into shared memory: in phase 1 the
-// chunk streams through a ring of kRing 16 KB blocks held in the (not yet
-// used) counter table; in phase 3 the next tile is copied into the stage
-// buffer while the current one (already in registers) is ranked and
-// scattered.  A copy may read up to 15 bytes past the last key: every
-// buffer this kernel reads carries 16 bytes of slack.  Waits are bounded.
-template <typename K, bool kExpand>
-__global__ void __launch_bounds__(ct::kThreads, 2)
-    k_radix_pass_ct(const K* __restrict__ kin, const uint32_t* __restrict__ vin_unused,
-                    void* __restrict__ kout_raw, uint32_t* __restrict__ vout, PassArgs a) {
-  using namespace ct;
-  extern __shared__ __align__(128) unsigned char smem[];
-  uint32_t* C = reinterpret_cast<uint32_t*>(smem);  // counter table, then the key exchange
-  K* xk = reinterpret_cast<K*>(smem);
-  K* stage = reinterpret_cast<K*>(smem + kTableBytes);
-  uint32_t* base = reinterpret_cast<uint32_t*>(smem + kTableBytes + stage_bytes<K>());
-  uint32_t* off = base + kBins;  // phase-1 histogram, then base - tile-local start
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(off + kBins);  // [0..kRing-1] ring, [kRing] stage
-  __shared__ uint32_t s_warp[kThreads / 32];
-  __shared__ uint32_t s_vrec[kExpand ? kMaxViews + 1 : 1];
-  __shared__ uint32_t s_vtile[kExpand ? kMaxViews + 1 : 1];
-  const uint32_t t = threadIdx.x;
-  const Chunk ch = chunk_of(a);
-  const uint32_t m = ch.m, beg = ch.beg, end = ch.end;
-  if (t == 0) {
-    for (int i = 0; i <= kRing; ++i) mbar_init(mbar + i, 1);
-    fence_mbar_init();
-  }
-  if constexpr (kExpand) {
-    for (uint32_t v = t; v <= a.nv; v += kThreads) {
-      s_vrec[v] = a.vrec_begin[v];
-      s_vtile[v] = a.vtile_begin[v];
-    }
-  }
-  for (uint32_t b = t; b < kBins; b += kThreads) off[b] = 0;
-  __syncthreads();
-  const uint64_t keep = policy_evict_last();
-  const uint64_t drop = policy_evict_first();
-  bool timed_out = false;
-
-  // ---- phase 1: histogram, keys streamed through the ring
-  {
-    constexpr uint32_t kPerBlock = kBlockBytes / sizeof(K);
-    const uint32_t nblk = (end - beg + kPerBlock - 1) / kPerBlock;
-    unsigned char* ring = smem;  // kRing * kBlockBytes <= kTableBytes
-    auto issue = [&](uint32_t blk) {
-      const uint32_t kb = beg + blk * kPerBlock;
-      const uint32_t cnt = min(kPerBlock, end - kb);
-      const uint32_t bytes = (cnt * static_cast<uint32_t>(sizeof(K)) + 15u) & ~15u;
-      bulk_load(ring + (blk % kRing) * kBlockBytes, kin + kb, bytes, mbar + (blk % kRing), keep);
-    };
-    if (t == 0)
-      for (uint32_t blk = 0; blk < nblk && blk < kRing; ++blk) issue(blk);
-    uint32_t issued = nblk < kRing ? nblk : kRing;  // same value in every thread
-    bool bad = false;
-    for (uint32_t blk = 0; blk < nblk; ++blk) {
-      // block-uniform decision: every thread leaves together or not at all
-      if (__syncthreads_or(!mbar_wait(mbar + (blk % kRing), (blk / kRing) & 1u))) {
-        timed_out = true;
-        if (t == 0)  // let the copies still in flight land (bounded)
-          for (uint32_t q = blk; q < issued; ++q) mbar_wait(mbar + (q % kRing), (q / kRing) & 1u);
-        break;
-      }
-      const K* kb = reinterpret_cast<const K*>(ring + (blk % kRing) * kBlockBytes);
-      const uint32_t cnt = min(kPerBlock, end - (beg + blk * kPerBlock));
-      for (uint32_t i = t; i < cnt; i += kThreads) {
-        const K key = kb[i];
-        bad |= (static_cast<uint64_t>(key) & a.bad_mask) != 0;
-        atomicAdd(&off[digit_of<K>(key, a.shift, a.mask, false)], 1u);
-      }
-      __syncthreads();  // every thread is done with this block before it is refilled
-      if (blk + kRing < nblk) {
-        if (t == 0) {
-          fence_proxy_async();
-          issue(blk + kRing);
-        }
-        ++issued;
-      }
-    }
-    if (__any_sync(0xffffffffu, bad) && lane_id() == 0)
-      latch_error(a.err, TDGS_ERR_INVALID_ARGUMENT, kSiteRadixKeys);
-  }
-  __syncthreads();
-  // ---- phase 2: offsets over chunks (the histogram is in off[])
-  for (uint32_t b = t; b < kBins; b += kThreads) a.H[static_cast<size_t>(blockIdx.x) * kBins + b] = off[b];
-  grid_barrier(a.bar, a.err);
-  {
-    const uint32_t lane = lane_id(), warp = t >> 5, G = gridDim.x, c = blockIdx.x;
-    constexpr uint32_t kCol = kMaxGrid / 32;
-    for (uint32_t b = c * (kThreads / 32) + warp; b < static_cast<uint32_t>(kBins); b += G * (kThreads / 32)) {
-      uint32_t h[kCol];
-#pragma unroll
-      for (uint32_t q = 0; q < kCol; ++q) {
-        const uint32_t cc = lane * kCol + q;
-        h[q] = cc < G ? __ldcg(a.H + static_cast<size_t>(cc) * kBins + b) : 0u;
-      }
-      uint32_t sum = 0;
-#pragma unroll
-      for (uint32_t q = 0; q < kCol; ++q) sum += h[q];
-      uint32_t x = sum;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t o = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= static_cast<uint32_t>(d)) x += o;
-      }
-      uint32_t run = x - sum;
-#pragma unroll
-      for (uint32_t q = 0; q < kCol; ++q) {
-        const uint32_t cc = lane * kCol + q;
-        if (cc < G) a.P[static_cast<size_t>(cc) * kBins + b] = run;
-        run += h[q];
-      }
-      if (lane == 31) a.tot[b] = x;
-    }
-  }
-  grid_barrier(a.bar, a.err);
-  {
-    const uint32_t v = t < kBins ? __ldcg(a.tot + t) : 0u;
-    const uint32_t run = block_excl_scan<kThreads / 32>(v, s_warp);
-    if (t < kBins) base[t] = run + __ldcg(a.P + static_cast<size_t>(blockIdx.x) * kBins + t);
-  }
-  __syncthreads();
-
-  // ---- phase 3: tiles; the next tile is copied while this one is processed
-  bool out_of_range = false;
-  const uint32_t ntile = (end - beg + kTileKeys - 1) / kTileKeys;
-  auto issue_tile = [&](uint32_t i) {
+  bool ok = true;
+  const uint32_t len = end - beg;
+  const uint32_t full = len / kTileKeys;
+  for (uint32_t i = 0; i < full; ++i) {
     const uint32_t tb = beg + i * kTileKeys;
-    const uint32_t cnt = min(static_cast<uint32_t>(kTileKeys), end - tb);
-    const uint32_t bytes = (cnt * static_cast<uint32_t>(sizeof(K)) + 15u) & ~15u;
-    bulk_load(stage, kin + tb, bytes, mbar + kRing, drop);
-  };
-  if (t == 0 && ntile > 0 && !timed_out) {
-    fence_proxy_async();
-    issue_tile(0);
+    ok &= rank_and_scatter<true, S, K, kVals, kExpand, kBits, kItems>(
+        kin + tb, kVals ? vin + tb : nullptr, kTileKeys, m, a, d31, sm, s_warp, s_vrec, s_vtile, kout_raw, vout);
   }
-  for (uint32_t i = 0; i < ntile && !timed_out; ++i) {
-    const uint32_t tb = beg + i * kTileKeys;
-    const uint32_t valid = min(static_cast<uint32_t>(kTileKeys), end - tb);
-    for (uint32_t z = t; z < kTableWords / 4; z += kThreads) reinterpret_cast<uint4*>(C)[z] = make_uint4(0, 0, 0, 0);
-    if (__syncthreads_or(!mbar_wait(mbar + kRing, i & 1u))) {
-      timed_out = true;
-      if (t == 0) mbar_wait(mbar + kRing, i & 1u);  // the pending copy, bounded
-      break;
-    }
-    K k[kItems];
-    const uint32_t first = t * kItems;
-#pragma unroll
-    for (int j = 0; j < kItems; ++j) k[j] = first + j < valid ? stage[first + j] : K(0);
-    __syncthreads();  // stage fully read; table zeroed
-    if (t == 0 && i + 1 < ntile) {
-      fence_proxy_async();
-      issue_tile(i + 1);
-    }
-    // 1. own-column counts
-    uint32_t r[kItems];
-#pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-      if (first + j < valid) {
-        uint32_t* cp = C + cell(digit_of<K>(k[j], a.shift, a.mask, false), t);
-        const uint32_t o = *cp;
-        *cp = o + 1;
-        r[j] = o;
-      }
-    }
-    __syncthreads();
-    // 2. exclusive scan in (digit, thread) order: thread t owns the 64
-    //    counters of digit t/4, threads 64*(t%4) .. 64*(t%4)+63
-    {
-      uint32_t* seg = C + (t >> 2) * kRow + (t & 3) * kQuarter;
-      uint32_t sum = 0;
-#pragma unroll 16
-      for (int q = 0; q < 64; ++q) sum += seg[q];
-      uint32_t run = block_excl_scan<kThreads / 32>(sum, s_warp);
-#pragma unroll 16
-      for (int q = 0; q < 64; ++q) {
-        const uint32_t x = seg[q];
-        seg[q] = run;
-        run += x;
-      }
-    }
-    __syncthreads();
-    // 3. ranks; per-digit tile start and count
-#pragma unroll
-    for (int j = 0; j < kItems; ++j)
-      if (first + j < valid) r[j] += C[cell(digit_of<K>(k[j], a.shift, a.mask, false), t)];
-    uint32_t cnt = 0;
-    if (t < kBins) {
-      const uint32_t s0 = C[cell(t, 0)];
-      const uint32_t s1 = t + 1 < kBins ? C[cell(t + 1, 0)] : valid;
-      cnt = s1 - s0;
-      off[t] = base[t] - s0;
-    }
-    __syncthreads();  // the table is overwritten by the exchange below
-#pragma unroll
-    for (int j = 0; j < kItems; ++j)
-      if (first + j < valid) xk[r[j]] = k[j];
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kItems; ++q) {
-      const uint32_t p = q * kThreads + t;
-      if (p < valid) {
-        const K key = xk[p];
-        const uint32_t dst = off[digit_of<K>(key, a.shift, a.mask, false)] + p;
-        if (dst < m) emit_key<K, kExpand>(a, key, dst, xk, p, valid, s_vrec, s_vtile, kout_raw, vout);
-        else out_of_range = true;
-      }
-    }
-    __syncthreads();
-    if (t < kBins) base[t] += cnt;
-    __syncthreads();
+  const uint32_t rest = len - full * kTileKeys;
+  if (rest) {
+    const uint32_t tb = beg + full * kTileKeys;
+    ok &= rank_and_scatter<false, S, K, kVals, kExpand, kBits, kItems>(
+        kin + tb, kVals ? vin + tb : nullptr, rest, m, a, d31, sm, s_warp, s_vrec, s_vtile, kout_raw, vout);
   }
-  if (timed_out && t == 0) latch_error(a.err, TDGS_ERR_TIMEOUT, kSiteCopyWait);
-  if (out_of_range) latch_error(a.err, TDGS_ERR_CAPACITY, kSiteRadixRange);
+  if (!ok) latch_error(a.err, TDGS_ERR_CAPACITY, kSiteRadixRange);
 }
 
 // --------------------------------------------------------------- host side
-using PassFn = void (*)(const void*, const uint32_t*, void*, uint32_t*, PassArgs);
-
 struct Kernel {
   const void* fn;     // the __global__ function
   int bits, threads, items;
   size_t smem;
   int min_blocks;
 };
-
-template <typename K, bool kExpand>
-Kernel make_ct_kernel() {
-  return Kernel{reinterpret_cast<const void*>(&k_radix_pass_ct<K, kExpand>), 6, ct::kThreads, ct::kItems,
-                ct::smem_bytes<K>(), 2};
-}
 
 template <typename K, bool kVals, bool kExpand, int kBits, int kThreads, int kItems>
 Kernel make_kernel() {

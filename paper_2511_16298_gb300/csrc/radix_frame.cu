@@ -12,20 +12,23 @@ const radix::Kernel& depth_kernel(int digit_bits) {
   static const radix::Kernel k8 = make_kernel<uint32_t, true, false, 8, 256, 16>();
   return digit_bits == 11 ? k11 : k8;
 }
-const radix::Kernel& stream_kernel(bool wide, bool expand, int kernel) {
-  static const radix::Kernel k[8] = {
-      make_kernel<uint32_t, false, false, 8, 256, 16>(),
-      make_kernel<uint32_t, false, true, 8, 256, 16>(),
-      make_kernel<uint64_t, false, false, 8, 256, 16>(),
-      make_kernel<uint64_t, false, true, 8, 256, 16>(),
-      radix::make_ct_kernel<uint32_t, false>(),
-      radix::make_ct_kernel<uint32_t, true>(),
-      radix::make_ct_kernel<uint64_t, false>(),
-      radix::make_ct_kernel<uint64_t, true>(),
+// Tile passes: digit kernels of 6, 8 and 12 bits, narrow (32-bit) or wide
+// (64-bit) packed elements, plain or expanding.
+const radix::Kernel& stream_kernel(bool wide, bool expand, uint32_t bits) {
+  static const radix::Kernel k[12] = {
+      make_kernel<uint32_t, false, false, 6, 256, 16>(),  make_kernel<uint32_t, false, true, 6, 256, 16>(),
+      make_kernel<uint64_t, false, false, 6, 256, 16>(),  make_kernel<uint64_t, false, true, 6, 256, 16>(),
+      make_kernel<uint32_t, false, false, 8, 256, 16>(),  make_kernel<uint32_t, false, true, 8, 256, 16>(),
+      make_kernel<uint64_t, false, false, 8, 256, 16>(),  make_kernel<uint64_t, false, true, 8, 256, 16>(),
+      make_kernel<uint32_t, false, false, 12, 256, 16>(), make_kernel<uint32_t, false, true, 12, 256, 16>(),
+      make_kernel<uint64_t, false, false, 12, 256, 16>(), make_kernel<uint64_t, false, true, 12, 256, 16>(),
   };
-  return k[(kernel == 1 ? 4 : 0) + (wide ? 2 : 0) + (expand ? 1 : 0)];
+  const int w = bits <= 6 ? 0 : (bits <= 8 ? 1 : 2);
+  return k[w * 4 + (wide ? 2 : 0) + (expand ? 1 : 0)];
 }
 }  // namespace
+
+uint32_t stream_kernel_bits(uint32_t width) { return width <= 6 ? 6u : (width <= 8 ? 8u : 12u); }
 
 uint32_t depth_sort_grid(uint32_t n, int digit_bits, int ctas_per_sm) {
   return radix::grid_for(depth_kernel(digit_bits), n, ctas_per_sm);
@@ -47,11 +50,11 @@ cudaError_t launch_depth_pass(int digit_bits, uint32_t grid, uint32_t pass, cons
   return radix::launch(depth_kernel(digit_bits), grid, kin, vin, kout, vout, a, scratch, s);
 }
 
-uint32_t stream_grid(bool wide, bool expand, int kernel, uint32_t m, int ctas_per_sm) {
-  return radix::grid_for(stream_kernel(wide, expand, kernel), m, ctas_per_sm);
+uint32_t stream_grid(bool wide, bool expand, uint32_t bits, uint32_t m, int ctas_per_sm) {
+  return radix::grid_for(stream_kernel(wide, expand, bits), m, ctas_per_sm);
 }
-size_t stream_scratch_words(bool wide, bool expand, int kernel, uint32_t grid) {
-  return radix::scratch_words(stream_kernel(wide, expand, kernel), grid);
+size_t stream_scratch_words(bool wide, bool expand, uint32_t bits, uint32_t grid) {
+  return radix::scratch_words(stream_kernel(wide, expand, bits), grid);
 }
 
 cudaError_t launch_stream_pass(const StreamPass& sp, uint32_t* scratch, uint32_t* bar,
@@ -68,12 +71,15 @@ cudaError_t launch_stream_pass(const StreamPass& sp, uint32_t* scratch, uint32_t
     a.vrec_begin = sp.views->rec_begin;
     a.vtile_begin = sp.views->tile_begin;
     a.nv = sp.views->nv;
+    a.pbeg = sp.views->pbeg;
   }
   a.rmin = sp.rmin;
   a.rmax = sp.rmax;
+  a.ranges = sp.ranges;
+  a.t_all = sp.t_all;
   a.bar = bar;
   a.err = err;
-  return radix::launch(stream_kernel(sp.wide, sp.expand, sp.kernel), sp.grid, sp.kin, nullptr, sp.kout, sp.vout,
+  return radix::launch(stream_kernel(sp.wide, sp.expand, sp.bits), sp.grid, sp.kin, nullptr, sp.kout, sp.vout,
                        a, scratch, s);
 }
 

@@ -11,12 +11,12 @@ using radix::make_kernel;
 const radix::Kernel& variant_kernel(int i) {
   static const radix::Kernel kV[] = {
       make_kernel<uint64_t, true, false, 8, 256, 16>(),
-      make_kernel<uint64_t, true, false, 8, 512, 16>(),
+      make_kernel<uint64_t, true, false, 9, 256, 16>(),
       make_kernel<uint64_t, true, false, 10, 256, 16>(),
-      make_kernel<uint64_t, true, false, 10, 512, 16>(),
       make_kernel<uint64_t, true, false, 11, 256, 16>(),
+      make_kernel<uint64_t, true, false, 8, 512, 16>(),
+      make_kernel<uint64_t, true, false, 9, 512, 16>(),
       make_kernel<uint64_t, true, false, 11, 512, 16>(),
-      make_kernel<uint64_t, true, false, 11, 256, 8>(),
   };
   return kV[i];
 }
@@ -31,8 +31,9 @@ PassVariant pass_variant(int i) {
 
 int default_pass_variant(uint32_t digit_bits) {
   if (digit_bits <= 8) return 0;
+  if (digit_bits <= 9) return 1;
   if (digit_bits <= 10) return 2;
-  return 4;
+  return 3;
 }
 
 SortPlan make_sort_plan(uint32_t m, uint32_t tile_bits, uint32_t flags, const Tuning& tu) {
@@ -42,7 +43,10 @@ SortPlan make_sort_plan(uint32_t m, uint32_t tile_bits, uint32_t flags, const Tu
   p.key_bits = 32 + tile_bits - (p.drop31 ? 1 : 0);
   p.bad_mask = tile_bits >= 32 ? 0ull : ~((1ull << (32 + tile_bits)) - 1);
   if (p.drop31) p.bad_mask |= 1ull << 31;
-  uint32_t max_bits = 11;
+  // 9-bit digits by default: wider digits save a pass but scatter shorter
+  // runs per digit (a 4096-key tile writes ~8 keys per digit at 9 bits, ~2
+  // at 11), and the partial-sector writes cost more than the pass
+  uint32_t max_bits = 9;
   const bool forced = variant_override >= 0 && variant_override < kNumVariants;
   if (forced) {
     max_bits = static_cast<uint32_t>(variant_kernel(variant_override).bits);

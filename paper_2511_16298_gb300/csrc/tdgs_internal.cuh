@@ -87,8 +87,7 @@ __device__ __forceinline__ TileRect tile_rect(const float4 rec, const FrameGeom&
 // which site latched it (kSite* below), for the host's error message.
 enum ErrorSite : uint32_t {
   kSiteNone = 0, kSiteCount, kSiteScan, kSiteScanTimeout, kSiteDuplicate, kSiteRanges,
-  kSiteRadixKeys, kSiteRadixRange, kSiteRadixCapacity, kSiteBarrier, kSiteViewsCount, kSiteViewsDup,
-  kSiteCopyWait
+  kSiteRadixKeys, kSiteRadixRange, kSiteRadixCapacity, kSiteBarrier, kSiteViewsCount, kSiteViewsDup
 };
 __device__ __forceinline__ void latch_error(uint32_t* err, uint32_t code, uint32_t site = kSiteNone) {
   if (atomicCAS(err, 0u, code) == 0u) err[1] = site;
@@ -186,14 +185,17 @@ size_t depth_sort_scratch_words(int digit_bits, uint32_t grid);
 cudaError_t launch_depth_pass(int digit_bits, uint32_t grid, uint32_t pass, const uint32_t* kin,
                               const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t n,
                               uint32_t* scratch, uint32_t* bar, uint32_t* err, cudaStream_t s);
-inline uint32_t depth_passes(int digit_bits) { return digit_bits == 11 ? 3u : 4u; }
+inline int depth_bits(int tuned) { return tuned == 11 ? 11 : 8; }
+inline uint32_t depth_passes(int tuned) { return depth_bits(tuned) == 8 ? 4u : 3u; }
 // Stable pass over the packed stream on tile bits [shift, shift + width).
 // expand: write the final (local tile << 32 | depth bits) keys and local
-// indices, and record each global tile's first/last sorted position.
+// indices; with rmin/rmax, record each global tile's first/last sorted
+// position; with ranges (a single pass over the whole tile id), write the
+// view-local tile ranges from the digit totals.
 // m_dev (optional): device copy of the element count, capped at m.
 struct StreamPass {
   bool wide, expand;
-  int kernel;              // Tuning::tile_kernel
+  uint32_t bits;           // compiled digit width (stream_kernel_bits)
   uint32_t grid;
   const void* kin;
   void* kout;
@@ -206,9 +208,13 @@ struct StreamPass {
   const ViewTable* views;  // expand only
   uint32_t* rmin;
   uint32_t* rmax;
+  uint2* ranges;
+  uint32_t t_all;
 };
-uint32_t stream_grid(bool wide, bool expand, int kernel, uint32_t m, int ctas_per_sm);
-size_t stream_scratch_words(bool wide, bool expand, int kernel, uint32_t grid);
+// Compiled digit width (6, 8 or 12) that holds a `width`-bit digit.
+uint32_t stream_kernel_bits(uint32_t width);
+uint32_t stream_grid(bool wide, bool expand, uint32_t bits, uint32_t m, int ctas_per_sm);
+size_t stream_scratch_words(bool wide, bool expand, uint32_t bits, uint32_t grid);
 cudaError_t launch_stream_pass(const StreamPass& sp, uint32_t* scratch, uint32_t* bar,
                                uint32_t* err, cudaStream_t s);
 
@@ -216,10 +222,9 @@ cudaError_t launch_stream_pass(const StreamPass& sp, uint32_t* scratch, uint32_t
 // Knobs picked by the autotuner (0 / -1 = built-in choice).
 struct Tuning {
   int sort_variant = -1;     // tdgs_sort_pairs pass kernel
-  int tile_digit_bits = 0;   // frame tile passes: digit width 4..8 (0 = 8)
-  int tile_kernel = 0;       // frame tile passes: 0 ballot ranking, 1 counter table (<= 6-bit digits)
+  int tile_digit_bits = 0;   // frame tile passes: widest digit, 4..12 (0 = 8)
   int ctas_per_sm = 0;       // persistent radix grids: CTAs per SM (0 = kernel default)
-  int depth_digit_bits = 0;  // depth sort: 11 (3 passes, match.any) or 8 (4 passes, ballots); 0 = 8
+  int depth_digit_bits = 0;  // depth sort: 11 (3 passes) or 8 (4 passes); 0 = 8
 };
 
 // ----------------------------------------------------------- radix sort

@@ -25,7 +25,7 @@ CUDA_ERROR = 4
 TIMEOUT = 5
 CAPACITY = 6
 SORT_DEPTH_POSITIVE = 1
-TUNE_SORT_VARIANT, TUNE_TILE_DIGIT_BITS, TUNE_TILE_KERNEL, TUNE_CTAS_PER_SM, TUNE_DEPTH_DIGIT_BITS = 0, 1, 2, 3, 4
+TUNE_SORT_VARIANT, TUNE_TILE_DIGIT_BITS, TUNE_CTAS_PER_SM, TUNE_DEPTH_DIGIT_BITS = 0, 1, 3, 4
 
 _lock = threading.Lock()
 _lib = None
@@ -235,8 +235,7 @@ class Context:
     def apply_tuning(self, knobs: dict):
         for k, v in knobs.items():
             self.set_tuning({"sort_variant": TUNE_SORT_VARIANT, "tile_digit_bits": TUNE_TILE_DIGIT_BITS,
-                             "tile_kernel": TUNE_TILE_KERNEL, "ctas_per_sm": TUNE_CTAS_PER_SM,
-                             "depth_digit_bits": TUNE_DEPTH_DIGIT_BITS}[k], v)
+                             "ctas_per_sm": TUNE_CTAS_PER_SM, "depth_digit_bits": TUNE_DEPTH_DIGIT_BITS}[k], v)
 
     @property
     def launches(self) -> int:

@@ -157,6 +157,23 @@ def test_sort_pairs_variants(ctx, oracle, variant, m, tile_bits, ties):
     assert np.array_equal(u32(sv), rv)
 
 
+@pytest.mark.parametrize("m", [5, 70_001])
+def test_sort_pairs_keys_8_byte_aligned(ctx, oracle, m):
+    """Keys that start 8 bytes past a 16-byte boundary (allowed by the ABI)
+    take the scalar histogram path of the first pass."""
+    k, v = _random_pairs(m, 99 + m, 44, True)
+    _, rk, rv = oracle.sort_pairs(k, v)
+    kt = torch.zeros(m + 1, dtype=torch.int64, device=DEV)
+    vt = torch.zeros(m + 1, dtype=torch.int32, device=DEV)
+    kt[1:] = torch.from_numpy(k.view(np.int64)).to(DEV)
+    vt[1:] = torch.from_numpy(v.view(np.int32)).to(DEV)
+    assert kt[1:].data_ptr() % 16 == 8
+    sk, sv = ctx.sort_pairs(kt[1:], vt[1:], 12, 0)
+    ctx.sync()
+    assert np.array_equal(u64(sk), rk)
+    assert np.array_equal(u32(sv), rv)
+
+
 def test_sort_pairs_depth_flag_violation(ctx):
     k = np.array([1, 2, 0x80000000], dtype=np.uint64)
     v = np.arange(3, dtype=np.uint32)

@@ -21,10 +21,11 @@ def ctx():
 
 
 @pytest.mark.parametrize("knobs", [
-    {"tile_kernel": 1, "tile_digit_bits": 6},
-    {"tile_kernel": 1, "tile_digit_bits": 4, "ctas_per_sm": 1},
-    {"tile_kernel": 0, "tile_digit_bits": 5, "ctas_per_sm": 3},
-    {"tile_kernel": 0, "tile_digit_bits": 8, "ctas_per_sm": 1, "depth_digit_bits": 8},
+    {"tile_digit_bits": 6},
+    {"tile_digit_bits": 4, "ctas_per_sm": 1},
+    {"tile_digit_bits": 5, "ctas_per_sm": 3},
+    {"tile_digit_bits": 8, "ctas_per_sm": 1, "depth_digit_bits": 8},
+    {"tile_digit_bits": 11, "ctas_per_sm": 2, "depth_digit_bits": 11},
 ])
 def test_frame_knobs_exact(ctx, oracle, knobs):
     frames = [synth.frame_small(0), synth.frame_large(2, n=60_000, width=1920, height=1080),
@@ -45,15 +46,17 @@ def test_frame_knobs_exact(ctx, oracle, knobs):
             ref = oracle.sort_frame(f.gaussians, f.width, f.height)
             assert np.array_equal(k.cpu().numpy().view(np.uint64), ref["keys"])
     finally:
-        ctx.apply_tuning({"tile_kernel": 0, "tile_digit_bits": 0, "ctas_per_sm": 0, "depth_digit_bits": 0})
+        ctx.apply_tuning({"tile_digit_bits": 0, "ctas_per_sm": 0, "depth_digit_bits": 0})
 
 
 def test_tuning_rejects_bad_values(ctx):
     with pytest.raises(T.TdgsError):
-        ctx.set_tuning(T.TUNE_TILE_DIGIT_BITS, 9)
+        ctx.set_tuning(T.TUNE_TILE_DIGIT_BITS, 13)
+    with pytest.raises(T.TdgsError):
+        ctx.set_tuning(2, 1)  # no such knob
     with pytest.raises(T.TdgsError):
         ctx.set_tuning(99, 1)
-    assert ctx.get_tuning(T.TUNE_TILE_KERNEL) == 0
+    assert ctx.get_tuning(T.TUNE_TILE_DIGIT_BITS) == 0
 
 
 def test_autotuner_table(ctx, tmp_path):
