@@ -111,11 +111,13 @@ uint32_t tdgs_tile_bits(tdgs_frame f);
 
 /* Tuning of the sort's digit passes (used by the autotuner; the paper has
  * no counterpart).  Variant i is a compiled pass kernel with
- * 2^bits digit bins, `threads` threads per block and `items` keys per
- * thread.  tdgs_context_set_sort_variant(ctx, -1) restores the built-in
- * choice; an index out of range returns TDGS_ERR_INVALID_ARGUMENT. */
+ * 2^bits digit bins, `threads` threads per block, `items` keys per thread
+ * and registers budgeted for `blocks_per_sm` resident blocks per SM.
+ * tdgs_context_set_sort_variant(ctx, -1) restores the built-in choice; an
+ * index out of range returns TDGS_ERR_INVALID_ARGUMENT.  Any output
+ * pointer may be NULL. */
 int tdgs_sort_variant_count(void);
-tdgs_status tdgs_sort_variant_info(int i, int* bits, int* threads, int* items);
+tdgs_status tdgs_sort_variant_info(int i, int* bits, int* threads, int* items, int* blocks_per_sm);
 tdgs_status tdgs_context_set_sort_variant(tdgs_context* ctx, int variant);
 
 /* Further tuning knobs of a context (value 0, or -1 for the sort variant,

@@ -318,12 +318,13 @@ uint32_t tdgs_tile_bits(tdgs_frame f) {
 
 int tdgs_sort_variant_count(void) { return num_pass_variants(); }
 
-tdgs_status tdgs_sort_variant_info(int i, int* bits, int* threads, int* items) {
+tdgs_status tdgs_sort_variant_info(int i, int* bits, int* threads, int* items, int* blocks_per_sm) {
   if (i < 0 || i >= num_pass_variants()) return TDGS_ERR_INVALID_ARGUMENT;
   const PassVariant v = pass_variant(i);
   if (bits) *bits = v.bits;
   if (threads) *threads = v.threads;
   if (items) *items = v.items;
+  if (blocks_per_sm) *blocks_per_sm = v.blocks_per_sm;
   return TDGS_OK;
 }
 

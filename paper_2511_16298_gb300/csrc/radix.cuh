@@ -171,7 +171,9 @@ struct PassArgs {
   const uint64_t* m_dev;       // optional device element count, capped at m
 };
 
-template <typename K, bool kVals, bool kExpand, int kBits, int kThreads, int kItems>
+// kOcc: CTAs per SM the register budget is sized for (launch bounds); 0
+// picks 2 for 64-bit keys, wide digits and expanding passes, 3 otherwise.
+template <typename K, bool kVals, bool kExpand, int kBits, int kThreads, int kItems, int kOcc>
 struct PassShape {
   static constexpr int kBins = 1 << kBits;
   static constexpr int kWarps = kThreads / 32;
@@ -179,12 +181,17 @@ struct PassShape {
   static constexpr int kBpt = (kBins + kThreads - 1) / kThreads;
   static constexpr int kCols = kBins / 2;  // counter words: two 16-bit digits each
   static constexpr int kCpt = (kCols + kThreads - 1) / kThreads;
+  // shared memory, no aliasing: per-warp counters | key exchange |
+  // gathered index and depth (expanding pass) | value exchange |
+  // base, lstart, off per digit
   static constexpr size_t kWhBytes = static_cast<size_t>(kWarps) * kBins * 2;
-  static constexpr size_t kXBytes = static_cast<size_t>(kTileKeys) * sizeof(K);
-  static constexpr size_t kUBytes = kWhBytes > kXBytes ? kWhBytes : kXBytes;
-  static constexpr size_t kSmem = kUBytes + static_cast<size_t>(kBins) * 8;
-  static constexpr int kMinBlocks = kThreads >= 512 ? 1 : ((sizeof(K) == 4 && !kVals && kBits <= 8) ? 3 : 2);
-  static_assert(kBits >= 1 && kBits <= 12, "digits of 1..12 bits");
+  static constexpr size_t kXkBytes = static_cast<size_t>(kTileKeys) * sizeof(K);
+  static constexpr size_t kXgBytes = kExpand ? static_cast<size_t>(kTileKeys) * 8 : 0;
+  static constexpr size_t kXvBytes = kVals ? static_cast<size_t>(kTileKeys) * 4 : 0;
+  static constexpr size_t kSmem = kWhBytes + kXkBytes + kXgBytes + kXvBytes + static_cast<size_t>(kBins) * 12;
+  static constexpr int kMinBlocks =
+      kOcc > 0 ? kOcc : (kThreads >= 512 ? 1 : ((kExpand || kBits > 10 || sizeof(K) == 8) ? 2 : 3));
+  static_assert(kBits >= 6 && kBits <= 12, "digits of 6..12 bits");
   static_assert(kTileKeys <= 32768, "per-warp counters and their prefixes are 16-bit");
   static_assert(kWhBytes % 16 == 0, "counters are cleared with 16-byte stores");
 };
@@ -223,7 +230,7 @@ __device__ __forceinline__ void count_key(K k, const PassArgs& a, bool d31, uint
 // between two grid barriers, then base[b] = first output position of this
 // chunk's keys with digit b.  hist: kBins words of shared scratch.  With
 // a.ranges set, the tile ranges are written from the digit totals.
-template <typename K, int kBins, int kThreads>
+template <typename K, int kBins, int kThreads, uint32_t kU = 8>
 __device__ __forceinline__ void chunk_bases(const K* __restrict__ kin, const PassArgs& a,
                                             uint32_t beg, uint32_t end, bool d31, uint32_t* base,
                                             uint32_t* hist, uint32_t* s_warp, const uint32_t* s_vtile) {
@@ -240,8 +247,7 @@ __device__ __forceinline__ void chunk_bases(const K* __restrict__ kin, const Pas
     const uint32_t len = end - beg;
     uint32_t done = 0;
     if ((reinterpret_cast<uintptr_t>(kc) & 15u) == 0) {
-      constexpr uint32_t kPer = 16 / sizeof(K);  // keys per 16-byte vector
-      constexpr uint32_t kU = 4;                 // vectors in flight per thread
+      constexpr uint32_t kPer = 16 / sizeof(K);  // keys per 16-byte vector; kU vectors in flight per thread
       const uint32_t nvec = len / kPer;
       for (uint32_t q0 = t; q0 < nvec; q0 += kThreads * kU) {
         uint4 w[kU];
@@ -327,21 +333,19 @@ __device__ __forceinline__ void chunk_bases(const K* __restrict__ kin, const Pas
 }
 
 // Output of one key at its sorted position dst.  Plain passes store the
-// key; the expanding pass stores (local tile << 32 | depth bits) and the
-// view-local Gaussian index, and (multi-pass tile sorts) records the
+// key; the expanding pass stores (local tile << 32 | depth bits dep) and
+// the view-local Gaussian index (gi is the global record index, gathered
+// when the tile was loaded), and (multi-pass tile sorts) records the
 // first/last position of each global tile run seen in this tile's exchange
 // buffer xk.
 template <typename K, bool kExpand>
-__device__ __forceinline__ void emit_key(const PassArgs& a, K key, uint32_t dst, const K* xk,
-                                         uint32_t p, uint32_t valid, const uint32_t* s_vrec,
+__device__ __forceinline__ void emit_key(const PassArgs& a, K key, uint32_t gi, uint32_t dep, uint32_t dst,
+                                         const K* xk, uint32_t p, uint32_t valid, const uint32_t* s_vrec,
                                          const uint32_t* s_vtile, void* kout_raw, uint32_t* vout) {
   if constexpr (kExpand) {
-    const uint32_t rk = static_cast<uint32_t>(key & ((static_cast<K>(1) << a.rbits) - 1));
     const uint32_t gt = static_cast<uint32_t>(key >> a.rbits);
-    const uint32_t gi = __ldg(a.sorder + rk);
     const uint32_t v = a.nv == 1 ? 0u : find_view(s_vrec, a.nv, gi);
-    static_cast<uint64_t*>(kout_raw)[dst] =
-        (static_cast<uint64_t>(gt - s_vtile[v]) << 32) | __ldg(a.sdepth + rk);
+    static_cast<uint64_t*>(kout_raw)[dst] = (static_cast<uint64_t>(gt - s_vtile[v]) << 32) | dep;
     vout[dst] = gi - s_vrec[v];
     if (a.rmin) {
       if (p == 0 || static_cast<uint32_t>(xk[p - 1] >> a.rbits) != gt) atomicMin(a.rmin + gt, dst);
@@ -355,16 +359,84 @@ __device__ __forceinline__ void emit_key(const PassArgs& a, K key, uint32_t dst,
 // Shared-memory layout of one pass CTA.
 template <typename K>
 struct Smem {
-  uint16_t* wh;     // [kWarps][kBins] per-warp digit counters while ranking
-  K* xk;            // key exchange afterwards (aliases wh)
-  uint32_t* xv;     // value exchange afterwards (aliases wh)
+  uint16_t* wh;     // [kWarps][kBins] per-warp digit counters, then exclusive prefixes over warps
+  K* xk;            // key exchange
+  uint32_t* xg;     // expanding pass: gathered record index
+  uint32_t* xd;     // expanding pass: gathered depth bits
+  uint32_t* xv;     // value exchange
   uint32_t* base;   // [kBins] running output base of this chunk per digit
-  uint32_t* lstart; // [kBins] tile-local digit start, then base - start
+  uint32_t* lstart; // [kBins] tile count per digit, then tile-local digit start
+  uint32_t* off;    // [kBins] base - tile-local start: output position = off[digit] + p
 };
+
+// Tile-local digit starts from the per-digit tile counts in lstart (one
+// warp when the digits fit 16 per lane, else the whole block), and per
+// digit: off = base - start, base += count.
+template <typename S, typename K>
+__device__ __forceinline__ void digit_starts(const Smem<K>& sm, uint32_t* s_warp) {
+  constexpr int kBins = S::kBins;
+  constexpr int kWarps = S::kWarps;
+  constexpr int kThreads = kWarps * 32;
+  const uint32_t t = threadIdx.x;
+  if constexpr (kBins <= 512) {
+    constexpr int kPer = kBins / 32;
+    if (t < 32) {
+      uint32_t c[kPer];
+      uint32_t sum = 0;
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        c[i] = sm.lstart[t * kPer + i];
+        sum += c[i];
+      }
+      uint32_t x = sum;
+#pragma unroll
+      for (int dd = 1; dd < 32; dd <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, x, dd);
+        if (t >= static_cast<uint32_t>(dd)) x += o;
+      }
+      uint32_t run = x - sum;
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const uint32_t b = t * kPer + i;
+        const uint32_t bs = sm.base[b];
+        sm.lstart[b] = run;
+        sm.off[b] = bs - run;
+        sm.base[b] = bs + c[i];
+        run += c[i];
+      }
+    }
+  } else {
+    constexpr int kBpt = S::kBpt;
+    uint32_t c[kBpt];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < kBpt; ++i) {
+      const uint32_t b = t * kBpt + i;
+      c[i] = b < kBins ? sm.lstart[b] : 0u;
+      sum += c[i];
+    }
+    uint32_t run = block_excl_scan<kWarps>(sum, s_warp);
+#pragma unroll
+    for (int i = 0; i < kBpt; ++i) {
+      const uint32_t b = t * kBpt + i;
+      if (b < kBins) {
+        const uint32_t bs = sm.base[b];
+        sm.lstart[b] = run;
+        sm.off[b] = bs - run;
+        sm.base[b] = bs + c[i];
+      }
+      run += c[i];
+    }
+    (void)kThreads;
+  }
+}
 
 // Phase 3 for one tile of `valid` keys starting at kt (kFull: valid ==
 // kTileKeys, no bounds checks).  Returns false if a destination fell
-// outside [0, m).
+// outside [0, m).  Block barriers per tile: after ranking, after the
+// prefix over warps, after the digit starts, after the exchange (and one
+// more for values).  Each warp's counter row is zero on entry and is
+// zeroed again by its own warp once read.
 template <bool kFull, typename S, typename K, bool kVals, bool kExpand, int kBits, int kItems>
 __device__ __forceinline__ bool rank_and_scatter(const K* __restrict__ kt, const uint32_t* __restrict__ vt,
                                                  uint32_t valid, uint32_t m, const PassArgs& a, bool d31,
@@ -374,68 +446,72 @@ __device__ __forceinline__ bool rank_and_scatter(const K* __restrict__ kt, const
   constexpr int kBins = S::kBins;
   constexpr int kWarps = S::kWarps;
   constexpr int kThreads = kWarps * 32;
-  constexpr int kBpt = S::kBpt;
   constexpr int kCols = S::kCols;
   constexpr int kCpt = S::kCpt;
   const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
   const uint32_t wbase = warp * 32 * kItems;
   bool ok = true;
 
-  // clear the per-warp counters (16-byte stores)
-  {
-    uint4* z = reinterpret_cast<uint4*>(sm.wh);
-    constexpr uint32_t kVec = static_cast<uint32_t>(S::kWhBytes / 16);
-    for (uint32_t i = t; i < kVec; i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
-  }
   K k[kItems];
-  uint32_t v[kVals ? kItems : 1];
   uint32_t d[kItems];
+  // expanding pass: the depth bits and record index of each element's
+  // depth rank are gathered now, so their latency hides behind the ranking
+  uint32_t gi[kExpand ? kItems : 1], dep[kExpand ? kItems : 1];
 #pragma unroll
   for (int j = 0; j < kItems; ++j) {
     const uint32_t idx = wbase + j * 32 + lane;
-    if (kFull || idx < valid) {
-      k[j] = __ldcs(kt + idx);
-      if constexpr (kVals) v[j] = __ldcs(vt + idx);
-    } else {
-      k[j] = K(0);
-      if constexpr (kVals) v[j] = 0u;
-    }
+    k[j] = (kFull || idx < valid) ? __ldcs(kt + idx) : K(0);
     d[j] = digit_of<K>(k[j], a.shift, a.mask, d31);
+    if constexpr (kExpand) {
+      gi[j] = dep[j] = 0u;
+      if (kFull || idx < valid) {
+        const uint32_t rk = static_cast<uint32_t>(k[j] & ((static_cast<K>(1) << a.rbits) - 1));
+        gi[j] = __ldg(a.sorder + rk);
+        dep[j] = __ldg(a.sdepth + rk);
+      }
+    }
   }
-  __syncthreads();
-  // rank within the warp: every lane of an equal-digit group reads the
-  // warp's counter, the group's highest lane writes it back bumped
+  // rank within the warp, kGroup items at a time: the equal-digit lane
+  // sets of the group first (independent ballot chains), then every lane
+  // of a set reads the warp's counter and the set's highest lane writes it
+  // back bumped
+  constexpr int kGroup = sizeof(K) == 8 ? 4 : 8;
+  static_assert(kItems % kGroup == 0, "items per thread: a multiple of the ranking group");
   uint16_t* my_wh = sm.wh + warp * kBins;
   uint32_t r[kItems];
   const uint32_t lt = lanemask_lt();
 #pragma unroll
-  for (int j = 0; j < kItems; ++j) {
-    uint32_t peers = equal_digit_lanes<kBits>(d[j]);
-    bool live = true;
-    if constexpr (!kFull) {
-      const uint32_t first = wbase + j * 32;
-      const uint32_t nlive = valid > first ? min(valid - first, 32u) : 0u;
-      live = lane < nlive;
-      peers &= nlive >= 32 ? 0xffffffffu : ((1u << nlive) - 1u);
+  for (int j0 = 0; j0 < kItems; j0 += kGroup) {
+#pragma unroll
+    for (int j = j0; j < j0 + kGroup; ++j) {
+      r[j] = equal_digit_lanes<kBits>(d[j]);
+      if constexpr (!kFull) {
+        const uint32_t first = wbase + j * 32;
+        const uint32_t nlive = valid > first ? min(valid - first, 32u) : 0u;
+        r[j] &= nlive >= 32 ? 0xffffffffu : ((1u << nlive) - 1u);
+      }
     }
-    const uint32_t before = my_wh[d[j]];
-    __syncwarp();
-    const uint32_t cnt = __popc(peers);
-    const uint32_t below = __popc(peers & lt);
-    if (live && below + 1 == cnt) my_wh[d[j]] = static_cast<uint16_t>(before + cnt);
-    __syncwarp();
-    r[j] = before + below;
+#pragma unroll
+    for (int j = j0; j < j0 + kGroup; ++j) {
+      const uint32_t peers = r[j];
+      const bool live = kFull || wbase + j * 32 + lane < valid;
+      const uint32_t before = my_wh[d[j]];
+      __syncwarp();
+      const uint32_t cnt = __popc(peers);
+      const uint32_t below = __popc(peers & lt);
+      if (live && below + 1 == cnt) my_wh[d[j]] = static_cast<uint16_t>(before + cnt);
+      __syncwarp();
+      r[j] = before + below;
+    }
   }
   __syncthreads();
   // exclusive prefix over warps per digit (two digits per 32-bit word);
   // tile count per digit into lstart
-  uint32_t cnt2[kCpt];
   {
     uint32_t* wh32 = reinterpret_cast<uint32_t*>(sm.wh);
 #pragma unroll
     for (int i = 0; i < kCpt; ++i) {
       const uint32_t c = t + i * kThreads;
-      cnt2[i] = 0;
       if (c < static_cast<uint32_t>(kCols)) {
         uint32_t run = 0;
 #pragma unroll
@@ -444,48 +520,41 @@ __device__ __forceinline__ bool rank_and_scatter(const K* __restrict__ kt, const
           wh32[w * kCols + c] = run;
           run += x;  // halves stay below 2^16: no carry between digits
         }
-        cnt2[i] = run;
         sm.lstart[2 * c] = run & 0xffffu;
         sm.lstart[2 * c + 1] = run >> 16;
       }
     }
   }
   __syncthreads();
-  {
-    uint32_t seg[kBpt];
-    uint32_t sum = 0;
-#pragma unroll
-    for (int i = 0; i < kBpt; ++i) {
-      const uint32_t b = t * kBpt + i;
-      seg[i] = b < kBins ? sm.lstart[b] : 0;
-      sum += seg[i];
-    }
-    uint32_t run = block_excl_scan<kWarps>(sum, s_warp);
-#pragma unroll
-    for (int i = 0; i < kBpt; ++i) {
-      const uint32_t b = t * kBpt + i;
-      if (b < kBins) sm.lstart[b] = run;
-      run += seg[i];
-    }
-  }
+  digit_starts<S, K>(sm, s_warp);
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < kItems; ++j) r[j] += sm.lstart[d[j]] + my_wh[d[j]];
-  __syncthreads();  // wh is overwritten by the exchange below; lstart becomes the offset
-#pragma unroll
-  for (int i = 0; i < kCpt; ++i) {
-    const uint32_t c = t + i * kThreads;
-    if (c < static_cast<uint32_t>(kCols)) {
-      const uint32_t b0 = 2 * c, b1 = 2 * c + 1;
-      sm.lstart[b0] = sm.base[b0] - sm.lstart[b0];
-      sm.lstart[b1] = sm.base[b1] - sm.lstart[b1];
-      sm.base[b0] += cnt2[i] & 0xffffu;
-      sm.base[b1] += cnt2[i] >> 16;
-    }
+  __syncwarp();
+  {  // this warp's counter row is read: zero it for the next tile
+    uint4* z = reinterpret_cast<uint4*>(my_wh);
+    for (uint32_t i = lane; i < static_cast<uint32_t>(kBins) / 8; i += 32) z[i] = make_uint4(0, 0, 0, 0);
   }
 #pragma unroll
-  for (int j = 0; j < kItems; ++j)
-    if (kFull || wbase + j * 32 + lane < valid) sm.xk[r[j]] = k[j];
+  for (int j = 0; j < kItems; ++j) {
+    if (kFull || wbase + j * 32 + lane < valid) {
+      sm.xk[r[j]] = k[j];
+      if constexpr (kExpand) {
+        sm.xg[r[j]] = gi[j];
+        sm.xd[r[j]] = dep[j];
+      }
+    }
+  }
+  // values are fetched only now (fewer registers live while ranking);
+  // the key scatter below hides their latency
+  uint32_t v[kVals ? kItems : 1];
+  if constexpr (kVals) {
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+      const uint32_t idx = wbase + j * 32 + lane;
+      v[j] = (kFull || idx < valid) ? __ldcs(vt + idx) : 0u;
+    }
+  }
   __syncthreads();
   // Scatter in digit order.  A destination outside [0, m) can only come
   // from a timed-out barrier or keys changed underneath the sort: it is
@@ -497,16 +566,18 @@ __device__ __forceinline__ bool rank_and_scatter(const K* __restrict__ kt, const
     dst[i] = 0xffffffffu;
     if (kFull || p < valid) {
       const K key = sm.xk[p];
-      dst[i] = sm.lstart[digit_of<K>(key, a.shift, a.mask, d31)] + p;
+      dst[i] = sm.off[digit_of<K>(key, a.shift, a.mask, d31)] + p;
       if (dst[i] < m) {
-        emit_key<K, kExpand>(a, key, dst[i], sm.xk, p, valid, s_vrec, s_vtile, kout_raw, vout);
+        if constexpr (kExpand)
+          emit_key<K, true>(a, key, sm.xg[p], sm.xd[p], dst[i], sm.xk, p, valid, s_vrec, s_vtile, kout_raw, vout);
+        else
+          emit_key<K, false>(a, key, 0u, 0u, dst[i], sm.xk, p, valid, s_vrec, s_vtile, kout_raw, vout);
       } else {
         ok = false;
       }
     }
   }
   if constexpr (kVals) {
-    __syncthreads();
 #pragma unroll
     for (int j = 0; j < kItems; ++j)
       if (kFull || wbase + j * 32 + lane < valid) sm.xv[r[j]] = v[j];
@@ -517,23 +588,32 @@ __device__ __forceinline__ bool rank_and_scatter(const K* __restrict__ kt, const
       if ((kFull || p < valid) && dst[i] < m) vout[dst[i]] = sm.xv[p];
     }
   }
-  __syncthreads();  // exchange buffers and offsets are reused by the next tile
   return ok;
 }
 
-template <typename K, bool kVals, bool kExpand, int kBits, int kThreads, int kItems>
-__global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits, kThreads, kItems>::kMinBlocks))
+template <typename K, bool kVals, bool kExpand, int kBits, int kThreads, int kItems, int kOcc>
+__global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits, kThreads, kItems, kOcc>::kMinBlocks))
     k_radix_pass(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
                  void* __restrict__ kout_raw, uint32_t* __restrict__ vout, PassArgs a) {
-  using S = PassShape<K, kVals, kExpand, kBits, kThreads, kItems>;
+  using S = PassShape<K, kVals, kExpand, kBits, kThreads, kItems, kOcc>;
   constexpr uint32_t kTileKeys = S::kTileKeys;
   extern __shared__ __align__(16) unsigned char smem[];
   Smem<K> sm;
-  sm.wh = reinterpret_cast<uint16_t*>(smem);
-  sm.xk = reinterpret_cast<K*>(smem);
-  sm.xv = reinterpret_cast<uint32_t*>(smem);
-  sm.base = reinterpret_cast<uint32_t*>(smem + S::kUBytes);
-  sm.lstart = sm.base + S::kBins;
+  {
+    unsigned char* q = smem;
+    sm.wh = reinterpret_cast<uint16_t*>(q);
+    q += S::kWhBytes;
+    sm.xk = reinterpret_cast<K*>(q);
+    q += S::kXkBytes;
+    sm.xg = reinterpret_cast<uint32_t*>(q);
+    sm.xd = sm.xg + (kExpand ? kTileKeys : 0);
+    q += S::kXgBytes;
+    sm.xv = reinterpret_cast<uint32_t*>(q);
+    q += S::kXvBytes;
+    sm.base = reinterpret_cast<uint32_t*>(q);
+    sm.lstart = sm.base + S::kBins;
+    sm.off = sm.lstart + S::kBins;
+  }
   __shared__ uint32_t s_warp[S::kWarps];
   __shared__ uint32_t s_vrec[kExpand ? kMaxViews + 1 : 1];
   __shared__ uint32_t s_vtile[kExpand ? kMaxViews + 1 : 1];
@@ -548,6 +628,11 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
       s_vtile[v] = a.vtile_begin[v];
     }
   }
+  {
+    uint4* z = reinterpret_cast<uint4*>(sm.wh);
+    for (uint32_t i = t; i < S::kWhBytes / 16; i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
+  }
+  // (chunk_bases starts and ends with a block barrier)
   chunk_bases<K, S::kBins, kThreads>(kin, a, beg, end, d31, sm.base, sm.lstart, s_warp, s_vtile);
 
   // ---- phase 3: stable rank + scatter, tile by tile
@@ -576,10 +661,10 @@ struct Kernel {
   int min_blocks;
 };
 
-template <typename K, bool kVals, bool kExpand, int kBits, int kThreads, int kItems>
+template <typename K, bool kVals, bool kExpand, int kBits, int kThreads, int kItems, int kOcc = 0>
 Kernel make_kernel() {
-  using S = PassShape<K, kVals, kExpand, kBits, kThreads, kItems>;
-  return Kernel{reinterpret_cast<const void*>(&k_radix_pass<K, kVals, kExpand, kBits, kThreads, kItems>),
+  using S = PassShape<K, kVals, kExpand, kBits, kThreads, kItems, kOcc>;
+  return Kernel{reinterpret_cast<const void*>(&k_radix_pass<K, kVals, kExpand, kBits, kThreads, kItems, kOcc>),
                 kBits, kThreads, kItems, S::kSmem, S::kMinBlocks};
 }
 

@@ -14,19 +14,21 @@ const radix::Kernel& variant_kernel(int i) {
       make_kernel<uint64_t, true, false, 9, 256, 16>(),
       make_kernel<uint64_t, true, false, 10, 256, 16>(),
       make_kernel<uint64_t, true, false, 11, 256, 16>(),
-      make_kernel<uint64_t, true, false, 8, 512, 16>(),
+      make_kernel<uint64_t, true, false, 9, 256, 16, 3>(),
+      make_kernel<uint64_t, true, false, 9, 256, 12, 3>(),
+      make_kernel<uint64_t, true, false, 8, 256, 12, 3>(),
+      make_kernel<uint64_t, true, false, 9, 256, 8, 4>(),
       make_kernel<uint64_t, true, false, 9, 512, 16>(),
-      make_kernel<uint64_t, true, false, 11, 512, 16>(),
   };
   return kV[i];
 }
-constexpr int kNumVariants = 7;
+constexpr int kNumVariants = 9;
 }  // namespace
 
 int num_pass_variants() { return kNumVariants; }
 PassVariant pass_variant(int i) {
   const radix::Kernel& k = variant_kernel(i);
-  return PassVariant{k.bits, k.threads, k.items};
+  return PassVariant{k.bits, k.threads, k.items, k.min_blocks};
 }
 
 int default_pass_variant(uint32_t digit_bits) {

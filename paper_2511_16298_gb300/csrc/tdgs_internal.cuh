@@ -244,9 +244,10 @@ struct SortPlan {
   uint32_t grid;       // resident CTAs = chunks (0 if the device query failed)
 };
 
-// Tunable pass-kernel configurations (digit bits, threads, items/thread).
+// Tunable pass-kernel configurations (digit bits, threads, items/thread,
+// CTAs per SM its register budget is sized for).
 struct PassVariant {
-  int bits, threads, items;
+  int bits, threads, items, blocks_per_sm;
 };
 int num_pass_variants();
 PassVariant pass_variant(int i);

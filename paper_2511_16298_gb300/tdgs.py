@@ -87,7 +87,7 @@ def lib():
                 "tdgs_tile_bits": ([F], u32),
                 "tdgs_sort_variant_count": ([], i32),
                 "tdgs_sort_variant_info": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
-                                            ctypes.POINTER(i32)], st),
+                                            ctypes.POINTER(i32), ctypes.POINTER(i32)], st),
                 "tdgs_context_set_sort_variant": ([P, i32], st),
                 "tdgs_context_set_tuning": ([P, i32, i32], st),
                 "tdgs_context_get_tuning": ([P, i32, ctypes.POINTER(i32)], st),
@@ -153,13 +153,15 @@ def scan_noalloc(counts: torch.Tensor, offsets=None, total=None, error=None):
     return offsets, total, error
 
 
-def sort_variants() -> list[tuple[int, int, int]]:
+def sort_variants() -> list[tuple[int, int, int, int]]:
+    """(digit bits, threads, items per thread, blocks per SM) of each
+    compiled pass kernel of tdgs_sort_pairs."""
     L = lib()
     out = []
     for i in range(L.tdgs_sort_variant_count()):
-        b, t, it = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        L.tdgs_sort_variant_info(i, ctypes.byref(b), ctypes.byref(t), ctypes.byref(it))
-        out.append((b.value, t.value, it.value))
+        b, t, it, o = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        L.tdgs_sort_variant_info(i, ctypes.byref(b), ctypes.byref(t), ctypes.byref(it), ctypes.byref(o))
+        out.append((b.value, t.value, it.value, o.value))
     return out
 
 

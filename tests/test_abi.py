@@ -49,8 +49,8 @@ def test_host_helpers(libtdgs):
     assert L.tdgs_status_string(0) == b"ok"
     assert L.tdgs_status_string(5) == b"cross-block wait timed out"
     assert L.tdgs_sort_variant_count() >= 3
-    for bits, threads, items in tdgs.sort_variants():
-        assert 8 <= bits <= 11 and threads % 32 == 0 and (threads * items) & (threads * items - 1) == 0
+    for bits, threads, items, occ in tdgs.sort_variants():
+        assert 8 <= bits <= 11 and threads % 32 == 0 and items >= 1 and 1 <= occ <= 4
 
 
 def test_context_create_rejects_bad_device(libtdgs):

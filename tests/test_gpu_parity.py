@@ -134,7 +134,7 @@ def _random_pairs(m, seed, key_bits, ties):
     return k, v
 
 
-@pytest.mark.parametrize("variant", range(7))
+@pytest.mark.parametrize("variant", range(9))
 @pytest.mark.parametrize("m,tile_bits,ties", [(1, 0, False), (4095, 8, True), (4096, 8, False),
                                                (8193, 12, True), (100_003, 13, True),
                                                (250_000, 32, False)])
