@@ -242,7 +242,7 @@ tdgs_status tdgs_sort_frame(tdgs_context* ctx, const tdgs_gaussian2d* g, uint32_
  *
  * It needs no context and allocates nothing (no cudaMalloc, cudaFree or
  * allocating library call).  Its scratch -- look-back status words, the
- * tile ticket and an error word -- is one fixed array of about 64 KB in
+ * tile ticket and an error word -- is one fixed array of about 16 KB in
  * the library's device memory, present on every GPU that loads the library
  * until the process exits.  Limits and behaviour:
  *   - n <= 16,777,216 counts; a larger n returns TDGS_ERR_INVALID_ARGUMENT.

@@ -48,13 +48,12 @@ struct Buffer {
 
 enum KernelId {
   kKCount, kKScan, kKDuplicate, kKRanges, kKRadixPass,
-  kKFrameCount, kKDepthSort, kKFrameScan, kKDupDepth, kKTilePass, kKTileExpand, kKRangesFinal,
-  kKPairBegin, kKNum
+  kKFrameCount, kKDepthSort, kKFrameScan, kKDupDepth, kKTilePass, kKTileExpand, kKRangesFinal, kKNum
 };
 const char* const kKernelNames[kKNum] = {
     "count_tiles",  "scan",       "duplicate_keys",     "tile_ranges",    "radix_pass",
     "frame_count",  "depth_sort", "scan_by_depth", "duplicate_by_depth", "tile_sort_pass",
-    "tile_expand_pass", "ranges_final", "view_pair_begin"};
+    "tile_expand_pass", "ranges_final"};
 
 // View table as stored in device memory (SoA, fixed maximum size).
 struct ViewBlob {
@@ -79,7 +78,7 @@ struct tdgs_context {
   int device = 0;
   DevStatus* d_status = nullptr;
   DevStatus* h_status = nullptr;  // pinned
-  uint32_t* d_tickets = nullptr;  // [0] scan tiles, [2..3] radix grid barrier
+  uint32_t* d_tickets = nullptr;  // [0] scan tiles, [1] count blocks, [2..3] radix grid barrier
   uint32_t ticket_base[2] = {0, 0};
   Buffer scan_status, sort_scratch;
   // fused-frame / multi-view buffers
@@ -664,8 +663,9 @@ tdgs_status run_front(tdgs_context* ctx, cudaStream_t s) {
   uint32_t* counts = static_cast<uint32_t*>(ctx->f_counts.p);
   uint32_t* dk[2] = {static_cast<uint32_t*>(ctx->f_dkey[0].p), static_cast<uint32_t*>(ctx->f_dkey[1].p)};
   uint32_t* dv[2] = {static_cast<uint32_t*>(ctx->f_dval[0].p), static_cast<uint32_t*>(ctx->f_dval[1].p)};
-  TDGS_TRACED(ctx, kKFrameCount, n_all, s, launch_views_count(vt, n_all, counts, dk[0], dv[0], err_word(ctx), s));
-  TDGS_TRACED(ctx, kKPairBegin, 1, s, launch_views_pair_begin(vt, s));
+  TDGS_CUDA(ctx, cudaMemsetAsync(ctx->d_tickets + 1, 0, 4, s));
+  TDGS_TRACED(ctx, kKFrameCount, n_all, s,
+              launch_views_count(vt, n_all, counts, dk[0], dv[0], err_word(ctx), ctx->d_tickets + 1, s));
   const int dbits = ctx->tuning.depth_digit_bits;
   const uint32_t dpasses = depth_passes(dbits);
   const uint32_t dgrid = depth_sort_grid(n_all ? n_all : 1, dbits, ctx->tuning.ctas_per_sm);

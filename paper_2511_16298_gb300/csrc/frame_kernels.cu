@@ -31,7 +31,7 @@ cudaError_t launch_count_tiles(const float4* g, uint32_t n, FrameGeom fg, uint32
 
 // --------------------------------------------------------- exclusive scan
 // Single-pass scan with decoupled look-back (Merrill & Garland, 2016).
-// Each block takes the next tile of 2048 items from a ticket counter (so
+// Each block takes the next tile of 8192 items from a ticket counter (so
 // every predecessor tile is already running or done), publishes its
 // aggregate, then walks back over its predecessors' status words 32 at a
 // time until it meets an inclusive prefix.  Status word: bits 63-62 flag
@@ -39,7 +39,7 @@ cudaError_t launch_count_tiles(const float4* g, uint32_t n, FrameGeom fg, uint32
 // so that an overflow of the 32-bit offsets is detected, not wrapped.
 namespace {
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = kScanTileItems / kScanThreads;  // 8
+constexpr int kScanItems = kScanTileItems / kScanThreads;  // 32
 constexpr uint64_t kFlagA = 1ull << 62;
 constexpr uint64_t kFlagP = 2ull << 62;
 constexpr uint64_t kValMask = (1ull << 62) - 1;

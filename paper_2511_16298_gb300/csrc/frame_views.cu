@@ -16,88 +16,135 @@ namespace tdgs {
 
 // Per record (global index i over all views): tile count, depth sort key
 // (raw depth bits of a visible Gaussian, all ones otherwise so culled ones
-// sort last), the record index, and the per-view pair totals.
+// sort last), the record index, and the per-view pair totals.  The last
+// block to finish turns the totals into pbeg (first pair of each view in
+// the sorted list; views are contiguous there because global tile ids are
+// view-major) and resets the ticket.
+constexpr int kCountUnroll = 4;
 __global__ void __launch_bounds__(256)
     k_views_count(ViewTable vt, uint32_t n_all, uint32_t* __restrict__ counts,
-                  uint32_t* __restrict__ dkey, uint32_t* __restrict__ dval, uint32_t* err) {
+                  uint32_t* __restrict__ dkey, uint32_t* __restrict__ dval, uint32_t* err,
+                  uint32_t* ticket) {
   __shared__ uint32_t s_begin[kMaxViews + 1];
   __shared__ unsigned long long s_tot[kMaxViews];
+  __shared__ const float4* s_g[kMaxViews];
+  __shared__ FrameGeom s_geom[kMaxViews];
+  __shared__ bool s_last;
   for (uint32_t v = threadIdx.x; v <= vt.nv; v += blockDim.x) s_begin[v] = vt.rec_begin[v];
-  for (uint32_t v = threadIdx.x; v < vt.nv; v += blockDim.x) s_tot[v] = 0;
+  for (uint32_t v = threadIdx.x; v < vt.nv; v += blockDim.x) {
+    s_tot[v] = 0;
+    s_g[v] = vt.g[v];
+    s_geom[v] = vt.geom[v];
+  }
   __syncthreads();
   bool bad = false;
+  const uint32_t lane = lane_id();
   const uint32_t stride = gridDim.x * blockDim.x;
-  // warp-uniform loop so the per-view totals can be reduced across the warp
-  for (uint32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n_all; i0 += stride) {
-    const uint32_t i = i0 + lane_id();
-    uint32_t v = 0, cnt = 0;
-    if (i < n_all) {
-      v = vt.nv == 1 ? 0u : find_view(s_begin, vt.nv, i);
-      const float4 rec = __ldg(vt.g[v] + (i - s_begin[v]));
-      const TileRect q = tile_rect(rec, vt.geom[v]);
-      bad |= q.invalid;
-      cnt = q.count;
-      counts[i] = q.count;
-      dkey[i] = q.count ? __float_as_uint(rec.z) : 0xffffffffu;
-      dval[i] = i;
-    }
-    const uint32_t v0 = __shfl_sync(0xffffffffu, v, 0);
-    if (__all_sync(0xffffffffu, v == v0 || i >= n_all)) {
-      unsigned long long sum = cnt;
+  // warp-uniform loop so the per-view totals can be reduced across the
+  // warp; kCountUnroll records per thread are in flight at once
+  for (uint32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n_all; i0 += stride * kCountUnroll) {
+    float4 rec[kCountUnroll];
+    uint32_t vv[kCountUnroll];
 #pragma unroll
-      for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
-      if (lane_id() == 0 && sum) atomicAdd(&s_tot[v0], sum);
-    } else if (cnt) {
-      atomicAdd(&s_tot[v], static_cast<unsigned long long>(cnt));
+    for (int u = 0; u < kCountUnroll; ++u) {
+      const uint32_t i = i0 + u * stride + lane;
+      vv[u] = 0;
+      rec[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < n_all) {
+        vv[u] = vt.nv == 1 ? 0u : find_view(s_begin, vt.nv, i);
+        rec[u] = __ldg(s_g[vv[u]] + (i - s_begin[vv[u]]));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kCountUnroll; ++u) {
+      const uint32_t i = i0 + u * stride + lane;
+      uint32_t cnt = 0;
+      const uint32_t v = vv[u];
+      if (i < n_all) {
+        const TileRect q = tile_rect(rec[u], s_geom[v]);
+        bad |= q.invalid;
+        cnt = q.count;
+        counts[i] = q.count;
+        dkey[i] = q.count ? __float_as_uint(rec[u].z) : 0xffffffffu;
+        dval[i] = i;
+      }
+      const uint32_t v0 = __shfl_sync(0xffffffffu, v, 0);
+      if (__all_sync(0xffffffffu, v == v0 || i >= n_all)) {
+        unsigned long long sum = cnt;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+        if (lane == 0 && sum) atomicAdd(&s_tot[v0], sum);
+      } else if (cnt) {
+        atomicAdd(&s_tot[v], static_cast<unsigned long long>(cnt));
+      }
     }
   }
-  if (__any_sync(0xffffffffu, bad) && lane_id() == 0) latch_error(err, TDGS_ERR_INVALID_ARGUMENT, kSiteViewsCount);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) latch_error(err, TDGS_ERR_INVALID_ARGUMENT, kSiteViewsCount);
   __syncthreads();
   for (uint32_t v = threadIdx.x; v < vt.nv; v += blockDim.x)
     if (s_tot[v]) atomicAdd(reinterpret_cast<unsigned long long*>(vt.vtot + v), s_tot[v]);
-}
-
-cudaError_t launch_views_count(const ViewTable& vt, uint32_t n_all, uint32_t* counts,
-                               uint32_t* dkey, uint32_t* dval, uint32_t* err, cudaStream_t s) {
-  if (n_all == 0) return cudaSuccess;
-  const uint32_t blocks = (n_all + 255) / 256;
-  const uint32_t grid = blocks < 152u * 8u ? blocks : 152u * 8u;
-  k_views_count<<<grid, 256, 0, s>>>(vt, n_all, counts, dkey, dval, err);
-  return cudaGetLastError();
-}
-
-// pbeg[v] = pairs of views < v (views are contiguous in the sorted list
-// because global tile ids are view-major).
-__global__ void __launch_bounds__(32) k_views_pair_begin(ViewTable vt) {
-  if (threadIdx.x == 0) {
-    uint64_t run = 0;
-    for (uint32_t v = 0; v < vt.nv; ++v) {
-      vt.pbeg[v] = static_cast<uint32_t>(run);
-      run += vt.vtot[v];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    for (uint32_t v = threadIdx.x; v < vt.nv; v += blockDim.x) s_tot[v] = __ldcg(reinterpret_cast<unsigned long long*>(vt.vtot + v));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint64_t run = 0;
+      for (uint32_t v = 0; v < vt.nv; ++v) {
+        vt.pbeg[v] = static_cast<uint32_t>(run);
+        run += s_tot[v];
+      }
+      vt.pbeg[vt.nv] = static_cast<uint32_t>(run);
+      *ticket = 0;
     }
-    vt.pbeg[vt.nv] = static_cast<uint32_t>(run);
   }
 }
 
-cudaError_t launch_views_pair_begin(const ViewTable& vt, cudaStream_t s) {
-  k_views_pair_begin<<<1, 32, 0, s>>>(vt);
+cudaError_t launch_views_count(const ViewTable& vt, uint32_t n_all, uint32_t* counts,
+                               uint32_t* dkey, uint32_t* dval, uint32_t* err, uint32_t* ticket,
+                               cudaStream_t s) {
+  const uint32_t blocks = (n_all + 256 * kCountUnroll - 1) / (256 * kCountUnroll);
+  const uint32_t grid = blocks < 1u ? 1u : (blocks < 152u * 8u ? blocks : 152u * 8u);
+  k_views_count<<<grid, 256, 0, s>>>(vt, n_all, counts, dkey, dval, err, ticket);
   return cudaGetLastError();
 }
 
 // Duplicate in depth order: depth position j is record sorder[j]; its
 // pairs start at soff[j]; each is (global tile << rbits) | j.  Warp-level
-// load-balanced expansion: lane l takes pair chunk + l, finds its owner by
-// a 5-step binary search over the lanes' start offsets, and derives the
-// tile from the local index (rows outer, columns inner).
+// load-balanced expansion over windows of 32 consecutive pairs: every
+// Gaussian of the warp's 32 depth positions publishes its rectangle in
+// shared memory and, when its first pair falls in the window, its lane at
+// that window position; lane l of the window finds the owner of pair l as
+// the nearest start at or before l (one OR-reduction and a count of
+// leading zeros), or the owner carried over from the previous window.
+// The row of a pair inside its rectangle is jj / width, from a float
+// reciprocal corrected by one step (exact for jj < 2^22), else an integer
+// division.  Rows are outer, columns inner.
 template <typename K>
 __global__ void __launch_bounds__(256)
     k_views_dup(ViewTable vt, const uint32_t* __restrict__ sorder,
                 const uint32_t* __restrict__ soff, uint32_t n_all, uint32_t rbits,
                 K* __restrict__ out, uint32_t cap, uint32_t* err) {
   __shared__ uint32_t s_begin[kMaxViews + 1];
+  __shared__ const float4* s_g[kMaxViews];
+  __shared__ FrameGeom s_geom[kMaxViews];
+  __shared__ uint32_t s_tb[kMaxViews];
+  // per warp and lane: {first pair - warp's first pair, global id of the
+  // rectangle's first tile, width in tiles, bits of 1 / width}; tiles per row
+  __shared__ uint4 s_info[8][32];
+  __shared__ uint32_t s_gx[8][32];
+  __shared__ uint32_t s_at[8][32];  // lane whose pairs start at a window position
   for (uint32_t v = threadIdx.x; v <= vt.nv; v += blockDim.x) s_begin[v] = vt.rec_begin[v];
+  for (uint32_t v = threadIdx.x; v < vt.nv; v += blockDim.x) {
+    s_g[v] = vt.g[v];
+    s_geom[v] = vt.geom[v];
+    s_tb[v] = vt.tile_begin[v];
+  }
   __syncthreads();
-  const uint32_t lane = lane_id();
+  const uint32_t lane = lane_id(), w8 = threadIdx.x >> 5;
   const uint32_t warps_total = (gridDim.x * blockDim.x) >> 5;
   bool over = false;
   for (uint32_t wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -107,50 +154,67 @@ __global__ void __launch_bounds__(256)
     q.x0 = q.y0 = q.x1 = q.y1 = 0;
     q.count = 0;
     uint64_t start = 0;
-    int32_t gx = 1;
-    uint32_t tb = 0;
+    uint32_t first = 0, gx = 1;
     const uint32_t gi = j < n_all ? __ldg(sorder + j) : 0xffffffffu;
     if (gi < n_all) {  // a depth order that is not a permutation is never followed out of bounds
       const uint32_t v = vt.nv == 1 ? 0u : find_view(s_begin, vt.nv, gi);
-      const FrameGeom fg = vt.geom[v];
-      q = tile_rect(__ldg(vt.g[v] + (gi - s_begin[v])), fg);
+      const FrameGeom fg = s_geom[v];
+      q = tile_rect(__ldg(s_g[v] + (gi - s_begin[v])), fg);
       start = __ldg(soff + j);
-      gx = fg.gx;
-      tb = vt.tile_begin[v];
+      gx = static_cast<uint32_t>(fg.gx);
+      first = s_tb[v] + static_cast<uint32_t>(q.y0) * gx + static_cast<uint32_t>(q.x0);
     }
-    const uint64_t end = start + q.count;
-    uint64_t end_max = end;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-      const uint64_t o = __shfl_xor_sync(0xffffffffu, end_max, d);
-      end_max = o > end_max ? o : end_max;
-    }
-    if (gi >= n_all) start = end_max;
+    // pairs of consecutive depth positions are consecutive, so the warp's
+    // last valid lane ends its range
+    const uint32_t last = min(31u, n_all - 1u - wg * 32u);
+    const uint64_t end_max = __shfl_sync(0xffffffffu, start + q.count, last);
+    if (end_max > cap) over = true;
+    // Positions relative to the warp's first pair, in 32 bits; pairs at or
+    // beyond cap are not written, and the window loop cannot wrap.
     const uint64_t begin = __shfl_sync(0xffffffffu, start, 0);
-    const int32_t w = q.x1 - q.x0;
-    for (uint64_t c = begin; c < end_max; c += 32) {
-      const uint64_t p = c + lane;
-      uint32_t lo = 0;
-#pragma unroll
-      for (uint32_t step = 16; step > 0; step >>= 1) {
-        const uint64_t sc = __shfl_sync(0xffffffffu, start, lo + step);
-        if (sc <= p) lo += step;
+    const uint64_t stop = end_max < cap ? end_max : cap;
+    const uint64_t span = stop > begin ? stop - begin : 0;
+    const uint32_t nrel = span < 0xffffffe0ull ? static_cast<uint32_t>(span) : 0xffffffe0u;
+    const uint64_t srel64 = start - begin;
+    const uint32_t srel = (q.count > 0 && srel64 < nrel) ? static_cast<uint32_t>(srel64) : 0xffffffffu;
+    const uint32_t wd = static_cast<uint32_t>(q.x1 - q.x0);
+    s_info[w8][lane] = make_uint4(srel, first, wd, __float_as_uint(wd ? __frcp_rn(static_cast<float>(wd)) : 0.0f));
+    s_gx[w8][lane] = gx;
+    // rows from the float reciprocal need jj < 2^22 (one correction step)
+    const bool exact_div = __any_sync(0xffffffffu, q.count > (1u << 22));
+    K* wout = out + begin;
+    const uint32_t rank0 = wg * 32u;
+    uint32_t carry = 0;
+    __syncwarp();
+    for (uint32_t c = 0; c < nrel; c += 32) {
+      // window positions where a Gaussian's pairs begin
+      const uint32_t at = srel - c;
+      const bool here = at < 32u;
+      if (here) s_at[w8][at] = lane;
+      const uint32_t starts = __reduce_or_sync(0xffffffffu, here ? 1u << at : 0u);
+      __syncwarp();
+      const uint32_t upto = starts & (0xffffffffu >> (31u - lane));  // positions <= lane
+      const uint32_t owner = upto ? s_at[w8][31u - __clz(upto)] : carry;
+      const uint32_t p = c + lane;
+      const uint4 in = s_info[w8][owner];
+      const uint32_t jj = p - in.x;
+      const uint32_t ow = in.z;
+      uint32_t ry = __float2uint_rz(__fmul_rn(__uint2float_rn(jj), __uint_as_float(in.w)));
+      uint32_t rx = jj - ry * ow;
+      const bool under = static_cast<int32_t>(rx) < 0;
+      ry = under ? ry - 1u : ry;
+      rx = under ? rx + ow : rx;
+      const bool past = rx >= ow;
+      ry = past ? ry + 1u : ry;
+      rx = past ? rx - ow : rx;
+      if (exact_div && ow) {
+        ry = jj / ow;
+        rx = jj - ry * ow;
       }
-      const uint64_t s0 = __shfl_sync(0xffffffffu, start, lo);
-      const int32_t ow = __shfl_sync(0xffffffffu, w, lo);
-      const int32_t ox0 = __shfl_sync(0xffffffffu, q.x0, lo);
-      const int32_t oy0 = __shfl_sync(0xffffffffu, q.y0, lo);
-      const int32_t ogx = __shfl_sync(0xffffffffu, gx, lo);
-      const uint32_t otb = __shfl_sync(0xffffffffu, tb, lo);
-      if (p < end_max && ow > 0) {
-        const uint32_t jj = static_cast<uint32_t>(p - s0);
-        const uint32_t ry = jj / static_cast<uint32_t>(ow);
-        const uint32_t rx = jj - ry * static_cast<uint32_t>(ow);
-        const uint64_t tile = otb + static_cast<uint64_t>(oy0 + ry) * static_cast<uint64_t>(ogx) +
-                              static_cast<uint64_t>(ox0 + rx);
-        if (p < cap) out[p] = static_cast<K>((tile << rbits) | (wg * 32u + lo));
-        else over = true;
-      }
+      const uint32_t tile = in.y + ry * s_gx[w8][owner] + rx;
+      if (p < nrel) wout[p] = (static_cast<K>(tile) << rbits) | static_cast<K>(rank0 + owner);
+      carry = __shfl_sync(0xffffffffu, owner, 31);
+      __syncwarp();
     }
   }
   if (__any_sync(0xffffffffu, over) && lane == 0) latch_error(err, TDGS_ERR_CAPACITY, kSiteViewsDup);

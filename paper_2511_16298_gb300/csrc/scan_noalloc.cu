@@ -13,15 +13,15 @@ namespace tdgs {
 namespace {
 
 constexpr uint32_t kNoAllocMaxItems = 1u << 24;                        // 16,777,216 counts
-constexpr uint32_t kNoAllocTiles = kNoAllocMaxItems / kScanTileItems;  // 8,192 status words
+constexpr uint32_t kNoAllocTiles = kNoAllocMaxItems / kScanTileItems;  // 2,048 status words
 
 struct NoAllocScratch {
   uint32_t ticket;                  // tile ticket, starts at 0 on every call
   uint32_t err[3];                  // latched error code and site
-  uint64_t status[kNoAllocTiles];   // one look-back word per 2048-count tile
+  uint64_t status[kNoAllocTiles];   // one look-back word per 8192-count tile
 };
 
-// Shared by every call on a device and kept between calls (about 64 KB per
+// Shared by every call on a device and kept between calls (about 16 KB per
 // device, held until the process exits).
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 

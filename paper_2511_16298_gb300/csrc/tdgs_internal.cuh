@@ -131,7 +131,7 @@ cudaError_t launch_count_tiles(const float4* g, uint32_t n, FrameGeom fg, uint32
 // Decoupled look-back exclusive scan.  With recs != nullptr the counts are
 // computed from the records (count and scan fused); otherwise read from
 // counts.  status: one uint64 per 2048-item block, zeroed by the caller.
-constexpr uint32_t kScanTileItems = 2048;
+constexpr uint32_t kScanTileItems = 8192;
 cudaError_t launch_scan(const uint32_t* counts, const float4* recs, const uint32_t* gather,
                         FrameGeom fg, uint32_t n, uint32_t* offsets, uint64_t* status,
                         uint32_t* ticket, uint32_t ticket_base, uint64_t* total64,
@@ -166,9 +166,11 @@ __device__ __forceinline__ uint32_t find_view(const uint32_t* begin, uint32_t nv
   return lo;
 }
 
+// Counts, depth keys and indices of all records, per-view pair totals, and
+// (last block) the first pair of each view.  ticket: a zero word, left zero.
 cudaError_t launch_views_count(const ViewTable& vt, uint32_t n_all, uint32_t* counts,
-                               uint32_t* dkey, uint32_t* dval, uint32_t* err, cudaStream_t s);
-cudaError_t launch_views_pair_begin(const ViewTable& vt, cudaStream_t s);
+                               uint32_t* dkey, uint32_t* dval, uint32_t* err, uint32_t* ticket,
+                               cudaStream_t s);
 cudaError_t launch_views_dup(const ViewTable& vt, const uint32_t* sorder, const uint32_t* soff,
                              uint32_t n_all, uint32_t rbits, void* out, bool wide, uint32_t cap,
                              uint32_t* err, cudaStream_t s);
