@@ -3,11 +3,10 @@
 Times candidate settings of a context's tuning knobs on a representative
 workload with CUDA events and keeps the fastest:
 
-* tdgs_sort_pairs: the pass kernel variant (digit width 8/10/11, threads,
-  keys per thread) and CTAs per SM of the persistent grid;
-* the fused frame / multi-view batch: tile-pass ranking kernel (warp
-  ballots or per-thread counter table), tile digit width (4..8) and CTAs
-  per SM.
+* tdgs_sort_pairs: the pass kernel variant (digit width 8..11, threads,
+  keys per thread, blocks per SM) and CTAs per SM of the persistent grid;
+* the fused frame / multi-view batch: widest tile digit (6, 8 or 12
+  bits), CTAs per SM and the depth sort's digit width (8 or 11).
 
 Results are stored as JSON keyed by workload shape (pair-count bucket and
 key bits, or Gaussians/tiles buckets), so a server can apply the table

@@ -627,10 +627,9 @@ tdgs_status ensure_record_buffers(tdgs_context* ctx, cudaStream_t s) {
   const uint32_t n_all = ctx->n_all;
   const uint32_t tiles = (n_all + kScanTileItems - 1) / kScanTileItems;
   if (st == TDGS_OK) st = ensure(ctx, ctx->scan_status, static_cast<size_t>(tiles) * 8 + 8, s);
-  const int dbits = ctx->tuning.depth_digit_bits;
-  const uint32_t dgrid = depth_sort_grid(n_all ? n_all : 1, dbits, ctx->tuning.ctas_per_sm);
-  if (dgrid == 0) return fail(ctx, TDGS_ERR_CUDA, "device query for the depth sort failed");
-  if (st == TDGS_OK) st = ensure(ctx, ctx->sort_scratch, depth_sort_scratch_words(dbits, dgrid) * 4, s);
+  const DepthPlan dp = plan_depth_sort(n_all, ctx->tuning.depth_digit_bits, ctx->tuning.ctas_per_sm);
+  if (dp.grid == 0) return fail(ctx, TDGS_ERR_CUDA, "device query for the depth sort failed");
+  if (st == TDGS_OK) st = ensure(ctx, ctx->sort_scratch, dp.scratch_words * 4, s);
   return st;
 }
 
@@ -666,14 +665,19 @@ tdgs_status run_front(tdgs_context* ctx, cudaStream_t s) {
   TDGS_CUDA(ctx, cudaMemsetAsync(ctx->d_tickets + 1, 0, 4, s));
   TDGS_TRACED(ctx, kKFrameCount, n_all, s,
               launch_views_count(vt, n_all, counts, dk[0], dv[0], err_word(ctx), ctx->d_tickets + 1, s));
-  const int dbits = ctx->tuning.depth_digit_bits;
-  const uint32_t dpasses = depth_passes(dbits);
-  const uint32_t dgrid = depth_sort_grid(n_all ? n_all : 1, dbits, ctx->tuning.ctas_per_sm);
-  for (uint32_t p = 0; p < dpasses; ++p) {
-    TDGS_TRACED(ctx, kKDepthSort, n_all, s,
-                launch_depth_pass(dbits, dgrid, p, dk[p & 1], dv[p & 1], dk[(p + 1) & 1], dv[(p + 1) & 1],
-                                  n_all, static_cast<uint32_t*>(ctx->sort_scratch.p), ctx->d_tickets + 2,
-                                  err_word(ctx), s));
+  const DepthPlan dp = plan_depth_sort(n_all, ctx->tuning.depth_digit_bits, ctx->tuning.ctas_per_sm);
+  const uint32_t dpasses = dp.passes;
+  uint32_t* scratch = static_cast<uint32_t*>(ctx->sort_scratch.p);
+  if (dp.resident) {
+    TDGS_TRACED(ctx, kKDepthSort, static_cast<uint64_t>(n_all) * dpasses, s,
+                launch_depth_resident(dp, dk[0], dv[0], dk[1], dv[1], n_all, scratch, ctx->d_tickets + 2,
+                                      err_word(ctx), s));
+  } else {
+    for (uint32_t p = 0; p < dpasses; ++p) {
+      TDGS_TRACED(ctx, kKDepthSort, n_all, s,
+                  launch_depth_pass(dp, p, dk[p & 1], dv[p & 1], dk[(p + 1) & 1], dv[(p + 1) & 1], n_all, scratch,
+                                    ctx->d_tickets + 2, err_word(ctx), s));
+    }
   }
   if (n_all) {
     tdgs_status st = do_scan(ctx, kKFrameScan, counts, nullptr, dv[dpasses & 1], FrameGeom{}, n_all,
@@ -691,7 +695,7 @@ tdgs_status run_back(tdgs_context* ctx, uint32_t m, const uint64_t* m_dev, cudaS
   const ViewTable vt = device_table(ctx);
   const Shape sh = shape_of(ctx);
   const uint32_t n_all = ctx->n_all;
-  const uint32_t dpasses = depth_passes(ctx->tuning.depth_digit_bits);
+  const uint32_t dpasses = plan_depth_sort(n_all, ctx->tuning.depth_digit_bits, ctx->tuning.ctas_per_sm).passes;
   const uint32_t* sdepth = static_cast<uint32_t*>(ctx->f_dkey[dpasses & 1].p);
   const uint32_t* sorder = static_cast<uint32_t*>(ctx->f_dval[dpasses & 1].p);
   uint32_t* scratch = static_cast<uint32_t*>(ctx->sort_scratch.p);

@@ -226,52 +226,18 @@ __device__ __forceinline__ void count_key(K k, const PassArgs& a, bool d31, uint
   atomicAdd(&hist[digit_of<K>(k, a.shift, a.mask, d31)], 1u);
 }
 
-// Phases 1-2: histogram of this chunk's digits, column scans over chunks
-// between two grid barriers, then base[b] = first output position of this
-// chunk's keys with digit b.  hist: kBins words of shared scratch.  With
-// a.ranges set, the tile ranges are written from the digit totals.
-template <typename K, int kBins, int kThreads, uint32_t kU = 8>
-__device__ __forceinline__ void chunk_bases(const K* __restrict__ kin, const PassArgs& a,
-                                            uint32_t beg, uint32_t end, bool d31, uint32_t* base,
-                                            uint32_t* hist, uint32_t* s_warp, const uint32_t* s_vtile) {
+// Phase 2, after every chunk has written its histogram row H[c][*]: a
+// grid barrier, one warp per digit scans the column over chunks (chunk
+// prefixes P, digit totals tot), a grid barrier, then base[b] = first
+// output position of this chunk's keys with digit b.  With a.ranges set,
+// the tile ranges are written from the digit totals.
+template <int kBins, int kThreads>
+__device__ __forceinline__ void scan_chunks(const PassArgs& a, uint32_t* base, uint32_t* s_warp,
+                                            const uint32_t* s_vtile) {
   constexpr int kWarps = kThreads / 32;
   constexpr int kBpt = (kBins + kThreads - 1) / kThreads;
   const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
   const uint32_t G = gridDim.x, c = blockIdx.x;
-  for (uint32_t b = t; b < kBins; b += kThreads) hist[b] = 0;
-  __syncthreads();
-  {
-    const uint64_t keep = policy_evict_last();
-    bool bad = false;
-    const K* kc = kin + beg;
-    const uint32_t len = end - beg;
-    uint32_t done = 0;
-    if ((reinterpret_cast<uintptr_t>(kc) & 15u) == 0) {
-      constexpr uint32_t kPer = 16 / sizeof(K);  // keys per 16-byte vector; kU vectors in flight per thread
-      const uint32_t nvec = len / kPer;
-      for (uint32_t q0 = t; q0 < nvec; q0 += kThreads * kU) {
-        uint4 w[kU];
-#pragma unroll
-        for (uint32_t u = 0; u < kU; ++u) {
-          const uint32_t q = q0 + u * kThreads;
-          w[u] = q < nvec ? ld_hint_v4(kc + q * kPer, keep) : make_uint4(0, 0, 0, 0);
-        }
-#pragma unroll
-        for (uint32_t u = 0; u < kU; ++u) {
-          if (q0 + u * kThreads < nvec) {
-            const K* e = reinterpret_cast<const K*>(&w[u]);
-#pragma unroll
-            for (uint32_t i = 0; i < kPer; ++i) count_key<K>(e[i], a, d31, hist, bad);
-          }
-        }
-      }
-      done = nvec * kPer;
-    }
-    for (uint32_t i = done + t; i < len; i += kThreads) count_key<K>(kc[i], a, d31, hist, bad);
-    if (__any_sync(0xffffffffu, bad) && lane == 0) latch_error(a.err, TDGS_ERR_INVALID_ARGUMENT, kSiteRadixKeys);
-  }
-  __syncthreads();
-  for (uint32_t b = t; b < kBins; b += kThreads) a.H[static_cast<size_t>(c) * kBins + b] = hist[b];
   grid_barrier(a.bar, a.err);
   // Lane l holds chunks l*kCol .. l*kCol+kCol-1 of one digit column; all
   // loads are issued before the scan so the column costs one L2 round trip.
@@ -330,6 +296,55 @@ __device__ __forceinline__ void chunk_bases(const K* __restrict__ kin, const Pas
     run += seg[i];
   }
   __syncthreads();
+}
+
+// Phases 1-2: histogram of this chunk's digits, column scans over chunks
+// between two grid barriers, then base[b] = first output position of this
+// chunk's keys with digit b.  hist: kBins words of shared scratch.  With
+// a.ranges set, the tile ranges are written from the digit totals.
+template <typename K, int kBins, int kThreads, uint32_t kU = 8>
+__device__ __forceinline__ void chunk_bases(const K* __restrict__ kin, const PassArgs& a,
+                                            uint32_t beg, uint32_t end, bool d31, uint32_t* base,
+                                            uint32_t* hist, uint32_t* s_warp, const uint32_t* s_vtile) {
+  constexpr int kWarps = kThreads / 32;
+  constexpr int kBpt = (kBins + kThreads - 1) / kThreads;
+  const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+  const uint32_t G = gridDim.x, c = blockIdx.x;
+  for (uint32_t b = t; b < kBins; b += kThreads) hist[b] = 0;
+  __syncthreads();
+  {
+    const uint64_t keep = policy_evict_last();
+    bool bad = false;
+    const K* kc = kin + beg;
+    const uint32_t len = end - beg;
+    uint32_t done = 0;
+    if ((reinterpret_cast<uintptr_t>(kc) & 15u) == 0) {
+      constexpr uint32_t kPer = 16 / sizeof(K);  // keys per 16-byte vector; kU vectors in flight per thread
+      const uint32_t nvec = len / kPer;
+      for (uint32_t q0 = t; q0 < nvec; q0 += kThreads * kU) {
+        uint4 w[kU];
+#pragma unroll
+        for (uint32_t u = 0; u < kU; ++u) {
+          const uint32_t q = q0 + u * kThreads;
+          w[u] = q < nvec ? ld_hint_v4(kc + q * kPer, keep) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < kU; ++u) {
+          if (q0 + u * kThreads < nvec) {
+            const K* e = reinterpret_cast<const K*>(&w[u]);
+#pragma unroll
+            for (uint32_t i = 0; i < kPer; ++i) count_key<K>(e[i], a, d31, hist, bad);
+          }
+        }
+      }
+      done = nvec * kPer;
+    }
+    for (uint32_t i = done + t; i < len; i += kThreads) count_key<K>(kc[i], a, d31, hist, bad);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) latch_error(a.err, TDGS_ERR_INVALID_ARGUMENT, kSiteRadixKeys);
+  }
+  __syncthreads();
+  for (uint32_t b = t; b < kBins; b += kThreads) a.H[static_cast<size_t>(c) * kBins + b] = hist[b];
+  scan_chunks<kBins, kThreads>(a, base, s_warp, s_vtile);
 }
 
 // Output of one key at its sorted position dst.  Plain passes store the
@@ -431,18 +446,23 @@ __device__ __forceinline__ void digit_starts(const Smem<K>& sm, uint32_t* s_warp
   }
 }
 
-// Phase 3 for one tile of `valid` keys starting at kt (kFull: valid ==
-// kTileKeys, no bounds checks).  Returns false if a destination fell
-// outside [0, m).  Block barriers per tile: after ranking, after the
-// prefix over warps, after the digit starts, after the exchange (and one
-// more for values).  Each warp's counter row is zero on entry and is
-// zeroed again by its own warp once read.
-template <bool kFull, typename S, typename K, bool kVals, bool kExpand, int kBits, int kItems>
-__device__ __forceinline__ bool rank_and_scatter(const K* __restrict__ kt, const uint32_t* __restrict__ vt,
-                                                 uint32_t valid, uint32_t m, const PassArgs& a, bool d31,
-                                                 const Smem<K>& sm, uint32_t* s_warp,
-                                                 const uint32_t* s_vrec, const uint32_t* s_vtile,
-                                                 void* kout_raw, uint32_t* vout) {
+// Registers of one tile between its ranking and its scatter.
+template <typename K, bool kExpand, int kItems>
+struct TileRegs {
+  K k[kItems];
+  uint32_t d[kItems];  // digits
+  uint32_t r[kItems];  // ranks: within the warp, then within the tile
+  uint32_t gi[kExpand ? kItems : 1], dep[kExpand ? kItems : 1];
+};
+
+// Phase 3, first half, for one tile of `valid` keys starting at kt
+// (kFull: valid == kTileKeys, no bounds checks): load, stable rank within
+// each warp, exclusive prefix over warps; on return (after a block
+// barrier) lstart holds the tile's count per digit.  Each warp's counter
+// row is zero on entry.
+template <bool kFull, typename S, typename K, bool kExpand, int kBits, int kItems>
+__device__ __forceinline__ void rank_tile(const K* __restrict__ kt, uint32_t valid, const PassArgs& a, bool d31,
+                                          const Smem<K>& sm, TileRegs<K, kExpand, kItems>& R) {
   constexpr int kBins = S::kBins;
   constexpr int kWarps = S::kWarps;
   constexpr int kThreads = kWarps * 32;
@@ -450,24 +470,19 @@ __device__ __forceinline__ bool rank_and_scatter(const K* __restrict__ kt, const
   constexpr int kCpt = S::kCpt;
   const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
   const uint32_t wbase = warp * 32 * kItems;
-  bool ok = true;
-
-  K k[kItems];
-  uint32_t d[kItems];
   // expanding pass: the depth bits and record index of each element's
   // depth rank are gathered now, so their latency hides behind the ranking
-  uint32_t gi[kExpand ? kItems : 1], dep[kExpand ? kItems : 1];
 #pragma unroll
   for (int j = 0; j < kItems; ++j) {
     const uint32_t idx = wbase + j * 32 + lane;
-    k[j] = (kFull || idx < valid) ? __ldcs(kt + idx) : K(0);
-    d[j] = digit_of<K>(k[j], a.shift, a.mask, d31);
+    R.k[j] = (kFull || idx < valid) ? __ldcs(kt + idx) : K(0);
+    R.d[j] = digit_of<K>(R.k[j], a.shift, a.mask, d31);
     if constexpr (kExpand) {
-      gi[j] = dep[j] = 0u;
+      R.gi[j] = R.dep[j] = 0u;
       if (kFull || idx < valid) {
-        const uint32_t rk = static_cast<uint32_t>(k[j] & ((static_cast<K>(1) << a.rbits) - 1));
-        gi[j] = __ldg(a.sorder + rk);
-        dep[j] = __ldg(a.sdepth + rk);
+        const uint32_t rk = static_cast<uint32_t>(R.k[j] & ((static_cast<K>(1) << a.rbits) - 1));
+        R.gi[j] = __ldg(a.sorder + rk);
+        R.dep[j] = __ldg(a.sdepth + rk);
       }
     }
   }
@@ -478,30 +493,29 @@ __device__ __forceinline__ bool rank_and_scatter(const K* __restrict__ kt, const
   constexpr int kGroup = sizeof(K) == 8 ? 4 : 8;
   static_assert(kItems % kGroup == 0, "items per thread: a multiple of the ranking group");
   uint16_t* my_wh = sm.wh + warp * kBins;
-  uint32_t r[kItems];
   const uint32_t lt = lanemask_lt();
 #pragma unroll
   for (int j0 = 0; j0 < kItems; j0 += kGroup) {
 #pragma unroll
     for (int j = j0; j < j0 + kGroup; ++j) {
-      r[j] = equal_digit_lanes<kBits>(d[j]);
+      R.r[j] = equal_digit_lanes<kBits>(R.d[j]);
       if constexpr (!kFull) {
         const uint32_t first = wbase + j * 32;
         const uint32_t nlive = valid > first ? min(valid - first, 32u) : 0u;
-        r[j] &= nlive >= 32 ? 0xffffffffu : ((1u << nlive) - 1u);
+        R.r[j] &= nlive >= 32 ? 0xffffffffu : ((1u << nlive) - 1u);
       }
     }
 #pragma unroll
     for (int j = j0; j < j0 + kGroup; ++j) {
-      const uint32_t peers = r[j];
+      const uint32_t peers = R.r[j];
       const bool live = kFull || wbase + j * 32 + lane < valid;
-      const uint32_t before = my_wh[d[j]];
+      const uint32_t before = my_wh[R.d[j]];
       __syncwarp();
       const uint32_t cnt = __popc(peers);
       const uint32_t below = __popc(peers & lt);
-      if (live && below + 1 == cnt) my_wh[d[j]] = static_cast<uint16_t>(before + cnt);
+      if (live && below + 1 == cnt) my_wh[R.d[j]] = static_cast<uint16_t>(before + cnt);
       __syncwarp();
-      r[j] = before + below;
+      R.r[j] = before + below;
     }
   }
   __syncthreads();
@@ -526,10 +540,29 @@ __device__ __forceinline__ bool rank_and_scatter(const K* __restrict__ kt, const
     }
   }
   __syncthreads();
+}
+
+// Phase 3, second half: digit starts (with base[] = this chunk's running
+// output base per digit), exchange into digit order, coalesced scatter.
+// Returns false if a destination fell outside [0, m).  Block barriers:
+// after the digit starts and after the exchange (and one more for values);
+// this warp's counter row is zeroed again.
+template <bool kFull, typename S, typename K, bool kVals, bool kExpand, int kBits, int kItems>
+__device__ __forceinline__ bool scatter_tile(const uint32_t* __restrict__ vt, uint32_t valid, uint32_t m,
+                                             const PassArgs& a, bool d31, const Smem<K>& sm, uint32_t* s_warp,
+                                             const uint32_t* s_vrec, const uint32_t* s_vtile, void* kout_raw,
+                                             uint32_t* vout, TileRegs<K, kExpand, kItems>& R) {
+  constexpr int kBins = S::kBins;
+  constexpr int kWarps = S::kWarps;
+  constexpr int kThreads = kWarps * 32;
+  const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+  const uint32_t wbase = warp * 32 * kItems;
+  uint16_t* my_wh = sm.wh + warp * kBins;
+  bool ok = true;
   digit_starts<S, K>(sm, s_warp);
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < kItems; ++j) r[j] += sm.lstart[d[j]] + my_wh[d[j]];
+  for (int j = 0; j < kItems; ++j) R.r[j] += sm.lstart[R.d[j]] + my_wh[R.d[j]];
   __syncwarp();
   {  // this warp's counter row is read: zero it for the next tile
     uint4* z = reinterpret_cast<uint4*>(my_wh);
@@ -538,10 +571,10 @@ __device__ __forceinline__ bool rank_and_scatter(const K* __restrict__ kt, const
 #pragma unroll
   for (int j = 0; j < kItems; ++j) {
     if (kFull || wbase + j * 32 + lane < valid) {
-      sm.xk[r[j]] = k[j];
+      sm.xk[R.r[j]] = R.k[j];
       if constexpr (kExpand) {
-        sm.xg[r[j]] = gi[j];
-        sm.xd[r[j]] = dep[j];
+        sm.xg[R.r[j]] = R.gi[j];
+        sm.xd[R.r[j]] = R.dep[j];
       }
     }
   }
@@ -580,7 +613,7 @@ __device__ __forceinline__ bool rank_and_scatter(const K* __restrict__ kt, const
   if constexpr (kVals) {
 #pragma unroll
     for (int j = 0; j < kItems; ++j)
-      if (kFull || wbase + j * 32 + lane < valid) sm.xv[r[j]] = v[j];
+      if (kFull || wbase + j * 32 + lane < valid) sm.xv[R.r[j]] = v[j];
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
@@ -589,6 +622,19 @@ __device__ __forceinline__ bool rank_and_scatter(const K* __restrict__ kt, const
     }
   }
   return ok;
+}
+
+// Phase 3 for one tile: both halves.
+template <bool kFull, typename S, typename K, bool kVals, bool kExpand, int kBits, int kItems>
+__device__ __forceinline__ bool rank_and_scatter(const K* __restrict__ kt, const uint32_t* __restrict__ vt,
+                                                 uint32_t valid, uint32_t m, const PassArgs& a, bool d31,
+                                                 const Smem<K>& sm, uint32_t* s_warp,
+                                                 const uint32_t* s_vrec, const uint32_t* s_vtile,
+                                                 void* kout_raw, uint32_t* vout) {
+  TileRegs<K, kExpand, kItems> R;
+  rank_tile<kFull, S, K, kExpand, kBits, kItems>(kt, valid, a, d31, sm, R);
+  return scatter_tile<kFull, S, K, kVals, kExpand, kBits, kItems>(vt, valid, m, a, d31, sm, s_warp, s_vrec,
+                                                                  s_vtile, kout_raw, vout, R);
 }
 
 template <typename K, bool kVals, bool kExpand, int kBits, int kThreads, int kItems, int kOcc>
@@ -653,6 +699,67 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
   if (!ok) latch_error(a.err, TDGS_ERR_CAPACITY, kSiteRadixRange);
 }
 
+// Several digit passes in one cooperative launch, for inputs of at most
+// one tile per CTA (chunk size <= kTileKeys).  Each pass ranks the CTA's
+// tile once, publishes the tile's digit counts as its chunk histogram,
+// scans the columns over chunks and scatters: no histogram read, no
+// second load of the keys and no launch between passes.  Buffers
+// ping-pong: pass p reads (k[p % 2], v[p % 2]) and writes the other pair.
+struct ResidentArgs {
+  uint32_t passes;
+  uint32_t shift[kMaxPasses], mask[kMaxPasses];
+};
+
+template <typename K, int kBits, int kThreads, int kItems, int kOcc>
+__global__ void __launch_bounds__(kThreads, kOcc)
+    k_radix_resident(K* __restrict__ k0, uint32_t* __restrict__ v0, K* __restrict__ k1,
+                     uint32_t* __restrict__ v1, PassArgs a, ResidentArgs ra) {
+  using S = PassShape<K, true, false, kBits, kThreads, kItems, kOcc>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  Smem<K> sm;
+  {
+    unsigned char* q = smem;
+    sm.wh = reinterpret_cast<uint16_t*>(q);
+    q += S::kWhBytes;
+    sm.xk = reinterpret_cast<K*>(q);
+    q += S::kXkBytes;
+    sm.xg = sm.xd = nullptr;
+    sm.xv = reinterpret_cast<uint32_t*>(q);
+    q += S::kXvBytes;
+    sm.base = reinterpret_cast<uint32_t*>(q);
+    sm.lstart = sm.base + S::kBins;
+    sm.off = sm.lstart + S::kBins;
+  }
+  __shared__ uint32_t s_warp[S::kWarps];
+  const uint32_t t = threadIdx.x, c = blockIdx.x;
+  const Chunk ch = chunk_of(a);
+  uint32_t valid = ch.end - ch.beg;
+  bool ok = valid <= static_cast<uint32_t>(S::kTileKeys);  // guaranteed by the host
+  if (!ok) valid = S::kTileKeys;
+  {
+    uint4* z = reinterpret_cast<uint4*>(sm.wh);
+    for (uint32_t i = t; i < S::kWhBytes / 16; i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
+  }
+  __syncthreads();
+  for (uint32_t p = 0; p < ra.passes; ++p) {
+    const K* kin = (p & 1) ? k1 : k0;
+    const uint32_t* vin = (p & 1) ? v1 : v0;
+    K* kout = (p & 1) ? k0 : k1;
+    uint32_t* vout = (p & 1) ? v0 : v1;
+    a.shift = ra.shift[p];
+    a.mask = ra.mask[p];
+    TileRegs<K, false, kItems> R;
+    rank_tile<false, S, K, false, kBits, kItems>(kin + ch.beg, valid, a, false, sm, R);
+    for (uint32_t b = t; b < static_cast<uint32_t>(S::kBins); b += kThreads)
+      a.H[static_cast<size_t>(c) * S::kBins + b] = sm.lstart[b];
+    scan_chunks<S::kBins, kThreads>(a, sm.base, s_warp, nullptr);
+    ok &= scatter_tile<false, S, K, true, false, kBits, kItems>(vin + ch.beg, valid, ch.m, a, false, sm, s_warp,
+                                                                 nullptr, nullptr, kout, vout, R);
+    grid_barrier(a.bar, a.err);  // the next pass reads what every CTA wrote
+  }
+  if (!ok) latch_error(a.err, TDGS_ERR_CAPACITY, kSiteRadixRange);
+}
+
 // --------------------------------------------------------------- host side
 struct Kernel {
   const void* fn;     // the __global__ function
@@ -666,6 +773,13 @@ Kernel make_kernel() {
   using S = PassShape<K, kVals, kExpand, kBits, kThreads, kItems, kOcc>;
   return Kernel{reinterpret_cast<const void*>(&k_radix_pass<K, kVals, kExpand, kBits, kThreads, kItems, kOcc>),
                 kBits, kThreads, kItems, S::kSmem, S::kMinBlocks};
+}
+
+template <typename K, int kBits, int kThreads, int kItems, int kOcc>
+Kernel make_resident_kernel() {
+  using S = PassShape<K, true, false, kBits, kThreads, kItems, kOcc>;
+  return Kernel{reinterpret_cast<const void*>(&k_radix_resident<K, kBits, kThreads, kItems, kOcc>), kBits,
+                kThreads, kItems, S::kSmem, kOcc};
 }
 
 // Resident CTAs of `k` on the current device (0 on failure); caches the
@@ -683,6 +797,15 @@ inline size_t scratch_words(const Kernel& k, uint32_t grid) {
 // Launch one pass (cooperative).  scratch: scratch_words() uint32 words.
 cudaError_t launch(const Kernel& k, uint32_t grid, const void* kin, const uint32_t* vin, void* kout,
                    uint32_t* vout, PassArgs a, uint32_t* scratch, cudaStream_t s);
+
+// Grid for the resident kernel `k` over m keys: all resident CTAs (at
+// most kMaxGrid), or 0 if m keys do not fit one tile per CTA.
+uint32_t resident_grid(const Kernel& k, uint32_t m, int ctas_per_sm = 0);
+
+// Launch all passes of a resident kernel (cooperative): k0/v0 hold the
+// input; the result is in (k0, v0) for an even pass count, else (k1, v1).
+cudaError_t launch_resident(const Kernel& k, uint32_t grid, void* k0, uint32_t* v0, void* k1, uint32_t* v1,
+                            PassArgs a, const ResidentArgs& ra, uint32_t* scratch, cudaStream_t s);
 
 }  // namespace radix
 }  // namespace tdgs

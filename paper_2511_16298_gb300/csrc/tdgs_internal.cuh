@@ -180,15 +180,24 @@ cudaError_t launch_views_ranges(const ViewTable& vt, const uint32_t* rmin, const
                                 uint32_t t_all, uint2* ranges, cudaStream_t s);
 
 // Radix passes of the frame path (radix_frame.cu).
-// Depth sort of the N Gaussians: (uint32 depth key, uint32 index), 32 bits.
-// digit_bits 11 (3 passes) or 8 (4 passes) over the 32 bits of the key.
-uint32_t depth_sort_grid(uint32_t n, int digit_bits, int ctas_per_sm);
-size_t depth_sort_scratch_words(int digit_bits, uint32_t grid);
-cudaError_t launch_depth_pass(int digit_bits, uint32_t grid, uint32_t pass, const uint32_t* kin,
-                              const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t n,
-                              uint32_t* scratch, uint32_t* bar, uint32_t* err, cudaStream_t s);
-inline int depth_bits(int tuned) { return tuned == 11 ? 11 : 8; }
-inline uint32_t depth_passes(int tuned) { return depth_bits(tuned) == 8 ? 4u : 3u; }
+// Depth sort of the N Gaussians: (uint32 depth key, uint32 index), all 32
+// key bits, 11-bit (3 passes) or 8-bit (4 passes) digits.  When the
+// Gaussians fit one tile per resident CTA all passes run in one
+// cooperative launch (resident); otherwise one launch per pass.  tuned_bits
+// 0 prefers 8-bit digits.
+struct DepthPlan {
+  bool resident;
+  int bits;
+  uint32_t passes, grid;  // grid 0: the device query failed
+  size_t scratch_words;
+};
+DepthPlan plan_depth_sort(uint32_t n, int tuned_bits, int ctas_per_sm);
+cudaError_t launch_depth_pass(const DepthPlan& dp, uint32_t pass, const uint32_t* kin, const uint32_t* vin,
+                              uint32_t* kout, uint32_t* vout, uint32_t n, uint32_t* scratch, uint32_t* bar,
+                              uint32_t* err, cudaStream_t s);
+// Result in (k0, v0) for an even pass count, else (k1, v1).
+cudaError_t launch_depth_resident(const DepthPlan& dp, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
+                                  uint32_t n, uint32_t* scratch, uint32_t* bar, uint32_t* err, cudaStream_t s);
 // Stable pass over the packed stream on tile bits [shift, shift + width).
 // expand: write the final (local tile << 32 | depth bits) keys and local
 // indices; with rmin/rmax, record each global tile's first/last sorted
