@@ -78,6 +78,7 @@ struct tdgs_context {
   int device = 0;
   DevStatus* d_status = nullptr;
   DevStatus* h_status = nullptr;  // pinned
+  cudaEvent_t ev_total = nullptr;  // recorded after the copy of the early pair count
   uint32_t* d_tickets = nullptr;  // [0] scan tiles, [1] count blocks, [2..3] radix grid barrier
   uint32_t ticket_base[2] = {0, 0};
   Buffer scan_status, sort_scratch;
@@ -386,6 +387,7 @@ tdgs_status tdgs_context_create(tdgs_context** out, int device) {
       cudaMallocHost(&ctx->h_views, sizeof(ViewBlob)) != cudaSuccess ||
       cudaMemset(ctx->d_status, 0, sizeof(DevStatus)) != cudaSuccess ||
       cudaMemset(ctx->d_tickets, 0, 4 * sizeof(uint32_t)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_total, cudaEventDisableTiming) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
     tdgs_context_destroy(ctx);
@@ -444,6 +446,7 @@ void tdgs_context_destroy(tdgs_context* ctx) {
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_tickets) cudaFree(ctx->d_tickets);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  if (ctx->ev_total) cudaEventDestroy(ctx->ev_total);
   delete ctx;
 }
 
@@ -655,7 +658,7 @@ tdgs_status ensure_pair_buffers(tdgs_context* ctx, uint64_t m, cudaStream_t s) {
 
 // Steps before the pair count is known: view table upload, counts, depth
 // sort, scan in depth order (total -> d_status->total).
-tdgs_status run_front(tdgs_context* ctx, cudaStream_t s) {
+tdgs_status run_front(tdgs_context* ctx, cudaStream_t s, bool early_total = false) {
   const ViewTable vt = device_table(ctx);
   const uint32_t n_all = ctx->n_all;
   TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->d_views, ctx->h_views, sizeof(ViewBlob), cudaMemcpyHostToDevice, s));
@@ -663,8 +666,14 @@ tdgs_status run_front(tdgs_context* ctx, cudaStream_t s) {
   uint32_t* dk[2] = {static_cast<uint32_t*>(ctx->f_dkey[0].p), static_cast<uint32_t*>(ctx->f_dkey[1].p)};
   uint32_t* dv[2] = {static_cast<uint32_t*>(ctx->f_dval[0].p), static_cast<uint32_t*>(ctx->f_dval[1].p)};
   TDGS_CUDA(ctx, cudaMemsetAsync(ctx->d_tickets + 1, 0, 4, s));
-  TDGS_TRACED(ctx, kKFrameCount, n_all, s,
-              launch_views_count(vt, n_all, counts, dk[0], dv[0], err_word(ctx), ctx->d_tickets + 1, s));
+  // launched even for zero Gaussians: it writes the view starts and M = 0
+  TDGS_TRACED(ctx, kKFrameCount, n_all ? n_all : 1, s,
+              launch_views_count(vt, n_all, counts, dk[0], dv[0], err_word(ctx), ctx->d_tickets + 1,
+                                 &ctx->d_status->total, s));
+  if (early_total) {  // M (and any latched error) as soon as the count kernel is done
+    TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    TDGS_CUDA(ctx, cudaEventRecord(ctx->ev_total, s));
+  }
   const DepthPlan dp = plan_depth_sort(n_all, ctx->tuning.depth_digit_bits, ctx->tuning.ctas_per_sm);
   const uint32_t dpasses = dp.passes;
   uint32_t* scratch = static_cast<uint32_t*>(ctx->sort_scratch.p);
@@ -751,21 +760,30 @@ tdgs_status run_back(tdgs_context* ctx, uint32_t m, const uint64_t* m_dev, cudaS
   return TDGS_OK;
 }
 
-// Exact mode: one host wait for the pair count (and the per-view counts).
+// Exact mode.  The count kernel already sums the pairs (M), so the host
+// copies M right after it and waits on that copy alone, while the depth
+// sort and the scan run; the back half is then enqueued with the exact M
+// before the GPU runs out of work.
 tdgs_status sort_views_exact(tdgs_context* ctx, cudaStream_t s, uint32_t* m_out) {
   tdgs_status st = ensure_record_buffers(ctx, s);
   if (st != TDGS_OK) return st;
-  st = run_front(ctx, s);
+  st = run_front(ctx, s, true);
   if (st != TDGS_OK) return st;
-  TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
-  TDGS_CUDA(ctx, cudaStreamSynchronize(s));
+  TDGS_CUDA(ctx, cudaEventSynchronize(ctx->ev_total));
   if (ctx->h_status->err) {
+    TDGS_CUDA(ctx, cudaStreamSynchronize(s));
+    TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    TDGS_CUDA(ctx, cudaStreamSynchronize(s));
     const tdgs_status e = static_cast<tdgs_status>(ctx->h_status->err);
     TDGS_CUDA(ctx, cudaMemsetAsync(&ctx->d_status->err, 0, 8, s));
     return fail(ctx, e, std::string("error latched on the device by ") + site_name(ctx->h_status->site));
   }
   const uint64_t total = ctx->h_status->total;
-  if (total > 0xffffffffull) return fail(ctx, TDGS_ERR_OVERFLOW, "pair count above 2^32-1");
+  if (total > 0xffffffffull) {  // the scan latches the same overflow: clear it
+    TDGS_CUDA(ctx, cudaStreamSynchronize(s));
+    TDGS_CUDA(ctx, cudaMemsetAsync(&ctx->d_status->err, 0, 8, s));
+    return fail(ctx, TDGS_ERR_OVERFLOW, "pair count above 2^32-1");
+  }
   const uint32_t m = static_cast<uint32_t>(total);
   st = ensure_pair_buffers(ctx, m, s);
   if (st != TDGS_OK) return st;

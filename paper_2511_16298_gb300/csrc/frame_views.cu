@@ -24,7 +24,7 @@ constexpr int kCountUnroll = 4;
 __global__ void __launch_bounds__(256)
     k_views_count(ViewTable vt, uint32_t n_all, uint32_t* __restrict__ counts,
                   uint32_t* __restrict__ dkey, uint32_t* __restrict__ dval, uint32_t* err,
-                  uint32_t* ticket) {
+                  uint32_t* ticket, uint64_t* total) {
   __shared__ uint32_t s_begin[kMaxViews + 1];
   __shared__ unsigned long long s_tot[kMaxViews];
   __shared__ const float4* s_g[kMaxViews];
@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(256)
         run += s_tot[v];
       }
       vt.pbeg[vt.nv] = static_cast<uint32_t>(run);
+      *total = run;
       *ticket = 0;
     }
   }
@@ -105,10 +106,10 @@ __global__ void __launch_bounds__(256)
 
 cudaError_t launch_views_count(const ViewTable& vt, uint32_t n_all, uint32_t* counts,
                                uint32_t* dkey, uint32_t* dval, uint32_t* err, uint32_t* ticket,
-                               cudaStream_t s) {
+                               uint64_t* total, cudaStream_t s) {
   const uint32_t blocks = (n_all + 256 * kCountUnroll - 1) / (256 * kCountUnroll);
   const uint32_t grid = blocks < 1u ? 1u : (blocks < 152u * 8u ? blocks : 152u * 8u);
-  k_views_count<<<grid, 256, 0, s>>>(vt, n_all, counts, dkey, dval, err, ticket);
+  k_views_count<<<grid, 256, 0, s>>>(vt, n_all, counts, dkey, dval, err, ticket, total);
   return cudaGetLastError();
 }
 

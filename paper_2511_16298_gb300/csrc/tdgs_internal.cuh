@@ -167,10 +167,11 @@ __device__ __forceinline__ uint32_t find_view(const uint32_t* begin, uint32_t nv
 }
 
 // Counts, depth keys and indices of all records, per-view pair totals, and
-// (last block) the first pair of each view.  ticket: a zero word, left zero.
+// (last block) the first pair of each view and the pair count in *total.
+// ticket: a zero word, left zero.
 cudaError_t launch_views_count(const ViewTable& vt, uint32_t n_all, uint32_t* counts,
                                uint32_t* dkey, uint32_t* dval, uint32_t* err, uint32_t* ticket,
-                               cudaStream_t s);
+                               uint64_t* total, cudaStream_t s);
 cudaError_t launch_views_dup(const ViewTable& vt, const uint32_t* sorder, const uint32_t* soff,
                              uint32_t n_all, uint32_t rbits, void* out, bool wide, uint32_t cap,
                              uint32_t* err, cudaStream_t s);

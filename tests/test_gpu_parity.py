@@ -257,6 +257,27 @@ def test_sort_frame_repeated_calls(ctx, oracle):
         _check_frame(ctx, oracle, synth.frame_random(100 + s, 20_000, 500, 300, depth_ties=0.3))
 
 
+def test_sort_frame_changing_counts(ctx, oracle):
+    """Consecutive frames of one shape whose pair counts grow, shrink to
+    zero and grow again stay exact (buffers sized from each frame's own
+    count)."""
+    base = synth.frame_random(300, 20_000, 640, 360, max_sigma=8.0)
+    m_base = _check_frame(ctx, oracle, base)
+    _check_frame(ctx, oracle, synth.frame_random(301, 20_000, 640, 360, max_sigma=8.0))   # fits
+    g3 = base.gaussians.copy()
+    g3["radius"] *= 3  # same shape, several times the pairs
+    m_big = _check_frame(ctx, oracle, synth.Frame(640, 360, g3, "big"))
+    assert m_big > 2 * m_base
+    culled = base.gaussians.copy()
+    culled["radius"] = 0  # same shape, no pairs
+    g = T.records_to_tensor(culled, DEV)
+    for _ in range(2):
+        k, v, r, m = ctx.sort_frame(g, 640, 360)
+        ctx.sync()
+        assert m == 0 and not u32(r).any()
+    _check_frame(ctx, oracle, base)  # from a zero count back to a full frame
+
+
 def test_sort_frame_scene_1m(ctx, oracle):
     m = _check_frame(ctx, oracle, synth.frame_scene(0))
     assert m > 5_000_000
