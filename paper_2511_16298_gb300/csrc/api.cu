@@ -79,11 +79,15 @@ struct tdgs_context {
   DevStatus* d_status = nullptr;
   DevStatus* h_status = nullptr;  // pinned
   cudaEvent_t ev_total = nullptr;  // recorded after the copy of the early pair count
-  uint32_t* d_tickets = nullptr;  // [0] scan tiles, [1] count blocks, [2..3] radix grid barrier
+  uint32_t* d_tickets = nullptr;  // [1] count blocks (reset by the kernel), [2..3] radix grid barrier
   uint32_t ticket_base[2] = {0, 0};
   Buffer scan_status, sort_scratch;
   // fused-frame / multi-view buffers
   Buffer f_counts, f_dkey[2], f_dval[2], f_soff, f_rminmax, f_stream[2], f_keys, f_values, f_ranges;
+  // f_rminmax holds first positions in its first half and one-past-last
+  // positions in its second half, kept at (all ones, zero) between frames:
+  // the ranges kernel resets what the last tile pass recorded
+  bool rminmax_dirty = true;
   ViewBlob* d_views = nullptr;  // device view table
   ViewBlob* h_views = nullptr;  // pinned staging of the table
   uint32_t nv = 0, n_all = 0, t_all = 0;
@@ -232,14 +236,15 @@ tdgs_status traced(tdgs_context* ctx, KernelId id, uint64_t items, cudaStream_t 
 tdgs_status do_scan(tdgs_context* ctx, KernelId id, const uint32_t* counts, const float4* recs,
                     const uint32_t* gather, FrameGeom fg, uint32_t n, uint32_t* offsets,
                     uint64_t* total64, uint32_t* total32, cudaStream_t s) {
+  // scan_status: the tile ticket in word 0, then one status word per tile;
+  // one memset clears both
   const uint32_t tiles = (n + kScanTileItems - 1) / kScanTileItems;
-  tdgs_status st = ensure(ctx, ctx->scan_status, static_cast<size_t>(tiles) * 8, s);
+  tdgs_status st = ensure(ctx, ctx->scan_status, static_cast<size_t>(tiles) * 8 + 8, s);
   if (st != TDGS_OK) return st;
-  TDGS_CUDA(ctx, cudaMemsetAsync(ctx->scan_status.p, 0, static_cast<size_t>(tiles) * 8, s));
-  TDGS_CUDA(ctx, cudaMemsetAsync(ctx->d_tickets + 0, 0, 4, s));
+  TDGS_CUDA(ctx, cudaMemsetAsync(ctx->scan_status.p, 0, static_cast<size_t>(tiles) * 8 + 8, s));
+  uint64_t* words = static_cast<uint64_t*>(ctx->scan_status.p);
   TDGS_TRACED(ctx, id, n, s,
-              launch_scan(counts, recs, gather, fg, n, offsets,
-                          static_cast<uint64_t*>(ctx->scan_status.p), ctx->d_tickets + 0, 0u,
+              launch_scan(counts, recs, gather, fg, n, offsets, words + 1, reinterpret_cast<uint32_t*>(words), 0u,
                           total64, total32, err_word(ctx), s));
   return TDGS_OK;
 }
@@ -625,7 +630,9 @@ tdgs_status ensure_record_buffers(tdgs_context* ctx, cudaStream_t s) {
   for (Buffer* b : {&ctx->f_counts, &ctx->f_dkey[0], &ctx->f_dkey[1], &ctx->f_dval[0],
                     &ctx->f_dval[1], &ctx->f_soff})
     if (st == TDGS_OK) st = ensure(ctx, *b, n4, s);
-  if (st == TDGS_OK) st = ensure(ctx, ctx->f_rminmax, static_cast<size_t>(ctx->t_all) * 8 + 16, s);
+  bool grown = false;
+  if (st == TDGS_OK) st = ensure(ctx, ctx->f_rminmax, static_cast<size_t>(ctx->t_all) * 8 + 16, s, &grown);
+  if (grown) ctx->rminmax_dirty = true;
   if (st == TDGS_OK) st = ensure(ctx, ctx->f_ranges, static_cast<size_t>(ctx->t_all) * 8 + 16, s);
   const uint32_t n_all = ctx->n_all;
   const uint32_t tiles = (n_all + kScanTileItems - 1) / kScanTileItems;
@@ -665,7 +672,6 @@ tdgs_status run_front(tdgs_context* ctx, cudaStream_t s, bool early_total = fals
   uint32_t* counts = static_cast<uint32_t*>(ctx->f_counts.p);
   uint32_t* dk[2] = {static_cast<uint32_t*>(ctx->f_dkey[0].p), static_cast<uint32_t*>(ctx->f_dkey[1].p)};
   uint32_t* dv[2] = {static_cast<uint32_t*>(ctx->f_dval[0].p), static_cast<uint32_t*>(ctx->f_dval[1].p)};
-  TDGS_CUDA(ctx, cudaMemsetAsync(ctx->d_tickets + 1, 0, 4, s));
   // launched even for zero Gaussians: it writes the view starts and M = 0
   TDGS_TRACED(ctx, kKFrameCount, n_all ? n_all : 1, s,
               launch_views_count(vt, n_all, counts, dk[0], dv[0], err_word(ctx), ctx->d_tickets + 1,
@@ -710,8 +716,9 @@ tdgs_status run_back(tdgs_context* ctx, uint32_t m, const uint64_t* m_dev, cudaS
   uint32_t* scratch = static_cast<uint32_t*>(ctx->sort_scratch.p);
   uint32_t* bar = ctx->d_tickets + 2;
   void* st[2] = {ctx->f_stream[0].p, ctx->f_stream[1].p};
+  const size_t half = ctx->f_rminmax.bytes / 8;  // tiles the buffer holds
   uint32_t* rmin = static_cast<uint32_t*>(ctx->f_rminmax.p);
-  uint32_t* rmax = rmin + ctx->t_all;
+  uint32_t* rmax = rmin + half;
   TDGS_TRACED(ctx, kKDupDepth, m ? n_all : 0, s,
               launch_views_dup(vt, sorder, static_cast<uint32_t*>(ctx->f_soff.p), n_all, sh.rbits, st[0],
                                sh.wide, m, err_word(ctx), s));
@@ -725,8 +732,11 @@ tdgs_status run_back(tdgs_context* ctx, uint32_t m, const uint64_t* m_dev, cudaS
     return TDGS_OK;
   }
   if (!single) {
-    TDGS_CUDA(ctx, cudaMemsetAsync(rmin, 0xff, static_cast<size_t>(ctx->t_all) * 4, s));
-    TDGS_CUDA(ctx, cudaMemsetAsync(rmax, 0, static_cast<size_t>(ctx->t_all) * 4, s));
+    if (ctx->rminmax_dirty) {
+      TDGS_CUDA(ctx, cudaMemsetAsync(rmin, 0xff, half * 4, s));
+      TDGS_CUDA(ctx, cudaMemsetAsync(rmax, 0, half * 4, s));
+    }
+    ctx->rminmax_dirty = true;  // until the ranges kernel below is enqueued
   }
   uint32_t shift = sh.rbits;
   for (uint32_t p = 0; p < sh.npass; ++p) {
@@ -755,8 +765,10 @@ tdgs_status run_back(tdgs_context* ctx, uint32_t m, const uint64_t* m_dev, cudaS
     TDGS_TRACED(ctx, last ? kKTileExpand : kKTilePass, m, s, launch_stream_pass(sp, scratch, bar, err_word(ctx), s));
     shift += width;
   }
-  if (!single)
+  if (!single) {
     TDGS_TRACED(ctx, kKRangesFinal, ctx->t_all, s, launch_views_ranges(vt, rmin, rmax, ctx->t_all, ranges, s));
+    ctx->rminmax_dirty = false;
+  }
   return TDGS_OK;
 }
 
