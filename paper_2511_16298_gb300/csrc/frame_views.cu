@@ -114,16 +114,32 @@ cudaError_t launch_views_count(const ViewTable& vt, uint32_t n_all, uint32_t* co
 }
 
 // Duplicate in depth order: depth position j is record sorder[j]; its
-// pairs start at soff[j]; each is (global tile << rbits) | j.  Warp-level
-// load-balanced expansion over windows of 32 consecutive pairs: every
-// Gaussian of the warp's 32 depth positions publishes its rectangle in
-// shared memory and, when its first pair falls in the window, its lane at
-// that window position; lane l of the window finds the owner of pair l as
-// the nearest start at or before l (one OR-reduction and a count of
-// leading zeros), or the owner carried over from the previous window.
-// The row of a pair inside its rectangle is jj / width, from a float
-// reciprocal corrected by one step (exact for jj < 2^22), else an integer
-// division.  Rows are outer, columns inner.
+// pairs start at soff[j]; each is (global tile << rbits) | j.  A warp owns
+// 32 consecutive depth positions; their pairs are consecutive in the
+// output.  Lane l of a window writes the 4 pairs of quad l (quads are
+// aligned to 4 output elements, so whole quads are one 16-byte store): it
+// finds the owner of its first pair by a binary search over the warp's
+// 32 starts in shared memory, splits that pair's index inside the
+// rectangle into row and column once (float reciprocal with one exact
+// correction step, or an integer division past 2^22), then steps column
+// by column, wrapping rows and moving to the next Gaussian when its pairs
+// are done.  Rows are outer, columns inner.
+template <typename K>
+__device__ __forceinline__ void store_quad(K* dst, const K (&e)[4], uint32_t valid_mask) {
+  if (valid_mask == 0xfu) {
+    if constexpr (sizeof(K) == 4) {
+      *reinterpret_cast<uint4*>(dst) = make_uint4(e[0], e[1], e[2], e[3]);
+    } else {
+      reinterpret_cast<ulonglong2*>(dst)[0] = make_ulonglong2(e[0], e[1]);
+      reinterpret_cast<ulonglong2*>(dst)[1] = make_ulonglong2(e[2], e[3]);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (valid_mask & (1u << i)) dst[i] = e[i];
+  }
+}
+
 template <typename K>
 __global__ void __launch_bounds__(256)
     k_views_dup(ViewTable vt, const uint32_t* __restrict__ sorder,
@@ -133,11 +149,14 @@ __global__ void __launch_bounds__(256)
   __shared__ const float4* s_g[kMaxViews];
   __shared__ FrameGeom s_geom[kMaxViews];
   __shared__ uint32_t s_tb[kMaxViews];
-  // per warp and lane: {first pair - warp's first pair, global id of the
-  // rectangle's first tile, width in tiles, bits of 1 / width}; tiles per row
-  __shared__ uint4 s_info[8][32];
+  // per warp and lane: first pair relative to the warp's first pair
+  // (non-decreasing; [32] = end of the warp's range), global id of the
+  // rectangle's first tile, width, 1 / width, tiles per row of the view
+  __shared__ uint32_t s_st[8][33];
+  __shared__ uint32_t s_first[8][32];
+  __shared__ uint32_t s_w[8][32];
+  __shared__ float s_rw[8][32];
   __shared__ uint32_t s_gx[8][32];
-  __shared__ uint32_t s_at[8][32];  // lane whose pairs start at a window position
   for (uint32_t v = threadIdx.x; v <= vt.nv; v += blockDim.x) s_begin[v] = vt.rec_begin[v];
   for (uint32_t v = threadIdx.x; v < vt.nv; v += blockDim.x) {
     s_g[v] = vt.g[v];
@@ -171,52 +190,85 @@ __global__ void __launch_bounds__(256)
     const uint64_t end_max = __shfl_sync(0xffffffffu, start + q.count, last);
     if (end_max > cap) over = true;
     // Positions relative to the warp's first pair, in 32 bits; pairs at or
-    // beyond cap are not written, and the window loop cannot wrap.
+    // beyond cap are not written.
     const uint64_t begin = __shfl_sync(0xffffffffu, start, 0);
     const uint64_t stop = end_max < cap ? end_max : cap;
     const uint64_t span = stop > begin ? stop - begin : 0;
-    const uint32_t nrel = span < 0xffffffe0ull ? static_cast<uint32_t>(span) : 0xffffffe0u;
+    const uint32_t nrel = span < 0xfffffff0ull ? static_cast<uint32_t>(span) : 0xfffffff0u;
     const uint64_t srel64 = start - begin;
-    const uint32_t srel = (q.count > 0 && srel64 < nrel) ? static_cast<uint32_t>(srel64) : 0xffffffffu;
     const uint32_t wd = static_cast<uint32_t>(q.x1 - q.x0);
-    s_info[w8][lane] = make_uint4(srel, first, wd, __float_as_uint(wd ? __frcp_rn(static_cast<float>(wd)) : 0.0f));
+    s_st[w8][lane] = (j < n_all && srel64 < nrel) ? static_cast<uint32_t>(srel64) : nrel;
+    if (lane == 0) s_st[w8][32] = nrel;
+    s_first[w8][lane] = first;
+    s_w[w8][lane] = wd;
+    s_rw[w8][lane] = wd ? __frcp_rn(static_cast<float>(wd)) : 0.0f;
     s_gx[w8][lane] = gx;
-    // rows from the float reciprocal need jj < 2^22 (one correction step)
-    const bool exact_div = __any_sync(0xffffffffu, q.count > (1u << 22));
-    K* wout = out + begin;
-    const uint32_t rank0 = wg * 32u;
-    uint32_t carry = 0;
     __syncwarp();
-    for (uint32_t c = 0; c < nrel; c += 32) {
-      // window positions where a Gaussian's pairs begin
-      const uint32_t at = srel - c;
-      const bool here = at < 32u;
-      if (here) s_at[w8][at] = lane;
-      const uint32_t starts = __reduce_or_sync(0xffffffffu, here ? 1u << at : 0u);
-      __syncwarp();
-      const uint32_t upto = starts & (0xffffffffu >> (31u - lane));  // positions <= lane
-      const uint32_t owner = upto ? s_at[w8][31u - __clz(upto)] : carry;
-      const uint32_t p = c + lane;
-      const uint4 in = s_info[w8][owner];
-      const uint32_t jj = p - in.x;
-      const uint32_t ow = in.z;
-      uint32_t ry = __float2uint_rz(__fmul_rn(__uint2float_rn(jj), __uint_as_float(in.w)));
-      uint32_t rx = jj - ry * ow;
-      const bool under = static_cast<int32_t>(rx) < 0;
-      ry = under ? ry - 1u : ry;
-      rx = under ? rx + ow : rx;
-      const bool past = rx >= ow;
-      ry = past ? ry + 1u : ry;
-      rx = past ? rx - ow : rx;
-      if (exact_div && ow) {
-        ry = jj / ow;
-        rx = jj - ry * ow;
+    const uint32_t lead = static_cast<uint32_t>(begin & 3u);  // quads are aligned to 4 output elements
+    const uint32_t nquad = (nrel + lead + 3u) / 4u;
+    K* qout = out + (begin - lead);
+    const uint32_t rank0 = wg * 32u;
+    for (uint32_t q0 = 0; q0 < nquad; q0 += 32) {
+      const uint32_t qi = q0 + lane;
+      if (qi < nquad) {
+        // relative position of the quad's first element (may be < 0 in the first quad)
+        const int64_t r0 = static_cast<int64_t>(qi) * 4 - lead;
+        const uint32_t x = r0 < 0 ? 0u : static_cast<uint32_t>(r0);
+        uint32_t owner = 0;
+#pragma unroll
+        for (uint32_t step = 16; step > 0; step >>= 1)
+          if (s_st[w8][owner + step] <= x) owner += step;
+        // row and column of pair x inside the owner's rectangle
+        uint32_t ow = s_w[w8][owner];
+        const uint32_t jj = x - s_st[w8][owner];
+        uint32_t ry, rx;
+        if (jj < (1u << 22)) {
+          ry = __float2uint_rz(__fmul_rn(__uint2float_rn(jj), s_rw[w8][owner]));
+          rx = jj - ry * ow;
+          if (static_cast<int32_t>(rx) < 0) {
+            --ry;
+            rx += ow;
+          } else if (rx >= ow) {
+            ++ry;
+            rx -= ow;
+          }
+        } else {
+          ry = jj / ow;
+          rx = jj - ry * ow;
+        }
+        uint32_t ogx = s_gx[w8][owner];
+        uint32_t row = s_first[w8][owner] + ry * ogx;
+        uint32_t next = s_st[w8][owner + 1];
+        K e[4];
+        uint32_t valid = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int64_t r = r0 + i;
+          e[i] = K(0);
+          if (r >= 0 && r < static_cast<int64_t>(nrel)) {
+            const uint32_t ru = static_cast<uint32_t>(r);
+            while (next <= ru) {  // the owner's pairs are done: the next Gaussian with pairs
+              ++owner;
+              next = s_st[w8][owner + 1];
+              if (next > ru) {
+                ow = s_w[w8][owner];
+                ogx = s_gx[w8][owner];
+                row = s_first[w8][owner];
+                rx = 0;
+              }
+            }
+            e[i] = (static_cast<K>(row + rx) << rbits) | static_cast<K>(rank0 + owner);
+            valid |= 1u << i;
+            if (++rx == ow) {
+              rx = 0;
+              row += ogx;
+            }
+          }
+        }
+        store_quad<K>(qout + static_cast<size_t>(qi) * 4, e, valid);
       }
-      const uint32_t tile = in.y + ry * s_gx[w8][owner] + rx;
-      if (p < nrel) wout[p] = (static_cast<K>(tile) << rbits) | static_cast<K>(rank0 + owner);
-      carry = __shfl_sync(0xffffffffu, owner, 31);
-      __syncwarp();
     }
+    __syncwarp();
   }
   if (__any_sync(0xffffffffu, over) && lane == 0) latch_error(err, TDGS_ERR_CAPACITY, kSiteViewsDup);
 }
