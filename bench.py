@@ -163,6 +163,20 @@ def algorithmic_bytes(kernel: str, items: int, n: int, m: int, tiles: int) -> fl
     return 0.0
 
 
+def combine_ranks(dist, seconds: float, units: float, device) -> tuple[float, float]:
+    """Whole-job figures over the ranks of a replica run: the slowest rank's
+    time and the units (pairs) all ranks processed.  Without a process group
+    the rank's own figures."""
+    if not dist:
+        return seconds, units
+    import torch
+    t_max = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u_sum = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u_sum, op=dist.ReduceOp.SUM)
+    return float(t_max.item()), float(u_sum.item())
+
+
 # --------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local_rank, dist):
     import torch
@@ -219,14 +233,7 @@ def run_ours(args, rank, world, local_rank, dist):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     dev_s = sum(step_ms) / 1e3
     pairs = m * args.steps
-    if dist:
-        t = torch.tensor([dev_s, float(pairs)], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-        dev_s_max, pairs_all = float(tmax[0]), float(t[1])
-    else:
-        dev_s_max, pairs_all = dev_s, float(pairs)
+    dev_s_max, pairs_all = combine_ranks(dist, dev_s, float(pairs), dev)
     value = pairs_all / dev_s_max
 
     # ---- per-kernel live timings -> roofline of the dominant kernel
@@ -326,11 +333,7 @@ def run_ours(args, rank, world, local_rank, dist):
             if i >= args.warmup:
                 pairs_e2e += mm
         e2e_s = time.perf_counter() - te
-        if dist:
-            t = torch.tensor([e2e_s, float(pairs_e2e)], dtype=torch.float64, device=dev)
-            dist.all_reduce(t[0:1], op=dist.ReduceOp.MAX)
-            dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-            e2e_s, pairs_e2e = float(t[0]), float(t[1])
+        e2e_s, pairs_e2e = combine_ranks(dist, e2e_s, float(pairs_e2e), dev)
         e2e = {"value": pairs_e2e / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": 16 * n,
                "d2h_bytes_per_step": 12 * m + 8 * T, "ms_per_step": round(e2e_s / args.steps * 1e3, 4)}
         ok = (np.array_equal(h_v[:m].numpy(), v.cpu().numpy()))
