@@ -128,12 +128,14 @@ def profiled_traffic(kernel: str):
     return float(tr.group(1)), int(items.group(1)) if items else None
 
 
-def algorithmic_bytes(kernel: str, items: int, n: int, m: int, tiles: int) -> float:
+def algorithmic_bytes(kernel: str, items: int, n: int, m: int, tiles: int, depth_passes: int = 1) -> float:
     """Minimum DRAM bytes of one launch (reads + writes), per kernel.
     items = the units the launch processed (Gaussians, pairs or tiles, as
     the library's tracer reports them); n, m, tiles = the frame's sizes.
     The fused-frame figures assume the packed (tile, depth rank) element
-    fits 32 bits, which holds for every single-frame workload timed here."""
+    fits 32 bits, which holds for every single-frame workload timed here.
+    depth_passes: digit passes one depth_sort launch ran (several in the
+    single-launch form, one per launch otherwise)."""
     # the five separate steps
     if kernel == "count_tiles":      # record in (16 B), count out (4 B)
         return 20.0 * items
@@ -148,8 +150,8 @@ def algorithmic_bytes(kernel: str, items: int, n: int, m: int, tiles: int) -> fl
     # fused frame
     if kernel == "frame_count":      # record in; count, depth key, index out
         return 28.0 * items
-    if kernel == "depth_sort":       # (u32 key, u32 index) in and out
-        return 16.0 * items
+    if kernel == "depth_sort":       # (u32 key, u32 index) in and out, per pass
+        return 16.0 * items * depth_passes
     if kernel == "scan_by_depth":    # index in, gathered count, offset out
         return 12.0 * items
     if kernel == "duplicate_by_depth":  # index, offset, record in; 4 B per pair out
@@ -230,6 +232,8 @@ def run_ours(args, rank, world, local_rank, dist):
     ctx.sync()
     ktimes = ctx.kernel_times()
     ctx.enable_timing(False)
+    dsl = ktimes.get("depth_sort", {}).get("launches", 0)
+    depth_passes = ctx.depth_passes() if dsl == args.steps else 1
     step_ms = [a.elapsed_time(b) for a, b in ev]
     dev_s = sum(step_ms) / 1e3
     pairs = m * args.steps
@@ -242,7 +246,7 @@ def run_ours(args, rank, world, local_rank, dist):
     for name, d in ktimes.items():
         per_launch_items = d["items"] / max(1, d["launches"])
         ms = d["ms"] / max(1, d["launches"])
-        ab = algorithmic_bytes(name, per_launch_items, n, m, T)
+        ab = algorithmic_bytes(name, per_launch_items, n, m, T, depth_passes)
         kernels[name] = {"launches": d["launches"], "avg_ms": round(ms, 5),
                          "share": None, "gbs": round(ab / (ms * 1e-3) / 1e9, 1) if ms > 0 else None}
     tot_ms = sum(d["ms"] for d in ktimes.values())
@@ -254,7 +258,7 @@ def run_ours(args, rank, world, local_rank, dist):
         d = ktimes[dom]
         per_items = d["items"] / d["launches"]
         ms = d["ms"] / d["launches"]
-        ab = algorithmic_bytes(dom, per_items, n, m, T)
+        ab = algorithmic_bytes(dom, per_items, n, m, T, depth_passes)
         ach = ab / (ms * 1e-3) / 1e9
         tr = profiled_traffic(dom)
         traffic = None
@@ -346,7 +350,8 @@ def run_ours(args, rank, world, local_rank, dist):
         "latency_ms": {"p50": round(statistics.median(step_ms), 4),
                        "p99": round(float(np.percentile(step_ms, 99)), 4),
                        "wall_ms_per_step": round(wall / args.steps * 1e3, 4)},
-        "pairs_per_frame": m, "n": n, "tiles": T, "kernels": kernels, "roofline": roof,
+        "pairs_per_frame": m, "n": n, "tiles": T, "depth_passes": depth_passes, "kernels": kernels,
+        "roofline": roof,
         "sort_pairs": sort_only, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(),
     }

@@ -160,6 +160,11 @@ uint64_t tdgs_context_launch_count(const tdgs_context* ctx);
 tdgs_status tdgs_context_enable_timing(tdgs_context* ctx, int enable);
 int tdgs_context_kernel_times(tdgs_context* ctx, tdgs_kernel_time* out, int max);
 
+/* Digit passes the last single-launch depth sort of the fused frame ran on
+ * this context (the count follows the frame's depth range: 1 to 4), or 0
+ * if none has run.  Waits for the work on `stream`. */
+tdgs_status tdgs_context_depth_passes(tdgs_context* ctx, int* passes, void* stream);
+
 /* ------------------------------------------------------- the five steps --- */
 
 /* Step 1 (Sec. II-A: each projected Gaussian is represented by the

@@ -83,7 +83,10 @@ struct tdgs_context {
   uint32_t ticket_base[2] = {0, 0};
   Buffer scan_status, sort_scratch;
   // fused-frame / multi-view buffers
-  Buffer f_counts, f_dkey[2], f_dval[2], f_soff, f_rminmax, f_stream[2], f_keys, f_values, f_ranges;
+  Buffer f_counts, f_dkey[3], f_dval[3], f_soff, f_rminmax, f_stream[2], f_keys, f_values, f_ranges;
+  // depth-key range: accumulators [0..1], result [2..3], passes of the last
+  // resident depth sort [4]
+  uint32_t* d_range = nullptr;
   // f_rminmax holds first positions in its first half and one-past-last
   // positions in its second half, kept at (all ones, zero) between frames:
   // the ranges kernel resets what the last tile pass recorded
@@ -387,6 +390,9 @@ tdgs_status tdgs_context_create(tdgs_context** out, int device) {
   ctx->device = device;
   if (cudaMalloc(&ctx->d_status, sizeof(DevStatus)) != cudaSuccess ||
       cudaMalloc(&ctx->d_tickets, 4 * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_range, 8 * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMemset(ctx->d_range, 0, 8 * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMemset(ctx->d_range, 0xff, sizeof(uint32_t)) != cudaSuccess ||
       cudaMallocHost(&ctx->h_status, sizeof(DevStatus)) != cudaSuccess ||
       cudaMalloc(&ctx->d_views, sizeof(ViewBlob)) != cudaSuccess ||
       cudaMallocHost(&ctx->h_views, sizeof(ViewBlob)) != cudaSuccess ||
@@ -409,6 +415,17 @@ tdgs_status tdgs_context_enable_timing(tdgs_context* ctx, int enable) {
   DeviceGuard g(ctx->device);
   clear_timings(ctx);
   ctx->timing = enable != 0;
+  return TDGS_OK;
+}
+
+tdgs_status tdgs_context_depth_passes(tdgs_context* ctx, int* passes, void* stream) {
+  if (!ctx || !passes) return TDGS_ERR_INVALID_ARGUMENT;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t v = 0;
+  TDGS_CUDA(ctx, cudaMemcpyAsync(&v, ctx->d_range + 4, 4, cudaMemcpyDeviceToHost, s));
+  TDGS_CUDA(ctx, cudaStreamSynchronize(s));
+  *passes = static_cast<int>(v);
   return TDGS_OK;
 }
 
@@ -441,7 +458,8 @@ void tdgs_context_destroy(tdgs_context* ctx) {
   drain_timings(ctx);
   for (cudaEvent_t e : ctx->free_events) cudaEventDestroy(e);
   Buffer* bufs[] = {&ctx->scan_status, &ctx->sort_scratch, &ctx->f_counts,    &ctx->f_dkey[0],
-                    &ctx->f_dkey[1],    &ctx->f_dval[0],     &ctx->f_dval[1],    &ctx->f_soff,
+                    &ctx->f_dkey[1],    &ctx->f_dkey[2],     &ctx->f_dval[0],    &ctx->f_dval[1],
+                    &ctx->f_dval[2],    &ctx->f_soff,
                     &ctx->f_rminmax,    &ctx->f_stream[0],   &ctx->f_stream[1],  &ctx->f_keys,
                     &ctx->f_values,     &ctx->f_ranges};
   if (ctx->d_views) cudaFree(ctx->d_views);
@@ -450,6 +468,7 @@ void tdgs_context_destroy(tdgs_context* ctx) {
     if (b->p) cudaFree(b->p);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_tickets) cudaFree(ctx->d_tickets);
+  if (ctx->d_range) cudaFree(ctx->d_range);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   if (ctx->ev_total) cudaEventDestroy(ctx->ev_total);
   delete ctx;
@@ -627,8 +646,8 @@ Shape shape_of(const tdgs_context* ctx) {
 tdgs_status ensure_record_buffers(tdgs_context* ctx, cudaStream_t s) {
   const size_t n4 = static_cast<size_t>(ctx->n_all) * 4 + 16;
   tdgs_status st = TDGS_OK;
-  for (Buffer* b : {&ctx->f_counts, &ctx->f_dkey[0], &ctx->f_dkey[1], &ctx->f_dval[0],
-                    &ctx->f_dval[1], &ctx->f_soff})
+  for (Buffer* b : {&ctx->f_counts, &ctx->f_dkey[0], &ctx->f_dkey[1], &ctx->f_dkey[2], &ctx->f_dval[0],
+                    &ctx->f_dval[1], &ctx->f_dval[2], &ctx->f_soff})
     if (st == TDGS_OK) st = ensure(ctx, *b, n4, s);
   bool grown = false;
   if (st == TDGS_OK) st = ensure(ctx, ctx->f_rminmax, static_cast<size_t>(ctx->t_all) * 8 + 16, s, &grown);
@@ -670,12 +689,14 @@ tdgs_status run_front(tdgs_context* ctx, cudaStream_t s, bool early_total = fals
   const uint32_t n_all = ctx->n_all;
   TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->d_views, ctx->h_views, sizeof(ViewBlob), cudaMemcpyHostToDevice, s));
   uint32_t* counts = static_cast<uint32_t*>(ctx->f_counts.p);
-  uint32_t* dk[2] = {static_cast<uint32_t*>(ctx->f_dkey[0].p), static_cast<uint32_t*>(ctx->f_dkey[1].p)};
-  uint32_t* dv[2] = {static_cast<uint32_t*>(ctx->f_dval[0].p), static_cast<uint32_t*>(ctx->f_dval[1].p)};
+  uint32_t* dk[3] = {static_cast<uint32_t*>(ctx->f_dkey[0].p), static_cast<uint32_t*>(ctx->f_dkey[1].p),
+                     static_cast<uint32_t*>(ctx->f_dkey[2].p)};
+  uint32_t* dv[3] = {static_cast<uint32_t*>(ctx->f_dval[0].p), static_cast<uint32_t*>(ctx->f_dval[1].p),
+                     static_cast<uint32_t*>(ctx->f_dval[2].p)};
   // launched even for zero Gaussians: it writes the view starts and M = 0
   TDGS_TRACED(ctx, kKFrameCount, n_all ? n_all : 1, s,
               launch_views_count(vt, n_all, counts, dk[0], dv[0], err_word(ctx), ctx->d_tickets + 1,
-                                 &ctx->d_status->total, s));
+                                 &ctx->d_status->total, ctx->d_range, s));
   if (early_total) {  // M (and any latched error) as soon as the count kernel is done
     TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     TDGS_CUDA(ctx, cudaEventRecord(ctx->ev_total, s));
@@ -683,10 +704,10 @@ tdgs_status run_front(tdgs_context* ctx, cudaStream_t s, bool early_total = fals
   const DepthPlan dp = plan_depth_sort(n_all, ctx->tuning.depth_digit_bits, ctx->tuning.ctas_per_sm);
   const uint32_t dpasses = dp.passes;
   uint32_t* scratch = static_cast<uint32_t*>(ctx->sort_scratch.p);
-  if (dp.resident) {
-    TDGS_TRACED(ctx, kKDepthSort, static_cast<uint64_t>(n_all) * dpasses, s,
-                launch_depth_resident(dp, dk[0], dv[0], dk[1], dv[1], n_all, scratch, ctx->d_tickets + 2,
-                                      err_word(ctx), s));
+  if (dp.resident) {  // one launch; its pass count follows the depth range
+    TDGS_TRACED(ctx, kKDepthSort, n_all, s,
+                launch_depth_resident(dp, dk[0], dv[0], dk[1], dv[1], dk[2], dv[2], ctx->d_range + 2, n_all,
+                                      scratch, ctx->d_tickets + 2, err_word(ctx), s));
   } else {
     for (uint32_t p = 0; p < dpasses; ++p) {
       TDGS_TRACED(ctx, kKDepthSort, n_all, s,
@@ -695,7 +716,7 @@ tdgs_status run_front(tdgs_context* ctx, cudaStream_t s, bool early_total = fals
     }
   }
   if (n_all) {
-    tdgs_status st = do_scan(ctx, kKFrameScan, counts, nullptr, dv[dpasses & 1], FrameGeom{}, n_all,
+    tdgs_status st = do_scan(ctx, kKFrameScan, counts, nullptr, dv[dp.result], FrameGeom{}, n_all,
                              static_cast<uint32_t*>(ctx->f_soff.p), &ctx->d_status->total, nullptr, s);
     if (st != TDGS_OK) return st;
   } else {
@@ -710,9 +731,9 @@ tdgs_status run_back(tdgs_context* ctx, uint32_t m, const uint64_t* m_dev, cudaS
   const ViewTable vt = device_table(ctx);
   const Shape sh = shape_of(ctx);
   const uint32_t n_all = ctx->n_all;
-  const uint32_t dpasses = plan_depth_sort(n_all, ctx->tuning.depth_digit_bits, ctx->tuning.ctas_per_sm).passes;
-  const uint32_t* sdepth = static_cast<uint32_t*>(ctx->f_dkey[dpasses & 1].p);
-  const uint32_t* sorder = static_cast<uint32_t*>(ctx->f_dval[dpasses & 1].p);
+  const uint32_t dres = plan_depth_sort(n_all, ctx->tuning.depth_digit_bits, ctx->tuning.ctas_per_sm).result;
+  const uint32_t* sdepth = static_cast<uint32_t*>(ctx->f_dkey[dres].p);
+  const uint32_t* sorder = static_cast<uint32_t*>(ctx->f_dval[dres].p);
   uint32_t* scratch = static_cast<uint32_t*>(ctx->sort_scratch.p);
   uint32_t* bar = ctx->d_tickets + 2;
   void* st[2] = {ctx->f_stream[0].p, ctx->f_stream[1].p};

@@ -19,25 +19,34 @@ namespace tdgs {
 // sort last), the record index, and the per-view pair totals.  The last
 // block to finish turns the totals into pbeg (first pair of each view in
 // the sorted list; views are contiguous there because global tile ids are
-// view-major) and resets the ticket.
+// view-major), writes the pair count M to *total and resets the ticket.
+// range[0..1] accumulate the smallest and largest depth key of a Gaussian
+// with pairs (reset to all ones / zero by the last block, which publishes
+// them in range[2..3] for the depth sort).
 constexpr int kCountUnroll = 4;
 __global__ void __launch_bounds__(256)
     k_views_count(ViewTable vt, uint32_t n_all, uint32_t* __restrict__ counts,
                   uint32_t* __restrict__ dkey, uint32_t* __restrict__ dval, uint32_t* err,
-                  uint32_t* ticket, uint64_t* total) {
+                  uint32_t* ticket, uint64_t* total, uint32_t* range) {
   __shared__ uint32_t s_begin[kMaxViews + 1];
   __shared__ unsigned long long s_tot[kMaxViews];
   __shared__ const float4* s_g[kMaxViews];
   __shared__ FrameGeom s_geom[kMaxViews];
   __shared__ bool s_last;
+  __shared__ uint32_t s_lo, s_hi;
   for (uint32_t v = threadIdx.x; v <= vt.nv; v += blockDim.x) s_begin[v] = vt.rec_begin[v];
   for (uint32_t v = threadIdx.x; v < vt.nv; v += blockDim.x) {
     s_tot[v] = 0;
     s_g[v] = vt.g[v];
     s_geom[v] = vt.geom[v];
   }
+  if (threadIdx.x == 0) {
+    s_lo = 0xffffffffu;
+    s_hi = 0u;
+  }
   __syncthreads();
   bool bad = false;
+  uint32_t lo = 0xffffffffu, hi = 0u;  // depth keys of Gaussians with pairs
   const uint32_t lane = lane_id();
   const uint32_t stride = gridDim.x * blockDim.x;
   // warp-uniform loop so the per-view totals can be reduced across the
@@ -65,8 +74,13 @@ __global__ void __launch_bounds__(256)
         bad |= q.invalid;
         cnt = q.count;
         counts[i] = q.count;
-        dkey[i] = q.count ? __float_as_uint(rec[u].z) : 0xffffffffu;
+        const uint32_t key = q.count ? __float_as_uint(rec[u].z) : 0xffffffffu;
+        dkey[i] = key;
         dval[i] = i;
+        if (q.count) {
+          lo = min(lo, key);
+          hi = max(hi, key);
+        }
       }
       const uint32_t v0 = __shfl_sync(0xffffffffu, v, 0);
       if (__all_sync(0xffffffffu, v == v0 || i >= n_all)) {
@@ -80,9 +94,19 @@ __global__ void __launch_bounds__(256)
     }
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) latch_error(err, TDGS_ERR_INVALID_ARGUMENT, kSiteViewsCount);
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  if (lane == 0) {
+    atomicMin(&s_lo, lo);
+    atomicMax(&s_hi, hi);
+  }
   __syncthreads();
   for (uint32_t v = threadIdx.x; v < vt.nv; v += blockDim.x)
     if (s_tot[v]) atomicAdd(reinterpret_cast<unsigned long long*>(vt.vtot + v), s_tot[v]);
+  if (threadIdx.x == 0) {
+    if (s_lo != 0xffffffffu) atomicMin(range, s_lo);
+    if (s_hi != 0u) atomicMax(range + 1, s_hi);
+  }
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
@@ -99,6 +123,10 @@ __global__ void __launch_bounds__(256)
       }
       vt.pbeg[vt.nv] = static_cast<uint32_t>(run);
       *total = run;
+      range[2] = __ldcg(range);
+      range[3] = __ldcg(range + 1);
+      range[0] = 0xffffffffu;
+      range[1] = 0u;
       *ticket = 0;
     }
   }
@@ -106,10 +134,10 @@ __global__ void __launch_bounds__(256)
 
 cudaError_t launch_views_count(const ViewTable& vt, uint32_t n_all, uint32_t* counts,
                                uint32_t* dkey, uint32_t* dval, uint32_t* err, uint32_t* ticket,
-                               uint64_t* total, cudaStream_t s) {
+                               uint64_t* total, uint32_t* range, cudaStream_t s) {
   const uint32_t blocks = (n_all + 256 * kCountUnroll - 1) / (256 * kCountUnroll);
   const uint32_t grid = blocks < 1u ? 1u : (blocks < 152u * 8u ? blocks : 152u * 8u);
-  k_views_count<<<grid, 256, 0, s>>>(vt, n_all, counts, dkey, dval, err, ticket, total);
+  k_views_count<<<grid, 256, 0, s>>>(vt, n_all, counts, dkey, dval, err, ticket, total, range);
   return cudaGetLastError();
 }
 

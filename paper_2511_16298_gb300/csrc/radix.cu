@@ -84,15 +84,16 @@ uint32_t resident_grid(const Kernel& k, uint32_t m, int ctas_per_sm) {
 }
 
 cudaError_t launch_resident(const Kernel& k, uint32_t grid, void* k0, uint32_t* v0, void* k1, uint32_t* v1,
-                            PassArgs a, const ResidentArgs& ra, uint32_t* scratch, cudaStream_t s) {
-  if (a.m == 0 || ra.passes == 0) return cudaSuccess;
+                            void* k2, uint32_t* v2, PassArgs a, const ResidentArgs& ra, uint32_t* scratch,
+                            cudaStream_t s) {
+  if (a.m == 0 || (ra.passes == 0 && !ra.range)) return cudaSuccess;
   if (grid == 0) return cudaErrorInvalidConfiguration;
   const uint32_t bins = 1u << k.bits;
   a.H = scratch;
   a.P = scratch + static_cast<size_t>(grid) * bins;
   a.tot = a.P + static_cast<size_t>(grid) * bins;
   ResidentArgs r = ra;
-  void* args[] = {(void*)&k0, (void*)&v0, (void*)&k1, (void*)&v1, (void*)&a, (void*)&r};
+  void* args[] = {(void*)&k0, (void*)&v0, (void*)&k1, (void*)&v1, (void*)&k2, (void*)&v2, (void*)&a, (void*)&r};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(k.threads);

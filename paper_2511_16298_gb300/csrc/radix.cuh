@@ -169,6 +169,9 @@ struct PassArgs {
   const uint32_t* pbeg;        // [nv+1] first pair of each view
   uint32_t t_all;
   const uint64_t* m_dev;       // optional device element count, capped at m
+  // order-preserving key compression (uint32 keys, resident depth sort):
+  // on load key' = key == all ones ? cull : key - sub; on store the inverse
+  uint32_t xform_in, xform_out, sub, cull;
 };
 
 // kOcc: CTAs per SM the register budget is sized for (launch bounds); 0
@@ -367,7 +370,10 @@ __device__ __forceinline__ void emit_key(const PassArgs& a, K key, uint32_t gi, 
       if (p + 1 == valid || static_cast<uint32_t>(xk[p + 1] >> a.rbits) != gt) atomicMax(a.rmax + gt, dst + 1);
     }
   } else {
-    static_cast<K*>(kout_raw)[dst] = key;
+    K out = key;
+    if constexpr (sizeof(K) == 4)
+      if (a.xform_out) out = key == a.cull ? 0xffffffffu : key + a.sub;
+    static_cast<K*>(kout_raw)[dst] = out;
   }
 }
 
@@ -476,6 +482,8 @@ __device__ __forceinline__ void rank_tile(const K* __restrict__ kt, uint32_t val
   for (int j = 0; j < kItems; ++j) {
     const uint32_t idx = wbase + j * 32 + lane;
     R.k[j] = (kFull || idx < valid) ? __ldcs(kt + idx) : K(0);
+    if constexpr (sizeof(K) == 4)
+      if (a.xform_in) R.k[j] = R.k[j] == 0xffffffffu ? a.cull : R.k[j] - a.sub;
     R.d[j] = digit_of<K>(R.k[j], a.shift, a.mask, d31);
     if constexpr (kExpand) {
       R.gi[j] = R.dep[j] = 0u;
@@ -708,12 +716,21 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
 struct ResidentArgs {
   uint32_t passes;
   uint32_t shift[kMaxPasses], mask[kMaxPasses];
+  // With range set (uint32 keys): range[0..1] = smallest and largest key
+  // other than all ones (largest < smallest: there is none).  Keys are
+  // compressed to key - smallest (all ones -> one past the largest), the
+  // pass count and digits follow from the compressed width, and the result
+  // always lands in (k1, v1): passes alternate between (k1, v1) and
+  // (k2, v2) so that the last one writes (k1, v1).  range[2] receives the
+  // number of passes run.
+  uint32_t* range;
 };
 
 template <typename K, int kBits, int kThreads, int kItems, int kOcc>
 __global__ void __launch_bounds__(kThreads, kOcc)
     k_radix_resident(K* __restrict__ k0, uint32_t* __restrict__ v0, K* __restrict__ k1,
-                     uint32_t* __restrict__ v1, PassArgs a, ResidentArgs ra) {
+                     uint32_t* __restrict__ v1, K* __restrict__ k2, uint32_t* __restrict__ v2, PassArgs a,
+                     ResidentArgs ra) {
   using S = PassShape<K, true, false, kBits, kThreads, kItems, kOcc>;
   extern __shared__ __align__(16) unsigned char smem[];
   Smem<K> sm;
@@ -741,13 +758,42 @@ __global__ void __launch_bounds__(kThreads, kOcc)
     for (uint32_t i = t; i < S::kWhBytes / 16; i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
   }
   __syncthreads();
-  for (uint32_t p = 0; p < ra.passes; ++p) {
-    const K* kin = (p & 1) ? k1 : k0;
-    const uint32_t* vin = (p & 1) ? v1 : v0;
-    K* kout = (p & 1) ? k0 : k1;
-    uint32_t* vout = (p & 1) ? v0 : v1;
-    a.shift = ra.shift[p];
-    a.mask = ra.mask[p];
+  uint32_t passes = ra.passes, width = 0;
+  if constexpr (sizeof(K) == 4) {
+    if (ra.range) {
+      const uint32_t lo = __ldcg(ra.range), hi = __ldcg(ra.range + 1);
+      const uint32_t cull = hi >= lo ? hi - lo + 1u : 0u;  // compressed keys are 0 .. cull
+      const uint32_t bits = cull ? 32u - static_cast<uint32_t>(__clz(cull)) : 0u;
+      passes = bits ? (bits + kBits - 1) / kBits : 1u;
+      width = (bits + passes - 1) / passes;
+      a.sub = lo;
+      a.cull = cull;
+      if (c == 0 && t == 0) ra.range[2] = passes;
+    }
+  }
+  for (uint32_t p = 0; p < passes; ++p) {
+    const K* kin;
+    const uint32_t* vin;
+    K* kout;
+    uint32_t* vout;
+    if (ra.range) {
+      const bool to_one = ((passes - 1 - p) & 1u) == 0;
+      kin = p == 0 ? k0 : (to_one ? k2 : k1);
+      vin = p == 0 ? v0 : (to_one ? v2 : v1);
+      kout = to_one ? k1 : k2;
+      vout = to_one ? v1 : v2;
+      a.shift = p * width;
+      a.mask = width ? (1u << width) - 1u : 0u;
+      a.xform_in = p == 0;
+      a.xform_out = p + 1 == passes;
+    } else {
+      kin = (p & 1) ? k1 : k0;
+      vin = (p & 1) ? v1 : v0;
+      kout = (p & 1) ? k0 : k1;
+      vout = (p & 1) ? v0 : v1;
+      a.shift = ra.shift[p];
+      a.mask = ra.mask[p];
+    }
     TileRegs<K, false, kItems> R;
     rank_tile<false, S, K, false, kBits, kItems>(kin + ch.beg, valid, a, false, sm, R);
     for (uint32_t b = t; b < static_cast<uint32_t>(S::kBins); b += kThreads)
@@ -803,9 +849,11 @@ cudaError_t launch(const Kernel& k, uint32_t grid, const void* kin, const uint32
 uint32_t resident_grid(const Kernel& k, uint32_t m, int ctas_per_sm = 0);
 
 // Launch all passes of a resident kernel (cooperative): k0/v0 hold the
-// input; the result is in (k0, v0) for an even pass count, else (k1, v1).
+// input; with ra.range the result is in (k1, v1) (k2/v2: a third pair of
+// buffers), else in (k0, v0) for an even pass count and (k1, v1) for an odd.
 cudaError_t launch_resident(const Kernel& k, uint32_t grid, void* k0, uint32_t* v0, void* k1, uint32_t* v1,
-                            PassArgs a, const ResidentArgs& ra, uint32_t* scratch, cudaStream_t s);
+                            void* k2, uint32_t* v2, PassArgs a, const ResidentArgs& ra, uint32_t* scratch,
+                            cudaStream_t s);
 
 }  // namespace radix
 }  // namespace tdgs

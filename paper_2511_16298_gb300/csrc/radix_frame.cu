@@ -31,35 +31,31 @@ const radix::Kernel& stream_kernel(bool wide, bool expand, uint32_t bits) {
 uint32_t stream_kernel_bits(uint32_t width) { return width <= 6 ? 6u : (width <= 8 ? 8u : 12u); }
 
 namespace {
-const radix::Kernel& resident_depth_kernel(int digit_bits) {
-  static const radix::Kernel k11 = radix::make_resident_kernel<uint32_t, 11, 256, 16, 2>();
-  static const radix::Kernel k8 = radix::make_resident_kernel<uint32_t, 8, 256, 16, 2>();
-  return digit_bits == 11 ? k11 : k8;
+const radix::Kernel& resident_depth_kernel() {
+  static const radix::Kernel k9 = radix::make_resident_kernel<uint32_t, 9, 256, 16, 2>();
+  return k9;
 }
 }  // namespace
 
 DepthPlan plan_depth_sort(uint32_t n, int tuned_bits, int ctas_per_sm) {
   DepthPlan p{};
   const uint32_t nn = n ? n : 1;
-  // one launch for all passes when the Gaussians fit one tile per CTA
-  // (8-bit digits first unless 11 is asked for); else one launch per pass
-  const int order[2] = {tuned_bits == 11 ? 11 : 8, tuned_bits == 8 ? 8 : 11};
-  for (int b : order) {
-    const radix::Kernel& k = resident_depth_kernel(b);
-    const uint32_t g = radix::resident_grid(k, nn, ctas_per_sm);
-    if (g) {
-      p.resident = true;
-      p.bits = b;
-      p.passes = b == 11 ? 3u : 4u;
-      p.grid = g;
-      p.scratch_words = radix::scratch_words(k, g);
-      return p;
-    }
+  const radix::Kernel& k = resident_depth_kernel();
+  const uint32_t g = radix::resident_grid(k, nn, ctas_per_sm);
+  if (g) {
+    p.resident = true;
+    p.bits = 9;
+    p.passes = 4;  // at most; the kernel runs as many as the key range needs
+    p.grid = g;
+    p.result = 1;
+    p.scratch_words = radix::scratch_words(k, g);
+    return p;
   }
   p.resident = false;
   p.bits = tuned_bits == 11 ? 11 : 8;
   p.passes = p.bits == 11 ? 3u : 4u;
   p.grid = radix::grid_for(depth_kernel(p.bits), nn, ctas_per_sm);
+  p.result = p.passes & 1u;
   p.scratch_words = radix::scratch_words(depth_kernel(p.bits), p.grid);
   return p;
 }
@@ -83,15 +79,15 @@ cudaError_t launch_depth_pass(const DepthPlan& dp, uint32_t pass, const uint32_t
 }
 
 cudaError_t launch_depth_resident(const DepthPlan& dp, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
-                                  uint32_t n, uint32_t* scratch, uint32_t* bar, uint32_t* err, cudaStream_t s) {
+                                  uint32_t* k2, uint32_t* v2, uint32_t* range, uint32_t n,
+                                  uint32_t* scratch, uint32_t* bar, uint32_t* err, cudaStream_t s) {
   radix::PassArgs a{};
   a.m = n;
   a.bar = bar;
   a.err = err;
   radix::ResidentArgs ra{};
-  ra.passes = dp.passes;
-  for (uint32_t p = 0; p < dp.passes; ++p) depth_digit(static_cast<uint32_t>(dp.bits), p, &ra.shift[p], &ra.mask[p]);
-  return radix::launch_resident(resident_depth_kernel(dp.bits), dp.grid, k0, v0, k1, v1, a, ra, scratch, s);
+  ra.range = range;
+  return radix::launch_resident(resident_depth_kernel(), dp.grid, k0, v0, k1, v1, k2, v2, a, ra, scratch, s);
 }
 
 uint32_t stream_grid(bool wide, bool expand, uint32_t bits, uint32_t m, int ctas_per_sm) {

@@ -168,10 +168,12 @@ __device__ __forceinline__ uint32_t find_view(const uint32_t* begin, uint32_t nv
 
 // Counts, depth keys and indices of all records, per-view pair totals, and
 // (last block) the first pair of each view and the pair count in *total.
-// ticket: a zero word, left zero.
+// ticket: a zero word, left zero.  range: four words, [0..1] all ones and
+// zero on entry and exit; [2..3] receive the smallest and largest depth key
+// of a Gaussian with pairs.
 cudaError_t launch_views_count(const ViewTable& vt, uint32_t n_all, uint32_t* counts,
                                uint32_t* dkey, uint32_t* dval, uint32_t* err, uint32_t* ticket,
-                               uint64_t* total, cudaStream_t s);
+                               uint64_t* total, uint32_t* range, cudaStream_t s);
 cudaError_t launch_views_dup(const ViewTable& vt, const uint32_t* sorder, const uint32_t* soff,
                              uint32_t n_all, uint32_t rbits, void* out, bool wide, uint32_t cap,
                              uint32_t* err, cudaStream_t s);
@@ -182,24 +184,30 @@ cudaError_t launch_views_ranges(const ViewTable& vt, uint32_t* rmin, uint32_t* r
                                 uint32_t t_all, uint2* ranges, cudaStream_t s);
 
 // Radix passes of the frame path (radix_frame.cu).
-// Depth sort of the N Gaussians: (uint32 depth key, uint32 index), all 32
-// key bits, 11-bit (3 passes) or 8-bit (4 passes) digits.  When the
-// Gaussians fit one tile per resident CTA all passes run in one
-// cooperative launch (resident); otherwise one launch per pass.  tuned_bits
-// 0 prefers 8-bit digits.
+// Depth sort of the N Gaussians: (uint32 depth key, uint32 index).  When
+// the Gaussians fit one tile per resident CTA all passes run in one
+// cooperative launch (resident) over keys compressed to their range
+// (key - smallest; culled Gaussians one past the largest), with as many
+// 9-bit digits as that range needs (3 for a range below 2^27, 4 at most).
+// Otherwise one launch per pass over all 32 bits: 8-bit (4 passes) or,
+// if tuned, 11-bit (3 passes) digits.
 struct DepthPlan {
-  bool resident;
+  bool resident;          // one launch; keys compressed to their range, passes chosen on the device
   int bits;
-  uint32_t passes, grid;  // grid 0: the device query failed
+  uint32_t passes, grid;  // passes: the most that run; grid 0: the device query failed
+  uint32_t result;        // which of the three buffer pairs holds the sorted keys and indices
   size_t scratch_words;
 };
 DepthPlan plan_depth_sort(uint32_t n, int tuned_bits, int ctas_per_sm);
 cudaError_t launch_depth_pass(const DepthPlan& dp, uint32_t pass, const uint32_t* kin, const uint32_t* vin,
                               uint32_t* kout, uint32_t* vout, uint32_t n, uint32_t* scratch, uint32_t* bar,
                               uint32_t* err, cudaStream_t s);
-// Result in (k0, v0) for an even pass count, else (k1, v1).
+// Result in (k1, v1); range[0..1]: the smallest and largest depth key of a
+// Gaussian with pairs (written by the count kernel); range[2] receives the
+// number of passes run.
 cudaError_t launch_depth_resident(const DepthPlan& dp, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
-                                  uint32_t n, uint32_t* scratch, uint32_t* bar, uint32_t* err, cudaStream_t s);
+                                  uint32_t* k2, uint32_t* v2, uint32_t* range, uint32_t n,
+                                  uint32_t* scratch, uint32_t* bar, uint32_t* err, cudaStream_t s);
 // Stable pass over the packed stream on tile bits [shift, shift + width).
 // expand: write the final (local tile << 32 | depth bits) keys and local
 // indices; with rmin/rmax, record each global tile's first/last sorted

@@ -94,6 +94,7 @@ def lib():
                 "tdgs_context_launch_count": ([P], ctypes.c_uint64),
                 "tdgs_context_enable_timing": ([P, i32], st),
                 "tdgs_context_kernel_times": ([P, ctypes.POINTER(_KernelTime), i32], i32),
+                "tdgs_context_depth_passes": ([P, ctypes.POINTER(i32), P], st),
                 "tdgs_count_tiles": ([P, P, u32, F, P, P], st),
                 "tdgs_scan": ([P, P, u32, P, P, P], st),
                 "tdgs_duplicate_keys": ([P, P, P, u32, F, P, P, u32, P], st),
@@ -256,6 +257,13 @@ class Context:
             raise TdgsError(INVALID_ARGUMENT, "tdgs_context_kernel_times")
         return {buf[i].name.decode(): {"launches": int(buf[i].launches), "items": int(buf[i].items),
                                        "ms": float(buf[i].total_ms)} for i in range(min(n, 16))}
+
+    def depth_passes(self) -> int:
+        """Digit passes of the last single-launch depth sort (0 if none)."""
+        v = ctypes.c_int(0)
+        self._check(lib().tdgs_context_depth_passes(self._h, ctypes.byref(v), _stream(self.device)),
+                    "tdgs_context_depth_passes")
+        return v.value
 
     # ------------------------------------------------------------ the steps
     def count_tiles(self, g: torch.Tensor, width: int, height: int, out=None) -> torch.Tensor:

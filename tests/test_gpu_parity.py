@@ -278,6 +278,28 @@ def test_sort_frame_changing_counts(ctx, oracle):
     _check_frame(ctx, oracle, base)  # from a zero count back to a full frame
 
 
+@pytest.mark.parametrize("depths,passes", [
+    ((2.5, 2.5), 1),            # one depth: one pass
+    ((1.0, 1.01), 2),           # a narrow range: 17 bits of keys
+    ((0.5, 80.0), 3),           # a scene-like range: < 2^27 keys
+    ((1e-30, 1e30), 4),         # the full range of positive floats
+])
+def test_depth_sort_pass_count(ctx, oracle, depths, passes):
+    """The single-launch depth sort compresses keys to their range and runs
+    as many 9-bit passes as the range needs; results stay exact, with
+    culled Gaussians and equal depths in the mix."""
+    rng = np.random.default_rng(passes)
+    n = 30_000
+    lo, hi = depths
+    d = np.exp(rng.uniform(np.log(lo), np.log(hi), size=n))
+    d[rng.integers(0, n, size=n // 10)] = lo  # ties at the smallest key
+    r = rng.integers(1, 12, size=n)
+    r[rng.integers(0, n, size=n // 20)] = 0  # culled
+    g = synth.records(rng.uniform(0, 640, n), rng.uniform(0, 360, n), d, r)
+    _check_frame(ctx, oracle, synth.Frame(640, 360, g, f"depths-{lo}-{hi}"))
+    assert ctx.depth_passes() == passes
+
+
 def test_sort_frame_scene_1m(ctx, oracle):
     m = _check_frame(ctx, oracle, synth.frame_scene(0))
     assert m > 5_000_000
