@@ -57,6 +57,16 @@ __device__ __forceinline__ void st_release32(uint32_t* p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Hint: bring [p, p + bytes) into L2 with one bulk prefetch (the 16-byte
+// aligned part of it; nothing is read into registers or shared memory).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint64_t bytes) {
+  const uint64_t a = reinterpret_cast<uint64_t>(p);
+  const uint64_t lo = (a + 15) & ~15ull, hi = (a + bytes) & ~15ull;
+  if (hi > lo)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"(static_cast<uint32_t>(hi - lo))
+                 : "memory");
+}
+
 // Self-resetting grid barrier for a cooperatively launched grid (all CTAs
 // resident).  bar[0] counts arrivals, bar[1] is the generation.  The wait is
 // bounded: on timeout the error is latched and the CTA moves on (every
@@ -687,14 +697,24 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
     for (uint32_t i = t; i < S::kWhBytes / 16; i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
   }
   // (chunk_bases starts and ends with a block barrier)
+  if constexpr (kVals)  // the first tile's values, while the histogram is built
+    if (t == 0 && end > beg) prefetch_l2(vin + beg, static_cast<uint64_t>(min(kTileKeys, end - beg)) * 4);
   chunk_bases<K, S::kBins, kThreads>(kin, a, beg, end, d31, sm.base, sm.lstart, s_warp, s_vtile);
+  if (t == 0 && end > beg)  // the first tile's keys again: phase 1 read the whole chunk since
+    prefetch_l2(kin + beg, static_cast<uint64_t>(min(kTileKeys, end - beg)) * sizeof(K));
 
-  // ---- phase 3: stable rank + scatter, tile by tile
+  // ---- phase 3: stable rank + scatter, tile by tile; while a tile is
+  // processed, the next one's keys and values are prefetched into L2
   bool ok = true;
   const uint32_t len = end - beg;
   const uint32_t full = len / kTileKeys;
   for (uint32_t i = 0; i < full; ++i) {
     const uint32_t tb = beg + i * kTileKeys;
+    if (t == 0 && tb + kTileKeys < end) {
+      const uint32_t cnt = min(kTileKeys, end - (tb + kTileKeys));
+      prefetch_l2(kin + tb + kTileKeys, static_cast<uint64_t>(cnt) * sizeof(K));
+      if constexpr (kVals) prefetch_l2(vin + tb + kTileKeys, static_cast<uint64_t>(cnt) * 4);
+    }
     ok &= rank_and_scatter<true, S, K, kVals, kExpand, kBits, kItems>(
         kin + tb, kVals ? vin + tb : nullptr, kTileKeys, m, a, d31, sm, s_warp, s_vrec, s_vtile, kout_raw, vout);
   }
