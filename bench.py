@@ -158,10 +158,8 @@ def algorithmic_bytes(kernel: str, items: int, n: int, m: int, tiles: int, depth
         return 24.0 * items + 4.0 * m
     if kernel == "tile_sort_pass":   # 4 B element in and out
         return 8.0 * items
-    if kernel == "tile_expand_pass":  # 4 B element in; u64 key + u32 value out; depth tables once
-        return 16.0 * items + 8.0 * n
-    if kernel == "ranges_final":     # run first/last in, range out, per tile
-        return 16.0 * items
+    if kernel == "tile_expand_pass":  # 4 B element in; u64 key + u32 value out; depth tables once;
+        return 16.0 * items + 8.0 * n + 16.0 * tiles  # per tile: first/last position in, range out
     return 0.0
 
 

@@ -48,12 +48,12 @@ struct Buffer {
 
 enum KernelId {
   kKCount, kKScan, kKDuplicate, kKRanges, kKRadixPass,
-  kKFrameCount, kKDepthSort, kKFrameScan, kKDupDepth, kKTilePass, kKTileExpand, kKRangesFinal, kKNum
+  kKFrameCount, kKDepthSort, kKFrameScan, kKDupDepth, kKTilePass, kKTileExpand, kKNum
 };
 const char* const kKernelNames[kKNum] = {
     "count_tiles",  "scan",       "duplicate_keys",     "tile_ranges",    "radix_pass",
     "frame_count",  "depth_sort", "scan_by_depth", "duplicate_by_depth", "tile_sort_pass",
-    "tile_expand_pass", "ranges_final"};
+    "tile_expand_pass"};
 
 // View table as stored in device memory (SoA, fixed maximum size).
 struct ViewBlob {
@@ -757,7 +757,7 @@ tdgs_status run_back(tdgs_context* ctx, uint32_t m, const uint64_t* m_dev, cudaS
       TDGS_CUDA(ctx, cudaMemsetAsync(rmin, 0xff, half * 4, s));
       TDGS_CUDA(ctx, cudaMemsetAsync(rmax, 0, half * 4, s));
     }
-    ctx->rminmax_dirty = true;  // until the ranges kernel below is enqueued
+    ctx->rminmax_dirty = true;  // until the last pass below is enqueued
   }
   uint32_t shift = sh.rbits;
   for (uint32_t p = 0; p < sh.npass; ++p) {
@@ -781,15 +781,12 @@ tdgs_status run_back(tdgs_context* ctx, uint32_t m, const uint64_t* m_dev, cudaS
     sp.views = &vt;
     sp.rmin = last && !single ? rmin : nullptr;
     sp.rmax = last && !single ? rmax : nullptr;
-    sp.ranges = last && single ? ranges : nullptr;
+    sp.ranges = last ? ranges : nullptr;
     sp.t_all = ctx->t_all;
     TDGS_TRACED(ctx, last ? kKTileExpand : kKTilePass, m, s, launch_stream_pass(sp, scratch, bar, err_word(ctx), s));
     shift += width;
   }
-  if (!single) {
-    TDGS_TRACED(ctx, kKRangesFinal, ctx->t_all, s, launch_views_ranges(vt, rmin, rmax, ctx->t_all, ranges, s));
-    ctx->rminmax_dirty = false;
-  }
+  if (!single) ctx->rminmax_dirty = false;  // the last pass turned them into ranges and reset them
   return TDGS_OK;
 }
 

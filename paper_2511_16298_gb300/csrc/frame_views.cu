@@ -317,38 +317,4 @@ cudaError_t launch_views_dup(const ViewTable& vt, const uint32_t* sorder, const 
   return cudaGetLastError();
 }
 
-// Identify Range: local [start, end) per tile from the first/last sorted
-// positions recorded by the last tile pass; {0, 0} for an empty tile.
-__global__ void __launch_bounds__(256)
-    k_views_ranges(ViewTable vt, uint32_t* __restrict__ rmin, uint32_t* __restrict__ rmax,
-                   uint32_t t_all, uint2* __restrict__ ranges) {
-  __shared__ uint32_t s_tb[kMaxViews + 1];
-  __shared__ uint32_t s_pb[kMaxViews + 1];
-  for (uint32_t v = threadIdx.x; v <= vt.nv; v += blockDim.x) {
-    s_tb[v] = vt.tile_begin[v];
-    s_pb[v] = vt.pbeg[v];
-  }
-  __syncthreads();
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < t_all; t += gridDim.x * blockDim.x) {
-    const uint32_t lo = rmin[t];
-    if (lo == 0xffffffffu) {
-      ranges[t] = make_uint2(0u, 0u);
-    } else {
-      const uint32_t pb = s_pb[vt.nv == 1 ? 0u : find_view(s_tb, vt.nv, t)];
-      ranges[t] = make_uint2(lo - pb, rmax[t] - pb);
-      rmin[t] = 0xffffffffu;  // back to the empty state for the next frame
-      rmax[t] = 0u;
-    }
-  }
-}
-
-cudaError_t launch_views_ranges(const ViewTable& vt, uint32_t* rmin, uint32_t* rmax,
-                                uint32_t t_all, uint2* ranges, cudaStream_t s) {
-  if (t_all == 0) return cudaSuccess;
-  const uint32_t blocks = (t_all + 255) / 256;
-  const uint32_t grid = blocks < 152u * 8u ? blocks : 152u * 8u;
-  k_views_ranges<<<grid, 256, 0, s>>>(vt, rmin, rmax, t_all, ranges);
-  return cudaGetLastError();
-}
-
 }  // namespace tdgs

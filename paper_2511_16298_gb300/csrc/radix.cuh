@@ -173,9 +173,11 @@ struct PassArgs {
   uint32_t nv;
   uint32_t* rmin;              // per global tile: first sorted position (atomicMin)
   uint32_t* rmax;              // per global tile: one past the last (atomicMax)
-  // single-pass expansion (the digit is the whole global tile id): ranges
-  // are written straight from the digit totals
-  uint2* ranges;               // [t_all] view-local [start, end), or null
+  // view-local tile ranges [start, end) (t_all entries), or null: a single
+  // pass over the whole tile id writes them from its digit totals; the last
+  // of several passes, after a grid barrier, from rmin/rmax (which it then
+  // resets to all ones / zero)
+  uint2* ranges;
   const uint32_t* pbeg;        // [nv+1] first pair of each view
   uint32_t t_all;
   const uint64_t* m_dev;       // optional device element count, capped at m
@@ -297,7 +299,7 @@ __device__ __forceinline__ void scan_chunks(const PassArgs& a, uint32_t* base, u
       base[b] = run + __ldcg(a.P + static_cast<size_t>(c) * kBins + b);
       // every tile's range, spread over the CTAs; positions are relative
       // to the view's first pair
-      if (a.ranges && b < a.t_all && b % G == c) {
+      if (a.ranges && !a.rmin && b < a.t_all && b % G == c) {
         uint2 rg = make_uint2(0u, 0u);
         if (seg[i]) {
           const uint32_t pb = a.pbeg[a.nv == 1 ? 0u : find_view(s_vtile, a.nv, b)];
@@ -725,6 +727,22 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
         kin + tb, kVals ? vin + tb : nullptr, rest, m, a, d31, sm, s_warp, s_vrec, s_vtile, kout_raw, vout);
   }
   if (!ok) latch_error(a.err, TDGS_ERR_CAPACITY, kSiteRadixRange);
+  if constexpr (kExpand) {
+    if (a.rmin && a.ranges) {
+      grid_barrier(a.bar, a.err);  // every tile's first and last position is recorded
+      for (uint32_t tt = blockIdx.x * kThreads + t; tt < a.t_all; tt += gridDim.x * kThreads) {
+        const uint32_t lo = __ldcg(a.rmin + tt);
+        if (lo == 0xffffffffu) {
+          a.ranges[tt] = make_uint2(0u, 0u);
+        } else {
+          const uint32_t pb = a.pbeg[a.nv == 1 ? 0u : find_view(s_vtile, a.nv, tt)];
+          a.ranges[tt] = make_uint2(lo - pb, __ldcg(a.rmax + tt) - pb);
+          a.rmin[tt] = 0xffffffffu;  // back to the empty state for the next frame
+          a.rmax[tt] = 0u;
+        }
+      }
+    }
+  }
 }
 
 // Several digit passes in one cooperative launch, for inputs of at most

@@ -177,11 +177,6 @@ cudaError_t launch_views_count(const ViewTable& vt, uint32_t n_all, uint32_t* co
 cudaError_t launch_views_dup(const ViewTable& vt, const uint32_t* sorder, const uint32_t* soff,
                              uint32_t n_all, uint32_t rbits, void* out, bool wide, uint32_t cap,
                              uint32_t* err, cudaStream_t s);
-// rmin/rmax: per global tile, first and one-past-last sorted position
-// (0xffffffff / 0 for an empty tile); writes local ranges per view and
-// resets rmin/rmax to the empty state.
-cudaError_t launch_views_ranges(const ViewTable& vt, uint32_t* rmin, uint32_t* rmax,
-                                uint32_t t_all, uint2* ranges, cudaStream_t s);
 
 // Radix passes of the frame path (radix_frame.cu).
 // Depth sort of the N Gaussians: (uint32 depth key, uint32 index).  When
