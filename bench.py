@@ -150,8 +150,10 @@ def algorithmic_bytes(kernel: str, items: int, n: int, m: int, tiles: int, depth
     # fused frame
     if kernel == "frame_count":      # record in; count, depth key, index out
         return 28.0 * items
-    if kernel == "depth_sort":       # (u32 key, u32 index) in and out, per pass
-        return 16.0 * items * depth_passes
+    if kernel == "depth_sort":       # (u32 key, u32 index) in and out, per pass; the
+        # single-launch form also scans the counts in depth order (index in,
+        # gathered count, offset out)
+        return 16.0 * items * depth_passes + (12.0 * items if depth_passes > 1 else 0.0)
     if kernel == "scan_by_depth":    # index in, gathered count, offset out
         return 12.0 * items
     if kernel == "duplicate_by_depth":  # index, offset, record in; 4 B per pair out

@@ -704,10 +704,11 @@ tdgs_status run_front(tdgs_context* ctx, cudaStream_t s, bool early_total = fals
   const DepthPlan dp = plan_depth_sort(n_all, ctx->tuning.depth_digit_bits, ctx->tuning.ctas_per_sm);
   const uint32_t dpasses = dp.passes;
   uint32_t* scratch = static_cast<uint32_t*>(ctx->sort_scratch.p);
-  if (dp.resident) {  // one launch; its pass count follows the depth range
+  if (dp.resident) {  // one launch: the sort (pass count from the depth range) and the offsets
     TDGS_TRACED(ctx, kKDepthSort, n_all, s,
-                launch_depth_resident(dp, dk[0], dv[0], dk[1], dv[1], dk[2], dv[2], ctx->d_range + 2, n_all,
-                                      scratch, ctx->d_tickets + 2, err_word(ctx), s));
+                launch_depth_resident(dp, dk[0], dv[0], dk[1], dv[1], dk[2], dv[2], ctx->d_range + 2, counts,
+                                      static_cast<uint32_t*>(ctx->f_soff.p), n_all, scratch, ctx->d_tickets + 2,
+                                      err_word(ctx), s));
   } else {
     for (uint32_t p = 0; p < dpasses; ++p) {
       TDGS_TRACED(ctx, kKDepthSort, n_all, s,
@@ -715,11 +716,11 @@ tdgs_status run_front(tdgs_context* ctx, cudaStream_t s, bool early_total = fals
                                     ctx->d_tickets + 2, err_word(ctx), s));
     }
   }
-  if (n_all) {
+  if (n_all && !dp.resident) {
     tdgs_status st = do_scan(ctx, kKFrameScan, counts, nullptr, dv[dp.result], FrameGeom{}, n_all,
                              static_cast<uint32_t*>(ctx->f_soff.p), &ctx->d_status->total, nullptr, s);
     if (st != TDGS_OK) return st;
-  } else {
+  } else if (n_all == 0) {
     TDGS_CUDA(ctx, cudaMemsetAsync(&ctx->d_status->total, 0, 8, s));
   }
   return TDGS_OK;

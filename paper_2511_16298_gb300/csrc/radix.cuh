@@ -762,6 +762,11 @@ struct ResidentArgs {
   // (k2, v2) so that the last one writes (k1, v1).  range[2] receives the
   // number of passes run.
   uint32_t* range;
+  // With counts set (and range): after the sort, offsets[p] = sum of
+  // counts[v1[q]] over q < p (the exclusive scan of the counts in sorted
+  // order); a sum above 2^32 - 1 latches TDGS_ERR_OVERFLOW.
+  const uint32_t* counts;
+  uint32_t* offsets;
 };
 
 template <typename K, int kBits, int kThreads, int kItems, int kOcc>
@@ -842,6 +847,85 @@ __global__ void __launch_bounds__(kThreads, kOcc)
     grid_barrier(a.bar, a.err);  // the next pass reads what every CTA wrote
   }
   if (!ok) latch_error(a.err, TDGS_ERR_CAPACITY, kSiteRadixRange);
+  if constexpr (sizeof(K) == 4) {
+    if (ra.range && ra.counts) {
+      // exclusive scan of the counts in sorted order: chunk c of the sorted
+      // indices, kItems consecutive positions per thread, chunk sums through
+      // a grid barrier
+      static_assert(kItems % 4 == 0, "16-byte loads of the sorted indices");
+      const uint32_t pos0 = ch.beg + t * kItems;
+      uint32_t cnt[kItems];
+      uint64_t sum = 0;
+#pragma unroll
+      for (int j = 0; j < kItems; j += 4) {
+        uint4 idx = make_uint4(0, 0, 0, 0);
+        if (pos0 + j + 4 <= ch.end) {
+          idx = __ldcg(reinterpret_cast<const uint4*>(v1 + pos0 + j));
+        } else {
+          if (pos0 + j < ch.end) idx.x = __ldcg(v1 + pos0 + j);
+          if (pos0 + j + 1 < ch.end) idx.y = __ldcg(v1 + pos0 + j + 1);
+          if (pos0 + j + 2 < ch.end) idx.z = __ldcg(v1 + pos0 + j + 2);
+        }
+        const uint32_t id[4] = {idx.x, idx.y, idx.z, idx.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t p = pos0 + j + u;
+          cnt[j + u] = (p < ch.end && id[u] < ch.m) ? __ldg(ra.counts + id[u]) : 0u;
+          sum += cnt[j + u];
+        }
+      }
+      // block scan of the per-thread sums (64-bit)
+      __shared__ unsigned long long s_sum[S::kWarps];
+      __shared__ unsigned long long s_base;
+      const uint32_t lane = lane_id(), warp = t >> 5;
+      unsigned long long x = sum;
+#pragma unroll
+      for (int dd = 1; dd < 32; dd <<= 1) {
+        const unsigned long long o = __shfl_up_sync(0xffffffffu, x, dd);
+        if (lane >= static_cast<uint32_t>(dd)) x += o;
+      }
+      if (lane == 31) s_sum[warp] = x;
+      __syncthreads();
+      if (t == 0) {
+        unsigned long long run = 0;
+        for (int w = 0; w < S::kWarps; ++w) {
+          const unsigned long long v = s_sum[w];
+          s_sum[w] = run;
+          run += v;
+        }
+        reinterpret_cast<unsigned long long*>(a.H)[c] = run;  // this chunk's sum
+      }
+      __syncthreads();
+      uint64_t run = x - sum + s_sum[warp];
+      grid_barrier(a.bar, a.err);  // every chunk's sum is published
+      if (warp == 0) {
+        unsigned long long before = 0;
+        for (uint32_t cc = lane; cc < c; cc += 32) before += __ldcg(reinterpret_cast<const unsigned long long*>(a.H) + cc);
+#pragma unroll
+        for (int dd = 16; dd > 0; dd >>= 1) before += __shfl_xor_sync(0xffffffffu, before, dd);
+        if (lane == 0) s_base = before;
+      }
+      __syncthreads();
+      run += s_base;
+      if (run + sum > 0xffffffffull) latch_error(a.err, TDGS_ERR_OVERFLOW, kSiteScan);
+#pragma unroll
+      for (int j = 0; j < kItems; j += 4) {
+        uint32_t o[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          o[u] = static_cast<uint32_t>(run);
+          run += cnt[j + u];
+        }
+        if (pos0 + j + 4 <= ch.end) {
+          *reinterpret_cast<uint4*>(ra.offsets + pos0 + j) = make_uint4(o[0], o[1], o[2], o[3]);
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (pos0 + j + u < ch.end) ra.offsets[pos0 + j + u] = o[u];
+        }
+      }
+    }
+  }
 }
 
 // --------------------------------------------------------------- host side

@@ -79,14 +79,17 @@ cudaError_t launch_depth_pass(const DepthPlan& dp, uint32_t pass, const uint32_t
 }
 
 cudaError_t launch_depth_resident(const DepthPlan& dp, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
-                                  uint32_t* k2, uint32_t* v2, uint32_t* range, uint32_t n,
-                                  uint32_t* scratch, uint32_t* bar, uint32_t* err, cudaStream_t s) {
+                                  uint32_t* k2, uint32_t* v2, uint32_t* range, const uint32_t* counts,
+                                  uint32_t* offsets, uint32_t n, uint32_t* scratch, uint32_t* bar, uint32_t* err,
+                                  cudaStream_t s) {
   radix::PassArgs a{};
   a.m = n;
   a.bar = bar;
   a.err = err;
   radix::ResidentArgs ra{};
   ra.range = range;
+  ra.counts = counts;
+  ra.offsets = offsets;
   return radix::launch_resident(resident_depth_kernel(), dp.grid, k0, v0, k1, v1, k2, v2, a, ra, scratch, s);
 }
 

@@ -199,10 +199,12 @@ cudaError_t launch_depth_pass(const DepthPlan& dp, uint32_t pass, const uint32_t
                               uint32_t* err, cudaStream_t s);
 // Result in (k1, v1); range[0..1]: the smallest and largest depth key of a
 // Gaussian with pairs (written by the count kernel); range[2] receives the
-// number of passes run.
+// number of passes run.  Then offsets = the exclusive scan of
+// counts[v1[.]] (the pair offsets in depth order).
 cudaError_t launch_depth_resident(const DepthPlan& dp, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
-                                  uint32_t* k2, uint32_t* v2, uint32_t* range, uint32_t n,
-                                  uint32_t* scratch, uint32_t* bar, uint32_t* err, cudaStream_t s);
+                                  uint32_t* k2, uint32_t* v2, uint32_t* range, const uint32_t* counts,
+                                  uint32_t* offsets, uint32_t n, uint32_t* scratch, uint32_t* bar, uint32_t* err,
+                                  cudaStream_t s);
 // Stable pass over the packed stream on tile bits [shift, shift + width).
 // expand: write the final (local tile << 32 | depth bits) keys and local
 // indices; with rmin/rmax, record each global tile's first/last sorted
