@@ -134,8 +134,9 @@ def algorithmic_bytes(kernel: str, items: int, n: int, m: int, tiles: int, depth
     the library's tracer reports them); n, m, tiles = the frame's sizes.
     The fused-frame figures assume the packed (tile, depth rank) element
     fits 32 bits, which holds for every single-frame workload timed here.
-    depth_passes: digit passes one depth_sort launch ran (several in the
-    single-launch form, one per launch otherwise)."""
+    depth_passes: digit passes one depth_sort launch ran; negative for the
+    single-launch form (all passes and the depth-order scan in one launch),
+    1 for one launch per pass."""
     # the five separate steps
     if kernel == "count_tiles":      # record in (16 B), count out (4 B)
         return 20.0 * items
@@ -153,7 +154,7 @@ def algorithmic_bytes(kernel: str, items: int, n: int, m: int, tiles: int, depth
     if kernel == "depth_sort":       # (u32 key, u32 index) in and out, per pass; the
         # single-launch form also scans the counts in depth order (index in,
         # gathered count, offset out)
-        return 16.0 * items * depth_passes + (12.0 * items if depth_passes > 1 else 0.0)
+        return 16.0 * items * abs(depth_passes) + (12.0 * items if depth_passes < 0 else 0.0)
     if kernel == "scan_by_depth":    # index in, gathered count, offset out
         return 12.0 * items
     if kernel == "duplicate_by_depth":  # index, offset, record in; 4 B per pair out
@@ -233,7 +234,7 @@ def run_ours(args, rank, world, local_rank, dist):
     ktimes = ctx.kernel_times()
     ctx.enable_timing(False)
     dsl = ktimes.get("depth_sort", {}).get("launches", 0)
-    depth_passes = ctx.depth_passes() if dsl == args.steps else 1
+    depth_passes = -ctx.depth_passes() if dsl == args.steps else 1
     step_ms = [a.elapsed_time(b) for a, b in ev]
     dev_s = sum(step_ms) / 1e3
     pairs = m * args.steps
@@ -350,7 +351,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "latency_ms": {"p50": round(statistics.median(step_ms), 4),
                        "p99": round(float(np.percentile(step_ms, 99)), 4),
                        "wall_ms_per_step": round(wall / args.steps * 1e3, 4)},
-        "pairs_per_frame": m, "n": n, "tiles": T, "depth_passes": depth_passes, "kernels": kernels,
+        "pairs_per_frame": m, "n": n, "tiles": T, "depth_passes": abs(depth_passes), "kernels": kernels,
         "roofline": roof,
         "sort_pairs": sort_only, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(),
