@@ -564,6 +564,7 @@ def main():
             "config": {"workload": "scene-1M: 1,000,000 projected Gaussians, 1280x720 image, "
                                    "3,600 16x16 tiles, 70% clustered means, seed=rank",
                        "gaussians": res["n"], "pairs": res["pairs_per_frame"],
+                       "depth_sort_passes": res["depth_passes"],
                        "tiles": res["tiles"], "parallelism": f"replicas x{world}",
                        "l2": "flushed between steps (256 MiB memset, outside the step events)",
                        "timing": "CUDA events around each tdgs_sort_frame call, summed; per-kernel "

@@ -83,7 +83,7 @@ struct tdgs_context {
   uint32_t ticket_base[2] = {0, 0};
   Buffer scan_status, sort_scratch;
   // fused-frame / multi-view buffers
-  Buffer f_counts, f_dkey[3], f_dval[3], f_soff, f_rminmax, f_stream[2], f_keys, f_values, f_ranges;
+  Buffer f_counts, f_dkey[3], f_dval[3], f_soff, f_sdo, f_rminmax, f_stream[2], f_keys, f_values, f_ranges;
   // depth-key range: accumulators [0..1], result [2..3], passes of the last
   // resident depth sort [4]
   uint32_t* d_range = nullptr;
@@ -459,7 +459,7 @@ void tdgs_context_destroy(tdgs_context* ctx) {
   for (cudaEvent_t e : ctx->free_events) cudaEventDestroy(e);
   Buffer* bufs[] = {&ctx->scan_status, &ctx->sort_scratch, &ctx->f_counts,    &ctx->f_dkey[0],
                     &ctx->f_dkey[1],    &ctx->f_dkey[2],     &ctx->f_dval[0],    &ctx->f_dval[1],
-                    &ctx->f_dval[2],    &ctx->f_soff,
+                    &ctx->f_dval[2],    &ctx->f_soff,       &ctx->f_sdo,
                     &ctx->f_rminmax,    &ctx->f_stream[0],   &ctx->f_stream[1],  &ctx->f_keys,
                     &ctx->f_values,     &ctx->f_ranges};
   if (ctx->d_views) cudaFree(ctx->d_views);
@@ -649,6 +649,7 @@ tdgs_status ensure_record_buffers(tdgs_context* ctx, cudaStream_t s) {
   for (Buffer* b : {&ctx->f_counts, &ctx->f_dkey[0], &ctx->f_dkey[1], &ctx->f_dkey[2], &ctx->f_dval[0],
                     &ctx->f_dval[1], &ctx->f_dval[2], &ctx->f_soff})
     if (st == TDGS_OK) st = ensure(ctx, *b, n4, s);
+  if (st == TDGS_OK) st = ensure(ctx, ctx->f_sdo, static_cast<size_t>(ctx->n_all) * 8 + 16, s);
   bool grown = false;
   if (st == TDGS_OK) st = ensure(ctx, ctx->f_rminmax, static_cast<size_t>(ctx->t_all) * 8 + 16, s, &grown);
   if (grown) ctx->rminmax_dirty = true;
@@ -733,8 +734,8 @@ tdgs_status run_back(tdgs_context* ctx, uint32_t m, const uint64_t* m_dev, cudaS
   const Shape sh = shape_of(ctx);
   const uint32_t n_all = ctx->n_all;
   const uint32_t dres = plan_depth_sort(n_all, ctx->tuning.depth_digit_bits, ctx->tuning.ctas_per_sm).result;
-  const uint32_t* sdepth = static_cast<uint32_t*>(ctx->f_dkey[dres].p);
   const uint32_t* sorder = static_cast<uint32_t*>(ctx->f_dval[dres].p);
+  uint2* sdo = static_cast<uint2*>(ctx->f_sdo.p);
   uint32_t* scratch = static_cast<uint32_t*>(ctx->sort_scratch.p);
   uint32_t* bar = ctx->d_tickets + 2;
   void* st[2] = {ctx->f_stream[0].p, ctx->f_stream[1].p};
@@ -743,7 +744,7 @@ tdgs_status run_back(tdgs_context* ctx, uint32_t m, const uint64_t* m_dev, cudaS
   uint32_t* rmax = rmin + half;
   TDGS_TRACED(ctx, kKDupDepth, m ? n_all : 0, s,
               launch_views_dup(vt, sorder, static_cast<uint32_t*>(ctx->f_soff.p), n_all, sh.rbits, st[0],
-                               sh.wide, m, err_word(ctx), s));
+                               sh.wide, m, sdo, err_word(ctx), s));
   // One pass over the whole tile id writes the ranges from its digit
   // totals; with several passes the last one records each tile's first and
   // last position and a small kernel turns them into ranges.
@@ -777,8 +778,7 @@ tdgs_status run_back(tdgs_context* ctx, uint32_t m, const uint64_t* m_dev, cudaS
     sp.shift = shift;
     sp.width = width;
     sp.rbits = sh.rbits;
-    sp.sdepth = sdepth;
-    sp.sorder = sorder;
+    sp.sdo = sdo;
     sp.views = &vt;
     sp.rmin = last && !single ? rmin : nullptr;
     sp.rmax = last && !single ? rmax : nullptr;

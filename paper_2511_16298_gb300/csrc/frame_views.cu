@@ -172,7 +172,7 @@ template <typename K>
 __global__ void __launch_bounds__(256)
     k_views_dup(ViewTable vt, const uint32_t* __restrict__ sorder,
                 const uint32_t* __restrict__ soff, uint32_t n_all, uint32_t rbits,
-                K* __restrict__ out, uint32_t cap, uint32_t* err) {
+                K* __restrict__ out, uint32_t cap, uint2* __restrict__ sdo, uint32_t* err) {
   __shared__ uint32_t s_begin[kMaxViews + 1];
   __shared__ const float4* s_g[kMaxViews];
   __shared__ FrameGeom s_geom[kMaxViews];
@@ -207,10 +207,13 @@ __global__ void __launch_bounds__(256)
     if (gi < n_all) {  // a depth order that is not a permutation is never followed out of bounds
       const uint32_t v = vt.nv == 1 ? 0u : find_view(s_begin, vt.nv, gi);
       const FrameGeom fg = s_geom[v];
-      q = tile_rect(__ldg(s_g[v] + (gi - s_begin[v])), fg);
+      const float4 rec = __ldg(s_g[v] + (gi - s_begin[v]));
+      q = tile_rect(rec, fg);
       start = __ldg(soff + j);
       gx = static_cast<uint32_t>(fg.gx);
       first = s_tb[v] + static_cast<uint32_t>(q.y0) * gx + static_cast<uint32_t>(q.x0);
+      // the depth key of the count kernel, beside the record index
+      sdo[j] = make_uint2(q.count ? __float_as_uint(rec.z) : 0xffffffffu, gi);
     }
     // pairs of consecutive depth positions are consecutive, so the warp's
     // last valid lane ends its range
@@ -303,17 +306,17 @@ __global__ void __launch_bounds__(256)
 
 cudaError_t launch_views_dup(const ViewTable& vt, const uint32_t* sorder, const uint32_t* soff,
                              uint32_t n_all, uint32_t rbits, void* out, bool wide, uint32_t cap,
-                             uint32_t* err, cudaStream_t s) {
+                             uint2* sdo, uint32_t* err, cudaStream_t s) {
   if (n_all == 0) return cudaSuccess;
   const uint32_t warps = (n_all + 31) / 32;
   const uint32_t blocks = (warps + 7) / 8;
   const uint32_t grid = blocks < 152u * 32u ? blocks : 152u * 32u;
   if (wide)
     k_views_dup<uint64_t><<<grid, 256, 0, s>>>(vt, sorder, soff, n_all, rbits,
-                                               static_cast<uint64_t*>(out), cap, err);
+                                               static_cast<uint64_t*>(out), cap, sdo, err);
   else
     k_views_dup<uint32_t><<<grid, 256, 0, s>>>(vt, sorder, soff, n_all, rbits,
-                                               static_cast<uint32_t*>(out), cap, err);
+                                               static_cast<uint32_t*>(out), cap, sdo, err);
   return cudaGetLastError();
 }
 

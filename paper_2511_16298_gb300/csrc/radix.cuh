@@ -67,19 +67,26 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint64_t bytes) {
                  : "memory");
 }
 
+__device__ __forceinline__ uint32_t atom_add_acq_rel32(uint32_t* p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 // Self-resetting grid barrier for a cooperatively launched grid (all CTAs
-// resident).  bar[0] counts arrivals, bar[1] is the generation.  The wait is
-// bounded: on timeout the error is latched and the CTA moves on (every
-// scatter stays bounds-checked).
+// resident).  bar[0] counts arrivals, bar[1] is the generation.  After the
+// block barrier, thread 0 arrives with an acquire-release add (publishing
+// its block's writes); the last arrival resets the count and releases the
+// next generation, which the others acquire.  The wait is bounded: on
+// timeout the error is latched and the CTA moves on (every scatter stays
+// bounds-checked).
 __device__ __forceinline__ void grid_barrier(uint32_t* bar, uint32_t* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const uint32_t gen = ld_acquire32(bar + 1);
-    __threadfence();
-    const uint32_t arrived = atomicAdd(bar, 1u);
+    const uint32_t arrived = atom_add_acq_rel32(bar, 1u);
     if (arrived == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
+      bar[0] = 0u;  // ordered before the release below
       st_release32(bar + 1, gen + 1);
     } else {
       uint32_t spins = 0;
@@ -88,10 +95,9 @@ __device__ __forceinline__ void grid_barrier(uint32_t* bar, uint32_t* err) {
           latch_error(err, TDGS_ERR_TIMEOUT, kSiteBarrier);
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
-    __threadfence();
   }
   __syncthreads();
 }
@@ -166,8 +172,7 @@ struct PassArgs {
   uint32_t* err;
   // expansion (frame path, last pass): element = (global tile << rbits) | rank
   uint32_t rbits;
-  const uint32_t* sdepth;      // depth bits by rank
-  const uint32_t* sorder;      // global record index by rank
+  const uint2* sdo;            // by rank: {depth bits, global record index}
   const uint32_t* vrec_begin;  // [nv+1] first record of each view
   const uint32_t* vtile_begin; // [nv+1] first global tile of each view
   uint32_t nv;
@@ -368,7 +373,7 @@ __device__ __forceinline__ void chunk_bases(const K* __restrict__ kin, const Pas
 // when the tile was loaded), and (multi-pass tile sorts) records the
 // first/last position of each global tile run seen in this tile's exchange
 // buffer xk.
-template <typename K, bool kExpand>
+template <typename K, bool kExpand, bool kXform = false>
 __device__ __forceinline__ void emit_key(const PassArgs& a, K key, uint32_t gi, uint32_t dep, uint32_t dst,
                                          const K* xk, uint32_t p, uint32_t valid, const uint32_t* s_vrec,
                                          const uint32_t* s_vtile, void* kout_raw, uint32_t* vout) {
@@ -383,7 +388,7 @@ __device__ __forceinline__ void emit_key(const PassArgs& a, K key, uint32_t gi, 
     }
   } else {
     K out = key;
-    if constexpr (sizeof(K) == 4)
+    if constexpr (kXform)
       if (a.xform_out) out = key == a.cull ? 0xffffffffu : key + a.sub;
     static_cast<K*>(kout_raw)[dst] = out;
   }
@@ -478,7 +483,8 @@ struct TileRegs {
 // each warp, exclusive prefix over warps; on return (after a block
 // barrier) lstart holds the tile's count per digit.  Each warp's counter
 // row is zero on entry.
-template <bool kFull, typename S, typename K, bool kExpand, int kBits, int kItems>
+// kXform: the resident depth sort's key compression may apply (a.xform_in).
+template <bool kFull, typename S, typename K, bool kExpand, int kBits, int kItems, bool kXform = false>
 __device__ __forceinline__ void rank_tile(const K* __restrict__ kt, uint32_t valid, const PassArgs& a, bool d31,
                                           const Smem<K>& sm, TileRegs<K, kExpand, kItems>& R) {
   constexpr int kBins = S::kBins;
@@ -494,15 +500,16 @@ __device__ __forceinline__ void rank_tile(const K* __restrict__ kt, uint32_t val
   for (int j = 0; j < kItems; ++j) {
     const uint32_t idx = wbase + j * 32 + lane;
     R.k[j] = (kFull || idx < valid) ? __ldcs(kt + idx) : K(0);
-    if constexpr (sizeof(K) == 4)
+    if constexpr (kXform)
       if (a.xform_in) R.k[j] = R.k[j] == 0xffffffffu ? a.cull : R.k[j] - a.sub;
     R.d[j] = digit_of<K>(R.k[j], a.shift, a.mask, d31);
     if constexpr (kExpand) {
       R.gi[j] = R.dep[j] = 0u;
       if (kFull || idx < valid) {
         const uint32_t rk = static_cast<uint32_t>(R.k[j] & ((static_cast<K>(1) << a.rbits) - 1));
-        R.gi[j] = __ldg(a.sorder + rk);
-        R.dep[j] = __ldg(a.sdepth + rk);
+        const uint2 dg = __ldg(a.sdo + rk);
+        R.dep[j] = dg.x;
+        R.gi[j] = dg.y;
       }
     }
   }
@@ -567,7 +574,8 @@ __device__ __forceinline__ void rank_tile(const K* __restrict__ kt, uint32_t val
 // Returns false if a destination fell outside [0, m).  Block barriers:
 // after the digit starts and after the exchange (and one more for values);
 // this warp's counter row is zeroed again.
-template <bool kFull, typename S, typename K, bool kVals, bool kExpand, int kBits, int kItems>
+template <bool kFull, typename S, typename K, bool kVals, bool kExpand, int kBits, int kItems,
+          bool kXform = false>
 __device__ __forceinline__ bool scatter_tile(const uint32_t* __restrict__ vt, uint32_t valid, uint32_t m,
                                              const PassArgs& a, bool d31, const Smem<K>& sm, uint32_t* s_warp,
                                              const uint32_t* s_vrec, const uint32_t* s_vtile, void* kout_raw,
@@ -624,7 +632,7 @@ __device__ __forceinline__ bool scatter_tile(const uint32_t* __restrict__ vt, ui
         if constexpr (kExpand)
           emit_key<K, true>(a, key, sm.xg[p], sm.xd[p], dst[i], sm.xk, p, valid, s_vrec, s_vtile, kout_raw, vout);
         else
-          emit_key<K, false>(a, key, 0u, 0u, dst[i], sm.xk, p, valid, s_vrec, s_vtile, kout_raw, vout);
+          emit_key<K, false, kXform>(a, key, 0u, 0u, dst[i], sm.xk, p, valid, s_vrec, s_vtile, kout_raw, vout);
       } else {
         ok = false;
       }
@@ -838,11 +846,12 @@ __global__ void __launch_bounds__(kThreads, kOcc)
       a.mask = ra.mask[p];
     }
     TileRegs<K, false, kItems> R;
-    rank_tile<false, S, K, false, kBits, kItems>(kin + ch.beg, valid, a, false, sm, R);
+    rank_tile<false, S, K, false, kBits, kItems, sizeof(K) == 4>(kin + ch.beg, valid, a, false, sm, R);
     for (uint32_t b = t; b < static_cast<uint32_t>(S::kBins); b += kThreads)
       a.H[static_cast<size_t>(c) * S::kBins + b] = sm.lstart[b];
     scan_chunks<S::kBins, kThreads>(a, sm.base, s_warp, nullptr);
-    ok &= scatter_tile<false, S, K, true, false, kBits, kItems>(vin + ch.beg, valid, ch.m, a, false, sm, s_warp,
+    ok &= scatter_tile<false, S, K, true, false, kBits, kItems, sizeof(K) == 4>(vin + ch.beg, valid, ch.m, a, false,
+                                                                                 sm, s_warp,
                                                                  nullptr, nullptr, kout, vout, R);
     grid_barrier(a.bar, a.err);  // the next pass reads what every CTA wrote
   }

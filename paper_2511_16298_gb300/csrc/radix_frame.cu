@@ -108,8 +108,7 @@ cudaError_t launch_stream_pass(const StreamPass& sp, uint32_t* scratch, uint32_t
   a.shift = sp.shift;
   a.mask = sp.width >= 32 ? 0xffffffffu : (1u << sp.width) - 1;
   a.rbits = sp.rbits;
-  a.sdepth = sp.sdepth;
-  a.sorder = sp.sorder;
+  a.sdo = sp.sdo;
   if (sp.expand && sp.views) {
     a.vrec_begin = sp.views->rec_begin;
     a.vtile_begin = sp.views->tile_begin;

@@ -174,9 +174,11 @@ __device__ __forceinline__ uint32_t find_view(const uint32_t* begin, uint32_t nv
 cudaError_t launch_views_count(const ViewTable& vt, uint32_t n_all, uint32_t* counts,
                                uint32_t* dkey, uint32_t* dval, uint32_t* err, uint32_t* ticket,
                                uint64_t* total, uint32_t* range, cudaStream_t s);
+// sdo: receives {depth key, record index} per depth position (read by the
+// expanding tile pass with one 8-byte load per pair).
 cudaError_t launch_views_dup(const ViewTable& vt, const uint32_t* sorder, const uint32_t* soff,
                              uint32_t n_all, uint32_t rbits, void* out, bool wide, uint32_t cap,
-                             uint32_t* err, cudaStream_t s);
+                             uint2* sdo, uint32_t* err, cudaStream_t s);
 
 // Radix passes of the frame path (radix_frame.cu).
 // Depth sort of the N Gaussians: (uint32 depth key, uint32 index).  When
@@ -221,8 +223,7 @@ struct StreamPass {
   uint32_t m;
   const uint64_t* m_dev;
   uint32_t shift, width, rbits;
-  const uint32_t* sdepth;
-  const uint32_t* sorder;
+  const uint2* sdo;  // by depth position: {depth bits, record index}
   const ViewTable* views;  // expand only
   uint32_t* rmin;
   uint32_t* rmax;
