@@ -157,8 +157,8 @@ def algorithmic_bytes(kernel: str, items: int, n: int, m: int, tiles: int, depth
         return 16.0 * items * abs(depth_passes) + (12.0 * items if depth_passes < 0 else 0.0)
     if kernel == "scan_by_depth":    # index in, gathered count, offset out
         return 12.0 * items
-    if kernel == "duplicate_by_depth":  # index, offset, record in; 4 B per pair out
-        return 24.0 * items + 4.0 * m
+    if kernel == "duplicate_by_depth":  # index, offset, record in; {depth key, index} out; 4 B per pair out
+        return 32.0 * items + 4.0 * m
     if kernel == "tile_sort_pass":   # 4 B element in and out
         return 8.0 * items
     if kernel == "tile_expand_pass":  # 4 B element in; u64 key + u32 value out; depth tables once;
