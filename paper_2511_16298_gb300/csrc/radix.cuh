@@ -202,15 +202,14 @@ struct PassShape {
   static constexpr int kCols = kBins / 2;  // counter words: two 16-bit digits each
   static constexpr int kCpt = (kCols + kThreads - 1) / kThreads;
   // shared memory, no aliasing: per-warp counters | key exchange |
-  // gathered index and depth (expanding pass) | value exchange |
+  // value exchange |
   // base, lstart, off per digit
   static constexpr size_t kWhBytes = static_cast<size_t>(kWarps) * kBins * 2;
   static constexpr size_t kXkBytes = static_cast<size_t>(kTileKeys) * sizeof(K);
-  static constexpr size_t kXgBytes = kExpand ? static_cast<size_t>(kTileKeys) * 8 : 0;
   static constexpr size_t kXvBytes = kVals ? static_cast<size_t>(kTileKeys) * 4 : 0;
-  static constexpr size_t kSmem = kWhBytes + kXkBytes + kXgBytes + kXvBytes + static_cast<size_t>(kBins) * 12;
+  static constexpr size_t kSmem = kWhBytes + kXkBytes + kXvBytes + static_cast<size_t>(kBins) * 12;
   static constexpr int kMinBlocks =
-      kOcc > 0 ? kOcc : (kThreads >= 512 ? 1 : ((kExpand || kBits > 10 || sizeof(K) == 8) ? 2 : 3));
+      kOcc > 0 ? kOcc : (kThreads >= 512 ? 1 : ((kBits > 10 || sizeof(K) == 8) ? 2 : 3));
   static_assert(kBits >= 6 && kBits <= 12, "digits of 6..12 bits");
   static_assert(kTileKeys <= 32768, "per-warp counters and their prefixes are 16-bit");
   static_assert(kWhBytes % 16 == 0, "counters are cleared with 16-byte stores");
@@ -399,8 +398,6 @@ template <typename K>
 struct Smem {
   uint16_t* wh;     // [kWarps][kBins] per-warp digit counters, then exclusive prefixes over warps
   K* xk;            // key exchange
-  uint32_t* xg;     // expanding pass: gathered record index
-  uint32_t* xd;     // expanding pass: gathered depth bits
   uint32_t* xv;     // value exchange
   uint32_t* base;   // [kBins] running output base of this chunk per digit
   uint32_t* lstart; // [kBins] tile count per digit, then tile-local digit start
@@ -475,7 +472,6 @@ struct TileRegs {
   K k[kItems];
   uint32_t d[kItems];  // digits
   uint32_t r[kItems];  // ranks: within the warp, then within the tile
-  uint32_t gi[kExpand ? kItems : 1], dep[kExpand ? kItems : 1];
 };
 
 // Phase 3, first half, for one tile of `valid` keys starting at kt
@@ -494,8 +490,6 @@ __device__ __forceinline__ void rank_tile(const K* __restrict__ kt, uint32_t val
   constexpr int kCpt = S::kCpt;
   const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
   const uint32_t wbase = warp * 32 * kItems;
-  // expanding pass: the depth bits and record index of each element's
-  // depth rank are gathered now, so their latency hides behind the ranking
 #pragma unroll
   for (int j = 0; j < kItems; ++j) {
     const uint32_t idx = wbase + j * 32 + lane;
@@ -503,15 +497,6 @@ __device__ __forceinline__ void rank_tile(const K* __restrict__ kt, uint32_t val
     if constexpr (kXform)
       if (a.xform_in) R.k[j] = R.k[j] == 0xffffffffu ? a.cull : R.k[j] - a.sub;
     R.d[j] = digit_of<K>(R.k[j], a.shift, a.mask, d31);
-    if constexpr (kExpand) {
-      R.gi[j] = R.dep[j] = 0u;
-      if (kFull || idx < valid) {
-        const uint32_t rk = static_cast<uint32_t>(R.k[j] & ((static_cast<K>(1) << a.rbits) - 1));
-        const uint2 dg = __ldg(a.sdo + rk);
-        R.dep[j] = dg.x;
-        R.gi[j] = dg.y;
-      }
-    }
   }
   // rank within the warp, kGroup items at a time: the equal-digit lane
   // sets of the group first (independent ballot chains), then every lane
@@ -600,10 +585,6 @@ __device__ __forceinline__ bool scatter_tile(const uint32_t* __restrict__ vt, ui
   for (int j = 0; j < kItems; ++j) {
     if (kFull || wbase + j * 32 + lane < valid) {
       sm.xk[R.r[j]] = R.k[j];
-      if constexpr (kExpand) {
-        sm.xg[R.r[j]] = R.gi[j];
-        sm.xd[R.r[j]] = R.dep[j];
-      }
     }
   }
   // values are fetched only now (fewer registers live while ranking);
@@ -621,20 +602,50 @@ __device__ __forceinline__ bool scatter_tile(const uint32_t* __restrict__ vt, ui
   // from a timed-out barrier or keys changed underneath the sort: it is
   // dropped and reported instead of written.
   uint32_t dst[kItems];
+  if constexpr (kExpand) {
+    // the expanding pass gathers {depth key, record index} of each
+    // element's depth position now, kHalf loads in flight before the stores
+    constexpr int kHalf = kItems >= 16 ? kItems / 2 : kItems;
 #pragma unroll
-  for (int i = 0; i < kItems; ++i) {
-    const uint32_t p = i * kThreads + t;
-    dst[i] = 0xffffffffu;
-    if (kFull || p < valid) {
-      const K key = sm.xk[p];
-      dst[i] = sm.off[digit_of<K>(key, a.shift, a.mask, d31)] + p;
-      if (dst[i] < m) {
-        if constexpr (kExpand)
-          emit_key<K, true>(a, key, sm.xg[p], sm.xd[p], dst[i], sm.xk, p, valid, s_vrec, s_vtile, kout_raw, vout);
-        else
+    for (int i0 = 0; i0 < kItems; i0 += kHalf) {
+      K key[kHalf];
+      uint32_t at[kHalf];
+      uint2 dg[kHalf];
+#pragma unroll
+      for (int h = 0; h < kHalf; ++h) {
+        const uint32_t p = (i0 + h) * kThreads + t;
+        at[h] = 0xffffffffu;
+        key[h] = K(0);
+        dg[h] = make_uint2(0u, 0u);
+        if (kFull || p < valid) {
+          key[h] = sm.xk[p];
+          at[h] = sm.off[digit_of<K>(key[h], a.shift, a.mask, d31)] + p;
+          if (at[h] < m) dg[h] = __ldg(a.sdo + static_cast<uint32_t>(key[h] & ((static_cast<K>(1) << a.rbits) - 1)));
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < kHalf; ++h) {
+        const uint32_t p = (i0 + h) * kThreads + t;
+        if (kFull || p < valid) {
+          if (at[h] < m)
+            emit_key<K, true>(a, key[h], dg[h].y, dg[h].x, at[h], sm.xk, p, valid, s_vrec, s_vtile, kout_raw, vout);
+          else
+            ok = false;
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      const uint32_t p = i * kThreads + t;
+      dst[i] = 0xffffffffu;
+      if (kFull || p < valid) {
+        const K key = sm.xk[p];
+        dst[i] = sm.off[digit_of<K>(key, a.shift, a.mask, d31)] + p;
+        if (dst[i] < m)
           emit_key<K, false, kXform>(a, key, 0u, 0u, dst[i], sm.xk, p, valid, s_vrec, s_vtile, kout_raw, vout);
-      } else {
-        ok = false;
+        else
+          ok = false;
       }
     }
   }
@@ -679,9 +690,6 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
     q += S::kWhBytes;
     sm.xk = reinterpret_cast<K*>(q);
     q += S::kXkBytes;
-    sm.xg = reinterpret_cast<uint32_t*>(q);
-    sm.xd = sm.xg + (kExpand ? kTileKeys : 0);
-    q += S::kXgBytes;
     sm.xv = reinterpret_cast<uint32_t*>(q);
     q += S::kXvBytes;
     sm.base = reinterpret_cast<uint32_t*>(q);
@@ -791,7 +799,6 @@ __global__ void __launch_bounds__(kThreads, kOcc)
     q += S::kWhBytes;
     sm.xk = reinterpret_cast<K*>(q);
     q += S::kXkBytes;
-    sm.xg = sm.xd = nullptr;
     sm.xv = reinterpret_cast<uint32_t*>(q);
     q += S::kXvBytes;
     sm.base = reinterpret_cast<uint32_t*>(q);
