@@ -248,7 +248,8 @@ __device__ __forceinline__ void count_key(K k, const PassArgs& a, bool d31, uint
 // Phase 2, after every chunk has written its histogram row H[c][*]: a
 // grid barrier, one warp per digit scans the column over chunks (chunk
 // prefixes P, digit totals tot), a grid barrier, then base[b] = first
-// output position of this chunk's keys with digit b.  With a.ranges set,
+// output position of this chunk's keys with digit b.  With at most 64
+// digits each CTA sums the rows itself after the first barrier.  With a.ranges set,
 // the tile ranges are written from the digit totals.
 template <int kBins, int kThreads>
 __device__ __forceinline__ void scan_chunks(const PassArgs& a, uint32_t* base, uint32_t* s_warp,
@@ -257,6 +258,54 @@ __device__ __forceinline__ void scan_chunks(const PassArgs& a, uint32_t* base, u
   constexpr int kBpt = (kBins + kThreads - 1) / kThreads;
   const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
   const uint32_t G = gridDim.x, c = blockIdx.x;
+  if constexpr (kBins <= 64) {
+    // Few digits: after one grid barrier every CTA sums the histogram rows
+    // itself (16-byte loads, kRows row groups in parallel): the rows of the
+    // chunks before it and all rows.  No second barrier, no P or tot.
+    constexpr int kQ = kBins / 4;          // 16-byte words per row
+    constexpr int kRows = kThreads / kQ;   // row groups
+    __shared__ uint4 s_pre[kRows][kQ];
+    __shared__ uint4 s_all[kRows][kQ];
+    grid_barrier(a.bar, a.err);
+    const uint32_t q = t % kQ, r = t / kQ;
+    uint4 pre = make_uint4(0, 0, 0, 0), all = make_uint4(0, 0, 0, 0);
+#pragma unroll 8
+    for (uint32_t cc = r; cc < G; cc += kRows) {
+      const uint4 h = __ldcg(reinterpret_cast<const uint4*>(a.H + static_cast<size_t>(cc) * kBins) + q);
+      all.x += h.x; all.y += h.y; all.z += h.z; all.w += h.w;
+      if (cc < c) {
+        pre.x += h.x; pre.y += h.y; pre.z += h.z; pre.w += h.w;
+      }
+    }
+    s_pre[r][q] = pre;
+    s_all[r][q] = all;
+    __syncthreads();
+    uint32_t seg = 0, before = 0;
+    if (t < static_cast<uint32_t>(kBins)) {
+      const uint32_t* sp = reinterpret_cast<const uint32_t*>(&s_pre[0][0]);
+      const uint32_t* sa = reinterpret_cast<const uint32_t*>(&s_all[0][0]);
+#pragma unroll
+      for (int rr = 0; rr < kRows; ++rr) {
+        seg += sa[rr * kBins + t];
+        before += sp[rr * kBins + t];
+      }
+    }
+    const uint32_t run = block_excl_scan<kWarps>(seg, s_warp);
+    if (t < static_cast<uint32_t>(kBins)) {
+      const uint32_t b = t;
+      base[b] = run + before;
+      if (a.ranges && !a.rmin && b < a.t_all && b % G == c) {
+        uint2 rg = make_uint2(0u, 0u);
+        if (seg) {
+          const uint32_t pb = a.pbeg[a.nv == 1 ? 0u : find_view(s_vtile, a.nv, b)];
+          rg = make_uint2(run - pb, run + seg - pb);
+        }
+        a.ranges[b] = rg;
+      }
+    }
+    __syncthreads();
+    return;
+  }
   grid_barrier(a.bar, a.err);
   // Lane l holds chunks l*kCol .. l*kCol+kCol-1 of one digit column; all
   // loads are issued before the scan so the column costs one L2 round trip.
