@@ -57,6 +57,8 @@ def load(path: str):
     L.oracle_duplicate.argtypes = [P, P, u32, u32, u32, P, P, u32]
     L.oracle_sort_pairs.argtypes = [P, P, u32]
     L.oracle_tile_ranges.argtypes = [P, u32, u32, P]
+    L.oracle_preprocess.argtypes = [P, P, u32, P, P, P]
+    L.oracle_preprocess.restype = ctypes.c_int
     L.oracle_num_tiles.argtypes = [u32, u32]
     L.oracle_num_tiles.restype = u32
     for f in ("oracle_count_tiles", "oracle_scan", "oracle_duplicate",
@@ -100,6 +102,9 @@ class Oracle:
 
     def sort_frame(self, g, width, height):
         return sort_frame(g, width, height, L=self._lib())
+
+    def preprocess(self, g3, cov, cam):
+        return preprocess(g3, cov, cam, L=self._lib())
 
 
 def _ptr(a: np.ndarray):
@@ -149,6 +154,27 @@ def tile_ranges(sorted_keys: np.ndarray, num_tiles: int, L=None):
     ranges = np.zeros((num_tiles, 2), dtype=np.uint32)
     st = (L or lib()).oracle_tile_ranges(_ptr(sorted_keys), len(sorted_keys), num_tiles, _ptr(ranges))
     return st, ranges
+
+
+_REC = np.dtype([("x", "<f4"), ("y", "<f4"), ("depth", "<f4"), ("radius", "<i4")])
+
+
+def preprocess(g3: np.ndarray, cov: np.ndarray, cam: np.ndarray, L=None):
+    """Preprocessing of 3D Gaussians for one camera: returns (status,
+    records, conic_opacity) with records as 16-byte (x, y, depth, radius)
+    and conic_opacity as (n, 4) float32.  g3: 16-byte records (mean,
+    opacity); cov: 32-byte records (xx, xy, xz, yy, yz, zz, pad, pad);
+    cam: one 76-byte camera block."""
+    g3 = np.ascontiguousarray(g3)
+    cov = np.ascontiguousarray(cov)
+    cam = np.ascontiguousarray(cam)
+    assert g3.dtype.itemsize == 16 and cov.dtype.itemsize == 32 and cam.dtype.itemsize == 76
+    assert cam.size == 1 and len(cov) == len(g3)
+    n = len(g3)
+    rec = np.zeros(n, dtype=_REC)
+    conic = np.zeros((n, 4), dtype=np.float32)
+    st = (L or lib()).oracle_preprocess(_ptr(g3), _ptr(cov), n, _ptr(cam.reshape(1)), _ptr(rec), _ptr(conic))
+    return st, rec, conic
 
 
 def num_tiles(width: int, height: int, L=None) -> int:

@@ -200,6 +200,105 @@ int oracle_tile_ranges(const uint64_t* sorted_keys, uint32_t m, uint32_t num_til
   return kOk;
 }
 
+// Preprocessing (Sec. II-A "Preprocessing"; inputs Table I, outputs
+// Table IV): camera transform of the mean, frustum culling, projection of
+// the mean to pixels, projection of the 3D covariance to the 2D footprint
+// covariance, its inverse (the conic) and the 3-sigma radius.  The paper
+// names the stage, its inputs and its outputs but prints no formulas; the
+// reading here is the EWA splatting projection of 3D Gaussian Splatting
+// (the pipeline the paper accelerates):
+//   t = R p + T                          camera-space mean (R row-major)
+//   culled unless t.z > near_z
+//   u = t.x / t.z, v = t.y / t.z;  x = fx u + cx,  y = fy v + cy
+//   Jacobian of the perspective map at the mean, with the slopes clamped to
+//   1.3 times the half field of view (lim_x = 0.65 W / fx, lim_y = 0.65 H / fy):
+//     J = [[fx / t.z, 0, -fx uc / t.z], [0, fy / t.z, -fy vc / t.z]]
+//   S2 = (J R) S3 (J R)^T + 0.3 I        (0.3: low-pass dilation)
+//   culled unless det(S2) > 0
+//   conic = (S2_yy, -S2_xy, S2_xx) / det
+//   lambda = mid + sqrt(max(0.1, mid^2 - det)),  mid = (S2_xx + S2_yy) / 2
+//   radius = ceil(3 sqrt(lambda))        (culled unless x, y, radius finite;
+//                                         radius capped at 2^30)
+// Precision: float32, every operation rounded in the order written (the
+// library computes in float32; the radius is an integer decided by float
+// arithmetic, so both sides decide it in the same precision and order).
+// The oracle is compiled with -ffp-contract=off (no fused multiply-add).
+// A culled Gaussian gets the record {0, 0, 0, 0} and the conic {0, 0, 0, 0}.
+struct G3 {  // Table I, Group 1: mean and opacity
+  float x, y, z, opacity;
+};
+struct C3 {  // Table I, Group 2: the six entries of the symmetric 3D covariance, two texels
+  float xx, xy, xz, yy, yz, zz, pad0, pad1;
+};
+struct Cam {
+  float rot[9];    // world -> camera rotation, row-major
+  float trans[3];  // camera-space translation
+  float fx, fy, cx, cy, near_z;
+  uint32_t width, height;
+};
+static_assert(sizeof(C3) == 32, "covariance is two 16-byte texels");
+static_assert(sizeof(Cam) == 76, "camera block: 19 four-byte fields");
+
+int oracle_preprocess(const G3* g, const C3* cov, uint32_t n, const Cam* cam, G2* rec,
+                      float* conic_opacity) {
+  if (!(cam->fx > 0.0f) || !(cam->fy > 0.0f) || cam->width == 0 || cam->height == 0) return kInvalid;
+  const float* R = cam->rot;
+  const float lim_x = (0.65f * static_cast<float>(cam->width)) / cam->fx;
+  const float lim_y = (0.65f * static_cast<float>(cam->height)) / cam->fy;
+  for (uint32_t i = 0; i < n; ++i) {
+    G2 out = {0.0f, 0.0f, 0.0f, 0};
+    float co[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const G3 p = g[i];
+    const float tx = ((R[0] * p.x + R[1] * p.y) + R[2] * p.z) + cam->trans[0];
+    const float ty = ((R[3] * p.x + R[4] * p.y) + R[5] * p.z) + cam->trans[1];
+    const float tz = ((R[6] * p.x + R[7] * p.y) + R[8] * p.z) + cam->trans[2];
+    bool keep = tz > cam->near_z;
+    if (keep) {
+      const float u = tx / tz, v = ty / tz;
+      const float px = cam->fx * u + cam->cx;
+      const float py = cam->fy * v + cam->cy;
+      const float uc = std::fmin(lim_x, std::fmax(-lim_x, u));
+      const float vc = std::fmin(lim_y, std::fmax(-lim_y, v));
+      const float j00 = cam->fx / tz, j02 = -((cam->fx * uc) / tz);
+      const float j11 = cam->fy / tz, j12 = -((cam->fy * vc) / tz);
+      float T[2][3];
+      for (int k = 0; k < 3; ++k) {
+        T[0][k] = j00 * R[k] + j02 * R[6 + k];
+        T[1][k] = j11 * R[3 + k] + j12 * R[6 + k];
+      }
+      const C3& c = cov[i];
+      const float S[3][3] = {{c.xx, c.xy, c.xz}, {c.xy, c.yy, c.yz}, {c.xz, c.yz, c.zz}};
+      float M[2][3];
+      for (int r = 0; r < 2; ++r)
+        for (int k = 0; k < 3; ++k) M[r][k] = (T[r][0] * S[0][k] + T[r][1] * S[1][k]) + T[r][2] * S[2][k];
+      const float a = ((M[0][0] * T[0][0] + M[0][1] * T[0][1]) + M[0][2] * T[0][2]) + 0.3f;
+      const float b = (M[0][0] * T[1][0] + M[0][1] * T[1][1]) + M[0][2] * T[1][2];
+      const float d = ((M[1][0] * T[1][0] + M[1][1] * T[1][1]) + M[1][2] * T[1][2]) + 0.3f;
+      const float det = a * d - b * b;
+      keep = det > 0.0f;
+      if (keep) {
+        const float mid = 0.5f * (a + d);
+        const float disc = mid * mid - det;
+        const float lambda = mid + std::sqrt(std::fmax(0.1f, disc));
+        float r = std::ceil(3.0f * std::sqrt(lambda));
+        keep = std::isfinite(px) && std::isfinite(py) && std::isfinite(r);
+        if (keep) {
+          if (r > 1073741824.0f) r = 1073741824.0f;
+          out = {px, py, tz, static_cast<int32_t>(r)};
+          co[0] = d / det;
+          co[1] = -(b / det);
+          co[2] = a / det;
+          co[3] = p.opacity;
+        }
+      }
+    }
+    rec[i] = out;
+    if (conic_opacity)
+      for (int k = 0; k < 4; ++k) conic_opacity[4 * static_cast<size_t>(i) + k] = co[k];
+  }
+  return kOk;
+}
+
 // Number of tiles and tile bits of an image (helpers for callers).
 uint32_t oracle_num_tiles(uint32_t width, uint32_t height) {
   return grid_dim(width) * grid_dim(height);

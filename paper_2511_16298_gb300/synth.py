@@ -19,6 +19,11 @@ stand-ins with the sizes and value distributions of those frames:
 * ``multiview``    - one 500,000-Gaussian 3D scene seen by 64 pinhole
   cameras (the projection happens here, as part of input generation).
 * ``request_trace``- a Poisson stream of frames of mixed size/resolution.
+* ``scene3d``      - the unprojected input of the preprocessing step: the
+  multiview scene's means with opacities and anisotropic 3D covariances
+  (Table I packing), and the same camera lattice as world-to-camera blocks.
+  Building each covariance from its scales and rotation is input generation;
+  projecting it is the method's and is not done here.
 
 All draws use ``numpy.random.default_rng(seed)`` in float64 and are rounded
 to float32 at the end; radius = ceil(3 * sigma) computed in float64.
@@ -207,6 +212,92 @@ def multiview(seed: int = 0, n: int = 500_000, views: int = 64, width: int = 128
         depth = np.where(ok, zc, 1.0)
         out.append(Frame(width, height, records(px, py, depth, r), f"view{v}"))
     return MultiView(out, scale0, seed)
+
+
+# ------------------------------------------------------------ 3D scene input
+# Table I packing: Group 1 = mean and opacity (one 16-byte texel), Group 2 =
+# the six entries of the symmetric 3D covariance (two texels).
+GAUSSIAN3D = np.dtype([("x", "<f4"), ("y", "<f4"), ("z", "<f4"), ("opacity", "<f4")])
+COV3D = np.dtype([("xx", "<f4"), ("xy", "<f4"), ("xz", "<f4"), ("yy", "<f4"), ("yz", "<f4"),
+                  ("zz", "<f4"), ("pad0", "<f4"), ("pad1", "<f4")])
+# World-to-camera block of a pinhole camera: p_cam = rot @ p + trans.
+CAMERA = np.dtype([("rot", "<f4", (9,)), ("trans", "<f4", (3,)), ("fx", "<f4"), ("fy", "<f4"),
+                   ("cx", "<f4"), ("cy", "<f4"), ("near_z", "<f4"), ("width", "<u4"),
+                   ("height", "<u4")])
+assert GAUSSIAN3D.itemsize == 16 and COV3D.itemsize == 32 and CAMERA.itemsize == 76
+
+
+@dataclasses.dataclass
+class Scene3D:
+    """Unprojected Gaussians and the cameras that see them."""
+
+    gaussians: np.ndarray  # GAUSSIAN3D
+    cov: np.ndarray        # COV3D
+    cameras: np.ndarray    # CAMERA, one per view
+    seed: int
+
+    @property
+    def n(self) -> int:
+        return int(self.gaussians.shape[0])
+
+
+def camera(eye, target, width: int, height: int, fx: float = 1108.5, fy: float = 1108.5,
+           near_z: float = 0.2) -> np.ndarray:
+    """One CAMERA block looking from ``eye`` at ``target`` with up = +y:
+    camera axes right, down, forward (rows of rot), principal point at the
+    image centre."""
+    eye = np.asarray(eye, dtype=np.float64)
+    fwd = np.asarray(target, dtype=np.float64) - eye
+    fwd /= np.linalg.norm(fwd)
+    right = np.cross(fwd, np.array([0.0, 1.0, 0.0]))
+    if np.linalg.norm(right) < 1e-6:
+        right = np.array([1.0, 0.0, 0.0])
+    right /= np.linalg.norm(right)
+    down = np.cross(fwd, right)
+    rot = np.stack([right, down, fwd])
+    c = np.zeros((), dtype=CAMERA)
+    c["rot"] = rot.reshape(9).astype(np.float32)
+    c["trans"] = (-(rot @ eye)).astype(np.float32)
+    c["fx"], c["fy"] = fx, fy
+    c["cx"], c["cy"] = width / 2.0, height / 2.0
+    c["near_z"] = near_z
+    c["width"], c["height"] = width, height
+    return c
+
+
+def scene3d(seed: int = 0, n: int = 500_000, views: int = 64, width: int = 1280, height: int = 720,
+            scale0: float = 0.03, cam_radius: float = 15.0) -> Scene3D:
+    """Means ~ U[0,1)^3 * 10 - 5 (the multiview scene's distribution);
+    per-axis scales s0 * lognormal(0, 0.5); rotations uniform (normalised
+    Gaussian quaternions); cov = Rq diag(s^2) Rq^T in float64, rounded to
+    float32; opacity ~ U[0.05, 1).  Cameras: Fibonacci lattice of a sphere
+    of radius ``cam_radius`` looking at the origin plus a jitter uniform in
+    a ball of radius 4, fx = fy = 1108.5, near plane 0.2."""
+    rng = np.random.default_rng(seed)
+    mean3 = rng.random((n, 3)) * 10.0 - 5.0
+    scales = scale0 * np.exp(rng.normal(0.0, 0.5, size=(n, 3)))
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+    rq = np.stack([
+        np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], 1),
+        np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], 1),
+        np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], 1),
+    ], 1)  # (n, 3, 3)
+    s3 = np.einsum("nij,nj,nkj->nik", rq, scales * scales, rq)
+    g = np.empty(n, dtype=GAUSSIAN3D)
+    g["x"], g["y"], g["z"] = (mean3[:, k].astype(np.float32) for k in range(3))
+    g["opacity"] = rng.uniform(0.05, 1.0, size=n).astype(np.float32)
+    cov = np.zeros(n, dtype=COV3D)
+    for name, (i, j) in (("xx", (0, 0)), ("xy", (0, 1)), ("xz", (0, 2)), ("yy", (1, 1)),
+                         ("yz", (1, 2)), ("zz", (2, 2))):
+        cov[name] = s3[:, i, j].astype(np.float32)
+    eye = _fibonacci_sphere(views) * cam_radius
+    u = rng.normal(size=(views, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    jitter = u * (4.0 * rng.random(views) ** (1.0 / 3.0))[:, None]
+    cams = np.stack([camera(eye[v], jitter[v], width, height) for v in range(views)])
+    return Scene3D(g, cov, cams, seed)
 
 
 # ------------------------------------------------------------ request trace

@@ -20,6 +20,7 @@ least one of them.
 from __future__ import annotations
 
 import json
+import math
 import os
 import struct
 
@@ -283,8 +284,147 @@ def check_float_order(samples: int = 10_000_000):
             assert (edge[i] < edge[j]) == (eb[i] < eb[j])
 
 
+# ------------------------------------------------------------ preprocessing
+def _cam(rot=None, trans=(0.0, 0.0, 0.0), fx=1000.0, fy=1000.0, cx=640.0, cy=360.0,
+         near=0.2, width=1280, height=720):
+    c = np.zeros((), dtype=synth.CAMERA)
+    c["rot"] = np.eye(3).reshape(9) if rot is None else np.asarray(rot, dtype=np.float64).reshape(9)
+    c["trans"] = trans
+    c["fx"], c["fy"], c["cx"], c["cy"], c["near_z"] = fx, fy, cx, cy, near
+    c["width"], c["height"] = width, height
+    return c
+
+
+def _g3(points, covs, opacity=0.5):
+    """points: (n, 3); covs: (n, 3, 3) symmetric."""
+    points = np.asarray(points, dtype=np.float64)
+    covs = np.asarray(covs, dtype=np.float64)
+    g = np.zeros(len(points), dtype=synth.GAUSSIAN3D)
+    g["x"], g["y"], g["z"] = points[:, 0], points[:, 1], points[:, 2]
+    g["opacity"] = opacity
+    c = np.zeros(len(points), dtype=synth.COV3D)
+    for name, (i, j) in (("xx", (0, 0)), ("xy", (0, 1)), ("xz", (0, 2)), ("yy", (1, 1)),
+                         ("yz", (1, 2)), ("zz", (2, 2))):
+        c[name] = covs[:, i, j]
+    return g, c
+
+
+def _footprint(a, b, c):
+    """Closed forms of a symmetric 2x2 [[a, b], [b, c]] in float64: the
+    larger eigenvalue with the 0.1 floor on the discriminant, the 3-sigma
+    radius (before ceil) and the inverse as (c, -b, a) / det."""
+    mid = 0.5 * (a + c)
+    det = a * c - b * b
+    lam = mid + math.sqrt(max(0.1, mid * mid - det))
+    return 3.0 * math.sqrt(lam), np.array([c / det, -b / det, a / det])
+
+
+def _check_case(O, pt, cov, cam, expect_xy, s2, tag):
+    """One Gaussian against closed forms: projected mean, depth, conic
+    (relative 2e-6 plus 1e-6 times the determinant's cancellation factor)
+    and the radius (exact, cases whose 3-sigma value lies
+    within 1e-3 of an integer are not used)."""
+    g, c = _g3([pt], [cov])
+    st, rec, con = O.preprocess(g, c, cam)
+    assert st == 0, tag
+    r3, conic = _footprint(*s2)
+    assert abs(r3 - round(r3)) > 1e-3, f"{tag}: pick a case away from an integer radius"
+    assert rec["radius"][0] == math.ceil(r3), (tag, rec["radius"][0], r3)
+    assert np.allclose([rec["x"][0], rec["y"][0]], expect_xy, rtol=1e-6, atol=1e-4), tag
+    assert rec["depth"][0] == np.float32(pt[2]), tag
+    a, b, c = s2
+    kappa = (abs(a * c) + b * b) / (a * c - b * b)  # cancellation in the determinant
+    assert np.allclose(con[0, :3], conic, rtol=2e-6 + kappa * 1e-6, atol=1e-9), (tag, con[0], conic)
+    assert con[0, 3] == np.float32(0.5), tag
+
+
+def check_preprocess(O):
+    """Projection of single Gaussians whose 2D footprint has a closed form
+    (identity camera unless stated; fx = fy = 1000, 1280x720, centre
+    (640, 360), near plane 0.2):
+    * on the optical axis, isotropic sigma s at depth z: footprint
+      (fx s / z)^2 + 0.3 on both axes, no cross term; equal axes put the
+      0.1 floor on the discriminant;
+    * off axis (X, Y, Z), diagonal covariance: with u = X/Z, v = Y/Z,
+      a = fx^2 (sx^2 + u^2 sz^2) / Z^2 + 0.3, b = fx fy u v sz^2 / Z^2,
+      c = fy^2 (sy^2 + v^2 sz^2) / Z^2 + 0.3;
+    * a slope beyond 1.3 x the half field of view: u is clamped to
+      0.65 W / fx in the footprint but not in the projected mean;
+    * on the axis with a full covariance: a = (fx/Z)^2 Sxx + 0.3,
+      b = fx fy / Z^2 Sxy, c = (fy/Z)^2 Syy + 0.3;
+    * invariance: rotating the scene and the camera together changes
+      nothing; culling at the near plane, behind the camera, for
+      non-finite means and for a negative covariance."""
+    fx = fy = 1000.0
+    cam = _cam()
+    # on axis, isotropic
+    for z, s in ((5.0, 0.0075), (2.0, 0.011), (10.0, 0.3), (40.0, 0.21)):
+        k = (fx * s / z) ** 2 + 0.3
+        _check_case(O, (0.0, 0.0, z), np.eye(3) * s * s, cam, (640.0, 360.0), (k, 0.0, k), f"axis z={z}")
+    # off axis, diagonal covariance
+    for (X, Y, Z), (sx, sy, sz) in (((0.7, -0.4, 6.0), (0.02, 0.05, 0.09)),
+                                     ((-1.1, 0.9, 3.5), (0.004, 0.003, 0.2)),
+                                     ((2.0, 1.0, 9.0), (0.1, 0.02, 0.03))):
+        u, v = X / Z, Y / Z
+        a = fx * fx * (sx * sx + u * u * sz * sz) / (Z * Z) + 0.3
+        b = fx * fy * u * v * sz * sz / (Z * Z)
+        c = fy * fy * (sy * sy + v * v * sz * sz) / (Z * Z) + 0.3
+        _check_case(O, (X, Y, Z), np.diag([sx * sx, sy * sy, sz * sz]), cam,
+                    (fx * u + 640.0, fy * v + 360.0), (a, b, c), f"off axis {X},{Y},{Z}")
+    # slope clamped (u = 1.4 > 0.65 * 1280 / 1000 = 0.832)
+    X, Z, sx, sy, sz = 7.0, 5.0, 0.01, 0.02, 0.05
+    lim = 0.65 * 1280 / fx
+    a = fx * fx * (sx * sx + lim * lim * sz * sz) / (Z * Z) + 0.3
+    c = fy * fy * (sy * sy) / (Z * Z) + 0.3
+    _check_case(O, (X, 0.0, Z), np.diag([sx * sx, sy * sy, sz * sz]), cam,
+                (fx * X / Z + 640.0, 360.0), (a, 0.0, c), "clamped slope")
+    # on axis, full covariance
+    S = np.array([[0.0009, 0.0004, -0.0002], [0.0004, 0.0016, 0.0003], [-0.0002, 0.0003, 0.0025]])
+    Z = 4.0
+    a = (fx / Z) ** 2 * S[0, 0] + 0.3
+    b = fx * fy / Z ** 2 * S[0, 1]
+    c = (fy / Z) ** 2 * S[1, 1] + 0.3
+    _check_case(O, (0.0, 0.0, Z), S, cam, (640.0, 360.0), (a, b, c), "full covariance")
+
+    # invariance under a common rotation of scene and camera
+    rng = np.random.default_rng(11)
+    pts = np.stack([rng.uniform(-2, 2, 64), rng.uniform(-1, 1, 64), rng.uniform(3, 12, 64)], 1)
+    A = rng.normal(size=(64, 3, 3)) * 0.03
+    covs = A @ A.transpose(0, 2, 1) + np.eye(3) * 1e-4
+    g, cv = _g3(pts, covs)
+    st0, rec0, con0 = O.preprocess(g, cv, cam)
+    th = 0.7
+    Q = np.array([[math.cos(th), 0, math.sin(th)], [0, 1, 0], [-math.sin(th), 0, math.cos(th)]])
+    g2, cv2 = _g3(pts @ Q.T, Q @ covs @ Q.T)
+    st1, rec1, con1 = O.preprocess(g2, cv2, _cam(rot=Q.T))
+    assert st0 == st1 == 0
+    assert np.allclose(rec0["x"], rec1["x"], rtol=1e-5, atol=2e-3)
+    assert np.allclose(rec0["y"], rec1["y"], rtol=1e-5, atol=2e-3)
+    assert np.allclose(rec0["depth"], rec1["depth"], rtol=1e-5)
+    assert np.allclose(con0, con1, rtol=2e-3, atol=1e-6)
+    assert np.all(np.abs(rec0["radius"] - rec1["radius"]) <= 1)
+    assert np.mean(rec0["radius"] == rec1["radius"]) > 0.9
+
+    # culling: at the near plane, just beyond it, behind, non-finite, negative covariance
+    near = np.float32(0.2)
+    beyond = float(np.nextafter(near, np.float32(1)))
+    pts = [(0, 0, float(near)), (0, 0, beyond), (0, 0, -3.0), (float("nan"), 0, 5.0),
+           (0, 0, float("inf")), (0, 0, 5.0)]
+    covs = [np.eye(3) * 1e-4] * 5 + [-np.eye(3)]
+    g, cv = _g3(pts, covs)
+    st, rec, con = O.preprocess(g, cv, cam)
+    assert st == 0
+    assert list(rec["radius"]) == [0, rec["radius"][1], 0, 0, 0, 0]
+    assert rec["radius"][1] > 0 and rec["depth"][1] == np.float32(beyond)
+    for i in (0, 2, 3, 4, 5):
+        assert tuple(rec[i]) == (0.0, 0.0, 0.0, 0) and not np.any(con[i])
+    # invalid camera
+    bad = _cam(fx=0.0)
+    assert O.preprocess(g, cv, bad)[0] == 1
+
+
 ALL_CHECKS = (check_golden, check_count_and_duplicate_bruteforce, check_special_cases,
-              check_validity, check_scan, check_sort)
+              check_validity, check_scan, check_sort, check_preprocess)
 
 
 def run_all(O) -> list[str]:

@@ -35,6 +35,15 @@ MUTANTS = {
                       "return keys[a] < keys[b] || (keys[a] == keys[b] && a > b); });"),
     "range_end_short": ("ranges[2 * prev + 1] = m;", "ranges[2 * prev + 1] = m - 1;"),
     "range_start_skipped": ("      ranges[2 * t] = k;\n", "      ranges[2 * t] = k ? k - 1 : 0;\n"),
+    "no_lowpass": ("M[0][2] * T[0][2]) + 0.3f;", "M[0][2] * T[0][2]);"),
+    "smaller_eigenvalue": ("const float lambda = mid + std::sqrt", "const float lambda = mid - std::sqrt"),
+    "no_discriminant_floor": ("std::fmax(0.1f, disc)", "std::fmax(0.0f, disc)"),
+    "jacobian_sign": ("j02 = -((cam->fx * uc) / tz);", "j02 = ((cam->fx * uc) / tz);"),
+    "no_slope_clamp": ("const float uc = std::fmin(lim_x, std::fmax(-lim_x, u));", "const float uc = u;"),
+    "cull_at_near_plane": ("bool keep = tz > cam->near_z;", "bool keep = tz >= cam->near_z;"),
+    "two_sigma": ("std::ceil(3.0f * std::sqrt(lambda))", "std::ceil(2.0f * std::sqrt(lambda))"),
+    "conic_swapped": ("co[0] = d / det;", "co[0] = a / det;"),
+    "rotation_transposed": ("T[0][k] = j00 * R[k] + j02 * R[6 + k];", "T[0][k] = j00 * R[3 * k] + j02 * R[6 + k];"),
 }
 
 
