@@ -217,8 +217,9 @@ int oracle_tile_ranges(const uint64_t* sorted_keys, uint32_t m, uint32_t num_til
 //   culled unless det(S2) > 0
 //   conic = (S2_yy, -S2_xy, S2_xx) / det
 //   lambda = mid + sqrt(max(0.1, mid^2 - det)),  mid = (S2_xx + S2_yy) / 2
-//   radius = ceil(3 sqrt(lambda))        (culled unless x, y, radius finite;
-//                                         radius capped at 2^30)
+//   radius = ceil(3 sqrt(lambda))        (culled unless x, y, depth and
+//                                         radius are finite; radius capped
+//                                         at 2^30)
 // Precision: float32, every operation rounded in the order written (the
 // library computes in float32; the radius is an integer decided by float
 // arithmetic, so both sides decide it in the same precision and order).
@@ -281,7 +282,7 @@ int oracle_preprocess(const G3* g, const C3* cov, uint32_t n, const Cam* cam, G2
         const float disc = mid * mid - det;
         const float lambda = mid + std::sqrt(std::fmax(0.1f, disc));
         float r = std::ceil(3.0f * std::sqrt(lambda));
-        keep = std::isfinite(px) && std::isfinite(py) && std::isfinite(r);
+        keep = std::isfinite(px) && std::isfinite(py) && std::isfinite(tz) && std::isfinite(r);
         if (keep) {
           if (r > 1073741824.0f) r = 1073741824.0f;
           out = {px, py, tz, static_cast<int32_t>(r)};

@@ -409,7 +409,7 @@ def check_preprocess(O):
     near = np.float32(0.2)
     beyond = float(np.nextafter(near, np.float32(1)))
     pts = [(0, 0, float(near)), (0, 0, beyond), (0, 0, -3.0), (float("nan"), 0, 5.0),
-           (0, 0, float("inf")), (0, 0, 5.0)]
+           (0, 0, float("inf")), (0, 0, 5.0)]  # the point at infinite depth: depth not finite
     covs = [np.eye(3) * 1e-4] * 5 + [-np.eye(3)]
     g, cv = _g3(pts, covs)
     st, rec, con = O.preprocess(g, cv, cam)
