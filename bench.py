@@ -429,6 +429,78 @@ def run_batched(args, local_rank):
             "batched": summ(t_batch), "batched_graph": summ(t_graph)}
 
 
+# ------------------------------------------------------- 3D frames
+def run_frame3d(args, local_rank):
+    """Preprocessing plus the sort from unprojected 3D Gaussians: the
+    500,000-Gaussian scene of the multi-view workload with anisotropic
+    covariances, camera 0 timed as a frame (tdgs_sort_frame_3d, L2 flushed
+    between steps), then every one of the 64 cameras in turn.  Roofline of
+    the preprocessing kernel: 48 B read + 32 B written per Gaussian."""
+    import torch
+
+    from paper_2511_16298_gb300 import synth, tdgs
+
+    dev = torch.device("cuda", local_rank)
+    sc = synth.scene3d(seed=0)
+    g = torch.from_numpy(sc.gaussians.view(np.float32).reshape(-1, 4).copy()).to(dev)
+    c = torch.from_numpy(sc.cov.view(np.float32).reshape(-1, 8).copy()).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ctx = tdgs.Context(local_rank)
+    stream = torch.cuda.current_stream(dev)
+    cam0 = sc.cameras[0]
+    for _ in range(args.warmup):
+        ctx.sort_frame_3d(g, c, cam0)
+        flush.zero_()
+    m = ctx.sort_frame_3d(g, c, cam0)[3]
+    ctx.sync()
+
+    def timed(fn, reps):
+        out = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            out.append(a.elapsed_time(b))
+        return out
+
+    t_frame = timed(lambda: ctx.sort_frame_3d(g, c, cam0), args.steps)
+    ctx.enable_timing(True)
+    timed(lambda: ctx.sort_frame_3d(g, c, cam0), args.steps)
+    ctx.sync()
+    kt = ctx.kernel_times()
+    ctx.enable_timing(False)
+    pre = kt.get("preprocess", {"ms": 0.0, "launches": 1})
+    pre_ms = pre["ms"] / max(1, pre["launches"])
+    peak, peak_kind = measured_peaks()
+    pre_gbs = 80.0 * sc.n / (pre_ms * 1e-3) / 1e9 if pre_ms > 0 else None
+    ms_views, m_views = [], 0
+    for v in range(len(sc.cameras)):
+        t = timed(lambda: ctx.sort_frame_3d(g, c, sc.cameras[v]), 1)
+        ms_views.append(t[0])
+        m_views += ctx.sort_frame_3d(g, c, sc.cameras[v])[3]
+    ctx.sync()
+    ctx.close()
+    return {"workload": "500,000 3D Gaussians (anisotropic covariances, seed 0), 1280x720 pinhole "
+                        "cameras on a radius-15 sphere; camera 0 as the frame",
+            "gaussians": sc.n, "pairs": m,
+            "frame": {"pairs_per_s": m / (statistics.median(t_frame) * 1e-3),
+                      "p50_ms": round(statistics.median(t_frame), 4),
+                      "p99_ms": round(float(np.percentile(t_frame, 99)), 4)},
+            "preprocess": {"avg_ms": round(pre_ms, 5), "bytes_per_gaussian": 80,
+                           "achieved_gbs": round(pre_gbs, 1) if pre_gbs else None,
+                           "peak": peak, "frac": round(pre_gbs / peak, 4) if pre_gbs else None,
+                           "peak_source": peak_kind},
+            "kernels": {k: {"launches": d["launches"], "avg_ms": round(d["ms"] / max(1, d["launches"]), 5)}
+                        for k, d in kt.items()},
+            "views_loop": {"views": len(ms_views), "pairs_total": m_views,
+                           "pairs_per_s": m_views / (sum(ms_views) * 1e-3),
+                           "p50_ms": round(statistics.median(ms_views), 4),
+                           "p99_ms": round(float(np.percentile(ms_views, 99)), 4)}}
+
+
 # ------------------------------------------------------- served requests
 def run_served(args, local_rank):
     """Poisson request stream (200 req/s): frames of 100k-3M Gaussians at
@@ -501,6 +573,7 @@ def main():
     ap.add_argument("--cpu-reps", type=int, default=5)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--sort-variant", type=int, default=-1,
                     help="pass kernel of the sort-only section (-1: the library's choice)")
@@ -545,6 +618,7 @@ def main():
     res = run_ours(args, rank, world, local_rank, dist)
     batched = None if args.no_batched else run_batched(args, local_rank)
     served = None if args.no_served else run_served(args, local_rank)
+    frame3d = None if args.no_3d else run_frame3d(args, local_rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -573,6 +647,7 @@ def main():
             "roofline": res["roofline"], "kernels": res["kernels"], "sort_pairs": res["sort_pairs"],
             "cpu_baseline": cpu, "e2e": res["e2e"], "gpu_launches": res["gpu_launches"],
             "clocks": res["clocks"], "batched_views": batched, "served": served,
+            "frame_3d": frame3d,
         }
         print(json.dumps(out))
     if dist:

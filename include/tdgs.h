@@ -15,6 +15,9 @@
  *   5. tdgs_tile_ranges    [start, end) of every tile in the sorted list
  *   +  tdgs_sort_frame     all five steps on context-owned buffers
  *   +  tdgs_sort_views     many views of one scene in one batched call
+ *   0. tdgs_preprocess     the Preprocessing stage before step 1: 3D
+ *                          Gaussians -> projected records for one camera
+ *   +  tdgs_sort_frame_3d  preprocessing and steps 1-5 in one call
  *
  * Conventions shared by every call
  *   - Data pointers are DEVICE pointers unless a parameter says "host".
@@ -236,6 +239,70 @@ tdgs_status tdgs_sort_frame(tdgs_context* ctx, const tdgs_gaussian2d* g, uint32_
                             tdgs_frame f, const uint64_t** sorted_keys,
                             const uint32_t** sorted_values, const tdgs_range** ranges,
                             uint32_t* m_out, void* stream);
+
+/* ------------------------------------------------------ preprocessing --- */
+
+/* One 3D Gaussian as the preprocessing stage reads it (Table I, Group 1:
+ * mean in world units and opacity), 16 bytes, 16-byte aligned in arrays. */
+typedef struct {
+  float x, y, z, opacity;
+} tdgs_gaussian3d;
+
+/* Its 3D covariance (Table I, Group 2: the six entries of the symmetric
+ * matrix in two 16-byte texels; pad0 and pad1 are ignored), 32 bytes,
+ * 16-byte aligned in arrays. */
+typedef struct {
+  float xx, xy, xz, yy, yz, zz, pad0, pad1;
+} tdgs_cov3d;
+
+/* Pinhole camera: camera-space point = rot * p + trans (rot row-major;
+ * camera x to the right and y down in the image, z along the view
+ * direction), focal lengths and principal point in pixels, near plane and
+ * image size in pixels.  76 bytes, passed by HOST pointer. */
+typedef struct {
+  float rot[9];
+  float trans[3];
+  float fx, fy, cx, cy;
+  float near_z;
+  uint32_t width, height;
+} tdgs_camera;
+
+/* Preprocessing (Sec. II-A "Preprocessing": frustum culling and projection
+ * of each Gaussian to its elliptical footprint; inputs Table I, outputs
+ * Table IV Groups 1-2).  The paper prints no formulas; the library applies
+ * the EWA projection of 3D Gaussian splatting, in float32 with every
+ * operation rounded in this order:
+ *   t = rot p + trans; culled unless t.z > near_z
+ *   u = t.x / t.z, v = t.y / t.z; record x = fx u + cx, y = fy v + cy,
+ *   depth = t.z
+ *   uc, vc = u, v clamped to +-(0.65 width / fx), +-(0.65 height / fy)
+ *   J = [[fx / t.z, 0, -fx uc / t.z], [0, fy / t.z, -fy vc / t.z]]
+ *   S2 = (J rot) S3 (J rot)^T + 0.3 I; culled unless det(S2) > 0
+ *   conic = (S2yy, -S2xy, S2xx) / det
+ *   radius = ceil(3 sqrt(mid + sqrt(max(0.1, mid^2 - det)))),
+ *   mid = (S2xx + S2yy) / 2; culled unless x, y, depth and radius are finite;
+ *   radius capped at 2^30.
+ * A culled Gaussian gets the record {0, 0, 0, 0} (radius 0: no tiles) and
+ * the conic {0, 0, 0, 0}.
+ * g, cov: n device entries; records: n device entries (16-byte aligned);
+ * conic_opacity: NULL or n x 4 device floats (conic a, b, c, opacity),
+ * 16-byte aligned.  cam: host.  Returns TDGS_ERR_INVALID_ARGUMENT for fx or
+ * fy not > 0 or not finite, a zero image size, or NULL / misaligned
+ * pointers with n > 0. */
+tdgs_status tdgs_preprocess(tdgs_context* ctx, const tdgs_gaussian3d* g, const tdgs_cov3d* cov,
+                            uint32_t n, const tdgs_camera* cam, tdgs_gaussian2d* records,
+                            float* conic_opacity, void* stream);
+
+/* tdgs_preprocess into context-owned buffers, then tdgs_sort_frame on the
+ * records for the camera's image.  *records and *conic_opacity (each may
+ * be NULL to skip) receive device pointers to the n projected records and
+ * n x 4 conic/opacity floats, valid like the sorted buffers (until the next
+ * call on the context). */
+tdgs_status tdgs_sort_frame_3d(tdgs_context* ctx, const tdgs_gaussian3d* g, const tdgs_cov3d* cov,
+                               uint32_t n, const tdgs_camera* cam, const tdgs_gaussian2d** records,
+                               const float** conic_opacity, const uint64_t** sorted_keys,
+                               const uint32_t** sorted_values, const tdgs_range** ranges,
+                               uint32_t* m_out, void* stream);
 
 /* ------------------------------------------------- scan without allocation */
 

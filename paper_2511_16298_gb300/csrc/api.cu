@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <new>
+#include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -48,12 +49,12 @@ struct Buffer {
 
 enum KernelId {
   kKCount, kKScan, kKDuplicate, kKRanges, kKRadixPass,
-  kKFrameCount, kKDepthSort, kKFrameScan, kKDupDepth, kKTilePass, kKTileExpand, kKNum
+  kKFrameCount, kKDepthSort, kKFrameScan, kKDupDepth, kKTilePass, kKTileExpand, kKPreprocess, kKNum
 };
 const char* const kKernelNames[kKNum] = {
     "count_tiles",  "scan",       "duplicate_keys",     "tile_ranges",    "radix_pass",
     "frame_count",  "depth_sort", "scan_by_depth", "duplicate_by_depth", "tile_sort_pass",
-    "tile_expand_pass"};
+    "tile_expand_pass", "preprocess"};
 
 // View table as stored in device memory (SoA, fixed maximum size).
 struct ViewBlob {
@@ -83,6 +84,7 @@ struct tdgs_context {
   uint32_t ticket_base[2] = {0, 0};
   Buffer scan_status, sort_scratch;
   // fused-frame / multi-view buffers
+  Buffer f_rec3, f_conic;  // projected records and conics of tdgs_sort_frame_3d
   Buffer f_counts, f_dkey[3], f_dval[3], f_soff, f_sdo, f_rminmax, f_stream[2], f_keys, f_values, f_ranges;
   // depth-key range: accumulators [0..1], result [2..3], passes of the last
   // resident depth sort [4]
@@ -459,7 +461,8 @@ void tdgs_context_destroy(tdgs_context* ctx) {
   for (cudaEvent_t e : ctx->free_events) cudaEventDestroy(e);
   Buffer* bufs[] = {&ctx->scan_status, &ctx->sort_scratch, &ctx->f_counts,    &ctx->f_dkey[0],
                     &ctx->f_dkey[1],    &ctx->f_dkey[2],     &ctx->f_dval[0],    &ctx->f_dval[1],
-                    &ctx->f_dval[2],    &ctx->f_soff,       &ctx->f_sdo,
+                    &ctx->f_dval[2],    &ctx->f_soff,       &ctx->f_sdo,        &ctx->f_rec3,
+                    &ctx->f_conic,
                     &ctx->f_rminmax,    &ctx->f_stream[0],   &ctx->f_stream[1],  &ctx->f_keys,
                     &ctx->f_values,     &ctx->f_ranges};
   if (ctx->d_views) cudaFree(ctx->d_views);
@@ -845,6 +848,17 @@ tdgs_status fill_results(tdgs_context* ctx, tdgs_view_result* results, uint32_t 
   return TDGS_OK;
 }
 
+// Camera validation for the preprocessing calls (host pointer).
+tdgs_status check_camera(tdgs_context* ctx, const tdgs_camera* cam, CameraDev* out) {
+  if (!cam) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "null camera");
+  if (!(cam->fx > 0.0f) || !(cam->fy > 0.0f) || !std::isfinite(cam->fx) || !std::isfinite(cam->fy))
+    return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "focal length must be finite and > 0");
+  if (cam->width == 0 || cam->height == 0) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "empty image");
+  static_assert(sizeof(tdgs_camera) == sizeof(CameraDev), "camera layout");
+  std::memcpy(out, cam, sizeof(CameraDev));
+  return TDGS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -870,6 +884,51 @@ tdgs_status tdgs_sort_frame(tdgs_context* ctx, const tdgs_gaussian2d* g, uint32_
   *ranges = static_cast<const tdgs_range*>(ctx->f_ranges.p);
   *m_out = m;
   return TDGS_OK;
+}
+
+tdgs_status tdgs_preprocess(tdgs_context* ctx, const tdgs_gaussian3d* g, const tdgs_cov3d* cov,
+                            uint32_t n, const tdgs_camera* cam, tdgs_gaussian2d* records,
+                            float* conic_opacity, void* stream) {
+  if (!ctx) return TDGS_ERR_INVALID_ARGUMENT;
+  CameraDev cd;
+  tdgs_status st = check_camera(ctx, cam, &cd);
+  if (st != TDGS_OK) return st;
+  if (n == 0) return TDGS_OK;
+  if (!g || !cov || !records) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "null pointer");
+  if (!aligned(g, 16) || !aligned(cov, 16) || !aligned(records, 16) ||
+      (conic_opacity && !aligned(conic_opacity, 16)))
+    return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "misaligned pointer");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TDGS_TRACED(ctx, kKPreprocess, n, s,
+              launch_preprocess(reinterpret_cast<const float4*>(g), reinterpret_cast<const float4*>(cov), n, cd,
+                                reinterpret_cast<float4*>(records), reinterpret_cast<float4*>(conic_opacity), s));
+  return TDGS_OK;
+}
+
+tdgs_status tdgs_sort_frame_3d(tdgs_context* ctx, const tdgs_gaussian3d* g, const tdgs_cov3d* cov,
+                               uint32_t n, const tdgs_camera* cam, const tdgs_gaussian2d** records,
+                               const float** conic_opacity, const uint64_t** sorted_keys,
+                               const uint32_t** sorted_values, const tdgs_range** ranges,
+                               uint32_t* m_out, void* stream) {
+  if (!ctx || !sorted_keys || !sorted_values || !ranges || !m_out) return TDGS_ERR_INVALID_ARGUMENT;
+  *m_out = 0;
+  CameraDev cd;
+  tdgs_status st = check_camera(ctx, cam, &cd);
+  if (st != TDGS_OK) return st;
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = static_cast<size_t>(n) * 16 + 16;
+  st = ensure(ctx, ctx->f_rec3, bytes, s);
+  if (st == TDGS_OK) st = ensure(ctx, ctx->f_conic, bytes, s);
+  if (st != TDGS_OK) return st;
+  st = tdgs_preprocess(ctx, g, cov, n, cam, static_cast<tdgs_gaussian2d*>(ctx->f_rec3.p),
+                       static_cast<float*>(ctx->f_conic.p), stream);
+  if (st != TDGS_OK) return st;
+  if (records) *records = static_cast<const tdgs_gaussian2d*>(ctx->f_rec3.p);
+  if (conic_opacity) *conic_opacity = static_cast<const float*>(ctx->f_conic.p);
+  return tdgs_sort_frame(ctx, static_cast<const tdgs_gaussian2d*>(ctx->f_rec3.p), n,
+                         tdgs_frame{cam->width, cam->height}, sorted_keys, sorted_values, ranges, m_out, stream);
 }
 
 tdgs_status tdgs_sort_views(tdgs_context* ctx, const tdgs_view* views, uint32_t num_views,

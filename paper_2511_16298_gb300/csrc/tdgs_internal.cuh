@@ -171,6 +171,20 @@ __device__ __forceinline__ uint32_t find_view(const uint32_t* begin, uint32_t nv
 // ticket: a zero word, left zero.  range: four words, [0..1] all ones and
 // zero on entry and exit; [2..3] receive the smallest and largest depth key
 // of a Gaussian with pairs.
+// Camera of the preprocessing kernel (the layout of tdgs_camera).
+struct CameraDev {
+  float rot[9];
+  float trans[3];
+  float fx, fy, cx, cy, near_z;
+  uint32_t width, height;
+};
+static_assert(sizeof(CameraDev) == 76, "camera block");
+// Preprocessing of n 3D Gaussians (g: mean + opacity; cov: two 16-byte
+// words per Gaussian) into 16-byte records and (if conic != nullptr)
+// conic/opacity words.
+cudaError_t launch_preprocess(const float4* g, const float4* cov, uint32_t n, const CameraDev& cam, float4* rec,
+                              float4* conic, cudaStream_t s);
+
 cudaError_t launch_views_count(const ViewTable& vt, uint32_t n_all, uint32_t* counts,
                                uint32_t* dkey, uint32_t* dval, uint32_t* err, uint32_t* ticket,
                                uint64_t* total, uint32_t* range, cudaStream_t s);

@@ -103,6 +103,10 @@ def lib():
                 "tdgs_sort_frame": ([P, P, u32, F, ctypes.POINTER(P), ctypes.POINTER(P),
                                      ctypes.POINTER(P), ctypes.POINTER(u32), P], st),
                 "tdgs_scan_noalloc": ([P, u32, P, P, P, P], st),
+                "tdgs_preprocess": ([P, P, P, u32, P, P, P, P], st),
+                "tdgs_sort_frame_3d": ([P, P, P, u32, P, ctypes.POINTER(P), ctypes.POINTER(P),
+                                        ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
+                                        ctypes.POINTER(u32), P], st),
                 "tdgs_sort_views": ([P, ctypes.POINTER(_View), u32, ctypes.POINTER(_ViewResult), P], st),
                 "tdgs_reserve_views": ([P, ctypes.POINTER(_View), u32, ctypes.c_uint64, P], st),
                 "tdgs_sort_views_async": ([P, ctypes.POINTER(_View), u32, P], st),
@@ -176,7 +180,7 @@ class _DeviceView:
 
 
 def _view(ptr: int, n: int, dtype: torch.dtype, device) -> torch.Tensor:
-    ts = {torch.int64: "<i8", torch.int32: "<i4"}[dtype]
+    ts = {torch.int64: "<i8", torch.int32: "<i4", torch.float32: "<f4"}[dtype]
     if n == 0 or not ptr:
         return torch.empty(0, dtype=dtype, device=device)
     return torch.as_tensor(_DeviceView(ptr, n, ts), device=device)
@@ -328,6 +332,53 @@ class Context:
         if copy:
             k, v, r = k.clone(), v.clone(), r.clone()
         return k, v, r, int(m.value)
+
+    # ------------------------------------------------------ preprocessing
+    @staticmethod
+    def _camera(cam):
+        """One 76-byte camera block (numpy CAMERA record) as a ctypes buffer."""
+        a = np.ascontiguousarray(np.asarray(cam).reshape(1))
+        assert a.dtype.itemsize == 76
+        return ctypes.create_string_buffer(a.tobytes(), 76)
+
+    def preprocess(self, g3: torch.Tensor, cov: torch.Tensor, cam, records=None, conic=None,
+                   with_conic: bool = True):
+        """Project n 3D Gaussians for one camera.  g3: (n, 4) float32 CUDA
+        tensor (mean, opacity); cov: (n, 8) float32 (xx, xy, xz, yy, yz, zz,
+        pad, pad); cam: a CAMERA record.  Returns (records (n, 4) int32
+        bit-view of the 16-byte records, conic (n, 4) float32 or None)."""
+        n = g3.shape[0]
+        if records is None:
+            records = torch.empty((n, 4), dtype=torch.int32, device=g3.device)
+        if conic is None and with_conic:
+            conic = torch.empty((n, 4), dtype=torch.float32, device=g3.device)
+        cb = self._camera(cam)
+        self._check(lib().tdgs_preprocess(self._h, _ptr(g3), _ptr(cov), n, ctypes.cast(cb, ctypes.c_void_p),
+                                          _ptr(records), _ptr(conic), _stream(self.device)), "tdgs_preprocess")
+        return records, conic
+
+    def sort_frame_3d(self, g3: torch.Tensor, cov: torch.Tensor, cam, copy: bool = False):
+        """Preprocessing and steps 1-5.  Returns (keys, values, ranges, m,
+        records, conic); the tensors are views of context buffers valid until
+        the next call on this context unless copy=True."""
+        n = g3.shape[0]
+        rp, cp, kp, vp, gp = (ctypes.c_void_p() for _ in range(5))
+        m = ctypes.c_uint32(0)
+        cb = self._camera(cam)
+        self._check(lib().tdgs_sort_frame_3d(self._h, _ptr(g3), _ptr(cov), n, ctypes.cast(cb, ctypes.c_void_p),
+                                             ctypes.byref(rp), ctypes.byref(cp), ctypes.byref(kp),
+                                             ctypes.byref(vp), ctypes.byref(gp), ctypes.byref(m),
+                                             _stream(self.device)), "tdgs_sort_frame_3d")
+        c = np.asarray(cam).reshape(())
+        T = num_tiles(int(c["width"]), int(c["height"]))
+        k = _view(kp.value or 0, m.value, torch.int64, self.device)
+        v = _view(vp.value or 0, m.value, torch.int32, self.device)
+        r = _view(gp.value or 0, 2 * T, torch.int32, self.device).view(T, 2)
+        rec = _view(rp.value or 0, 4 * n, torch.int32, self.device).view(n, 4)
+        con = _view(cp.value or 0, 4 * n, torch.float32, self.device).view(n, 4)
+        if copy:
+            k, v, r, rec, con = k.clone(), v.clone(), r.clone(), rec.clone(), con.clone()
+        return k, v, r, int(m.value), rec, con
 
     # ------------------------------------------------------------ views
     @staticmethod

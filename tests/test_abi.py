@@ -60,3 +60,16 @@ def test_context_create_rejects_bad_device(libtdgs):
     assert not h.value
     assert tdgs.lib().tdgs_context_create(None, 0) == tdgs.INVALID_ARGUMENT
     tdgs.lib().tdgs_context_destroy(None)  # no-op
+
+
+def test_preprocess_host_checks(libtdgs):
+    """Layouts of the preprocessing structs and the host-side argument
+    checks that need no device."""
+    from paper_2511_16298_gb300 import synth, tdgs
+    assert synth.GAUSSIAN3D.itemsize == 16 and synth.COV3D.itemsize == 32
+    assert synth.CAMERA.itemsize == 76
+    L = tdgs.lib()
+    cam = synth.camera((0.0, 0.0, -10.0), (0.0, 0.0, 0.0), 640, 360)
+    buf = ctypes.create_string_buffer(cam.tobytes(), 76)
+    assert L.tdgs_preprocess(None, None, None, 0, ctypes.cast(buf, ctypes.c_void_p), None, None,
+                             None) == tdgs.INVALID_ARGUMENT
