@@ -248,22 +248,25 @@ __device__ __forceinline__ void count_key(K k, const PassArgs& a, bool d31, uint
 // Phase 2, after every chunk has written its histogram row H[c][*]: a
 // grid barrier, one warp per digit scans the column over chunks (chunk
 // prefixes P, digit totals tot), a grid barrier, then base[b] = first
-// output position of this chunk's keys with digit b.  With at most 64
-// digits each CTA sums the rows itself after the first barrier.  With a.ranges set,
+// output position of this chunk's keys with digit b.  With kRowSum (at
+// most 64 digits, or a resident grid of few chunks) each CTA sums the rows
+// itself after the first barrier.  With a.ranges set,
 // the tile ranges are written from the digit totals.
-template <int kBins, int kThreads>
+template <int kBins, int kThreads, bool kRowSum = (kBins <= 64)>
 __device__ __forceinline__ void scan_chunks(const PassArgs& a, uint32_t* base, uint32_t* s_warp,
                                             const uint32_t* s_vtile) {
   constexpr int kWarps = kThreads / 32;
   constexpr int kBpt = (kBins + kThreads - 1) / kThreads;
   const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
   const uint32_t G = gridDim.x, c = blockIdx.x;
-  if constexpr (kBins <= 64) {
-    // Few digits: after one grid barrier every CTA sums the histogram rows
-    // itself (16-byte loads, kRows row groups in parallel): the rows of the
-    // chunks before it and all rows.  No second barrier, no P or tot.
+  if constexpr (kRowSum) {
+    // Few digits or few chunks: after one grid barrier every CTA sums the
+    // histogram rows itself (16-byte loads, kRows row groups in parallel):
+    // the rows of the chunks before it and all rows.  No second barrier, no
+    // P or tot.
     constexpr int kQ = kBins / 4;          // 16-byte words per row
     constexpr int kRows = kThreads / kQ;   // row groups
+    static_assert(kBins <= kThreads && kThreads % kQ == 0, "one digit per thread in the row sums");
     __shared__ uint4 s_pre[kRows][kQ];
     __shared__ uint4 s_all[kRows][kQ];
     grid_barrier(a.bar, a.err);
@@ -834,7 +837,7 @@ struct ResidentArgs {
   uint32_t* offsets;
 };
 
-template <typename K, int kBits, int kThreads, int kItems, int kOcc>
+template <typename K, int kBits, int kThreads, int kItems, int kOcc, bool kRowSum>
 __global__ void __launch_bounds__(kThreads, kOcc)
     k_radix_resident(K* __restrict__ k0, uint32_t* __restrict__ v0, K* __restrict__ k1,
                      uint32_t* __restrict__ v1, K* __restrict__ k2, uint32_t* __restrict__ v2, PassArgs a,
@@ -905,7 +908,7 @@ __global__ void __launch_bounds__(kThreads, kOcc)
     rank_tile<false, S, K, false, kBits, kItems, sizeof(K) == 4>(kin + ch.beg, valid, a, false, sm, R);
     for (uint32_t b = t; b < static_cast<uint32_t>(S::kBins); b += kThreads)
       a.H[static_cast<size_t>(c) * S::kBins + b] = sm.lstart[b];
-    scan_chunks<S::kBins, kThreads>(a, sm.base, s_warp, nullptr);
+    scan_chunks<S::kBins, kThreads, kRowSum>(a, sm.base, s_warp, nullptr);
     ok &= scatter_tile<false, S, K, true, false, kBits, kItems, sizeof(K) == 4>(vin + ch.beg, valid, ch.m, a, false,
                                                                                  sm, s_warp,
                                                                  nullptr, nullptr, kout, vout, R);
@@ -1008,10 +1011,10 @@ Kernel make_kernel() {
                 kBits, kThreads, kItems, S::kSmem, S::kMinBlocks};
 }
 
-template <typename K, int kBits, int kThreads, int kItems, int kOcc>
+template <typename K, int kBits, int kThreads, int kItems, int kOcc, bool kRowSum = false>
 Kernel make_resident_kernel() {
   using S = PassShape<K, true, false, kBits, kThreads, kItems, kOcc>;
-  return Kernel{reinterpret_cast<const void*>(&k_radix_resident<K, kBits, kThreads, kItems, kOcc>), kBits,
+  return Kernel{reinterpret_cast<const void*>(&k_radix_resident<K, kBits, kThreads, kItems, kOcc, kRowSum>), kBits,
                 kThreads, kItems, S::kSmem, kOcc};
 }
 

@@ -32,7 +32,7 @@ uint32_t stream_kernel_bits(uint32_t width) { return width <= 6 ? 6u : (width <=
 
 namespace {
 const radix::Kernel& resident_depth_kernel() {
-  static const radix::Kernel k9 = radix::make_resident_kernel<uint32_t, 9, 256, 16, 2>();
+  static const radix::Kernel k9 = radix::make_resident_kernel<uint32_t, 9, 512, 16, 1, true>();
   return k9;
 }
 }  // namespace
