@@ -312,6 +312,31 @@ def run_ours(args, rank, world, local_rank, dist):
                      "pass_avg_ms": round(op["ms"] / op["launches"], 5) if op else None,
                      "pass_frac": round(24.0 * op["items"] / op["launches"] / (op["ms"] / op["launches"] * 1e-3)
                                         / 1e9 / peak, 4) if op else None}
+        # the paper's bitonic network (Sec. III) on the same pairs, for comparison
+        if not args.no_bitonic:
+            bt = []
+            for i in range(args.warmup + max(3, args.steps // 2)):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctx.sort_pairs_bitonic(k0, v0, kw, vw)
+                b.record(stream)
+                if i >= args.warmup:
+                    bt.append((a, b))
+            torch.cuda.synchronize(dev)
+            ctx.sync()
+            bms = [a.elapsed_time(b) for a, b in bt]
+            n2 = 1 << max(12, (m - 1).bit_length())
+            stages = n2.bit_length() - 1
+            bmean = statistics.mean(bms)
+            # each launch reads and writes every padded pair once (12 B each way)
+            launches = 1 + sum((k - 12 + 3) // 4 + 1 for k in range(13, stages + 1))
+            sort_only["bitonic"] = {
+                "pairs_per_s": m / (bmean * 1e-3), "ms_mean": round(bmean, 4), "padded_pairs": n2,
+                "launches": launches, "bytes_moved": 24 * n2 * launches,
+                "achieved_gbs": round(24 * n2 * launches / (bmean * 1e-3) / 1e9, 1),
+                "frac": round(24 * n2 * launches / (bmean * 1e-3) / 1e9 / peak, 4),
+                "slowdown_vs_radix": round(bmean / smean, 2)}
         del k0, v0, ka, va, kw, vw
 
     # ---- end to end through the public API with host buffers
@@ -574,6 +599,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--no-bitonic", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--sort-variant", type=int, default=-1,
                     help="pass kernel of the sort-only section (-1: the library's choice)")

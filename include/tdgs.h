@@ -220,6 +220,19 @@ tdgs_status tdgs_sort_pairs(tdgs_context* ctx, uint64_t* keys, uint32_t* values,
                             uint32_t tile_bits, uint32_t flags, int* result_in_alt,
                             void* stream);
 
+/* Step 4 as the paper builds it (Sec. III, Algorithms 1-2): a bitonic
+ * sorting network over the pairs padded to a power of two (at least 4096),
+ * ascending by key and then by value.  When pairs with equal keys appear
+ * with ascending values -- as tdgs_duplicate_keys emits them -- the result
+ * is identical to tdgs_sort_pairs; otherwise equal keys end up ordered by
+ * value.  keys_in/values_in (m pairs) are read; keys_out/values_out receive
+ * the sorted pairs and may be the same arrays.  The context holds a scratch
+ * copy of the padded pairs (12 bytes per padded pair).  m <= 2^31.  It is
+ * slower than tdgs_sort_pairs on this GPU (O(m log^2 m) work against a few
+ * radix passes) and is kept as the paper's method for comparison. */
+tdgs_status tdgs_sort_pairs_bitonic(tdgs_context* ctx, const uint64_t* keys_in, const uint32_t* values_in,
+                                    uint64_t* keys_out, uint32_t* values_out, uint32_t m, void* stream);
+
 /* Step 5 (Identify Range, Sec. IV-B and Table VI): ranges[t] = first and
  * one-past-last position of tile t (= key >> 32) in sorted_keys, {0, 0} for
  * a tile with no pairs.  sorted_keys must be ordered by tile.  A tile id

@@ -49,12 +49,12 @@ struct Buffer {
 
 enum KernelId {
   kKCount, kKScan, kKDuplicate, kKRanges, kKRadixPass,
-  kKFrameCount, kKDepthSort, kKFrameScan, kKDupDepth, kKTilePass, kKTileExpand, kKPreprocess, kKNum
+  kKFrameCount, kKDepthSort, kKFrameScan, kKDupDepth, kKTilePass, kKTileExpand, kKPreprocess, kKBitonic, kKNum
 };
 const char* const kKernelNames[kKNum] = {
     "count_tiles",  "scan",       "duplicate_keys",     "tile_ranges",    "radix_pass",
     "frame_count",  "depth_sort", "scan_by_depth", "duplicate_by_depth", "tile_sort_pass",
-    "tile_expand_pass", "preprocess"};
+    "tile_expand_pass", "preprocess", "bitonic_sort"};
 
 // View table as stored in device memory (SoA, fixed maximum size).
 struct ViewBlob {
@@ -85,6 +85,7 @@ struct tdgs_context {
   Buffer scan_status, sort_scratch;
   // fused-frame / multi-view buffers
   Buffer f_rec3, f_conic;  // projected records and conics of tdgs_sort_frame_3d
+  Buffer b_keys, b_vals;   // padded scratch of tdgs_sort_pairs_bitonic
   Buffer f_counts, f_dkey[3], f_dval[3], f_soff, f_sdo, f_rminmax, f_stream[2], f_keys, f_values, f_ranges;
   // depth-key range: accumulators [0..1], result [2..3], passes of the last
   // resident depth sort [4]
@@ -462,7 +463,7 @@ void tdgs_context_destroy(tdgs_context* ctx) {
   Buffer* bufs[] = {&ctx->scan_status, &ctx->sort_scratch, &ctx->f_counts,    &ctx->f_dkey[0],
                     &ctx->f_dkey[1],    &ctx->f_dkey[2],     &ctx->f_dval[0],    &ctx->f_dval[1],
                     &ctx->f_dval[2],    &ctx->f_soff,       &ctx->f_sdo,        &ctx->f_rec3,
-                    &ctx->f_conic,
+                    &ctx->f_conic,      &ctx->b_keys,       &ctx->b_vals,
                     &ctx->f_rminmax,    &ctx->f_stream[0],   &ctx->f_stream[1],  &ctx->f_keys,
                     &ctx->f_values,     &ctx->f_ranges};
   if (ctx->d_views) cudaFree(ctx->d_views);
@@ -551,6 +552,26 @@ tdgs_status tdgs_sort_pairs(tdgs_context* ctx, uint64_t* keys, uint32_t* values,
   DeviceGuard dg(ctx->device);
   return do_sort(ctx, keys, values, keys_alt, values_alt, m, tile_bits, flags, result_in_alt,
                  static_cast<cudaStream_t>(stream));
+}
+
+tdgs_status tdgs_sort_pairs_bitonic(tdgs_context* ctx, const uint64_t* keys_in, const uint32_t* values_in,
+                                    uint64_t* keys_out, uint32_t* values_out, uint32_t m, void* stream) {
+  if (!ctx) return TDGS_ERR_INVALID_ARGUMENT;
+  if (m == 0) return TDGS_OK;
+  if (m > (1u << 31)) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "at most 2^31 pairs");
+  if (!keys_in || !values_in || !keys_out || !values_out) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "null pointer");
+  if (!aligned(keys_in, 8) || !aligned(keys_out, 8) || !aligned(values_in, 4) || !aligned(values_out, 4))
+    return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "misaligned pointer");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t n2 = bitonic_padded(m);
+  tdgs_status st = ensure(ctx, ctx->b_keys, n2 * 8, s);
+  if (st == TDGS_OK) st = ensure(ctx, ctx->b_vals, n2 * 4, s);
+  if (st != TDGS_OK) return st;
+  TDGS_TRACED(ctx, kKBitonic, m, s,
+              launch_bitonic(keys_in, values_in, m, keys_out, values_out, static_cast<uint64_t*>(ctx->b_keys.p),
+                             static_cast<uint32_t*>(ctx->b_vals.p), s));
+  return TDGS_OK;
 }
 
 tdgs_status tdgs_tile_ranges(tdgs_context* ctx, const uint64_t* sorted_keys, uint32_t m,

@@ -249,10 +249,10 @@ __device__ __forceinline__ void count_key(K k, const PassArgs& a, bool d31, uint
 // grid barrier, one warp per digit scans the column over chunks (chunk
 // prefixes P, digit totals tot), a grid barrier, then base[b] = first
 // output position of this chunk's keys with digit b.  With kRowSum (at
-// most 64 digits, or a resident grid of few chunks) each CTA sums the rows
-// itself after the first barrier.  With a.ranges set,
+// most 64 digits, or 512-thread CTAs: one per SM, so at most 152 chunks)
+// each CTA sums the rows itself after the first barrier.  With a.ranges set,
 // the tile ranges are written from the digit totals.
-template <int kBins, int kThreads, bool kRowSum = (kBins <= 64)>
+template <int kBins, int kThreads, bool kRowSum = (kBins <= 64 || (kThreads >= 512 && kBins <= kThreads))>
 __device__ __forceinline__ void scan_chunks(const PassArgs& a, uint32_t* base, uint32_t* s_warp,
                                             const uint32_t* s_vtile) {
   constexpr int kWarps = kThreads / 32;

@@ -171,6 +171,13 @@ __device__ __forceinline__ uint32_t find_view(const uint32_t* begin, uint32_t nv
 // ticket: a zero word, left zero.  range: four words, [0..1] all ones and
 // zero on entry and exit; [2..3] receive the smallest and largest depth key
 // of a Gaussian with pairs.
+// Bitonic sort of m (key, value) pairs by (key, value) (tdgs_sort_pairs_bitonic):
+// kin/vin -> kout/vout (may alias), scratch ks/vs of bitonic_padded(m) pairs.
+uint32_t bitonic_padded(uint32_t m);
+uint32_t bitonic_launches(uint32_t m);
+cudaError_t launch_bitonic(const uint64_t* kin, const uint32_t* vin, uint32_t m, uint64_t* kout, uint32_t* vout,
+                           uint64_t* ks, uint32_t* vs, cudaStream_t s);
+
 // Camera of the preprocessing kernel (the layout of tdgs_camera).
 struct CameraDev {
   float rot[9];

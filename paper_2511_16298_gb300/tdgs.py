@@ -104,6 +104,7 @@ def lib():
                                      ctypes.POINTER(P), ctypes.POINTER(u32), P], st),
                 "tdgs_scan_noalloc": ([P, u32, P, P, P, P], st),
                 "tdgs_preprocess": ([P, P, P, u32, P, P, P, P], st),
+                "tdgs_sort_pairs_bitonic": ([P, P, P, P, P, u32, P], st),
                 "tdgs_sort_frame_3d": ([P, P, P, u32, P, ctypes.POINTER(P), ctypes.POINTER(P),
                                         ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                                         ctypes.POINTER(u32), P], st),
@@ -307,6 +308,19 @@ class Context:
                                           _ptr(values_alt), m, tile_bits, flags, ctypes.byref(alt),
                                           _stream(self.device)), "tdgs_sort_pairs")
         return (keys_alt, values_alt) if alt.value else (keys, values)
+
+    def sort_pairs_bitonic(self, keys, values, keys_out=None, values_out=None):
+        """The paper's bitonic network: sorts by (key, value); returns
+        (keys_out, values_out) (new tensors unless given; may be the inputs)."""
+        m = keys.shape[0]
+        if keys_out is None:
+            keys_out = torch.empty_like(keys)
+        if values_out is None:
+            values_out = torch.empty_like(values)
+        self._check(lib().tdgs_sort_pairs_bitonic(self._h, _ptr(keys), _ptr(values), _ptr(keys_out),
+                                                  _ptr(values_out), m, _stream(self.device)),
+                    "tdgs_sort_pairs_bitonic")
+        return keys_out, values_out
 
     def tile_ranges(self, sorted_keys, num_tiles: int, m=None, out=None) -> torch.Tensor:
         m = sorted_keys.shape[0] if m is None else m
