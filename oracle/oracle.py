@@ -57,6 +57,8 @@ def load(path: str):
     L.oracle_duplicate.argtypes = [P, P, u32, u32, u32, P, P, u32]
     L.oracle_sort_pairs.argtypes = [P, P, u32]
     L.oracle_tile_ranges.argtypes = [P, u32, u32, P]
+    L.oracle_render.argtypes = [P, P, P, P, P, u32, u32, P, P]
+    L.oracle_render.restype = ctypes.c_int
     L.oracle_preprocess.argtypes = [P, P, u32, P, P, P]
     L.oracle_preprocess.restype = ctypes.c_int
     L.oracle_num_tiles.argtypes = [u32, u32]
@@ -105,6 +107,9 @@ class Oracle:
 
     def preprocess(self, g3, cov, cam):
         return preprocess(g3, cov, cam, L=self._lib())
+
+    def render(self, rec, conic, rgb, sorted_values, ranges, width, height, background):
+        return render(rec, conic, rgb, sorted_values, ranges, width, height, background, L=self._lib())
 
 
 def _ptr(a: np.ndarray):
@@ -175,6 +180,23 @@ def preprocess(g3: np.ndarray, cov: np.ndarray, cam: np.ndarray, L=None):
     conic = np.zeros((n, 4), dtype=np.float32)
     st = (L or lib()).oracle_preprocess(_ptr(g3), _ptr(cov), n, _ptr(cam.reshape(1)), _ptr(rec), _ptr(conic))
     return st, rec, conic
+
+
+def render(rec, conic, rgb, sorted_values, ranges, width: int, height: int, background, L=None):
+    """Front-to-back blend of each tile's sorted Gaussians: returns (status,
+    image (height, width, 3) float32).  rec: 16-byte records; conic: (n, 4)
+    float32 (a, b, c, opacity); rgb: (n, 3) float32; sorted_values: the
+    sorted Gaussian indices; ranges: (tiles, 2) uint32."""
+    rec = np.ascontiguousarray(rec)
+    conic = np.ascontiguousarray(conic, dtype=np.float32)
+    rgb = np.ascontiguousarray(rgb, dtype=np.float32)
+    sv = np.ascontiguousarray(sorted_values, dtype=np.uint32)
+    rg = np.ascontiguousarray(ranges, dtype=np.uint32)
+    bg = np.ascontiguousarray(background, dtype=np.float32)
+    img = np.zeros((height, width, 3), dtype=np.float32)
+    st = (L or lib()).oracle_render(_ptr(rec), _ptr(conic), _ptr(rgb), _ptr(sv), _ptr(rg), width, height,
+                                    _ptr(bg), _ptr(img))
+    return st, img
 
 
 def num_tiles(width: int, height: int, L=None) -> int:

@@ -300,6 +300,51 @@ int oracle_preprocess(const G3* g, const C3* cov, uint32_t n, const Cam* cam, G2
   return kOk;
 }
 
+// Rendering (Sec. II-A "Rendering": alpha blending of each tile's sorted
+// Gaussians per pixel; Sec. IV-C: one 16x16 tile per work group).  The
+// paper names the blend without formulas; the reading is the front-to-back
+// compositing of 3D Gaussian splatting.  For pixel (px, py) of tile t (the
+// sample point is the pixel's integer coordinate), walking the tile's list
+// sorted_values[ranges[t].start .. ranges[t].end) in order with
+// transmittance T = 1 and colour C = 0:
+//   d = (x - px, y - py)                      x, y: the Gaussian's 2D mean
+//   power = -0.5 (a dx^2 + c dy^2) - b dx dy   (a, b, c): its conic
+//   skip if power > 0
+//   alpha = min(0.99, opacity exp(power)); skip if alpha < 1/255
+//   T' = T (1 - alpha); stop the pixel if T' < 1e-4 (without this Gaussian)
+//   C += rgb alpha T; T = T'
+// and the pixel is C + T * background.  Float32 in this order (exp from
+// the C library), so the GPU's result differs only through exp's last bits
+// and the threshold decisions they can flip.
+int oracle_render(const G2* rec, const float* conic_opacity, const float* rgb, const uint32_t* sorted_values,
+                  const uint32_t* ranges, uint32_t width, uint32_t height, const float* background,
+                  float* image) {
+  if (width == 0 || height == 0) return kInvalid;
+  const uint32_t gx = grid_dim(width);
+  for (uint32_t py = 0; py < height; ++py)
+    for (uint32_t px = 0; px < width; ++px) {
+      const uint32_t t = (py / 16u) * gx + px / 16u;
+      const float fx = static_cast<float>(px), fy = static_cast<float>(py);
+      float T = 1.0f, C[3] = {0.0f, 0.0f, 0.0f};
+      for (uint32_t k = ranges[2 * t]; k < ranges[2 * t + 1]; ++k) {
+        const uint32_t i = sorted_values[k];
+        const float* co = conic_opacity + 4 * static_cast<size_t>(i);
+        const float dx = rec[i].x - fx, dy = rec[i].y - fy;
+        const float power = -0.5f * (co[0] * dx * dx + co[2] * dy * dy) - co[1] * dx * dy;
+        if (power > 0.0f) continue;
+        const float alpha = std::fmin(0.99f, co[3] * std::exp(power));
+        if (alpha < 1.0f / 255.0f) continue;
+        const float test_t = T * (1.0f - alpha);
+        if (test_t < 0.0001f) break;
+        for (int ch = 0; ch < 3; ++ch) C[ch] += rgb[3 * static_cast<size_t>(i) + ch] * alpha * T;
+        T = test_t;
+      }
+      float* o = image + 3 * (static_cast<size_t>(py) * width + px);
+      for (int ch = 0; ch < 3; ++ch) o[ch] = C[ch] + T * background[ch];
+    }
+  return kOk;
+}
+
 // Number of tiles and tile bits of an image (helpers for callers).
 uint32_t oracle_num_tiles(uint32_t width, uint32_t height) {
   return grid_dim(width) * grid_dim(height);

@@ -235,6 +235,7 @@ class Scene3D:
     cov: np.ndarray        # COV3D
     cameras: np.ndarray    # CAMERA, one per view
     seed: int
+    rgb: np.ndarray = None  # (n, 3) float32 colours in [0, 1) (Table IV, Group 3)
 
     @property
     def n(self) -> int:
@@ -270,7 +271,8 @@ def scene3d(seed: int = 0, n: int = 500_000, views: int = 64, width: int = 1280,
     """Means ~ U[0,1)^3 * 10 - 5 (the multiview scene's distribution);
     per-axis scales s0 * lognormal(0, 0.5); rotations uniform (normalised
     Gaussian quaternions); cov = Rq diag(s^2) Rq^T in float64, rounded to
-    float32; opacity ~ U[0.05, 1).  Cameras: Fibonacci lattice of a sphere
+    float32; opacity ~ U[0.05, 1); colours ~ U[0, 1)^3 (drawn last).
+    Cameras: Fibonacci lattice of a sphere
     of radius ``cam_radius`` looking at the origin plus a jitter uniform in
     a ball of radius 4, fx = fy = 1108.5, near plane 0.2."""
     rng = np.random.default_rng(seed)
@@ -297,7 +299,8 @@ def scene3d(seed: int = 0, n: int = 500_000, views: int = 64, width: int = 1280,
     u /= np.linalg.norm(u, axis=1, keepdims=True)
     jitter = u * (4.0 * rng.random(views) ** (1.0 / 3.0))[:, None]
     cams = np.stack([camera(eye[v], jitter[v], width, height) for v in range(views)])
-    return Scene3D(g, cov, cams, seed)
+    rgb = rng.random((n, 3)).astype(np.float32)
+    return Scene3D(g, cov, cams, seed, rgb)
 
 
 # ------------------------------------------------------------ request trace

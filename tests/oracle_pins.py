@@ -423,8 +423,98 @@ def check_preprocess(O):
     assert O.preprocess(g, cv, bad)[0] == 1
 
 
+# ------------------------------------------------------------ rendering
+def _render_case(O, gs, order_by_tile, width, height, bg=(0.1, 0.2, 0.3)):
+    """gs: list of (x, y, a, b, c, opacity, (r, g, bl)); order_by_tile: per
+    tile the list of Gaussian indices front to back."""
+    n = len(gs)
+    rec = np.zeros(n, dtype=synth.GAUSSIAN2D)
+    conic = np.zeros((n, 4), dtype=np.float32)
+    rgb = np.zeros((n, 3), dtype=np.float32)
+    for i, (x, y, a, b, c, o, col) in enumerate(gs):
+        rec[i] = (x, y, 1.0 + i, 5)
+        conic[i] = (a, b, c, o)
+        rgb[i] = col
+    values, ranges = [], np.zeros((len(order_by_tile), 2), dtype=np.uint32)
+    for t, lst in enumerate(order_by_tile):
+        ranges[t] = (len(values), len(values) + len(lst))
+        values += lst
+    st, img = O.render(rec, conic, rgb, np.array(values, dtype=np.uint32), ranges, width, height, bg)
+    assert st == 0
+    return img.astype(np.float64)
+
+
+def _alpha(o, a, b, c, dx, dy):
+    p = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy
+    if p > 0:
+        return 0.0
+    al = min(0.99, o * math.exp(p))
+    return 0.0 if al < 1.0 / 255.0 else al
+
+
+def check_render(O):
+    """Front-to-back blending against closed forms in float64 (tolerance
+    1e-5; pixels whose alpha lies within 1e-4 of the 1/255 cut are not
+    used): one Gaussian over a 16x16 tile (colour alpha + (1 - alpha)
+    background, Gaussian falloff through the conic, cut below 1/255); two
+    Gaussians in both orders (order matters); opaque layers stopping when
+    the transmittance would drop below 1e-4 (three of five contribute at
+    alpha 0.95); an indefinite conic (pixels with positive exponent are
+    skipped); tiles of a 64x20 image (row-major tile ids, each pixel sees
+    only its own tile's list); an opaque Gaussian (alpha capped at 0.99); an
+    empty list (background)."""
+    bg = np.array([0.1, 0.2, 0.3])
+    col = np.array([1.0, 0.5, 0.25])
+    g0 = (5.0, 7.0, 0.5, 0.0, 0.5, 0.6, tuple(col))
+    img = _render_case(O, [g0], [[0]], 16, 16)
+    for py in range(16):
+        for px in range(16):
+            dx, dy = 5.0 - px, 7.0 - py
+            p = -0.25 * (dx * dx + dy * dy)
+            raw = 0.6 * math.exp(p)
+            if abs(raw - 1 / 255) < 1e-4:
+                continue
+            al = _alpha(0.6, 0.5, 0.0, 0.5, dx, dy)
+            assert np.allclose(img[py, px], col * al + (1 - al) * bg, atol=1e-5), (px, py)
+    # two Gaussians at one point, both orders
+    c2 = np.array([0.0, 0.0, 1.0])
+    g1 = (5.0, 7.0, 0.5, 0.0, 0.5, 0.5, tuple(c2))
+    a0, a1 = 0.6, 0.5
+    front = _render_case(O, [g0, g1], [[0, 1]], 16, 16)[7, 5]
+    back = _render_case(O, [g0, g1], [[1, 0]], 16, 16)[7, 5]
+    assert np.allclose(front, col * a0 + c2 * a1 * (1 - a0) + (1 - a0) * (1 - a1) * bg, atol=1e-6)
+    assert np.allclose(back, c2 * a1 + col * a0 * (1 - a1) + (1 - a0) * (1 - a1) * bg, atol=1e-6)
+    # opaque layers: alpha = 0.95 each; T = 0.05, 0.0025, 1.25e-4, then 6.25e-6 < 1e-4 stops
+    cols = [np.array(v) for v in ((1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (0, 1, 1))]
+    layers = [(3.0, 3.0, 0.5, 0.0, 0.5, 0.95, tuple(cc)) for cc in cols]
+    px = _render_case(O, layers, [[0, 1, 2, 3, 4]], 16, 16)[3, 3]
+    want = sum(cols[k] * 0.95 * 0.05 ** k for k in range(3)) + 0.05 ** 3 * bg
+    assert np.allclose(px, want, atol=1e-6), (px, want)
+    # indefinite conic: power = -dx dy > 0 where dx dy < 0
+    gi = (8.0, 8.0, 0.0, 1.0, 0.0, 0.5, tuple(col))
+    img = _render_case(O, [gi], [[0]], 16, 16)
+    for (qx, qy) in ((9, 7), (7, 9), (12, 3)):
+        assert np.allclose(img[qy, qx], bg, atol=1e-7)
+    al = _alpha(0.5, 0.0, 1.0, 0.0, 8.0 - 9, 8.0 - 9)
+    assert al > 0 and np.allclose(img[9, 9], col * al + (1 - al) * bg, atol=1e-5)
+    # tiles of a 64x20 image: 4 x 2 tiles, the Gaussian listed in tile 1 only (row 0, column 1)
+    gt = (20.0, 5.0, 0.02, 0.0, 0.02, 0.8, tuple(col))
+    img = _render_case(O, [gt], [[], [0], [], [], [], [], [], []], 64, 20)
+    assert np.allclose(img[5, 20], col * 0.8 + 0.2 * bg, atol=1e-6)
+    assert np.allclose(img[5, 15], bg, atol=1e-7) and np.allclose(img[16, 20], bg, atol=1e-7)
+    assert np.allclose(img[5, 32], bg, atol=1e-7)
+    inside = _alpha(0.8, 0.02, 0.0, 0.02, 20.0 - 31, 5.0 - 15)
+    assert np.allclose(img[15, 31], col * inside + (1 - inside) * bg, atol=1e-5)
+    # an opaque Gaussian: alpha capped at 0.99
+    go = (4.0, 4.0, 0.5, 0.0, 0.5, 1.0, tuple(col))
+    assert np.allclose(_render_case(O, [go], [[0]], 16, 16)[4, 4], col * 0.99 + 0.01 * bg, atol=1e-6)
+    # empty list: background everywhere
+    img = _render_case(O, [g0], [[]], 16, 16)
+    assert np.allclose(img, np.broadcast_to(bg, img.shape), atol=1e-7)
+
+
 ALL_CHECKS = (check_golden, check_count_and_duplicate_bruteforce, check_special_cases,
-              check_validity, check_scan, check_sort, check_preprocess)
+              check_validity, check_scan, check_sort, check_preprocess, check_render)
 
 
 def run_all(O) -> list[str]:

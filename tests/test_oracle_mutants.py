@@ -43,6 +43,19 @@ MUTANTS = {
     "cull_at_near_plane": ("bool keep = tz > cam->near_z;", "bool keep = tz >= cam->near_z;"),
     "two_sigma": ("std::ceil(3.0f * std::sqrt(lambda))", "std::ceil(2.0f * std::sqrt(lambda))"),
     "conic_swapped": ("co[0] = d / det;", "co[0] = a / det;"),
+    "render_no_early_stop": ("if (test_t < 0.0001f) break;", ""),
+    "render_back_to_front": ("        const uint32_t i = sorted_values[k];",
+                             "        const uint32_t i = sorted_values[ranges[2 * t] + ranges[2 * t + 1] - 1 - k];"),
+    "render_no_alpha_cap": ("std::fmin(0.99f, co[3] * std::exp(power))", "co[3] * std::exp(power)"),
+    "render_cut_1_64": ("if (alpha < 1.0f / 255.0f) continue;", "if (alpha < 1.0f / 64.0f) continue;"),
+    "render_t_before_colour": ("for (int ch = 0; ch < 3; ++ch) C[ch] += rgb[3 * static_cast<size_t>(i) + ch] * alpha * T;\n        T = test_t;",
+                               "T = test_t;\n        for (int ch = 0; ch < 3; ++ch) C[ch] += rgb[3 * static_cast<size_t>(i) + ch] * alpha * T;"),
+    "render_no_background": ("o[ch] = C[ch] + T * background[ch];", "o[ch] = C[ch];"),
+    "render_tile_transposed": ("const uint32_t t = (py / 16u) * gx + px / 16u;",
+                               "const uint32_t t = (px / 16u) * gx + py / 16u;"),
+    "render_cross_sign": ("- co[1] * dx * dy;", "+ co[1] * dx * dy;"),
+    "render_pixel_centre": ("const float fx = static_cast<float>(px), fy = static_cast<float>(py);",
+                            "const float fx = static_cast<float>(px) + 0.5f, fy = static_cast<float>(py) + 0.5f;"),
     "rotation_transposed": ("T[0][k] = j00 * R[k] + j02 * R[6 + k];", "T[0][k] = j00 * R[3 * k] + j02 * R[6 + k];"),
 }
 
