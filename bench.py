@@ -501,6 +501,17 @@ def run_frame3d(args, local_rank):
     pre_ms = pre["ms"] / max(1, pre["launches"])
     peak, peak_kind = measured_peaks()
     pre_gbs = 80.0 * sc.n / (pre_ms * 1e-3) / 1e9 if pre_ms > 0 else None
+    # rendering (Sec. IV-C) of camera 0 and the whole pipeline
+    # (preprocess + sort + render) per image
+    rgb = torch.from_numpy(sc.rgb.copy()).to(dev)
+    k_, v_, r_, m_, rec_, con_ = ctx.sort_frame_3d(g, c, cam0)
+    img = torch.empty((int(cam0["height"]), int(cam0["width"]), 3), dtype=torch.float32, device=dev)
+    bg = (0.0, 0.0, 0.0)
+    for _ in range(args.warmup):
+        ctx.render(rec_, con_, rgb, v_, r_, int(cam0["width"]), int(cam0["height"]), bg, img)
+    t_render = timed(lambda: ctx.render(rec_, con_, rgb, v_, r_, int(cam0["width"]), int(cam0["height"]),
+                                        bg, img), args.steps)
+    t_pipe = timed(lambda: ctx.render_frame_3d(g, c, rgb, cam0, bg, img), args.steps)
     ms_views, m_views = [], 0
     for v in range(len(sc.cameras)):
         t = timed(lambda: ctx.sort_frame_3d(g, c, sc.cameras[v]), 1)
@@ -520,6 +531,12 @@ def run_frame3d(args, local_rank):
                            "peak_source": peak_kind},
             "kernels": {k: {"launches": d["launches"], "avg_ms": round(d["ms"] / max(1, d["launches"]), 5)}
                         for k, d in kt.items()},
+            "render": {"p50_ms": round(statistics.median(t_render), 4),
+                       "p99_ms": round(float(np.percentile(t_render, 99)), 4),
+                       "pixels": int(cam0["width"]) * int(cam0["height"])},
+            "pipeline_preprocess_sort_render": {"p50_ms": round(statistics.median(t_pipe), 4),
+                                                "p99_ms": round(float(np.percentile(t_pipe, 99)), 4),
+                                                "images_per_s": round(1e3 / statistics.median(t_pipe), 1)},
             "views_loop": {"views": len(ms_views), "pairs_total": m_views,
                            "pairs_per_s": m_views / (sum(ms_views) * 1e-3),
                            "p50_ms": round(statistics.median(ms_views), 4),

@@ -18,6 +18,8 @@
  *   0. tdgs_preprocess     the Preprocessing stage before step 1: 3D
  *                          Gaussians -> projected records for one camera
  *   +  tdgs_sort_frame_3d  preprocessing and steps 1-5 in one call
+ *   6. tdgs_render         the Rendering stage after step 5: front-to-back
+ *                          alpha blending of every tile into an image
  *
  * Conventions shared by every call
  *   - Data pointers are DEVICE pointers unless a parameter says "host".
@@ -316,6 +318,27 @@ tdgs_status tdgs_sort_frame_3d(tdgs_context* ctx, const tdgs_gaussian3d* g, cons
                                const float** conic_opacity, const uint64_t** sorted_keys,
                                const uint32_t** sorted_values, const tdgs_range** ranges,
                                uint32_t* m_out, void* stream);
+
+/* Rendering (Sec. II-A "Rendering"; Sec. IV-C: one 16x16 tile per thread
+ * block, four pixels per thread).  Each pixel blends its tile's Gaussians
+ * sorted_values[ranges[t].start .. ranges[t].end) front to back; the
+ * paper prints no formulas, the library applies the compositing of 3D
+ * Gaussian splatting in float32 with every operation rounded in this order
+ * (sample point = the pixel's integer coordinate; T = 1, C = 0):
+ *   d = (x - px, y - py); power = -0.5 (a dx^2 + c dy^2) - b dx dy
+ *   skip if power > 0; alpha = min(0.99, opacity exp(power));
+ *   skip if alpha < 1/255; T' = T (1 - alpha); stop if T' < 1e-4;
+ *   C += rgb alpha T; T = T'
+ * and the pixel is C + T background.
+ * records (n, 16-byte aligned), conic_opacity (n x 4 floats: a, b, c,
+ * opacity; 16-byte aligned), rgb (n x 3 floats), sorted_values and ranges
+ * (as tdgs_sort_frame returns them; sorted_values may be NULL when every
+ * range is empty): device.  background: 3 HOST floats.
+ * image: device, height x width x 3 floats (interleaved RGB, row-major).
+ * A sorted value >= n is skipped and latches TDGS_ERR_INVALID_ARGUMENT. */
+tdgs_status tdgs_render(tdgs_context* ctx, const tdgs_gaussian2d* records, const float* conic_opacity,
+                        const float* rgb, uint32_t n, const uint32_t* sorted_values, const tdgs_range* ranges,
+                        tdgs_frame f, const float* background, float* image, void* stream);
 
 /* ------------------------------------------------- scan without allocation */
 

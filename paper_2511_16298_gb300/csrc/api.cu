@@ -38,6 +38,7 @@ const char* site_name(uint32_t site) {
     case kSiteBarrier: return "radix pass grid barrier wait";
     case kSiteViewsCount: return "frame count";
     case kSiteViewsDup: return "duplicate by depth";
+    case kSiteRender: return "render (a sorted value is not a Gaussian index)";
   }
   return "device";
 }
@@ -49,12 +50,12 @@ struct Buffer {
 
 enum KernelId {
   kKCount, kKScan, kKDuplicate, kKRanges, kKRadixPass,
-  kKFrameCount, kKDepthSort, kKFrameScan, kKDupDepth, kKTilePass, kKTileExpand, kKPreprocess, kKBitonic, kKNum
+  kKFrameCount, kKDepthSort, kKFrameScan, kKDupDepth, kKTilePass, kKTileExpand, kKPreprocess, kKBitonic, kKRender, kKNum
 };
 const char* const kKernelNames[kKNum] = {
     "count_tiles",  "scan",       "duplicate_keys",     "tile_ranges",    "radix_pass",
     "frame_count",  "depth_sort", "scan_by_depth", "duplicate_by_depth", "tile_sort_pass",
-    "tile_expand_pass", "preprocess", "bitonic_sort"};
+    "tile_expand_pass", "preprocess", "bitonic_sort", "render"};
 
 // View table as stored in device memory (SoA, fixed maximum size).
 struct ViewBlob {
@@ -950,6 +951,27 @@ tdgs_status tdgs_sort_frame_3d(tdgs_context* ctx, const tdgs_gaussian3d* g, cons
   if (conic_opacity) *conic_opacity = static_cast<const float*>(ctx->f_conic.p);
   return tdgs_sort_frame(ctx, static_cast<const tdgs_gaussian2d*>(ctx->f_rec3.p), n,
                          tdgs_frame{cam->width, cam->height}, sorted_keys, sorted_values, ranges, m_out, stream);
+}
+
+tdgs_status tdgs_render(tdgs_context* ctx, const tdgs_gaussian2d* records, const float* conic_opacity,
+                        const float* rgb, uint32_t n, const uint32_t* sorted_values, const tdgs_range* ranges,
+                        tdgs_frame f, const float* background, float* image, void* stream) {
+  if (!ctx) return TDGS_ERR_INVALID_ARGUMENT;
+  if (f.width == 0 || f.height == 0) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "empty image");
+  if (!ranges || !image || !background) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "null pointer");
+  if (n && (!records || !conic_opacity || !rgb))
+    return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "null pointer");
+  if (!aligned(records, 16) || !aligned(conic_opacity, 16) || !aligned(rgb, 4) || !aligned(sorted_values, 4) ||
+      !aligned(ranges, 8) || !aligned(image, 4))
+    return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "misaligned pointer");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint64_t tiles = static_cast<uint64_t>((f.width + 15) / 16) * ((f.height + 15) / 16);
+  TDGS_TRACED(ctx, kKRender, tiles, s,
+              launch_render(reinterpret_cast<const float4*>(records), reinterpret_cast<const float4*>(conic_opacity),
+                            rgb, sorted_values, reinterpret_cast<const uint2*>(ranges), f.width, f.height,
+                            background, n, image, err_word(ctx), s));
+  return TDGS_OK;
 }
 
 tdgs_status tdgs_sort_views(tdgs_context* ctx, const tdgs_view* views, uint32_t num_views,

@@ -1,0 +1,124 @@
+// Rendering (Sec. II-A "Rendering"; Sec. IV-C "Efficient Tile-Based
+// Rendering"): one thread block per 16x16 tile blends the tile's sorted
+// Gaussians front to back into every pixel.  As in the paper each thread
+// owns four pixels (64 threads per tile: column t % 16, rows t / 16 + 4k),
+// so every Gaussian fetched into shared memory is applied four times per
+// thread, and the three colour channels are unrolled.
+//
+// Per pixel (sample point = the pixel's integer coordinate), in float32
+// with each operation rounded in this order (no fused multiply-adds):
+//   d = mean - pixel; power = -0.5 (a dx^2 + c dy^2) - b dx dy
+//   skip if power > 0; alpha = min(0.99, opacity exp(power));
+//   skip if alpha < 1/255; T' = T (1 - alpha); stop if T' < 1e-4;
+//   C += rgb alpha T; T = T'
+// and the pixel is C + T background.  The block stops fetching when all
+// its pixels have stopped.
+#include "tdgs_internal.cuh"
+
+namespace tdgs {
+
+namespace {
+
+constexpr int kRenderThreads = 64;
+constexpr int kPix = 4;  // pixels per thread
+
+__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+
+__global__ void __launch_bounds__(kRenderThreads)
+    k_render(const float4* __restrict__ rec, const float4* __restrict__ conic, const float* __restrict__ rgb,
+             const uint32_t* __restrict__ values, const uint2* __restrict__ ranges, uint32_t gx, uint32_t width,
+             uint32_t height, float3 bg, uint32_t n, float* __restrict__ image, uint32_t* err) {
+  __shared__ float2 s_xy[kRenderThreads];
+  __shared__ float4 s_co[kRenderThreads];
+  __shared__ float s_rgb[kRenderThreads][3];
+  const uint32_t tile = blockIdx.x, t = threadIdx.x;
+  const uint32_t px = (tile % gx) * 16 + (t & 15);
+  const uint32_t py0 = (tile / gx) * 16 + (t >> 4);
+  const float fx = __uint2float_rn(px);
+  float fy[kPix], T[kPix], C[kPix][3];
+  bool done[kPix];
+#pragma unroll
+  for (int k = 0; k < kPix; ++k) {
+    const uint32_t py = py0 + 4 * k;
+    fy[k] = __uint2float_rn(py);
+    T[k] = 1.0f;
+    C[k][0] = C[k][1] = C[k][2] = 0.0f;
+    done[k] = !(px < width && py < height);
+  }
+  const uint2 r = ranges[tile];
+  bool bad = false;
+  for (uint32_t b = r.x; b < r.y; b += kRenderThreads) {
+    const bool mine_done = done[0] && done[1] && done[2] && done[3];
+    if (__syncthreads_count(mine_done) == kRenderThreads) break;
+    const uint32_t idx = b + t;
+    if (idx < r.y) {
+      uint32_t g = values[idx];
+      if (g >= n) {  // not an index of this frame: skipped and reported
+        bad = true;
+        s_co[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        s_xy[t] = make_float2(0.f, 0.f);
+        s_rgb[t][0] = s_rgb[t][1] = s_rgb[t][2] = 0.f;
+      } else {
+        const float4 q = __ldg(rec + g);
+        s_xy[t] = make_float2(q.x, q.y);
+        s_co[t] = __ldg(conic + g);
+        s_rgb[t][0] = __ldg(rgb + 3 * static_cast<size_t>(g));
+        s_rgb[t][1] = __ldg(rgb + 3 * static_cast<size_t>(g) + 1);
+        s_rgb[t][2] = __ldg(rgb + 3 * static_cast<size_t>(g) + 2);
+      }
+    }
+    __syncthreads();
+    const uint32_t cnt = min(static_cast<uint32_t>(kRenderThreads), r.y - b);
+    for (uint32_t j = 0; j < cnt; ++j) {
+      const float2 xy = s_xy[j];
+      const float4 co = s_co[j];
+      const float dx = sub(xy.x, fx);
+#pragma unroll
+      for (int k = 0; k < kPix; ++k) {
+        if (done[k]) continue;
+        const float dy = sub(xy.y, fy[k]);
+        const float q2 = add(mul(mul(co.x, dx), dx), mul(mul(co.z, dy), dy));
+        const float power = sub(mul(-0.5f, q2), mul(mul(co.y, dx), dy));
+        if (power > 0.0f) continue;
+        const float alpha = fminf(0.99f, mul(co.w, expf(power)));
+        if (alpha < 1.0f / 255.0f) continue;
+        const float test_t = mul(T[k], sub(1.0f, alpha));
+        if (test_t < 0.0001f) {
+          done[k] = true;
+          continue;
+        }
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) C[k][ch] = add(C[k][ch], mul(mul(s_rgb[j][ch], alpha), T[k]));
+        T[k] = test_t;
+      }
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && (t & 31) == 0) latch_error(err, TDGS_ERR_INVALID_ARGUMENT, kSiteRender);
+#pragma unroll
+  for (int k = 0; k < kPix; ++k) {
+    const uint32_t py = py0 + 4 * k;
+    if (px < width && py < height) {
+      float* o = image + 3 * (static_cast<size_t>(py) * width + px);
+      o[0] = add(C[k][0], mul(T[k], bg.x));
+      o[1] = add(C[k][1], mul(T[k], bg.y));
+      o[2] = add(C[k][2], mul(T[k], bg.z));
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_render(const float4* rec, const float4* conic, const float* rgb, const uint32_t* values,
+                          const uint2* ranges, uint32_t width, uint32_t height, const float* bg, uint32_t n,
+                          float* image, uint32_t* err, cudaStream_t s) {
+  const uint32_t gx = (width + 15) / 16, gy = (height + 15) / 16;
+  const uint32_t tiles = gx * gy;
+  if (tiles == 0) return cudaSuccess;
+  k_render<<<tiles, kRenderThreads, 0, s>>>(rec, conic, rgb, values, ranges, gx, width, height,
+                                            make_float3(bg[0], bg[1], bg[2]), n, image, err);
+  return cudaGetLastError();
+}
+
+}  // namespace tdgs

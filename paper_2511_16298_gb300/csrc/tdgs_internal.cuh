@@ -87,7 +87,8 @@ __device__ __forceinline__ TileRect tile_rect(const float4 rec, const FrameGeom&
 // which site latched it (kSite* below), for the host's error message.
 enum ErrorSite : uint32_t {
   kSiteNone = 0, kSiteCount, kSiteScan, kSiteScanTimeout, kSiteDuplicate, kSiteRanges,
-  kSiteRadixKeys, kSiteRadixRange, kSiteRadixCapacity, kSiteBarrier, kSiteViewsCount, kSiteViewsDup
+  kSiteRadixKeys, kSiteRadixRange, kSiteRadixCapacity, kSiteBarrier, kSiteViewsCount, kSiteViewsDup,
+  kSiteRender
 };
 __device__ __forceinline__ void latch_error(uint32_t* err, uint32_t code, uint32_t site = kSiteNone) {
   if (atomicCAS(err, 0u, code) == 0u) err[1] = site;
@@ -177,6 +178,13 @@ uint32_t bitonic_padded(uint32_t m);
 uint32_t bitonic_launches(uint32_t m);
 cudaError_t launch_bitonic(const uint64_t* kin, const uint32_t* vin, uint32_t m, uint64_t* kout, uint32_t* vout,
                            uint64_t* ks, uint32_t* vs, cudaStream_t s);
+
+// Front-to-back blending of each 16x16 tile's sorted Gaussians into an
+// interleaved float RGB image (height x width x 3); bg: 3 host floats; n:
+// Gaussians (a sorted value >= n is skipped and latches an error).
+cudaError_t launch_render(const float4* rec, const float4* conic, const float* rgb, const uint32_t* values,
+                          const uint2* ranges, uint32_t width, uint32_t height, const float* bg, uint32_t n,
+                          float* image, uint32_t* err, cudaStream_t s);
 
 // Camera of the preprocessing kernel (the layout of tdgs_camera).
 struct CameraDev {

@@ -105,6 +105,7 @@ def lib():
                 "tdgs_scan_noalloc": ([P, u32, P, P, P, P], st),
                 "tdgs_preprocess": ([P, P, P, u32, P, P, P, P], st),
                 "tdgs_sort_pairs_bitonic": ([P, P, P, P, P, u32, P], st),
+                "tdgs_render": ([P, P, P, P, u32, P, P, F, P, P, P], st),
                 "tdgs_sort_frame_3d": ([P, P, P, u32, P, ctypes.POINTER(P), ctypes.POINTER(P),
                                         ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                                         ctypes.POINTER(u32), P], st),
@@ -393,6 +394,29 @@ class Context:
         if copy:
             k, v, r, rec, con = k.clone(), v.clone(), r.clone(), rec.clone(), con.clone()
         return k, v, r, int(m.value), rec, con
+
+    def render(self, records, conic, rgb, values, ranges, width: int, height: int,
+               background=(0.0, 0.0, 0.0), out=None) -> torch.Tensor:
+        """Front-to-back blend of every tile: returns a (height, width, 3)
+        float32 image.  records: (n, 4) int32 bit-view of the 16-byte
+        records; conic: (n, 4) float32; rgb: (n, 3) float32; values, ranges:
+        as sort_frame returns them."""
+        n = records.shape[0]
+        if out is None:
+            out = torch.empty((height, width, 3), dtype=torch.float32, device=self.device)
+        bg = (ctypes.c_float * 3)(*background)
+        self._check(lib().tdgs_render(self._h, _ptr(records), _ptr(conic), _ptr(rgb), n, _ptr(values),
+                                      _ptr(ranges), _Frame(width, height), ctypes.cast(bg, ctypes.c_void_p),
+                                      _ptr(out), _stream(self.device)), "tdgs_render")
+        return out
+
+    def render_frame_3d(self, g3, cov, rgb, cam, background=(0.0, 0.0, 0.0), out=None):
+        """Preprocessing, sort and render of one camera's image: returns
+        (image, m)."""
+        k, v, r, m, rec, con = self.sort_frame_3d(g3, cov, cam)
+        c = np.asarray(cam).reshape(())
+        img = self.render(rec, con, rgb, v, r, int(c["width"]), int(c["height"]), background, out)
+        return img, m
 
     # ------------------------------------------------------------ views
     @staticmethod

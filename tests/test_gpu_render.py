@@ -1,0 +1,92 @@
+"""Rendering (tdgs_render) against the CPU oracle's blend.
+
+Both sides blend in float32 in the same order; they differ only through
+exp (the GPU's expf against the C library's), whose last-bit differences
+can flip a threshold decision (the 1/255 cut or the 1e-4 stop) now and
+then.  The bar: no pixel channel off by more than 0.02 (a few flipped
+contributions of at most 1/255 each), at most 0.1 % of pixels off by more
+than 1e-4, and a mean absolute difference below 1e-6."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2511_16298_gb300 import synth
+from paper_2511_16298_gb300 import tdgs as T
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+BG = (0.2, 0.3, 0.4)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2511_16298_gb300 import build
+    build.build()
+    c = T.Context(0)
+    yield c
+    c.close()
+
+
+def dev_scene(sc):
+    g = torch.from_numpy(sc.gaussians.view(np.float32).reshape(-1, 4).copy()).to(DEV)
+    c = torch.from_numpy(sc.cov.view(np.float32).reshape(-1, 8).copy()).to(DEV)
+    rgb = torch.from_numpy(sc.rgb.copy()).to(DEV)
+    return g, c, rgb
+
+
+def oracle_image(oracle, sc, cam):
+    st, rec, con = oracle.preprocess(sc.gaussians, sc.cov, cam)
+    W, H = int(cam["width"]), int(cam["height"])
+    ref = oracle.sort_frame(rec, W, H)
+    assert ref["status"] == 0
+    st, img = oracle.render(rec, con, sc.rgb, ref["values"], ref["ranges"], W, H, BG)
+    assert st == 0
+    return img, ref["m"]
+
+
+def compare(got, want):
+    d = np.abs(got.astype(np.float64) - want.astype(np.float64))
+    assert d.max() <= 0.02, d.max()
+    per_px = d.max(axis=2)
+    assert np.mean(per_px > 1e-4) <= 1e-3, np.mean(per_px > 1e-4)
+    assert d.mean() < 1e-6, d.mean()
+
+
+@pytest.mark.parametrize("view", [0, 1, 2, 5])
+def test_render_matches_oracle(ctx, oracle, view):
+    sc = synth.scene3d(seed=2, n=30_000, views=6, width=640, height=360, scale0=0.05)
+    g, c, rgb = dev_scene(sc)
+    img, m = ctx.render_frame_3d(g, c, rgb, sc.cameras[view], BG)
+    want, m_ref = oracle_image(oracle, sc, sc.cameras[view])
+    assert m == m_ref and m > 0
+    compare(img.cpu().numpy(), want)
+
+
+def test_render_odd_image_size(ctx, oracle):
+    """Partial edge tiles: 200 x 75 pixels."""
+    sc = synth.scene3d(seed=4, n=5_000, views=2, width=200, height=75, scale0=0.08)
+    g, c, rgb = dev_scene(sc)
+    img, m = ctx.render_frame_3d(g, c, rgb, sc.cameras[1], BG)
+    want, _ = oracle_image(oracle, sc, sc.cameras[1])
+    compare(img.cpu().numpy(), want)
+
+
+def test_render_empty_frame_is_background(ctx):
+    sc = synth.scene3d(seed=5, n=1000, views=1, width=64, height=48)
+    cam = sc.cameras[0].copy()
+    cam["trans"] = (0.0, 0.0, -1000.0)  # everything behind the camera
+    g, c, rgb = dev_scene(sc)
+    img, m = ctx.render_frame_3d(g, c, rgb, cam, BG)
+    assert m == 0
+    assert torch.allclose(img, torch.tensor(BG, device=DEV).expand_as(img))
+
+
+def test_render_scene_full_size(ctx, oracle):
+    """The 500,000-Gaussian scene seen by one 1280x720 camera."""
+    sc = synth.scene3d(seed=0, n=500_000, views=1)
+    g, c, rgb = dev_scene(sc)
+    img, m = ctx.render_frame_3d(g, c, rgb, sc.cameras[0], BG)
+    want, m_ref = oracle_image(oracle, sc, sc.cameras[0])
+    assert m == m_ref
+    compare(img.cpu().numpy(), want)
