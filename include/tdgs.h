@@ -308,8 +308,11 @@ tdgs_status tdgs_preprocess(tdgs_context* ctx, const tdgs_gaussian3d* g, const t
                             uint32_t n, const tdgs_camera* cam, tdgs_gaussian2d* records,
                             float* conic_opacity, void* stream);
 
-/* tdgs_preprocess into context-owned buffers, then tdgs_sort_frame on the
- * records for the camera's image.  *records and *conic_opacity (each may
+/* Preprocessing and steps 1-5 for the camera's image, with the projection
+ * fused into the count kernel of the fused frame (each Gaussian is
+ * projected, stored and counted in one pass; results identical to
+ * tdgs_preprocess followed by tdgs_sort_frame).  *records and
+ * *conic_opacity (each may
  * be NULL to skip) receive device pointers to the n projected records and
  * n x 4 conic/opacity floats, valid like the sorted buffers (until the next
  * call on the context). */

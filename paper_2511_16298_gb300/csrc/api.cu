@@ -50,12 +50,12 @@ struct Buffer {
 
 enum KernelId {
   kKCount, kKScan, kKDuplicate, kKRanges, kKRadixPass,
-  kKFrameCount, kKDepthSort, kKFrameScan, kKDupDepth, kKTilePass, kKTileExpand, kKPreprocess, kKBitonic, kKRender, kKNum
+  kKFrameCount, kKDepthSort, kKFrameScan, kKDupDepth, kKTilePass, kKTileExpand, kKPreprocess, kKBitonic, kKRender, kKPreCount, kKNum
 };
 const char* const kKernelNames[kKNum] = {
     "count_tiles",  "scan",       "duplicate_keys",     "tile_ranges",    "radix_pass",
     "frame_count",  "depth_sort", "scan_by_depth", "duplicate_by_depth", "tile_sort_pass",
-    "tile_expand_pass", "preprocess", "bitonic_sort", "render"};
+    "tile_expand_pass", "preprocess", "bitonic_sort", "render", "preprocess_count"};
 
 // View table as stored in device memory (SoA, fixed maximum size).
 struct ViewBlob {
@@ -86,6 +86,8 @@ struct tdgs_context {
   Buffer scan_status, sort_scratch;
   // fused-frame / multi-view buffers
   Buffer f_rec3, f_conic;  // projected records and conics of tdgs_sort_frame_3d
+  Proj3D proj{};           // tdgs_sort_frame_3d: the count kernel projects first
+  bool proj_on = false;
   Buffer b_keys, b_vals;   // padded scratch of tdgs_sort_pairs_bitonic
   Buffer f_counts, f_dkey[3], f_dval[3], f_soff, f_sdo, f_rminmax, f_stream[2], f_keys, f_values, f_ranges;
   // depth-key range: accumulators [0..1], result [2..3], passes of the last
@@ -720,9 +722,9 @@ tdgs_status run_front(tdgs_context* ctx, cudaStream_t s, bool early_total = fals
   uint32_t* dv[3] = {static_cast<uint32_t*>(ctx->f_dval[0].p), static_cast<uint32_t*>(ctx->f_dval[1].p),
                      static_cast<uint32_t*>(ctx->f_dval[2].p)};
   // launched even for zero Gaussians: it writes the view starts and M = 0
-  TDGS_TRACED(ctx, kKFrameCount, n_all ? n_all : 1, s,
+  TDGS_TRACED(ctx, ctx->proj_on ? kKPreCount : kKFrameCount, n_all ? n_all : 1, s,
               launch_views_count(vt, n_all, counts, dk[0], dv[0], err_word(ctx), ctx->d_tickets + 1,
-                                 &ctx->d_status->total, ctx->d_range, s));
+                                 &ctx->d_status->total, ctx->d_range, s, ctx->proj_on ? &ctx->proj : nullptr));
   if (early_total) {  // M (and any latched error) as soon as the count kernel is done
     TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     TDGS_CUDA(ctx, cudaEventRecord(ctx->ev_total, s));
@@ -940,17 +942,32 @@ tdgs_status tdgs_sort_frame_3d(tdgs_context* ctx, const tdgs_gaussian3d* g, cons
   if (st != TDGS_OK) return st;
   DeviceGuard dg(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n && (!g || !cov)) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "null pointer");
+  if (!aligned(g, 16) || !aligned(cov, 16)) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "misaligned pointer");
   const size_t bytes = static_cast<size_t>(n) * 16 + 16;
   st = ensure(ctx, ctx->f_rec3, bytes, s);
   if (st == TDGS_OK) st = ensure(ctx, ctx->f_conic, bytes, s);
   if (st != TDGS_OK) return st;
-  st = tdgs_preprocess(ctx, g, cov, n, cam, static_cast<tdgs_gaussian2d*>(ctx->f_rec3.p),
-                       static_cast<float*>(ctx->f_conic.p), stream);
+  // the count kernel of the fused frame projects each Gaussian first
+  // (preprocessing fused with the count) and stores records and conics
+  tdgs_view view{static_cast<const tdgs_gaussian2d*>(ctx->f_rec3.p), n, tdgs_frame{cam->width, cam->height}};
+  st = stage_views(ctx, &view, 1);
+  if (st != TDGS_OK) return st;
+  ctx->reserved = false;
+  ctx->proj = Proj3D{reinterpret_cast<const float4*>(g), reinterpret_cast<const float4*>(cov),
+                     static_cast<float4*>(ctx->f_rec3.p), static_cast<float4*>(ctx->f_conic.p), cd};
+  ctx->proj_on = true;
+  uint32_t m = 0;
+  st = sort_views_exact(ctx, s, &m);
+  ctx->proj_on = false;
   if (st != TDGS_OK) return st;
   if (records) *records = static_cast<const tdgs_gaussian2d*>(ctx->f_rec3.p);
   if (conic_opacity) *conic_opacity = static_cast<const float*>(ctx->f_conic.p);
-  return tdgs_sort_frame(ctx, static_cast<const tdgs_gaussian2d*>(ctx->f_rec3.p), n,
-                         tdgs_frame{cam->width, cam->height}, sorted_keys, sorted_values, ranges, m_out, stream);
+  *sorted_keys = static_cast<const uint64_t*>(ctx->f_keys.p);
+  *sorted_values = static_cast<const uint32_t*>(ctx->f_values.p);
+  *ranges = static_cast<const tdgs_range*>(ctx->f_ranges.p);
+  *m_out = m;
+  return TDGS_OK;
 }
 
 tdgs_status tdgs_render(tdgs_context* ctx, const tdgs_gaussian2d* records, const float* conic_opacity,

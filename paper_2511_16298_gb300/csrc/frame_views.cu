@@ -10,7 +10,7 @@
 // the 64-bit keys defines: ties of the 64-bit key are pairs of distinct
 // Gaussians of one view in the same tile with equal depth, and both orders
 // put them in index order.
-#include "tdgs_internal.cuh"
+#include "project.cuh"
 
 namespace tdgs {
 
@@ -23,11 +23,15 @@ namespace tdgs {
 // range[0..1] accumulate the smallest and largest depth key of a Gaussian
 // with pairs (reset to all ones / zero by the last block, which publishes
 // them in range[2..3] for the depth sort).
+// kProject: one view whose records are first computed from 3D Gaussians
+// (the preprocessing stage fused into the count, proj::project) and stored
+// for the later kernels.
 constexpr int kCountUnroll = 4;
+template <bool kProject>
 __global__ void __launch_bounds__(256)
     k_views_count(ViewTable vt, uint32_t n_all, uint32_t* __restrict__ counts,
                   uint32_t* __restrict__ dkey, uint32_t* __restrict__ dval, uint32_t* err,
-                  uint32_t* ticket, uint64_t* total, uint32_t* range) {
+                  uint32_t* ticket, uint64_t* total, uint32_t* range, Proj3D pj) {
   __shared__ uint32_t s_begin[kMaxViews + 1];
   __shared__ unsigned long long s_tot[kMaxViews];
   __shared__ const float4* s_g[kMaxViews];
@@ -47,6 +51,7 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   bool bad = false;
   uint32_t lo = 0xffffffffu, hi = 0u;  // depth keys of Gaussians with pairs
+  const float2 lim = kProject ? proj::slope_limits(pj.cam) : make_float2(0.f, 0.f);
   const uint32_t lane = lane_id();
   const uint32_t stride = gridDim.x * blockDim.x;
   // warp-uniform loop so the per-view totals can be reduced across the
@@ -60,8 +65,16 @@ __global__ void __launch_bounds__(256)
       vv[u] = 0;
       rec[u] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (i < n_all) {
-        vv[u] = vt.nv == 1 ? 0u : find_view(s_begin, vt.nv, i);
-        rec[u] = __ldg(s_g[vv[u]] + (i - s_begin[vv[u]]));
+        if constexpr (kProject) {
+          float4 co;
+          proj::project(__ldg(pj.g + i), __ldg(pj.cov + 2 * static_cast<size_t>(i)),
+                        __ldg(pj.cov + 2 * static_cast<size_t>(i) + 1), pj.cam, lim, rec[u], co);
+          pj.rec[i] = rec[u];
+          pj.conic[i] = co;
+        } else {
+          vv[u] = vt.nv == 1 ? 0u : find_view(s_begin, vt.nv, i);
+          rec[u] = __ldg(s_g[vv[u]] + (i - s_begin[vv[u]]));
+        }
       }
     }
 #pragma unroll
@@ -134,10 +147,13 @@ __global__ void __launch_bounds__(256)
 
 cudaError_t launch_views_count(const ViewTable& vt, uint32_t n_all, uint32_t* counts,
                                uint32_t* dkey, uint32_t* dval, uint32_t* err, uint32_t* ticket,
-                               uint64_t* total, uint32_t* range, cudaStream_t s) {
+                               uint64_t* total, uint32_t* range, cudaStream_t s, const Proj3D* proj) {
   const uint32_t blocks = (n_all + 256 * kCountUnroll - 1) / (256 * kCountUnroll);
   const uint32_t grid = blocks < 1u ? 1u : (blocks < 152u * 8u ? blocks : 152u * 8u);
-  k_views_count<<<grid, 256, 0, s>>>(vt, n_all, counts, dkey, dval, err, ticket, total, range);
+  if (proj)
+    k_views_count<true><<<grid, 256, 0, s>>>(vt, n_all, counts, dkey, dval, err, ticket, total, range, *proj);
+  else
+    k_views_count<false><<<grid, 256, 0, s>>>(vt, n_all, counts, dkey, dval, err, ticket, total, range, Proj3D{});
   return cudaGetLastError();
 }
 

@@ -200,9 +200,21 @@ static_assert(sizeof(CameraDev) == 76, "camera block");
 cudaError_t launch_preprocess(const float4* g, const float4* cov, uint32_t n, const CameraDev& cam, float4* rec,
                               float4* conic, cudaStream_t s);
 
+// Preprocessing fused into the count kernel (one view): the kernel
+// projects Gaussian i from g[i] and cov[2i..2i+1] for cam, stores the
+// record and conic, and counts it.
+struct Proj3D {
+  const float4* g;
+  const float4* cov;
+  float4* rec;
+  float4* conic;
+  CameraDev cam;
+};
+
 cudaError_t launch_views_count(const ViewTable& vt, uint32_t n_all, uint32_t* counts,
                                uint32_t* dkey, uint32_t* dval, uint32_t* err, uint32_t* ticket,
-                               uint64_t* total, uint32_t* range, cudaStream_t s);
+                               uint64_t* total, uint32_t* range, cudaStream_t s,
+                               const Proj3D* proj = nullptr);
 // sdo: receives {depth key, record index} per depth position (read by the
 // expanding tile pass with one 8-byte load per pair).
 cudaError_t launch_views_dup(const ViewTable& vt, const uint32_t* sorder, const uint32_t* soff,
