@@ -529,8 +529,10 @@ struct TileRegs {
 // Phase 3, first half, for one tile of `valid` keys starting at kt
 // (kFull: valid == kTileKeys, no bounds checks): load, stable rank within
 // each warp, exclusive prefix over warps; on return (after a block
-// barrier) lstart holds the tile's count per digit.  Each warp's counter
-// row is zero on entry.
+// barrier) lstart holds the tile's count per digit -- with more than 64
+// digits; with at most 64 the per-warp counts are left for scatter_tile,
+// which folds the prefix into its one-warp digit starts.  Each warp's
+// counter row is zero on entry.
 // kXform: the resident depth sort's key compression may apply (a.xform_in).
 template <bool kFull, typename S, typename K, bool kExpand, int kBits, int kItems, bool kXform = false>
 __device__ __forceinline__ void rank_tile(const K* __restrict__ kt, uint32_t valid, const PassArgs& a, bool d31,
@@ -584,8 +586,10 @@ __device__ __forceinline__ void rank_tile(const K* __restrict__ kt, uint32_t val
   }
   __syncthreads();
   // exclusive prefix over warps per digit (two digits per 32-bit word);
-  // tile count per digit into lstart
-  {
+  // tile count per digit into lstart.  With at most 64 digits scatter_tile
+  // does this together with the digit starts in one warp (one block
+  // barrier less per tile).
+  if constexpr (S::kBins > 64) {
     uint32_t* wh32 = reinterpret_cast<uint32_t*>(sm.wh);
 #pragma unroll
     for (int i = 0; i < kCpt; ++i) {
@@ -602,8 +606,8 @@ __device__ __forceinline__ void rank_tile(const K* __restrict__ kt, uint32_t val
         sm.lstart[2 * c + 1] = run >> 16;
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 // Phase 3, second half: digit starts (with base[] = this chunk's running
@@ -624,7 +628,44 @@ __device__ __forceinline__ bool scatter_tile(const uint32_t* __restrict__ vt, ui
   const uint32_t wbase = warp * 32 * kItems;
   uint16_t* my_wh = sm.wh + warp * kBins;
   bool ok = true;
-  digit_starts<S, K>(sm, s_warp);
+  if constexpr (kBins <= 64) {
+    // one warp: prefix over warps of each counter column (two digits per
+    // word, lane = column), the tile's count per digit, the digit starts
+    constexpr int kCols = S::kCols;
+    if (t < 32) {
+      uint32_t* wh32 = reinterpret_cast<uint32_t*>(sm.wh);
+      uint32_t run = 0;
+      if (lane < static_cast<uint32_t>(kCols)) {
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+          const uint32_t x = wh32[w * kCols + lane];
+          wh32[w * kCols + lane] = run;
+          run += x;  // halves stay below 2^16: no carry between digits
+        }
+      }
+      const uint32_t c0 = run & 0xffffu, c1 = run >> 16;
+      const uint32_t sum = c0 + c1;
+      uint32_t x = sum;
+#pragma unroll
+      for (int dd = 1; dd < 32; dd <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, x, dd);
+        if (lane >= static_cast<uint32_t>(dd)) x += o;
+      }
+      if (lane < static_cast<uint32_t>(kCols)) {
+        const uint32_t st0 = x - sum, st1 = st0 + c0;
+        const uint32_t b0 = 2 * lane, b1 = b0 + 1;
+        const uint32_t bs0 = sm.base[b0], bs1 = sm.base[b1];
+        sm.lstart[b0] = st0;
+        sm.lstart[b1] = st1;
+        sm.off[b0] = bs0 - st0;
+        sm.off[b1] = bs1 - st1;
+        sm.base[b0] = bs0 + c0;
+        sm.base[b1] = bs1 + c1;
+      }
+    }
+  } else {
+    digit_starts<S, K>(sm, s_warp);
+  }
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < kItems; ++j) R.r[j] += sm.lstart[R.d[j]] + my_wh[R.d[j]];
@@ -843,6 +884,7 @@ __global__ void __launch_bounds__(kThreads, kOcc)
                      uint32_t* __restrict__ v1, K* __restrict__ k2, uint32_t* __restrict__ v2, PassArgs a,
                      ResidentArgs ra) {
   using S = PassShape<K, true, false, kBits, kThreads, kItems, kOcc>;
+  static_assert(S::kBins > 64, "the resident kernel reads the tile counts right after rank_tile");
   extern __shared__ __align__(16) unsigned char smem[];
   Smem<K> sm;
   {
