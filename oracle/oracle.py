@@ -57,6 +57,8 @@ def load(path: str):
     L.oracle_duplicate.argtypes = [P, P, u32, u32, u32, P, P, u32]
     L.oracle_sort_pairs.argtypes = [P, P, u32]
     L.oracle_tile_ranges.argtypes = [P, u32, u32, P]
+    L.oracle_sort_frame_normalized.argtypes = [P, u32, u32, u32, P, P, u32, P, P]
+    L.oracle_sort_frame_normalized.restype = ctypes.c_int
     L.oracle_render.argtypes = [P, P, P, P, P, u32, u32, P, P]
     L.oracle_render.restype = ctypes.c_int
     L.oracle_preprocess.argtypes = [P, P, u32, P, P, P]
@@ -107,6 +109,9 @@ class Oracle:
 
     def preprocess(self, g3, cov, cam):
         return preprocess(g3, cov, cam, L=self._lib())
+
+    def sort_frame_normalized(self, g, width, height):
+        return sort_frame_normalized(g, width, height, L=self._lib())
 
     def render(self, rec, conic, rgb, sorted_values, ranges, width, height, background):
         return render(rec, conic, rgb, sorted_values, ranges, width, height, background, L=self._lib())
@@ -180,6 +185,22 @@ def preprocess(g3: np.ndarray, cov: np.ndarray, cam: np.ndarray, L=None):
     conic = np.zeros((n, 4), dtype=np.float32)
     st = (L or lib()).oracle_preprocess(_ptr(g3), _ptr(cov), n, _ptr(cam.reshape(1)), _ptr(rec), _ptr(conic))
     return st, rec, conic
+
+
+def sort_frame_normalized(g: np.ndarray, width: int, height: int, L=None):
+    """The 32-bit normalised-key frame (tile << 10 | 10-bit normalised
+    depth): returns (status, keys uint32, values uint32, ranges (T, 2))."""
+    g = _records(g)
+    st, counts = count_tiles(g, width, height, L)
+    m_cap = int(counts.astype(np.uint64).sum()) if st == OK else 0
+    keys = np.zeros(m_cap, dtype=np.uint32)
+    values = np.zeros(m_cap, dtype=np.uint32)
+    T = num_tiles(width, height, L)
+    ranges = np.zeros((T, 2), dtype=np.uint32)
+    m = np.zeros(1, dtype=np.uint32)
+    st = (L or lib()).oracle_sort_frame_normalized(_ptr(g), len(g), width, height, _ptr(keys), _ptr(values),
+                                                   m_cap, _ptr(m), _ptr(ranges))
+    return st, keys[:int(m[0])], values[:int(m[0])], ranges
 
 
 def render(rec, conic, rgb, sorted_values, ranges, width: int, height: int, background, L=None):

@@ -345,6 +345,72 @@ int oracle_render(const G2* rec, const float* conic_opacity, const float* rgb, c
   return kOk;
 }
 
+// The paper's 32-bit key (Sec. IV-B "key normalization"): 20 bits of tile
+// number and the depth normalised to the range 2^10, so that a float-based
+// sort can order by tile, then depth.  The figure that fixes the layout is
+// not in the text; the reading here:
+//   visible Gaussians: those with pairs (count > 0);
+//   dmin, dmax: their smallest and largest depth (float32);
+//   scale = 1024 / (dmax - dmin) (0 if dmax == dmin);
+//   q = min(1023, floor((depth - dmin) * scale))   (float32, in this order)
+//   key32 = tile << 10 | q   (bits 30 and 31 clear: the bit pattern of a
+//                             positive float, so float and integer order agree)
+// requiring tile < 2^20.  Pairs are emitted like oracle_duplicate (same
+// order and values) and sorted stably by key32; ranges come from
+// key32 >> 10.  Depths closer than 1/1024 of the range collapse to one q
+// and then keep index order: the result differs from the exact 64-bit sort
+// wherever that happens.
+int oracle_sort_frame_normalized(const G2* g, uint32_t n, uint32_t width, uint32_t height, uint32_t* keys,
+                                 uint32_t* values, uint32_t m_cap, uint32_t* m_out, uint32_t* ranges) {
+  if (width == 0 || height == 0) return kInvalid;
+  const int32_t gx = static_cast<int32_t>(grid_dim(width));
+  const int32_t gy = static_cast<int32_t>(grid_dim(height));
+  if (static_cast<uint64_t>(gx) * static_cast<uint64_t>(gy) > (1ull << 20)) return kInvalid;
+  std::vector<uint32_t> counts(n);
+  if (oracle_count_tiles(g, n, width, height, counts.data()) != kOk) return kInvalid;
+  float dmin = 0.0f, dmax = 0.0f;
+  bool any = false;
+  uint64_t m = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    if (!counts[i]) continue;
+    m += counts[i];
+    if (!any || g[i].depth < dmin) dmin = g[i].depth;
+    if (!any || g[i].depth > dmax) dmax = g[i].depth;
+    any = true;
+  }
+  if (m > m_cap) return kInvalid;
+  const float scale = dmax > dmin ? 1024.0f / (dmax - dmin) : 0.0f;
+  std::vector<uint32_t> k0, v0;
+  k0.reserve(m);
+  v0.reserve(m);
+  for (uint32_t i = 0; i < n; ++i) {
+    if (!counts[i]) continue;
+    const Rect q = tile_rect(g[i], gx, gy);
+    const float f = std::floor((g[i].depth - dmin) * scale);
+    const uint32_t qd = f >= 1023.0f ? 1023u : static_cast<uint32_t>(f);
+    for (int32_t ty = q.y0; ty < q.y1; ++ty)
+      for (int32_t tx = q.x0; tx < q.x1; ++tx) {
+        const uint32_t tile = static_cast<uint32_t>(ty) * static_cast<uint32_t>(gx) + static_cast<uint32_t>(tx);
+        k0.push_back((tile << 10) | qd);
+        v0.push_back(i);
+      }
+  }
+  std::vector<uint32_t> idx(m);
+  for (uint32_t k = 0; k < m; ++k) idx[k] = k;
+  std::stable_sort(idx.begin(), idx.end(), [&k0](uint32_t a, uint32_t b) { return k0[a] < k0[b]; });
+  const uint32_t tiles = static_cast<uint32_t>(gx * gy);
+  for (uint32_t t = 0; t < tiles; ++t) ranges[2 * t] = ranges[2 * t + 1] = 0;
+  for (uint32_t k = 0; k < m; ++k) {
+    keys[k] = k0[idx[k]];
+    values[k] = v0[idx[k]];
+    const uint32_t t = keys[k] >> 10;
+    if (k == 0 || (keys[k - 1] >> 10) != t) ranges[2 * t] = k;
+    ranges[2 * t + 1] = k + 1;
+  }
+  *m_out = static_cast<uint32_t>(m);
+  return kOk;
+}
+
 // Number of tiles and tile bits of an image (helpers for callers).
 uint32_t oracle_num_tiles(uint32_t width, uint32_t height) {
   return grid_dim(width) * grid_dim(height);

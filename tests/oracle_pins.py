@@ -513,8 +513,57 @@ def check_render(O):
     assert np.allclose(img, np.broadcast_to(bg, img.shape), atol=1e-7)
 
 
+# ------------------------------------------------------------ 32-bit normalised key
+def check_normalized(O):
+    """The 32-bit key (tile << 10 | normalised depth) against hand-computed
+    cases: three visible depths 1, 2, 3 in one tile map to 0, 512, 1023
+    (range 2, scale 512, the top clamped to 1023) while a culled Gaussian
+    with a smaller depth does not move the range; depths closer than
+    range/1024 collapse and keep index order (where the exact sort reverses
+    them); tiles come first; well-separated depths reproduce the exact
+    sort's values; more than 2^20 tiles are rejected; ranges partition the
+    list."""
+    g = synth.records([4.0, 8.0, 12.0, 5.0], [4.0, 8.0, 12.0, 5.0], [3.0, 1.0, 2.0, 0.5], [2, 2, 2, 0])
+    st, k, v, r = O.sort_frame_normalized(g, 16, 16)
+    assert st == 0
+    assert list(k) == [0, 512, 1023] and list(v) == [1, 2, 0]
+    assert list(r[0]) == [0, 3]
+    # collapse: depth 1.0005 (index 0) and 1.0 (index 1) share q = 0 (range 2)
+    g = synth.records([4.0, 6.0, 8.0], [4.0, 6.0, 8.0], [1.0005, 1.0, 3.0], [2, 2, 2])
+    st, k, v, r = O.sort_frame_normalized(g, 16, 16)
+    assert list(k) == [0, 0, 1023] and list(v) == [0, 1, 2]
+    exact = O.sort_frame(g, 16, 16)
+    assert list(exact["values"]) == [1, 0, 2]
+    # tile first: a far Gaussian in tile 0 before a near one in tile 1 (32x16 image)
+    g = synth.records([4.0, 20.0], [4.0, 4.0], [9.0, 1.0], [2, 2])
+    st, k, v, r = O.sort_frame_normalized(g, 32, 16)
+    assert list(k) == [1023, (1 << 10) | 0] and list(v) == [0, 1]
+    assert [list(x) for x in r] == [[0, 1], [1, 2]]
+    # well-separated depths (step 4 over a range of 1996: every q distinct)
+    rng = np.random.default_rng(5)
+    n = 500
+    x = rng.uniform(0, 200, n)
+    y = rng.uniform(0, 120, n)
+    d = 1.0 + 4.0 * rng.permutation(n)
+    g = synth.records(x, y, d, rng.integers(1, 30, n))
+    st, k, v, r = O.sort_frame_normalized(g, 200, 120)
+    exact = O.sort_frame(g, 200, 120)
+    assert st == 0 and np.array_equal(v, exact["values"])
+    assert np.array_equal(k >> 10, (exact["keys"] >> np.uint64(32)).astype(np.uint32))
+    assert np.array_equal(r, exact["ranges"])
+    # more than 2^20 tiles
+    g1 = synth.records([4.0], [4.0], [1.0], [2])
+    assert O.sort_frame_normalized(g1, 16400, 16400)[0] == 1
+    # ranges partition the list in tile order
+    fr = synth.frame_small(1, n=3000, width=200, height=150)
+    st, k, v, r = O.sort_frame_normalized(fr.gaussians, fr.width, fr.height)
+    assert np.all(np.diff(k.astype(np.int64)) >= 0)
+    nz = r[r[:, 1] > r[:, 0]]
+    assert nz[0, 0] == 0 and nz[-1, 1] == len(k) and np.all(nz[1:, 0] == nz[:-1, 1])
+
+
 ALL_CHECKS = (check_golden, check_count_and_duplicate_bruteforce, check_special_cases,
-              check_validity, check_scan, check_sort, check_preprocess, check_render)
+              check_validity, check_scan, check_sort, check_preprocess, check_render, check_normalized)
 
 
 def run_all(O) -> list[str]:

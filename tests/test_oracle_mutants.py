@@ -56,6 +56,14 @@ MUTANTS = {
     "render_cross_sign": ("- co[1] * dx * dy;", "+ co[1] * dx * dy;"),
     "render_pixel_centre": ("const float fx = static_cast<float>(px), fy = static_cast<float>(py);",
                             "const float fx = static_cast<float>(px) + 0.5f, fy = static_cast<float>(py) + 0.5f;"),
+    "norm_scale_1023": ("1024.0f / (dmax - dmin)", "1023.0f / (dmax - dmin)"),
+    "norm_no_clamp": ("f >= 1023.0f ? 1023u : static_cast<uint32_t>(f)", "static_cast<uint32_t>(f)"),
+    "norm_range_includes_culled": ("    if (!counts[i]) continue;\n    m += counts[i];",
+                                   "    if (g[i].depth < dmin || !any) { dmin = g[i].depth; any = true; }\n"
+                                   "    if (!counts[i]) continue;\n    m += counts[i];"),
+    "norm_ties_reversed": ("[&k0](uint32_t a, uint32_t b) { return k0[a] < k0[b]; }",
+                           "[&k0](uint32_t a, uint32_t b) { return k0[a] < k0[b] || (k0[a] == k0[b] && a > b); }"),
+    "norm_shift_12": ("k0.push_back((tile << 10) | qd);", "k0.push_back((tile << 12) | qd);"),
     "rotation_transposed": ("T[0][k] = j00 * R[k] + j02 * R[6 + k];", "T[0][k] = j00 * R[3 * k] + j02 * R[6 + k];"),
 }
 
