@@ -341,6 +341,28 @@ def run_ours(args, rank, world, local_rank, dist):
                 "achieved_gbs": round(24 * n2 * launches / (bmean * 1e-3) / 1e9, 1),
                 "frac": round(24 * n2 * launches / (bmean * 1e-3) / 1e9 / peak, 4),
                 "slowdown_vs_radix": round(bmean / smean, 2)}
+        # the paper's 32-bit normalised key (Sec. IV-B) on the same frame:
+        # lossy, so the share of positions whose Gaussian differs from the
+        # exact order is reported beside the time
+        if not args.no_bitonic:
+            nt = []
+            for i in range(args.warmup + args.steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                nk, nv, nr, nm = ctx.sort_frame_normalized(g, W, H)
+                b.record(stream)
+                if i >= args.warmup:
+                    nt.append((a, b))
+            torch.cuda.synchronize(dev)
+            nms = [a.elapsed_time(b) for a, b in nt]
+            exact_v = ctx.sort_frame(g, W, H)[1]
+            differs = float((nv != exact_v).float().mean().item())
+            sort_only["normalized_key_frame"] = {
+                "pairs_per_s": nm / (statistics.median(nms) * 1e-3), "p50_ms": round(statistics.median(nms), 4),
+                "key_bytes": 4, "sorted_bits": 10 + fr.tile_bits,
+                "positions_differing_from_exact": round(differs, 5),
+                "note": "includes its host wait for the pair count (count + scan, then the rest)"}
         del k0, v0, ka, va, kw, vw
 
     # ---- end to end through the public API with host buffers: records

@@ -18,6 +18,8 @@
  *   0. tdgs_preprocess     the Preprocessing stage before step 1: 3D
  *                          Gaussians -> projected records for one camera
  *   +  tdgs_sort_frame_3d  preprocessing and steps 1-5 in one call
+ *   +  tdgs_sort_frame_normalized  steps 1-5 with the paper's 32-bit
+ *                          normalised key (lossy; for comparison)
  *   6. tdgs_render         the Rendering stage after step 5: front-to-back
  *                          alpha blending of every tile into an image
  *
@@ -321,6 +323,24 @@ tdgs_status tdgs_sort_frame_3d(tdgs_context* ctx, const tdgs_gaussian3d* g, cons
                                const float** conic_opacity, const uint64_t** sorted_keys,
                                const uint32_t** sorted_values, const tdgs_range** ranges,
                                uint32_t* m_out, void* stream);
+
+/* Steps 1-5 with the paper's 32-bit key (Sec. IV-B "key normalization":
+ * 20 bits of tile number and the depth normalised to the range 2^10).  The
+ * figure fixing the layout is not in the text; the library's reading:
+ *   visible = Gaussians with pairs; dmin, dmax = their smallest and largest
+ *   depth; scale = 1024 / (dmax - dmin) (0 if equal);
+ *   q = min(1023, floor((depth - dmin) * scale)) in float32 in this order;
+ *   key = tile << 10 | q (bits 30-31 clear: a positive float's bit pattern)
+ * The pairs are emitted like tdgs_duplicate_keys and sorted stably by the
+ * 32-bit key; ranges come from key >> 10.  Depths closer than 1/1024 of the
+ * range get one q and keep index order, so the order differs from
+ * tdgs_sort_frame wherever that happens (it is lossy by design).  At most
+ * 2^20 tiles (else TDGS_ERR_INVALID_ARGUMENT).  Outputs: device pointers into
+ * context-owned buffers (m keys, m values, tdgs_num_tiles(f) ranges), valid
+ * until the next call on the context; host *m_out.  Waits once (pair count). */
+tdgs_status tdgs_sort_frame_normalized(tdgs_context* ctx, const tdgs_gaussian2d* g, uint32_t n, tdgs_frame f,
+                                       const uint32_t** sorted_keys, const uint32_t** sorted_values,
+                                       const tdgs_range** ranges, uint32_t* m_out, void* stream);
 
 /* Rendering (Sec. II-A "Rendering"; Sec. IV-C: one 16x16 tile per thread
  * block, four pixels per thread).  Each pixel blends its tile's Gaussians

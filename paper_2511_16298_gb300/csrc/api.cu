@@ -50,12 +50,14 @@ struct Buffer {
 
 enum KernelId {
   kKCount, kKScan, kKDuplicate, kKRanges, kKRadixPass,
-  kKFrameCount, kKDepthSort, kKFrameScan, kKDupDepth, kKTilePass, kKTileExpand, kKPreprocess, kKBitonic, kKRender, kKPreCount, kKNum
+  kKFrameCount, kKDepthSort, kKFrameScan, kKDupDepth, kKTilePass, kKTileExpand, kKPreprocess, kKBitonic, kKRender, kKPreCount, kKNormRange, kKNormDup, kKNormPass,
+  kKNormRanges, kKNum
 };
 const char* const kKernelNames[kKNum] = {
     "count_tiles",  "scan",       "duplicate_keys",     "tile_ranges",    "radix_pass",
     "frame_count",  "depth_sort", "scan_by_depth", "duplicate_by_depth", "tile_sort_pass",
-    "tile_expand_pass", "preprocess", "bitonic_sort", "render", "preprocess_count"};
+    "tile_expand_pass", "preprocess", "bitonic_sort", "render", "preprocess_count", "norm_range",
+    "norm_duplicate", "norm_sort_pass", "norm_ranges"};
 
 // View table as stored in device memory (SoA, fixed maximum size).
 struct ViewBlob {
@@ -89,6 +91,7 @@ struct tdgs_context {
   Proj3D proj{};           // tdgs_sort_frame_3d: the count kernel projects first
   bool proj_on = false;
   Buffer b_keys, b_vals;   // padded scratch of tdgs_sort_pairs_bitonic
+  Buffer n_counts, n_offs, n_norm, n_keys[2], n_vals[2], n_ranges;  // tdgs_sort_frame_normalized
   Buffer f_counts, f_dkey[3], f_dval[3], f_soff, f_sdo, f_rminmax, f_stream[2], f_keys, f_values, f_ranges;
   // depth-key range: accumulators [0..1], result [2..3], passes of the last
   // resident depth sort [4]
@@ -466,7 +469,9 @@ void tdgs_context_destroy(tdgs_context* ctx) {
   Buffer* bufs[] = {&ctx->scan_status, &ctx->sort_scratch, &ctx->f_counts,    &ctx->f_dkey[0],
                     &ctx->f_dkey[1],    &ctx->f_dkey[2],     &ctx->f_dval[0],    &ctx->f_dval[1],
                     &ctx->f_dval[2],    &ctx->f_soff,       &ctx->f_sdo,        &ctx->f_rec3,
-                    &ctx->f_conic,      &ctx->b_keys,       &ctx->b_vals,
+                    &ctx->f_conic,      &ctx->b_keys,       &ctx->b_vals,       &ctx->n_counts,
+                    &ctx->n_offs,       &ctx->n_norm,       &ctx->n_keys[0],    &ctx->n_keys[1],
+                    &ctx->n_vals[0],    &ctx->n_vals[1],    &ctx->n_ranges,
                     &ctx->f_rminmax,    &ctx->f_stream[0],   &ctx->f_stream[1],  &ctx->f_keys,
                     &ctx->f_values,     &ctx->f_ranges};
   if (ctx->d_views) cudaFree(ctx->d_views);
@@ -966,6 +971,78 @@ tdgs_status tdgs_sort_frame_3d(tdgs_context* ctx, const tdgs_gaussian3d* g, cons
   *sorted_keys = static_cast<const uint64_t*>(ctx->f_keys.p);
   *sorted_values = static_cast<const uint32_t*>(ctx->f_values.p);
   *ranges = static_cast<const tdgs_range*>(ctx->f_ranges.p);
+  *m_out = m;
+  return TDGS_OK;
+}
+
+tdgs_status tdgs_sort_frame_normalized(tdgs_context* ctx, const tdgs_gaussian2d* g, uint32_t n, tdgs_frame f,
+                                       const uint32_t** sorted_keys, const uint32_t** sorted_values,
+                                       const tdgs_range** ranges, uint32_t* m_out, void* stream) {
+  if (!ctx || !sorted_keys || !sorted_values || !ranges || !m_out) return TDGS_ERR_INVALID_ARGUMENT;
+  *m_out = 0;
+  if (f.width == 0 || f.height == 0) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "empty image");
+  const uint64_t T = static_cast<uint64_t>((f.width + 15) / 16) * ((f.height + 15) / 16);
+  if (T > (1u << 20)) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "the 32-bit key holds at most 2^20 tiles");
+  if (n && !g) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "null pointer");
+  if (!aligned(g, 16)) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "misaligned pointer");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t n4 = static_cast<size_t>(n) * 4 + 16;
+  tdgs_status st = ensure(ctx, ctx->n_counts, n4, s);
+  if (st == TDGS_OK) st = ensure(ctx, ctx->n_offs, n4, s);
+  if (st == TDGS_OK) st = ensure(ctx, ctx->n_norm, 16, s);
+  if (st == TDGS_OK) st = ensure(ctx, ctx->n_ranges, T * 8 + 16, s);
+  if (st != TDGS_OK) return st;
+  uint32_t* counts = static_cast<uint32_t*>(ctx->n_counts.p);
+  uint32_t* offs = static_cast<uint32_t*>(ctx->n_offs.p);
+  uint32_t* norm = static_cast<uint32_t*>(ctx->n_norm.p);
+  uint2* rg = static_cast<uint2*>(ctx->n_ranges.p);
+  const float4* g4 = reinterpret_cast<const float4*>(g);
+  const FrameGeom geom = make_geom(f);
+  TDGS_CUDA(ctx, cudaMemsetAsync(rg, 0, T * 8, s));
+  uint32_t m = 0;
+  if (n) {
+    TDGS_TRACED(ctx, kKCount, n, s, launch_count_tiles(g4, n, geom, counts, err_word(ctx), s));
+    TDGS_CUDA(ctx, cudaMemsetAsync(norm, 0xff, 4, s));
+    TDGS_CUDA(ctx, cudaMemsetAsync(norm + 1, 0, 4, s));
+    TDGS_TRACED(ctx, kKNormRange, n, s, launch_norm_range(g4, counts, n, norm, s));
+    st = do_scan(ctx, kKScan, counts, nullptr, nullptr, FrameGeom{}, n, offs, &ctx->d_status->total, nullptr, s);
+    if (st != TDGS_OK) return st;
+    TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    TDGS_CUDA(ctx, cudaStreamSynchronize(s));
+    if (ctx->h_status->err) return read_and_clear_error(ctx, s);
+    if (ctx->h_status->total > 0xffffffffull) return fail(ctx, TDGS_ERR_OVERFLOW, "pair count above 2^32-1");
+    m = static_cast<uint32_t>(ctx->h_status->total);
+  }
+  const size_t m4 = static_cast<size_t>(m) * 4 + 16;
+  for (int i = 0; i < 2 && st == TDGS_OK; ++i) {
+    st = ensure(ctx, ctx->n_keys[i], m4, s);
+    if (st == TDGS_OK) st = ensure(ctx, ctx->n_vals[i], m4, s);
+  }
+  if (st != TDGS_OK) return st;
+  uint32_t* k[2] = {static_cast<uint32_t*>(ctx->n_keys[0].p), static_cast<uint32_t*>(ctx->n_keys[1].p)};
+  uint32_t* v[2] = {static_cast<uint32_t*>(ctx->n_vals[0].p), static_cast<uint32_t*>(ctx->n_vals[1].p)};
+  uint32_t res = 0;
+  if (m) {
+    TDGS_TRACED(ctx, kKNormDup, n, s, launch_duplicate_norm(g4, offs, n, geom, k[0], v[0], m, norm, err_word(ctx), s));
+    uint32_t tb = 0;
+    while ((1ull << tb) < T) ++tb;
+    const DepthPlan dp = plan_key32_sort(m, 10 + tb, ctx->tuning.ctas_per_sm);
+    if (dp.grid == 0) return fail(ctx, TDGS_ERR_CUDA, "device query for the sort plan failed");
+    st = ensure(ctx, ctx->sort_scratch, dp.scratch_words * 4, s);
+    if (st != TDGS_OK) return st;
+    for (uint32_t p = 0; p < dp.passes; ++p)
+      TDGS_TRACED(ctx, kKNormPass, m, s,
+                  launch_depth_pass(dp, p, k[p & 1], v[p & 1], k[(p + 1) & 1], v[(p + 1) & 1], m,
+                                    static_cast<uint32_t*>(ctx->sort_scratch.p), ctx->d_tickets + 2,
+                                    err_word(ctx), s));
+    res = dp.result;
+    TDGS_TRACED(ctx, kKNormRanges, m, s,
+                launch_tile_ranges_norm(k[res], m, static_cast<uint32_t>(T), rg, err_word(ctx), s));
+  }
+  *sorted_keys = k[res];
+  *sorted_values = v[res];
+  *ranges = reinterpret_cast<const tdgs_range*>(rg);
   *m_out = m;
   return TDGS_OK;
 }

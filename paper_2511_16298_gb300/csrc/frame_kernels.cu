@@ -204,10 +204,21 @@ cudaError_t launch_scan(const uint32_t* counts, const float4* recs, const uint32
 // over the lanes' start offsets (shuffles), and derives (ty, tx) from the
 // local index (row-major within the Gaussian's tile rectangle).  Every
 // store is a fully coalesced 256-byte (keys) / 128-byte (values) run.
+// kNorm: the paper's 32-bit key (Sec. IV-B), tile << 10 | q with q the
+// depth normalised to 2^10 over the visible range norm[0..1] (float bits):
+// scale = 1024 / (dmax - dmin) (0 if equal), q = min(1023, floor((depth -
+// dmin) * scale)), in float32 in this order.
+template <bool kNorm>
 __global__ void __launch_bounds__(256)
     k_duplicate(const float4* __restrict__ g, const uint32_t* __restrict__ offsets, uint32_t n,
-                FrameGeom fg, uint64_t* __restrict__ keys, uint32_t* __restrict__ values,
-                uint32_t cap, uint32_t* err) {
+                FrameGeom fg, void* __restrict__ keys_raw, uint32_t* __restrict__ values,
+                uint32_t cap, const uint32_t* __restrict__ norm, uint32_t* err) {
+  float dmin = 0.0f, scale = 0.0f;
+  if constexpr (kNorm) {
+    dmin = __uint_as_float(norm[0]);
+    const float dmax = __uint_as_float(norm[1]);
+    scale = dmax > dmin ? __fdiv_rn(1024.0f, __fsub_rn(dmax, dmin)) : 0.0f;
+  }
   const uint32_t lane = lane_id();
   const uint32_t warps_total = (gridDim.x * blockDim.x) >> 5;
   bool bad = false, over = false;
@@ -224,7 +235,11 @@ __global__ void __launch_bounds__(256)
       q.x0 = q.y0 = q.x1 = q.y1 = 0;
       q.count = 0;
     }
-    const uint32_t depth_bits = i < n ? __float_as_uint(__ldg(&g[i].z)) : 0u;
+    uint32_t depth_bits = i < n ? __float_as_uint(__ldg(&g[i].z)) : 0u;
+    if constexpr (kNorm) {
+      const float f = floorf(__fmul_rn(__fsub_rn(__uint_as_float(depth_bits), dmin), scale));
+      depth_bits = f >= 1023.0f ? 1023u : static_cast<uint32_t>(f);
+    }
     uint64_t end = start + q.count;
     // warp range [begin, end_max)
     uint64_t end_max = end;
@@ -256,7 +271,10 @@ __global__ void __launch_bounds__(256)
         const uint64_t tile = static_cast<uint64_t>(oy0 + ry) * static_cast<uint64_t>(fg.gx) +
                               static_cast<uint64_t>(ox0 + rx);
         if (p < cap) {
-          keys[p] = (tile << 32) | od;
+          if constexpr (kNorm)
+            static_cast<uint32_t*>(keys_raw)[p] = (static_cast<uint32_t>(tile) << 10) | od;
+          else
+            static_cast<uint64_t*>(keys_raw)[p] = (tile << 32) | od;
           values[p] = wg * 32u + lo;
         } else {
           over = true;
@@ -275,7 +293,47 @@ cudaError_t launch_duplicate(const float4* g, const uint32_t* offsets, uint32_t 
   const uint32_t warps = (n + 31) / 32;
   const uint32_t blocks = (warps + 7) / 8;
   const uint32_t grid = blocks < 152u * 32u ? blocks : 152u * 32u;
-  k_duplicate<<<grid, 256, 0, s>>>(g, offsets, n, fg, keys, values, cap, err);
+  k_duplicate<false><<<grid, 256, 0, s>>>(g, offsets, n, fg, keys, values, cap, nullptr, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_duplicate_norm(const float4* g, const uint32_t* offsets, uint32_t n, FrameGeom fg,
+                                  uint32_t* keys, uint32_t* values, uint32_t cap, const uint32_t* norm,
+                                  uint32_t* err, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const uint32_t warps = (n + 31) / 32;
+  const uint32_t blocks = (warps + 7) / 8;
+  const uint32_t grid = blocks < 152u * 32u ? blocks : 152u * 32u;
+  k_duplicate<true><<<grid, 256, 0, s>>>(g, offsets, n, fg, keys, values, cap, norm, err);
+  return cudaGetLastError();
+}
+
+// Smallest and largest depth (float bits; positive finite depths order as
+// unsigned integers) of the Gaussians with pairs: norm[0] min, norm[1] max
+// (all ones / zero on entry).
+__global__ void __launch_bounds__(256) k_norm_range(const float4* __restrict__ g, const uint32_t* __restrict__ counts,
+                                                    uint32_t n, uint32_t* norm) {
+  uint32_t lo = 0xffffffffu, hi = 0u;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (__ldg(counts + i)) {
+      const uint32_t b = __float_as_uint(__ldg(&g[i].z));
+      lo = min(lo, b);
+      hi = max(hi, b);
+    }
+  }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  if (lane_id() == 0) {
+    if (lo != 0xffffffffu) atomicMin(norm, lo);
+    if (hi != 0u) atomicMax(norm + 1, hi);
+  }
+}
+
+cudaError_t launch_norm_range(const float4* g, const uint32_t* counts, uint32_t n, uint32_t* norm, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const uint32_t blocks = (n + 255) / 256;
+  const uint32_t grid = blocks < 152u * 8u ? blocks : 152u * 8u;
+  k_norm_range<<<grid, 256, 0, s>>>(g, counts, n, norm);
   return cudaGetLastError();
 }
 
@@ -283,18 +341,21 @@ cudaError_t launch_duplicate(const float4* g, const uint32_t* offsets, uint32_t 
 // Identify Range: a tile's range starts where its id differs from the
 // previous key's and ends where it differs from the next key's.  ranges is
 // zeroed beforehand, so tiles without pairs stay {0, 0}.
-__global__ void __launch_bounds__(256) k_tile_ranges(const uint64_t* __restrict__ keys, uint32_t m,
+// K, kShift: 64-bit keys with the tile above bit 32, or the 32-bit
+// normalised keys with the tile above bit 10.
+template <typename K, int kShift>
+__global__ void __launch_bounds__(256) k_tile_ranges(const K* __restrict__ keys, uint32_t m,
                                                      uint32_t num_tiles, uint2* ranges,
                                                      uint32_t* err) {
   bool bad = false;
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
-    const uint64_t t = __ldg(keys + k) >> 32;
+    const uint64_t t = static_cast<uint64_t>(__ldg(keys + k)) >> kShift;
     if (t >= num_tiles) {
       bad = true;
       continue;
     }
-    const uint64_t prev = k > 0 ? (__ldg(keys + k - 1) >> 32) : ~0ull;
-    const uint64_t next = k + 1 < m ? (__ldg(keys + k + 1) >> 32) : ~0ull;
+    const uint64_t prev = k > 0 ? (static_cast<uint64_t>(__ldg(keys + k - 1)) >> kShift) : ~0ull;
+    const uint64_t next = k + 1 < m ? (static_cast<uint64_t>(__ldg(keys + k + 1)) >> kShift) : ~0ull;
     if (t != prev) ranges[t].x = k;
     if (t != next) ranges[t].y = k + 1;
   }
@@ -306,7 +367,16 @@ cudaError_t launch_tile_ranges(const uint64_t* keys, uint32_t m, uint32_t num_ti
   if (m == 0) return cudaSuccess;
   const uint32_t blocks = (m + 255) / 256;
   const uint32_t grid = blocks < 152u * 16u ? blocks : 152u * 16u;
-  k_tile_ranges<<<grid, 256, 0, s>>>(keys, m, num_tiles, ranges, err);
+  k_tile_ranges<uint64_t, 32><<<grid, 256, 0, s>>>(keys, m, num_tiles, ranges, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_ranges_norm(const uint32_t* keys, uint32_t m, uint32_t num_tiles, uint2* ranges,
+                                    uint32_t* err, cudaStream_t s) {
+  if (m == 0) return cudaSuccess;
+  const uint32_t blocks = (m + 255) / 256;
+  const uint32_t grid = blocks < 152u * 16u ? blocks : 152u * 16u;
+  k_tile_ranges<uint32_t, 10><<<grid, 256, 0, s>>>(keys, m, num_tiles, ranges, err);
   return cudaGetLastError();
 }
 

@@ -60,6 +60,17 @@ DepthPlan plan_depth_sort(uint32_t n, int tuned_bits, int ctas_per_sm) {
   return p;
 }
 
+DepthPlan plan_key32_sort(uint32_t m, uint32_t key_bits, int ctas_per_sm) {
+  DepthPlan p{};
+  p.resident = false;
+  p.bits = 11;
+  p.passes = key_bits ? (key_bits + 10) / 11 : 1;
+  p.grid = radix::grid_for(depth_kernel(11), m ? m : 1, ctas_per_sm);
+  p.result = p.passes & 1u;
+  p.scratch_words = radix::scratch_words(depth_kernel(11), p.grid);
+  return p;
+}
+
 namespace {
 void depth_digit(uint32_t bits, uint32_t pass, uint32_t* shift, uint32_t* mask) {
   *shift = pass * bits;

@@ -144,6 +144,15 @@ cudaError_t launch_duplicate(const float4* g, const uint32_t* offsets, uint32_t 
 
 cudaError_t launch_tile_ranges(const uint64_t* keys, uint32_t m, uint32_t num_tiles,
                                uint2* ranges, uint32_t* err, cudaStream_t s);
+// The paper's 32-bit normalised key (Sec. IV-B): depth range of the
+// Gaussians with pairs (norm[0..1], float bits, all ones / zero on entry),
+// duplication into tile << 10 | 10-bit normalised depth, ranges from them.
+cudaError_t launch_norm_range(const float4* g, const uint32_t* counts, uint32_t n, uint32_t* norm, cudaStream_t s);
+cudaError_t launch_duplicate_norm(const float4* g, const uint32_t* offsets, uint32_t n, FrameGeom fg,
+                                  uint32_t* keys, uint32_t* values, uint32_t cap, const uint32_t* norm,
+                                  uint32_t* err, cudaStream_t s);
+cudaError_t launch_tile_ranges_norm(const uint32_t* keys, uint32_t m, uint32_t num_tiles, uint2* ranges,
+                                    uint32_t* err, cudaStream_t s);
 
 // ---- depth-first frame path over a table of views (one view = one frame)
 constexpr uint32_t kMaxViews = 256;
@@ -237,6 +246,9 @@ struct DepthPlan {
   size_t scratch_words;
 };
 DepthPlan plan_depth_sort(uint32_t n, int tuned_bits, int ctas_per_sm);
+// Stable sort of m (u32 key, u32 value) pairs on the low key_bits bits with
+// the per-pass 11-bit kernel (launch_depth_pass); result in pair passes & 1.
+DepthPlan plan_key32_sort(uint32_t m, uint32_t key_bits, int ctas_per_sm);
 cudaError_t launch_depth_pass(const DepthPlan& dp, uint32_t pass, const uint32_t* kin, const uint32_t* vin,
                               uint32_t* kout, uint32_t* vout, uint32_t n, uint32_t* scratch, uint32_t* bar,
                               uint32_t* err, cudaStream_t s);

@@ -106,6 +106,8 @@ def lib():
                 "tdgs_preprocess": ([P, P, P, u32, P, P, P, P], st),
                 "tdgs_sort_pairs_bitonic": ([P, P, P, P, P, u32, P], st),
                 "tdgs_render": ([P, P, P, P, u32, P, P, F, P, P, P], st),
+                "tdgs_sort_frame_normalized": ([P, P, u32, F, ctypes.POINTER(P), ctypes.POINTER(P),
+                                                ctypes.POINTER(P), ctypes.POINTER(u32), P], st),
                 "tdgs_sort_frame_3d": ([P, P, P, u32, P, ctypes.POINTER(P), ctypes.POINTER(P),
                                         ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                                         ctypes.POINTER(u32), P], st),
@@ -342,6 +344,24 @@ class Context:
                                           ctypes.byref(m), _stream(self.device)), "tdgs_sort_frame")
         T = num_tiles(width, height)
         k = _view(kp.value or 0, m.value, torch.int64, self.device)
+        v = _view(vp.value or 0, m.value, torch.int32, self.device)
+        r = _view(rp.value or 0, 2 * T, torch.int32, self.device).view(T, 2)
+        if copy:
+            k, v, r = k.clone(), v.clone(), r.clone()
+        return k, v, r, int(m.value)
+
+    def sort_frame_normalized(self, g: torch.Tensor, width: int, height: int, copy: bool = False):
+        """Steps 1-5 with the paper's 32-bit normalised key (tile << 10 |
+        10-bit depth).  Returns (keys int32, values int32, ranges, m)."""
+        n = g.shape[0]
+        kp, vp, rp = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        m = ctypes.c_uint32(0)
+        self._check(lib().tdgs_sort_frame_normalized(self._h, _ptr(g), n, _Frame(width, height),
+                                                     ctypes.byref(kp), ctypes.byref(vp), ctypes.byref(rp),
+                                                     ctypes.byref(m), _stream(self.device)),
+                    "tdgs_sort_frame_normalized")
+        T = num_tiles(width, height)
+        k = _view(kp.value or 0, m.value, torch.int32, self.device)
         v = _view(vp.value or 0, m.value, torch.int32, self.device)
         r = _view(rp.value or 0, 2 * T, torch.int32, self.device).view(T, 2)
         if copy:
