@@ -324,6 +324,13 @@ tdgs_status tdgs_sort_frame_3d(tdgs_context* ctx, const tdgs_gaussian3d* g, cons
                                const uint32_t** sorted_values, const tdgs_range** ranges,
                                uint32_t* m_out, void* stream);
 
+/* Device pointers to the projected records (16 bytes each) and conic /
+ * opacity words (4 floats each) of the last tdgs_sort_frame_3d or
+ * tdgs_sort_views_3d call on ctx (view after view), valid until the next
+ * call on the context. */
+tdgs_status tdgs_context_projected(tdgs_context* ctx, const tdgs_gaussian2d** records,
+                                   const float** conic_opacity);
+
 /* Steps 1-5 with the paper's 32-bit key (Sec. IV-B "key normalization":
  * 20 bits of tile number and the depth normalised to the range 2^10).  The
  * figure fixing the layout is not in the text; the library's reading:
@@ -435,6 +442,18 @@ tdgs_status tdgs_sort_views_async(tdgs_context* ctx, const tdgs_view* views, uin
 /* After tdgs_sort_views_async: wait for `stream`, return the first latched
  * error, else fill results[num_views]. */
 tdgs_status tdgs_views_results(tdgs_context* ctx, tdgs_view_result* results, uint32_t num_views,
+                               void* stream);
+
+/* Preprocessing and steps 1-5 for num_views (<= 256) cameras of the same
+ * n 3D Gaussians in one batch (the multi-view form of tdgs_sort_frame_3d;
+ * the sort is that of tdgs_sort_views): view v is camera cams[v] (host
+ * array) with its own image size; results[num_views] (host) as
+ * tdgs_sort_views fills them, each byte-identical to tdgs_sort_frame_3d
+ * with that camera alone.  The projected records and conics of view v are
+ * n entries at offset v * n of the buffers tdgs_context_projected returns.
+ * n * num_views < 2^32. */
+tdgs_status tdgs_sort_views_3d(tdgs_context* ctx, const tdgs_gaussian3d* g, const tdgs_cov3d* cov, uint32_t n,
+                               const tdgs_camera* cams, uint32_t num_views, tdgs_view_result* results,
                                void* stream);
 
 #ifdef __cplusplus

@@ -88,7 +88,8 @@ struct tdgs_context {
   Buffer scan_status, sort_scratch;
   // fused-frame / multi-view buffers
   Buffer f_rec3, f_conic;  // projected records and conics of tdgs_sort_frame_3d
-  Proj3D proj{};           // tdgs_sort_frame_3d: the count kernel projects first
+  Buffer d_cams;           // cameras of the 3D calls (device)
+  Proj3D proj{};           // 3D calls: the count kernel projects first
   bool proj_on = false;
   Buffer b_keys, b_vals;   // padded scratch of tdgs_sort_pairs_bitonic
   Buffer n_counts, n_offs, n_norm, n_keys[2], n_vals[2], n_ranges;  // tdgs_sort_frame_normalized
@@ -469,7 +470,7 @@ void tdgs_context_destroy(tdgs_context* ctx) {
   Buffer* bufs[] = {&ctx->scan_status, &ctx->sort_scratch, &ctx->f_counts,    &ctx->f_dkey[0],
                     &ctx->f_dkey[1],    &ctx->f_dkey[2],     &ctx->f_dval[0],    &ctx->f_dval[1],
                     &ctx->f_dval[2],    &ctx->f_soff,       &ctx->f_sdo,        &ctx->f_rec3,
-                    &ctx->f_conic,      &ctx->b_keys,       &ctx->b_vals,       &ctx->n_counts,
+                    &ctx->f_conic,      &ctx->d_cams,       &ctx->b_keys,       &ctx->b_vals,       &ctx->n_counts,
                     &ctx->n_offs,       &ctx->n_norm,       &ctx->n_keys[0],    &ctx->n_keys[1],
                     &ctx->n_vals[0],    &ctx->n_vals[1],    &ctx->n_ranges,
                     &ctx->f_rminmax,    &ctx->f_stream[0],   &ctx->f_stream[1],  &ctx->f_keys,
@@ -888,6 +889,45 @@ tdgs_status check_camera(tdgs_context* ctx, const tdgs_camera* cam, CameraDev* o
   return TDGS_OK;
 }
 
+// Preprocessing fused into the count kernel for nv cameras of the same n
+// 3D Gaussians, then the rest of the fused frame over the nv views.
+tdgs_status sort_views_3d(tdgs_context* ctx, const tdgs_gaussian3d* g, const tdgs_cov3d* cov, uint32_t n,
+                          const tdgs_camera* cams, uint32_t nv, cudaStream_t s, uint32_t* m_out) {
+  if (nv == 0 || nv > kMaxViews) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "view count out of range");
+  if (!cams) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "null camera");
+  std::vector<CameraDev> cd(nv);
+  for (uint32_t v = 0; v < nv; ++v) {
+    tdgs_status st = check_camera(ctx, cams + v, &cd[v]);
+    if (st != TDGS_OK) return st;
+  }
+  if (n && (!g || !cov)) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "null pointer");
+  if (!aligned(g, 16) || !aligned(cov, 16)) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "misaligned pointer");
+  if (static_cast<uint64_t>(n) * nv > 0xffffffffull)
+    return fail(ctx, TDGS_ERR_OVERFLOW, "too many Gaussians in one batch");
+  const size_t total = static_cast<size_t>(n) * nv;
+  tdgs_status st = ensure(ctx, ctx->f_rec3, total * 16 + 16, s);
+  if (st == TDGS_OK) st = ensure(ctx, ctx->f_conic, total * 16 + 16, s);
+  if (st == TDGS_OK) st = ensure(ctx, ctx->d_cams, sizeof(CameraDev) * nv, s);
+  if (st != TDGS_OK) return st;
+  TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->d_cams.p, cd.data(), sizeof(CameraDev) * nv, cudaMemcpyHostToDevice, s));
+  // the count kernel projects each view's Gaussians first (preprocessing
+  // fused with the count) and stores records and conics view after view
+  std::vector<tdgs_view> views(nv);
+  const tdgs_gaussian2d* rec = static_cast<const tdgs_gaussian2d*>(ctx->f_rec3.p);
+  for (uint32_t v = 0; v < nv; ++v) views[v] = tdgs_view{rec + static_cast<size_t>(v) * n, n,
+                                                        tdgs_frame{cams[v].width, cams[v].height}};
+  st = stage_views(ctx, views.data(), nv);
+  if (st != TDGS_OK) return st;
+  ctx->reserved = false;
+  ctx->proj = Proj3D{reinterpret_cast<const float4*>(g), reinterpret_cast<const float4*>(cov),
+                     static_cast<float4*>(ctx->f_rec3.p), static_cast<float4*>(ctx->f_conic.p),
+                     static_cast<const CameraDev*>(ctx->d_cams.p), cd[0]};
+  ctx->proj_on = true;
+  st = sort_views_exact(ctx, s, m_out);
+  ctx->proj_on = false;
+  return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -942,29 +982,10 @@ tdgs_status tdgs_sort_frame_3d(tdgs_context* ctx, const tdgs_gaussian3d* g, cons
                                uint32_t* m_out, void* stream) {
   if (!ctx || !sorted_keys || !sorted_values || !ranges || !m_out) return TDGS_ERR_INVALID_ARGUMENT;
   *m_out = 0;
-  CameraDev cd;
-  tdgs_status st = check_camera(ctx, cam, &cd);
-  if (st != TDGS_OK) return st;
   DeviceGuard dg(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (n && (!g || !cov)) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "null pointer");
-  if (!aligned(g, 16) || !aligned(cov, 16)) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "misaligned pointer");
-  const size_t bytes = static_cast<size_t>(n) * 16 + 16;
-  st = ensure(ctx, ctx->f_rec3, bytes, s);
-  if (st == TDGS_OK) st = ensure(ctx, ctx->f_conic, bytes, s);
-  if (st != TDGS_OK) return st;
-  // the count kernel of the fused frame projects each Gaussian first
-  // (preprocessing fused with the count) and stores records and conics
-  tdgs_view view{static_cast<const tdgs_gaussian2d*>(ctx->f_rec3.p), n, tdgs_frame{cam->width, cam->height}};
-  st = stage_views(ctx, &view, 1);
-  if (st != TDGS_OK) return st;
-  ctx->reserved = false;
-  ctx->proj = Proj3D{reinterpret_cast<const float4*>(g), reinterpret_cast<const float4*>(cov),
-                     static_cast<float4*>(ctx->f_rec3.p), static_cast<float4*>(ctx->f_conic.p), cd};
-  ctx->proj_on = true;
   uint32_t m = 0;
-  st = sort_views_exact(ctx, s, &m);
-  ctx->proj_on = false;
+  tdgs_status st = sort_views_3d(ctx, g, cov, n, cam, 1, s, &m);
   if (st != TDGS_OK) return st;
   if (records) *records = static_cast<const tdgs_gaussian2d*>(ctx->f_rec3.p);
   if (conic_opacity) *conic_opacity = static_cast<const float*>(ctx->f_conic.p);
@@ -972,6 +993,26 @@ tdgs_status tdgs_sort_frame_3d(tdgs_context* ctx, const tdgs_gaussian3d* g, cons
   *sorted_values = static_cast<const uint32_t*>(ctx->f_values.p);
   *ranges = static_cast<const tdgs_range*>(ctx->f_ranges.p);
   *m_out = m;
+  return TDGS_OK;
+}
+
+tdgs_status tdgs_sort_views_3d(tdgs_context* ctx, const tdgs_gaussian3d* g, const tdgs_cov3d* cov, uint32_t n,
+                               const tdgs_camera* cams, uint32_t num_views, tdgs_view_result* results,
+                               void* stream) {
+  if (!ctx || !results) return TDGS_ERR_INVALID_ARGUMENT;
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t m = 0;
+  tdgs_status st = sort_views_3d(ctx, g, cov, n, cams, num_views, s, &m);
+  if (st != TDGS_OK) return st;
+  return fill_results(ctx, results, num_views, s);
+}
+
+tdgs_status tdgs_context_projected(tdgs_context* ctx, const tdgs_gaussian2d** records,
+                                   const float** conic_opacity) {
+  if (!ctx) return TDGS_ERR_INVALID_ARGUMENT;
+  if (records) *records = static_cast<const tdgs_gaussian2d*>(ctx->f_rec3.p);
+  if (conic_opacity) *conic_opacity = static_cast<const float*>(ctx->f_conic.p);
   return TDGS_OK;
 }
 

@@ -23,9 +23,9 @@ namespace tdgs {
 // range[0..1] accumulate the smallest and largest depth key of a Gaussian
 // with pairs (reset to all ones / zero by the last block, which publishes
 // them in range[2..3] for the depth sort).
-// kProject: one view whose records are first computed from 3D Gaussians
-// (the preprocessing stage fused into the count, proj::project) and stored
-// for the later kernels.
+// kProject: every view's records are first computed from the same 3D
+// Gaussians with the view's camera (the preprocessing stage fused into the
+// count, proj::project) and stored for the later kernels.
 constexpr int kCountUnroll = 4;
 template <bool kProject>
 __global__ void __launch_bounds__(256)
@@ -38,11 +38,17 @@ __global__ void __launch_bounds__(256)
   __shared__ FrameGeom s_geom[kMaxViews];
   __shared__ bool s_last;
   __shared__ uint32_t s_lo, s_hi;
+  __shared__ CameraDev s_cam[kProject ? kMaxViews : 1];
+  __shared__ float2 s_lim[kProject ? kMaxViews : 1];
   for (uint32_t v = threadIdx.x; v <= vt.nv; v += blockDim.x) s_begin[v] = vt.rec_begin[v];
   for (uint32_t v = threadIdx.x; v < vt.nv; v += blockDim.x) {
     s_tot[v] = 0;
     s_g[v] = vt.g[v];
     s_geom[v] = vt.geom[v];
+    if constexpr (kProject) {
+      s_cam[v] = pj.cams[v];
+      s_lim[v] = proj::slope_limits(pj.cams[v]);
+    }
   }
   if (threadIdx.x == 0) {
     s_lo = 0xffffffffu;
@@ -51,24 +57,35 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   bool bad = false;
   uint32_t lo = 0xffffffffu, hi = 0u;  // depth keys of Gaussians with pairs
-  const float2 lim = kProject ? proj::slope_limits(pj.cam) : make_float2(0.f, 0.f);
+  // one view reads its camera from the kernel parameters, many views
+  // from shared memory
+  const float2 lim0 = kProject ? proj::slope_limits(pj.cam0) : make_float2(0.f, 0.f);
   const uint32_t lane = lane_id();
   const uint32_t stride = gridDim.x * blockDim.x;
   // warp-uniform loop so the per-view totals can be reduced across the
-  // warp; kCountUnroll records per thread are in flight at once
-  for (uint32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n_all; i0 += stride * kCountUnroll) {
-    float4 rec[kCountUnroll];
-    uint32_t vv[kCountUnroll];
+  // warp; kUnroll records per thread are in flight at once (two when each
+  // needs three 16-byte loads and the projection)
+  constexpr int kUnroll = kProject ? 2 : kCountUnroll;
+  for (uint32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n_all; i0 += stride * kUnroll) {
+    float4 rec[kUnroll];
+    uint32_t vv[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kCountUnroll; ++u) {
+    for (int u = 0; u < kUnroll; ++u) {
       const uint32_t i = i0 + u * stride + lane;
       vv[u] = 0;
       rec[u] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (i < n_all) {
         if constexpr (kProject) {
           float4 co;
-          proj::project(__ldg(pj.g + i), __ldg(pj.cov + 2 * static_cast<size_t>(i)),
-                        __ldg(pj.cov + 2 * static_cast<size_t>(i) + 1), pj.cam, lim, rec[u], co);
+          if (vt.nv == 1) {
+            proj::project(__ldg(pj.g + i), __ldg(pj.cov + 2 * static_cast<size_t>(i)),
+                          __ldg(pj.cov + 2 * static_cast<size_t>(i) + 1), pj.cam0, lim0, rec[u], co);
+          } else {
+            vv[u] = find_view(s_begin, vt.nv, i);
+            const uint32_t l = i - s_begin[vv[u]];
+            proj::project(__ldg(pj.g + l), __ldg(pj.cov + 2 * static_cast<size_t>(l)),
+                          __ldg(pj.cov + 2 * static_cast<size_t>(l) + 1), s_cam[vv[u]], s_lim[vv[u]], rec[u], co);
+          }
           pj.rec[i] = rec[u];
           pj.conic[i] = co;
         } else {
@@ -78,7 +95,7 @@ __global__ void __launch_bounds__(256)
       }
     }
 #pragma unroll
-    for (int u = 0; u < kCountUnroll; ++u) {
+    for (int u = 0; u < kUnroll; ++u) {
       const uint32_t i = i0 + u * stride + lane;
       uint32_t cnt = 0;
       const uint32_t v = vv[u];
@@ -148,7 +165,8 @@ __global__ void __launch_bounds__(256)
 cudaError_t launch_views_count(const ViewTable& vt, uint32_t n_all, uint32_t* counts,
                                uint32_t* dkey, uint32_t* dval, uint32_t* err, uint32_t* ticket,
                                uint64_t* total, uint32_t* range, cudaStream_t s, const Proj3D* proj) {
-  const uint32_t blocks = (n_all + 256 * kCountUnroll - 1) / (256 * kCountUnroll);
+  const uint32_t per_block = 256u * (proj ? 2u : static_cast<uint32_t>(kCountUnroll));
+  const uint32_t blocks = (n_all + per_block - 1) / per_block;
   const uint32_t grid = blocks < 1u ? 1u : (blocks < 152u * 8u ? blocks : 152u * 8u);
   if (proj)
     k_views_count<true><<<grid, 256, 0, s>>>(vt, n_all, counts, dkey, dval, err, ticket, total, range, *proj);

@@ -209,15 +209,17 @@ static_assert(sizeof(CameraDev) == 76, "camera block");
 cudaError_t launch_preprocess(const float4* g, const float4* cov, uint32_t n, const CameraDev& cam, float4* rec,
                               float4* conic, cudaStream_t s);
 
-// Preprocessing fused into the count kernel (one view): the kernel
-// projects Gaussian i from g[i] and cov[2i..2i+1] for cam, stores the
-// record and conic, and counts it.
+// Preprocessing fused into the count kernel: every view is the same n3
+// Gaussians seen by its own camera; global record i of view v (local
+// index l = i - rec_begin[v]) is projected from g[l] and cov[2l..2l+1] for
+// cams[v], stored as rec[i] / conic[i], and counted.
 struct Proj3D {
   const float4* g;
   const float4* cov;
   float4* rec;
   float4* conic;
-  CameraDev cam;
+  const CameraDev* cams;  // device, one per view
+  CameraDev cam0;         // cams[0], passed by value (kernel parameter space) for one view
 };
 
 cudaError_t launch_views_count(const ViewTable& vt, uint32_t n_all, uint32_t* counts,

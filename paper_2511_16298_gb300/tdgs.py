@@ -106,6 +106,8 @@ def lib():
                 "tdgs_preprocess": ([P, P, P, u32, P, P, P, P], st),
                 "tdgs_sort_pairs_bitonic": ([P, P, P, P, P, u32, P], st),
                 "tdgs_render": ([P, P, P, P, u32, P, P, F, P, P, P], st),
+                "tdgs_sort_views_3d": ([P, P, P, u32, P, u32, ctypes.POINTER(_ViewResult), P], st),
+                "tdgs_context_projected": ([P, ctypes.POINTER(P), ctypes.POINTER(P)], st),
                 "tdgs_sort_frame_normalized": ([P, P, u32, F, ctypes.POINTER(P), ctypes.POINTER(P),
                                                 ctypes.POINTER(P), ctypes.POINTER(u32), P], st),
                 "tdgs_sort_frame_3d": ([P, P, P, u32, P, ctypes.POINTER(P), ctypes.POINTER(P),
@@ -349,6 +351,31 @@ class Context:
         if copy:
             k, v, r = k.clone(), v.clone(), r.clone()
         return k, v, r, int(m.value)
+
+    def sort_views_3d(self, g3: torch.Tensor, cov: torch.Tensor, cams, copy: bool = False):
+        """Preprocessing and the sort for every camera of ``cams`` (a CAMERA
+        array) over the same 3D Gaussians in one batch.  Returns a list of
+        (keys, values, ranges, m) per view (views of context buffers unless
+        copy=True)."""
+        cams = np.ascontiguousarray(np.asarray(cams).reshape(-1))
+        assert cams.dtype.itemsize == 76
+        nv = len(cams)
+        cb = ctypes.create_string_buffer(cams.tobytes(), 76 * nv)
+        res = (_ViewResult * nv)()
+        self._check(lib().tdgs_sort_views_3d(self._h, _ptr(g3), _ptr(cov), g3.shape[0],
+                                             ctypes.cast(cb, ctypes.c_void_p), nv, res, _stream(self.device)),
+                    "tdgs_sort_views_3d")
+        return self._results(res, nv, copy)
+
+    def projected(self, n_total: int):
+        """(records (n_total, 4) int32, conic (n_total, 4) float32) of the
+        last 3D call, view after view."""
+        rp, cp = ctypes.c_void_p(), ctypes.c_void_p()
+        self._check(lib().tdgs_context_projected(self._h, ctypes.byref(rp), ctypes.byref(cp)),
+                    "tdgs_context_projected")
+        rec = _view(rp.value or 0, 4 * n_total, torch.int32, self.device).view(n_total, 4)
+        con = _view(cp.value or 0, 4 * n_total, torch.float32, self.device).view(n_total, 4)
+        return rec, con
 
     def sort_frame_normalized(self, g: torch.Tensor, width: int, height: int, copy: bool = False):
         """Steps 1-5 with the paper's 32-bit normalised key (tile << 10 |
