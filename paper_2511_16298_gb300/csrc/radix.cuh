@@ -430,9 +430,14 @@ __device__ __forceinline__ void emit_key(const PassArgs& a, K key, uint32_t gi, 
                                          const uint32_t* s_vtile, void* kout_raw, uint32_t* vout) {
   if constexpr (kExpand) {
     const uint32_t gt = static_cast<uint32_t>(key >> a.rbits);
-    const uint32_t v = a.nv == 1 ? 0u : find_view(s_vrec, a.nv, gi);
-    static_cast<uint64_t*>(kout_raw)[dst] = (static_cast<uint64_t>(gt - s_vtile[v]) << 32) | dep;
-    vout[dst] = gi - s_vrec[v];
+    uint32_t tb = 0, rb = 0;  // first global tile and record of the view (0 for one view)
+    if (a.nv != 1) {
+      const uint32_t v = find_view(s_vrec, a.nv, gi);
+      tb = s_vtile[v];
+      rb = s_vrec[v];
+    }
+    static_cast<uint64_t*>(kout_raw)[dst] = (static_cast<uint64_t>(gt - tb) << 32) | dep;
+    vout[dst] = gi - rb;
     if (a.rmin) {
       if (p == 0 || static_cast<uint32_t>(xk[p - 1] >> a.rbits) != gt) atomicMin(a.rmin + gt, dst);
       if (p + 1 == valid || static_cast<uint32_t>(xk[p + 1] >> a.rbits) != gt) atomicMax(a.rmax + gt, dst + 1);
