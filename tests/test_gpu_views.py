@@ -104,3 +104,21 @@ def test_views_full_config_sampled(ctx, oracle):
     assert min(ms) > 0
     for i in (0, 17, 31, 50, 63):
         check_view(oracle, mv.views[i], out[i])
+
+
+def test_views_maximum_count(ctx, oracle):
+    """256 views (the maximum) of ragged sizes, some empty, in one batch;
+    257 views are rejected."""
+    rng = np.random.default_rng(17)
+    frames = []
+    for i in range(256):
+        n = 0 if i % 37 == 0 else int(rng.integers(1, 400))
+        w, h = int(rng.integers(1, 300)), int(rng.integers(1, 200))
+        frames.append(synth.frame_random(100 + i, n, w, h) if n else synth.Frame(w, h, synth.records([], [], [], []), "e"))
+    gs = [T.records_to_tensor(f.gaussians, DEV) for f in frames]
+    res = ctx.sort_views([(g, f.width, f.height) for g, f in zip(gs, frames)], copy=True)
+    for f, r in zip(frames, res):
+        check_view(oracle, f, r)
+    with pytest.raises(T.TdgsError) as e:
+        ctx.sort_views([(gs[1], frames[1].width, frames[1].height)] * 257)
+    assert e.value.status == T.INVALID_ARGUMENT
