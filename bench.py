@@ -644,6 +644,22 @@ def run_served(args, local_rank):
 
 
 # ------------------------------------------------------------ CPU oracle
+def host_cpu() -> str:
+    """Host CPU description for the CPU-baseline figures: architecture,
+    logical cores, and the model name or part number /proc/cpuinfo gives."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part") and not model:
+                    model = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return f"{platform.machine()}, {os.cpu_count()} logical cores" + (f", {model}" if model else "")
+
+
 def oracle_baseline(frame, reps: int):
     from oracle import oracle as O
     O.build()
@@ -700,7 +716,7 @@ def main():
             "ms_per_step": round(sum(t) / len(t) * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": "scene-1M sample: 250,000 Gaussians, 1280x720, 3600 tiles"},
-            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
                              "sample": desc},
             "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}))
@@ -721,9 +737,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         fr = synth.frame_scene(seed=0)
         m, t = oracle_baseline(fr, args.cpu_reps)
-        cpu = {"value": m * len(t) / sum(t), "unit": "pairs/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": m * len(t) / sum(t), "unit": "pairs/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
                "sample": f"{len(t)} full frames of the 1M-Gaussian 1280x720 workload "
-                         f"({m} pairs each), single thread"}
+                         f"({m} pairs each), single thread",
+               "frame_s_median": round(statistics.median(t), 4)}
     if dist:
         dist.barrier()
     if rank == 0:
