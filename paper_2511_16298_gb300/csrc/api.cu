@@ -83,6 +83,8 @@ struct tdgs_context {
   DevStatus* d_status = nullptr;
   DevStatus* h_status = nullptr;  // pinned
   cudaEvent_t ev_total = nullptr;  // recorded after the copy of the early pair count
+  cudaEvent_t ev_count = nullptr;  // recorded after the count kernel
+  cudaStream_t side = nullptr;     // carries that copy, off the frame's stream
   uint32_t* d_tickets = nullptr;  // [1] count blocks (reset by the kernel), [2..3] radix grid barrier
   uint32_t ticket_base[2] = {0, 0};
   Buffer scan_status, sort_scratch;
@@ -409,6 +411,8 @@ tdgs_status tdgs_context_create(tdgs_context** out, int device) {
       cudaMemset(ctx->d_status, 0, sizeof(DevStatus)) != cudaSuccess ||
       cudaMemset(ctx->d_tickets, 0, 4 * sizeof(uint32_t)) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_total, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_count, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
     tdgs_context_destroy(ctx);
@@ -484,6 +488,8 @@ void tdgs_context_destroy(tdgs_context* ctx) {
   if (ctx->d_range) cudaFree(ctx->d_range);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   if (ctx->ev_total) cudaEventDestroy(ctx->ev_total);
+  if (ctx->ev_count) cudaEventDestroy(ctx->ev_count);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   delete ctx;
 }
 
@@ -731,9 +737,14 @@ tdgs_status run_front(tdgs_context* ctx, cudaStream_t s, bool early_total = fals
   TDGS_TRACED(ctx, ctx->proj_on ? kKPreCount : kKFrameCount, n_all ? n_all : 1, s,
               launch_views_count(vt, n_all, counts, dk[0], dv[0], err_word(ctx), ctx->d_tickets + 1,
                                  &ctx->d_status->total, ctx->d_range, s, ctx->proj_on ? &ctx->proj : nullptr));
-  if (early_total) {  // M (and any latched error) as soon as the count kernel is done
-    TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
-    TDGS_CUDA(ctx, cudaEventRecord(ctx->ev_total, s));
+  if (early_total) {
+    // M (and any latched error) as soon as the count kernel is done; the
+    // copy runs on a side stream so the depth sort does not wait for it
+    TDGS_CUDA(ctx, cudaEventRecord(ctx->ev_count, s));
+    TDGS_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_count, 0));
+    TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost,
+                                   ctx->side));
+    TDGS_CUDA(ctx, cudaEventRecord(ctx->ev_total, ctx->side));
   }
   const DepthPlan dp = plan_depth_sort(n_all, ctx->tuning.depth_digit_bits, ctx->tuning.ctas_per_sm);
   const uint32_t dpasses = dp.passes;
