@@ -655,6 +655,8 @@ def host_cpu() -> str:
                 key = line.split(":")[0].strip().lower()
                 if key in ("model name", "cpu part") and not model:
                     model = line.split(":", 1)[1].strip()
+                    if key == "cpu part":
+                        model = "CPU part " + model
     except OSError:
         pass
     return f"{platform.machine()}, {os.cpu_count()} logical cores" + (f", {model}" if model else "")
