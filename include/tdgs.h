@@ -370,6 +370,17 @@ tdgs_status tdgs_render(tdgs_context* ctx, const tdgs_gaussian2d* records, const
                         const float* rgb, uint32_t n, const uint32_t* sorted_values, const tdgs_range* ranges,
                         tdgs_frame f, const float* background, float* image, void* stream);
 
+/* ------------------------------------------------ failure detection --- */
+
+/* Failure-detection check of the cross-block waits: launches two blocks of
+ * which only one reaches the library's grid barrier (the same code the
+ * radix passes use, on barrier words of its own).  The waiting block gives
+ * up after the barrier's bounded wait (2^21 polls, about 0.1-2 s) and
+ * latches TDGS_ERR_TIMEOUT, which the next tdgs_context_sync (or
+ * tdgs_sort_frame) returns and clears; the context stays usable.  No GPU
+ * fault or hang is involved. */
+tdgs_status tdgs_diag_barrier_timeout(tdgs_context* ctx, void* stream);
+
 /* ------------------------------------------------- scan without allocation */
 
 /* The exclusive scan of tdgs_scan (offsets, total, 64-bit overflow check)

@@ -91,6 +91,7 @@ struct tdgs_context {
   // fused-frame / multi-view buffers
   Buffer f_rec3, f_conic;  // projected records and conics of tdgs_sort_frame_3d
   Buffer d_cams;           // cameras of the 3D calls (device)
+  Buffer diag;             // barrier words of tdgs_diag_barrier_timeout
   Proj3D proj{};           // 3D calls: the count kernel projects first
   bool proj_on = false;
   Buffer b_keys, b_vals;   // padded scratch of tdgs_sort_pairs_bitonic
@@ -474,7 +475,7 @@ void tdgs_context_destroy(tdgs_context* ctx) {
   Buffer* bufs[] = {&ctx->scan_status, &ctx->sort_scratch, &ctx->f_counts,    &ctx->f_dkey[0],
                     &ctx->f_dkey[1],    &ctx->f_dkey[2],     &ctx->f_dval[0],    &ctx->f_dval[1],
                     &ctx->f_dval[2],    &ctx->f_soff,       &ctx->f_sdo,        &ctx->f_rec3,
-                    &ctx->f_conic,      &ctx->d_cams,       &ctx->b_keys,       &ctx->b_vals,       &ctx->n_counts,
+                    &ctx->f_conic,      &ctx->d_cams,       &ctx->diag,       &ctx->b_keys,       &ctx->b_vals,       &ctx->n_counts,
                     &ctx->n_offs,       &ctx->n_norm,       &ctx->n_keys[0],    &ctx->n_keys[1],
                     &ctx->n_vals[0],    &ctx->n_vals[1],    &ctx->n_ranges,
                     &ctx->f_rminmax,    &ctx->f_stream[0],   &ctx->f_stream[1],  &ctx->f_keys,
@@ -1017,6 +1018,17 @@ tdgs_status tdgs_sort_views_3d(tdgs_context* ctx, const tdgs_gaussian3d* g, cons
   tdgs_status st = sort_views_3d(ctx, g, cov, n, cams, num_views, s, &m);
   if (st != TDGS_OK) return st;
   return fill_results(ctx, results, num_views, s);
+}
+
+tdgs_status tdgs_diag_barrier_timeout(tdgs_context* ctx, void* stream) {
+  if (!ctx) return TDGS_ERR_INVALID_ARGUMENT;
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  tdgs_status st = ensure(ctx, ctx->diag, 16, s);
+  if (st != TDGS_OK) return st;
+  TDGS_CUDA(ctx, cudaMemsetAsync(ctx->diag.p, 0, 16, s));
+  TDGS_CUDA(ctx, launch_diag_barrier_timeout(static_cast<uint32_t*>(ctx->diag.p), err_word(ctx), s));
+  return TDGS_OK;
 }
 
 tdgs_status tdgs_context_projected(tdgs_context* ctx, const tdgs_gaussian2d** records,

@@ -105,6 +105,7 @@ def lib():
                 "tdgs_scan_noalloc": ([P, u32, P, P, P, P], st),
                 "tdgs_preprocess": ([P, P, P, u32, P, P, P, P], st),
                 "tdgs_sort_pairs_bitonic": ([P, P, P, P, P, u32, P], st),
+                "tdgs_diag_barrier_timeout": ([P, P], st),
                 "tdgs_render": ([P, P, P, P, u32, P, P, F, P, P, P], st),
                 "tdgs_sort_views_3d": ([P, P, P, u32, P, u32, ctypes.POINTER(_ViewResult), P], st),
                 "tdgs_context_projected": ([P, ctypes.POINTER(P), ctypes.POINTER(P)], st),
@@ -313,6 +314,12 @@ class Context:
                                           _ptr(values_alt), m, tile_bits, flags, ctypes.byref(alt),
                                           _stream(self.device)), "tdgs_sort_pairs")
         return (keys_alt, values_alt) if alt.value else (keys, values)
+
+    def diag_barrier_timeout(self):
+        """Failure-detection check: a grid barrier one block never reaches;
+        the next sync() raises TdgsError(TIMEOUT) and the context stays
+        usable."""
+        self._check(lib().tdgs_diag_barrier_timeout(self._h, _stream(self.device)), "tdgs_diag_barrier_timeout")
 
     def sort_pairs_bitonic(self, keys, values, keys_out=None, values_out=None):
         """The paper's bitonic network: sorts by (key, value); returns
