@@ -1020,6 +1020,17 @@ tdgs_status tdgs_sort_views_3d(tdgs_context* ctx, const tdgs_gaussian3d* g, cons
   return fill_results(ctx, results, num_views, s);
 }
 
+}  // extern "C"
+
+namespace tdgs {
+// Failure-detection check (diag.cu): two blocks of which only one reaches
+// the radix passes' grid barrier on bar (two zeroed words of its own); the
+// bounded wait gives up and latches TDGS_ERR_TIMEOUT in err.
+cudaError_t launch_diag_barrier_timeout(uint32_t* bar, uint32_t* err, cudaStream_t s);
+}  // namespace tdgs
+
+extern "C" {
+
 tdgs_status tdgs_diag_barrier_timeout(tdgs_context* ctx, void* stream) {
   if (!ctx) return TDGS_ERR_INVALID_ARGUMENT;
   DeviceGuard dg(ctx->device);

@@ -107,19 +107,5 @@ cudaError_t launch_resident(const Kernel& k, uint32_t grid, void* k0, uint32_t* 
   return cudaLaunchKernelExC(&cfg, k.fn, args);
 }
 
-namespace {
-// Failure-detection check: of two blocks only block 1 reaches the grid
-// barrier, so its bounded wait runs out and latches TDGS_ERR_TIMEOUT.
-__global__ void k_diag_barrier_timeout(uint32_t* bar, uint32_t* err) {
-  if (blockIdx.x == 1) grid_barrier(bar, err);
-}
-}  // namespace
-
 }  // namespace radix
-
-cudaError_t launch_diag_barrier_timeout(uint32_t* bar, uint32_t* err, cudaStream_t s) {
-  radix::k_diag_barrier_timeout<<<2, 32, 0, s>>>(bar, err);
-  return cudaGetLastError();
-}
-
 }  // namespace tdgs

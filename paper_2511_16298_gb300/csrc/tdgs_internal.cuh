@@ -195,11 +195,6 @@ cudaError_t launch_render(const float4* rec, const float4* conic, const float* r
                           const uint2* ranges, uint32_t width, uint32_t height, const float* bg, uint32_t n,
                           float* image, uint32_t* err, cudaStream_t s);
 
-// Failure-detection check: two blocks of which only one reaches the radix
-// passes' grid barrier on bar (two zeroed words of its own); the bounded
-// wait gives up and latches TDGS_ERR_TIMEOUT in err.
-cudaError_t launch_diag_barrier_timeout(uint32_t* bar, uint32_t* err, cudaStream_t s);
-
 // Camera of the preprocessing kernel (the layout of tdgs_camera).
 struct CameraDev {
   float rot[9];
