@@ -339,12 +339,12 @@ def run_ours(args, rank, world, local_rank, dist):
             stages = n2.bit_length() - 1
             bmean = statistics.mean(bms)
             # each launch reads and writes every padded pair once (12 B each way)
-            launches = 1 + sum((k - 12 + 3) // 4 + 1 for k in range(13, stages + 1))
+            b_launches = 1 + sum((k - 12 + 3) // 4 + 1 for k in range(13, stages + 1))
             sort_only["bitonic"] = {
                 "pairs_per_s": m / (bmean * 1e-3), "ms_mean": round(bmean, 4), "padded_pairs": n2,
-                "launches": launches, "bytes_moved": 24 * n2 * launches,
-                "achieved_gbs": round(24 * n2 * launches / (bmean * 1e-3) / 1e9, 1),
-                "frac": round(24 * n2 * launches / (bmean * 1e-3) / 1e9 / peak, 4),
+                "launches": b_launches, "bytes_moved": 24 * n2 * b_launches,
+                "achieved_gbs": round(24 * n2 * b_launches / (bmean * 1e-3) / 1e9, 1),
+                "frac": round(24 * n2 * b_launches / (bmean * 1e-3) / 1e9 / peak, 4),
                 "slowdown_vs_radix": round(bmean / smean, 2)}
         # the paper's 32-bit normalised key (Sec. IV-B) on the same frame:
         # lossy, so the share of positions whose Gaussian differs from the
