@@ -353,8 +353,8 @@ tdgs_status tdgs_sort_frame_normalized(tdgs_context* ctx, const tdgs_gaussian2d*
  * block, four pixels per thread).  Each pixel blends its tile's Gaussians
  * sorted_values[ranges[t].start .. ranges[t].end) front to back; the
  * paper prints no formulas, the library applies the compositing of 3D
- * Gaussian splatting in float32 (multiply-adds may be fused; sample point =
- * the pixel's integer coordinate; T = 1, C = 0):
+ * Gaussian splatting in float32 (multiply-adds may be fused, exp is CUDA's
+ * fast __expf; sample point = the pixel's integer coordinate; T = 1, C = 0):
  *   d = (x - px, y - py); power = -0.5 (a dx^2 + c dy^2) - b dx dy
  *   skip if power > 0; alpha = min(0.99, opacity exp(power));
  *   skip if alpha < 1/255; T' = T (1 - alpha); stop if T' < 1e-4;

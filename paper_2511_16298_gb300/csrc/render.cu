@@ -6,8 +6,8 @@
 // thread, and the three colour channels are unrolled.
 //
 // Per pixel (sample point = the pixel's integer coordinate), in float32
-// (the compiler may fuse multiply-adds: the result is compared with the
-// oracle's blend within a tolerance anyway, because exp differs):
+// with CUDA's fast exponential and multiply-adds the compiler may fuse
+// (the result is compared with the oracle's blend within a tolerance):
 //   d = mean - pixel; power = -0.5 (a dx^2 + c dy^2) - b dx dy
 //   skip if power > 0; alpha = min(0.99, opacity exp(power));
 //   skip if alpha < 1/255; T' = T (1 - alpha); stop if T' < 1e-4;
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kRenderThreads)
         const float dy = xy.y - fy[k];
         const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
         if (power > 0.0f) continue;
-        const float alpha = fminf(0.99f, co.w * expf(power));
+        const float alpha = fminf(0.99f, co.w * __expf(power));
         if (alpha < 1.0f / 255.0f) continue;
         const float test_t = T[k] * (1.0f - alpha);
         if (test_t < 0.0001f) {
