@@ -350,7 +350,7 @@ tdgs_status tdgs_sort_frame_normalized(tdgs_context* ctx, const tdgs_gaussian2d*
                                        const tdgs_range** ranges, uint32_t* m_out, void* stream);
 
 /* Rendering (Sec. II-A "Rendering"; Sec. IV-C: one 16x16 tile per thread
- * block, four pixels per thread).  Each pixel blends its tile's Gaussians
+ * block; one pixel per thread here).  Each pixel blends its tile's Gaussians
  * sorted_values[ranges[t].start .. ranges[t].end) front to back; the
  * paper prints no formulas, the library applies the compositing of 3D
  * Gaussian splatting in float32 (multiply-adds may be fused, exp is CUDA's
