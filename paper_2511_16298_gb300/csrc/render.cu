@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(kRenderThreads)
   __shared__ float2 s_xy[kRenderThreads];
   __shared__ float4 s_co[kRenderThreads];
   __shared__ float s_rgb[kRenderThreads][3];
+  __shared__ float s_cut[kRenderThreads];  // exponent below which alpha < 1/255
   const uint32_t tile = blockIdx.x, t = threadIdx.x;
   const uint32_t px = (tile % gx) * 16 + (t & 15);
   const uint32_t py0 = (tile / gx) * 16 + (t >> 4);
@@ -63,12 +64,17 @@ __global__ void __launch_bounds__(kRenderThreads)
       if (g >= n) {  // not an index of this frame: skipped and reported
         bad = true;
         s_co[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        s_cut[t] = __int_as_float(0x7f800000);
         s_xy[t] = make_float2(0.f, 0.f);
         s_rgb[t][0] = s_rgb[t][1] = s_rgb[t][2] = 0.f;
       } else {
         const float4 q = __ldg(rec + g);
         s_xy[t] = make_float2(q.x, q.y);
-        s_co[t] = __ldg(conic + g);
+        const float4 c = __ldg(conic + g);
+        s_co[t] = c;
+        // opacity * exp(power) < 1/255 exactly when power < -ln(255 opacity):
+        // far pixels skip the exponential (the 1/255 test below stays)
+        s_cut[t] = c.w > 0.0f ? -__logf(255.0f * c.w) : __int_as_float(0x7f800000);
         s_rgb[t][0] = __ldg(rgb + 3 * static_cast<size_t>(g));
         s_rgb[t][1] = __ldg(rgb + 3 * static_cast<size_t>(g) + 1);
         s_rgb[t][2] = __ldg(rgb + 3 * static_cast<size_t>(g) + 2);
@@ -79,13 +85,14 @@ __global__ void __launch_bounds__(kRenderThreads)
     for (uint32_t j = 0; j < cnt; ++j) {
       const float2 xy = s_xy[j];
       const float4 co = s_co[j];
+      const float cut = s_cut[j];
       const float dx = xy.x - fx;
 #pragma unroll
       for (int k = 0; k < kPix; ++k) {
         if (done[k]) continue;
         const float dy = xy.y - fy[k];
         const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
-        if (power > 0.0f) continue;
+        if (power > 0.0f || power < cut) continue;
         const float alpha = fminf(0.99f, co.w * __expf(power));
         if (alpha < 1.0f / 255.0f) continue;
         const float test_t = T[k] * (1.0f - alpha);
