@@ -184,3 +184,21 @@ def test_sort_views_3d_full_scene_sampled(ctx, oracle):
         assert np.array_equal(k.cpu().numpy().view(np.uint64), ref["keys"])
         assert np.array_equal(vv.cpu().numpy().view(np.uint32), ref["values"])
         assert np.array_equal(r.cpu().numpy().view(np.uint32), ref["ranges"])
+
+
+def test_sort_views_3d_mixed_resolutions(ctx, oracle):
+    """Cameras of different image sizes in one 3D batch."""
+    sc = small_scene()
+    cams = sc.cameras[:3].copy()
+    cams[1]["width"], cams[1]["height"], cams[1]["cx"], cams[1]["cy"] = 200, 90, 100.0, 45.0
+    cams[2]["width"], cams[2]["height"], cams[2]["cx"], cams[2]["cy"] = 1000, 700, 500.0, 350.0
+    g, c = dev3(sc.gaussians, sc.cov)
+    res = ctx.sort_views_3d(g, c, cams, copy=True)
+    for v in range(3):
+        st, orec, _ = oracle.preprocess(sc.gaussians, sc.cov, cams[v])
+        ref = oracle.sort_frame(orec, int(cams[v]["width"]), int(cams[v]["height"]))
+        k, vv, r, m = res[v]
+        assert m == ref["m"]
+        assert np.array_equal(k.cpu().numpy().view(np.uint64), ref["keys"])
+        assert np.array_equal(vv.cpu().numpy().view(np.uint32), ref["values"])
+        assert np.array_equal(r.cpu().numpy().view(np.uint32), ref["ranges"])
