@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "render.cuh"
 #include "tdgs_internal.cuh"
 
 using namespace tdgs;
@@ -51,13 +52,13 @@ struct Buffer {
 enum KernelId {
   kKCount, kKScan, kKDuplicate, kKRanges, kKRadixPass,
   kKFrameCount, kKDepthSort, kKFrameScan, kKDupDepth, kKTilePass, kKTileExpand, kKPreprocess, kKBitonic, kKRender, kKPreCount, kKNormRange, kKNormDup, kKNormPass,
-  kKNormRanges, kKNum
+  kKNormRanges, kKRenderOrder, kKNum
 };
 const char* const kKernelNames[kKNum] = {
     "count_tiles",  "scan",       "duplicate_keys",     "tile_ranges",    "radix_pass",
     "frame_count",  "depth_sort", "scan_by_depth", "duplicate_by_depth", "tile_sort_pass",
     "tile_expand_pass", "preprocess", "bitonic_sort", "render", "preprocess_count", "norm_range",
-    "norm_duplicate", "norm_sort_pass", "norm_ranges"};
+    "norm_duplicate", "norm_sort_pass", "norm_ranges", "render_order"};
 
 // View table as stored in device memory (SoA, fixed maximum size).
 struct ViewBlob {
@@ -92,6 +93,8 @@ struct tdgs_context {
   Buffer f_rec3, f_conic;  // projected records and conics of tdgs_sort_frame_3d
   Buffer d_cams;           // cameras of the 3D calls (device)
   Buffer diag;             // barrier words of tdgs_diag_barrier_timeout
+  Buffer r_order;          // tile order of tdgs_render (heaviest first)
+  uint32_t render_wave = 0;  // rendering blocks resident at once (0: not queried yet)
   Proj3D proj{};           // 3D calls: the count kernel projects first
   bool proj_on = false;
   Buffer b_keys, b_vals;   // padded scratch of tdgs_sort_pairs_bitonic
@@ -479,7 +482,7 @@ void tdgs_context_destroy(tdgs_context* ctx) {
                     &ctx->n_offs,       &ctx->n_norm,       &ctx->n_keys[0],    &ctx->n_keys[1],
                     &ctx->n_vals[0],    &ctx->n_vals[1],    &ctx->n_ranges,
                     &ctx->f_rminmax,    &ctx->f_stream[0],   &ctx->f_stream[1],  &ctx->f_keys,
-                    &ctx->f_values,     &ctx->f_ranges};
+                    &ctx->f_values,     &ctx->f_ranges,     &ctx->r_order};
   if (ctx->d_views) cudaFree(ctx->d_views);
   if (ctx->h_views) cudaFreeHost(ctx->h_views);
   for (Buffer* b : bufs)
@@ -1136,10 +1139,24 @@ tdgs_status tdgs_render(tdgs_context* ctx, const tdgs_gaussian2d* records, const
   DeviceGuard dg(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const uint64_t tiles = static_cast<uint64_t>((f.width + 15) / 16) * ((f.height + 15) / 16);
+  if (tiles > 0x7fffffffull) return fail(ctx, TDGS_ERR_INVALID_ARGUMENT, "image too large");
+  const float4* rec4 = reinterpret_cast<const float4*>(records);
+  const float4* con4 = reinterpret_cast<const float4*>(conic_opacity);
+  const uint2* rg = reinterpret_cast<const uint2*>(ranges);
+  if (ctx->render_wave == 0) ctx->render_wave = render_wave_blocks(ctx->device);
+  if (tiles <= ctx->render_wave) {  // one wave: the order cannot shorten it
+    TDGS_TRACED(ctx, kKRender, tiles, s,
+                launch_render(rec4, con4, rgb, sorted_values, rg, f.width, f.height, background, n, image,
+                              err_word(ctx), s));
+    return TDGS_OK;
+  }
+  tdgs_status st = ensure(ctx, ctx->r_order, tiles * 4, s);
+  if (st != TDGS_OK) return st;
+  uint32_t* order = static_cast<uint32_t*>(ctx->r_order.p);
+  TDGS_TRACED(ctx, kKRenderOrder, tiles, s, launch_render_order(rg, static_cast<uint32_t>(tiles), order, s));
   TDGS_TRACED(ctx, kKRender, tiles, s,
-              launch_render(reinterpret_cast<const float4*>(records), reinterpret_cast<const float4*>(conic_opacity),
-                            rgb, sorted_values, reinterpret_cast<const uint2*>(ranges), f.width, f.height,
-                            background, n, image, err_word(ctx), s));
+              launch_render_ordered(rec4, con4, rgb, sorted_values, rg, order, f.width, f.height, background, n,
+                                    image, err_word(ctx), s));
   return TDGS_OK;
 }
 

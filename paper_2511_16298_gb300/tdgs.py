@@ -262,12 +262,13 @@ class Context:
     def kernel_times(self) -> dict:
         """{kernel: {"launches", "items", "ms"}} since the last read (waits
         for the recorded events)."""
-        buf = (_KernelTime * 16)()
-        n = lib().tdgs_context_kernel_times(self._h, buf, 16)
+        cap = 64  # more than the library's kernel kinds; the call clears the record
+        buf = (_KernelTime * cap)()
+        n = lib().tdgs_context_kernel_times(self._h, buf, cap)
         if n < 0:
             raise TdgsError(INVALID_ARGUMENT, "tdgs_context_kernel_times")
         return {buf[i].name.decode(): {"launches": int(buf[i].launches), "items": int(buf[i].items),
-                                       "ms": float(buf[i].total_ms)} for i in range(min(n, 16))}
+                                       "ms": float(buf[i].total_ms)} for i in range(min(n, cap))}
 
     def depth_passes(self) -> int:
         """Digit passes of the last single-launch depth sort (0 if none)."""

@@ -90,3 +90,50 @@ def test_render_scene_full_size(ctx, oracle):
     want, m_ref = oracle_image(oracle, sc, sc.cameras[0])
     assert m == m_ref
     compare(img.cpu().numpy(), want)
+
+
+def test_render_heaviest_first_path(ctx, oracle):
+    """An image with more tiles than one wave of resident blocks (3600 at
+    1280x720) takes the ordered path: a tile-order launch, then the blend;
+    a 640x360 image (920 tiles) renders in raster order without it.  Both
+    images match the oracle."""
+    sc = synth.scene3d(seed=6, n=40_000, views=2, scale0=0.05)
+    g, c, rgb = dev_scene(sc)
+    small = sc.cameras[1].copy()
+    small["width"], small["height"], small["cx"], small["cy"] = 640, 360, 320.0, 180.0
+    for cam, ordered in ((sc.cameras[0], True), (small, False)):
+        ctx.enable_timing(True)
+        img, m = ctx.render_frame_3d(g, c, rgb, cam, BG)
+        kt = ctx.kernel_times()
+        ctx.enable_timing(False)
+        assert kt["render"]["launches"] == 1
+        assert ("render_order" in kt) == ordered, kt.keys()
+        want, m_ref = oracle_image(oracle, sc, cam)
+        assert m == m_ref and m > 0
+        compare(img.cpu().numpy(), want)
+
+
+def test_render_ordered_empty_frame_is_background(ctx):
+    """Ordered path with every tile empty (the order kernel's all-zero
+    maximum): the image is the background."""
+    sc = synth.scene3d(seed=7, n=2000, views=1)
+    cam = sc.cameras[0].copy()
+    cam["trans"] = (0.0, 0.0, -1000.0)
+    g, c, rgb = dev_scene(sc)
+    img, m = ctx.render_frame_3d(g, c, rgb, cam, BG)
+    assert m == 0
+    assert torch.allclose(img, torch.tensor(BG, device=DEV).expand_as(img))
+
+
+def test_render_ordered_skewed_tiles(ctx, oracle):
+    """The scene pushed into the bottom-right corner of a 1280x720 image
+    (principal point there): a few heavy tiles, thousands of empty ones,
+    on the ordered path."""
+    sc = synth.scene3d(seed=8, n=20_000, views=1, scale0=0.05)
+    cam = sc.cameras[0].copy()
+    cam["cx"], cam["cy"] = 1200.0, 680.0  # principal point near the far corner
+    g, c, rgb = dev_scene(sc)
+    img, m = ctx.render_frame_3d(g, c, rgb, cam, BG)
+    want, m_ref = oracle_image(oracle, sc, cam)
+    assert m == m_ref and m > 0
+    compare(img.cpu().numpy(), want)
