@@ -19,9 +19,13 @@
 //    atomics and may differ between calls; no pixel depends on it.  Images
 //    whose tiles all fit in one wave render in raster order without it.
 //  * the staged conic is stored as (-a/2, -b, -c/2), so the exponent is
-//    dx (A dx + B dy) + C dy^2 in five operations, and the blend loop over
-//    the staged Gaussians is unrolled eight times (242 -> 231 us against
-//    four; two pixels per thread measured 243-265 us).
+//    dx (A dx + B dy) + C dy^2 in five operations; each staged Gaussian is
+//    two 16-byte shared-memory words, read with two loads per step; the
+//    blend loop is unrolled eight times (242 -> 231 us against four; two
+//    pixels per thread measured 243-265 us) and the launch bound asks for
+//    8 blocks per SM (32 registers).  A finished pixel keeps testing its
+//    flag each step: letting it run on with T = 0 instead made whole
+//    finished warps do every step's arithmetic (361 against 241 us).
 //
 // Per pixel (sample point = the pixel's integer coordinate), in float32
 // with CUDA's fast exponential and multiply-adds (the result is compared
@@ -88,15 +92,16 @@ __global__ void __launch_bounds__(kOrderThreads)
 }
 
 
-__global__ void __launch_bounds__(kRenderThreads)
+__global__ void __launch_bounds__(kRenderThreads, 2048 / kRenderThreads)
     k_render(const float4* __restrict__ rec, const float4* __restrict__ conic, const float* __restrict__ rgb,
              const uint32_t* __restrict__ values, const uint2* __restrict__ ranges,
              const uint32_t* __restrict__ order, uint32_t gx, uint32_t width,
              uint32_t height, float3 bg, uint32_t n, float* __restrict__ image, uint32_t* err) {
-  __shared__ float2 s_xy[kRenderThreads];
-  __shared__ float4 s_co[kRenderThreads];  // -a/2, -b, -c/2, opacity
+  // staged Gaussians, two 16-byte loads per step: (x, y, cut, -c/2) and
+  // (-a/2, -b, opacity, -); cut = the exponent below which alpha < 1/255
+  __shared__ float4 s_g0[kRenderThreads];
+  __shared__ float4 s_g1[kRenderThreads];
   __shared__ float s_rgb[kRenderThreads][3];
-  __shared__ float s_cut[kRenderThreads];  // exponent below which alpha < 1/255
   const uint32_t tile = order ? order[blockIdx.x] : blockIdx.x, t = threadIdx.x;
   const uint32_t px = (tile % gx) * 16 + (t & 15);
   const uint32_t py0 = (tile / gx) * 16 + (t >> 4);
@@ -123,18 +128,17 @@ __global__ void __launch_bounds__(kRenderThreads)
       uint32_t g = values[idx];
       if (g >= n) {  // not an index of this frame: skipped and reported
         bad = true;
-        s_co[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-        s_cut[t] = __int_as_float(0x7f800000);
-        s_xy[t] = make_float2(0.f, 0.f);
+        s_g0[t] = make_float4(0.f, 0.f, __int_as_float(0x7f800000), 0.f);
+        s_g1[t] = make_float4(0.f, 0.f, 0.f, 0.f);
         s_rgb[t][0] = s_rgb[t][1] = s_rgb[t][2] = 0.f;
       } else {
         const float4 q = __ldg(rec + g);
-        s_xy[t] = make_float2(q.x, q.y);
         const float4 c = __ldg(conic + g);
-        s_co[t] = make_float4(-0.5f * c.x, -c.y, -0.5f * c.z, c.w);
         // opacity * exp(power) < 1/255 exactly when power < -ln(255 opacity):
         // far pixels skip the exponential (the 1/255 test below stays)
-        s_cut[t] = c.w > 0.0f ? -__logf(255.0f * c.w) : __int_as_float(0x7f800000);
+        const float cut = c.w > 0.0f ? -__logf(255.0f * c.w) : __int_as_float(0x7f800000);
+        s_g0[t] = make_float4(q.x, q.y, cut, -0.5f * c.z);
+        s_g1[t] = make_float4(-0.5f * c.x, -c.y, c.w, 0.f);
         s_rgb[t][0] = __ldg(rgb + 3 * static_cast<size_t>(g));
         s_rgb[t][1] = __ldg(rgb + 3 * static_cast<size_t>(g) + 1);
         s_rgb[t][2] = __ldg(rgb + 3 * static_cast<size_t>(g) + 2);
@@ -144,17 +148,16 @@ __global__ void __launch_bounds__(kRenderThreads)
     const uint32_t cnt = min(static_cast<uint32_t>(kRenderThreads), r.y - b);
 #pragma unroll 8
     for (uint32_t j = 0; j < cnt; ++j) {
-      const float2 xy = s_xy[j];
-      const float4 co = s_co[j];
-      const float cut = s_cut[j];
-      const float dx = xy.x - fx;
+      const float4 g0 = s_g0[j];
+      const float4 g1 = s_g1[j];
+      const float dx = g0.x - fx;
 #pragma unroll
       for (int k = 0; k < kPix; ++k) {
         if (done[k]) continue;
-        const float dy = xy.y - fy[k];
-        const float power = fmaf(dx, fmaf(co.x, dx, co.y * dy), co.z * dy * dy);
-        if (power > 0.0f || power < cut) continue;
-        const float alpha = fminf(0.99f, co.w * __expf(power));
+        const float dy = g0.y - fy[k];
+        const float power = fmaf(dx, fmaf(g1.x, dx, g1.y * dy), g0.w * dy * dy);
+        if (power > 0.0f || power < g0.z) continue;
+        const float alpha = fminf(0.99f, g1.z * __expf(power));
         if (alpha < 1.0f / 255.0f) continue;
         const float test_t = T[k] * (1.0f - alpha);
         if (test_t < 0.0001f) {
