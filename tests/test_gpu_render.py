@@ -137,3 +137,45 @@ def test_render_ordered_skewed_tiles(ctx, oracle):
     want, m_ref = oracle_image(oracle, sc, cam)
     assert m == m_ref and m > 0
     compare(img.cpu().numpy(), want)
+
+
+def test_render_4k_image(ctx, oracle):
+    """3840x2160 (32,400 tiles): the tile-order kernel's block loops over
+    many tiles per thread."""
+    sc = synth.scene3d(seed=9, n=20_000, views=1, width=3840, height=2160, scale0=0.05)
+    cam = sc.cameras[0].copy()
+    cam["fx"], cam["fy"] = 3325.5, 3325.5
+    g, c, rgb = dev_scene(sc)
+    img, m = ctx.render_frame_3d(g, c, rgb, cam, BG)
+    want, m_ref = oracle_image(oracle, sc, cam)
+    assert m == m_ref and m > 0
+    compare(img.cpu().numpy(), want)
+
+
+def test_render_inverted_ranges_are_empty(ctx, oracle):
+    """A range whose start is past its end holds no Gaussians, on the GPU
+    as in the oracle's loop; inverted here: every seventh tile and the
+    heaviest one (the first in heaviest-first order)."""
+    sc = synth.scene3d(seed=10, n=30_000, views=1, scale0=0.05)
+    cam = sc.cameras[0]
+    g, c, rgb = dev_scene(sc)
+    k, v, r, m, rec, con = ctx.sort_frame_3d(g, c, cam, copy=True)
+    rr = r.cpu().numpy().view(np.uint32).copy()
+    lens = rr[:, 1].astype(np.int64) - rr[:, 0]
+    flip = np.zeros(len(rr), dtype=bool)
+    flip[::7] = True
+    flip[int(np.argmax(lens))] = True
+    flip &= lens > 0
+    assert flip.sum() > 10
+    rr[flip] = rr[flip][:, ::-1]
+    W, H = int(cam["width"]), int(cam["height"])
+    r2 = torch.from_numpy(rr.view(np.int32)).to(DEV)
+    img = ctx.render(rec, con, rgb, v, r2, W, H, BG)
+    rec_h = rec.cpu().numpy().view(synth.GAUSSIAN2D).reshape(-1)
+    st, want = oracle.render(rec_h, con.cpu().numpy(), sc.rgb, v.cpu().numpy().view(np.uint32), rr, W, H, BG)
+    assert st == 0
+    compare(img.cpu().numpy(), want)
+    gx = (W + 15) // 16
+    t = int(np.argmax(lens))
+    tile = img[(t // gx) * 16:(t // gx) * 16 + 16, (t % gx) * 16:(t % gx) * 16 + 16].cpu()
+    assert torch.allclose(tile, torch.tensor(BG).expand_as(tile))
