@@ -350,7 +350,8 @@ tdgs_status tdgs_sort_frame_normalized(tdgs_context* ctx, const tdgs_gaussian2d*
                                        const tdgs_range** ranges, uint32_t* m_out, void* stream);
 
 /* Rendering (Sec. II-A "Rendering"; Sec. IV-C: one 16x16 tile per thread
- * block; one pixel per thread here).  Each pixel blends its tile's Gaussians
+ * block; one pixel per thread here, exponent coefficients staged in shared
+ * memory).  Each pixel blends its tile's Gaussians
  * sorted_values[ranges[t].start .. ranges[t].end) front to back; the
  * paper prints no formulas, the library applies the compositing of 3D
  * Gaussian splatting in float32 (multiply-adds may be fused, exp is CUDA's
@@ -365,7 +366,14 @@ tdgs_status tdgs_sort_frame_normalized(tdgs_context* ctx, const tdgs_gaussian2d*
  * (as tdgs_sort_frame returns them; sorted_values may be NULL when every
  * range is empty): device.  background: 3 HOST floats.
  * image: device, height x width x 3 floats (interleaved RGB, row-major).
- * A sorted value >= n is skipped and latches TDGS_ERR_INVALID_ARGUMENT. */
+ * A sorted value >= n is skipped and latches TDGS_ERR_INVALID_ARGUMENT; a
+ * range whose start is not below its end is an empty tile.
+ * Scheduling: when the image has more tiles than one wave of resident
+ * rendering blocks, a one-block kernel first orders the tiles by Gaussian
+ * count (heaviest first, 64 buckets) into a context-owned buffer of 4 B
+ * per tile, which the first such call allocates (draining the stream), and
+ * block b renders the b-th tile of that order; otherwise the tiles render
+ * in raster order with one launch.  No pixel depends on the order. */
 tdgs_status tdgs_render(tdgs_context* ctx, const tdgs_gaussian2d* records, const float* conic_opacity,
                         const float* rgb, uint32_t n, const uint32_t* sorted_values, const tdgs_range* ranges,
                         tdgs_frame f, const float* background, float* image, void* stream);
