@@ -48,6 +48,7 @@ constexpr int kRenderThreads = 256 / kPix;      // one 16x16 tile per block
 constexpr int kRowStep = kRenderThreads / 16;   // rows between a thread's pixels
 constexpr int kOrderThreads = 1024;             // the tile-order kernel's one block
 constexpr uint32_t kOrderBuckets = 64;          // Gaussian-count buckets, heaviest first
+static_assert(kOrderBuckets == 64, "the bucket scan takes two counts per lane of one warp");
 
 __device__ __forceinline__ uint32_t tile_len(uint2 r) { return r.y > r.x ? r.y - r.x : 0u; }
 
