@@ -135,9 +135,15 @@ tdgs_status tdgs_context_set_sort_variant(tdgs_context* ctx, int variant);
  *                              over the tile bits (built-in: 8)
  *   TDGS_TUNE_CTAS_PER_SM      CTAs per SM of the persistent radix grids
  *                              (capped by occupancy)
- *   TDGS_TUNE_DEPTH_DIGIT_BITS digit width of the frame's depth sort: 8
- *                              (4 passes, the built-in choice) or 11
- *                              (3 passes) */
+ *   TDGS_TUNE_DEPTH_DIGIT_BITS digit width of the frame's depth sort when
+ *                              it runs as one launch per pass (frames or
+ *                              batches above the single-launch sort's
+ *                              capacity, one 8192-key tile per resident
+ *                              CTA: about 1.25M Gaussians on 152 SMs):
+ *                              8 (4 passes, the built-in choice) or 11
+ *                              (3 passes).  The single-launch sort below
+ *                              that capacity always takes 9-bit digits and
+ *                              only the passes the depth range needs. */
 enum {
   TDGS_TUNE_SORT_VARIANT = 0,
   TDGS_TUNE_TILE_DIGIT_BITS = 1,
