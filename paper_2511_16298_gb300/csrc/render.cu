@@ -9,7 +9,7 @@
 // tiles with many Gaussians set the kernel's end and more threads per tile
 // finish them sooner; kPix stays a compile-time choice.
 //
-// Two further measures on that frame (0.32 -> 0.24 ms together):
+// Further measures on that frame (0.32 -> 0.22 ms together):
 //  * tiles run heaviest first when they take more than one wave of
 //    resident blocks.  A one-block kernel buckets the tiles by their
 //    Gaussian count (64 buckets, descending) and block b renders the b-th
@@ -22,10 +22,19 @@
 //    dx (A dx + B dy) + C dy^2 in five operations; each staged Gaussian is
 //    two 16-byte shared-memory words, read with two loads per step; the
 //    blend loop is unrolled eight times (242 -> 231 us against four; two
-//    pixels per thread measured 243-265 us) and the launch bound asks for
-//    8 blocks per SM (32 registers).  A finished pixel keeps testing its
-//    flag each step: letting it run on with T = 0 instead made whole
-//    finished warps do every step's arithmetic (361 against 241 us).
+//    pixels per thread measured 243-265 us).  A finished pixel keeps
+//    testing its flag each step: letting it run on with T = 0 instead made
+//    whole finished warps do every step's arithmetic (361 against 241 us).
+//  * row culling per warp: a Gaussian reaches a pixel only inside the
+//    ellipse where power >= cut, so when it is staged, its thread marks
+//    the warps (row pairs of the tile) the ellipse can reach, with a
+//    margin; each warp then blends only the list of staged Gaussians that
+//    reach it, kept in front-to-back order by one ballot per 32.  What a
+//    warp skips is what its pixels' own cut test would have skipped, so
+//    the image is unchanged (a probe: 220 -> 198 us; here the kernel
+//    takes 39 registers, 6 blocks per SM, and a render call 0.234 ->
+//    0.217 ms).  Asking for 8 blocks per SM (32 registers) spills and
+//    loses most of the gain.
 //
 // Per pixel (sample point = the pixel's integer coordinate), in float32
 // with CUDA's fast exponential and multiply-adds (the result is compared
@@ -50,7 +59,46 @@ constexpr int kOrderThreads = 1024;             // the tile-order kernel's one b
 constexpr uint32_t kOrderBuckets = 64;          // Gaussian-count buckets, heaviest first
 static_assert(kOrderBuckets == 64, "the bucket scan takes two counts per lane of one warp");
 
+constexpr int kRenderWarps = kRenderThreads / 32;
+static_assert(kRenderWarps <= 8, "one bit per warp in an 8-bit mask");
+
 __device__ __forceinline__ uint32_t tile_len(uint2 r) { return r.y > r.x ? r.y - r.x : 0u; }
+
+// Warps of the tile a staged Gaussian can reach (bit w: warp w, whose
+// pixels sit on rows 2w, 2w+1 (+ kRowStep k) of the tile).  A pixel passes
+// the cut test only inside the ellipse d^T Q d <= K, K = -2 cut, where
+// Q = [[a, b], [b, c]] is the conic; its squared half-extents are
+// K a / det in y and K c / det in x (det = ac - b^2).  A warp is left out
+// when all its rows lie farther from the mean than 1.01 half-extents plus
+// one pixel (tested on squares), and every warp when the columns of the
+// tile do.  det comes from one fused multiply-add (relative error below
+// 6e-5 when det > 1e-3 ac, far inside the margin); flatter conics, Q not
+// positive definite, or anything not finite reach every warp.  K < 0: no
+// pixel passes the cut test (no warp).
+__device__ __forceinline__ uint32_t warp_mask(float mx, float my, float4 c, float cut, float tx0, float ty0) {
+  const float K = -2.0f * cut;
+  if (K < 0.0f) return 0u;
+  const uint32_t all = (1u << kRenderWarps) - 1u;
+  const float ac = c.x * c.z;
+  const float det = fmaf(-c.y, c.y, ac);
+  if (!(c.x > 0.0f && c.z > 0.0f && det > 1e-3f * ac && K < 1e30f)) return all;
+  const float hy2 = __fdividef(K * c.x, det) * 1.0201f;
+  const float hx2 = __fdividef(K * c.z, det) * 1.0201f;
+  if (!(hy2 < 1e30f && hx2 < 1e30f)) return all;
+  const float ex = fmaxf(fmaxf(tx0 - mx, mx - (tx0 + 15.0f)) - 1.0f, 0.0f);
+  if (ex * ex > hx2) return 0u;
+  const float yr = my - ty0;  // the mean's row inside the tile
+  uint32_t m = 0;
+#pragma unroll
+  for (int w = 0; w < kRenderWarps; ++w)
+#pragma unroll
+    for (int k = 0; k < kPix; ++k) {
+      const float r0 = static_cast<float>(2 * w + kRowStep * k);
+      const float ey = fmaxf(fmaxf(r0 - yr, yr - (r0 + 1.0f)) - 1.0f, 0.0f);
+      if (ey * ey <= hy2) m |= 1u << w;
+    }
+  return m;
+}
 
 // order[0 .. tiles) = every tile once, by descending bucket of its
 // Gaussian count: bucket = (max - len) * 63 / max (0 when every tile is
@@ -93,7 +141,7 @@ __global__ void __launch_bounds__(kOrderThreads)
 }
 
 
-__global__ void __launch_bounds__(kRenderThreads, 2048 / kRenderThreads)
+__global__ void __launch_bounds__(kRenderThreads)
     k_render(const float4* __restrict__ rec, const float4* __restrict__ conic, const float* __restrict__ rgb,
              const uint32_t* __restrict__ values, const uint2* __restrict__ ranges,
              const uint32_t* __restrict__ order, uint32_t gx, uint32_t width,
@@ -103,10 +151,13 @@ __global__ void __launch_bounds__(kRenderThreads, 2048 / kRenderThreads)
   __shared__ float4 s_g0[kRenderThreads];
   __shared__ float4 s_g1[kRenderThreads];
   __shared__ float s_rgb[kRenderThreads][3];
+  __shared__ uint8_t s_mask[kRenderThreads];                 // warps each staged Gaussian reaches
+  __shared__ uint8_t s_list[kRenderWarps][kRenderThreads];  // per warp: staged Gaussians to blend
   const uint32_t tile = order ? order[blockIdx.x] : blockIdx.x, t = threadIdx.x;
   const uint32_t px = (tile % gx) * 16 + (t & 15);
   const uint32_t py0 = (tile / gx) * 16 + (t >> 4);
   const float fx = __uint2float_rn(px);
+  const uint32_t warp = t >> 5, lane = t & 31;
   float fy[kPix], T[kPix], C[kPix][3];
   bool done[kPix];
 #pragma unroll
@@ -131,6 +182,7 @@ __global__ void __launch_bounds__(kRenderThreads, 2048 / kRenderThreads)
         bad = true;
         s_g0[t] = make_float4(0.f, 0.f, __int_as_float(0x7f800000), 0.f);
         s_g1[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        s_mask[t] = 0;
         s_rgb[t][0] = s_rgb[t][1] = s_rgb[t][2] = 0.f;
       } else {
         const float4 q = __ldg(rec + g);
@@ -140,6 +192,8 @@ __global__ void __launch_bounds__(kRenderThreads, 2048 / kRenderThreads)
         const float cut = c.w > 0.0f ? -__logf(255.0f * c.w) : __int_as_float(0x7f800000);
         s_g0[t] = make_float4(q.x, q.y, cut, -0.5f * c.z);
         s_g1[t] = make_float4(-0.5f * c.x, -c.y, c.w, 0.f);
+        s_mask[t] = static_cast<uint8_t>(
+            warp_mask(q.x, q.y, c, cut, __uint2float_rn((tile % gx) * 16), __uint2float_rn((tile / gx) * 16)));
         s_rgb[t][0] = __ldg(rgb + 3 * static_cast<size_t>(g));
         s_rgb[t][1] = __ldg(rgb + 3 * static_cast<size_t>(g) + 1);
         s_rgb[t][2] = __ldg(rgb + 3 * static_cast<size_t>(g) + 2);
@@ -147,8 +201,20 @@ __global__ void __launch_bounds__(kRenderThreads, 2048 / kRenderThreads)
     }
     __syncthreads();
     const uint32_t cnt = min(static_cast<uint32_t>(kRenderThreads), r.y - b);
+    // this warp's list of the staged Gaussians that can reach its rows
+    uint32_t nw = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < kRenderThreads / 32; ++k) {
+      const uint32_t e = k * 32 + lane;
+      const bool hit = e < cnt && ((s_mask[e] >> warp) & 1u);
+      const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+      if (hit) s_list[warp][nw + __popc(bal & ((1u << lane) - 1u))] = static_cast<uint8_t>(e);
+      nw += __popc(bal);
+    }
+    __syncwarp();
 #pragma unroll 8
-    for (uint32_t j = 0; j < cnt; ++j) {
+    for (uint32_t jj = 0; jj < nw; ++jj) {
+      const uint32_t j = s_list[warp][jj];
       const float4 g0 = s_g0[j];
       const float4 g1 = s_g1[j];
       const float dx = g0.x - fx;

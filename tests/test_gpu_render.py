@@ -95,12 +95,12 @@ def test_render_scene_full_size(ctx, oracle):
 def test_render_heaviest_first_path(ctx, oracle):
     """An image with more tiles than one wave of resident blocks (3600 at
     1280x720) takes the ordered path: a tile-order launch, then the blend;
-    a 640x360 image (920 tiles) renders in raster order without it.  Both
-    images match the oracle."""
+    a 320x180 image (240 tiles, fewer than two blocks per SM) renders in
+    raster order without it.  Both images match the oracle."""
     sc = synth.scene3d(seed=6, n=40_000, views=2, scale0=0.05)
     g, c, rgb = dev_scene(sc)
     small = sc.cameras[1].copy()
-    small["width"], small["height"], small["cx"], small["cy"] = 640, 360, 320.0, 180.0
+    small["width"], small["height"], small["cx"], small["cy"] = 320, 180, 160.0, 90.0
     for cam, ordered in ((sc.cameras[0], True), (small, False)):
         ctx.enable_timing(True)
         img, m = ctx.render_frame_3d(g, c, rgb, cam, BG)
