@@ -357,7 +357,8 @@ tdgs_status tdgs_sort_frame_normalized(tdgs_context* ctx, const tdgs_gaussian2d*
 
 /* Rendering (Sec. II-A "Rendering"; Sec. IV-C: one 16x16 tile per thread
  * block; one pixel per thread here, exponent coefficients staged in shared
- * memory).  Each pixel blends its tile's Gaussians
+ * memory, and each warp skips the staged Gaussians whose cut-off ellipse
+ * cannot reach its rows, which leaves every pixel unchanged).  Each pixel blends its tile's Gaussians
  * sorted_values[ranges[t].start .. ranges[t].end) front to back; the
  * paper prints no formulas, the library applies the compositing of 3D
  * Gaussian splatting in float32 (multiply-adds may be fused, exp is CUDA's
