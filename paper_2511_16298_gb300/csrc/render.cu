@@ -9,7 +9,7 @@
 // tiles with many Gaussians set the kernel's end and more threads per tile
 // finish them sooner; kPix stays a compile-time choice.
 //
-// Further measures on that frame (0.32 -> 0.22 ms together):
+// Further measures on that frame (0.32 -> 0.21 ms together):
 //  * tiles run heaviest first when they take more than one wave of
 //    resident blocks.  A one-block kernel buckets the tiles by their
 //    Gaussian count (64 buckets, descending) and block b renders the b-th
@@ -33,8 +33,9 @@
 //    warp skips is what its pixels' own cut test would have skipped, so
 //    the image is unchanged (a probe: 220 -> 198 us; here the kernel
 //    takes 39 registers, 6 blocks per SM, and a render call 0.234 ->
-//    0.217 ms).  Asking for 8 blocks per SM (32 registers) spills and
-//    loses most of the gain.
+//    0.217 ms, 0.208 ms with the quarter-pixel margin of warp_mask
+//    instead of one pixel).  Asking for 8 blocks per SM (32 registers)
+//    spills and loses most of the gain.
 //
 // Per pixel (sample point = the pixel's integer coordinate), in float32
 // with CUDA's fast exponential and multiply-adds (the result is compared
@@ -70,11 +71,13 @@ __device__ __forceinline__ uint32_t tile_len(uint2 r) { return r.y > r.x ? r.y -
 // Q = [[a, b], [b, c]] is the conic; its squared half-extents are
 // K a / det in y and K c / det in x (det = ac - b^2).  A warp is left out
 // when all its rows lie farther from the mean than 1.01 half-extents plus
-// one pixel (tested on squares), and every warp when the columns of the
-// tile do.  det comes from one fused multiply-add (relative error below
-// 6e-5 when det > 1e-3 ac, far inside the margin); flatter conics, Q not
-// positive definite, or anything not finite reach every warp.  K < 0: no
-// pixel passes the cut test (no warp).
+// a quarter pixel (tested on squares), and every warp when the columns of
+// the tile do.  det comes from one fused multiply-add (relative error
+// below 6e-5 when det > 1e-3 ac, inside the 1 %); with |cut| <= ln 255 and
+// the terms of the exponent below sqrt(ac / det) K, float rounding moves
+// the cut boundary by about 1e-3 pixel at most, inside the quarter pixel.
+// Flatter conics, Q not positive definite, or anything not finite reach
+// every warp.  K < 0: no pixel passes the cut test (no warp).
 __device__ __forceinline__ uint32_t warp_mask(float mx, float my, float4 c, float cut, float tx0, float ty0) {
   const float K = -2.0f * cut;
   if (K < 0.0f) return 0u;
@@ -85,7 +88,7 @@ __device__ __forceinline__ uint32_t warp_mask(float mx, float my, float4 c, floa
   const float hy2 = __fdividef(K * c.x, det) * 1.0201f;
   const float hx2 = __fdividef(K * c.z, det) * 1.0201f;
   if (!(hy2 < 1e30f && hx2 < 1e30f)) return all;
-  const float ex = fmaxf(fmaxf(tx0 - mx, mx - (tx0 + 15.0f)) - 1.0f, 0.0f);
+  const float ex = fmaxf(fmaxf(tx0 - mx, mx - (tx0 + 15.0f)) - 0.25f, 0.0f);
   if (ex * ex > hx2) return 0u;
   const float yr = my - ty0;  // the mean's row inside the tile
   uint32_t m = 0;
@@ -94,7 +97,7 @@ __device__ __forceinline__ uint32_t warp_mask(float mx, float my, float4 c, floa
 #pragma unroll
     for (int k = 0; k < kPix; ++k) {
       const float r0 = static_cast<float>(2 * w + kRowStep * k);
-      const float ey = fmaxf(fmaxf(r0 - yr, yr - (r0 + 1.0f)) - 1.0f, 0.0f);
+      const float ey = fmaxf(fmaxf(r0 - yr, yr - (r0 + 1.0f)) - 0.25f, 0.0f);
       if (ey * ey <= hy2) m |= 1u << w;
     }
   return m;
