@@ -45,12 +45,12 @@ def oracle_image(oracle, sc, cam):
     return img, ref["m"]
 
 
-def compare(got, want):
+def compare(got, want, frac=1e-3, mean=1e-6):
     d = np.abs(got.astype(np.float64) - want.astype(np.float64))
     assert d.max() <= 0.02, d.max()
     per_px = d.max(axis=2)
-    assert np.mean(per_px > 1e-4) <= 1e-3, np.mean(per_px > 1e-4)
-    assert d.mean() < 1e-6, d.mean()
+    assert np.mean(per_px > 1e-4) <= frac, np.mean(per_px > 1e-4)
+    assert d.mean() < mean, d.mean()
 
 
 @pytest.mark.parametrize("view", [0, 1, 2, 5])
@@ -179,3 +179,69 @@ def test_render_inverted_ranges_are_empty(ctx, oracle):
     t = int(np.argmax(lens))
     tile = img[(t // gx) * 16:(t // gx) * 16 + 16, (t % gx) * 16:(t % gx) * 16 + 16].cpu()
     assert torch.allclose(tile, torch.tensor(BG).expand_as(tile))
+
+
+def extreme_conics(seed, n, W, H):
+    """Records and conics built directly (no projection): 2D covariances
+    with axis ratios from 1 to 3000 at random angles (so det / ac runs
+    from 1 down to about 1e-6, on both sides of the culling's 1e-3
+    threshold), scales from 0.3 to 12 pixels, opacities from 0.02 to 0.6
+    with one in twenty below 1/255 (no pixel passes) and 3 % of the conics
+    indefinite (b^2 > ac, which reach every warp; their rectangles capped
+    at 12 pixels).  Sparse enough that most pixels do not saturate."""
+    rng = np.random.default_rng(seed)
+    s1 = np.exp(rng.uniform(np.log(0.3), np.log(12.0), n))
+    ratio = np.exp(rng.uniform(0.0, np.log(3000.0), n))
+    s2 = np.minimum(s1 * ratio, 120.0)
+    th = rng.uniform(0.0, np.pi, n)
+    cs, sn = np.cos(th), np.sin(th)
+    # Q = R diag(1/s1^2, 1/s2^2) R^T in float64, rounded to float32
+    i1, i2 = 1.0 / s1 ** 2, 1.0 / s2 ** 2
+    a = cs * cs * i1 + sn * sn * i2
+    b = cs * sn * (i1 - i2)
+    c = sn * sn * i1 + cs * cs * i2
+    bad = rng.random(n) < 0.03
+    b = np.where(bad, np.sqrt(a * c) * rng.uniform(1.01, 3.0, n), b)
+    op = np.where(rng.random(n) < 0.05, rng.uniform(0.002, 0.0039, n), rng.uniform(0.02, 0.6, n))
+    con = np.stack([a, b, c, op], 1).astype(np.float32)
+    rec = np.zeros(n, dtype=synth.GAUSSIAN2D)
+    rec["x"] = rng.uniform(-20.0, W + 20.0, n).astype(np.float32)
+    rec["y"] = rng.uniform(-20.0, H + 20.0, n).astype(np.float32)
+    rec["depth"] = rng.uniform(0.5, 50.0, n).astype(np.float32)
+    rad = np.ceil(3.0 * np.maximum(s1, s2))
+    rec["radius"] = np.where(bad, np.minimum(rad, 12), np.minimum(rad, 360)).astype(np.int32)
+    rgb = rng.random((n, 3)).astype(np.float32)
+    return rec, con, rgb
+
+
+@pytest.mark.parametrize("W,H", [(1280, 720), (320, 180)])
+def test_render_extreme_conics(ctx, oracle, W, H):
+    """Elongated, near-singular and indefinite conics and tiny opacities,
+    on the ordered (1280x720) and raster-order (320x180) paths: the
+    per-warp culling must leave every pixel as the oracle's blend has it.
+    Each side sorts the records itself (compared first) and renders with
+    its own lists.
+
+    Bar: max |d| <= 0.02 as everywhere (a Gaussian culled wrongly would
+    move a pixel by up to alpha * colour), but up to 1 % of pixels above
+    1e-4 and a mean below 1e-5: with axis ratios up to 3000 the exponent's
+    terms nearly cancel, and the kernel's fused form dx (A dx + B dy) +
+    C dy^2 rounds differently from the oracle's written order.  A CPU
+    blend with the kernel's form, float32 exp and no culling differs from
+    the oracle on 0.16 % (1280x720) and 0.12 % (320x180) of pixels, mean
+    1.8e-6 and 1.2e-6."""
+    rec, con, rgb = extreme_conics(11, 3000 if W > 640 else 800, W, H)
+    g = tdgs_records(rec)
+    k, v, r, m = ctx.sort_frame(g, W, H, copy=True)
+    ref = oracle.sort_frame(rec, W, H)
+    assert ref["status"] == 0 and m == ref["m"] > 0
+    assert np.array_equal(v.cpu().numpy().view(np.uint32), ref["values"])
+    assert np.array_equal(r.cpu().numpy().view(np.uint32).reshape(-1), ref["ranges"].reshape(-1))
+    img = ctx.render(g, torch.from_numpy(con).to(DEV), torch.from_numpy(rgb).to(DEV), v, r, W, H, BG)
+    st, want = oracle.render(rec, con, rgb, ref["values"], ref["ranges"], W, H, BG)
+    assert st == 0
+    compare(img.cpu().numpy(), want, frac=1e-2, mean=1e-5)
+
+
+def tdgs_records(rec):
+    return torch.from_numpy(np.ascontiguousarray(rec).view(np.int32).reshape(-1, 4).copy()).to(DEV)
