@@ -68,6 +68,12 @@ MUTANTS = {
 }
 
 
+def test_unmutated_oracle_passes_every_pin(oracle):
+    """A mutant counts as caught only if the real oracle passes the same pins."""
+    from tests import oracle_pins as P
+    assert P.run_all(oracle) == []
+
+
 @pytest.fixture(scope="module")
 def src_text():
     return open(SRC).read()

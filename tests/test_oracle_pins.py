@@ -42,3 +42,18 @@ def test_float_bit_order():
 ])
 def test_frame_invariants(oracle, make):
     P.check_frame_invariants(oracle, [make()])
+
+
+def test_preprocess_pins(oracle):
+    """Projection and footprint (Sec. II-A "Preprocessing"; Tables I and IV)."""
+    P.check_preprocess(oracle)
+
+
+def test_render_pins(oracle):
+    """Front-to-back blending (Sec. II-A "Rendering"; Sec. IV-C)."""
+    P.check_render(oracle)
+
+
+def test_normalized_pins(oracle):
+    """The 32-bit tile/depth key (Sec. IV-B)."""
+    P.check_normalized(oracle)
