@@ -399,10 +399,11 @@ tdgs_status tdgs_diag_barrier_timeout(tdgs_context* ctx, void* stream);
 /* ------------------------------------------------- scan without allocation */
 
 /* The exclusive scan of tdgs_scan (offsets, total, 64-bit overflow check)
- * for callers that cannot allocate device memory: code running while a CUDA
- * graph is captured, real-time loops that must never reach the device
- * allocator, or plugins whose device memory belongs to a host application.
- * The paper has no counterpart; it is a deployment convenience.
+ * for callers that cannot allocate device memory: real-time loops that
+ * must never reach the device allocator (an allocation can block or
+ * synchronise the device), or plugins whose device memory belongs to a
+ * host application that does not let them allocate.  The paper has no
+ * counterpart; it is a deployment convenience.
  *
  * It needs no context and allocates nothing (no cudaMalloc, cudaFree or
  * allocating library call).  Its scratch -- look-back status words, the
@@ -410,14 +411,17 @@ tdgs_status tdgs_diag_barrier_timeout(tdgs_context* ctx, void* stream);
  * the library's device memory, present on every GPU that loads the library
  * until the process exits.  Limits and behaviour:
  *   - n <= 16,777,216 counts; a larger n returns TDGS_ERR_INVALID_ARGUMENT.
- *   - The first call on a device looks up the array's address on that
- *     device (make that first call before any stream capture).
- *   - Every call on a device shares the array: calls whose GPU work
- *     overlaps (different streams, or threads without ordering) race and
- *     give wrong results.  Order them on one stream.
+ *   - The first call in each CUDA context (normally once per device: the
+ *     device's primary context) looks up the array's address in that
+ *     context; make that first call before any stream capture.
+ *   - Every call shares the array, which keeps the last call's contents;
+ *     each call clears the words it uses on `stream` before its kernel.
+ *     Calls whose GPU work overlaps (different streams, or threads without
+ *     ordering) race and give wrong results.  Order them on one stream.
  *   - total_dev (may be NULL) receives the sum, 0xFFFFFFFF on overflow;
  *     error_dev (may be NULL) receives 0 or the error the GPU detected
  *     (TDGS_ERR_OVERFLOW, or TDGS_ERR_TIMEOUT from a bounded wait).
+ *   - n == 0 writes total 0 and error 0 and launches no scan kernel.
  * counts, offsets, total_dev, error_dev: device pointers, 4-byte aligned. */
 tdgs_status tdgs_scan_noalloc(const uint32_t* counts, uint32_t n, uint32_t* offsets,
                               uint32_t* total_dev, uint32_t* error_dev, void* stream);

@@ -1,10 +1,12 @@
 // tdgs_scan_noalloc: the exclusive scan of tdgs_scan for callers that
-// cannot allocate device memory -- for example code that runs while a CUDA
-// graph is being captured, real-time loops that must never hit the device
-// allocator (which can block or synchronise), or plugins whose device memory
-// belongs to a host application.  Its scratch (look-back status words, the
-// tile ticket and the error word) lives in one file-scope device array of
-// fixed size instead of context-owned buffers.
+// cannot allocate device memory -- real-time loops that must never reach
+// the device allocator (an allocation can block or synchronise the
+// device), or plugins whose device memory belongs to a host application
+// that does not let them allocate.  Its scratch (look-back status words,
+// the tile ticket and the error word) lives in one file-scope device array
+// of fixed size instead of context-owned buffers.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "tdgs_internal.cuh"
@@ -21,28 +23,84 @@ struct NoAllocScratch {
   uint64_t status[kNoAllocTiles];   // one look-back word per 8192-count tile
 };
 
-// Shared by every call on a device and kept between calls (about 16 KB per
-// device, held until the process exits).
+// Shared by every call in a context and kept between calls (about 16 KB
+// per device, held until the process exits).
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
-// Host code must not use g_noalloc_scratch as an address: the device
-// address is looked up once per device with that device current.
+// Host code must not use g_noalloc_scratch as an address: in host code the
+// name is a host-side stand-in.  The device address belongs to the CUDA
+// context that loaded the module, so it is looked up with cudaGetSymbolAddress
+// in the current context and cached by that context's unique id (a context
+// made current by a host application, or one created after
+// cudaDeviceReset, gets its own lookup).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+struct DriverFns {
+  CtxGetCurrentFn get_current = nullptr;
+  CtxGetIdFn get_id = nullptr;
+};
+
+const DriverFns& driver_fns() {
+  static const DriverFns fns = [] {
+    DriverFns f;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      f.get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      f.get_id = reinterpret_cast<CtxGetIdFn>(p);
+    cudaGetLastError();
+    return f;
+  }();
+  return fns;
+}
+
+// The unique id of the current context, or 0 if there is none or it
+// cannot be read.
+unsigned long long current_context_id() {
+  const DriverFns& f = driver_fns();
+  if (!f.get_current || !f.get_id) return 0;
+  CUcontext c = nullptr;
+  if (f.get_current(&c) != CUDA_SUCCESS || !c) return 0;
+  unsigned long long id = 0;
+  if (f.get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+struct CacheEntry {
+  unsigned long long ctx_id;
+  NoAllocScratch* addr;
+};
+constexpr int kCacheEntries = 64;
 std::mutex g_mu;
-NoAllocScratch* g_addr[64] = {};
+CacheEntry g_cache[kCacheEntries] = {};
+int g_cache_next = 0;
 
 cudaError_t scratch_address(NoAllocScratch** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  const unsigned long long id = current_context_id();
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = static_cast<NoAllocScratch*>(p);
+  if (id) {
+    for (const CacheEntry& c : g_cache)
+      if (c.ctx_id == id) {
+        *out = c.addr;
+        return cudaSuccess;
+      }
   }
-  *out = g_addr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<NoAllocScratch*>(p);
+  // The lookup may have made the device's primary context current; cache
+  // under the id of the context the address was taken in.
+  const unsigned long long id_after = id ? id : current_context_id();
+  if (id_after) {
+    g_cache[g_cache_next] = CacheEntry{id_after, *out};
+    g_cache_next = (g_cache_next + 1) % kCacheEntries;
+  }
   return cudaSuccess;
 }
 

@@ -131,7 +131,7 @@ cudaError_t launch_count_tiles(const float4* g, uint32_t n, FrameGeom fg, uint32
 
 // Decoupled look-back exclusive scan.  With recs != nullptr the counts are
 // computed from the records (count and scan fused); otherwise read from
-// counts.  status: one uint64 per 2048-item block, zeroed by the caller.
+// counts.  status: one uint64 per kScanTileItems (8192) counts, zeroed by the caller.
 constexpr uint32_t kScanTileItems = 8192;
 cudaError_t launch_scan(const uint32_t* counts, const float4* recs, const uint32_t* gather,
                         FrameGeom fg, uint32_t n, uint32_t* offsets, uint64_t* status,
