@@ -144,8 +144,10 @@ def algorithmic_bytes(kernel: str, items: int, n: int, m: int, tiles: int, depth
         return 8.0 * items
     if kernel == "duplicate_keys":   # record + offset in per Gaussian, 12 B per pair out
         return 20.0 * items + 12.0 * m
-    if kernel == "radix_pass":       # (u64 key, u32 value) in and out
+    if kernel in ("radix_pass", "onesweep_pass"):  # (u64 key, u32 value) in and out
         return 24.0 * items
+    if kernel == "sort_histogram":   # every key read once for all passes' digit counts
+        return 8.0 * items
     if kernel == "tile_ranges":      # key in per pair, range out per tile
         return 8.0 * items + 8.0 * tiles
     # fused frame
@@ -168,6 +170,16 @@ def algorithmic_bytes(kernel: str, items: int, n: int, m: int, tiles: int, depth
     if kernel == "tile_expand_pass":  # 4 B element in; u64 key + u32 value out; depth tables once;
         return 16.0 * items + 8.0 * n + 16.0 * tiles  # per tile: first/last position in, range out
     return 0.0
+
+
+def sort_pass_stats(skt: dict, reps: int) -> tuple[int, dict | None, dict | None]:
+    """(passes per sort, pass-kernel totals, histogram totals) of the
+    tdgs_sort_pairs launches in the tracer's totals: the onesweep form (one
+    histogram launch, then one pass launch per digit) or the chunked pass
+    kernels."""
+    op = skt.get("onesweep_pass") or skt.get("radix_pass")
+    passes = op["launches"] // reps if op else 0
+    return passes, op, skt.get("sort_histogram")
 
 
 def combine_ranks(dist, seconds: float, units: float, device) -> tuple[float, float]:
@@ -309,12 +321,13 @@ def run_ours(args, rank, world, local_rank, dist):
         ctx.enable_timing(False)
         ctx.set_sort_variant(-1)
         sms = [a.elapsed_time(b) for a, b in sev]
-        passes = skt.get("radix_pass", {}).get("launches", 0) // (args.warmup + args.steps)
+        passes, op, hop = sort_pass_stats(skt, args.warmup + args.steps)
         sbytes = m * (8 + 24 * passes)
         smean = statistics.mean(sms)
-        op = skt.get("radix_pass")
         sort_only = {"pairs_per_s": m / (smean * 1e-3), "ms_mean": round(smean, 4),
                      "ms_p50": round(statistics.median(sms), 4), "passes": passes,
+                     "kernel": "onesweep_pass" if "onesweep_pass" in skt else "radix_pass",
+                     "histogram_ms": round(hop["ms"] / hop["launches"], 5) if hop else None,
                      "algorithmic_bytes": sbytes,
                      "achieved_gbs": round(sbytes / (smean * 1e-3) / 1e9, 1),
                      "frac": round(sbytes / (smean * 1e-3) / 1e9 / peak, 4),
@@ -561,7 +574,7 @@ def run_large(args, local_rank):
     skt = ctx.kernel_times()
     ctx.enable_timing(False)
     sms = [a.elapsed_time(b) for a, b in sev]
-    passes = skt.get("radix_pass", {}).get("launches", 0) // reps
+    passes, _, _ = sort_pass_stats(skt, reps)
     sbytes = m * (8 + 24 * passes)
     smean = statistics.mean(sms)
     ctx.close()

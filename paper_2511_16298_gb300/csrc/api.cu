@@ -52,13 +52,13 @@ struct Buffer {
 enum KernelId {
   kKCount, kKScan, kKDuplicate, kKRanges, kKRadixPass,
   kKFrameCount, kKDepthSort, kKFrameScan, kKDupDepth, kKTilePass, kKTileExpand, kKPreprocess, kKBitonic, kKRender, kKPreCount, kKNormRange, kKNormDup, kKNormPass,
-  kKNormRanges, kKRenderOrder, kKNum
+  kKNormRanges, kKRenderOrder, kKSortHist, kKOnesweep, kKNum
 };
 const char* const kKernelNames[kKNum] = {
     "count_tiles",  "scan",       "duplicate_keys",     "tile_ranges",    "radix_pass",
     "frame_count",  "depth_sort", "scan_by_depth", "duplicate_by_depth", "tile_sort_pass",
     "tile_expand_pass", "preprocess", "bitonic_sort", "render", "preprocess_count", "norm_range",
-    "norm_duplicate", "norm_sort_pass", "norm_ranges", "render_order"};
+    "norm_duplicate", "norm_sort_pass", "norm_ranges", "render_order", "sort_histogram", "onesweep_pass"};
 
 // View table as stored in device memory (SoA, fixed maximum size).
 struct ViewBlob {
@@ -89,6 +89,7 @@ struct tdgs_context {
   uint32_t* d_tickets = nullptr;  // [1] count blocks (reset by the kernel), [2..3] radix grid barrier
   uint32_t ticket_base[2] = {0, 0};
   Buffer scan_status, sort_scratch;
+  Buffer os_scratch;  // onesweep sort: histograms, digit starts, tickets, look-back status
   // fused-frame / multi-view buffers
   Buffer f_rec3, f_conic;  // projected records and conics of tdgs_sort_frame_3d
   Buffer d_cams;           // cameras of the 3D calls (device)
@@ -274,6 +275,26 @@ tdgs_status do_sort(tdgs_context* ctx, uint64_t* keys, uint32_t* values, uint64_
   *result_in_alt = 0;
   if (m == 0) return TDGS_OK;
   const SortPlan plan = make_sort_plan(m, tile_bits, flags, ctx->tuning);
+  if (ctx->tuning.sort_variant < 0 && onesweep_eligible(m, keys, values, keys_alt, values_alt)) {
+    bool grown = false;
+    tdgs_status st = ensure(ctx, ctx->os_scratch, onesweep_scratch_words(m) * 4, s, &grown);
+    if (st != TDGS_OK) return st;
+    uint32_t* scratch = static_cast<uint32_t*>(ctx->os_scratch.p);
+    if (grown) TDGS_CUDA(ctx, cudaMemsetAsync(scratch, 0, onesweep_header_words() * 4, s));
+    TDGS_TRACED(ctx, kKSortHist, m, s, launch_onesweep_hist(plan, keys, m, scratch, err_word(ctx), s));
+    uint64_t* kin = keys;
+    uint32_t* vin = values;
+    uint64_t* kout = keys_alt;
+    uint32_t* vout = values_alt;
+    for (uint32_t p = 0; p < plan.passes; ++p) {
+      TDGS_TRACED(ctx, kKOnesweep, m, s,
+                  launch_onesweep_pass(plan, p, kin, vin, kout, vout, m, scratch, err_word(ctx), s));
+      std::swap(kin, kout);
+      std::swap(vin, vout);
+    }
+    *result_in_alt = static_cast<int>(plan.passes & 1u);
+    return TDGS_OK;
+  }
   if (plan.grid == 0) return fail(ctx, TDGS_ERR_CUDA, "device query for the sort plan failed");
   tdgs_status st = ensure(ctx, ctx->sort_scratch, radix_scratch_words(plan) * 4, s);
   if (st != TDGS_OK) return st;
@@ -475,7 +496,7 @@ void tdgs_context_destroy(tdgs_context* ctx) {
   DeviceGuard g(ctx->device);
   drain_timings(ctx);
   for (cudaEvent_t e : ctx->free_events) cudaEventDestroy(e);
-  Buffer* bufs[] = {&ctx->scan_status, &ctx->sort_scratch, &ctx->f_counts,    &ctx->f_dkey[0],
+  Buffer* bufs[] = {&ctx->scan_status, &ctx->sort_scratch, &ctx->os_scratch, &ctx->f_counts, &ctx->f_dkey[0],
                     &ctx->f_dkey[1],    &ctx->f_dkey[2],     &ctx->f_dval[0],    &ctx->f_dval[1],
                     &ctx->f_dval[2],    &ctx->f_soff,       &ctx->f_sdo,        &ctx->f_rec3,
                     &ctx->f_conic,      &ctx->d_cams,       &ctx->diag,       &ctx->b_keys,       &ctx->b_vals,       &ctx->n_counts,

@@ -1,0 +1,714 @@
+// tdgs_sort_pairs as a onesweep LSD radix sort (the Sorting step of
+// Sec. II-A: instances ordered by tile, then by depth; sorting is 86-89 % of
+// the frame in Table VI).
+//
+//   k_onesweep_hist  reads every key once and builds the digit histograms of
+//                    all passes at once (shared-memory counters per CTA,
+//                    then global atomics); the last CTA scans them into each
+//                    pass's digit starts.  It also clears the first pass's
+//                    look-back status and the tile tickets.
+//   k_onesweep_pass  one launch per digit.  Persistent CTAs take tiles of
+//                    4096 pairs in ticket order; each tile is copied into
+//                    shared memory by one bulk copy (double buffered: the
+//                    next tile is in flight while this one is ranked),
+//                    ranked stably with one ballot per digit bit, and its
+//                    per-digit counts are published at once.  A decoupled
+//                    look-back over the predecessors' status words -- a
+//                    window of tiles per L2 round trip -- gives the tile's
+//                    global position per digit; the tile is then exchanged
+//                    into digit order in shared memory and written out with
+//                    coalesced stores.  Every key and value is read once and
+//                    written once per pass.
+//
+// Tickets make the look-back deadlock-free without co-residency: a tile
+// only waits on tiles with smaller tickets, and the smallest unfinished
+// ticket is always the one its CTA is working on.  Every wait is bounded
+// and latches TDGS_ERR_TIMEOUT when it runs out; every scatter is checked
+// against the pair count.
+#include <mutex>
+
+#include "radix.cuh"
+
+namespace tdgs {
+namespace onesweep {
+
+constexpr int kBits = 9;
+constexpr uint32_t kBins = 1u << kBits;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 16;
+constexpr uint32_t kTileKeys = kThreads * kItems;  // 4096
+constexpr int kGroup = 4;                          // items ranked together (independent ballot chains)
+constexpr uint32_t kFlagA = 1u << 30;              // status: this tile's own count
+constexpr uint32_t kFlagP = 2u << 30;              // status: inclusive prefix over tiles <= this one
+constexpr uint32_t kCountMask = (1u << 30) - 1u;
+constexpr uint32_t kMaxPairs = 1u << 30;           // counts in a status word have 30 bits
+
+static_assert(kBins == 2 * kThreads, "two digits per thread in the look-back and the digit scan");
+
+struct TileBuf {
+  uint64_t k[kTileKeys];
+  uint32_t v[kTileKeys];
+};
+constexpr size_t kWhBytes = static_cast<size_t>(kWarps) * kBins * 2;  // per-warp 16-bit counters
+constexpr size_t kSmem = 2 * sizeof(TileBuf) + kWhBytes + 2 * kBins * 4;
+
+// Digit of one key for one pass: bits [shift, shift + width) of the key,
+// or of (tile bits : depth bits 30..0) when bit 31 is dropped.  The host
+// folds both cases into a funnel shift (see make_digit).
+struct Digit {
+  uint32_t sh;       // shift applied to (hi : lo') or to hi alone
+  uint32_t hi_only;  // the digit lies in the high word
+  uint32_t lo_shl;   // 1 when bit 31 is dropped (lo' = lo << 1), else 0
+  uint32_t mask;
+};
+__device__ __forceinline__ uint32_t digit(uint64_t k, const Digit& g) {
+  const uint32_t lo = static_cast<uint32_t>(k) << g.lo_shl, hi = static_cast<uint32_t>(k >> 32);
+  const uint32_t d = g.hi_only ? (hi >> g.sh) : __funnelshift_r(lo, hi, g.sh);
+  return d & g.mask;
+}
+
+struct HistArgs {
+  uint32_t m, passes, ntiles;
+  uint32_t drop31;               // sorted key = (tile bits : depth bits 30..0)
+  uint32_t mask[kMaxPasses];     // digit p = bits [p * width, p * width + width) & mask[p]
+  uint64_t bad_mask;   // key bits that must be zero
+  uint32_t* hist;      // [kMaxPasses][kBins], zero on entry, left zero
+  uint32_t* gstart;    // [kMaxPasses][kBins] digit starts (exclusive scan of hist)
+  uint32_t* done;      // CTA counter, zero on entry, left zero
+  uint32_t* tickets;   // [kMaxPasses] tile tickets, cleared here
+  uint32_t* status0;   // [ntiles][kBins] look-back status of pass 0, cleared here
+  uint32_t* err;
+};
+
+struct PassArgs {
+  uint32_t m, ntiles;
+  Digit dg;
+  const uint32_t* gstart;  // [kBins] this pass's digit starts
+  uint32_t* status;        // [ntiles][kBins] this pass's status (all zero on entry)
+  uint32_t* status_next;   // [ntiles][kBins] the next pass's, cleared here (or null)
+  uint32_t* ticket;        // zero on entry
+  uint32_t* err;
+};
+
+// ----------------------------------------------------------- histograms
+// kW: the digit width of every pass but the last (8 or 9 for 31..64 key
+// bits), so that each pass's digit comes from a shift by a constant.
+template <int kW>
+__global__ void __launch_bounds__(256) k_onesweep_hist(const uint64_t* __restrict__ keys, HistArgs a) {
+  __shared__ uint32_t h[kMaxPasses * kBins];
+  __shared__ uint32_t s_warp[8];
+  __shared__ bool s_last;
+  const uint32_t t = threadIdx.x;
+  const uint32_t np = a.passes;
+  for (uint32_t i = t; i < np * kBins; i += 256) h[i] = 0;
+  // housekeeping for the passes: tickets and pass 0's look-back status
+  if (blockIdx.x == 0 && t < kMaxPasses) a.tickets[t] = 0;
+  {
+    uint4* z = reinterpret_cast<uint4*>(a.status0);
+    const size_t nz = static_cast<size_t>(a.ntiles) * kBins / 4;
+    for (size_t i = static_cast<size_t>(blockIdx.x) * 256 + t; i < nz; i += static_cast<size_t>(gridDim.x) * 256)
+      z[i] = make_uint4(0, 0, 0, 0);
+  }
+  __syncthreads();
+  // This CTA's chunk, cut into one contiguous run per thread (lanes far
+  // apart in the input rarely share a digit, so the shared-memory atomics
+  // of one warp seldom collide); 32-byte steps keep whole sectors per load.
+  const uint32_t m = a.m;
+  const uint64_t per_cta = ((static_cast<uint64_t>(m) + gridDim.x - 1) / gridDim.x + 3) & ~3ull;
+  const uint64_t cb = blockIdx.x * per_cta;
+  const uint32_t beg = static_cast<uint32_t>(cb < m ? cb : m);
+  const uint32_t end = static_cast<uint32_t>(cb + per_cta < m ? cb + per_cta : m);
+  const uint32_t len = end - beg;
+  const uint32_t per_thr = ((len + 255) / 256 + 3) & ~3u;
+  const uint32_t tb = min(beg + t * per_thr, end), te = min(tb + per_thr, end);
+  bool bad = false;
+  const bool d31 = a.drop31 != 0;
+  auto count = [&](uint64_t k) {
+    bad |= (k & a.bad_mask) != 0;
+    const uint64_t e = d31 ? ((k & 0x7fffffffull) | ((k >> 32) << 31)) : k;
+#pragma unroll
+    for (uint32_t p = 0; p < kMaxPasses; ++p)
+      if (p < np) atomicAdd(&h[p * kBins + (static_cast<uint32_t>(e >> (p * kW)) & a.mask[p])], 1u);
+  };
+  uint32_t i = tb;
+  if ((reinterpret_cast<uintptr_t>(keys) & 15u) == 0) {
+    constexpr uint32_t kU = 4;  // 32-byte steps in flight per thread
+    for (; i + 4 * kU <= te; i += 4 * kU) {
+      uint4 w[2 * kU];
+#pragma unroll
+      for (uint32_t u = 0; u < 2 * kU; ++u) w[u] = __ldcs(reinterpret_cast<const uint4*>(keys + i) + u);
+#pragma unroll
+      for (uint32_t u = 0; u < 2 * kU; ++u) {
+        count((static_cast<uint64_t>(w[u].y) << 32) | w[u].x);
+        count((static_cast<uint64_t>(w[u].w) << 32) | w[u].z);
+      }
+    }
+  }
+  for (; i < te; ++i) count(keys[i]);
+  if (__any_sync(0xffffffffu, bad) && lane_id() == 0) latch_error(a.err, TDGS_ERR_INVALID_ARGUMENT, kSiteRadixKeys);
+  __syncthreads();
+  for (uint32_t q = t; q < np * kBins; q += 256)
+    if (h[q]) atomicAdd(a.hist + q, h[q]);
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(a.done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // last CTA: digit starts of every pass, then leave hist and done zero
+  for (uint32_t p = 0; p < np; ++p) {
+    const uint32_t c0 = __ldcg(a.hist + p * kBins + 2 * t), c1 = __ldcg(a.hist + p * kBins + 2 * t + 1);
+    const uint32_t s0 = radix::block_excl_scan<8>(c0 + c1, s_warp);
+    a.gstart[p * kBins + 2 * t] = s0;
+    a.gstart[p * kBins + 2 * t + 1] = s0 + c0;
+    a.hist[p * kBins + 2 * t] = 0;
+    a.hist[p * kBins + 2 * t + 1] = 0;
+  }
+  if (t == 0) *a.done = 0;
+}
+
+// ------------------------------------------------------ shared-memory TMA
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+// One arrival that expects `bytes` of bulk-copy data, then the copies of
+// the tile's keys and values (16-byte aligned, multiples of 16 bytes).
+__device__ __forceinline__ void load_tile(TileBuf* b, uint64_t* bar, const uint64_t* kin, const uint32_t* vin,
+                                          uint32_t first, uint32_t nbulk) {
+  const uint32_t kb = nbulk * 8, vb = nbulk * 4;
+  if (nbulk == 0) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+                 : "memory");
+    return;
+  }
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                   smem_addr(bar)),
+               "r"(kb + vb)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(b->k)),
+               "l"(kin + first), "r"(kb), "r"(smem_addr(bar))
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(b->v)),
+               "l"(vin + first), "r"(vb), "r"(smem_addr(bar))
+               : "memory");
+}
+// Bounded wait for phase `parity` of `bar`; false (error latched) if the
+// copy did not arrive.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* err) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  latch_error(err, TDGS_ERR_TIMEOUT, kSiteBarrier);
+  return false;
+}
+
+__device__ __forceinline__ uint2 ld_relaxed_v2(const uint32_t* p) {
+  uint2 v;
+  asm volatile("ld.relaxed.gpu.global.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_v2(uint32_t* p, uint32_t x, uint32_t y) {
+  asm volatile("st.relaxed.gpu.global.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(x), "r"(y) : "memory");
+}
+
+// ------------------------------------------------ tile prefixes per digit
+// Exclusive sum of v over the CTA.
+__device__ __forceinline__ uint32_t cta_excl_scan(uint32_t v, uint32_t* s_warp) {
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t o = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= static_cast<uint32_t>(d)) x += o;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < kWarps ? s_warp[lane] : 0u;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t o = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= static_cast<uint32_t>(d)) w += o;
+    }
+    if (lane < kWarps) s_warp[lane] = w;
+  }
+  __syncthreads();
+  const uint32_t r = x - v + (warp ? s_warp[warp - 1] : 0u);
+  __syncthreads();
+  return r;
+}
+
+// The scan CTAs: the last kScanCtas CTAs of the grid take no tiles; scan
+// CTA c owns digits [64 c, 64 c + 64).  Lane l of every warp owns digit
+// pair 64 c + 2 l, +1; warp w reads rows (tiles) k + 8 w .. k + 8 w + 7 of
+// it, so one round reads 64 rows per pair at once (one L2 round trip).
+// Per pair, the rows up to the first tile whose counts are not out yet are
+// consumed in order: running sums plus the sums of the warps before give
+// each row its inclusive prefix, which overwrites its counts.  The next
+// round starts at the first row not consumed (after a short sleep when no
+// pair moved).  The scan waits only on counts, which every tile publishes
+// without waiting on anything, so it always finishes (the wait is
+// bounded).  Spreading the digits over several CTAs spreads the status
+// traffic (about 4 KB per tile) over several SMs.
+constexpr uint32_t kScanCtas = 8;
+constexpr uint32_t kSegRows = 8;  // rows per warp and round
+static_assert(kBins == 64 * kScanCtas && kWarps * kSegRows == 64, "scan layout");
+__device__ __forceinline__ void scan_tiles(uint32_t* __restrict__ status, uint32_t ntiles, uint32_t c,
+                                           uint32_t* err) {
+  __shared__ uint32_t s_stop[kWarps][32], s_sum0[kWarps][32], s_sum1[kWarps][32];
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  uint32_t* col = status + 64 * c + 2 * lane;
+  uint32_t k = 0, run0 = 0, run1 = 0, idle = 0;  // per pair: first row not consumed, its sums
+  while (__syncthreads_or(k < ntiles)) {
+    const uint32_t r0 = k + kSegRows * warp;
+    uint2 w[kSegRows];
+#pragma unroll
+    for (uint32_t q = 0; q < kSegRows; ++q)
+      w[q] = r0 + q < ntiles ? ld_relaxed_v2(col + static_cast<size_t>(r0 + q) * kBins) : make_uint2(0u, 0u);
+    uint32_t stop = kSegRows, t0 = 0, t1 = 0;  // first unusable row of the segment; sums before it
+#pragma unroll
+    for (uint32_t q = 0; q < kSegRows; ++q) {
+      const bool ready = r0 + q < ntiles && (w[q].x & ~kCountMask) != 0 && (w[q].y & ~kCountMask) != 0;
+      if (!ready && stop == kSegRows) stop = q;
+      if (stop == kSegRows) {
+        t0 += w[q].x & kCountMask;
+        t1 += w[q].y & kCountMask;
+      }
+    }
+    s_stop[warp][lane] = stop;
+    s_sum0[warp][lane] = t0;
+    s_sum1[warp][lane] = t1;
+    __syncthreads();
+    // this pair's rows consumed in this round: every warp's segment up to
+    // the first one that stops early
+    uint32_t before0 = 0, before1 = 0, all0 = 0, all1 = 0, used = 0;
+    bool open = true;  // segments so far were complete
+#pragma unroll
+    for (uint32_t v = 0; v < kWarps; ++v) {
+      if (open) {
+        if (v < warp) {
+          before0 += s_sum0[v][lane];
+          before1 += s_sum1[v][lane];
+        }
+        all0 += s_sum0[v][lane];
+        all1 += s_sum1[v][lane];
+        used += s_stop[v][lane];
+        open = s_stop[v][lane] == kSegRows;
+      }
+    }
+    // this warp's segment lies inside the consumed rows if every earlier
+    // segment was complete
+    bool mine = true;
+#pragma unroll
+    for (uint32_t v = 0; v < kWarps; ++v)
+      if (v < warp && s_stop[v][lane] != kSegRows) mine = false;
+    if (mine) {
+      uint32_t p0 = run0 + before0, p1 = run1 + before1;
+#pragma unroll
+      for (uint32_t q = 0; q < kSegRows; ++q) {
+        if (q < stop) {
+          p0 += w[q].x & kCountMask;
+          p1 += w[q].y & kCountMask;
+          st_relaxed_v2(col + static_cast<size_t>(r0 + q) * kBins, kFlagP | (p0 & kCountMask),
+                        kFlagP | (p1 & kCountMask));
+        }
+      }
+    }
+    k += used;
+    run0 += all0;
+    run1 += all1;
+    // no pair of the CTA moved: wait a little (bounded)
+    if (!__syncthreads_or(used != 0 || k >= ntiles)) {
+      if (++idle > kSpinLimit) {
+        latch_error(err, TDGS_ERR_TIMEOUT, kSiteBarrier);
+        return;
+      }
+      __nanosleep(64);
+    }
+  }
+}
+
+// Exclusive prefix of digits 2t and 2t+1 for tile `tile` > 0: the inclusive
+// prefix the scan CTAs wrote for tile - 1 (bounded wait).
+__device__ __forceinline__ void wait_prefix(const uint32_t* __restrict__ status, uint32_t tile, uint32_t t,
+                                            uint32_t& e0, uint32_t& e1, uint32_t* err) {
+  const uint32_t* row = status + static_cast<size_t>(tile - 1) * kBins + 2 * t;
+  uint2 w = ld_relaxed_v2(row);
+  uint32_t spins = 0;
+  while ((w.x & ~kCountMask) != kFlagP || (w.y & ~kCountMask) != kFlagP) {
+    if (++spins > kSpinLimit) {
+      latch_error(err, TDGS_ERR_TIMEOUT, kSiteBarrier);
+      break;
+    }
+    __nanosleep(32);
+    w = ld_relaxed_v2(row);
+  }
+  e0 = w.x & kCountMask;
+  e1 = w.y & kCountMask;
+}
+
+// ------------------------------------------------------------- one pass
+// Stable rank of one tile held in shared memory (tile order: warp, item,
+// lane): r[j] = number of earlier items of this warp with the same digit;
+// the warp's counter row (zero on entry) ends holding its count per digit.
+__device__ __forceinline__ void rank_in_warps(const TileBuf& tb, uint32_t valid, const Digit& dg, uint16_t* my_wh,
+                                              uint32_t (&r)[kItems]) {
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  const uint32_t wbase = warp * 32 * kItems;
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int j0 = 0; j0 < kItems; j0 += kGroup) {
+    uint32_t d[kGroup];
+#pragma unroll
+    for (int g = 0; g < kGroup; ++g) {
+      const uint32_t idx = wbase + (j0 + g) * 32 + lane;
+      d[g] = digit(idx < valid ? tb.k[idx] : 0ull, dg);
+      r[j0 + g] = radix::equal_digit_lanes<kBits>(d[g]);
+      const uint32_t fi = wbase + (j0 + g) * 32;
+      const uint32_t nlive = valid > fi ? min(valid - fi, 32u) : 0u;
+      r[j0 + g] &= nlive >= 32 ? 0xffffffffu : ((1u << nlive) - 1u);
+    }
+#pragma unroll
+    for (int g = 0; g < kGroup; ++g) {
+      const uint32_t peers = r[j0 + g];
+      const bool live = wbase + (j0 + g) * 32 + lane < valid;
+      const uint32_t before = my_wh[d[g]];
+      __syncwarp();
+      const uint32_t cnt = __popc(peers), below = __popc(peers & lt);
+      if (live && below + 1 == cnt) my_wh[d[g]] = static_cast<uint16_t>(before + cnt);
+      __syncwarp();
+      r[j0 + g] = before + below;
+    }
+  }
+}
+
+// The compute warps of a CTA are software-pipelined over its tiles:
+// iteration i ranks tile k_i, publishes its per-digit counts and exchanges
+// it into digit order in shared memory; then it takes the prefix of tile
+// k_(i-1) (ranked one iteration earlier) from the scan CTAs and scatters
+// that tile.  The prefix is needed a whole ranking phase after the counts
+// went out, so the scan has (nearly always) produced it.  Ranking never
+// waits for another CTA, so every tile with a ticket publishes its counts
+// and the scan always completes.  Launched cooperatively: the scan CTAs
+// must run alongside every other CTA.
+__global__ void __launch_bounds__(kThreads, 2)
+    k_onesweep_pass(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
+                    uint32_t* __restrict__ vout, PassArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  TileBuf* buf = reinterpret_cast<TileBuf*>(smem);
+  uint16_t* wh = reinterpret_cast<uint16_t*>(smem + 2 * sizeof(TileBuf));
+  uint32_t* lstart = reinterpret_cast<uint32_t*>(smem + 2 * sizeof(TileBuf) + kWhBytes);
+  uint32_t* off = lstart + kBins;
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t s_tile[2];
+  __shared__ uint32_t s_warp[kWarps];
+
+  const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+  const uint32_t m = a.m, ntiles = a.ntiles;
+  if (blockIdx.x >= gridDim.x - kScanCtas) {  // a scan CTA
+    scan_tiles(a.status, ntiles, blockIdx.x - (gridDim.x - kScanCtas), a.err);
+    return;
+  }
+  const Digit dg = a.dg;
+  uint16_t* my_wh = wh + warp * kBins;
+  {
+    uint4* z = reinterpret_cast<uint4*>(wh);
+    for (uint32_t i = t; i < kWhBytes / 16; i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
+  }
+  const uint32_t g0 = __ldg(a.gstart + 2 * t), g1 = __ldg(a.gstart + 2 * t + 1);
+  auto bulk_items = [&](uint32_t tile) {
+    const uint32_t first = tile * kTileKeys;
+    const uint32_t valid = min(kTileKeys, m - first);
+    return valid & ~3u;  // the last 1-3 items of a ragged tile are read by threads
+  };
+  if (t == 0) {
+    mbar_init(&mbar[0]);
+    mbar_init(&mbar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const uint32_t first = atomicAdd(a.ticket, 1u);
+    s_tile[1] = first;
+    if (first < ntiles) load_tile(&buf[0], &mbar[0], kin, vin, first * kTileKeys, bulk_items(first));
+  }
+  __syncthreads();
+  uint32_t cur = s_tile[1];
+  uint32_t phase = 0;  // bit b: parity of the next wait on mbar[b]
+  bool ok = true;
+  bool have_prev = false;
+  uint32_t prev = 0, pc0 = 0, ps0 = 0, pvalid = 0;  // the tile waiting for its scatter
+  for (uint32_t it = 0;; ++it) {
+    const bool have_cur = cur < ntiles;
+    if (!have_cur && !have_prev) break;
+    const uint32_t b = it & 1u;  // cur is in buf[b], prev in buf[b ^ 1]
+    uint32_t c0 = 0, c1 = 0, s0 = 0, valid = 0;
+    // The next tile's ticket is taken at the start of the iteration and its
+    // data prefetched into L2 once the ticket returns; the copy into shared
+    // memory goes out at the end of the iteration (when its buffer is free)
+    // and then comes from L2.  Its counts are published in the next
+    // iteration, and the tiles after it look back one more iteration later,
+    // so taking it here costs them no waiting.
+    uint32_t nxt = ntiles;
+    if (t == 0 && have_cur) nxt = atomicAdd(a.ticket, 1u);
+    if (have_cur) {
+      TileBuf& tb = buf[b];
+      const uint32_t first = cur * kTileKeys;
+      valid = min(kTileKeys, m - first);
+      const bool arrived = mbar_wait(&mbar[b], (phase >> b) & 1u, a.err);
+      if (__syncthreads_or(!arrived)) {
+        // A copy that never arrived (error latched): the whole CTA stops
+        // together.  Thread 0 waits once more, bounded, for that copy (the
+        // only one in flight), so nothing lands in shared memory after the
+        // CTA exits.
+        if (t == 0) (void)mbar_wait(&mbar[b], (phase >> b) & 1u, a.err);
+        break;
+      }
+      phase ^= 1u << b;
+      if (valid != kTileKeys) {  // ragged last tile: its last 1-3 items by plain loads
+        const uint32_t nb = valid & ~3u;
+        if (t < valid - nb) {
+          tb.k[nb + t] = kin[first + nb + t];
+          tb.v[nb + t] = vin[first + nb + t];
+        }
+        __syncthreads();
+      }
+      // ---- stable rank within each warp
+      uint32_t r[kItems];
+      rank_in_warps(tb, valid, dg, my_wh, r);
+      if (t == 0 && nxt < ntiles) {
+        const uint32_t nf = nxt * kTileKeys, nv = min(kTileKeys, m - nf);
+        radix::prefetch_l2(kin + nf, static_cast<uint64_t>(nv) * 8);
+        radix::prefetch_l2(vin + nf, static_cast<uint64_t>(nv) * 4);
+      }
+      __syncthreads();
+      // ---- per-digit counts (column t holds digits 2t and 2t+1), prefixes over warps
+      {
+        uint32_t* wh32 = reinterpret_cast<uint32_t*>(wh);
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+          const uint32_t x = wh32[w * (kBins / 2) + t];
+          wh32[w * (kBins / 2) + t] = run;
+          run += x;  // halves stay below 2^16: no carry between digits
+        }
+        c0 = run & 0xffffu;
+        c1 = run >> 16;
+      }
+      // ---- publish the counts (tile 0: its counts are its inclusive prefix)
+      st_relaxed_v2(a.status + static_cast<size_t>(cur) * kBins + 2 * t, kFlagA | c0, kFlagA | c1);
+      // ---- tile-local digit starts, positions, exchange into digit order
+      s0 = cta_excl_scan(c0 + c1, s_warp);
+      lstart[2 * t] = s0;
+      lstart[2 * t + 1] = s0 + c0;
+      __syncthreads();
+      const uint32_t wbase = warp * 32 * kItems;
+      uint64_t kr[kItems];
+      uint32_t vr[kItems];
+#pragma unroll
+      for (int j = 0; j < kItems; ++j) {
+        const uint32_t idx = wbase + j * 32 + lane;
+        if (idx < valid) {
+          kr[j] = tb.k[idx];
+          vr[j] = tb.v[idx];
+          const uint32_t dd = digit(kr[j], dg);
+          r[j] += lstart[dd] + my_wh[dd];
+        }
+      }
+      __syncwarp();
+      {  // this warp's counter row is read: zero it for the next tile
+        uint4* z = reinterpret_cast<uint4*>(my_wh);
+        for (uint32_t i = lane; i < kBins / 8; i += 32) z[i] = make_uint4(0, 0, 0, 0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < kItems; ++j) {
+        if (wbase + j * 32 + lane < valid && r[j] < kTileKeys) {
+          tb.k[r[j]] = kr[j];
+          tb.v[r[j]] = vr[j];
+        }
+      }
+    }
+    // ---- the previous tile: its prefix, output positions
+    if (have_prev) {
+      uint32_t e0 = 0, e1 = 0;
+      if (prev != 0) wait_prefix(a.status, prev, t, e0, e1, a.err);
+      if (a.status_next)
+        *reinterpret_cast<uint2*>(a.status_next + static_cast<size_t>(prev) * kBins + 2 * t) = make_uint2(0u, 0u);
+      off[2 * t] = g0 + e0 - ps0;
+      off[2 * t + 1] = g1 + e1 - (ps0 + pc0);
+    }
+    __syncthreads();  // cur is in digit order; off[] of prev is complete
+    // ---- coalesced scatter of the previous tile in digit order
+    if (have_prev) {
+      const TileBuf& pb = buf[b ^ 1u];
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        const uint32_t p = i * kThreads + t;
+        if (p < pvalid) {
+          const uint64_t key = pb.k[p];
+          const uint32_t dst = off[digit(key, dg)] + p;
+          if (dst < m) {
+            kout[dst] = key;
+            vout[dst] = pb.v[p];
+          } else {
+            ok = false;
+          }
+        }
+      }
+    }
+    if (t == 0) s_tile[b] = nxt;
+    __syncthreads();  // buf[b ^ 1] is free; the next tile's number is visible
+    if (t == 0 && nxt < ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      load_tile(&buf[b ^ 1u], &mbar[b ^ 1u], kin, vin, nxt * kTileKeys, bulk_items(nxt));
+    }
+    have_prev = have_cur;
+    if (have_cur) {
+      prev = cur;
+      pc0 = c0;
+      ps0 = s0;
+      pvalid = valid;
+    }
+    cur = s_tile[b];
+  }
+  if (!ok) latch_error(a.err, TDGS_ERR_CAPACITY, kSiteRadixRange);
+}
+
+
+}  // namespace onesweep
+
+// ------------------------------------------------------------ host side
+namespace {
+std::mutex g_mu;
+uint32_t g_grid[64] = {};  // resident pass CTAs per device (0: not queried)
+
+uint32_t pass_grid() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_grid[dev]) {
+    const void* fn = reinterpret_cast<const void*>(&onesweep::k_onesweep_pass);
+    int sms = 0, occ = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(onesweep::kSmem)) !=
+        cudaSuccess)
+      return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, onesweep::kThreads, onesweep::kSmem) != cudaSuccess ||
+        occ <= 0)
+      return 0;
+    g_grid[dev] = static_cast<uint32_t>(sms * occ);
+  }
+  return g_grid[dev];
+}
+
+onesweep::Digit make_digit(uint32_t shift, uint32_t mask, bool drop31) {
+  onesweep::Digit d{};
+  const uint32_t s = shift + (drop31 ? 1u : 0u);
+  d.lo_shl = drop31 ? 1u : 0u;
+  d.hi_only = s >= 32 ? 1u : 0u;
+  d.sh = s >= 32 ? s - 32 : s;
+  d.mask = mask;
+  return d;
+}
+}  // namespace
+
+bool onesweep_eligible(uint32_t m, const void* keys, const void* values, const void* keys_alt,
+                       const void* values_alt) {
+  auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  return m > 0 && m < onesweep::kMaxPairs && a16(keys) && a16(values) && a16(keys_alt) && a16(values_alt);
+}
+
+size_t onesweep_scratch_words(uint32_t m) {
+  const size_t ntiles = (static_cast<size_t>(m) + onesweep::kTileKeys - 1) / onesweep::kTileKeys;
+  return onesweep_header_words() + 2 * ntiles * onesweep::kBins;
+}
+
+size_t onesweep_header_words() {
+  // hist | gstart | done + tickets (padded to 16 bytes)
+  return 2 * static_cast<size_t>(kMaxPasses) * onesweep::kBins + 4 + kMaxPasses;
+}
+
+uint32_t onesweep_tile_keys() { return onesweep::kTileKeys; }
+
+cudaError_t launch_onesweep_hist(const SortPlan& plan, const uint64_t* keys, uint32_t m, uint32_t* scratch,
+                                 uint32_t* err, cudaStream_t s) {
+  using namespace onesweep;
+  HistArgs a{};
+  a.m = m;
+  a.passes = plan.passes;
+  a.ntiles = (m + kTileKeys - 1) / kTileKeys;
+  a.drop31 = plan.drop31 ? 1u : 0u;
+  for (uint32_t p = 0; p < plan.passes; ++p) {
+    if (plan.shift[p] != p * plan.digit_bits) return cudaErrorInvalidValue;
+    a.mask[p] = plan.mask[p];
+  }
+  a.bad_mask = plan.bad_mask;
+  a.hist = scratch;
+  a.gstart = scratch + kMaxPasses * kBins;
+  a.done = scratch + 2 * kMaxPasses * kBins;
+  a.tickets = a.done + 4;
+  a.status0 = scratch + onesweep_header_words();
+  a.err = err;
+  int sms = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return cudaErrorInvalidDevice;
+  // about 32 KB of keys per thread block, at most 4 blocks per SM
+  uint32_t grid = (m + 4095) / 4096;
+  const uint32_t cap = static_cast<uint32_t>(sms) * 4;
+  if (grid > cap) grid = cap;
+  if (grid == 0) grid = 1;
+  switch (plan.digit_bits) {
+    case 9: k_onesweep_hist<9><<<grid, 256, 0, s>>>(keys, a); break;
+    case 8: k_onesweep_hist<8><<<grid, 256, 0, s>>>(keys, a); break;
+    case 7: k_onesweep_hist<7><<<grid, 256, 0, s>>>(keys, a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_onesweep_pass(const SortPlan& plan, uint32_t pass, const uint64_t* kin, const uint32_t* vin,
+                                 uint64_t* kout, uint32_t* vout, uint32_t m, uint32_t* scratch, uint32_t* err,
+                                 cudaStream_t s) {
+  using namespace onesweep;
+  const uint32_t resident = pass_grid();
+  if (resident == 0) return cudaErrorInvalidConfiguration;
+  PassArgs a{};
+  a.m = m;
+  a.ntiles = (m + kTileKeys - 1) / kTileKeys;
+  a.dg = make_digit(plan.shift[pass], plan.mask[pass], plan.drop31);
+  a.gstart = scratch + kMaxPasses * kBins + pass * kBins;
+  a.ticket = scratch + 2 * kMaxPasses * kBins + 4 + pass;
+  uint32_t* st = scratch + onesweep_header_words();
+  const size_t rows = static_cast<size_t>(a.ntiles) * kBins;
+  a.status = st + (pass & 1u) * rows;
+  a.status_next = pass + 1 < plan.passes ? st + ((pass + 1) & 1u) * rows : nullptr;
+  a.err = err;
+  // CTAs that take tiles while they last, plus the scan CTAs (all resident)
+  if (resident < 2 * kScanCtas) return cudaErrorInvalidConfiguration;
+  const uint32_t grid = (a.ntiles < resident - kScanCtas ? a.ntiles : resident - kScanCtas) + kScanCtas;
+  void* args[] = {(void*)&kin, (void*)&vin, (void*)&kout, (void*)&vout, (void*)&a};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = kSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(&k_onesweep_pass), args);
+}
+
+}  // namespace tdgs

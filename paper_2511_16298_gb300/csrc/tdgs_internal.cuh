@@ -336,4 +336,22 @@ cudaError_t launch_radix_pass(const SortPlan& plan, uint32_t pass, const uint64_
                               const uint32_t* vin, uint64_t* kout, uint32_t* vout, uint32_t m,
                               uint32_t* scratch, uint32_t* bar, uint32_t* err, cudaStream_t s);
 
+// Onesweep form of tdgs_sort_pairs (onesweep.cu): one histogram launch
+// that reads the keys once, then one launch per digit pass with a
+// decoupled look-back.  Eligible for 0 < m < 2^30 pairs with all four
+// buffers 16-byte aligned (the tiles arrive by bulk copies).  Scratch:
+// onesweep_scratch_words(m) uint32 words whose first
+// onesweep_header_words() are zero when first used (the kernels leave
+// them zero).  Passes ping-pong between (keys, values) and the alternates.
+bool onesweep_eligible(uint32_t m, const void* keys, const void* values, const void* keys_alt,
+                       const void* values_alt);
+size_t onesweep_scratch_words(uint32_t m);
+size_t onesweep_header_words();
+uint32_t onesweep_tile_keys();
+cudaError_t launch_onesweep_hist(const SortPlan& plan, const uint64_t* keys, uint32_t m, uint32_t* scratch,
+                                 uint32_t* err, cudaStream_t s);
+cudaError_t launch_onesweep_pass(const SortPlan& plan, uint32_t pass, const uint64_t* kin, const uint32_t* vin,
+                                 uint64_t* kout, uint32_t* vout, uint32_t m, uint32_t* scratch, uint32_t* err,
+                                 cudaStream_t s);
+
 }  // namespace tdgs

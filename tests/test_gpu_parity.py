@@ -157,10 +157,54 @@ def test_sort_pairs_variants(ctx, oracle, variant, m, tile_bits, ties):
     assert np.array_equal(u32(sv), rv)
 
 
+@pytest.mark.parametrize("m,tile_bits,ties", [(1, 0, False), (2, 4, True), (3, 12, False), (4, 12, True),
+                                               (4095, 8, True), (4096, 12, False), (4097, 12, True),
+                                               (4099, 13, False), (8195, 13, True), (1_000_003, 12, True),
+                                               (3_000_001, 13, False), (1_500_007, 32, False)])
+def test_sort_pairs_onesweep(ctx, oracle, m, tile_bits, ties):
+    """The default tdgs_sort_pairs (onesweep: one histogram launch, then one
+    look-back pass per digit) at ragged sizes: fewer than four pairs (no
+    bulk copy), a ragged last tile with 1-3 pairs read by plain loads, and
+    more tiles than resident CTAs (several tiles per CTA)."""
+    k, v = _random_pairs(m, 7 * m + tile_bits, 32 + tile_bits if tile_bits < 32 else 63, ties)
+    if tile_bits == 32:
+        k |= np.uint64(1) << np.uint64(63)
+    _, rk, rv = oracle.sort_pairs(k, v)
+    kt = torch.from_numpy(k.view(np.int64)).to(DEV)
+    vt = torch.from_numpy(v.view(np.int32)).to(DEV)
+    sk, sv = ctx.sort_pairs(kt, vt, tile_bits, 0)
+    ctx.sync()
+    assert np.array_equal(u64(sk), rk)
+    assert np.array_equal(u32(sv), rv)
+
+
+def test_sort_pairs_onesweep_skewed_and_repeated(ctx, oracle):
+    """All keys equal (one digit takes every pair of every tile), one hot tile
+    with random depths, then sizes that shrink and grow between calls on the
+    same context (the histogram and ticket state must reset itself)."""
+    cases = []
+    m = 300_001
+    cases.append((np.full(m, (5 << 32) | 0x3f800000, dtype=np.uint64), 12))
+    rng = np.random.default_rng(11)
+    hot = (np.uint64(17) << np.uint64(32)) | rng.integers(0x3f000000, 0x42000000, size=m, dtype=np.uint64)
+    cases.append((hot, 12))
+    for mm in (2_000_003, 9_999, 777_777, 5):
+        cases.append((rng.integers(0, 1 << 44, size=mm, dtype=np.uint64), 12))
+    for k, tb in cases:
+        v = rng.permutation(len(k)).astype(np.uint32)
+        _, rk, rv = oracle.sort_pairs(k, v)
+        sk, sv = ctx.sort_pairs(torch.from_numpy(k.view(np.int64)).to(DEV),
+                                torch.from_numpy(v.view(np.int32)).to(DEV), tb, 0)
+        ctx.sync()
+        assert np.array_equal(u64(sk), rk)
+        assert np.array_equal(u32(sv), rv)
+
+
 @pytest.mark.parametrize("m", [5, 70_001])
 def test_sort_pairs_keys_8_byte_aligned(ctx, oracle, m):
     """Keys that start 8 bytes past a 16-byte boundary (allowed by the ABI)
-    take the scalar histogram path of the first pass."""
+    cannot arrive by bulk copies: the sort takes the chunked pass kernels
+    (and the scalar histogram path of their first pass)."""
     k, v = _random_pairs(m, 99 + m, 44, True)
     _, rk, rv = oracle.sort_pairs(k, v)
     kt = torch.zeros(m + 1, dtype=torch.int64, device=DEV)
