@@ -51,7 +51,7 @@ struct TileBuf {
   uint32_t v[kTileKeys];
 };
 constexpr size_t kWhBytes = static_cast<size_t>(kWarps) * kBins * 2;  // per-warp 16-bit counters
-constexpr size_t kSmem = 2 * sizeof(TileBuf) + kWhBytes + 2 * kBins * 4;
+constexpr size_t kSmem = 2 * sizeof(TileBuf) + kWhBytes + 3 * kBins * 4;
 
 // Digit of one key for one pass: bits [shift, shift + width) of the key,
 // or of (tile bits : depth bits 30..0) when bit 31 is dropped.  The host
@@ -61,21 +61,30 @@ struct Digit {
   uint32_t hi_only;  // the digit lies in the high word
   uint32_t lo_shl;   // 1 when bit 31 is dropped (lo' = lo << 1), else 0
   uint32_t mask;
+  uint32_t mode;     // kDigitLo / kDigitHi: the digit is a bit field of one word at msh
+  uint32_t msh;
 };
+constexpr int kDigitLo = 0, kDigitHi = 1, kDigitAny = 2;
 __device__ __forceinline__ uint32_t digit(uint64_t k, const Digit& g) {
   const uint32_t lo = static_cast<uint32_t>(k) << g.lo_shl, hi = static_cast<uint32_t>(k >> 32);
   const uint32_t d = g.hi_only ? (hi >> g.sh) : __funnelshift_r(lo, hi, g.sh);
   return d & g.mask;
 }
+// The same digit when the pass's field lies in one word (most passes).
+template <int kMode>
+__device__ __forceinline__ uint32_t digit_m(uint64_t k, const Digit& g) {
+  if constexpr (kMode == kDigitLo) return (static_cast<uint32_t>(k) >> g.msh) & g.mask;
+  if constexpr (kMode == kDigitHi) return (static_cast<uint32_t>(k >> 32) >> g.msh) & g.mask;
+  return digit(k, g);
+}
 
 struct HistArgs {
   uint32_t m, passes, ntiles;
-  uint32_t drop31;               // sorted key = (tile bits : depth bits 30..0)
-  uint32_t mask[kMaxPasses];     // digit p = bits [p * width, p * width + width) & mask[p]
+  Digit dg[kMaxPasses];
   uint64_t bad_mask;   // key bits that must be zero
   uint32_t* hist;      // [kMaxPasses][kBins], zero on entry, left zero
   uint32_t* gstart;    // [kMaxPasses][kBins] digit starts (exclusive scan of hist)
-  uint32_t* done;      // CTA counter, zero on entry, left zero
+  uint32_t* done;      // block counter, zero on entry, left zero
   uint32_t* tickets;   // [kMaxPasses] tile tickets, cleared here
   uint32_t* status0;   // [ntiles][kBins] look-back status of pass 0, cleared here
   uint32_t* err;
@@ -84,7 +93,10 @@ struct HistArgs {
 struct PassArgs {
   uint32_t m, ntiles;
   Digit dg;
-  const uint32_t* gstart;  // [kBins] this pass's digit starts
+  Digit dgn;               // the next pass's digit (counted while ranking)
+  const uint32_t* gstart;  // [kBins] this pass's digit starts (pass 0), or null
+  const uint32_t* hist;    // [kBins] this pass's digit counts (later passes; gstart is null)
+  uint32_t* hist_next;     // [kBins] the next pass's digit counts, accumulated here (or null)
   uint32_t* status;        // [ntiles][kBins] this pass's status (all zero on entry)
   uint32_t* status_next;   // [ntiles][kBins] the next pass's, cleared here (or null)
   uint32_t* ticket;        // zero on entry
@@ -92,63 +104,75 @@ struct PassArgs {
 };
 
 // ----------------------------------------------------------- histograms
-// kW: the digit width of every pass but the last (8 or 9 for 31..64 key
-// bits), so that each pass's digit comes from a shift by a constant.
-template <int kW>
-__global__ void __launch_bounds__(256) k_onesweep_hist(const uint64_t* __restrict__ keys, HistArgs a) {
-  __shared__ uint32_t h[kMaxPasses * kBins];
-  __shared__ uint32_t s_warp[8];
+// Digit counts of the first pass (each pass counts the next one's digits
+// while it ranks).  Thread t of a block reads 8 consecutive keys (64
+// bytes; a warp reads 2 KB contiguously) and adds runs of equal digits with
+// one shared-memory atomic each: duplicated keys come in runs (one
+// Gaussian's tiles share its depth).  The block's next chunk is prefetched
+// into L2 while it counts.  Few blocks (4 per SM) keep the final global
+// atomics on the counters few.
+constexpr int kHistThreads = 512;
+__global__ void __launch_bounds__(kHistThreads) k_onesweep_hist(const uint64_t* __restrict__ keys, HistArgs a) {
+  __shared__ uint32_t h[kBins];
+  __shared__ uint32_t s_warp[kHistThreads / 32];
   __shared__ bool s_last;
   const uint32_t t = threadIdx.x;
-  const uint32_t np = a.passes;
-  for (uint32_t i = t; i < np * kBins; i += 256) h[i] = 0;
-  // housekeeping for the passes: tickets and pass 0's look-back status
-  if (blockIdx.x == 0 && t < kMaxPasses) a.tickets[t] = 0;
+  for (uint32_t i = t; i < kBins; i += kHistThreads) h[i] = 0;
+  // housekeeping for the passes: tile tickets, later passes' counters,
+  // pass 0's look-back status
+  if (blockIdx.x == 0) {
+    if (t < kMaxPasses) a.tickets[t] = 0;
+    for (uint32_t i = kBins + t; i < kMaxPasses * kBins; i += kHistThreads) a.hist[i] = 0;
+  }
   {
     uint4* z = reinterpret_cast<uint4*>(a.status0);
     const size_t nz = static_cast<size_t>(a.ntiles) * kBins / 4;
-    for (size_t i = static_cast<size_t>(blockIdx.x) * 256 + t; i < nz; i += static_cast<size_t>(gridDim.x) * 256)
+    for (size_t i = static_cast<size_t>(blockIdx.x) * kHistThreads + t; i < nz;
+         i += static_cast<size_t>(gridDim.x) * kHistThreads)
       z[i] = make_uint4(0, 0, 0, 0);
   }
   __syncthreads();
-  // This CTA's chunk, cut into one contiguous run per thread (lanes far
-  // apart in the input rarely share a digit, so the shared-memory atomics
-  // of one warp seldom collide); 32-byte steps keep whole sectors per load.
   const uint32_t m = a.m;
-  const uint64_t per_cta = ((static_cast<uint64_t>(m) + gridDim.x - 1) / gridDim.x + 3) & ~3ull;
-  const uint64_t cb = blockIdx.x * per_cta;
-  const uint32_t beg = static_cast<uint32_t>(cb < m ? cb : m);
-  const uint32_t end = static_cast<uint32_t>(cb + per_cta < m ? cb + per_cta : m);
-  const uint32_t len = end - beg;
-  const uint32_t per_thr = ((len + 255) / 256 + 3) & ~3u;
-  const uint32_t tb = min(beg + t * per_thr, end), te = min(tb + per_thr, end);
+  const uint32_t mask0 = a.dg[0].mask;  // the first digit is bits [0, width) of the key's low word
+  const bool vec = (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
+  constexpr uint32_t kStep = 8 * kHistThreads;  // keys per block and step: 8 consecutive per thread
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kStep;
   bool bad = false;
-  const bool d31 = a.drop31 != 0;
-  auto count = [&](uint64_t k) {
-    bad |= (k & a.bad_mask) != 0;
-    const uint64_t e = d31 ? ((k & 0x7fffffffull) | ((k >> 32) << 31)) : k;
+  for (uint64_t base = static_cast<uint64_t>(blockIdx.x) * kStep; base < m; base += stride) {
+    if (t == 0 && base + stride < m)  // the next step's keys into L2 while this step counts
+      radix::prefetch_l2(keys + base + stride, (min(static_cast<uint64_t>(kStep), m - (base + stride))) * 8);
+    const uint64_t i0 = base + 8 * t;
+    uint64_t k[8];
+    if (vec && i0 + 8 <= m) {
 #pragma unroll
-    for (uint32_t p = 0; p < kMaxPasses; ++p)
-      if (p < np) atomicAdd(&h[p * kBins + (static_cast<uint32_t>(e >> (p * kW)) & a.mask[p])], 1u);
-  };
-  uint32_t i = tb;
-  if ((reinterpret_cast<uintptr_t>(keys) & 15u) == 0) {
-    constexpr uint32_t kU = 4;  // 32-byte steps in flight per thread
-    for (; i + 4 * kU <= te; i += 4 * kU) {
-      uint4 w[2 * kU];
+      for (int u = 0; u < 4; ++u) {
+        const uint4 w = __ldcs(reinterpret_cast<const uint4*>(keys + i0) + u);
+        k[2 * u] = (static_cast<uint64_t>(w.y) << 32) | w.x;
+        k[2 * u + 1] = (static_cast<uint64_t>(w.w) << 32) | w.z;
+      }
+    } else {
 #pragma unroll
-      for (uint32_t u = 0; u < 2 * kU; ++u) w[u] = __ldcs(reinterpret_cast<const uint4*>(keys + i) + u);
+      for (int j = 0; j < 8; ++j) k[j] = i0 + j < m ? keys[i0 + j] : 0ull;
+    }
+    uint32_t run_d = 0, run_n = 0;  // runs of equal digits: one atomic each
 #pragma unroll
-      for (uint32_t u = 0; u < 2 * kU; ++u) {
-        count((static_cast<uint64_t>(w[u].y) << 32) | w[u].x);
-        count((static_cast<uint64_t>(w[u].w) << 32) | w[u].z);
+    for (int j = 0; j < 8; ++j) {
+      if (i0 + j < m) {
+        bad |= (k[j] & a.bad_mask) != 0;
+        const uint32_t d = static_cast<uint32_t>(k[j]) & mask0;
+        if (run_n && d != run_d) {
+          atomicAdd(&h[run_d], run_n);
+          run_n = 0;
+        }
+        run_d = d;
+        ++run_n;
       }
     }
+    if (run_n) atomicAdd(&h[run_d], run_n);
   }
-  for (; i < te; ++i) count(keys[i]);
   if (__any_sync(0xffffffffu, bad) && lane_id() == 0) latch_error(a.err, TDGS_ERR_INVALID_ARGUMENT, kSiteRadixKeys);
   __syncthreads();
-  for (uint32_t q = t; q < np * kBins; q += 256)
+  for (uint32_t q = t; q < kBins; q += kHistThreads)
     if (h[q]) atomicAdd(a.hist + q, h[q]);
   __threadfence();
   __syncthreads();
@@ -156,15 +180,11 @@ __global__ void __launch_bounds__(256) k_onesweep_hist(const uint64_t* __restric
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  // last CTA: digit starts of every pass, then leave hist and done zero
-  for (uint32_t p = 0; p < np; ++p) {
-    const uint32_t c0 = __ldcg(a.hist + p * kBins + 2 * t), c1 = __ldcg(a.hist + p * kBins + 2 * t + 1);
-    const uint32_t s0 = radix::block_excl_scan<8>(c0 + c1, s_warp);
-    a.gstart[p * kBins + 2 * t] = s0;
-    a.gstart[p * kBins + 2 * t + 1] = s0 + c0;
-    a.hist[p * kBins + 2 * t] = 0;
-    a.hist[p * kBins + 2 * t + 1] = 0;
-  }
+  // last block: the first pass's digit starts; leave its counters and the
+  // block counter zero
+  const uint32_t c = __ldcg(a.hist + t);
+  a.gstart[t] = radix::block_excl_scan<kHistThreads / 32>(c, s_warp);
+  a.hist[t] = 0;
   if (t == 0) *a.done = 0;
 }
 
@@ -266,8 +286,10 @@ constexpr uint32_t kScanCtas = 8;
 constexpr uint32_t kSegRows = 8;  // rows per warp and round
 static_assert(kBins == 64 * kScanCtas && kWarps * kSegRows == 64, "scan layout");
 __device__ __forceinline__ void scan_tiles(uint32_t* __restrict__ status, uint32_t ntiles, uint32_t c,
-                                           uint32_t* err) {
-  __shared__ uint32_t s_stop[kWarps][32], s_sum0[kWarps][32], s_sum1[kWarps][32];
+                                           uint32_t* err, uint32_t* sm) {
+  uint32_t(*s_stop)[32] = reinterpret_cast<uint32_t(*)[32]>(sm);
+  uint32_t(*s_sum0)[32] = reinterpret_cast<uint32_t(*)[32]>(sm + kWarps * 32);
+  uint32_t(*s_sum1)[32] = reinterpret_cast<uint32_t(*)[32]>(sm + 2 * kWarps * 32);
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   uint32_t* col = status + 64 * c + 2 * lane;
   uint32_t k = 0, run0 = 0, run1 = 0, idle = 0;  // per pair: first row not consumed, its sums
@@ -363,8 +385,9 @@ __device__ __forceinline__ void wait_prefix(const uint32_t* __restrict__ status,
 // Stable rank of one tile held in shared memory (tile order: warp, item,
 // lane): r[j] = number of earlier items of this warp with the same digit;
 // the warp's counter row (zero on entry) ends holding its count per digit.
+template <int kMode>
 __device__ __forceinline__ void rank_in_warps(const TileBuf& tb, uint32_t valid, const Digit& dg, uint16_t* my_wh,
-                                              uint32_t (&r)[kItems]) {
+                                              uint32_t (&r)[kItems], const Digit& dgn, uint32_t* hn) {
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t wbase = warp * 32 * kItems;
   const uint32_t lt = lanemask_lt();
@@ -374,7 +397,9 @@ __device__ __forceinline__ void rank_in_warps(const TileBuf& tb, uint32_t valid,
 #pragma unroll
     for (int g = 0; g < kGroup; ++g) {
       const uint32_t idx = wbase + (j0 + g) * 32 + lane;
-      d[g] = digit(idx < valid ? tb.k[idx] : 0ull, dg);
+      const uint64_t key = idx < valid ? tb.k[idx] : 0ull;
+      d[g] = digit_m<kMode>(key, dg);
+      if (hn && idx < valid) atomicAdd(&hn[digit(key, dgn)], 1u);
       r[j0 + g] = radix::equal_digit_lanes<kBits>(d[g]);
       const uint32_t fi = wbase + (j0 + g) * 32;
       const uint32_t nlive = valid > fi ? min(valid - fi, 32u) : 0u;
@@ -402,7 +427,9 @@ __device__ __forceinline__ void rank_in_warps(const TileBuf& tb, uint32_t valid,
 // went out, so the scan has (nearly always) produced it.  Ranking never
 // waits for another CTA, so every tile with a ticket publishes its counts
 // and the scan always completes.  Launched cooperatively: the scan CTAs
-// must run alongside every other CTA.
+// must run alongside every other CTA.  While ranking, the CTA also counts
+// the next pass's digits; the counts reach hist_next when it finishes.
+template <int kMode>
 __global__ void __launch_bounds__(kThreads, 2)
     k_onesweep_pass(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
                     uint32_t* __restrict__ vout, PassArgs a) {
@@ -411,6 +438,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   uint16_t* wh = reinterpret_cast<uint16_t*>(smem + 2 * sizeof(TileBuf));
   uint32_t* lstart = reinterpret_cast<uint32_t*>(smem + 2 * sizeof(TileBuf) + kWhBytes);
   uint32_t* off = lstart + kBins;
+  uint32_t* hn = a.hist_next ? off + kBins : nullptr;  // next pass's digit counts of this CTA
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t s_tile[2];
   __shared__ uint32_t s_warp[kWarps];
@@ -418,7 +446,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
   const uint32_t m = a.m, ntiles = a.ntiles;
   if (blockIdx.x >= gridDim.x - kScanCtas) {  // a scan CTA
-    scan_tiles(a.status, ntiles, blockIdx.x - (gridDim.x - kScanCtas), a.err);
+    scan_tiles(a.status, ntiles, blockIdx.x - (gridDim.x - kScanCtas), a.err, reinterpret_cast<uint32_t*>(smem));
     return;
   }
   const Digit dg = a.dg;
@@ -427,7 +455,19 @@ __global__ void __launch_bounds__(kThreads, 2)
     uint4* z = reinterpret_cast<uint4*>(wh);
     for (uint32_t i = t; i < kWhBytes / 16; i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
   }
-  const uint32_t g0 = __ldg(a.gstart + 2 * t), g1 = __ldg(a.gstart + 2 * t + 1);
+  if (hn) {
+    hn[2 * t] = 0;
+    hn[2 * t + 1] = 0;
+  }
+  uint32_t g0, g1;  // this pass's first output position of digits 2t and 2t+1
+  if (a.gstart) {
+    g0 = __ldg(a.gstart + 2 * t);
+    g1 = __ldg(a.gstart + 2 * t + 1);
+  } else {
+    const uint32_t h0 = __ldcg(a.hist + 2 * t), h1 = __ldcg(a.hist + 2 * t + 1);
+    g0 = cta_excl_scan(h0 + h1, s_warp);
+    g1 = g0 + h0;
+  }
   auto bulk_items = [&](uint32_t tile) {
     const uint32_t first = tile * kTileKeys;
     const uint32_t valid = min(kTileKeys, m - first);
@@ -485,7 +525,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       // ---- stable rank within each warp
       uint32_t r[kItems];
-      rank_in_warps(tb, valid, dg, my_wh, r);
+      rank_in_warps<kMode>(tb, valid, dg, my_wh, r, a.dgn, hn);
       if (t == 0 && nxt < ntiles) {
         const uint32_t nf = nxt * kTileKeys, nv = min(kTileKeys, m - nf);
         radix::prefetch_l2(kin + nf, static_cast<uint64_t>(nv) * 8);
@@ -521,7 +561,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (idx < valid) {
           kr[j] = tb.k[idx];
           vr[j] = tb.v[idx];
-          const uint32_t dd = digit(kr[j], dg);
+          const uint32_t dd = digit_m<kMode>(kr[j], dg);
           r[j] += lstart[dd] + my_wh[dd];
         }
       }
@@ -557,7 +597,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const uint32_t p = i * kThreads + t;
         if (p < pvalid) {
           const uint64_t key = pb.k[p];
-          const uint32_t dst = off[digit(key, dg)] + p;
+          const uint32_t dst = off[digit_m<kMode>(key, dg)] + p;
           if (dst < m) {
             kout[dst] = key;
             vout[dst] = pb.v[p];
@@ -583,6 +623,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     cur = s_tile[b];
   }
   if (!ok) latch_error(a.err, TDGS_ERR_CAPACITY, kSiteRadixRange);
+  if (hn) {  // this CTA's counts of the next pass's digits
+    __syncthreads();
+    for (uint32_t i = t; i < kBins; i += kThreads)
+      if (hn[i]) atomicAdd(a.hist_next + i, hn[i]);
+  }
 }
 
 
@@ -598,7 +643,7 @@ uint32_t pass_grid() {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_grid[dev]) {
-    const void* fn = reinterpret_cast<const void*>(&onesweep::k_onesweep_pass);
+    const void* fn = reinterpret_cast<const void*>(&onesweep::k_onesweep_pass<onesweep::kDigitAny>);
     int sms = 0, occ = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(onesweep::kSmem)) !=
@@ -619,6 +664,20 @@ onesweep::Digit make_digit(uint32_t shift, uint32_t mask, bool drop31) {
   d.hi_only = s >= 32 ? 1u : 0u;
   d.sh = s >= 32 ? s - 32 : s;
   d.mask = mask;
+  // one-word digits: bits [0, 31) (or [0, 32) without the drop) are the
+  // low word's; bits from 31 on (32 on) are the high word's
+  const uint32_t width = static_cast<uint32_t>(__builtin_popcount(mask));
+  const uint32_t split = drop31 ? 31u : 32u;
+  if (shift + width <= split) {
+    d.mode = onesweep::kDigitLo;
+    d.msh = shift;
+  } else if (shift >= split) {
+    d.mode = onesweep::kDigitHi;
+    d.msh = shift - split;
+  } else {
+    d.mode = onesweep::kDigitAny;
+    d.msh = 0;
+  }
   return d;
 }
 }  // namespace
@@ -646,13 +705,9 @@ cudaError_t launch_onesweep_hist(const SortPlan& plan, const uint64_t* keys, uin
   using namespace onesweep;
   HistArgs a{};
   a.m = m;
-  a.passes = plan.passes;
+  a.passes = 1;  // the first pass's digits; each pass counts the next one's
   a.ntiles = (m + kTileKeys - 1) / kTileKeys;
-  a.drop31 = plan.drop31 ? 1u : 0u;
-  for (uint32_t p = 0; p < plan.passes; ++p) {
-    if (plan.shift[p] != p * plan.digit_bits) return cudaErrorInvalidValue;
-    a.mask[p] = plan.mask[p];
-  }
+  a.dg[0] = make_digit(plan.shift[0], plan.mask[0], plan.drop31);
   a.bad_mask = plan.bad_mask;
   a.hist = scratch;
   a.gstart = scratch + kMaxPasses * kBins;
@@ -663,17 +718,12 @@ cudaError_t launch_onesweep_hist(const SortPlan& plan, const uint64_t* keys, uin
   int sms = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return cudaErrorInvalidDevice;
-  // about 32 KB of keys per thread block, at most 4 blocks per SM
-  uint32_t grid = (m + 4095) / 4096;
+  // 32 KB of keys per block and step, 4 blocks per SM
+  uint32_t grid = (m + 8 * kHistThreads - 1) / (8 * kHistThreads);
   const uint32_t cap = static_cast<uint32_t>(sms) * 4;
   if (grid > cap) grid = cap;
   if (grid == 0) grid = 1;
-  switch (plan.digit_bits) {
-    case 9: k_onesweep_hist<9><<<grid, 256, 0, s>>>(keys, a); break;
-    case 8: k_onesweep_hist<8><<<grid, 256, 0, s>>>(keys, a); break;
-    case 7: k_onesweep_hist<7><<<grid, 256, 0, s>>>(keys, a); break;
-    default: return cudaErrorInvalidValue;
-  }
+  k_onesweep_hist<<<grid, kHistThreads, 0, s>>>(keys, a);
   return cudaGetLastError();
 }
 
@@ -687,7 +737,14 @@ cudaError_t launch_onesweep_pass(const SortPlan& plan, uint32_t pass, const uint
   a.m = m;
   a.ntiles = (m + kTileKeys - 1) / kTileKeys;
   a.dg = make_digit(plan.shift[pass], plan.mask[pass], plan.drop31);
-  a.gstart = scratch + kMaxPasses * kBins + pass * kBins;
+  if (pass + 1 < plan.passes) {
+    a.dgn = make_digit(plan.shift[pass + 1], plan.mask[pass + 1], plan.drop31);
+    a.hist_next = scratch + (pass + 1) * kBins;
+  }
+  if (pass == 0)
+    a.gstart = scratch + kMaxPasses * kBins;
+  else
+    a.hist = scratch + pass * kBins;
   a.ticket = scratch + 2 * kMaxPasses * kBins + 4 + pass;
   uint32_t* st = scratch + onesweep_header_words();
   const size_t rows = static_cast<size_t>(a.ntiles) * kBins;
@@ -708,7 +765,12 @@ cudaError_t launch_onesweep_pass(const SortPlan& plan, uint32_t pass, const uint
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(&k_onesweep_pass), args);
+  const void* fn = a.dg.mode == kDigitLo   ? reinterpret_cast<const void*>(&k_onesweep_pass<kDigitLo>)
+                   : a.dg.mode == kDigitHi ? reinterpret_cast<const void*>(&k_onesweep_pass<kDigitHi>)
+                                           : reinterpret_cast<const void*>(&k_onesweep_pass<kDigitAny>);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmem)) != cudaSuccess)
+    return cudaErrorInvalidConfiguration;
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 }  // namespace tdgs
