@@ -480,6 +480,12 @@ def run_batched(args, local_rank):
     per_view = [a.elapsed_time(b) for a, b in ms_view[2 * len(gs):]]
     res = ctx.sort_views(views)
     m_total = sum(r[3] for r in res)
+    view_pairs = [r[3] for r in res]
+    # the batch's knobs (digit width of the tile passes, CTAs per SM, depth
+    # digit width) from the autotuner, measured on this batch
+    from paper_2511_16298_gb300 import autotune
+    tuned = autotune.tune_views(ctx, views, reps=2)
+    ctx.apply_tuning(tuned["best"])
     t_batch = timed(lambda: ctx.sort_views(views), reps)
     ctx.reserve_views(views, int(m_total * 1.1) + 1024)
     graph = torch.cuda.CUDAGraph()
@@ -498,12 +504,74 @@ def run_batched(args, local_rank):
         return {"pairs_per_s": m_total / (statistics.median(ts) * 1e-3), "p50_ms": round(statistics.median(ts), 4),
                 "p99_ms": round(float(np.percentile(ts, 99)), 4)}
     ms = [r[3] for r in res]
-    return {"workload": "64 pinhole cameras (1280x720) of one 500,000-Gaussian scene, seed 0",
+    return {"workload": "64 pinhole cameras (1280x720) of one 500,000-Gaussian scene at distances "
+                        "log-uniform in 3.75-15 and look-at jitter up to 8, scale 0.05, seed 0",
             "views": len(gs), "pairs_total": m_total, "pairs_per_view_min": min(ms),
-            "pairs_per_view_max": max(ms), "plain_per_view_loop": summ(t_plain),
+            "pairs_per_view_max": max(ms),
+            "pairs_per_view_p10_p50_p90": [int(x) for x in np.percentile(view_pairs, [10, 50, 90])],
+            "knobs": tuned["best"], "knobs_ms": round(tuned["ms"], 4),
+            "plain_per_view_loop": summ(t_plain),
             "plain_view_latency_ms": {"p50": round(statistics.median(per_view), 4),
                                       "p99": round(float(np.percentile(per_view, 99)), 4)},
             "batched": summ(t_batch), "batched_graph": summ(t_graph)}
+
+
+# ------------------------------------------------- the 10k-Gaussian frame
+def run_small(args, local_rank):
+    """The 10,000-Gaussian 256x256 frame (256 tiles): latency of
+    tdgs_sort_frame (CUDA events, 200 steps after 10 warm-ups), and the same
+    through host buffers (records from pinned memory, keys, values and ranges
+    back to pinned memory, one frame at a time).  Everything fits in L2 and
+    the frame is launch-bound, so no roofline fraction is given."""
+    import torch
+
+    from paper_2511_16298_gb300 import synth, tdgs
+
+    dev = torch.device("cuda", local_rank)
+    fr = synth.frame_small(0)
+    g = tdgs.records_to_tensor(fr.gaussians, dev)
+    ctx = tdgs.Context(local_rank)
+    stream = torch.cuda.current_stream(dev)
+    steps, warm = 200, 10
+    for _ in range(warm):
+        ctx.sort_frame(g, fr.width, fr.height)
+    ctx.sync()
+    l0 = ctx.launches
+    ts = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        k, v, rg, m = ctx.sort_frame(g, fr.width, fr.height)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ts.append(a.elapsed_time(b))
+    launches = (ctx.launches - l0) / steps
+    # host to host: pinned records in, sorted pairs and ranges out
+    hrec = torch.from_numpy(np.ascontiguousarray(fr.gaussians).view(np.int32).reshape(-1, 4)).pin_memory()
+    drec = torch.empty_like(hrec, device=dev)
+    hk = torch.empty(m, dtype=torch.int64).pin_memory()
+    hv = torch.empty(m, dtype=torch.int32).pin_memory()
+    hr = torch.empty(rg.shape, dtype=torch.int32).pin_memory()
+    te = []
+    for i in range(steps + warm):
+        t0 = time.perf_counter()
+        drec.copy_(hrec, non_blocking=True)
+        k, v, rg, mm = ctx.sort_frame(drec, fr.width, fr.height)
+        hk[:mm].copy_(k, non_blocking=True)
+        hv[:mm].copy_(v, non_blocking=True)
+        hr.copy_(rg, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        if i >= warm:
+            te.append((time.perf_counter() - t0) * 1e3)
+    ctx.close()
+    return {"workload": "small-10k: 10,000 projected Gaussians, 256x256 image, 256 tiles, seed 0",
+            "pairs": m, "steps": steps, "warmup": warm, "launches_per_frame": launches,
+            "device_ms": {"p50": round(statistics.median(ts), 4), "p99": round(float(np.percentile(ts, 99)), 4),
+                          "mean": round(statistics.mean(ts), 4)},
+            "host_to_host_ms": {"p50": round(statistics.median(te), 4),
+                                "p99": round(float(np.percentile(te, 99)), 4)},
+            "pairs_per_s_p50": m / (statistics.median(ts) * 1e-3),
+            "roofline": "not meaningful: the frame's 0.7 MB of pairs stay in L2; launch-bound"}
 
 
 # ------------------------------------------------- the 3M-Gaussian frame
@@ -698,47 +766,107 @@ def run_frame3d(args, local_rank):
 
 # ------------------------------------------------------- served requests
 def run_served(args, local_rank):
-    """Poisson request stream (200 req/s): frames of 100k-3M Gaussians at
-    640x360 / 1280x720 / 1920x1080, 40 GB HBM budget, replayed in wall
-    time, plain (one request per launch, one slot) against continuous
-    batching (two slots); then a closed-loop burst to saturate."""
+    """Poisson request stream (200 req/s, the whole trace): frames of
+    100k-3M Gaussians at 640x360 / 1280x720 / 1920x1080, 40 GB HBM budget,
+    every result downloaded to pinned host memory before its latency is
+    taken.  Plain (one request per launch, one slot) against continuous
+    batching (two slots, the measured cost model decides which queued
+    requests run together, knobs from a tuning table made at start-up);
+    each replayed in wall time and as a closed-loop burst, three times,
+    medians reported."""
     import torch
 
-    from paper_2511_16298_gb300 import serve, synth
+    from paper_2511_16298_gb300 import autotune, serve, synth
 
     trace = synth.request_trace(seed=0, count=args.serve_requests)
-    frames = [r.frame() for r in trace]
-    host = [torch.from_numpy(np.ascontiguousarray(f.gaussians).view(np.int32).reshape(-1, 4)).pin_memory()
-            for f in frames]
-    out = {"workload": f"first {len(trace)} requests of a seed-0 Poisson trace at 200 req/s "
-                       "(N log-uniform in [1e5, 3e6]), 40 GB HBM budget"}
-    for name, batching, slots in (("plain", False, 1), ("batched", True, 2)):
+    base_n = 3_000_000
+    pool = {k: torch.from_numpy(v.view(np.int32).reshape(-1, 4)).pin_memory()
+            for k, v in synth.request_pool(base_n).items()}
+    reqs = []
+    for r in trace:
+        w = r.window(base_n)
+        reqs.append((r, pool[(r.width, r.height)][w:w + r.n]))
+
+    def mkreq(i):
+        r, h = reqs[i]
+        return serve.Request(-1, h, r.n, r.width, r.height, 0, time.perf_counter(), None)
+
+    # the cost model, measured: single frames of each size class and
+    # batches of each element form
+    by_size = sorted(range(len(reqs)), key=lambda i: reqs[i][0].n)
+    small = [i for i in by_size if reqs[i][0].n < 300_000][:4]
+    mid720 = [i for i in by_size if reqs[i][0].width == 1280 and 700_000 < reqs[i][0].n < 1_000_000][:2]
+    big = [by_size[-1]]
+    cal = [[mkreq(i)] for i in small[:1] + mid720[:1] + big]
+    cal += [[mkreq(i) for i in small], [mkreq(i) for i in mid720], [mkreq(big[0]), mkreq(small[0])]]
+    ex = serve.GpuExecutor(local_rank, slots=1, download=True)
+    cm = ex.calibrate(cal)
+    # tuning table for the batch shapes the cost model forms most: the
+    # small-frame batch and the large frame alone
+    table = autotune.Table("")  # made here, not stored
+    tv_small = [(ex._buffer(0, k, reqs[i][0].n).copy_(reqs[i][1]), reqs[i][0].width, reqs[i][0].height)
+                for k, i in enumerate(small)]
+    table.record(autotune.tune_views(ex.ctx[0], tv_small, reps=2))
+    tv_big = [(ex._buffer(0, 0, reqs[big[0]][0].n).copy_(reqs[big[0]][1]), reqs[big[0]][0].width,
+               reqs[big[0]][0].height)]
+    table.record(autotune.tune_views(ex.ctx[0], tv_big, reps=2))
+    ex.close()
+
+    out = {"workload": f"the {len(trace)} requests of a seed-0 Poisson trace at 200 req/s "
+                       "(N log-uniform in [1e5, 3e6], resolutions 640x360/1280x720/1920x1080; frames are "
+                       "seeded windows of three 3M-Gaussian base frames), 40 GB HBM budget, results "
+                       "downloaded to pinned host memory inside the latency",
+           "cost_model": {"overhead_us": round(cm.overhead_s * 1e6, 1),
+                          "pair_ps_32bit": round(cm.pair_s_narrow * 1e12, 2),
+                          "pair_ps_64bit": round(cm.pair_s_wide * 1e12, 2),
+                          "pairs_per_gaussian": round(cm.pairs_per_gaussian, 2)},
+           "tuning_table": table.entries}
+    reps = 3
+
+    def replay(s, mode):
+        t0 = time.perf_counter()
+        futs = []
+        for r, h in reqs:
+            if mode == "trace":
+                dt = t0 + r.arrival_s - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+            futs.append(s.submit(r.rid, h, r.n, r.width, r.height))
+        res = [fu.result(timeout=600) for fu in futs]
+        return res, time.perf_counter() - t0
+
+    configs = [("plain", False, 1, False), ("batched", True, 2, True)]
+    if os.environ.get("TDGS_SERVE_UNTUNED"):
+        configs.append(("batched_untuned", True, 2, False))
+    for name, batching, slots, tuned in configs:
+        # one executor per configuration, its device buffers and pinned
+        # staging grown to steady state by an untimed burst of the whole trace
+        ex = serve.GpuExecutor(local_rank, slots=slots, download=True, table=table if tuned else None)
+        kw = dict(slots=slots, hbm_budget=40 << 30, max_batch=16, batching=batching,
+                  policy=cm.joins if batching else None)
+        with serve.Server(ex, **kw) as s:
+            replay(s, "burst")
+        torch.cuda.synchronize()
         for mode in ("trace", "burst"):
-            ex = serve.GpuExecutor(local_rank, slots=slots)
-            # warm the slots' buffers with the largest frame
-            big = int(np.argmax([f.n for f in frames]))
-            for sl in range(slots):
-                ex(sl, [serve.Request(-1, host[big], frames[big].n, frames[big].width,
-                                      frames[big].height, 0, time.perf_counter(), None)])
-            torch.cuda.synchronize()
-            with serve.Server(ex, slots=slots, hbm_budget=40 << 30, max_batch=16, batching=batching,
-                              policy=serve.narrow_batches if batching else None) as s:
-                t0 = time.perf_counter()
-                futs = []
-                for r, h, f in zip(trace, host, frames):
-                    if mode == "trace":
-                        dt = t0 + r.arrival_s - time.perf_counter()
-                        if dt > 0:
-                            time.sleep(dt)
-                    futs.append(s.submit(r.rid, h, f.n, f.width, f.height))
-                res = [fu.result(timeout=600) for fu in futs]
-                wall = time.perf_counter() - t0
-            ex.close()
-            lat = [r.latency_s * 1e3 for r in res]
-            pairs = sum(r.m for r in res)
-            out[f"{name}_{mode}"] = {"pairs_per_s": pairs / wall, "p50_ms": round(statistics.median(lat), 3),
-                                     "p99_ms": round(float(np.percentile(lat, 99)), 3),
-                                     "mean_batch": round(statistics.mean(s.batches), 2), "wall_s": round(wall, 3)}
+            runs = []
+            for _ in range(reps):
+                tuned0 = ex.tuned_batches
+                with serve.Server(ex, **kw) as s:
+                    res, wall = replay(s, mode)
+                    resident = s.resident_bytes()
+                lat = [q.latency_s * 1e3 for q in res]
+                runs.append({"pairs_per_s": sum(q.m for q in res) / wall,
+                             "p50_ms": statistics.median(lat), "p99_ms": float(np.percentile(lat, 99)),
+                             "mean_batch": statistics.mean(s.batches), "wall_s": wall,
+                             "tuned_batches": ex.tuned_batches - tuned0, "resident_gb": resident / 1e9})
+            med = {k: statistics.median(r[k] for r in runs) for k in runs[0]}
+            out[f"{name}_{mode}"] = {
+                "pairs_per_s": med["pairs_per_s"], "p50_ms": round(med["p50_ms"], 3),
+                "p99_ms": round(med["p99_ms"], 3), "mean_batch": round(med["mean_batch"], 2),
+                "wall_s": round(med["wall_s"], 3), "tuned_batches": int(med["tuned_batches"]),
+                "resident_gb": round(med["resident_gb"], 2), "runs": reps,
+                "p99_ms_runs": [round(r["p99_ms"], 3) for r in runs]}
+        ex.close()
     return out
 
 
@@ -789,7 +917,8 @@ def main():
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-bitonic", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--sort-variant", type=int, default=-1,
                     help="pass kernel of the sort-only section (-1: the library's choice)")
     args = ap.parse_args()
@@ -835,6 +964,7 @@ def main():
     served = None if args.no_served else run_served(args, local_rank)
     frame3d = None if args.no_3d else run_frame3d(args, local_rank)
     large = None if args.no_large else run_large(args, local_rank)
+    small = None if args.no_small else run_small(args, local_rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -864,7 +994,7 @@ def main():
             "roofline": res["roofline"], "kernels": res["kernels"], "sort_pairs": res["sort_pairs"],
             "cpu_baseline": cpu, "e2e": res["e2e"], "gpu_launches": res["gpu_launches"],
             "clocks": res["clocks"], "batched_views": batched, "served": served,
-            "frame_3d": frame3d, "large_frame": large,
+            "frame_3d": frame3d, "large_frame": large, "small_frame": small,
         }
         print(json.dumps(out))
     if dist:

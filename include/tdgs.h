@@ -224,7 +224,14 @@ tdgs_status tdgs_duplicate_keys(tdgs_context* ctx, const tdgs_gaussian2d* g,
  * *result_in_alt (host int) tells where the sorted pairs are: 0 = keys/
  * values, 1 = keys_alt/values_alt.  The other pair of buffers is clobbered.
  * tile_bits <= 32.  Keys changed by someone else while the sort runs can
- * send a pair outside [0, m); it is dropped and TDGS_ERR_CAPACITY latched. */
+ * send a pair outside [0, m); it is dropped and TDGS_ERR_CAPACITY latched.
+ * Form: with all four buffers 16-byte aligned and m < 2^30 (and no sort
+ * variant chosen by tdgs_context_set_sort_variant), a onesweep LSD radix sort:
+ * one launch reads the keys once for the first digit's counts, then one
+ * launch per 9-bit digit reads and writes every pair once (its tiles go
+ * through shared memory by bulk copy; scan blocks of the same cooperative
+ * launch turn the tiles' digit counts into prefixes); every other case
+ * takes the chunked per-digit passes.  Both give the same bytes. */
 tdgs_status tdgs_sort_pairs(tdgs_context* ctx, uint64_t* keys, uint32_t* values,
                             uint64_t* keys_alt, uint32_t* values_alt, uint32_t m,
                             uint32_t tile_bits, uint32_t flags, int* result_in_alt,

@@ -173,21 +173,27 @@ def _fibonacci_sphere(k: int) -> np.ndarray:
 
 
 def multiview(seed: int = 0, n: int = 500_000, views: int = 64, width: int = 1280,
-              height: int = 720, scale0: float = 0.03, cam_radius: float = 15.0) -> MultiView:
+              height: int = 720, scale0: float = 0.05, cam_radius: float = 15.0,
+              dist_range: tuple[float, float] = (0.25, 1.0), jitter_radius: float = 8.0) -> MultiView:
     """One scene, many cameras.  Means ~ U[0,1)^3 * 10 - 5; isotropic scale
-    s ~ lognormal(ln scale0, 0.5); cameras on a Fibonacci lattice of a
-    sphere of radius ``cam_radius`` looking at the origin plus a jitter
-    drawn uniformly from a ball of radius 4, up = +y.  Pinhole with
-    fx = fy = 1108.5, principal point at the image centre.  Per view:
-    depth = view-space z, radius 0 (culled) where z <= 0.2, otherwise
-    r = ceil(3 * fx * s / z) and the mean is projected."""
+    s ~ lognormal(ln scale0, 0.5); camera v sits on a Fibonacci lattice of
+    directions at distance cam_radius * f_v, f_v log-uniform in
+    ``dist_range`` (some cameras inside the cube), looking at the origin
+    plus a jitter drawn uniformly from a ball of radius ``jitter_radius``
+    (some look partly away), up = +y.  Pinhole with fx = fy = 1108.5,
+    principal point at the image centre.  Per view: depth = view-space z,
+    radius 0 (culled) where z <= 0.2, otherwise r = ceil(3 * fx * s / z)
+    and the mean is projected.  The defaults spread the views' pair counts
+    over about 0.4M-4.2M (seed 0: 151M pairs in all), the uneven per-view
+    load a batched multi-view sort is for."""
     rng = np.random.default_rng(seed)
     mean3 = rng.random((n, 3)) * 10.0 - 5.0
     scale = rng.lognormal(math.log(scale0), 0.5, size=n)
-    eye = _fibonacci_sphere(views) * cam_radius
     u = rng.normal(size=(views, 3))
     u /= np.linalg.norm(u, axis=1, keepdims=True)
-    jitter = u * (4.0 * rng.random(views) ** (1.0 / 3.0))[:, None]
+    jitter = u * (jitter_radius * rng.random(views) ** (1.0 / 3.0))[:, None]
+    lo, hi = dist_range
+    eye = _fibonacci_sphere(views) * (cam_radius * lo * (hi / lo) ** rng.random(views))[:, None]
     fx = fy = 1108.5
     cx, cy = width / 2.0, height / 2.0
     out = []
@@ -319,6 +325,26 @@ class Request:
     def frame(self) -> Frame:
         """Frame of this request, drawn like the scene-scale frame."""
         return frame_scene(self.seed, self.n, self.width, self.height)
+
+    def window(self, base_n: int) -> int:
+        """First Gaussian of this request's window in a request pool base
+        frame of base_n Gaussians (drawn from the request's seed)."""
+        return int(np.random.default_rng(self.seed).integers(0, base_n))
+
+
+def request_pool(base_n: int = 3_000_000, base_seed: int = 500) -> dict:
+    """Gaussians for a long request stream without generating every frame:
+    per resolution, a base frame drawn like the scene-scale frame
+    (base_seed + resolution index), shuffled, and stored twice in a row, so
+    that a request of n <= base_n Gaussians is the contiguous slice
+    [w, w + n) at its window offset w -- a random subset with the scene
+    frame's distribution.  Returns {(width, height): records (2 * base_n)}."""
+    out = {}
+    for k, (w, h) in enumerate(RESOLUTIONS):
+        fr = frame_scene(base_seed + k, base_n, w, h)
+        g = fr.gaussians[np.random.default_rng(base_seed + 10 + k).permutation(base_n)]
+        out[(w, h)] = np.concatenate([g, g])
+    return out
 
 
 def request_trace(seed: int = 0, count: int = 2000, rate_hz: float = 200.0,
