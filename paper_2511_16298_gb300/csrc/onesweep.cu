@@ -27,22 +27,19 @@
 // against the pair count.
 #include <mutex>
 
-#include "radix.cuh"
+#include "onesweep.cuh"
 
 namespace tdgs {
 namespace onesweep {
 
+using namespace osw;
+
 constexpr int kBits = 9;
 constexpr uint32_t kBins = 1u << kBits;
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
 constexpr int kItems = 16;
 constexpr uint32_t kTileKeys = kThreads * kItems;  // 4096
 constexpr int kGroup = 4;                          // items ranked together (independent ballot chains)
-constexpr uint32_t kFlagA = 1u << 30;              // status: this tile's own count
-constexpr uint32_t kFlagP = 2u << 30;              // status: inclusive prefix over tiles <= this one
-constexpr uint32_t kCountMask = (1u << 30) - 1u;
-constexpr uint32_t kMaxPairs = 1u << 30;           // counts in a status word have 30 bits
+constexpr uint32_t kScanCtas = scan_ctas<kBins>();
 
 static_assert(kBins == 2 * kThreads, "two digits per thread in the look-back and the digit scan");
 
@@ -188,197 +185,16 @@ __global__ void __launch_bounds__(kHistThreads) k_onesweep_hist(const uint64_t* 
   if (t == 0) *a.done = 0;
 }
 
-// ------------------------------------------------------ shared-memory TMA
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
-}
-// One arrival that expects `bytes` of bulk-copy data, then the copies of
-// the tile's keys and values (16-byte aligned, multiples of 16 bytes).
+// One tile's keys and values (first `nbulk` pairs, a multiple of 4) by bulk
+// copies completing on `bar`.
 __device__ __forceinline__ void load_tile(TileBuf* b, uint64_t* bar, const uint64_t* kin, const uint32_t* vin,
                                           uint32_t first, uint32_t nbulk) {
   const uint32_t kb = nbulk * 8, vb = nbulk * 4;
-  if (nbulk == 0) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
-                 : "memory");
-    return;
+  mbar_arrive(bar, kb + vb);
+  if (nbulk) {
+    bulk_g2s(b->k, kin + first, kb, bar);
+    bulk_g2s(b->v, vin + first, vb, bar);
   }
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
-                   smem_addr(bar)),
-               "r"(kb + vb)
-               : "memory");
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_addr(b->k)),
-               "l"(kin + first), "r"(kb), "r"(smem_addr(bar))
-               : "memory");
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_addr(b->v)),
-               "l"(vin + first), "r"(vb), "r"(smem_addr(bar))
-               : "memory");
-}
-// Bounded wait for phase `parity` of `bar`; false (error latched) if the
-// copy did not arrive.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* err) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  latch_error(err, TDGS_ERR_TIMEOUT, kSiteBarrier);
-  return false;
-}
-
-__device__ __forceinline__ uint2 ld_relaxed_v2(const uint32_t* p) {
-  uint2 v;
-  asm volatile("ld.relaxed.gpu.global.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_relaxed_v2(uint32_t* p, uint32_t x, uint32_t y) {
-  asm volatile("st.relaxed.gpu.global.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(x), "r"(y) : "memory");
-}
-
-// ------------------------------------------------ tile prefixes per digit
-// Exclusive sum of v over the CTA.
-__device__ __forceinline__ uint32_t cta_excl_scan(uint32_t v, uint32_t* s_warp) {
-  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  uint32_t x = v;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t o = __shfl_up_sync(0xffffffffu, x, d);
-    if (lane >= static_cast<uint32_t>(d)) x += o;
-  }
-  if (lane == 31) s_warp[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t w = lane < kWarps ? s_warp[lane] : 0u;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t o = __shfl_up_sync(0xffffffffu, w, d);
-      if (lane >= static_cast<uint32_t>(d)) w += o;
-    }
-    if (lane < kWarps) s_warp[lane] = w;
-  }
-  __syncthreads();
-  const uint32_t r = x - v + (warp ? s_warp[warp - 1] : 0u);
-  __syncthreads();
-  return r;
-}
-
-// The scan CTAs: the last kScanCtas CTAs of the grid take no tiles; scan
-// CTA c owns digits [64 c, 64 c + 64).  Lane l of every warp owns digit
-// pair 64 c + 2 l, +1; warp w reads rows (tiles) k + 8 w .. k + 8 w + 7 of
-// it, so one round reads 64 rows per pair at once (one L2 round trip).
-// Per pair, the rows up to the first tile whose counts are not out yet are
-// consumed in order: running sums plus the sums of the warps before give
-// each row its inclusive prefix, which overwrites its counts.  The next
-// round starts at the first row not consumed (after a short sleep when no
-// pair moved).  The scan waits only on counts, which every tile publishes
-// without waiting on anything, so it always finishes (the wait is
-// bounded).  Spreading the digits over several CTAs spreads the status
-// traffic (about 4 KB per tile) over several SMs.
-constexpr uint32_t kScanCtas = 8;
-constexpr uint32_t kSegRows = 8;  // rows per warp and round
-static_assert(kBins == 64 * kScanCtas && kWarps * kSegRows == 64, "scan layout");
-__device__ __forceinline__ void scan_tiles(uint32_t* __restrict__ status, uint32_t ntiles, uint32_t c,
-                                           uint32_t* err, uint32_t* sm) {
-  uint32_t(*s_stop)[32] = reinterpret_cast<uint32_t(*)[32]>(sm);
-  uint32_t(*s_sum0)[32] = reinterpret_cast<uint32_t(*)[32]>(sm + kWarps * 32);
-  uint32_t(*s_sum1)[32] = reinterpret_cast<uint32_t(*)[32]>(sm + 2 * kWarps * 32);
-  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  uint32_t* col = status + 64 * c + 2 * lane;
-  uint32_t k = 0, run0 = 0, run1 = 0, idle = 0;  // per pair: first row not consumed, its sums
-  while (__syncthreads_or(k < ntiles)) {
-    const uint32_t r0 = k + kSegRows * warp;
-    uint2 w[kSegRows];
-#pragma unroll
-    for (uint32_t q = 0; q < kSegRows; ++q)
-      w[q] = r0 + q < ntiles ? ld_relaxed_v2(col + static_cast<size_t>(r0 + q) * kBins) : make_uint2(0u, 0u);
-    uint32_t stop = kSegRows, t0 = 0, t1 = 0;  // first unusable row of the segment; sums before it
-#pragma unroll
-    for (uint32_t q = 0; q < kSegRows; ++q) {
-      const bool ready = r0 + q < ntiles && (w[q].x & ~kCountMask) != 0 && (w[q].y & ~kCountMask) != 0;
-      if (!ready && stop == kSegRows) stop = q;
-      if (stop == kSegRows) {
-        t0 += w[q].x & kCountMask;
-        t1 += w[q].y & kCountMask;
-      }
-    }
-    s_stop[warp][lane] = stop;
-    s_sum0[warp][lane] = t0;
-    s_sum1[warp][lane] = t1;
-    __syncthreads();
-    // this pair's rows consumed in this round: every warp's segment up to
-    // the first one that stops early
-    uint32_t before0 = 0, before1 = 0, all0 = 0, all1 = 0, used = 0;
-    bool open = true;  // segments so far were complete
-#pragma unroll
-    for (uint32_t v = 0; v < kWarps; ++v) {
-      if (open) {
-        if (v < warp) {
-          before0 += s_sum0[v][lane];
-          before1 += s_sum1[v][lane];
-        }
-        all0 += s_sum0[v][lane];
-        all1 += s_sum1[v][lane];
-        used += s_stop[v][lane];
-        open = s_stop[v][lane] == kSegRows;
-      }
-    }
-    // this warp's segment lies inside the consumed rows if every earlier
-    // segment was complete
-    bool mine = true;
-#pragma unroll
-    for (uint32_t v = 0; v < kWarps; ++v)
-      if (v < warp && s_stop[v][lane] != kSegRows) mine = false;
-    if (mine) {
-      uint32_t p0 = run0 + before0, p1 = run1 + before1;
-#pragma unroll
-      for (uint32_t q = 0; q < kSegRows; ++q) {
-        if (q < stop) {
-          p0 += w[q].x & kCountMask;
-          p1 += w[q].y & kCountMask;
-          st_relaxed_v2(col + static_cast<size_t>(r0 + q) * kBins, kFlagP | (p0 & kCountMask),
-                        kFlagP | (p1 & kCountMask));
-        }
-      }
-    }
-    k += used;
-    run0 += all0;
-    run1 += all1;
-    // no pair of the CTA moved: wait a little (bounded)
-    if (!__syncthreads_or(used != 0 || k >= ntiles)) {
-      if (++idle > kSpinLimit) {
-        latch_error(err, TDGS_ERR_TIMEOUT, kSiteBarrier);
-        return;
-      }
-      __nanosleep(64);
-    }
-  }
-}
-
-// Exclusive prefix of digits 2t and 2t+1 for tile `tile` > 0: the inclusive
-// prefix the scan CTAs wrote for tile - 1 (bounded wait).
-__device__ __forceinline__ void wait_prefix(const uint32_t* __restrict__ status, uint32_t tile, uint32_t t,
-                                            uint32_t& e0, uint32_t& e1, uint32_t* err) {
-  const uint32_t* row = status + static_cast<size_t>(tile - 1) * kBins + 2 * t;
-  uint2 w = ld_relaxed_v2(row);
-  uint32_t spins = 0;
-  while ((w.x & ~kCountMask) != kFlagP || (w.y & ~kCountMask) != kFlagP) {
-    if (++spins > kSpinLimit) {
-      latch_error(err, TDGS_ERR_TIMEOUT, kSiteBarrier);
-      break;
-    }
-    __nanosleep(32);
-    w = ld_relaxed_v2(row);
-  }
-  e0 = w.x & kCountMask;
-  e1 = w.y & kCountMask;
 }
 
 // ------------------------------------------------------------- one pass
@@ -446,7 +262,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
   const uint32_t m = a.m, ntiles = a.ntiles;
   if (blockIdx.x >= gridDim.x - kScanCtas) {  // a scan CTA
-    scan_tiles(a.status, ntiles, blockIdx.x - (gridDim.x - kScanCtas), a.err, reinterpret_cast<uint32_t*>(smem));
+    scan_tiles<kBins>(a.status, ntiles, blockIdx.x - (gridDim.x - kScanCtas), a.err, reinterpret_cast<uint32_t*>(smem));
     return;
   }
   const Digit dg = a.dg;
@@ -582,7 +398,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     // ---- the previous tile: its prefix, output positions
     if (have_prev) {
       uint32_t e0 = 0, e1 = 0;
-      if (prev != 0) wait_prefix(a.status, prev, t, e0, e1, a.err);
+      if (prev != 0) wait_prefix<kBins>(a.status, prev, t, e0, e1, a.err);
       if (a.status_next)
         *reinterpret_cast<uint2*>(a.status_next + static_cast<size_t>(prev) * kBins + 2 * t) = make_uint2(0u, 0u);
       off[2 * t] = g0 + e0 - ps0;
