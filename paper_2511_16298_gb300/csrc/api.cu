@@ -83,9 +83,12 @@ struct tdgs_context {
   int device = 0;
   DevStatus* d_status = nullptr;
   DevStatus* h_status = nullptr;  // pinned
-  cudaEvent_t ev_total = nullptr;  // recorded after the copy of the early pair count
+  // Pinned and mapped: the count kernel writes the pair count and the error
+  // word here itself, so reading them back needs no copy (a copy would
+  // queue behind other streams' large downloads on the copy engine).
+  DevStatus* h_early = nullptr;
+  DevStatus* d_early = nullptr;    // its device address
   cudaEvent_t ev_count = nullptr;  // recorded after the count kernel
-  cudaStream_t side = nullptr;     // carries that copy, off the frame's stream
   uint32_t* d_tickets = nullptr;  // [1] count blocks (reset by the kernel), [2..3] radix grid barrier
   uint32_t ticket_base[2] = {0, 0};
   Buffer scan_status, sort_scratch;
@@ -431,13 +434,13 @@ tdgs_status tdgs_context_create(tdgs_context** out, int device) {
       cudaMemset(ctx->d_range, 0, 8 * sizeof(uint32_t)) != cudaSuccess ||
       cudaMemset(ctx->d_range, 0xff, sizeof(uint32_t)) != cudaSuccess ||
       cudaMallocHost(&ctx->h_status, sizeof(DevStatus)) != cudaSuccess ||
+      cudaHostAlloc(&ctx->h_early, sizeof(DevStatus), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer(reinterpret_cast<void**>(&ctx->d_early), ctx->h_early, 0) != cudaSuccess ||
       cudaMalloc(&ctx->d_views, sizeof(ViewBlob)) != cudaSuccess ||
       cudaMallocHost(&ctx->h_views, sizeof(ViewBlob)) != cudaSuccess ||
       cudaMemset(ctx->d_status, 0, sizeof(DevStatus)) != cudaSuccess ||
       cudaMemset(ctx->d_tickets, 0, 4 * sizeof(uint32_t)) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->ev_total, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_count, cudaEventDisableTiming) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
     tdgs_context_destroy(ctx);
@@ -512,9 +515,8 @@ void tdgs_context_destroy(tdgs_context* ctx) {
   if (ctx->d_tickets) cudaFree(ctx->d_tickets);
   if (ctx->d_range) cudaFree(ctx->d_range);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
-  if (ctx->ev_total) cudaEventDestroy(ctx->ev_total);
+  if (ctx->h_early) cudaFreeHost(ctx->h_early);
   if (ctx->ev_count) cudaEventDestroy(ctx->ev_count);
-  if (ctx->side) cudaStreamDestroy(ctx->side);
   delete ctx;
 }
 
@@ -761,15 +763,12 @@ tdgs_status run_front(tdgs_context* ctx, cudaStream_t s, bool early_total = fals
   // launched even for zero Gaussians: it writes the view starts and M = 0
   TDGS_TRACED(ctx, ctx->proj_on ? kKPreCount : kKFrameCount, n_all ? n_all : 1, s,
               launch_views_count(vt, n_all, counts, dk[0], dv[0], err_word(ctx), ctx->d_tickets + 1,
-                                 &ctx->d_status->total, ctx->d_range, s, ctx->proj_on ? &ctx->proj : nullptr));
+                                 &ctx->d_status->total, ctx->d_range, early_total ? ctx->d_early : nullptr, s,
+                                 ctx->proj_on ? &ctx->proj : nullptr));
   if (early_total) {
-    // M (and any latched error) as soon as the count kernel is done; the
-    // copy runs on a side stream so the depth sort does not wait for it
+    // M (and any latched error) as soon as the count kernel is done: the
+    // kernel wrote them to the mapped host status (h_early)
     TDGS_CUDA(ctx, cudaEventRecord(ctx->ev_count, s));
-    TDGS_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_count, 0));
-    TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost,
-                                   ctx->side));
-    TDGS_CUDA(ctx, cudaEventRecord(ctx->ev_total, ctx->side));
   }
   const DepthPlan dp = plan_depth_sort(n_all, ctx->tuning.depth_digit_bits, ctx->tuning.ctas_per_sm);
   const uint32_t dpasses = dp.passes;
@@ -869,8 +868,11 @@ tdgs_status sort_views_exact(tdgs_context* ctx, cudaStream_t s, uint32_t* m_out)
   if (st != TDGS_OK) return st;
   st = run_front(ctx, s, true);
   if (st != TDGS_OK) return st;
-  TDGS_CUDA(ctx, cudaEventSynchronize(ctx->ev_total));
-  if (ctx->h_status->err) {
+  TDGS_CUDA(ctx, cudaEventSynchronize(ctx->ev_count));
+  const volatile DevStatus* early = ctx->h_early;
+  const uint32_t early_err = early->err;
+  const uint64_t early_total = early->total;
+  if (early_err) {
     TDGS_CUDA(ctx, cudaStreamSynchronize(s));
     TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     TDGS_CUDA(ctx, cudaStreamSynchronize(s));
@@ -878,7 +880,7 @@ tdgs_status sort_views_exact(tdgs_context* ctx, cudaStream_t s, uint32_t* m_out)
     TDGS_CUDA(ctx, cudaMemsetAsync(&ctx->d_status->err, 0, 8, s));
     return fail(ctx, e, std::string("error latched on the device by ") + site_name(ctx->h_status->site));
   }
-  const uint64_t total = ctx->h_status->total;
+  const uint64_t total = early_total;
   if (total > 0xffffffffull) {  // the scan latches the same overflow: clear it
     TDGS_CUDA(ctx, cudaStreamSynchronize(s));
     TDGS_CUDA(ctx, cudaMemsetAsync(&ctx->d_status->err, 0, 8, s));

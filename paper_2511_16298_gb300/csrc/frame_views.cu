@@ -31,7 +31,7 @@ template <bool kProject>
 __global__ void __launch_bounds__(256)
     k_views_count(ViewTable vt, uint32_t n_all, uint32_t* __restrict__ counts,
                   uint32_t* __restrict__ dkey, uint32_t* __restrict__ dval, uint32_t* err,
-                  uint32_t* ticket, uint64_t* total, uint32_t* range, Proj3D pj) {
+                  uint32_t* ticket, uint64_t* total, uint32_t* range, uint32_t* host_status, Proj3D pj) {
   __shared__ uint32_t s_begin[kMaxViews + 1];
   __shared__ unsigned long long s_tot[kMaxViews];
   __shared__ const float4* s_g[kMaxViews];
@@ -153,6 +153,14 @@ __global__ void __launch_bounds__(256)
       }
       vt.pbeg[vt.nv] = static_cast<uint32_t>(run);
       *total = run;
+      if (host_status) {
+        // the same for the host, in mapped pinned memory: {total, error,
+        // site} (errors latched by every other block are visible here)
+        reinterpret_cast<volatile unsigned long long*>(host_status)[0] = run;
+        reinterpret_cast<volatile uint32_t*>(host_status)[2] = __ldcg(err);
+        reinterpret_cast<volatile uint32_t*>(host_status)[3] = __ldcg(err + 1);
+        __threadfence_system();
+      }
       range[2] = __ldcg(range);
       range[3] = __ldcg(range + 1);
       range[0] = 0xffffffffu;
@@ -164,14 +172,17 @@ __global__ void __launch_bounds__(256)
 
 cudaError_t launch_views_count(const ViewTable& vt, uint32_t n_all, uint32_t* counts,
                                uint32_t* dkey, uint32_t* dval, uint32_t* err, uint32_t* ticket,
-                               uint64_t* total, uint32_t* range, cudaStream_t s, const Proj3D* proj) {
+                               uint64_t* total, uint32_t* range, void* host_status, cudaStream_t s,
+                               const Proj3D* proj) {
   const uint32_t per_block = 256u * (proj ? 2u : static_cast<uint32_t>(kCountUnroll));
   const uint32_t blocks = (n_all + per_block - 1) / per_block;
   const uint32_t grid = blocks < 1u ? 1u : (blocks < 152u * 8u ? blocks : 152u * 8u);
   if (proj)
-    k_views_count<true><<<grid, 256, 0, s>>>(vt, n_all, counts, dkey, dval, err, ticket, total, range, *proj);
+    k_views_count<true><<<grid, 256, 0, s>>>(vt, n_all, counts, dkey, dval, err, ticket, total, range,
+                                             static_cast<uint32_t*>(host_status), *proj);
   else
-    k_views_count<false><<<grid, 256, 0, s>>>(vt, n_all, counts, dkey, dval, err, ticket, total, range, Proj3D{});
+    k_views_count<false><<<grid, 256, 0, s>>>(vt, n_all, counts, dkey, dval, err, ticket, total, range,
+                                              static_cast<uint32_t*>(host_status), Proj3D{});
   return cudaGetLastError();
 }
 

@@ -222,9 +222,12 @@ struct Proj3D {
   CameraDev cam0;         // cams[0], passed by value (kernel parameter space) for one view
 };
 
+// host_status (optional): device address of mapped pinned memory that
+// also receives {uint64 pair count, uint32 error, uint32 site} from the
+// last block (the host reads it after an event on the kernel, no copy).
 cudaError_t launch_views_count(const ViewTable& vt, uint32_t n_all, uint32_t* counts,
                                uint32_t* dkey, uint32_t* dval, uint32_t* err, uint32_t* ticket,
-                               uint64_t* total, uint32_t* range, cudaStream_t s,
+                               uint64_t* total, uint32_t* range, void* host_status, cudaStream_t s,
                                const Proj3D* proj = nullptr);
 // sdo: receives {depth key, record index} per depth position (read by the
 // expanding tile pass with one 8-byte load per pair).
