@@ -105,10 +105,17 @@ def measured_peaks():
 
 
 def kernel_source_sha() -> str:
-    """Hash of the sources the radix passes are built from."""
+    """Hash of the sources the chunked radix pass kernels are compiled
+    from: the radix files and the device part of the internal header (its
+    host-side declarations, after the "host side" marker, do not enter the
+    kernels)."""
     h = hashlib.sha256()
-    for f in ("radix.cuh", "radix.cu", "radix_frame.cu", "sort_kernels.cu", "tdgs_internal.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2511_16298_gb300", "csrc", f), "rb").read())
+    csrc = os.path.join(ROOT, "paper_2511_16298_gb300", "csrc")
+    for f in ("radix.cuh", "radix.cu", "radix_frame.cu", "sort_kernels.cu"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    hdr = open(os.path.join(csrc, "tdgs_internal.cuh"), "rb").read()
+    cut = hdr.find(b"// ------------------------------------------------------------- host side")
+    h.update(hdr if cut < 0 else hdr[:cut])
     return h.hexdigest()
 
 
