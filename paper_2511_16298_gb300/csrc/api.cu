@@ -93,6 +93,12 @@ struct tdgs_context {
   uint32_t ticket_base[2] = {0, 0};
   Buffer scan_status, sort_scratch;
   Buffer os_scratch;  // onesweep sort: histograms, digit starts, tickets, look-back status
+  Buffer f_dsort;     // single-launch depth sort: barrier counters, totals, rows (kept zero between launches)
+  // State that kernels keep between launches, to be cleared before its next
+  // use after an error was latched on the device (a bounded wait may have
+  // given up mid-launch): the depth sort's buffer, the onesweep header, the
+  // radix grid barrier words.
+  bool dsort_dirty = true, os_dirty = false, bar_dirty = false;
   // fused-frame / multi-view buffers
   Buffer f_rec3, f_conic;  // projected records and conics of tdgs_sort_frame_3d
   Buffer d_cams;           // cameras of the 3D calls (device)
@@ -182,6 +188,18 @@ tdgs_status ensure(tdgs_context* ctx, Buffer& b, size_t bytes, cudaStream_t s,
 }
 
 uint32_t* err_word(tdgs_context* ctx) { return &ctx->d_status->err; }
+
+void note_device_error(tdgs_context* ctx) { ctx->dsort_dirty = ctx->os_dirty = ctx->bar_dirty = true; }
+
+// The radix grid barrier words back to zero if an error was latched since
+// their last use.
+tdgs_status clear_barrier_if_dirty(tdgs_context* ctx, cudaStream_t s) {
+  if (ctx->bar_dirty) {
+    TDGS_CUDA(ctx, cudaMemsetAsync(ctx->d_tickets + 2, 0, 2 * sizeof(uint32_t), s));
+    ctx->bar_dirty = false;
+  }
+  return TDGS_OK;
+}
 
 cudaEvent_t take_event(tdgs_context* ctx) {
   if (!ctx->free_events.empty()) {
@@ -277,13 +295,15 @@ tdgs_status do_sort(tdgs_context* ctx, uint64_t* keys, uint32_t* values, uint64_
                     int* result_in_alt, cudaStream_t s) {
   *result_in_alt = 0;
   if (m == 0) return TDGS_OK;
+  if (tdgs_status st0 = clear_barrier_if_dirty(ctx, s); st0 != TDGS_OK) return st0;
   const SortPlan plan = make_sort_plan(m, tile_bits, flags, ctx->tuning);
   if (ctx->tuning.sort_variant < 0 && onesweep_eligible(m, keys, values, keys_alt, values_alt)) {
     bool grown = false;
     tdgs_status st = ensure(ctx, ctx->os_scratch, onesweep_scratch_words(m) * 4, s, &grown);
     if (st != TDGS_OK) return st;
     uint32_t* scratch = static_cast<uint32_t*>(ctx->os_scratch.p);
-    if (grown) TDGS_CUDA(ctx, cudaMemsetAsync(scratch, 0, onesweep_header_words() * 4, s));
+    if (grown || ctx->os_dirty) TDGS_CUDA(ctx, cudaMemsetAsync(scratch, 0, onesweep_header_words() * 4, s));
+    ctx->os_dirty = false;
     TDGS_TRACED(ctx, kKSortHist, m, s, launch_onesweep_hist(plan, keys, m, scratch, err_word(ctx), s));
     uint64_t* kin = keys;
     uint32_t* vin = values;
@@ -323,6 +343,7 @@ tdgs_status read_and_clear_error(tdgs_context* ctx, cudaStream_t s) {
   TDGS_CUDA(ctx, cudaStreamSynchronize(s));
   const uint32_t e = ctx->h_status->err;
   if (e != 0) {
+    note_device_error(ctx);
     TDGS_CUDA(ctx, cudaMemsetAsync(&ctx->d_status->err, 0, 8, s));
     TDGS_CUDA(ctx, cudaStreamSynchronize(s));
     return fail(ctx, static_cast<tdgs_status>(e),
@@ -499,7 +520,7 @@ void tdgs_context_destroy(tdgs_context* ctx) {
   DeviceGuard g(ctx->device);
   drain_timings(ctx);
   for (cudaEvent_t e : ctx->free_events) cudaEventDestroy(e);
-  Buffer* bufs[] = {&ctx->scan_status, &ctx->sort_scratch, &ctx->os_scratch, &ctx->f_counts, &ctx->f_dkey[0],
+  Buffer* bufs[] = {&ctx->scan_status, &ctx->sort_scratch, &ctx->os_scratch, &ctx->f_dsort, &ctx->f_counts, &ctx->f_dkey[0],
                     &ctx->f_dkey[1],    &ctx->f_dkey[2],     &ctx->f_dval[0],    &ctx->f_dval[1],
                     &ctx->f_dval[2],    &ctx->f_soff,       &ctx->f_sdo,        &ctx->f_rec3,
                     &ctx->f_conic,      &ctx->d_cams,       &ctx->diag,       &ctx->b_keys,       &ctx->b_vals,       &ctx->n_counts,
@@ -726,6 +747,14 @@ tdgs_status ensure_record_buffers(tdgs_context* ctx, cudaStream_t s) {
   const DepthPlan dp = plan_depth_sort(n_all, ctx->tuning.depth_digit_bits, ctx->tuning.ctas_per_sm);
   if (dp.grid == 0) return fail(ctx, TDGS_ERR_CUDA, "device query for the depth sort failed");
   if (st == TDGS_OK) st = ensure(ctx, ctx->sort_scratch, dp.scratch_words * 4, s);
+  if (st == TDGS_OK && dp.resident) {
+    grown = false;
+    st = ensure(ctx, ctx->f_dsort, depth_sort_scratch_words(dp.grid) * 4, s, &grown);
+    if (st == TDGS_OK && (grown || ctx->dsort_dirty)) {
+      TDGS_CUDA(ctx, cudaMemsetAsync(ctx->f_dsort.p, 0, ctx->f_dsort.bytes, s));
+      ctx->dsort_dirty = false;
+    }
+  }
   return st;
 }
 
@@ -754,6 +783,7 @@ tdgs_status ensure_pair_buffers(tdgs_context* ctx, uint64_t m, cudaStream_t s) {
 tdgs_status run_front(tdgs_context* ctx, cudaStream_t s, bool early_total = false) {
   const ViewTable vt = device_table(ctx);
   const uint32_t n_all = ctx->n_all;
+  if (tdgs_status st0 = clear_barrier_if_dirty(ctx, s); st0 != TDGS_OK) return st0;
   TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->d_views, ctx->h_views, sizeof(ViewBlob), cudaMemcpyHostToDevice, s));
   uint32_t* counts = static_cast<uint32_t*>(ctx->f_counts.p);
   uint32_t* dk[3] = {static_cast<uint32_t*>(ctx->f_dkey[0].p), static_cast<uint32_t*>(ctx->f_dkey[1].p),
@@ -775,9 +805,9 @@ tdgs_status run_front(tdgs_context* ctx, cudaStream_t s, bool early_total = fals
   uint32_t* scratch = static_cast<uint32_t*>(ctx->sort_scratch.p);
   if (dp.resident) {  // one launch: the sort (pass count from the depth range) and the offsets
     TDGS_TRACED(ctx, kKDepthSort, n_all, s,
-                launch_depth_resident(dp, dk[0], dv[0], dk[1], dv[1], dk[2], dv[2], ctx->d_range + 2, counts,
-                                      static_cast<uint32_t*>(ctx->f_soff.p), n_all, scratch, ctx->d_tickets + 2,
-                                      err_word(ctx), s));
+                launch_depth_sort(dp.grid, dk[0], dk[1], dv[1], dk[2], dv[2], ctx->d_range + 2, counts,
+                                  static_cast<uint32_t*>(ctx->f_soff.p), n_all,
+                                  static_cast<uint32_t*>(ctx->f_dsort.p), err_word(ctx), s));
   } else {
     for (uint32_t p = 0; p < dpasses; ++p) {
       TDGS_TRACED(ctx, kKDepthSort, n_all, s,
@@ -873,6 +903,7 @@ tdgs_status sort_views_exact(tdgs_context* ctx, cudaStream_t s, uint32_t* m_out)
   const uint32_t early_err = early->err;
   const uint64_t early_total = early->total;
   if (early_err) {
+    note_device_error(ctx);
     TDGS_CUDA(ctx, cudaStreamSynchronize(s));
     TDGS_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     TDGS_CUDA(ctx, cudaStreamSynchronize(s));

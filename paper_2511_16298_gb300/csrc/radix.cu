@@ -74,38 +74,5 @@ cudaError_t launch(const Kernel& k, uint32_t grid, const void* kin, const uint32
   return cudaLaunchKernelExC(&cfg, k.fn, args);
 }
 
-uint32_t resident_grid(const Kernel& k, uint32_t m, int ctas_per_sm) {
-  uint32_t g = resident_ctas(k, ctas_per_sm);
-  if (g > kMaxGrid) g = kMaxGrid;
-  if (g == 0) return 0;
-  const uint64_t chunk = ((static_cast<uint64_t>(m) + g - 1) / g + 3) & ~3ull;
-  const uint64_t tile = static_cast<uint64_t>(k.threads) * k.items;
-  return chunk <= tile ? g : 0;
-}
-
-cudaError_t launch_resident(const Kernel& k, uint32_t grid, void* k0, uint32_t* v0, void* k1, uint32_t* v1,
-                            void* k2, uint32_t* v2, PassArgs a, const ResidentArgs& ra, uint32_t* scratch,
-                            cudaStream_t s) {
-  if (a.m == 0 || (ra.passes == 0 && !ra.range)) return cudaSuccess;
-  if (grid == 0) return cudaErrorInvalidConfiguration;
-  const uint32_t bins = 1u << k.bits;
-  a.H = scratch;
-  a.P = scratch + static_cast<size_t>(grid) * bins;
-  a.tot = a.P + static_cast<size_t>(grid) * bins;
-  ResidentArgs r = ra;
-  void* args[] = {(void*)&k0, (void*)&v0, (void*)&k1, (void*)&v1, (void*)&k2, (void*)&v2, (void*)&a, (void*)&r};
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(k.threads);
-  cfg.dynamicSmemBytes = k.smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelExC(&cfg, k.fn, args);
-}
-
 }  // namespace radix
 }  // namespace tdgs

@@ -859,190 +859,6 @@ __global__ void __launch_bounds__(kThreads, (PassShape<K, kVals, kExpand, kBits,
   }
 }
 
-// Several digit passes in one cooperative launch, for inputs of at most
-// one tile per CTA (chunk size <= kTileKeys).  Each pass ranks the CTA's
-// tile once, publishes the tile's digit counts as its chunk histogram,
-// scans the columns over chunks and scatters: no histogram read, no
-// second load of the keys and no launch between passes.  Buffers
-// ping-pong: pass p reads (k[p % 2], v[p % 2]) and writes the other pair.
-struct ResidentArgs {
-  uint32_t passes;
-  uint32_t shift[kMaxPasses], mask[kMaxPasses];
-  // With range set (uint32 keys): range[0..1] = smallest and largest key
-  // other than all ones (largest < smallest: there is none).  Keys are
-  // compressed to key - smallest (all ones -> one past the largest), the
-  // pass count and digits follow from the compressed width, and the result
-  // always lands in (k1, v1): passes alternate between (k1, v1) and
-  // (k2, v2) so that the last one writes (k1, v1).  range[2] receives the
-  // number of passes run.
-  uint32_t* range;
-  // With counts set (and range): after the sort, offsets[p] = sum of
-  // counts[v1[q]] over q < p (the exclusive scan of the counts in sorted
-  // order); a sum above 2^32 - 1 latches TDGS_ERR_OVERFLOW.
-  const uint32_t* counts;
-  uint32_t* offsets;
-};
-
-template <typename K, int kBits, int kThreads, int kItems, int kOcc, bool kRowSum>
-__global__ void __launch_bounds__(kThreads, kOcc)
-    k_radix_resident(K* __restrict__ k0, uint32_t* __restrict__ v0, K* __restrict__ k1,
-                     uint32_t* __restrict__ v1, K* __restrict__ k2, uint32_t* __restrict__ v2, PassArgs a,
-                     ResidentArgs ra) {
-  using S = PassShape<K, true, false, kBits, kThreads, kItems, kOcc>;
-  static_assert(S::kBins > 64, "the resident kernel reads the tile counts right after rank_tile");
-  extern __shared__ __align__(16) unsigned char smem[];
-  Smem<K> sm;
-  {
-    unsigned char* q = smem;
-    sm.wh = reinterpret_cast<uint16_t*>(q);
-    q += S::kWhBytes;
-    sm.xk = reinterpret_cast<K*>(q);
-    q += S::kXkBytes;
-    sm.xv = reinterpret_cast<uint32_t*>(q);
-    q += S::kXvBytes;
-    sm.base = reinterpret_cast<uint32_t*>(q);
-    sm.lstart = sm.base + S::kBins;
-    sm.off = sm.lstart + S::kBins;
-  }
-  __shared__ uint32_t s_warp[S::kWarps];
-  const uint32_t t = threadIdx.x, c = blockIdx.x;
-  const Chunk ch = chunk_of(a);
-  uint32_t valid = ch.end - ch.beg;
-  bool ok = valid <= static_cast<uint32_t>(S::kTileKeys);  // guaranteed by the host
-  if (!ok) valid = S::kTileKeys;
-  {
-    uint4* z = reinterpret_cast<uint4*>(sm.wh);
-    for (uint32_t i = t; i < S::kWhBytes / 16; i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
-  }
-  __syncthreads();
-  uint32_t passes = ra.passes, width = 0;
-  if constexpr (sizeof(K) == 4) {
-    if (ra.range) {
-      const uint32_t lo = __ldcg(ra.range), hi = __ldcg(ra.range + 1);
-      const uint32_t cull = hi >= lo ? hi - lo + 1u : 0u;  // compressed keys are 0 .. cull
-      const uint32_t bits = cull ? 32u - static_cast<uint32_t>(__clz(cull)) : 0u;
-      passes = bits ? (bits + kBits - 1) / kBits : 1u;
-      width = (bits + passes - 1) / passes;
-      a.sub = lo;
-      a.cull = cull;
-      if (c == 0 && t == 0) ra.range[2] = passes;
-    }
-  }
-  for (uint32_t p = 0; p < passes; ++p) {
-    const K* kin;
-    const uint32_t* vin;
-    K* kout;
-    uint32_t* vout;
-    if (ra.range) {
-      const bool to_one = ((passes - 1 - p) & 1u) == 0;
-      kin = p == 0 ? k0 : (to_one ? k2 : k1);
-      vin = p == 0 ? v0 : (to_one ? v2 : v1);
-      kout = to_one ? k1 : k2;
-      vout = to_one ? v1 : v2;
-      a.shift = p * width;
-      a.mask = width ? (1u << width) - 1u : 0u;
-      a.xform_in = p == 0;
-      a.xform_out = p + 1 == passes;
-    } else {
-      kin = (p & 1) ? k1 : k0;
-      vin = (p & 1) ? v1 : v0;
-      kout = (p & 1) ? k0 : k1;
-      vout = (p & 1) ? v0 : v1;
-      a.shift = ra.shift[p];
-      a.mask = ra.mask[p];
-    }
-    TileRegs<K, false, kItems> R;
-    rank_tile<false, S, K, false, kBits, kItems, sizeof(K) == 4>(kin + ch.beg, valid, a, false, sm, R);
-    for (uint32_t b = t; b < static_cast<uint32_t>(S::kBins); b += kThreads)
-      a.H[static_cast<size_t>(c) * S::kBins + b] = sm.lstart[b];
-    scan_chunks<S::kBins, kThreads, kRowSum>(a, sm.base, s_warp, nullptr);
-    ok &= scatter_tile<false, S, K, true, false, kBits, kItems, sizeof(K) == 4>(vin + ch.beg, valid, ch.m, a, false,
-                                                                                 sm, s_warp,
-                                                                 nullptr, nullptr, kout, vout, R);
-    grid_barrier(a.bar, a.err);  // the next pass reads what every CTA wrote
-  }
-  if (!ok) latch_error(a.err, TDGS_ERR_CAPACITY, kSiteRadixRange);
-  if constexpr (sizeof(K) == 4) {
-    if (ra.range && ra.counts) {
-      // exclusive scan of the counts in sorted order: chunk c of the sorted
-      // indices, kItems consecutive positions per thread, chunk sums through
-      // a grid barrier
-      static_assert(kItems % 4 == 0, "16-byte loads of the sorted indices");
-      const uint32_t pos0 = ch.beg + t * kItems;
-      uint32_t cnt[kItems];
-      uint64_t sum = 0;
-#pragma unroll
-      for (int j = 0; j < kItems; j += 4) {
-        uint4 idx = make_uint4(0, 0, 0, 0);
-        if (pos0 + j + 4 <= ch.end) {
-          idx = __ldcg(reinterpret_cast<const uint4*>(v1 + pos0 + j));
-        } else {
-          if (pos0 + j < ch.end) idx.x = __ldcg(v1 + pos0 + j);
-          if (pos0 + j + 1 < ch.end) idx.y = __ldcg(v1 + pos0 + j + 1);
-          if (pos0 + j + 2 < ch.end) idx.z = __ldcg(v1 + pos0 + j + 2);
-        }
-        const uint32_t id[4] = {idx.x, idx.y, idx.z, idx.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const uint32_t p = pos0 + j + u;
-          cnt[j + u] = (p < ch.end && id[u] < ch.m) ? __ldg(ra.counts + id[u]) : 0u;
-          sum += cnt[j + u];
-        }
-      }
-      // block scan of the per-thread sums (64-bit)
-      __shared__ unsigned long long s_sum[S::kWarps];
-      __shared__ unsigned long long s_base;
-      const uint32_t lane = lane_id(), warp = t >> 5;
-      unsigned long long x = sum;
-#pragma unroll
-      for (int dd = 1; dd < 32; dd <<= 1) {
-        const unsigned long long o = __shfl_up_sync(0xffffffffu, x, dd);
-        if (lane >= static_cast<uint32_t>(dd)) x += o;
-      }
-      if (lane == 31) s_sum[warp] = x;
-      __syncthreads();
-      if (t == 0) {
-        unsigned long long run = 0;
-        for (int w = 0; w < S::kWarps; ++w) {
-          const unsigned long long v = s_sum[w];
-          s_sum[w] = run;
-          run += v;
-        }
-        reinterpret_cast<unsigned long long*>(a.H)[c] = run;  // this chunk's sum
-      }
-      __syncthreads();
-      uint64_t run = x - sum + s_sum[warp];
-      grid_barrier(a.bar, a.err);  // every chunk's sum is published
-      if (warp == 0) {
-        unsigned long long before = 0;
-        for (uint32_t cc = lane; cc < c; cc += 32) before += __ldcg(reinterpret_cast<const unsigned long long*>(a.H) + cc);
-#pragma unroll
-        for (int dd = 16; dd > 0; dd >>= 1) before += __shfl_xor_sync(0xffffffffu, before, dd);
-        if (lane == 0) s_base = before;
-      }
-      __syncthreads();
-      run += s_base;
-      if (run + sum > 0xffffffffull) latch_error(a.err, TDGS_ERR_OVERFLOW, kSiteScan);
-#pragma unroll
-      for (int j = 0; j < kItems; j += 4) {
-        uint32_t o[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          o[u] = static_cast<uint32_t>(run);
-          run += cnt[j + u];
-        }
-        if (pos0 + j + 4 <= ch.end) {
-          *reinterpret_cast<uint4*>(ra.offsets + pos0 + j) = make_uint4(o[0], o[1], o[2], o[3]);
-        } else {
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (pos0 + j + u < ch.end) ra.offsets[pos0 + j + u] = o[u];
-        }
-      }
-    }
-  }
-}
-
 // --------------------------------------------------------------- host side
 struct Kernel {
   const void* fn;     // the __global__ function
@@ -1056,13 +872,6 @@ Kernel make_kernel() {
   using S = PassShape<K, kVals, kExpand, kBits, kThreads, kItems, kOcc>;
   return Kernel{reinterpret_cast<const void*>(&k_radix_pass<K, kVals, kExpand, kBits, kThreads, kItems, kOcc>),
                 kBits, kThreads, kItems, S::kSmem, S::kMinBlocks};
-}
-
-template <typename K, int kBits, int kThreads, int kItems, int kOcc, bool kRowSum = false>
-Kernel make_resident_kernel() {
-  using S = PassShape<K, true, false, kBits, kThreads, kItems, kOcc>;
-  return Kernel{reinterpret_cast<const void*>(&k_radix_resident<K, kBits, kThreads, kItems, kOcc, kRowSum>), kBits,
-                kThreads, kItems, S::kSmem, kOcc};
 }
 
 // Resident CTAs of `k` on the current device (0 on failure); caches the
@@ -1080,17 +889,6 @@ inline size_t scratch_words(const Kernel& k, uint32_t grid) {
 // Launch one pass (cooperative).  scratch: scratch_words() uint32 words.
 cudaError_t launch(const Kernel& k, uint32_t grid, const void* kin, const uint32_t* vin, void* kout,
                    uint32_t* vout, PassArgs a, uint32_t* scratch, cudaStream_t s);
-
-// Grid for the resident kernel `k` over m keys: all resident CTAs (at
-// most kMaxGrid), or 0 if m keys do not fit one tile per CTA.
-uint32_t resident_grid(const Kernel& k, uint32_t m, int ctas_per_sm = 0);
-
-// Launch all passes of a resident kernel (cooperative): k0/v0 hold the
-// input; with ra.range the result is in (k1, v1) (k2/v2: a third pair of
-// buffers), else in (k0, v0) for an even pass count and (k1, v1) for an odd.
-cudaError_t launch_resident(const Kernel& k, uint32_t grid, void* k0, uint32_t* v0, void* k1, uint32_t* v1,
-                            void* k2, uint32_t* v2, PassArgs a, const ResidentArgs& ra, uint32_t* scratch,
-                            cudaStream_t s);
 
 }  // namespace radix
 }  // namespace tdgs

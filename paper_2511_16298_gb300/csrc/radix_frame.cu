@@ -30,25 +30,17 @@ const radix::Kernel& stream_kernel(bool wide, bool expand, uint32_t bits) {
 
 uint32_t stream_kernel_bits(uint32_t width) { return width <= 6 ? 6u : (width <= 8 ? 8u : 12u); }
 
-namespace {
-const radix::Kernel& resident_depth_kernel() {
-  static const radix::Kernel k9 = radix::make_resident_kernel<uint32_t, 9, 512, 16, 1, true>();
-  return k9;
-}
-}  // namespace
-
 DepthPlan plan_depth_sort(uint32_t n, int tuned_bits, int ctas_per_sm) {
   DepthPlan p{};
   const uint32_t nn = n ? n : 1;
-  const radix::Kernel& k = resident_depth_kernel();
-  const uint32_t g = radix::resident_grid(k, nn, ctas_per_sm);
-  if (g) {
+  const uint32_t g = depth_sort_grid();
+  if (g && nn <= depth_sort_capacity(g)) {
     p.resident = true;
     p.bits = 9;
     p.passes = 4;  // at most; the kernel runs as many as the key range needs
     p.grid = g;
     p.result = 1;
-    p.scratch_words = radix::scratch_words(k, g);
+    p.scratch_words = 0;  // its state lives in a buffer of its own (depth_sort_scratch_words)
     return p;
   }
   p.resident = false;
@@ -87,21 +79,6 @@ cudaError_t launch_depth_pass(const DepthPlan& dp, uint32_t pass, const uint32_t
   a.bar = bar;
   a.err = err;
   return radix::launch(depth_kernel(dp.bits), dp.grid, kin, vin, kout, vout, a, scratch, s);
-}
-
-cudaError_t launch_depth_resident(const DepthPlan& dp, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
-                                  uint32_t* k2, uint32_t* v2, uint32_t* range, const uint32_t* counts,
-                                  uint32_t* offsets, uint32_t n, uint32_t* scratch, uint32_t* bar, uint32_t* err,
-                                  cudaStream_t s) {
-  radix::PassArgs a{};
-  a.m = n;
-  a.bar = bar;
-  a.err = err;
-  radix::ResidentArgs ra{};
-  ra.range = range;
-  ra.counts = counts;
-  ra.offsets = offsets;
-  return radix::launch_resident(resident_depth_kernel(), dp.grid, k0, v0, k1, v1, k2, v2, a, ra, scratch, s);
 }
 
 uint32_t stream_grid(bool wide, bool expand, uint32_t bits, uint32_t m, int ctas_per_sm) {

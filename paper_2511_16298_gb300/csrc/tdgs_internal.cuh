@@ -235,14 +235,15 @@ cudaError_t launch_views_dup(const ViewTable& vt, const uint32_t* sorder, const 
                              uint32_t n_all, uint32_t rbits, void* out, bool wide, uint32_t cap,
                              uint2* sdo, uint32_t* err, cudaStream_t s);
 
-// Radix passes of the frame path (radix_frame.cu).
+// Radix passes of the frame path (radix_frame.cu, depth_sort.cu).
 // Depth sort of the N Gaussians: (uint32 depth key, uint32 index).  When
-// the Gaussians fit one tile per resident CTA all passes run in one
-// cooperative launch (resident) over keys compressed to their range
-// (key - smallest; culled Gaussians one past the largest), with as many
-// 9-bit digits as that range needs (3 for a range below 2^27, 4 at most).
-// Otherwise one launch per pass over all 32 bits: 8-bit (4 passes) or,
-// if tuned, 11-bit (3 passes) digits.
+// the Gaussians fit one 8192-key chunk per resident CTA the whole sort and
+// the scan of the tile counts in depth order run in one cooperative launch
+// (launch_depth_sort) over keys compressed to their range (key - smallest;
+// culled Gaussians one past the largest), with as many 9-bit digits as that
+// range needs (3 for a range below 2^27, 4 at most).  Otherwise one launch
+// per pass over all 32 bits: 8-bit (4 passes) or, if tuned, 11-bit (3
+// passes) digits.
 struct DepthPlan {
   bool resident;          // one launch; keys compressed to their range, passes chosen on the device
   int bits;
@@ -257,14 +258,21 @@ DepthPlan plan_key32_sort(uint32_t m, uint32_t key_bits, int ctas_per_sm);
 cudaError_t launch_depth_pass(const DepthPlan& dp, uint32_t pass, const uint32_t* kin, const uint32_t* vin,
                               uint32_t* kout, uint32_t* vout, uint32_t n, uint32_t* scratch, uint32_t* bar,
                               uint32_t* err, cudaStream_t s);
-// Result in (k1, v1); range[0..1]: the smallest and largest depth key of a
+// Single-launch depth sort (depth_sort.cu).  Grid: one CTA per SM (0 if
+// the device query failed); it takes n <= depth_sort_capacity(grid) keys.
+// key0: the depth keys; range[0..1]: the smallest and largest key of a
 // Gaussian with pairs (written by the count kernel); range[2] receives the
-// number of passes run.  Then offsets = the exclusive scan of
-// counts[v1[.]] (the pair offsets in depth order).
-cudaError_t launch_depth_resident(const DepthPlan& dp, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
-                                  uint32_t* k2, uint32_t* v2, uint32_t* range, const uint32_t* counts,
-                                  uint32_t* offsets, uint32_t n, uint32_t* scratch, uint32_t* bar, uint32_t* err,
-                                  cudaStream_t s);
+// number of passes run.  Results: v1 = record indices in depth order,
+// offsets = the exclusive scan of counts[v1[.]] (the pair offsets in depth
+// order); k1 receives counts[v1[.]], (k2, v2) are intermediate.  scratch:
+// depth_sort_scratch_words(grid) words of state kept between launches,
+// zero before the first launch and after an error latched in err.
+uint32_t depth_sort_grid();
+uint32_t depth_sort_capacity(uint32_t grid);
+size_t depth_sort_scratch_words(uint32_t grid);
+cudaError_t launch_depth_sort(uint32_t grid, const uint32_t* key0, uint32_t* k1, uint32_t* v1, uint32_t* k2,
+                              uint32_t* v2, uint32_t* range, const uint32_t* counts, uint32_t* offsets, uint32_t n,
+                              uint32_t* scratch, uint32_t* err, cudaStream_t s);
 // Stable pass over the packed stream on tile bits [shift, shift + width).
 // expand: write the final (local tile << 32 | depth bits) keys and local
 // indices; with rmin/rmax, record each global tile's first/last sorted

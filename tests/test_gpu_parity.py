@@ -344,6 +344,38 @@ def test_depth_sort_pass_count(ctx, oracle, depths, passes):
     assert ctx.depth_passes() == passes
 
 
+def _depth_range_frame(seed, lo, hi, n=20_000):
+    rng = np.random.default_rng(seed)
+    d = np.exp(rng.uniform(np.log(lo), np.log(hi), size=n))
+    d[rng.integers(0, n, size=n // 10)] = hi  # ties at the largest key
+    r = rng.integers(1, 10, size=n)
+    r[rng.integers(0, n, size=n // 20)] = 0  # culled
+    g = synth.records(rng.uniform(0, 640, n), rng.uniform(0, 360, n), d, r)
+    return synth.Frame(640, 360, g, f"depths-{seed}")
+
+
+def test_depth_sort_alternating_pass_counts(ctx, oracle):
+    """Consecutive frames on one context whose depth ranges need 4, 1, 3,
+    2, 4, 2, 3 and 1 passes: the single-launch sort's counters, totals and
+    count rows are reset for every pass count (each frame exact)."""
+    ranges = [(1e-30, 1e30), (3.0, 3.0), (0.5, 80.0), (1.0, 1.01), (1e-20, 1e20), (2.0, 2.02),
+              (0.2, 50.0), (7.0, 7.0)]
+    want = [4, 1, 3, 2, 4, 2, 3, 1]
+    for i, ((lo, hi), passes) in enumerate(zip(ranges, want)):
+        _check_frame(ctx, oracle, _depth_range_frame(40 + i, lo, hi))
+        assert ctx.depth_passes() == passes
+
+
+def test_depth_sort_at_capacity(ctx, oracle):
+    """N = SMs x 8192 Gaussians, the most the single-launch depth sort takes
+    (every CTA a full chunk), and one more (the per-pass launches)."""
+    cap = torch.cuda.get_device_properties(0).multi_processor_count * 8192
+    for n in (cap, cap + 1):
+        fr = synth.frame_random(77, n, 1280, 720, max_sigma=6.0)
+        _check_frame(ctx, oracle, fr)
+        assert ctx.depth_passes() >= 1
+
+
 def test_sort_frame_scene_1m(ctx, oracle):
     m = _check_frame(ctx, oracle, synth.frame_scene(0))
     assert m > 5_000_000
