@@ -29,9 +29,15 @@
 // count is read again at the end), loaded in order in pass 0.  The last
 // pass writes the sorted record indices and, at each sorted position, the
 // tile count (the sorted keys are not needed later): no gather of the
-// counts in depth order.  After the final barrier each chunk sums its counts, publishes
-// the sum tagged with the launch number and adds the sums of the chunks
-// before it: the pair offsets, with no further barrier.
+// counts in depth order.  Output positions grow with the exchange position,
+// so each warp adds the counts it writes into per-chunk sums by runs of
+// equal chunk (one shuffle reduction per run); the sums reach global
+// memory by atomics before the final barrier, after which each chunk scans
+// its counts from the sum of the chunks before it: the pair offsets.
+//
+// Each pass's values (pass 0: the tile counts) come into shared memory by
+// one bulk copy issued when the pass starts, so their latency hides behind
+// the ranking.
 //
 // A barrier is an arrival counter of its own: a CTA adds one with release
 // semantics and waits (acquire, bounded) until the count reaches the grid
@@ -40,7 +46,7 @@
 // launches (counters, totals, rows, launch number) lives in a dedicated
 // zero-initialised buffer, which the host clears again after an error was
 // latched on the device.
-#include "radix.cuh"
+#include "onesweep.cuh"
 
 namespace tdgs {
 namespace depth {
@@ -55,6 +61,8 @@ constexpr uint32_t kRecMask = (1u << kValueBits) - 1u;
 constexpr uint32_t kCntEscape = (1u << (32 - kValueBits)) - 1u;  // 1023: the count is gathered again
 using S = radix::PassShape<uint32_t, true, false, kBits, kThreads, kItems, 1>;
 constexpr uint32_t kTileKeys = S::kTileKeys;
+constexpr size_t kSmem = S::kSmem + kTileKeys * 4;  // + the staged values
+static_assert(S::kSmem % 16 == 0, "the staged values start 16-byte aligned");
 static_assert(kTileKeys == 8192, "one 8192-key chunk per CTA");
 static_assert(kTileKeys < (1u << 14), "a chunk's count of one digit fits 14 bits");
 static_assert(static_cast<uint64_t>(kMaxGrid) * kTileKeys <= (1ull << kValueBits), "record index bits");
@@ -66,13 +74,13 @@ constexpr uint32_t kSlots = 8;                      // barrier counters, one lin
 constexpr uint32_t kFinalSlot = kSlots - 1;         // before the offsets
 constexpr uint32_t kSeqWord = kSlots * kLine;       // launch number
 constexpr uint32_t kHistWord = kSeqWord + kLine;    // [kMaxPasses][kBins] digit totals
-constexpr uint32_t kSumWord = kHistWord + kMaxPasses * kBins;  // [kMaxGrid] u64 tagged chunk sums
-constexpr uint32_t kRowWord = kSumWord + 2 * kMaxGrid;         // [kMaxPasses][G][kBins / 2] rows
+constexpr uint32_t kSumWord = kHistWord + kMaxPasses * kBins;  // [kMaxGrid] counts per output chunk
+constexpr uint32_t kRowWord = kSumWord + kMaxGrid;             // [kMaxPasses][G][kBins / 2] rows
 constexpr uint32_t kRowWords = kBins / 2;
 constexpr uint32_t kRowGroups = kThreads / (kBins / 8);        // rows read in parallel (8)
 constexpr uint32_t kRowBatch = 10;                             // rows per thread in flight
 static_assert(kSlots >= kMaxPasses + 1, "pass 0's barrier, the ends of passes 0..P-2 and the final one");
-static_assert(kRowWord % 4 == 0 && kSumWord % 2 == 0, "aligned rows and sums");
+static_assert(kRowWord % 4 == 0, "16-byte aligned rows");
 
 __device__ __forceinline__ void red_release_add(uint32_t* p, uint32_t v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -90,15 +98,6 @@ __device__ __forceinline__ void st_relaxed_v4(uint32_t* p, uint4 v) {
                "r"(v.w)
                : "memory");
 }
-__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
-  uint64_t v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
 // Grid barrier on a counter used once per launch (bounded wait).
 __device__ __forceinline__ void arrive_and_wait(uint32_t* slot, uint32_t grid, uint32_t* err) {
   __syncthreads();
@@ -114,6 +113,38 @@ __device__ __forceinline__ void arrive_and_wait(uint32_t* slot, uint32_t grid, u
     }
   }
   __syncthreads();
+}
+
+// Exclusive sums of (a, b) over the CTA, both at once (the caller
+// synchronises before s_w2 is used again).
+__device__ __forceinline__ uint2 excl_scan2(uint32_t a, uint32_t b, uint2* s_w2) {
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  uint32_t x = a, y = b;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t xo = __shfl_up_sync(0xffffffffu, x, d), yo = __shfl_up_sync(0xffffffffu, y, d);
+    if (lane >= static_cast<uint32_t>(d)) {
+      x += xo;
+      y += yo;
+    }
+  }
+  if (lane == 31) s_w2[warp] = make_uint2(x, y);
+  __syncthreads();
+  if (warp == 0) {
+    uint2 w = lane < kWarps ? s_w2[lane] : make_uint2(0u, 0u);
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t xo = __shfl_up_sync(0xffffffffu, w.x, d), yo = __shfl_up_sync(0xffffffffu, w.y, d);
+      if (lane >= static_cast<uint32_t>(d)) {
+        w.x += xo;
+        w.y += yo;
+      }
+    }
+    if (lane < kWarps) s_w2[lane] = w;
+  }
+  __syncthreads();
+  const uint2 before = warp ? s_w2[warp - 1] : make_uint2(0u, 0u);
+  return make_uint2(x - a + before.x, y - b + before.y);
 }
 
 // A row word holds two 16-bit counts, each tagged in its top two bits.
@@ -182,13 +213,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     sm.lstart = sm.base + kBins;
     sm.off = sm.lstart + kBins;
   }
+  uint32_t* vstage = reinterpret_cast<uint32_t*>(smem + S::kSmem);  // this pass's values, in chunk order
   // the row sums of the groups share the value exchange buffer (not live then)
   uint32_t* s_part = sm.xv;
   static_assert(S::kXvBytes >= kRowGroups * kBins * 4, "row-sum partials fit the value exchange");
   __shared__ uint32_t s_hx[kMaxPasses - 1][kBins];  // pass 0: this chunk's counts of the later digits
-  __shared__ uint32_t s_warp[kWarps];
+  __shared__ uint2 s_warp2[kWarps];
   __shared__ unsigned long long s_sum[kWarps];
   __shared__ unsigned long long s_base;
+  __shared__ __align__(8) uint64_t s_mbar;
   const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5, c = blockIdx.x, G = gridDim.x;
   const uint32_t Sz = ((n + G - 1) / G + 3) & ~3u;
   const uint32_t beg = min(c * Sz, n), end = min(beg + Sz, n);
@@ -201,12 +234,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (uint32_t i = t; i < (kMaxPasses - 1) * kBins; i += kThreads) (&s_hx[0][0])[i] = 0u;
   }
   uint32_t* hist = scratch + kHistWord;
-  uint64_t* sums = reinterpret_cast<uint64_t*>(scratch + kSumWord);
+  uint32_t* csum = scratch + kSumWord;
   uint32_t* rows = scratch + kRowWord;
   const uint32_t seq = __ldcg(scratch + kSeqWord);
   const uint32_t tag2 = (seq % 3u + 1u) * 0x40004000u;
   const uint32_t tag16 = (seq % 3u + 1u) << 14;
-  const uint64_t tag32 = static_cast<uint64_t>((seq & 0x7fffffffu) + 1u) << 32;
   // digits from the compressed range
   const uint32_t lo = __ldcg(range), hi = __ldcg(range + 1);
   const uint32_t cull = hi >= lo ? hi - lo + 1u : 0u;  // compressed keys are 0 .. cull
@@ -217,6 +249,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (c == 0 && t == 0) {
     range[2] = passes;
     scratch[kFinalSlot * kLine] = 0u;  // the previous launch's final barrier
+  }
+  if (c == 0)  // this launch's chunk sums (added to after the first barrier)
+    for (uint32_t i = t; i < G; i += kThreads) csum[i] = 0u;
+  const uint32_t nbulk = valid & ~3u;  // values by bulk copy; the last 1-3 by plain loads
+  if (t == 0) {
+    osw::mbar_init(&s_mbar);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   radix::PassArgs a{};
   a.m = n;
@@ -237,6 +276,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t* vout = to_one ? v1 : v2;
     a.shift = p * width;
     a.xform_in = p == 0;
+    const uint32_t* vsrc = p == 0 ? counts : vin;
+    if (t == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      osw::mbar_arrive(&s_mbar, nbulk * 4);
+      if (nbulk) osw::bulk_g2s(vstage, vsrc + beg, nbulk * 4, &s_mbar);
+    }
     radix::TileRegs<uint32_t, false, kItems> R;
     radix::rank_tile<false, S, uint32_t, false, kBits, kItems, true>(kin + beg, valid, a, false, sm, R);
     // publish this chunk's digit counts (lstart) as a tagged row
@@ -278,12 +323,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (uint32_t gg = 0; gg < kRowGroups; ++gg) sum += s_part[gg * kBins + t];
       const uint32_t before = low_half ? sum : tot - own - sum;
-      const uint32_t start = radix::block_excl_scan<kWarps>(tot, s_warp);
-      sm.base[t] = start + before;
-      __syncthreads();
+      // digit starts over all keys and inside this chunk in one scan;
+      // output position of the chunk's p-th key in digit order = off[digit] + p
+      const uint2 st = excl_scan2(tot, own, s_warp2);
+      sm.lstart[t] = st.y;
+      sm.off[t] = st.x + before - st.y;
     }
-    // tile-local digit starts, exchange into digit order, coalesced scatter
-    radix::digit_starts<S, uint32_t>(sm, s_warp);
+    if (!osw::mbar_wait(&s_mbar, p & 1u, err) && t == 0) (void)osw::mbar_wait(&s_mbar, p & 1u, err);
     __syncthreads();
     const uint32_t wbase = warp * 32 * kItems;
     uint16_t* my_wh = sm.wh + warp * kBins;
@@ -294,94 +340,127 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint4* z = reinterpret_cast<uint4*>(my_wh);
       for (uint32_t i = lane; i < kBins / 8; i += 32) z[i] = make_uint4(0, 0, 0, 0);
     }
+    // (key, value) -- in the last pass (digit, value) -- in one 8-byte
+    // exchange over both exchange buffers
+    uint32_t v[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+      const uint32_t idx = wbase + j * 32 + lane;
+      v[j] = 0u;
+      if (idx < valid) {
+        const uint32_t x = idx < nbulk ? vstage[idx] : __ldg(vsrc + beg + idx);
+        v[j] = p == 0 ? (beg + idx) | (min(x, kCntEscape) << kValueBits) : x;
+      }
+    }
+    uint64_t* x64 = reinterpret_cast<uint64_t*>(sm.xk);
+    static_assert(S::kXkBytes + S::kXvBytes >= kTileKeys * 8, "the 8-byte exchange spans both buffers");
+#pragma unroll
+    for (int j = 0; j < kItems; ++j)
+      if (wbase + j * 32 + lane < valid) x64[R.r[j]] = (static_cast<uint64_t>(last ? R.d[j] : R.k[j]) << 32) | v[j];
+    __syncthreads();
     if (!last) {
-#pragma unroll
-      for (int j = 0; j < kItems; ++j)
-        if (wbase + j * 32 + lane < valid) sm.xk[R.r[j]] = R.k[j];
-      uint32_t v[kItems];
-#pragma unroll
-      for (int j = 0; j < kItems; ++j) {
-        const uint32_t idx = wbase + j * 32 + lane;
-        v[j] = 0u;
-        if (idx < valid) {
-          if (p == 0)
-            v[j] = (beg + idx) | (min(__ldg(counts + beg + idx), kCntEscape) << kValueBits);
-          else
-            v[j] = __ldcs(vin + beg + idx);
-        }
-      }
-      __syncthreads();
-      uint32_t dst[kItems];
-#pragma unroll
-      for (int i = 0; i < kItems; ++i) {
-        const uint32_t pos = i * kThreads + t;
-        dst[i] = 0xffffffffu;
-        if (pos < valid) {
-          const uint32_t key = sm.xk[pos];
-          dst[i] = sm.off[(key >> a.shift) & mask] + pos;
-          if (dst[i] < n)
-            kout[dst[i]] = key;
-          else
-            ok = false;
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < kItems; ++j)
-        if (wbase + j * 32 + lane < valid) sm.xv[R.r[j]] = v[j];
-      __syncthreads();
-#pragma unroll
-      for (int i = 0; i < kItems; ++i) {
-        const uint32_t pos = i * kThreads + t;
-        if (pos < valid && dst[i] < n) vout[dst[i]] = sm.xv[pos];
-      }
-      arrive_and_wait(scratch + (1 + p) * kLine, G, err);
-    } else {
-      // (digit, value) in one 8-byte exchange over both exchange buffers;
-      // each sorted position gets its record index (v1) and that
-      // Gaussian's tile count (k1)
-      uint32_t v[kItems];
-#pragma unroll
-      for (int j = 0; j < kItems; ++j) {
-        const uint32_t idx = wbase + j * 32 + lane;
-        v[j] = 0u;
-        if (idx < valid) {
-          if (p == 0)
-            v[j] = (beg + idx) | (min(__ldg(counts + beg + idx), kCntEscape) << kValueBits);
-          else
-            v[j] = __ldcs(vin + beg + idx);
-        }
-      }
-      uint64_t* x64 = reinterpret_cast<uint64_t*>(sm.xk);
-      static_assert(S::kXkBytes + S::kXvBytes >= kTileKeys * 8, "the 8-byte exchange spans both buffers");
-#pragma unroll
-      for (int j = 0; j < kItems; ++j)
-        if (wbase + j * 32 + lane < valid) x64[R.r[j]] = (static_cast<uint64_t>(R.d[j]) << 32) | v[j];
-      __syncthreads();
 #pragma unroll
       for (int i = 0; i < kItems; ++i) {
         const uint32_t pos = i * kThreads + t;
         if (pos < valid) {
           const uint64_t x = x64[pos];
-          const uint32_t w = static_cast<uint32_t>(x), rec = w & kRecMask;
-          const uint32_t dst = sm.off[static_cast<uint32_t>(x >> 32)] + pos;
-          if (dst < n && rec < n) {
-            uint32_t cnt = w >> kValueBits;
-            if (cnt == kCntEscape) cnt = __ldg(counts + rec);
-            v1[dst] = rec;
-            k1[dst] = cnt;
+          const uint32_t key = static_cast<uint32_t>(x >> 32);
+          const uint32_t dst = sm.off[(key >> a.shift) & mask] + pos;
+          if (dst < n) {
+            kout[dst] = key;
+            vout[dst] = static_cast<uint32_t>(x);
           } else {
             ok = false;
           }
         }
       }
+      arrive_and_wait(scratch + (1 + p) * kLine, G, err);
+    } else {
+      // each sorted position gets its record index (v1) and that
+      // Gaussian's tile count (k1); the counts are summed per output chunk
+      // per-warp rows of counts per output chunk, over the staged values
+      // (read before the exchange barrier above)
+      static_assert(kWarps * kMaxGrid * 4 <= kTileKeys * 4, "per-warp chunk sums fit the staging buffer");
+      uint32_t* w_csum = vstage + warp * kMaxGrid;
+      for (uint32_t k = lane; k < G; k += 32) w_csum[k] = 0u;
+      __syncwarp();
+      const float inv_sz = 1.0f / static_cast<float>(Sz);
+      uint32_t q[kItems], cnt[kItems];  // output chunk (all ones: none) and count per item
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        const uint32_t pos = i * kThreads + t;
+        q[i] = 0xffffffffu;
+        cnt[i] = 0u;
+        if (pos < valid) {
+          const uint64_t x = x64[pos];
+          const uint32_t w = static_cast<uint32_t>(x), rec = w & kRecMask;
+          const uint32_t dst = sm.off[static_cast<uint32_t>(x >> 32)] + pos;
+          if (dst < n && rec < n) {
+            uint32_t c1 = w >> kValueBits;
+            if (c1 == kCntEscape) c1 = __ldg(counts + rec);
+            cnt[i] = c1;
+            v1[dst] = rec;
+            k1[dst] = c1;
+            // dst / Sz: a float estimate (dst < 2^22 is exact) corrected by one
+            uint32_t qq = static_cast<uint32_t>(static_cast<float>(dst) * inv_sz);
+            if (qq * Sz > dst) --qq;
+            else if ((qq + 1u) * Sz <= dst) ++qq;
+            q[i] = qq;
+          } else {
+            ok = false;
+          }
+        }
+      }
+      // q never decreases from lane to lane, so equal chunks are runs: an
+      // inclusive scan of the counts over the lanes (all items at once),
+      // then a run's last lane adds its scan and its first lane subtracts
+      // the scan before it (modulo 2^32, exact for every chunk sum)
+      uint32_t incl[kItems];
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) incl[i] = cnt[i];
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+          const uint32_t o = __shfl_up_sync(0xffffffffu, incl[i], d);
+          if (lane >= static_cast<uint32_t>(d)) incl[i] += o;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        const uint32_t qp = __shfl_up_sync(0xffffffffu, q[i], 1), qn = __shfl_down_sync(0xffffffffu, q[i], 1);
+        if (q[i] != 0xffffffffu) {
+          if (lane == 31 || qn != q[i]) atomicAdd(&w_csum[q[i]], incl[i]);
+          if (lane != 0 && qp != q[i]) atomicAdd(&w_csum[q[i]], cnt[i] - incl[i]);
+        }
+      }
+      __syncthreads();
+      for (uint32_t k = t; k < G; k += kThreads) {
+        uint32_t sum = 0;
+#pragma unroll
+        for (uint32_t w = 0; w < kWarps; ++w) sum += vstage[w * kMaxGrid + k];
+        if (sum) atomicAdd(csum + k, sum);
+      }
       arrive_and_wait(scratch + kFinalSlot * kLine, G, err);
     }
   }
   if (!ok) latch_error(err, TDGS_ERR_CAPACITY, kSiteRadixRange);
-  // The pair offsets: counts in depth order (k1) scanned; kItems consecutive
-  // positions per thread, chunk sums by a tagged look-back.
+  // The pair offsets: counts in depth order (k1) scanned from the sum of
+  // the chunks before this one; kItems consecutive positions per thread.
   {
     static_assert(kItems % 4 == 0, "16-byte loads of the counts");
+    if (warp == 0) {
+      constexpr uint32_t kPer = kMaxGrid / 32;
+      uint64_t before = 0;
+#pragma unroll
+      for (uint32_t i = 0; i < kPer; ++i) {
+        const uint32_t cc = lane + 32 * i;
+        if (cc < c) before += __ldcg(csum + cc);
+      }
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) before += __shfl_xor_sync(0xffffffffu, before, d);
+      if (lane == 0) s_base = before;
+    }
     const uint32_t pos0 = beg + t * kItems;
     uint32_t cnt[kItems];
     uint64_t sum = 0;
@@ -410,61 +489,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 31) s_sum[warp] = xs;
     __syncthreads();
     if (t == 0) {
-      unsigned long long run = 0;
+      unsigned long long run = s_base;
       for (uint32_t w = 0; w < kWarps; ++w) {
         const unsigned long long v = s_sum[w];
         s_sum[w] = run;
         run += v;
       }
-      // this chunk's sum for the chunks after it (saturated: an overflow
-      // is latched below)
-      st_relaxed_u64(sums + c, tag32 | (run > 0xffffffffull ? 0xffffffffull : run));
-      s_base = run;
+      if (run > 0xffffffffull) latch_error(err, TDGS_ERR_OVERFLOW, kSiteScan);
     }
     __syncthreads();
-    const uint64_t csum = s_base;
     uint64_t run = xs - sum + s_sum[warp];
-    __syncthreads();
-    if (warp == 0) {
-      // all sums of the chunks before this one in flight at once, then the
-      // ones not yet published again (bounded)
-      constexpr uint32_t kPer = kMaxGrid / 32;
-      uint64_t w[kPer];
-      uint32_t pend = 0;
-#pragma unroll
-      for (uint32_t i = 0; i < kPer; ++i) {
-        const uint32_t cc = lane + 32 * i;
-        w[i] = tag32;
-        if (cc < c) {
-          w[i] = ld_relaxed_u64(sums + cc);
-          if ((w[i] & 0xffffffff00000000ull) != tag32) pend |= 1u << i;
-        }
-      }
-      uint32_t spins = 0;
-      while (pend) {
-        if (++spins > kSpinLimit) {
-          latch_error(err, TDGS_ERR_TIMEOUT, kSiteBarrier);
-          break;
-        }
-        __nanosleep(32);
-#pragma unroll
-        for (uint32_t i = 0; i < kPer; ++i) {
-          if (pend & (1u << i)) {
-            w[i] = ld_relaxed_u64(sums + lane + 32 * i);
-            if ((w[i] & 0xffffffff00000000ull) == tag32) pend &= ~(1u << i);
-          }
-        }
-      }
-      unsigned long long before = 0;
-#pragma unroll
-      for (uint32_t i = 0; i < kPer; ++i) before += w[i] & 0xffffffffull;
-#pragma unroll
-      for (int d = 16; d > 0; d >>= 1) before += __shfl_xor_sync(0xffffffffu, before, d);
-      if (lane == 0) s_base = before;
-    }
-    __syncthreads();
-    run += s_base;
-    if (t == 0 && s_base + csum > 0xffffffffull) latch_error(err, TDGS_ERR_OVERFLOW, kSiteScan);
 #pragma unroll
     for (int j = 0; j < kItems; j += 4) {
       uint32_t o[4];
@@ -501,7 +535,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // ------------------------------------------------------------- host side
 uint32_t depth_sort_grid() {
   static const radix::Kernel k{reinterpret_cast<const void*>(&depth::k_depth_sort), depth::kBits, depth::kThreads,
-                               depth::kItems, depth::S::kSmem, 1};
+                               depth::kItems, depth::kSmem, 1};
   uint32_t g = radix::resident_ctas(k, 1);
   return g > radix::kMaxGrid ? radix::kMaxGrid : g;
 }
@@ -526,7 +560,7 @@ cudaError_t launch_depth_sort(uint32_t grid, const uint32_t* key0, uint32_t* k1,
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(depth::kThreads);
-  cfg.dynamicSmemBytes = depth::S::kSmem;
+  cfg.dynamicSmemBytes = depth::kSmem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
