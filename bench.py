@@ -168,6 +168,11 @@ def algorithmic_bytes(kernel: str, items: int, n: int, m: int, tiles: int, depth
         # single-launch form also scans the counts in depth order (index in,
         # gathered count, offset out)
         return 16.0 * items * abs(depth_passes) + (12.0 * items if depth_passes < 0 else 0.0)
+    if kernel == "count_depth_sort":  # the tile count step and the single-launch depth sort:
+        # record in (16 B); per pass (u32 key, u32 value) in and out (pass 0
+        # reads no key, the last writes index and count); offsets: count in,
+        # offset out
+        return 16.0 * items + 16.0 * items * abs(depth_passes) + 8.0 * items
     if kernel == "scan_by_depth":    # index in, gathered count, offset out
         return 12.0 * items
     if kernel == "duplicate_by_depth":  # index, offset, record in; {depth key, index} out; 4 B per pair out
@@ -261,7 +266,7 @@ def run_ours(args, rank, world, local_rank, dist):
     ctx.sync()
     ktimes = ctx.kernel_times()
     ctx.enable_timing(False)
-    dsl = ktimes.get("depth_sort", {}).get("launches", 0)
+    dsl = ktimes.get("depth_sort", {}).get("launches", 0) + ktimes.get("count_depth_sort", {}).get("launches", 0)
     depth_passes = -ctx.depth_passes() if dsl == args.steps else 1
     step_ms = [a.elapsed_time(b) for a, b in ev]
     dev_s = sum(step_ms) / 1e3

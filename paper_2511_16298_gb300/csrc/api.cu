@@ -44,6 +44,17 @@ const char* site_name(uint32_t site) {
   return "device";
 }
 
+// The early pair count in mapped host memory: the count kernel writes
+// {total, err, site}; the single launch that counts and sorts writes the
+// tagged word seq (16 bits) << 48 | min(error, 255) << 40 | min(M, 2^40 - 1).
+struct EarlyStatus {
+  uint64_t total;
+  uint32_t err;
+  uint32_t site;
+  uint64_t tagged;
+  uint64_t pad;
+};
+
 struct Buffer {
   void* p = nullptr;
   size_t bytes = 0;
@@ -52,13 +63,14 @@ struct Buffer {
 enum KernelId {
   kKCount, kKScan, kKDuplicate, kKRanges, kKRadixPass,
   kKFrameCount, kKDepthSort, kKFrameScan, kKDupDepth, kKTilePass, kKTileExpand, kKPreprocess, kKBitonic, kKRender, kKPreCount, kKNormRange, kKNormDup, kKNormPass,
-  kKNormRanges, kKRenderOrder, kKSortHist, kKOnesweep, kKNum
+  kKNormRanges, kKRenderOrder, kKSortHist, kKOnesweep, kKCountDepth, kKNum
 };
 const char* const kKernelNames[kKNum] = {
     "count_tiles",  "scan",       "duplicate_keys",     "tile_ranges",    "radix_pass",
     "frame_count",  "depth_sort", "scan_by_depth", "duplicate_by_depth", "tile_sort_pass",
     "tile_expand_pass", "preprocess", "bitonic_sort", "render", "preprocess_count", "norm_range",
-    "norm_duplicate", "norm_sort_pass", "norm_ranges", "render_order", "sort_histogram", "onesweep_pass"};
+    "norm_duplicate", "norm_sort_pass", "norm_ranges", "render_order", "sort_histogram", "onesweep_pass",
+    "count_depth_sort"};
 
 // View table as stored in device memory (SoA, fixed maximum size).
 struct ViewBlob {
@@ -86,9 +98,11 @@ struct tdgs_context {
   // Pinned and mapped: the count kernel writes the pair count and the error
   // word here itself, so reading them back needs no copy (a copy would
   // queue behind other streams' large downloads on the copy engine).
-  DevStatus* h_early = nullptr;
-  DevStatus* d_early = nullptr;    // its device address
-  cudaEvent_t ev_count = nullptr;  // recorded after the count kernel
+  EarlyStatus* h_early = nullptr;
+  EarlyStatus* d_early = nullptr;  // its device address
+  cudaEvent_t ev_count = nullptr;  // recorded after the count kernel (or the launch that counts and sorts)
+  uint32_t early_seq = 0;          // the last seq asked of the launch that counts and sorts
+  bool early_fused = false;        // the last front half counted inside the depth sort
   uint32_t* d_tickets = nullptr;  // [1] count blocks (reset by the kernel), [2..3] radix grid barrier
   uint32_t ticket_base[2] = {0, 0};
   Buffer scan_status, sort_scratch;
@@ -455,7 +469,7 @@ tdgs_status tdgs_context_create(tdgs_context** out, int device) {
       cudaMemset(ctx->d_range, 0, 8 * sizeof(uint32_t)) != cudaSuccess ||
       cudaMemset(ctx->d_range, 0xff, sizeof(uint32_t)) != cudaSuccess ||
       cudaMallocHost(&ctx->h_status, sizeof(DevStatus)) != cudaSuccess ||
-      cudaHostAlloc(&ctx->h_early, sizeof(DevStatus), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostAlloc(&ctx->h_early, sizeof(EarlyStatus), cudaHostAllocMapped) != cudaSuccess ||
       cudaHostGetDevicePointer(reinterpret_cast<void**>(&ctx->d_early), ctx->h_early, 0) != cudaSuccess ||
       cudaMalloc(&ctx->d_views, sizeof(ViewBlob)) != cudaSuccess ||
       cudaMallocHost(&ctx->h_views, sizeof(ViewBlob)) != cudaSuccess ||
@@ -467,6 +481,8 @@ tdgs_status tdgs_context_create(tdgs_context** out, int device) {
     tdgs_context_destroy(ctx);
     return TDGS_ERR_OUT_OF_MEMORY;
   }
+  // pinned memory may come back from an earlier allocation: no stale seq
+  std::memset(ctx->h_early, 0, sizeof(EarlyStatus));
   *out = ctx;
   return TDGS_OK;
 }
@@ -790,6 +806,34 @@ tdgs_status run_front(tdgs_context* ctx, cudaStream_t s, bool early_total = fals
                      static_cast<uint32_t*>(ctx->f_dkey[2].p)};
   uint32_t* dv[3] = {static_cast<uint32_t*>(ctx->f_dval[0].p), static_cast<uint32_t*>(ctx->f_dval[1].p),
                      static_cast<uint32_t*>(ctx->f_dval[2].p)};
+  const DepthPlan dp = plan_depth_sort(n_all, ctx->tuning.depth_digit_bits, ctx->tuning.ctas_per_sm);
+  DepthSortArgs da{};
+  da.vt = vt;
+  da.total = &ctx->d_status->total;
+  da.k1 = dk[1];
+  da.v1 = dv[1];
+  da.k2 = dk[2];
+  da.v2 = dv[2];
+  da.counts = counts;
+  da.offsets = static_cast<uint32_t*>(ctx->f_soff.p);
+  da.range = ctx->d_range;
+  da.n = n_all;
+  da.scratch = static_cast<uint32_t*>(ctx->f_dsort.p);
+  da.err = err_word(ctx);
+  ctx->early_fused = dp.resident && n_all > 0 && !ctx->proj_on;
+  if (ctx->early_fused) {
+    // one launch: counts, M (also to the mapped host status, tagged with a
+    // fresh seq), the depth sort and the offsets
+    if (early_total) {
+      da.host_status = reinterpret_cast<uint32_t*>(&ctx->d_early->tagged);
+      ctx->early_seq = (ctx->early_seq + 1) & 0xffffu;
+      if (ctx->early_seq == 0) ctx->early_seq = 1;  // 0: never written
+      da.host_seq = ctx->early_seq;
+    }
+    TDGS_TRACED(ctx, kKCountDepth, n_all, s, launch_count_depth_sort(dp.grid, da, s));
+    if (early_total) TDGS_CUDA(ctx, cudaEventRecord(ctx->ev_count, s));
+    return TDGS_OK;
+  }
   // launched even for zero Gaussians: it writes the view starts and M = 0
   TDGS_TRACED(ctx, ctx->proj_on ? kKPreCount : kKFrameCount, n_all ? n_all : 1, s,
               launch_views_count(vt, n_all, counts, dk[0], dv[0], err_word(ctx), ctx->d_tickets + 1,
@@ -800,14 +844,11 @@ tdgs_status run_front(tdgs_context* ctx, cudaStream_t s, bool early_total = fals
     // kernel wrote them to the mapped host status (h_early)
     TDGS_CUDA(ctx, cudaEventRecord(ctx->ev_count, s));
   }
-  const DepthPlan dp = plan_depth_sort(n_all, ctx->tuning.depth_digit_bits, ctx->tuning.ctas_per_sm);
   const uint32_t dpasses = dp.passes;
   uint32_t* scratch = static_cast<uint32_t*>(ctx->sort_scratch.p);
   if (dp.resident) {  // one launch: the sort (pass count from the depth range) and the offsets
-    TDGS_TRACED(ctx, kKDepthSort, n_all, s,
-                launch_depth_sort(dp.grid, dk[0], dk[1], dv[1], dk[2], dv[2], ctx->d_range + 2, counts,
-                                  static_cast<uint32_t*>(ctx->f_soff.p), n_all,
-                                  static_cast<uint32_t*>(ctx->f_dsort.p), err_word(ctx), s));
+    da.key0 = dk[0];
+    TDGS_TRACED(ctx, kKDepthSort, n_all, s, launch_depth_sort(dp.grid, da, s));
   } else {
     for (uint32_t p = 0; p < dpasses; ++p) {
       TDGS_TRACED(ctx, kKDepthSort, n_all, s,
@@ -898,10 +939,31 @@ tdgs_status sort_views_exact(tdgs_context* ctx, cudaStream_t s, uint32_t* m_out)
   if (st != TDGS_OK) return st;
   st = run_front(ctx, s, true);
   if (st != TDGS_OK) return st;
-  TDGS_CUDA(ctx, cudaEventSynchronize(ctx->ev_count));
-  const volatile DevStatus* early = ctx->h_early;
-  const uint32_t early_err = early->err;
-  const uint64_t early_total = early->total;
+  uint32_t early_err = 0;
+  uint64_t early_total = 0;
+  if (ctx->early_fused) {
+    // the launch that counts and sorts writes M early and keeps running:
+    // wait for the word with its seq
+    uint64_t* tp = &ctx->h_early->tagged;
+    uint64_t w = __atomic_load_n(tp, __ATOMIC_ACQUIRE);
+    while ((w >> 48) != ctx->early_seq) {
+      const cudaError_t q = cudaEventQuery(ctx->ev_count);
+      if (q == cudaSuccess) {
+        w = __atomic_load_n(tp, __ATOMIC_ACQUIRE);
+        if ((w >> 48) == ctx->early_seq) break;
+        return fail(ctx, TDGS_ERR_CUDA, "the depth sort ended without reporting the pair count");
+      }
+      if (q != cudaErrorNotReady) return cuda_fail(ctx, q, "cudaEventQuery");
+      w = __atomic_load_n(tp, __ATOMIC_ACQUIRE);
+    }
+    early_err = static_cast<uint32_t>((w >> 40) & 0xffu);
+    early_total = w & ((1ull << 40) - 1);
+  } else {
+    TDGS_CUDA(ctx, cudaEventSynchronize(ctx->ev_count));
+    const volatile EarlyStatus* early = ctx->h_early;
+    early_err = early->err;
+    early_total = early->total;
+  }
   if (early_err) {
     note_device_error(ctx);
     TDGS_CUDA(ctx, cudaStreamSynchronize(s));

@@ -74,7 +74,8 @@ constexpr uint32_t kSlots = 8;                      // barrier counters, one lin
 constexpr uint32_t kFinalSlot = kSlots - 1;         // before the offsets
 constexpr uint32_t kSeqWord = kSlots * kLine;       // launch number
 constexpr uint32_t kHistWord = kSeqWord + kLine;    // [kMaxPasses][kBins] digit totals
-constexpr uint32_t kSumWord = kHistWord + kMaxPasses * kBins;  // [kMaxGrid] counts per output chunk
+constexpr uint32_t kRawWord = kHistWord + kMaxPasses * kBins;  // fused count: [kBins] keys by low 9 bits, culled
+constexpr uint32_t kSumWord = kRawWord + kBins + kLine;          // [kMaxGrid] counts per output chunk
 constexpr uint32_t kRowWord = kSumWord + kMaxGrid;             // [kMaxPasses][G][kBins / 2] rows
 constexpr uint32_t kRowWords = kBins / 2;
 constexpr uint32_t kRowGroups = kThreads / (kBins / 8);        // rows read in parallel (8)
@@ -194,11 +195,22 @@ __device__ __forceinline__ void sum_rows(const uint32_t* __restrict__ rows, uint
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
-    k_depth_sort(const uint32_t* __restrict__ key0, uint32_t* __restrict__ k1, uint32_t* __restrict__ v1,
-                 uint32_t* __restrict__ k2, uint32_t* __restrict__ v2, const uint32_t* __restrict__ counts,
-                 uint32_t* __restrict__ offsets, uint32_t* __restrict__ range, uint32_t n,
-                 uint32_t* __restrict__ scratch, uint32_t* __restrict__ err) {
+// kCount: the tile count step runs first in the same launch (records of
+// the view table in, keys kept in registers); else the keys come from the
+// count kernel (key0) with the range it published.
+template <bool kCount>
+__global__ void __launch_bounds__(kThreads, 1) k_depth_sort(DepthSortArgs A) {
+  const uint32_t* __restrict__ key0 = A.key0;
+  uint32_t* __restrict__ k1 = A.k1;
+  uint32_t* __restrict__ v1 = A.v1;
+  uint32_t* __restrict__ k2 = A.k2;
+  uint32_t* __restrict__ v2 = A.v2;
+  uint32_t* __restrict__ counts = A.counts;
+  uint32_t* __restrict__ offsets = A.offsets;
+  uint32_t* __restrict__ range = A.range;
+  uint32_t* __restrict__ scratch = A.scratch;
+  uint32_t* __restrict__ err = A.err;
+  const uint32_t n = A.n;
   extern __shared__ __align__(16) unsigned char smem[];
   radix::Smem<uint32_t> sm;
   {
@@ -239,15 +251,138 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t seq = __ldcg(scratch + kSeqWord);
   const uint32_t tag2 = (seq % 3u + 1u) * 0x40004000u;
   const uint32_t tag16 = (seq % 3u + 1u) << 14;
+  uint32_t* raw = scratch + kRawWord;
+  radix::TileRegs<uint32_t, false, kItems> R;
+  __shared__ uint32_t s_h0[kCount ? kBins : 1];  // fused count: pass 0's digit totals
+  uint32_t lo, hi;
+  if constexpr (kCount) {
+    // ---- the tile count step (Sec. II-A): per record its tile count and
+    // depth key (raw depth bits; all ones without pairs), kept in R.k and,
+    // for the counts, in the staging buffer; per view its pair total; the
+    // smallest / largest key with pairs; the keys' low 9 bits counted
+    __shared__ uint32_t s_begin[kMaxViews + 1];
+    __shared__ const float4* s_g[kMaxViews];
+    __shared__ FrameGeom s_geom[kMaxViews];
+    __shared__ unsigned long long s_tot[kMaxViews];
+    __shared__ uint32_t s_raw[kBins];
+    __shared__ uint32_t s_lo, s_hi, s_cull;
+    const ViewTable& vt = A.vt;
+    const uint32_t nv = vt.nv;
+    for (uint32_t v = t; v <= nv; v += kThreads) s_begin[v] = vt.rec_begin[v];
+    for (uint32_t v = t; v < nv; v += kThreads) {
+      s_g[v] = vt.g[v];
+      s_geom[v] = vt.geom[v];
+      s_tot[v] = 0ull;
+    }
+    s_raw[t] = 0u;
+    s_h0[t] = 0u;
+    if (t == 0) {
+      s_lo = 0xffffffffu;
+      s_hi = 0u;
+      s_cull = 0u;
+    }
+    __syncthreads();
+    const uint32_t wbase = warp * 32 * kItems;
+    uint32_t klo = 0xffffffffu, khi = 0u, nculled = 0u;
+    unsigned long long tsum = 0;  // one view: this thread's pairs
+    bool bad = false;
+    constexpr int kGroup = 16;  // records in flight per thread
+#pragma unroll
+    for (int j0 = 0; j0 < kItems; j0 += kGroup) {
+      float4 rec[kGroup];
+      uint32_t vv[kGroup];
+#pragma unroll
+      for (int u = 0; u < kGroup; ++u) {
+        const uint32_t idx = wbase + (j0 + u) * 32 + lane, i = beg + idx;
+        vv[u] = 0u;
+        rec[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (idx < valid) {
+          vv[u] = nv == 1 ? 0u : find_view(s_begin, nv, i);
+          rec[u] = __ldg(s_g[vv[u]] + (i - s_begin[vv[u]]));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kGroup; ++u) {
+        const int j = j0 + u;
+        const uint32_t idx = wbase + j * 32 + lane;
+        R.k[j] = 0xffffffffu;
+        if (idx < valid) {
+          const TileRect tr = tile_rect(rec[u], s_geom[vv[u]]);
+          bad |= tr.invalid;
+          const uint32_t cnt = tr.count;
+          vstage[idx] = cnt;
+          if (cnt >= kCntEscape) counts[beg + idx] = cnt;
+          if (cnt) {
+            const uint32_t key = __float_as_uint(rec[u].z);
+            R.k[j] = key;
+            klo = min(klo, key);
+            khi = max(khi, key);
+            atomicAdd(&s_raw[key & (kBins - 1)], 1u);
+            if (nv == 1)
+              tsum += cnt;
+            else
+              atomicAdd(&s_tot[vv[u]], static_cast<unsigned long long>(cnt));
+          } else {
+            ++nculled;
+          }
+        }
+      }
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) latch_error(err, TDGS_ERR_INVALID_ARGUMENT, kSiteViewsCount);
+    klo = __reduce_min_sync(0xffffffffu, klo);
+    khi = __reduce_max_sync(0xffffffffu, khi);
+    nculled = __reduce_add_sync(0xffffffffu, nculled);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, d);
+    if (lane == 0) {
+      atomicMin(&s_lo, klo);
+      atomicMax(&s_hi, khi);
+      if (nculled) atomicAdd(&s_cull, nculled);
+      if (nv == 1 && tsum) atomicAdd(&s_tot[0], tsum);
+    }
+    __syncthreads();
+    if (s_raw[t]) atomicAdd(raw + t, s_raw[t]);
+    for (uint32_t v = t; v < nv; v += kThreads)
+      if (s_tot[v]) atomicAdd(reinterpret_cast<unsigned long long*>(vt.vtot + v), s_tot[v]);
+    if (t == 0) {
+      if (s_lo != 0xffffffffu) atomicMin(range, s_lo);
+      if (s_hi != 0u) atomicMax(range + 1, s_hi);
+      if (s_cull) atomicAdd(raw + kBins, s_cull);
+    }
+    arrive_and_wait(scratch, G, err);  // every record counted
+    lo = __ldcg(range);
+    hi = __ldcg(range + 1);
+    if (c == 0 && t == 0) {
+      // each view's first pair in the sorted list and M, also for the host
+      uint64_t run = 0;
+      for (uint32_t v = 0; v < nv; ++v) {
+        vt.pbeg[v] = static_cast<uint32_t>(run);
+        run += __ldcg(reinterpret_cast<const unsigned long long*>(vt.vtot + v));
+      }
+      vt.pbeg[nv] = static_cast<uint32_t>(run);
+      *A.total = run;
+      range[2] = lo;
+      range[3] = hi;
+      if (A.host_status) {
+        // one 8-byte store (no fence: nothing else needs ordering with it)
+        const uint64_t m40 = run < (1ull << 40) ? run : (1ull << 40) - 1;
+        const uint64_t e8 = min(__ldcg(err), 255u);
+        *reinterpret_cast<volatile uint64_t*>(A.host_status) =
+            (static_cast<uint64_t>(A.host_seq) << 48) | (e8 << 40) | m40;
+      }
+    }
+  } else {
+    lo = __ldcg(range + 2);
+    hi = __ldcg(range + 3);
+  }
   // digits from the compressed range
-  const uint32_t lo = __ldcg(range), hi = __ldcg(range + 1);
   const uint32_t cull = hi >= lo ? hi - lo + 1u : 0u;  // compressed keys are 0 .. cull
   const uint32_t bits = cull ? 32u - static_cast<uint32_t>(__clz(cull)) : 0u;
   const uint32_t passes = bits ? (bits + kBits - 1) / kBits : 1u;
   const uint32_t width = (bits + passes - 1) / passes;
   const uint32_t mask = width ? (1u << width) - 1u : 0u;
   if (c == 0 && t == 0) {
-    range[2] = passes;
+    range[4] = passes;
     scratch[kFinalSlot * kLine] = 0u;  // the previous launch's final barrier
   }
   if (c == 0)  // this launch's chunk sums (added to after the first barrier)
@@ -256,6 +391,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (t == 0) {
     osw::mbar_init(&s_mbar);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if constexpr (kCount) {
+    // pass 0's digit totals: digit 0 of key - lo is (low 9 bits - lo) & mask
+    // (width <= 9); the culled keys all have cull & mask
+    const uint32_t r = __ldcg(raw + t);
+    if (r) atomicAdd(&s_h0[(t - lo) & mask], r);
+    if (t == 0) {
+      const uint32_t nc = __ldcg(raw + kBins);
+      if (nc) atomicAdd(&s_h0[cull & mask], nc);
+    }
   }
   radix::PassArgs a{};
   a.m = n;
@@ -277,13 +422,39 @@ __global__ void __launch_bounds__(kThreads, 1)
     a.shift = p * width;
     a.xform_in = p == 0;
     const uint32_t* vsrc = p == 0 ? counts : vin;
+    const bool counted = kCount && p == 0;  // values (the counts) already staged by the count step
+    const uint32_t nstaged = counted ? valid : nbulk;
     if (t == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      osw::mbar_arrive(&s_mbar, nbulk * 4);
-      if (nbulk) osw::bulk_g2s(vstage, vsrc + beg, nbulk * 4, &s_mbar);
+      osw::mbar_arrive(&s_mbar, counted ? 0u : nbulk * 4);
+      if (!counted && nbulk) osw::bulk_g2s(vstage, vsrc + beg, nbulk * 4, &s_mbar);
     }
-    radix::TileRegs<uint32_t, false, kItems> R;
-    radix::rank_tile<false, S, uint32_t, false, kBits, kItems, true>(kin + beg, valid, a, false, sm, R);
+    {
+      // this pass's keys: pass 0 compresses them (from the count step's
+      // registers or from key0), later passes read them as written
+      const uint32_t wbase = warp * 32 * kItems;
+      if (counted) {
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+          const uint32_t idx = wbase + j * 32 + lane;
+          R.k[j] = idx < valid ? (R.k[j] == 0xffffffffu ? cull : R.k[j] - lo) : 0u;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+          const uint32_t idx = wbase + j * 32 + lane;
+          R.k[j] = idx < valid ? __ldcs(kin + beg + idx) : 0u;
+        }
+        if (p == 0) {
+#pragma unroll
+          for (int j = 0; j < kItems; ++j)
+            if (wbase + j * 32 + lane < valid) R.k[j] = R.k[j] == 0xffffffffu ? cull : R.k[j] - lo;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kItems; ++j) R.d[j] = (R.k[j] >> a.shift) & mask;
+      radix::rank_keys<false, S, uint32_t, false, kBits, kItems>(valid, sm, R);
+    }
     // publish this chunk's digit counts (lstart) as a tagged row
     if (t < kBins / 8) {
       const uint32_t* ls = sm.lstart + 8 * t;
@@ -295,7 +466,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       st_relaxed_v4(rows + (static_cast<size_t>(p) * G + c) * kRowWords + 4 * t, w);
     }
     if (p == 0) {
-      // every pass's digit totals, ready after one grid barrier
+      // every later pass's digit totals (ready at this pass's end barrier);
+      // pass 0's own after one more barrier, unless the count step gave them
       const uint32_t wbase = warp * 32 * kItems;
       for (uint32_t pp = 1; pp < passes; ++pp) {
 #pragma unroll
@@ -303,15 +475,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (wbase + j * 32 + lane < valid) atomicAdd(&s_hx[pp - 1][(R.k[j] >> (pp * width)) & mask], 1u);
       }
       __syncthreads();
-      if (sm.lstart[t]) atomicAdd(hist + t, sm.lstart[t]);
       for (uint32_t pp = 1; pp < passes; ++pp)
         if (s_hx[pp - 1][t]) atomicAdd(hist + pp * kBins + t, s_hx[pp - 1][t]);
-      arrive_and_wait(scratch, G, err);
+      if constexpr (!kCount) {
+        if (sm.lstart[t]) atomicAdd(hist + t, sm.lstart[t]);
+        arrive_and_wait(scratch, G, err);
+      }
     }
     // output base per digit: keys of smaller digits + this digit's keys in
     // the chunks before this one
     {
-      const uint32_t tot = __ldcg(hist + p * kBins + t);
+      const uint32_t tot = (kCount && p == 0) ? s_h0[t] : __ldcg(hist + p * kBins + t);
       const uint32_t own = sm.lstart[t];
       uint32_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       sum_rows(rows + static_cast<size_t>(p) * G * kRowWords, low_half ? 0u : c + 1, low_half ? c : G, g, q,
@@ -348,7 +522,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t idx = wbase + j * 32 + lane;
       v[j] = 0u;
       if (idx < valid) {
-        const uint32_t x = idx < nbulk ? vstage[idx] : __ldg(vsrc + beg + idx);
+        const uint32_t x = idx < nstaged ? vstage[idx] : __ldg(vsrc + beg + idx);
         v[j] = p == 0 ? (beg + idx) | (min(x, kCntEscape) << kValueBits) : x;
       }
     }
@@ -525,6 +699,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (c == 0) {
     for (uint32_t i = t; i < passes * kBins; i += kThreads) hist[i] = 0u;
+    if constexpr (kCount) {
+      raw[t] = 0u;
+      if (t == 0) {
+        raw[kBins] = 0u;
+        range[0] = 0xffffffffu;
+        range[1] = 0u;
+      }
+    }
     if (t < passes) scratch[t * kLine] = 0u;  // slots 0 .. passes-1
     if (t == 0) scratch[kSeqWord] = seq + 1u;
   }
@@ -533,10 +715,39 @@ __global__ void __launch_bounds__(kThreads, 1)
 }  // namespace depth
 
 // ------------------------------------------------------------- host side
+namespace {
+radix::Kernel depth_kernel(bool count) {
+  return radix::Kernel{count ? reinterpret_cast<const void*>(&depth::k_depth_sort<true>)
+                             : reinterpret_cast<const void*>(&depth::k_depth_sort<false>),
+                       depth::kBits, depth::kThreads, depth::kItems, depth::kSmem, 1};
+}
+
+cudaError_t launch_depth(bool count, uint32_t grid, const DepthSortArgs& a, cudaStream_t s) {
+  if (a.n == 0) return cudaSuccess;
+  if (grid == 0 || grid > radix::kMaxGrid || a.n > depth_sort_capacity(grid)) return cudaErrorInvalidConfiguration;
+  if (count && a.vt.nv > kMaxViews) return cudaErrorInvalidValue;
+  DepthSortArgs args = a;
+  void* params[] = {(void*)&args};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(depth::kThreads);
+  cfg.dynamicSmemBytes = depth::kSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, depth_kernel(count).fn, params);
+}
+}  // namespace
+
 uint32_t depth_sort_grid() {
-  static const radix::Kernel k{reinterpret_cast<const void*>(&depth::k_depth_sort), depth::kBits, depth::kThreads,
-                               depth::kItems, depth::kSmem, 1};
-  uint32_t g = radix::resident_ctas(k, 1);
+  // both forms: one CTA per SM (the occupancy query also sets their shared
+  // memory limit on this device)
+  const uint32_t g0 = radix::resident_ctas(depth_kernel(false), 1);
+  const uint32_t g1 = radix::resident_ctas(depth_kernel(true), 1);
+  const uint32_t g = g0 < g1 ? g0 : g1;
   return g > radix::kMaxGrid ? radix::kMaxGrid : g;
 }
 
@@ -550,24 +761,12 @@ size_t depth_sort_scratch_words(uint32_t grid) {
   return depth::kRowWord + static_cast<size_t>(depth::kMaxPasses) * grid * depth::kRowWords;
 }
 
-cudaError_t launch_depth_sort(uint32_t grid, const uint32_t* key0, uint32_t* k1, uint32_t* v1, uint32_t* k2,
-                              uint32_t* v2, uint32_t* range, const uint32_t* counts, uint32_t* offsets, uint32_t n,
-                              uint32_t* scratch, uint32_t* err, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  if (grid == 0 || grid > radix::kMaxGrid || n > depth_sort_capacity(grid)) return cudaErrorInvalidConfiguration;
-  void* args[] = {(void*)&key0, (void*)&k1, (void*)&v1, (void*)&k2, (void*)&v2, (void*)&counts,
-                  (void*)&offsets, (void*)&range, (void*)&n, (void*)&scratch, (void*)&err};
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(depth::kThreads);
-  cfg.dynamicSmemBytes = depth::kSmem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(&depth::k_depth_sort), args);
+cudaError_t launch_depth_sort(uint32_t grid, const DepthSortArgs& a, cudaStream_t s) {
+  return launch_depth(false, grid, a, s);
+}
+
+cudaError_t launch_count_depth_sort(uint32_t grid, const DepthSortArgs& a, cudaStream_t s) {
+  return launch_depth(true, grid, a, s);
 }
 
 }  // namespace tdgs

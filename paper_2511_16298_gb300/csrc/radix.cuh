@@ -538,16 +538,17 @@ struct TileRegs {
 // digits; with at most 64 the per-warp counts are left for scatter_tile,
 // which folds the prefix into its one-warp digit starts.  Each warp's
 // counter row is zero on entry.
-// kXform: the resident depth sort's key compression may apply (a.xform_in).
+// kXform: the single-launch depth sort's key compression may apply
+// (a.xform_in).  rank_keys is the same after the load, for keys and digits
+// already in R.k / R.d (item j of lane l of warp w is tile item
+// w * 32 * kItems + j * 32 + l).
+template <bool kFull, typename S, typename K, bool kExpand, int kBits, int kItems>
+__device__ __forceinline__ void rank_keys(uint32_t valid, const Smem<K>& sm, TileRegs<K, kExpand, kItems>& R);
+
 template <bool kFull, typename S, typename K, bool kExpand, int kBits, int kItems, bool kXform = false>
 __device__ __forceinline__ void rank_tile(const K* __restrict__ kt, uint32_t valid, const PassArgs& a, bool d31,
                                           const Smem<K>& sm, TileRegs<K, kExpand, kItems>& R) {
-  constexpr int kBins = S::kBins;
-  constexpr int kWarps = S::kWarps;
-  constexpr int kThreads = kWarps * 32;
-  constexpr int kCols = S::kCols;
-  constexpr int kCpt = S::kCpt;
-  const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t wbase = warp * 32 * kItems;
 #pragma unroll
   for (int j = 0; j < kItems; ++j) {
@@ -557,6 +558,18 @@ __device__ __forceinline__ void rank_tile(const K* __restrict__ kt, uint32_t val
       if (a.xform_in) R.k[j] = R.k[j] == 0xffffffffu ? a.cull : R.k[j] - a.sub;
     R.d[j] = digit_of<K>(R.k[j], a.shift, a.mask, d31);
   }
+  rank_keys<kFull, S, K, kExpand, kBits, kItems>(valid, sm, R);
+}
+
+template <bool kFull, typename S, typename K, bool kExpand, int kBits, int kItems>
+__device__ __forceinline__ void rank_keys(uint32_t valid, const Smem<K>& sm, TileRegs<K, kExpand, kItems>& R) {
+  constexpr int kBins = S::kBins;
+  constexpr int kWarps = S::kWarps;
+  constexpr int kThreads = kWarps * 32;
+  constexpr int kCols = S::kCols;
+  constexpr int kCpt = S::kCpt;
+  const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+  const uint32_t wbase = warp * 32 * kItems;
   // rank within the warp, kGroup items at a time: the equal-digit lane
   // sets of the group first (independent ballot chains), then every lane
   // of a set reads the warp's counter and the set's highest lane writes it

@@ -260,19 +260,41 @@ cudaError_t launch_depth_pass(const DepthPlan& dp, uint32_t pass, const uint32_t
                               uint32_t* err, cudaStream_t s);
 // Single-launch depth sort (depth_sort.cu).  Grid: one CTA per SM (0 if
 // the device query failed); it takes n <= depth_sort_capacity(grid) keys.
-// key0: the depth keys; range[0..1]: the smallest and largest key of a
-// Gaussian with pairs (written by the count kernel); range[2] receives the
-// number of passes run.  Results: v1 = record indices in depth order,
-// offsets = the exclusive scan of counts[v1[.]] (the pair offsets in depth
-// order); k1 receives counts[v1[.]], (k2, v2) are intermediate.  scratch:
-// depth_sort_scratch_words(grid) words of state kept between launches,
-// zero before the first launch and after an error latched in err.
+// Results: v1 = record indices in depth order, offsets = the exclusive scan
+// of the tile counts in that order (the pair offsets in depth order); k1
+// receives the counts in depth order, (k2, v2) are intermediate.  range:
+// [0..1] running smallest / largest key of a Gaussian with pairs (all ones
+// / zero between frames), [2..3] that range for the sort, [4] receives the
+// number of passes run.  scratch: depth_sort_scratch_words(grid) words of
+// state kept between launches, zero before the first launch and after an
+// error latched in err.
+//  * With count (launch_count_depth_sort) the tile count step runs in the
+//    same launch: the records of the view table in; each view's pair total
+//    and first pair (vt), M (total) and range[2..3] out, and one 8-byte
+//    word to host_status (mapped host memory, or null): host_seq (16 bits)
+//    << 48 | min(latched error, 255) << 40 | min(M, 2^40 - 1); counts
+//    receives only counts of 1023 or more.
+//  * Without (launch_depth_sort): key0 = the count kernel's depth keys,
+//    counts its tile counts, range[2..3] its range.
+struct DepthSortArgs {
+  const uint32_t* key0;
+  ViewTable vt;
+  uint64_t* total;
+  uint32_t* host_status;
+  uint32_t host_seq;
+  uint32_t *k1, *v1, *k2, *v2;
+  uint32_t* counts;
+  uint32_t* offsets;
+  uint32_t* range;
+  uint32_t n;
+  uint32_t* scratch;
+  uint32_t* err;
+};
 uint32_t depth_sort_grid();
 uint32_t depth_sort_capacity(uint32_t grid);
 size_t depth_sort_scratch_words(uint32_t grid);
-cudaError_t launch_depth_sort(uint32_t grid, const uint32_t* key0, uint32_t* k1, uint32_t* v1, uint32_t* k2,
-                              uint32_t* v2, uint32_t* range, const uint32_t* counts, uint32_t* offsets, uint32_t n,
-                              uint32_t* scratch, uint32_t* err, cudaStream_t s);
+cudaError_t launch_depth_sort(uint32_t grid, const DepthSortArgs& a, cudaStream_t s);
+cudaError_t launch_count_depth_sort(uint32_t grid, const DepthSortArgs& a, cudaStream_t s);
 // Stable pass over the packed stream on tile bits [shift, shift + width).
 // expand: write the final (local tile << 32 | depth bits) keys and local
 // indices; with rmin/rmax, record each global tile's first/last sorted

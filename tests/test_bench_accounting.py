@@ -15,6 +15,8 @@ def test_frame_kernels():
     assert ab("depth_sort", N, N, M, T, depth_passes=-3) == 16 * N * 3 + 12 * N
     # one launch per pass
     assert ab("depth_sort", N, N, M, T, depth_passes=1) == 16 * N
+    # the count step and the depth sort in one launch: record in, 3 passes, offsets
+    assert ab("count_depth_sort", N, N, M, T, depth_passes=-3) == 16 * N + 16 * N * 3 + 8 * N
     assert ab("duplicate_by_depth", N, N, M, T) == 32 * N + 4 * M
     assert ab("tile_sort_pass", M, N, M, T) == 8 * M
     assert ab("tile_expand_pass", M, N, M, T) == 16 * M + 8 * N + 16 * T == 196_307_856
