@@ -820,7 +820,7 @@ tdgs_status run_front(tdgs_context* ctx, cudaStream_t s, bool early_total = fals
   da.n = n_all;
   da.scratch = static_cast<uint32_t*>(ctx->f_dsort.p);
   da.err = err_word(ctx);
-  ctx->early_fused = dp.resident && n_all > 0 && !ctx->proj_on;
+  ctx->early_fused = dp.resident && n_all > 0 && n_all <= depth_sort_count_capacity(dp.grid) && !ctx->proj_on;
   if (ctx->early_fused) {
     // one launch: counts, M (also to the mapped host status, tagged with a
     // fresh seq), the depth sort and the offsets

@@ -1,49 +1,59 @@
 // Depth sort of the frame path in one cooperative launch (Sec. II-A,
 // Sorting: a frame's Gaussians ordered by depth before their pairs are
 // emitted), followed by the exclusive scan of their tile counts in that
-// order (the first pair of every Gaussian).
+// order (the first pair of every Gaussian).  Three forms:
+//  * k_depth_sort<true>: the tile count step first (records in, keys kept
+//    in registers), then the sort; one 8192-key tile per CTA.
+//  * k_depth_sort<false>: keys and counts from the count kernel; one tile
+//    per CTA.
+//  * k_depth_sort_tiles: the same with 2 to 4 tiles per CTA.
 //
 // The N depth keys (raw float bits; all ones for a Gaussian without pairs)
 // are compressed to key - smallest (all ones -> one past the largest) and
 // sorted stably, least significant digit first, with as many digits of at
 // most 9 bits as the compressed range needs.  One CTA of 512 threads per SM
-// owns one chunk of at most 8192 keys and ranks it in shared memory in
-// every pass (radix::rank_tile).
+// owns one chunk and ranks each of its tiles in shared memory in every pass
+// (radix::rank_keys).
 //
 // A chunk's output base per digit = the keys of smaller digits (all
 // chunks) + the keys of that digit in the chunks before it.  Neither needs
 // a column scan between two grid barriers here:
-//  * Digit totals.  Pass 0 adds each chunk's counts of every pass's digit
-//    into per-pass totals (global atomics) before the launch's one extra
-//    grid barrier; later passes find their totals ready.
+//  * Digit totals.  Pass 0 adds each chunk's counts of every later pass's
+//    digit into per-pass totals (global atomics); they are complete at pass
+//    0's end.  Pass 0's own totals come from the count step's histogram of
+//    the keys' low 9 bits (digit 0 of key - smallest is a rotation of it),
+//    or, without the count step, from the same atomics and one extra grid
+//    barrier.
 //  * Chunk counts.  Each chunk publishes its 512 digit counts as one 1 KB
-//    row of 16-bit words (14-bit count, 2-bit launch tag).  Chunk c reads
-//    rows 0..c-1 if it lies in the first half of the grid, else rows
-//    c+1..G-1, which it subtracts with its own counts from the totals: no
-//    CTA reads more than half of the rows, and it waits for those rows
-//    only (their tags), not for a barrier.
+//    row of 16-bit words holding count + 1 (rows are zero between
+//    launches, so 0 means "not written yet").  Chunk c reads rows 0..c-1 if
+//    it lies in the first half of the grid, else rows c+1..G-1, which it
+//    subtracts with its own counts from the totals: no CTA reads more than
+//    half of the rows, and it waits for those rows only, not for a barrier.
 //  * One grid barrier ends each pass: the next pass reads what every CTA
 //    wrote.
 // The value that travels with a key is the record index (22 bits) with the
 // Gaussian's tile count in the top 10 bits (1023: at least that many, the
-// count is read again at the end), loaded in order in pass 0.  The last
-// pass writes the sorted record indices and, at each sorted position, the
-// tile count (the sorted keys are not needed later): no gather of the
-// counts in depth order.  Output positions grow with the exchange position,
-// so each warp adds the counts it writes into per-chunk sums by runs of
-// equal chunk (one shuffle reduction per run); the sums reach global
-// memory by atomics before the final barrier, after which each chunk scans
-// its counts from the sum of the chunks before it: the pair offsets.
+// count is read again at the end), made in pass 0.  The last pass writes
+// the sorted record indices and, at each sorted position, the tile count
+// (the sorted keys are not needed later): no gather of the counts in depth
+// order.  Output positions grow with the exchange position, so each warp
+// adds the counts it writes into per-chunk sums by runs of equal chunk (a
+// lane scan; a run's last lane adds, its first lane subtracts); the sums
+// reach global memory by atomics before the final barrier, after which
+// each chunk scans its counts from the sum of the chunks before it: the
+// pair offsets.
 //
-// Each pass's values (pass 0: the tile counts) come into shared memory by
-// one bulk copy issued when the pass starts, so their latency hides behind
-// the ranking.
+// Each tile's values (pass 0: the tile counts) come into shared memory by
+// one bulk copy issued before the tile is ranked, so their latency hides
+// behind the ranking; keys and values cross the exchange as one 8-byte
+// word.
 //
 // A barrier is an arrival counter of its own: a CTA adds one with release
 // semantics and waits (acquire, bounded) until the count reaches the grid
 // size.  The counters used mid-launch are reset after the final barrier,
 // the final one at the start of the next launch.  State kept between
-// launches (counters, totals, rows, launch number) lives in a dedicated
+// launches (counters, totals, rows, histogram) lives in a dedicated
 // zero-initialised buffer, which the host clears again after an error was
 // latched on the device.
 #include "onesweep.cuh"
@@ -72,8 +82,7 @@ static_assert(kThreads == static_cast<int>(kBins), "one digit per thread in the 
 constexpr uint32_t kLine = 32;                      // one 128-byte line
 constexpr uint32_t kSlots = 8;                      // barrier counters, one line each
 constexpr uint32_t kFinalSlot = kSlots - 1;         // before the offsets
-constexpr uint32_t kSeqWord = kSlots * kLine;       // launch number
-constexpr uint32_t kHistWord = kSeqWord + kLine;    // [kMaxPasses][kBins] digit totals
+constexpr uint32_t kHistWord = kSlots * kLine;      // [kMaxPasses][kBins] digit totals
 constexpr uint32_t kRawWord = kHistWord + kMaxPasses * kBins;  // fused count: [kBins] keys by low 9 bits, culled
 constexpr uint32_t kSumWord = kRawWord + kBins + kLine;          // [kMaxGrid] counts per output chunk
 constexpr uint32_t kRowWord = kSumWord + kMaxGrid;             // [kMaxPasses][G][kBins / 2] rows
@@ -148,25 +157,25 @@ __device__ __forceinline__ uint2 excl_scan2(uint32_t a, uint32_t b, uint2* s_w2)
   return make_uint2(x - a + before.x, y - b + before.y);
 }
 
-// A row word holds two 16-bit counts, each tagged in its top two bits.
-__device__ __forceinline__ bool row_ready(const uint4& w, uint32_t tag2) {
-  return ((w.x & 0xc000c000u) == tag2) & ((w.y & 0xc000c000u) == tag2) & ((w.z & 0xc000c000u) == tag2) &
-         ((w.w & 0xc000c000u) == tag2);
+// A row word holds two 16-bit fields, count + 1 each (0: not written yet;
+// rows are zero between launches).
+__device__ __forceinline__ bool row_ready(const uint4& w) {
+  return (__vcmpeq2(w.x, 0u) | __vcmpeq2(w.y, 0u) | __vcmpeq2(w.z, 0u) | __vcmpeq2(w.w, 0u)) == 0u;
 }
 
 // Sum of bins 8q..8q+7 over rows r_lo + g, r_lo + g + kRowGroups, ... < r_hi
-// of one pass, waiting (bounded) until each row carries this launch's tag.
+// of one pass, waiting (bounded) until each row is written.
 __device__ __forceinline__ void sum_rows(const uint32_t* __restrict__ rows, uint32_t r_lo, uint32_t r_hi,
-                                         uint32_t g, uint32_t q, uint32_t tag2, uint32_t acc[8], uint32_t* err) {
+                                         uint32_t g, uint32_t q, uint32_t acc[8], uint32_t* err) {
   for (uint32_t r0 = r_lo + g; r0 < r_hi; r0 += kRowGroups * kRowBatch) {
     uint4 w[kRowBatch];
     uint32_t pend = 0;
 #pragma unroll
     for (uint32_t i = 0; i < kRowBatch; ++i) {
       const uint32_t r = r0 + i * kRowGroups;
-      w[i] = make_uint4(tag2, tag2, tag2, tag2);  // rows past the range count zero
+      w[i] = make_uint4(0x10001u, 0x10001u, 0x10001u, 0x10001u);  // rows past the range count zero
       if (r < r_hi) w[i] = ld_relaxed_v4(rows + static_cast<size_t>(r) * kRowWords + 4 * q);
-      if (!row_ready(w[i], tag2)) pend |= 1u << i;
+      if (!row_ready(w[i])) pend |= 1u << i;
     }
     uint32_t spins = 0;
     while (pend) {
@@ -179,7 +188,7 @@ __device__ __forceinline__ void sum_rows(const uint32_t* __restrict__ rows, uint
       for (uint32_t i = 0; i < kRowBatch; ++i) {
         if (pend & (1u << i)) {
           w[i] = ld_relaxed_v4(rows + static_cast<size_t>(r0 + i * kRowGroups) * kRowWords + 4 * q);
-          if (row_ready(w[i], tag2)) pend &= ~(1u << i);
+          if (row_ready(w[i])) pend &= ~(1u << i);
         }
       }
     }
@@ -188,11 +197,228 @@ __device__ __forceinline__ void sum_rows(const uint32_t* __restrict__ rows, uint
       const uint32_t x[4] = {w[i].x, w[i].y, w[i].z, w[i].w};
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        acc[2 * u] += x[u] & 0x3fffu;
-        acc[2 * u + 1] += (x[u] >> 16) & 0x3fffu;
+        acc[2 * u] += (x[u] & 0xffffu) - 1u;
+        acc[2 * u + 1] += (x[u] >> 16) - 1u;
       }
     }
   }
+}
+
+// One ranked tile of `valid` keys (tile items start at record tb): ranks
+// into tile positions, the (key, value) -- in the last pass (digit, value)
+// -- exchange through shared memory, and the scatter to off[digit] + tile
+// position.  Values come from vstage (items below nstaged) or vsrc + tb;
+// pass 0 (first) makes each value the record index with the tile count in
+// its top bits.  The last pass writes v1 (record index) and k1 (count) and
+// adds the counts it writes into the per-output-chunk sums csum (chunks of
+// Sz positions; vstage is free by then and holds per-warp sums).  Returns
+// false if a destination fell outside [0, n).  Ends with a block barrier.
+__device__ __forceinline__ bool exchange_scatter(const radix::Smem<uint32_t>& sm, uint32_t* vstage,
+                                                 radix::TileRegs<uint32_t, false, kItems>& R, uint32_t valid,
+                                                 uint32_t tb, uint32_t nstaged, const uint32_t* vsrc, bool first,
+                                                 bool last, uint32_t shift, uint32_t mask, uint32_t n,
+                                                 uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                 uint32_t* __restrict__ k1, uint32_t* __restrict__ v1,
+                                                 const uint32_t* __restrict__ counts, uint32_t Sz, uint32_t G,
+                                                 uint32_t* __restrict__ csum) {
+  const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+  bool ok = true;
+  const uint32_t wbase = warp * 32 * kItems;
+  uint16_t* my_wh = sm.wh + warp * kBins;
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) R.r[j] += sm.lstart[R.d[j]] + my_wh[R.d[j]];
+  __syncwarp();
+  {
+    uint4* z = reinterpret_cast<uint4*>(my_wh);
+    for (uint32_t i = lane; i < kBins / 8; i += 32) z[i] = make_uint4(0, 0, 0, 0);
+  }
+  // (key, value) -- in the last pass (digit, value) -- in one 8-byte
+  // exchange over both exchange buffers
+  uint32_t v[kItems];
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    const uint32_t idx = wbase + j * 32 + lane;
+    v[j] = 0u;
+    if (idx < valid) {
+      const uint32_t x = idx < nstaged ? vstage[idx] : __ldg(vsrc + tb + idx);
+      v[j] = first ? (tb + idx) | (min(x, kCntEscape) << kValueBits) : x;
+    }
+  }
+  uint64_t* x64 = reinterpret_cast<uint64_t*>(sm.xk);
+  static_assert(S::kXkBytes + S::kXvBytes >= kTileKeys * 8, "the 8-byte exchange spans both buffers");
+#pragma unroll
+  for (int j = 0; j < kItems; ++j)
+    if (wbase + j * 32 + lane < valid) x64[R.r[j]] = (static_cast<uint64_t>(last ? R.d[j] : R.k[j]) << 32) | v[j];
+  __syncthreads();
+  if (!last) {
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      const uint32_t pos = i * kThreads + t;
+      if (pos < valid) {
+        const uint64_t x = x64[pos];
+        const uint32_t key = static_cast<uint32_t>(x >> 32);
+        const uint32_t dst = sm.off[(key >> shift) & mask] + pos;
+        if (dst < n) {
+          kout[dst] = key;
+          vout[dst] = static_cast<uint32_t>(x);
+        } else {
+          ok = false;
+        }
+      }
+    }
+  } else {
+    // each sorted position gets its record index (v1) and that
+    // Gaussian's tile count (k1); the counts are summed per output chunk
+    // per-warp rows of counts per output chunk, over the staged values
+    // (read before the exchange barrier above)
+    static_assert(kWarps * kMaxGrid * 4 <= kTileKeys * 4, "per-warp chunk sums fit the staging buffer");
+    uint32_t* w_csum = vstage + warp * kMaxGrid;
+    for (uint32_t k = lane; k < G; k += 32) w_csum[k] = 0u;
+    __syncwarp();
+    const float inv_sz = 1.0f / static_cast<float>(Sz);
+    uint32_t q[kItems], cnt[kItems];  // output chunk (all ones: none) and count per item
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      const uint32_t pos = i * kThreads + t;
+      q[i] = 0xffffffffu;
+      cnt[i] = 0u;
+      if (pos < valid) {
+        const uint64_t x = x64[pos];
+        const uint32_t w = static_cast<uint32_t>(x), rec = w & kRecMask;
+        const uint32_t dst = sm.off[static_cast<uint32_t>(x >> 32)] + pos;
+        if (dst < n && rec < n) {
+          uint32_t c1 = w >> kValueBits;
+          if (c1 == kCntEscape) c1 = __ldg(counts + rec);
+          cnt[i] = c1;
+          v1[dst] = rec;
+          k1[dst] = c1;
+          // dst / Sz: a float estimate (dst < 2^22 is exact) corrected by one
+          uint32_t qq = static_cast<uint32_t>(static_cast<float>(dst) * inv_sz);
+          if (qq * Sz > dst) --qq;
+          else if ((qq + 1u) * Sz <= dst) ++qq;
+          q[i] = qq;
+        } else {
+          ok = false;
+        }
+      }
+    }
+    // q never decreases from lane to lane, so equal chunks are runs: an
+    // inclusive scan of the counts over the lanes (all items at once),
+    // then a run's last lane adds its scan and its first lane subtracts
+    // the scan before it (modulo 2^32, exact for every chunk sum)
+    uint32_t incl[kItems];
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) incl[i] = cnt[i];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, incl[i], d);
+        if (lane >= static_cast<uint32_t>(d)) incl[i] += o;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      const uint32_t qp = __shfl_up_sync(0xffffffffu, q[i], 1), qn = __shfl_down_sync(0xffffffffu, q[i], 1);
+      if (q[i] != 0xffffffffu) {
+        if (lane == 31 || qn != q[i]) atomicAdd(&w_csum[q[i]], incl[i]);
+        if (lane != 0 && qp != q[i]) atomicAdd(&w_csum[q[i]], cnt[i] - incl[i]);
+      }
+    }
+    __syncthreads();
+    for (uint32_t k = t; k < G; k += kThreads) {
+      uint32_t sum = 0;
+#pragma unroll
+      for (uint32_t w = 0; w < kWarps; ++w) sum += vstage[w * kMaxGrid + k];
+      if (sum) atomicAdd(csum + k, sum);
+    }
+  }
+  __syncthreads();
+  return ok;
+}
+
+// Sum of the chunk sums csum[0 .. c) (one warp; every lane returns it).
+__device__ __forceinline__ uint64_t chunks_before(const uint32_t* csum, uint32_t c) {
+  constexpr uint32_t kPer = kMaxGrid / 32;
+  const uint32_t lane = lane_id();
+  uint64_t before = 0;
+#pragma unroll
+  for (uint32_t i = 0; i < kPer; ++i) {
+    const uint32_t cc = lane + 32 * i;
+    if (cc < c) before += __ldcg(csum + cc);
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) before += __shfl_xor_sync(0xffffffffu, before, d);
+  return before;
+}
+
+// Pair offsets of positions [b, e) (at most kTileKeys; b a multiple of 4):
+// the exclusive scan of the counts k1 from `base`, kItems consecutive
+// positions per thread.  Returns base + their sum; a sum above 2^32 - 1
+// latches TDGS_ERR_OVERFLOW.  Block barriers inside.
+__device__ __forceinline__ uint64_t scan_offsets(const uint32_t* __restrict__ k1, uint32_t* __restrict__ offsets,
+                                                 uint32_t b, uint32_t e, uint64_t base, unsigned long long* s_sum,
+                                                 uint32_t* err) {
+  static_assert(kItems % 4 == 0, "16-byte loads of the counts");
+  const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+  const uint32_t pos0 = b + t * kItems;
+  uint32_t cnt[kItems];
+  uint64_t sum = 0;
+#pragma unroll
+  for (int j = 0; j < kItems; j += 4) {
+    uint4 x = make_uint4(0, 0, 0, 0);
+    if (pos0 + j + 4 <= e) {
+      x = __ldcg(reinterpret_cast<const uint4*>(k1 + pos0 + j));
+    } else {
+      if (pos0 + j < e) x.x = __ldcg(k1 + pos0 + j);
+      if (pos0 + j + 1 < e) x.y = __ldcg(k1 + pos0 + j + 1);
+      if (pos0 + j + 2 < e) x.z = __ldcg(k1 + pos0 + j + 2);
+    }
+    cnt[j] = x.x;
+    cnt[j + 1] = x.y;
+    cnt[j + 2] = x.z;
+    cnt[j + 3] = x.w;
+    sum += static_cast<uint64_t>(x.x) + x.y + x.z + x.w;
+  }
+  unsigned long long xs = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned long long o = __shfl_up_sync(0xffffffffu, xs, d);
+    if (lane >= static_cast<uint32_t>(d)) xs += o;
+  }
+  if (lane == 31) s_sum[warp] = xs;
+  __syncthreads();
+  if (t == 0) {
+    unsigned long long run = base;
+    for (uint32_t w = 0; w < kWarps; ++w) {
+      const unsigned long long v = s_sum[w];
+      s_sum[w] = run;
+      run += v;
+    }
+    s_sum[kWarps] = run;
+    if (run > 0xffffffffull) latch_error(err, TDGS_ERR_OVERFLOW, kSiteScan);
+  }
+  __syncthreads();
+  uint64_t run = xs - sum + s_sum[warp];
+  const uint64_t total = s_sum[kWarps];
+#pragma unroll
+  for (int j = 0; j < kItems; j += 4) {
+    uint32_t o[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      o[u] = static_cast<uint32_t>(run);
+      run += cnt[j + u];
+    }
+    if (pos0 + j + 4 <= e) {
+      *reinterpret_cast<uint4*>(offsets + pos0 + j) = make_uint4(o[0], o[1], o[2], o[3]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (pos0 + j + u < e) offsets[pos0 + j + u] = o[u];
+    }
+  }
+  __syncthreads();  // s_sum is free again
+  return total;
 }
 
 // kCount: the tile count step runs first in the same launch (records of
@@ -231,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_depth_sort(DepthSortArgs A) {
   static_assert(S::kXvBytes >= kRowGroups * kBins * 4, "row-sum partials fit the value exchange");
   __shared__ uint32_t s_hx[kMaxPasses - 1][kBins];  // pass 0: this chunk's counts of the later digits
   __shared__ uint2 s_warp2[kWarps];
-  __shared__ unsigned long long s_sum[kWarps];
+  __shared__ unsigned long long s_sum[kWarps + 1];
   __shared__ unsigned long long s_base;
   __shared__ __align__(8) uint64_t s_mbar;
   const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5, c = blockIdx.x, G = gridDim.x;
@@ -248,9 +474,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_depth_sort(DepthSortArgs A) {
   uint32_t* hist = scratch + kHistWord;
   uint32_t* csum = scratch + kSumWord;
   uint32_t* rows = scratch + kRowWord;
-  const uint32_t seq = __ldcg(scratch + kSeqWord);
-  const uint32_t tag2 = (seq % 3u + 1u) * 0x40004000u;
-  const uint32_t tag16 = (seq % 3u + 1u) << 14;
   uint32_t* raw = scratch + kRawWord;
   radix::TileRegs<uint32_t, false, kItems> R;
   __shared__ uint32_t s_h0[kCount ? kBins : 1];  // fused count: pass 0's digit totals
@@ -459,10 +682,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_depth_sort(DepthSortArgs A) {
     if (t < kBins / 8) {
       const uint32_t* ls = sm.lstart + 8 * t;
       uint4 w;
-      w.x = (ls[0] | tag16) | ((ls[1] | tag16) << 16);
-      w.y = (ls[2] | tag16) | ((ls[3] | tag16) << 16);
-      w.z = (ls[4] | tag16) | ((ls[5] | tag16) << 16);
-      w.w = (ls[6] | tag16) | ((ls[7] | tag16) << 16);
+      w.x = (ls[0] + 1u) | ((ls[1] + 1u) << 16);
+      w.y = (ls[2] + 1u) | ((ls[3] + 1u) << 16);
+      w.z = (ls[4] + 1u) | ((ls[5] + 1u) << 16);
+      w.w = (ls[6] + 1u) | ((ls[7] + 1u) << 16);
       st_relaxed_v4(rows + (static_cast<size_t>(p) * G + c) * kRowWords + 4 * t, w);
     }
     if (p == 0) {
@@ -489,7 +712,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_depth_sort(DepthSortArgs A) {
       const uint32_t own = sm.lstart[t];
       uint32_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       sum_rows(rows + static_cast<size_t>(p) * G * kRowWords, low_half ? 0u : c + 1, low_half ? c : G, g, q,
-               tag2, acc, err);
+               acc, err);
 #pragma unroll
       for (int i = 0; i < 8; ++i) s_part[g * kBins + 8 * q + i] = acc[i];
       __syncthreads();
@@ -505,194 +728,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_depth_sort(DepthSortArgs A) {
     }
     if (!osw::mbar_wait(&s_mbar, p & 1u, err) && t == 0) (void)osw::mbar_wait(&s_mbar, p & 1u, err);
     __syncthreads();
-    const uint32_t wbase = warp * 32 * kItems;
-    uint16_t* my_wh = sm.wh + warp * kBins;
-#pragma unroll
-    for (int j = 0; j < kItems; ++j) R.r[j] += sm.lstart[R.d[j]] + my_wh[R.d[j]];
-    __syncwarp();
-    {
-      uint4* z = reinterpret_cast<uint4*>(my_wh);
-      for (uint32_t i = lane; i < kBins / 8; i += 32) z[i] = make_uint4(0, 0, 0, 0);
-    }
-    // (key, value) -- in the last pass (digit, value) -- in one 8-byte
-    // exchange over both exchange buffers
-    uint32_t v[kItems];
-#pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-      const uint32_t idx = wbase + j * 32 + lane;
-      v[j] = 0u;
-      if (idx < valid) {
-        const uint32_t x = idx < nstaged ? vstage[idx] : __ldg(vsrc + beg + idx);
-        v[j] = p == 0 ? (beg + idx) | (min(x, kCntEscape) << kValueBits) : x;
-      }
-    }
-    uint64_t* x64 = reinterpret_cast<uint64_t*>(sm.xk);
-    static_assert(S::kXkBytes + S::kXvBytes >= kTileKeys * 8, "the 8-byte exchange spans both buffers");
-#pragma unroll
-    for (int j = 0; j < kItems; ++j)
-      if (wbase + j * 32 + lane < valid) x64[R.r[j]] = (static_cast<uint64_t>(last ? R.d[j] : R.k[j]) << 32) | v[j];
-    __syncthreads();
-    if (!last) {
-#pragma unroll
-      for (int i = 0; i < kItems; ++i) {
-        const uint32_t pos = i * kThreads + t;
-        if (pos < valid) {
-          const uint64_t x = x64[pos];
-          const uint32_t key = static_cast<uint32_t>(x >> 32);
-          const uint32_t dst = sm.off[(key >> a.shift) & mask] + pos;
-          if (dst < n) {
-            kout[dst] = key;
-            vout[dst] = static_cast<uint32_t>(x);
-          } else {
-            ok = false;
-          }
-        }
-      }
-      arrive_and_wait(scratch + (1 + p) * kLine, G, err);
-    } else {
-      // each sorted position gets its record index (v1) and that
-      // Gaussian's tile count (k1); the counts are summed per output chunk
-      // per-warp rows of counts per output chunk, over the staged values
-      // (read before the exchange barrier above)
-      static_assert(kWarps * kMaxGrid * 4 <= kTileKeys * 4, "per-warp chunk sums fit the staging buffer");
-      uint32_t* w_csum = vstage + warp * kMaxGrid;
-      for (uint32_t k = lane; k < G; k += 32) w_csum[k] = 0u;
-      __syncwarp();
-      const float inv_sz = 1.0f / static_cast<float>(Sz);
-      uint32_t q[kItems], cnt[kItems];  // output chunk (all ones: none) and count per item
-#pragma unroll
-      for (int i = 0; i < kItems; ++i) {
-        const uint32_t pos = i * kThreads + t;
-        q[i] = 0xffffffffu;
-        cnt[i] = 0u;
-        if (pos < valid) {
-          const uint64_t x = x64[pos];
-          const uint32_t w = static_cast<uint32_t>(x), rec = w & kRecMask;
-          const uint32_t dst = sm.off[static_cast<uint32_t>(x >> 32)] + pos;
-          if (dst < n && rec < n) {
-            uint32_t c1 = w >> kValueBits;
-            if (c1 == kCntEscape) c1 = __ldg(counts + rec);
-            cnt[i] = c1;
-            v1[dst] = rec;
-            k1[dst] = c1;
-            // dst / Sz: a float estimate (dst < 2^22 is exact) corrected by one
-            uint32_t qq = static_cast<uint32_t>(static_cast<float>(dst) * inv_sz);
-            if (qq * Sz > dst) --qq;
-            else if ((qq + 1u) * Sz <= dst) ++qq;
-            q[i] = qq;
-          } else {
-            ok = false;
-          }
-        }
-      }
-      // q never decreases from lane to lane, so equal chunks are runs: an
-      // inclusive scan of the counts over the lanes (all items at once),
-      // then a run's last lane adds its scan and its first lane subtracts
-      // the scan before it (modulo 2^32, exact for every chunk sum)
-      uint32_t incl[kItems];
-#pragma unroll
-      for (int i = 0; i < kItems; ++i) incl[i] = cnt[i];
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-#pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-          const uint32_t o = __shfl_up_sync(0xffffffffu, incl[i], d);
-          if (lane >= static_cast<uint32_t>(d)) incl[i] += o;
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < kItems; ++i) {
-        const uint32_t qp = __shfl_up_sync(0xffffffffu, q[i], 1), qn = __shfl_down_sync(0xffffffffu, q[i], 1);
-        if (q[i] != 0xffffffffu) {
-          if (lane == 31 || qn != q[i]) atomicAdd(&w_csum[q[i]], incl[i]);
-          if (lane != 0 && qp != q[i]) atomicAdd(&w_csum[q[i]], cnt[i] - incl[i]);
-        }
-      }
-      __syncthreads();
-      for (uint32_t k = t; k < G; k += kThreads) {
-        uint32_t sum = 0;
-#pragma unroll
-        for (uint32_t w = 0; w < kWarps; ++w) sum += vstage[w * kMaxGrid + k];
-        if (sum) atomicAdd(csum + k, sum);
-      }
-      arrive_and_wait(scratch + kFinalSlot * kLine, G, err);
-    }
+    ok &= exchange_scatter(sm, vstage, R, valid, beg, nstaged, vsrc, p == 0, last, a.shift, mask, n, kout, vout,
+                           k1, v1, counts, Sz, G, csum);
+    arrive_and_wait(scratch + (last ? kFinalSlot : 1 + p) * kLine, G, err);
   }
   if (!ok) latch_error(err, TDGS_ERR_CAPACITY, kSiteRadixRange);
   // The pair offsets: counts in depth order (k1) scanned from the sum of
-  // the chunks before this one; kItems consecutive positions per thread.
-  {
-    static_assert(kItems % 4 == 0, "16-byte loads of the counts");
-    if (warp == 0) {
-      constexpr uint32_t kPer = kMaxGrid / 32;
-      uint64_t before = 0;
-#pragma unroll
-      for (uint32_t i = 0; i < kPer; ++i) {
-        const uint32_t cc = lane + 32 * i;
-        if (cc < c) before += __ldcg(csum + cc);
-      }
-#pragma unroll
-      for (int d = 16; d > 0; d >>= 1) before += __shfl_xor_sync(0xffffffffu, before, d);
-      if (lane == 0) s_base = before;
-    }
-    const uint32_t pos0 = beg + t * kItems;
-    uint32_t cnt[kItems];
-    uint64_t sum = 0;
-#pragma unroll
-    for (int j = 0; j < kItems; j += 4) {
-      uint4 x = make_uint4(0, 0, 0, 0);
-      if (pos0 + j + 4 <= end) {
-        x = __ldcg(reinterpret_cast<const uint4*>(k1 + pos0 + j));
-      } else {
-        if (pos0 + j < end) x.x = __ldcg(k1 + pos0 + j);
-        if (pos0 + j + 1 < end) x.y = __ldcg(k1 + pos0 + j + 1);
-        if (pos0 + j + 2 < end) x.z = __ldcg(k1 + pos0 + j + 2);
-      }
-      cnt[j] = x.x;
-      cnt[j + 1] = x.y;
-      cnt[j + 2] = x.z;
-      cnt[j + 3] = x.w;
-      sum += static_cast<uint64_t>(x.x) + x.y + x.z + x.w;
-    }
-    unsigned long long xs = sum;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const unsigned long long o = __shfl_up_sync(0xffffffffu, xs, d);
-      if (lane >= static_cast<uint32_t>(d)) xs += o;
-    }
-    if (lane == 31) s_sum[warp] = xs;
-    __syncthreads();
-    if (t == 0) {
-      unsigned long long run = s_base;
-      for (uint32_t w = 0; w < kWarps; ++w) {
-        const unsigned long long v = s_sum[w];
-        s_sum[w] = run;
-        run += v;
-      }
-      if (run > 0xffffffffull) latch_error(err, TDGS_ERR_OVERFLOW, kSiteScan);
-    }
-    __syncthreads();
-    uint64_t run = xs - sum + s_sum[warp];
-#pragma unroll
-    for (int j = 0; j < kItems; j += 4) {
-      uint32_t o[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        o[u] = static_cast<uint32_t>(run);
-        run += cnt[j + u];
-      }
-      if (pos0 + j + 4 <= end) {
-        *reinterpret_cast<uint4*>(offsets + pos0 + j) = make_uint4(o[0], o[1], o[2], o[3]);
-      } else {
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (pos0 + j + u < end) offsets[pos0 + j + u] = o[u];
-      }
-    }
+  // the chunks before this one.
+  if (warp == 0) {
+    uint64_t before = chunks_before(csum, c);
+    if (lane == 0) s_base = before;
   }
+  __syncthreads();
+  scan_offsets(k1, offsets, beg, end, s_base, s_sum, err);
   // Reset for the next launch (every reader of these is past the final
-  // barrier): this chunk's rows; CTA 0 the totals, the mid-launch counters
-  // and the launch number.
+  // barrier): this chunk's rows; CTA 0 the totals, the histogram of the
+  // count step, the key range and the mid-launch counters.
   for (uint32_t i = t; i < passes * (kRowWords / 4); i += kThreads) {
     const uint32_t pp = i / (kRowWords / 4), w = i % (kRowWords / 4);
     reinterpret_cast<uint4*>(rows + (static_cast<size_t>(pp) * G + c) * kRowWords)[w] = make_uint4(0, 0, 0, 0);
@@ -708,7 +759,208 @@ __global__ void __launch_bounds__(kThreads, 1) k_depth_sort(DepthSortArgs A) {
       }
     }
     if (t < passes) scratch[t * kLine] = 0u;  // slots 0 .. passes-1
-    if (t == 0) scratch[kSeqWord] = seq + 1u;
+  }
+}
+
+// The same sort for chunks of 2 to kMaxTiles tiles of 8192 keys per CTA
+// (keys and counts from the count kernel).  Each pass first counts every
+// tile's digits (shared-memory atomics; pass 0 also the later passes'
+// digits), publishes the chunk's counts as its row and turns them into the
+// chunk's bases as above; then it ranks and scatters the tiles one after
+// the other, each from the running base per digit.
+constexpr uint32_t kMaxTiles = 4;
+__global__ void __launch_bounds__(kThreads, 1) k_depth_sort_tiles(DepthSortArgs A) {
+  const uint32_t* __restrict__ key0 = A.key0;
+  uint32_t* __restrict__ k1 = A.k1;
+  uint32_t* __restrict__ v1 = A.v1;
+  uint32_t* __restrict__ k2 = A.k2;
+  uint32_t* __restrict__ v2 = A.v2;
+  uint32_t* __restrict__ counts = A.counts;
+  uint32_t* __restrict__ range = A.range;
+  uint32_t* __restrict__ scratch = A.scratch;
+  uint32_t* __restrict__ err = A.err;
+  const uint32_t n = A.n;
+  extern __shared__ __align__(16) unsigned char smem[];
+  radix::Smem<uint32_t> sm;
+  {
+    unsigned char* p = smem;
+    sm.wh = reinterpret_cast<uint16_t*>(p);
+    p += S::kWhBytes;
+    sm.xk = reinterpret_cast<uint32_t*>(p);
+    p += S::kXkBytes;
+    sm.xv = reinterpret_cast<uint32_t*>(p);
+    p += S::kXvBytes;
+    sm.base = reinterpret_cast<uint32_t*>(p);
+    sm.lstart = sm.base + kBins;
+    sm.off = sm.lstart + kBins;
+  }
+  uint32_t* vstage = reinterpret_cast<uint32_t*>(smem + S::kSmem);
+  uint32_t* s_part = sm.xv;
+  __shared__ uint32_t s_tc[kMaxTiles][kBins];       // this pass's digit counts per tile
+  __shared__ uint32_t s_hx[kMaxPasses - 1][kBins];  // pass 0: the later digits' counts
+  __shared__ uint2 s_warp2[kWarps];
+  __shared__ unsigned long long s_sum[kWarps + 1];
+  __shared__ unsigned long long s_base;
+  __shared__ __align__(8) uint64_t s_mbar;
+  const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5, c = blockIdx.x, G = gridDim.x;
+  const uint32_t Sz = ((n + G - 1) / G + 3) & ~3u;
+  const uint32_t beg = min(c * Sz, n), end = min(beg + Sz, n);
+  uint32_t tiles = (end - beg + kTileKeys - 1) / kTileKeys;
+  bool ok = tiles <= kMaxTiles;  // guaranteed by the host
+  if (!ok) tiles = kMaxTiles;
+  {
+    uint4* z = reinterpret_cast<uint4*>(sm.wh);
+    for (uint32_t i = t; i < S::kWhBytes / 16; i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
+    for (uint32_t i = t; i < (kMaxPasses - 1) * kBins; i += kThreads) (&s_hx[0][0])[i] = 0u;
+  }
+  uint32_t* hist = scratch + kHistWord;
+  uint32_t* csum = scratch + kSumWord;
+  uint32_t* rows = scratch + kRowWord;
+  const uint32_t lo = __ldcg(range + 2), hi = __ldcg(range + 3);
+  const uint32_t cull = hi >= lo ? hi - lo + 1u : 0u;
+  const uint32_t bits = cull ? 32u - static_cast<uint32_t>(__clz(cull)) : 0u;
+  const uint32_t passes = bits ? (bits + kBits - 1) / kBits : 1u;
+  const uint32_t width = (bits + passes - 1) / passes;
+  const uint32_t mask = width ? (1u << width) - 1u : 0u;
+  if (c == 0 && t == 0) {
+    range[4] = passes;
+    scratch[kFinalSlot * kLine] = 0u;
+  }
+  if (c == 0)
+    for (uint32_t i = t; i < G; i += kThreads) csum[i] = 0u;
+  if (t == 0) {
+    osw::mbar_init(&s_mbar);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const uint32_t g = t / (kBins / 8), q = t % (kBins / 8);
+  const bool low_half = c < G / 2;
+  const uint32_t wbase = warp * 32 * kItems;
+  uint32_t phase = 0;  // staging copies so far (mbarrier parity)
+  for (uint32_t p = 0; p < passes; ++p) {
+    const bool last = p + 1 == passes;
+    const bool to_one = ((passes - 1 - p) & 1u) == 0;
+    const uint32_t* kin = p == 0 ? key0 : (to_one ? k2 : k1);
+    const uint32_t* vin = to_one ? v2 : v1;
+    uint32_t* kout = to_one ? k1 : k2;
+    uint32_t* vout = to_one ? v1 : v2;
+    const uint32_t* vsrc = p == 0 ? counts : vin;
+    const uint32_t shift = p * width;
+    // ---- every tile's digit counts (pass 0: compressed keys, and the
+    // later passes' digits)
+    for (uint32_t i = t; i < tiles * kBins; i += kThreads) (&s_tc[0][0])[i] = 0u;
+    __syncthreads();
+    for (uint32_t ti = 0; ti < tiles; ++ti) {
+      const uint32_t tb = beg + ti * kTileKeys, valid = min(kTileKeys, end - tb);
+#pragma unroll
+      for (int j = 0; j < kItems; ++j) {
+        const uint32_t idx = wbase + j * 32 + lane;
+        if (idx < valid) {
+          uint32_t k = __ldcs(kin + tb + idx);
+          if (p == 0) {
+            k = k == 0xffffffffu ? cull : k - lo;
+            for (uint32_t pp = 1; pp < passes; ++pp) atomicAdd(&s_hx[pp - 1][(k >> (pp * width)) & mask], 1u);
+          }
+          atomicAdd(&s_tc[ti][(k >> shift) & mask], 1u);
+        }
+      }
+    }
+    __syncthreads();
+    uint32_t own = 0;
+    for (uint32_t ti = 0; ti < tiles; ++ti) own += s_tc[ti][t];
+    sm.lstart[t] = own;
+    __syncthreads();
+    if (t < kBins / 8) {
+      const uint32_t* ls = sm.lstart + 8 * t;
+      uint4 w;
+      w.x = (ls[0] + 1u) | ((ls[1] + 1u) << 16);
+      w.y = (ls[2] + 1u) | ((ls[3] + 1u) << 16);
+      w.z = (ls[4] + 1u) | ((ls[5] + 1u) << 16);
+      w.w = (ls[6] + 1u) | ((ls[7] + 1u) << 16);
+      st_relaxed_v4(rows + (static_cast<size_t>(p) * G + c) * kRowWords + 4 * t, w);
+    }
+    if (p == 0) {
+      if (own) atomicAdd(hist + t, own);
+      for (uint32_t pp = 1; pp < passes; ++pp)
+        if (s_hx[pp - 1][t]) atomicAdd(hist + pp * kBins + t, s_hx[pp - 1][t]);
+      arrive_and_wait(scratch, G, err);
+    }
+    // ---- the chunk's running output base per digit (sm.base)
+    {
+      const uint32_t tot = __ldcg(hist + p * kBins + t);
+      uint32_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      sum_rows(rows + static_cast<size_t>(p) * G * kRowWords, low_half ? 0u : c + 1, low_half ? c : G, g, q,
+               acc, err);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) s_part[g * kBins + 8 * q + i] = acc[i];
+      __syncthreads();
+      uint32_t sum = 0;
+#pragma unroll
+      for (uint32_t gg = 0; gg < kRowGroups; ++gg) sum += s_part[gg * kBins + t];
+      const uint32_t before = low_half ? sum : tot - own - sum;
+      sm.base[t] = excl_scan2(tot, 0u, s_warp2).x + before;
+      __syncthreads();
+    }
+    // ---- the tiles: stage values, rank, scatter from the running base
+    for (uint32_t ti = 0; ti < tiles; ++ti) {
+      const uint32_t tb = beg + ti * kTileKeys, valid = min(kTileKeys, end - tb);
+      const uint32_t nbulk = valid & ~3u;
+      if (t == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        osw::mbar_arrive(&s_mbar, nbulk * 4);
+        if (nbulk) osw::bulk_g2s(vstage, vsrc + tb, nbulk * 4, &s_mbar);
+      }
+      radix::TileRegs<uint32_t, false, kItems> R;
+#pragma unroll
+      for (int j = 0; j < kItems; ++j) {
+        const uint32_t idx = wbase + j * 32 + lane;
+        R.k[j] = idx < valid ? __ldcs(kin + tb + idx) : 0u;
+      }
+      if (p == 0) {
+#pragma unroll
+        for (int j = 0; j < kItems; ++j)
+          if (wbase + j * 32 + lane < valid) R.k[j] = R.k[j] == 0xffffffffu ? cull : R.k[j] - lo;
+      }
+#pragma unroll
+      for (int j = 0; j < kItems; ++j) R.d[j] = (R.k[j] >> shift) & mask;
+      radix::rank_keys<false, S, uint32_t, false, kBits, kItems>(valid, sm, R);
+      // this tile's digit starts; its keys go to base + tile position - start
+      {
+        const uint32_t cnt = sm.lstart[t];
+        const uint32_t st = excl_scan2(cnt, 0u, s_warp2).x;
+        const uint32_t bs = sm.base[t];
+        sm.lstart[t] = st;
+        sm.off[t] = bs - st;
+        sm.base[t] = bs + cnt;
+      }
+      if (!osw::mbar_wait(&s_mbar, phase & 1u, err) && t == 0) (void)osw::mbar_wait(&s_mbar, phase & 1u, err);
+      ++phase;
+      __syncthreads();
+      ok &= exchange_scatter(sm, vstage, R, valid, tb, nbulk, vsrc, p == 0, last, shift, mask, n, kout, vout, k1,
+                             v1, counts, Sz, G, csum);
+    }
+    arrive_and_wait(scratch + (last ? kFinalSlot : 1 + p) * kLine, G, err);
+  }
+  if (!ok) latch_error(err, TDGS_ERR_CAPACITY, kSiteRadixRange);
+  // ---- the pair offsets, tile by tile from the sum of the chunks before
+  if (warp == 0) {
+    const uint64_t before = chunks_before(csum, c);
+    if (lane == 0) s_base = before;
+  }
+  __syncthreads();
+  uint64_t run = s_base;
+  for (uint32_t ti = 0; ti < tiles; ++ti) {
+    const uint32_t tb = beg + ti * kTileKeys;
+    run = scan_offsets(k1, A.offsets, tb, min(tb + kTileKeys, end), run, s_sum, err);
+  }
+  // ---- reset for the next launch
+  for (uint32_t i = t; i < passes * (kRowWords / 4); i += kThreads) {
+    const uint32_t pp = i / (kRowWords / 4), w = i % (kRowWords / 4);
+    reinterpret_cast<uint4*>(rows + (static_cast<size_t>(pp) * G + c) * kRowWords)[w] = make_uint4(0, 0, 0, 0);
+  }
+  if (c == 0) {
+    for (uint32_t i = t; i < passes * kBins; i += kThreads) hist[i] = 0u;
+    if (t < passes) scratch[t * kLine] = 0u;
   }
 }
 
@@ -716,16 +968,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_depth_sort(DepthSortArgs A) {
 
 // ------------------------------------------------------------- host side
 namespace {
-radix::Kernel depth_kernel(bool count) {
-  return radix::Kernel{count ? reinterpret_cast<const void*>(&depth::k_depth_sort<true>)
-                             : reinterpret_cast<const void*>(&depth::k_depth_sort<false>),
-                       depth::kBits, depth::kThreads, depth::kItems, depth::kSmem, 1};
+enum class Form { kCount, kOne, kTiles };
+radix::Kernel depth_kernel(Form f) {
+  const void* fn = f == Form::kCount ? reinterpret_cast<const void*>(&depth::k_depth_sort<true>)
+                   : f == Form::kOne ? reinterpret_cast<const void*>(&depth::k_depth_sort<false>)
+                                     : reinterpret_cast<const void*>(&depth::k_depth_sort_tiles);
+  return radix::Kernel{fn, depth::kBits, depth::kThreads, depth::kItems, depth::kSmem, 1};
 }
 
-cudaError_t launch_depth(bool count, uint32_t grid, const DepthSortArgs& a, cudaStream_t s) {
+cudaError_t launch_depth(Form f, uint32_t grid, const DepthSortArgs& a, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
   if (grid == 0 || grid > radix::kMaxGrid || a.n > depth_sort_capacity(grid)) return cudaErrorInvalidConfiguration;
-  if (count && a.vt.nv > kMaxViews) return cudaErrorInvalidValue;
+  if (f != Form::kTiles && a.n > depth_sort_count_capacity(grid)) return cudaErrorInvalidConfiguration;
+  if (f == Form::kCount && a.vt.nv > kMaxViews) return cudaErrorInvalidValue;
   DepthSortArgs args = a;
   void* params[] = {(void*)&args};
   cudaLaunchConfig_t cfg = {};
@@ -738,23 +993,31 @@ cudaError_t launch_depth(bool count, uint32_t grid, const DepthSortArgs& a, cuda
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelExC(&cfg, depth_kernel(count).fn, params);
+  return cudaLaunchKernelExC(&cfg, depth_kernel(f).fn, params);
 }
 }  // namespace
 
 uint32_t depth_sort_grid() {
-  // both forms: one CTA per SM (the occupancy query also sets their shared
+  // every form: one CTA per SM (the occupancy query also sets their shared
   // memory limit on this device)
-  const uint32_t g0 = radix::resident_ctas(depth_kernel(false), 1);
-  const uint32_t g1 = radix::resident_ctas(depth_kernel(true), 1);
-  const uint32_t g = g0 < g1 ? g0 : g1;
-  return g > radix::kMaxGrid ? radix::kMaxGrid : g;
+  uint32_t g = radix::kMaxGrid;
+  for (Form f : {Form::kCount, Form::kOne, Form::kTiles}) {
+    const uint32_t r = radix::resident_ctas(depth_kernel(f), 1);
+    if (r < g) g = r;
+  }
+  return g;
 }
 
-uint32_t depth_sort_capacity(uint32_t grid) {
+uint32_t depth_sort_count_capacity(uint32_t grid) {
   // chunks of ceil(n / G) keys rounded up to a multiple of 4 fit one tile
   // (8192, itself a multiple of 4) exactly when n <= G * 8192
   return grid * depth::kTileKeys;
+}
+
+uint32_t depth_sort_capacity(uint32_t grid) {
+  // up to kMaxTiles tiles per CTA; record indices below 2^22
+  const uint64_t c = static_cast<uint64_t>(grid) * depth::kTileKeys * depth::kMaxTiles;
+  return static_cast<uint32_t>(c < (1ull << depth::kValueBits) ? c : (1ull << depth::kValueBits));
 }
 
 size_t depth_sort_scratch_words(uint32_t grid) {
@@ -762,11 +1025,11 @@ size_t depth_sort_scratch_words(uint32_t grid) {
 }
 
 cudaError_t launch_depth_sort(uint32_t grid, const DepthSortArgs& a, cudaStream_t s) {
-  return launch_depth(false, grid, a, s);
+  return launch_depth(a.n <= depth_sort_count_capacity(grid) ? Form::kOne : Form::kTiles, grid, a, s);
 }
 
 cudaError_t launch_count_depth_sort(uint32_t grid, const DepthSortArgs& a, cudaStream_t s) {
-  return launch_depth(true, grid, a, s);
+  return launch_depth(Form::kCount, grid, a, s);
 }
 
 }  // namespace tdgs

@@ -376,6 +376,27 @@ def test_depth_sort_at_capacity(ctx, oracle):
         assert ctx.depth_passes() >= 1
 
 
+@pytest.mark.parametrize("mult", [2, 3, 4])
+def test_depth_sort_several_tiles_per_cta(ctx, oracle, mult):
+    """Above SMs x 8192 Gaussians the single launch takes 2 to 4 tiles of
+    8192 per CTA (up to 2^22 Gaussians); ragged last chunks included."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = min(mult * sms * 8192 - 5 * mult, 1 << 22)
+    fr = synth.frame_random(90 + mult, n, 1920, 1080, max_sigma=4.0)
+    _check_frame(ctx, oracle, fr)
+    assert 1 <= ctx.depth_passes() <= 4
+
+
+def test_depth_sort_several_tiles_alternating_pass_counts(ctx, oracle):
+    """The multi-tile form's counters, totals and rows are reset for every
+    pass count too."""
+    n = torch.cuda.get_device_properties(0).multi_processor_count * 8192 + 4099
+    for i, ((lo, hi), passes) in enumerate([((1e-30, 1e30), 4), ((3.0, 3.0), 1), ((0.5, 80.0), 3),
+                                             ((1.0, 1.01), 2)]):
+        _check_frame(ctx, oracle, _depth_range_frame(60 + i, lo, hi, n=n))
+        assert ctx.depth_passes() == passes
+
+
 def test_sort_frame_scene_1m(ctx, oracle):
     m = _check_frame(ctx, oracle, synth.frame_scene(0))
     assert m > 5_000_000
