@@ -204,17 +204,18 @@ __device__ __forceinline__ void sum_rows(const uint32_t* __restrict__ rows, uint
   }
 }
 
-// One ranked tile of `valid` keys (tile items start at record tb): ranks
-// into tile positions, the (key, value) -- in the last pass (digit, value)
-// -- exchange through shared memory, and the scatter to off[digit] + tile
-// position.  Values come from vstage (items below nstaged) or vsrc + tb;
+// One ranked tile of `valid` keys (tile items start at record tb; item j of
+// this thread goes to tile position pos[j]): the (key, value) -- in the
+// last pass (digit, value); hi[j] is the key or the digit -- exchange
+// through shared memory, and the scatter to off[digit] + tile position.  Values come from vstage (items below nstaged) or vsrc + tb;
 // pass 0 (first) makes each value the record index with the tile count in
 // its top bits.  The last pass writes v1 (record index) and k1 (count) and
 // adds the counts it writes into the per-output-chunk sums csum (chunks of
 // Sz positions; vstage is free by then and holds per-warp sums).  Returns
 // false if a destination fell outside [0, n).  Ends with a block barrier.
 __device__ __forceinline__ bool exchange_scatter(const radix::Smem<uint32_t>& sm, uint32_t* vstage,
-                                                 radix::TileRegs<uint32_t, false, kItems>& R, uint32_t valid,
+                                                 const uint32_t (&hi)[kItems], const uint32_t (&pos)[kItems],
+                                                 uint32_t valid,
                                                  uint32_t tb, uint32_t nstaged, const uint32_t* vsrc, bool first,
                                                  bool last, uint32_t shift, uint32_t mask, uint32_t n,
                                                  uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
@@ -224,14 +225,6 @@ __device__ __forceinline__ bool exchange_scatter(const radix::Smem<uint32_t>& sm
   const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
   bool ok = true;
   const uint32_t wbase = warp * 32 * kItems;
-  uint16_t* my_wh = sm.wh + warp * kBins;
-#pragma unroll
-  for (int j = 0; j < kItems; ++j) R.r[j] += sm.lstart[R.d[j]] + my_wh[R.d[j]];
-  __syncwarp();
-  {
-    uint4* z = reinterpret_cast<uint4*>(my_wh);
-    for (uint32_t i = lane; i < kBins / 8; i += 32) z[i] = make_uint4(0, 0, 0, 0);
-  }
   // (key, value) -- in the last pass (digit, value) -- in one 8-byte
   // exchange over both exchange buffers
   uint32_t v[kItems];
@@ -248,16 +241,16 @@ __device__ __forceinline__ bool exchange_scatter(const radix::Smem<uint32_t>& sm
   static_assert(S::kXkBytes + S::kXvBytes >= kTileKeys * 8, "the 8-byte exchange spans both buffers");
 #pragma unroll
   for (int j = 0; j < kItems; ++j)
-    if (wbase + j * 32 + lane < valid) x64[R.r[j]] = (static_cast<uint64_t>(last ? R.d[j] : R.k[j]) << 32) | v[j];
+    if (wbase + j * 32 + lane < valid) x64[pos[j]] = (static_cast<uint64_t>(hi[j]) << 32) | v[j];
   __syncthreads();
   if (!last) {
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
-      const uint32_t pos = i * kThreads + t;
-      if (pos < valid) {
-        const uint64_t x = x64[pos];
+      const uint32_t xp = i * kThreads + t;
+      if (xp < valid) {
+        const uint64_t x = x64[xp];
         const uint32_t key = static_cast<uint32_t>(x >> 32);
-        const uint32_t dst = sm.off[(key >> shift) & mask] + pos;
+        const uint32_t dst = sm.off[(key >> shift) & mask] + xp;
         if (dst < n) {
           kout[dst] = key;
           vout[dst] = static_cast<uint32_t>(x);
@@ -279,13 +272,13 @@ __device__ __forceinline__ bool exchange_scatter(const radix::Smem<uint32_t>& sm
     uint32_t q[kItems], cnt[kItems];  // output chunk (all ones: none) and count per item
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
-      const uint32_t pos = i * kThreads + t;
+      const uint32_t xp = i * kThreads + t;
       q[i] = 0xffffffffu;
       cnt[i] = 0u;
-      if (pos < valid) {
-        const uint64_t x = x64[pos];
+      if (xp < valid) {
+        const uint64_t x = x64[xp];
         const uint32_t w = static_cast<uint32_t>(x), rec = w & kRecMask;
-        const uint32_t dst = sm.off[static_cast<uint32_t>(x >> 32)] + pos;
+        const uint32_t dst = sm.off[static_cast<uint32_t>(x >> 32)] + xp;
         if (dst < n && rec < n) {
           uint32_t c1 = w >> kValueBits;
           if (c1 == kCntEscape) c1 = __ldg(counts + rec);
@@ -728,8 +721,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_depth_sort(DepthSortArgs A) {
     }
     if (!osw::mbar_wait(&s_mbar, p & 1u, err) && t == 0) (void)osw::mbar_wait(&s_mbar, p & 1u, err);
     __syncthreads();
-    ok &= exchange_scatter(sm, vstage, R, valid, beg, nstaged, vsrc, p == 0, last, a.shift, mask, n, kout, vout,
-                           k1, v1, counts, Sz, G, csum);
+    {
+      // ranks into tile positions; this warp's counter row back to zero
+      uint16_t* my_wh = sm.wh + warp * kBins;
+#pragma unroll
+      for (int j = 0; j < kItems; ++j) R.r[j] += sm.lstart[R.d[j]] + my_wh[R.d[j]];
+      __syncwarp();
+      uint4* z = reinterpret_cast<uint4*>(my_wh);
+      for (uint32_t i = lane; i < kBins / 8; i += 32) z[i] = make_uint4(0, 0, 0, 0);
+    }
+    uint32_t hk[kItems];  // exchanged with each value: the key, in the last pass its digit
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) hk[j] = last ? R.d[j] : R.k[j];
+    ok &= exchange_scatter(sm, vstage, hk, R.r, valid, beg, nstaged, vsrc, p == 0, last, a.shift, mask, n, kout,
+                           vout, k1, v1, counts, Sz, G, csum);
     arrive_and_wait(scratch + (last ? kFinalSlot : 1 + p) * kLine, G, err);
   }
   if (!ok) latch_error(err, TDGS_ERR_CAPACITY, kSiteRadixRange);
@@ -763,12 +768,64 @@ __global__ void __launch_bounds__(kThreads, 1) k_depth_sort(DepthSortArgs A) {
 }
 
 // The same sort for chunks of 2 to kMaxTiles tiles of 8192 keys per CTA
-// (keys and counts from the count kernel).  Each pass first counts every
-// tile's digits (shared-memory atomics; pass 0 also the later passes'
-// digits), publishes the chunk's counts as its row and turns them into the
-// chunk's bases as above; then it ranks and scatters the tiles one after
-// the other, each from the running base per digit.
+// (keys and counts from the count kernel).  Each pass ranks every tile of
+// the chunk once and keeps each key's position in its tile (16 bits, in
+// shared memory) and the tile's digit counts; publishes the chunk's counts
+// as its row; reads all rows (the digit totals and the chunks before it,
+// so no totals are kept between passes and no extra barrier is needed);
+// then reloads each tile's keys and scatters them from the running base
+// per digit, the next tile's values arriving by bulk copy meanwhile.
 constexpr uint32_t kMaxTiles = 4;
+constexpr size_t kSmemTiles = S::kSmem + 2 * kTileKeys * 4 + kMaxTiles * kTileKeys * 2;
+
+// Sums of bins 8q..8q+7 over all rows g, g + kRowGroups, ... < G of one
+// pass (all: every row; lo: rows below c), waiting (bounded) until each
+// row is written.
+__device__ __forceinline__ void sum_all_rows(const uint32_t* __restrict__ rows, uint32_t G, uint32_t c, uint32_t g,
+                                             uint32_t q, uint32_t lo[8], uint32_t all[8], uint32_t* err) {
+  for (uint32_t r0 = g; r0 < G; r0 += kRowGroups * kRowBatch) {
+    uint4 w[kRowBatch];
+    uint32_t pend = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < kRowBatch; ++i) {
+      const uint32_t r = r0 + i * kRowGroups;
+      w[i] = make_uint4(0x10001u, 0x10001u, 0x10001u, 0x10001u);  // rows past G count zero
+      if (r < G) w[i] = ld_relaxed_v4(rows + static_cast<size_t>(r) * kRowWords + 4 * q);
+      if (!row_ready(w[i])) pend |= 1u << i;
+    }
+    uint32_t spins = 0;
+    while (pend) {
+      if (++spins > kSpinLimit) {
+        latch_error(err, TDGS_ERR_TIMEOUT, kSiteBarrier);
+        break;
+      }
+      __nanosleep(32);
+#pragma unroll
+      for (uint32_t i = 0; i < kRowBatch; ++i) {
+        if (pend & (1u << i)) {
+          w[i] = ld_relaxed_v4(rows + static_cast<size_t>(r0 + i * kRowGroups) * kRowWords + 4 * q);
+          if (row_ready(w[i])) pend &= ~(1u << i);
+        }
+      }
+    }
+#pragma unroll
+    for (uint32_t i = 0; i < kRowBatch; ++i) {
+      const bool below = r0 + i * kRowGroups < c;
+      const uint32_t x[4] = {w[i].x, w[i].y, w[i].z, w[i].w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t c0 = (x[u] & 0xffffu) - 1u, c1 = (x[u] >> 16) - 1u;
+        all[2 * u] += c0;
+        all[2 * u + 1] += c1;
+        if (below) {
+          lo[2 * u] += c0;
+          lo[2 * u + 1] += c1;
+        }
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 1) k_depth_sort_tiles(DepthSortArgs A) {
   const uint32_t* __restrict__ key0 = A.key0;
   uint32_t* __restrict__ k1 = A.k1;
@@ -794,14 +851,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_depth_sort_tiles(DepthSortArgs 
     sm.lstart = sm.base + kBins;
     sm.off = sm.lstart + kBins;
   }
-  uint32_t* vstage = reinterpret_cast<uint32_t*>(smem + S::kSmem);
-  uint32_t* s_part = sm.xv;
-  __shared__ uint32_t s_tc[kMaxTiles][kBins];       // this pass's digit counts per tile
-  __shared__ uint32_t s_hx[kMaxPasses - 1][kBins];  // pass 0: the later digits' counts
+  uint32_t* vst[2] = {reinterpret_cast<uint32_t*>(smem + S::kSmem),
+                      reinterpret_cast<uint32_t*>(smem + S::kSmem) + kTileKeys};  // staged values, two tiles
+  uint16_t* s_pos = reinterpret_cast<uint16_t*>(smem + S::kSmem + 2 * kTileKeys * 4);  // [tile][item] position
+  static_assert(S::kXkBytes >= kRowGroups * kBins * 4 && S::kXvBytes >= kRowGroups * kBins * 4,
+                "row-sum partials fit the exchange buffers");
+  __shared__ uint32_t s_tc[kMaxTiles][kBins];  // this pass's digit counts per tile
   __shared__ uint2 s_warp2[kWarps];
   __shared__ unsigned long long s_sum[kWarps + 1];
   __shared__ unsigned long long s_base;
-  __shared__ __align__(8) uint64_t s_mbar;
+  __shared__ __align__(8) uint64_t s_mbar[2];
   const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5, c = blockIdx.x, G = gridDim.x;
   const uint32_t Sz = ((n + G - 1) / G + 3) & ~3u;
   const uint32_t beg = min(c * Sz, n), end = min(beg + Sz, n);
@@ -811,9 +870,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_depth_sort_tiles(DepthSortArgs 
   {
     uint4* z = reinterpret_cast<uint4*>(sm.wh);
     for (uint32_t i = t; i < S::kWhBytes / 16; i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
-    for (uint32_t i = t; i < (kMaxPasses - 1) * kBins; i += kThreads) (&s_hx[0][0])[i] = 0u;
   }
-  uint32_t* hist = scratch + kHistWord;
   uint32_t* csum = scratch + kSumWord;
   uint32_t* rows = scratch + kRowWord;
   const uint32_t lo = __ldcg(range + 2), hi = __ldcg(range + 3);
@@ -829,14 +886,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_depth_sort_tiles(DepthSortArgs 
   if (c == 0)
     for (uint32_t i = t; i < G; i += kThreads) csum[i] = 0u;
   if (t == 0) {
-    osw::mbar_init(&s_mbar);
+    osw::mbar_init(&s_mbar[0]);
+    osw::mbar_init(&s_mbar[1]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   const uint32_t g = t / (kBins / 8), q = t % (kBins / 8);
-  const bool low_half = c < G / 2;
   const uint32_t wbase = warp * 32 * kItems;
-  uint32_t phase = 0;  // staging copies so far (mbarrier parity)
+  uint32_t par = 0;  // bit b: the phase parity of buffer b's next copy
   for (uint32_t p = 0; p < passes; ++p) {
     const bool last = p + 1 == passes;
     const bool to_one = ((passes - 1 - p) & 1u) == 0;
@@ -846,70 +903,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_depth_sort_tiles(DepthSortArgs 
     uint32_t* vout = to_one ? v1 : v2;
     const uint32_t* vsrc = p == 0 ? counts : vin;
     const uint32_t shift = p * width;
-    // ---- every tile's digit counts (pass 0: compressed keys, and the
-    // later passes' digits)
-    for (uint32_t i = t; i < tiles * kBins; i += kThreads) (&s_tc[0][0])[i] = 0u;
-    __syncthreads();
+    auto stage = [&](uint32_t ti) {  // thread 0: the bulk copy of tile ti's values
+      const uint32_t tb = beg + ti * kTileKeys, nbulk = min(kTileKeys, end - tb) & ~3u;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      osw::mbar_arrive(&s_mbar[ti & 1u], nbulk * 4);
+      if (nbulk) osw::bulk_g2s(vst[ti & 1u], vsrc + tb, nbulk * 4, &s_mbar[ti & 1u]);
+    };
+    // ---- rank every tile once: its digit counts and each key's position
     for (uint32_t ti = 0; ti < tiles; ++ti) {
       const uint32_t tb = beg + ti * kTileKeys, valid = min(kTileKeys, end - tb);
-#pragma unroll
-      for (int j = 0; j < kItems; ++j) {
-        const uint32_t idx = wbase + j * 32 + lane;
-        if (idx < valid) {
-          uint32_t k = __ldcs(kin + tb + idx);
-          if (p == 0) {
-            k = k == 0xffffffffu ? cull : k - lo;
-            for (uint32_t pp = 1; pp < passes; ++pp) atomicAdd(&s_hx[pp - 1][(k >> (pp * width)) & mask], 1u);
-          }
-          atomicAdd(&s_tc[ti][(k >> shift) & mask], 1u);
-        }
-      }
-    }
-    __syncthreads();
-    uint32_t own = 0;
-    for (uint32_t ti = 0; ti < tiles; ++ti) own += s_tc[ti][t];
-    sm.lstart[t] = own;
-    __syncthreads();
-    if (t < kBins / 8) {
-      const uint32_t* ls = sm.lstart + 8 * t;
-      uint4 w;
-      w.x = (ls[0] + 1u) | ((ls[1] + 1u) << 16);
-      w.y = (ls[2] + 1u) | ((ls[3] + 1u) << 16);
-      w.z = (ls[4] + 1u) | ((ls[5] + 1u) << 16);
-      w.w = (ls[6] + 1u) | ((ls[7] + 1u) << 16);
-      st_relaxed_v4(rows + (static_cast<size_t>(p) * G + c) * kRowWords + 4 * t, w);
-    }
-    if (p == 0) {
-      if (own) atomicAdd(hist + t, own);
-      for (uint32_t pp = 1; pp < passes; ++pp)
-        if (s_hx[pp - 1][t]) atomicAdd(hist + pp * kBins + t, s_hx[pp - 1][t]);
-      arrive_and_wait(scratch, G, err);
-    }
-    // ---- the chunk's running output base per digit (sm.base)
-    {
-      const uint32_t tot = __ldcg(hist + p * kBins + t);
-      uint32_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      sum_rows(rows + static_cast<size_t>(p) * G * kRowWords, low_half ? 0u : c + 1, low_half ? c : G, g, q,
-               acc, err);
-#pragma unroll
-      for (int i = 0; i < 8; ++i) s_part[g * kBins + 8 * q + i] = acc[i];
-      __syncthreads();
-      uint32_t sum = 0;
-#pragma unroll
-      for (uint32_t gg = 0; gg < kRowGroups; ++gg) sum += s_part[gg * kBins + t];
-      const uint32_t before = low_half ? sum : tot - own - sum;
-      sm.base[t] = excl_scan2(tot, 0u, s_warp2).x + before;
-      __syncthreads();
-    }
-    // ---- the tiles: stage values, rank, scatter from the running base
-    for (uint32_t ti = 0; ti < tiles; ++ti) {
-      const uint32_t tb = beg + ti * kTileKeys, valid = min(kTileKeys, end - tb);
-      const uint32_t nbulk = valid & ~3u;
-      if (t == 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        osw::mbar_arrive(&s_mbar, nbulk * 4);
-        if (nbulk) osw::bulk_g2s(vstage, vsrc + tb, nbulk * 4, &s_mbar);
-      }
       radix::TileRegs<uint32_t, false, kItems> R;
 #pragma unroll
       for (int j = 0; j < kItems; ++j) {
@@ -924,20 +926,85 @@ __global__ void __launch_bounds__(kThreads, 1) k_depth_sort_tiles(DepthSortArgs 
 #pragma unroll
       for (int j = 0; j < kItems; ++j) R.d[j] = (R.k[j] >> shift) & mask;
       radix::rank_keys<false, S, uint32_t, false, kBits, kItems>(valid, sm, R);
-      // this tile's digit starts; its keys go to base + tile position - start
+      const uint32_t cnt = sm.lstart[t];
+      s_tc[ti][t] = cnt;
+      sm.lstart[t] = excl_scan2(cnt, 0u, s_warp2).x;
+      __syncthreads();
+      uint16_t* my_wh = sm.wh + warp * kBins;
+#pragma unroll
+      for (int j = 0; j < kItems; ++j) {
+        const uint32_t idx = wbase + j * 32 + lane;
+        if (idx < valid) s_pos[ti * kTileKeys + idx] = static_cast<uint16_t>(R.r[j] + sm.lstart[R.d[j]] + my_wh[R.d[j]]);
+      }
+      __syncwarp();
+      uint4* z = reinterpret_cast<uint4*>(my_wh);
+      for (uint32_t i = lane; i < kBins / 8; i += 32) z[i] = make_uint4(0, 0, 0, 0);
+      __syncthreads();
+    }
+    if (t == 0 && tiles) stage(0);  // overlaps with the rows below
+    // ---- publish the chunk's counts; totals and the chunks before it
+    uint32_t own = 0;
+    for (uint32_t ti = 0; ti < tiles; ++ti) own += s_tc[ti][t];
+    sm.lstart[t] = own;
+    __syncthreads();
+    if (t < kBins / 8) {
+      const uint32_t* ls = sm.lstart + 8 * t;
+      uint4 w;
+      w.x = (ls[0] + 1u) | ((ls[1] + 1u) << 16);
+      w.y = (ls[2] + 1u) | ((ls[3] + 1u) << 16);
+      w.z = (ls[4] + 1u) | ((ls[5] + 1u) << 16);
+      w.w = (ls[6] + 1u) | ((ls[7] + 1u) << 16);
+      st_relaxed_v4(rows + (static_cast<size_t>(p) * G + c) * kRowWords + 4 * t, w);
+    }
+    {
+      uint32_t acc_lo[8] = {0, 0, 0, 0, 0, 0, 0, 0}, acc_all[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      sum_all_rows(rows + static_cast<size_t>(p) * G * kRowWords, G, c, g, q, acc_lo, acc_all, err);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        sm.xv[g * kBins + 8 * q + i] = acc_lo[i];
+        sm.xk[g * kBins + 8 * q + i] = acc_all[i];
+      }
+      __syncthreads();
+      uint32_t before = 0, tot = 0;
+#pragma unroll
+      for (uint32_t gg = 0; gg < kRowGroups; ++gg) {
+        before += sm.xv[gg * kBins + t];
+        tot += sm.xk[gg * kBins + t];
+      }
+      sm.base[t] = excl_scan2(tot, 0u, s_warp2).x + before;  // this chunk's first position per digit
+      __syncthreads();
+    }
+    // ---- the tiles, from the running base per digit
+    for (uint32_t ti = 0; ti < tiles; ++ti) {
+      const uint32_t tb = beg + ti * kTileKeys, valid = min(kTileKeys, end - tb);
+      const uint32_t b = ti & 1u;
+      if (t == 0 && ti + 1 < tiles) stage(ti + 1);
       {
-        const uint32_t cnt = sm.lstart[t];
+        const uint32_t cnt = s_tc[ti][t];
         const uint32_t st = excl_scan2(cnt, 0u, s_warp2).x;
         const uint32_t bs = sm.base[t];
-        sm.lstart[t] = st;
         sm.off[t] = bs - st;
         sm.base[t] = bs + cnt;
       }
-      if (!osw::mbar_wait(&s_mbar, phase & 1u, err) && t == 0) (void)osw::mbar_wait(&s_mbar, phase & 1u, err);
-      ++phase;
+      uint32_t hk[kItems], pos[kItems];
+#pragma unroll
+      for (int j = 0; j < kItems; ++j) {
+        const uint32_t idx = wbase + j * 32 + lane;
+        uint32_t k = 0u;
+        pos[j] = 0u;
+        if (idx < valid) {
+          k = __ldcs(kin + tb + idx);
+          if (p == 0) k = k == 0xffffffffu ? cull : k - lo;
+          pos[j] = s_pos[ti * kTileKeys + idx];
+        }
+        hk[j] = last ? (k >> shift) & mask : k;
+      }
+      if (!osw::mbar_wait(&s_mbar[b], (par >> b) & 1u, err) && t == 0)
+        (void)osw::mbar_wait(&s_mbar[b], (par >> b) & 1u, err);
+      par ^= 1u << b;
       __syncthreads();
-      ok &= exchange_scatter(sm, vstage, R, valid, tb, nbulk, vsrc, p == 0, last, shift, mask, n, kout, vout, k1,
-                             v1, counts, Sz, G, csum);
+      ok &= exchange_scatter(sm, vst[b], hk, pos, valid, tb, valid & ~3u, vsrc, p == 0, last, shift, mask, n, kout,
+                             vout, k1, v1, counts, Sz, G, csum);
     }
     arrive_and_wait(scratch + (last ? kFinalSlot : 1 + p) * kLine, G, err);
   }
@@ -953,15 +1020,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_depth_sort_tiles(DepthSortArgs 
     const uint32_t tb = beg + ti * kTileKeys;
     run = scan_offsets(k1, A.offsets, tb, min(tb + kTileKeys, end), run, s_sum, err);
   }
-  // ---- reset for the next launch
+  // ---- reset for the next launch: this chunk's rows; CTA 0 the counters
   for (uint32_t i = t; i < passes * (kRowWords / 4); i += kThreads) {
     const uint32_t pp = i / (kRowWords / 4), w = i % (kRowWords / 4);
     reinterpret_cast<uint4*>(rows + (static_cast<size_t>(pp) * G + c) * kRowWords)[w] = make_uint4(0, 0, 0, 0);
   }
-  if (c == 0) {
-    for (uint32_t i = t; i < passes * kBins; i += kThreads) hist[i] = 0u;
-    if (t < passes) scratch[t * kLine] = 0u;
-  }
+  if (c == 0 && t < passes) scratch[(1 + t) * kLine] = 0u;  // slots 1 .. passes (the last is unused)
 }
 
 }  // namespace depth
@@ -973,7 +1037,8 @@ radix::Kernel depth_kernel(Form f) {
   const void* fn = f == Form::kCount ? reinterpret_cast<const void*>(&depth::k_depth_sort<true>)
                    : f == Form::kOne ? reinterpret_cast<const void*>(&depth::k_depth_sort<false>)
                                      : reinterpret_cast<const void*>(&depth::k_depth_sort_tiles);
-  return radix::Kernel{fn, depth::kBits, depth::kThreads, depth::kItems, depth::kSmem, 1};
+  return radix::Kernel{fn, depth::kBits, depth::kThreads, depth::kItems,
+                       f == Form::kTiles ? depth::kSmemTiles : depth::kSmem, 1};
 }
 
 cudaError_t launch_depth(Form f, uint32_t grid, const DepthSortArgs& a, cudaStream_t s) {
@@ -986,7 +1051,7 @@ cudaError_t launch_depth(Form f, uint32_t grid, const DepthSortArgs& a, cudaStre
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(depth::kThreads);
-  cfg.dynamicSmemBytes = depth::kSmem;
+  cfg.dynamicSmemBytes = f == Form::kTiles ? depth::kSmemTiles : depth::kSmem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
