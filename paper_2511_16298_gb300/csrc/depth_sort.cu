@@ -620,8 +620,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_depth_sort(DepthSortArgs A) {
   }
   radix::PassArgs a{};
   a.m = n;
-  a.sub = lo;
-  a.cull = cull;
   a.mask = mask;
   a.err = err;
   __syncthreads();
@@ -636,7 +634,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_depth_sort(DepthSortArgs A) {
     uint32_t* kout = to_one ? k1 : k2;
     uint32_t* vout = to_one ? v1 : v2;
     a.shift = p * width;
-    a.xform_in = p == 0;
     const uint32_t* vsrc = p == 0 ? counts : vin;
     const bool counted = kCount && p == 0;  // values (the counts) already staged by the count step
     const uint32_t nstaged = counted ? valid : nbulk;

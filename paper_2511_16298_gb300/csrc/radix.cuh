@@ -186,9 +186,6 @@ struct PassArgs {
   const uint32_t* pbeg;        // [nv+1] first pair of each view
   uint32_t t_all;
   const uint64_t* m_dev;       // optional device element count, capped at m
-  // order-preserving key compression (uint32 keys, resident depth sort):
-  // on load key' = key == all ones ? cull : key - sub; on store the inverse
-  uint32_t xform_in, xform_out, sub, cull;
 };
 
 // kOcc: CTAs per SM the register budget is sized for (launch bounds); 0
@@ -424,7 +421,7 @@ __device__ __forceinline__ void chunk_bases(const K* __restrict__ kin, const Pas
 // when the tile was loaded), and (multi-pass tile sorts) records the
 // first/last position of each global tile run seen in this tile's exchange
 // buffer xk.
-template <typename K, bool kExpand, bool kXform = false>
+template <typename K, bool kExpand>
 __device__ __forceinline__ void emit_key(const PassArgs& a, K key, uint32_t gi, uint32_t dep, uint32_t dst,
                                          const K* xk, uint32_t p, uint32_t valid, const uint32_t* s_vrec,
                                          const uint32_t* s_vtile, void* kout_raw, uint32_t* vout) {
@@ -443,10 +440,7 @@ __device__ __forceinline__ void emit_key(const PassArgs& a, K key, uint32_t gi, 
       if (p + 1 == valid || static_cast<uint32_t>(xk[p + 1] >> a.rbits) != gt) atomicMax(a.rmax + gt, dst + 1);
     }
   } else {
-    K out = key;
-    if constexpr (kXform)
-      if (a.xform_out) out = key == a.cull ? 0xffffffffu : key + a.sub;
-    static_cast<K*>(kout_raw)[dst] = out;
+    static_cast<K*>(kout_raw)[dst] = key;
   }
 }
 
@@ -538,14 +532,13 @@ struct TileRegs {
 // digits; with at most 64 the per-warp counts are left for scatter_tile,
 // which folds the prefix into its one-warp digit starts.  Each warp's
 // counter row is zero on entry.
-// kXform: the single-launch depth sort's key compression may apply
-// (a.xform_in).  rank_keys is the same after the load, for keys and digits
-// already in R.k / R.d (item j of lane l of warp w is tile item
-// w * 32 * kItems + j * 32 + l).
+// rank_keys is the same after the load, for keys and digits already in
+// R.k / R.d (item j of lane l of warp w is tile item w * 32 * kItems +
+// j * 32 + l).
 template <bool kFull, typename S, typename K, bool kExpand, int kBits, int kItems>
 __device__ __forceinline__ void rank_keys(uint32_t valid, const Smem<K>& sm, TileRegs<K, kExpand, kItems>& R);
 
-template <bool kFull, typename S, typename K, bool kExpand, int kBits, int kItems, bool kXform = false>
+template <bool kFull, typename S, typename K, bool kExpand, int kBits, int kItems>
 __device__ __forceinline__ void rank_tile(const K* __restrict__ kt, uint32_t valid, const PassArgs& a, bool d31,
                                           const Smem<K>& sm, TileRegs<K, kExpand, kItems>& R) {
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
@@ -554,8 +547,6 @@ __device__ __forceinline__ void rank_tile(const K* __restrict__ kt, uint32_t val
   for (int j = 0; j < kItems; ++j) {
     const uint32_t idx = wbase + j * 32 + lane;
     R.k[j] = (kFull || idx < valid) ? __ldcs(kt + idx) : K(0);
-    if constexpr (kXform)
-      if (a.xform_in) R.k[j] = R.k[j] == 0xffffffffu ? a.cull : R.k[j] - a.sub;
     R.d[j] = digit_of<K>(R.k[j], a.shift, a.mask, d31);
   }
   rank_keys<kFull, S, K, kExpand, kBits, kItems>(valid, sm, R);
@@ -633,8 +624,7 @@ __device__ __forceinline__ void rank_keys(uint32_t valid, const Smem<K>& sm, Til
 // Returns false if a destination fell outside [0, m).  Block barriers:
 // after the digit starts and after the exchange (and one more for values);
 // this warp's counter row is zeroed again.
-template <bool kFull, typename S, typename K, bool kVals, bool kExpand, int kBits, int kItems,
-          bool kXform = false>
+template <bool kFull, typename S, typename K, bool kVals, bool kExpand, int kBits, int kItems>
 __device__ __forceinline__ bool scatter_tile(const uint32_t* __restrict__ vt, uint32_t valid, uint32_t m,
                                              const PassArgs& a, bool d31, const Smem<K>& sm, uint32_t* s_warp,
                                              const uint32_t* s_vrec, const uint32_t* s_vtile, void* kout_raw,
@@ -754,7 +744,7 @@ __device__ __forceinline__ bool scatter_tile(const uint32_t* __restrict__ vt, ui
         const K key = sm.xk[p];
         dst[i] = sm.off[digit_of<K>(key, a.shift, a.mask, d31)] + p;
         if (dst[i] < m)
-          emit_key<K, false, kXform>(a, key, 0u, 0u, dst[i], sm.xk, p, valid, s_vrec, s_vtile, kout_raw, vout);
+          emit_key<K, false>(a, key, 0u, 0u, dst[i], sm.xk, p, valid, s_vrec, s_vtile, kout_raw, vout);
         else
           ok = false;
       }
