@@ -420,11 +420,13 @@ __device__ __forceinline__ void chunk_bases(const K* __restrict__ kin, const Pas
 // the view-local Gaussian index (gi is the global record index, gathered
 // when the tile was loaded), and (multi-pass tile sorts) records the
 // first/last position of each global tile run seen in this tile's exchange
-// buffer xk.
+// buffer xk (run_ends: this element's own test; false when the tile's runs
+// were recorded per digit).
 template <typename K, bool kExpand>
 __device__ __forceinline__ void emit_key(const PassArgs& a, K key, uint32_t gi, uint32_t dep, uint32_t dst,
                                          const K* xk, uint32_t p, uint32_t valid, const uint32_t* s_vrec,
-                                         const uint32_t* s_vtile, void* kout_raw, uint32_t* vout) {
+                                         const uint32_t* s_vtile, void* kout_raw, uint32_t* vout,
+                                         bool run_ends = true) {
   if constexpr (kExpand) {
     const uint32_t gt = static_cast<uint32_t>(key >> a.rbits);
     uint32_t tb = 0, rb = 0;  // first global tile and record of the view (0 for one view)
@@ -435,7 +437,7 @@ __device__ __forceinline__ void emit_key(const PassArgs& a, K key, uint32_t gi, 
     }
     static_cast<uint64_t*>(kout_raw)[dst] = (static_cast<uint64_t>(gt - tb) << 32) | dep;
     vout[dst] = gi - rb;
-    if (a.rmin) {
+    if (a.rmin && run_ends) {
       if (p == 0 || static_cast<uint32_t>(xk[p - 1] >> a.rbits) != gt) atomicMin(a.rmin + gt, dst);
       if (p + 1 == valid || static_cast<uint32_t>(xk[p + 1] >> a.rbits) != gt) atomicMax(a.rmax + gt, dst + 1);
     }
@@ -636,6 +638,9 @@ __device__ __forceinline__ bool scatter_tile(const uint32_t* __restrict__ vt, ui
   const uint32_t wbase = warp * 32 * kItems;
   uint16_t* my_wh = sm.wh + warp * kBins;
   bool ok = true;
+  __shared__ uint32_t s_low;  // expanding pass: tile item 0's tile bits below this pass's digit
+  if constexpr (kExpand)
+    if (t == 0) s_low = static_cast<uint32_t>(R.k[0] >> a.rbits) & ((1u << (a.shift - a.rbits)) - 1u);
   if constexpr (kBins <= 64) {
     // one warp: prefix over warps of each counter column (two digits per
     // word, lane = column), the tile's count per digit, the digit starts
@@ -698,7 +703,41 @@ __device__ __forceinline__ bool scatter_tile(const uint32_t* __restrict__ vt, ui
       v[j] = (kFull || idx < valid) ? __ldcs(vt + idx) : 0u;
     }
   }
-  __syncthreads();
+  // The expanding pass of a multi-pass tile sort records each tile run's
+  // first and last position.  When the tile's elements share the tile bits
+  // the earlier passes sorted by (its first and last element do: the input
+  // is sorted by them), each digit run is one tile: one thread per digit
+  // records its ends.  Otherwise every element tests its neighbours.
+  bool per_digit = false;
+  if constexpr (kExpand) {
+    if (a.rmin) {
+      const uint32_t lb = a.shift - a.rbits;  // tile bits sorted by the earlier passes
+      const uint32_t lmask = (1u << lb) - 1u;
+      const uint32_t lo0 = s_low;  // written before the digit-start barrier
+      bool same = true;
+#pragma unroll
+      for (int j = 0; j < kItems; ++j)
+        if (kFull || wbase + j * 32 + lane < valid) same &= (static_cast<uint32_t>(R.k[j] >> a.rbits) & lmask) == lo0;
+      per_digit = __syncthreads_and(same) != 0;
+      if (per_digit) {
+        for (uint32_t d = t; d < static_cast<uint32_t>(kBins); d += kThreads) {
+          const uint32_t st = sm.lstart[d];
+          const uint32_t en = d + 1 < static_cast<uint32_t>(kBins) ? sm.lstart[d + 1] : valid;
+          if (en > st) {
+            const uint32_t gt = (d << lb) | lo0, first = sm.off[d] + st;
+            if (first < m && first + (en - st) <= m) {
+              atomicMin(a.rmin + gt, first);
+              atomicMax(a.rmax + gt, first + (en - st));
+            }
+          }
+        }
+      }
+    } else {
+      __syncthreads();
+    }
+  } else {
+    __syncthreads();
+  }
   // Scatter in digit order.  A destination outside [0, m) can only come
   // from a timed-out barrier or keys changed underneath the sort: it is
   // dropped and reported instead of written.
@@ -729,7 +768,8 @@ __device__ __forceinline__ bool scatter_tile(const uint32_t* __restrict__ vt, ui
         const uint32_t p = (i0 + h) * kThreads + t;
         if (kFull || p < valid) {
           if (at[h] < m)
-            emit_key<K, true>(a, key[h], dg[h].y, dg[h].x, at[h], sm.xk, p, valid, s_vrec, s_vtile, kout_raw, vout);
+            emit_key<K, true>(a, key[h], dg[h].y, dg[h].x, at[h], sm.xk, p, valid, s_vrec, s_vtile, kout_raw, vout,
+                              !per_digit);
           else
             ok = false;
         }
