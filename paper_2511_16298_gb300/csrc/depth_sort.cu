@@ -74,7 +74,7 @@ constexpr uint32_t kTileKeys = S::kTileKeys;
 constexpr size_t kSmem = S::kSmem + kTileKeys * 4;  // + the staged values
 static_assert(S::kSmem % 16 == 0, "the staged values start 16-byte aligned");
 static_assert(kTileKeys == 8192, "one 8192-key chunk per CTA");
-static_assert(kTileKeys < (1u << 14), "a chunk's count of one digit fits 14 bits");
+static_assert(4 * kTileKeys + 1 < (1u << 16), "a chunk's count of one digit, plus one, fits a 16-bit row field");
 static_assert(static_cast<uint64_t>(kMaxGrid) * kTileKeys <= (1ull << kValueBits), "record index bits");
 static_assert(kThreads == static_cast<int>(kBins), "one digit per thread in the base computation");
 
@@ -207,7 +207,8 @@ __device__ __forceinline__ void sum_rows(const uint32_t* __restrict__ rows, uint
 // One ranked tile of `valid` keys (tile items start at record tb; item j of
 // this thread goes to tile position pos[j]): the (key, value) -- in the
 // last pass (digit, value); hi[j] is the key or the digit -- exchange
-// through shared memory, and the scatter to off[digit] + tile position.  Values come from vstage (items below nstaged) or vsrc + tb;
+// through shared memory, and the scatter to off[digit] + tile position.
+// Values come from vstage (items below nstaged) or vsrc + tb;
 // pass 0 (first) makes each value the record index with the tile count in
 // its top bits.  The last pass writes v1 (record index) and k1 (count) and
 // adds the counts it writes into the per-output-chunk sums csum (chunks of
@@ -668,7 +669,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_depth_sort(DepthSortArgs A) {
       for (int j = 0; j < kItems; ++j) R.d[j] = (R.k[j] >> a.shift) & mask;
       radix::rank_keys<false, S, uint32_t, false, kBits, kItems>(valid, sm, R);
     }
-    // publish this chunk's digit counts (lstart) as a tagged row
+    // publish this chunk's digit counts (lstart) as its row (count + 1)
     if (t < kBins / 8) {
       const uint32_t* ls = sm.lstart + 8 * t;
       uint4 w;
