@@ -51,28 +51,23 @@ constexpr size_t kWhBytes = static_cast<size_t>(kWarps) * kBins * 2;  // per-war
 constexpr size_t kSmem = 2 * sizeof(TileBuf) + kWhBytes + 3 * kBins * 4;
 
 // Digit of one key for one pass: bits [shift, shift + width) of the key,
-// or of (tile bits : depth bits 30..0) when bit 31 is dropped.  The host
-// folds both cases into a funnel shift (see make_digit).
+// or of (tile bits : depth bits 30..0) when bit 31 is dropped (the keys
+// then have bit 31 clear).  Three forms, chosen on the host (make_digit)
+// and compiled separately: a bit field of the low word, a bit field of the
+// high word, or a field spanning both, (lo >> msh) | (hi << hsh).
 struct Digit {
-  uint32_t sh;       // shift applied to (hi : lo') or to hi alone
-  uint32_t hi_only;  // the digit lies in the high word
-  uint32_t lo_shl;   // 1 when bit 31 is dropped (lo' = lo << 1), else 0
+  uint32_t mode;  // kDigitLo, kDigitHi or kDigitSpan
+  uint32_t msh;   // right shift of the word holding the field (the low word for a span)
+  uint32_t hsh;   // span: left shift of the high word
   uint32_t mask;
-  uint32_t mode;     // kDigitLo / kDigitHi: the digit is a bit field of one word at msh
-  uint32_t msh;
 };
-constexpr int kDigitLo = 0, kDigitHi = 1, kDigitAny = 2;
-__device__ __forceinline__ uint32_t digit(uint64_t k, const Digit& g) {
-  const uint32_t lo = static_cast<uint32_t>(k) << g.lo_shl, hi = static_cast<uint32_t>(k >> 32);
-  const uint32_t d = g.hi_only ? (hi >> g.sh) : __funnelshift_r(lo, hi, g.sh);
-  return d & g.mask;
-}
-// The same digit when the pass's field lies in one word (most passes).
+constexpr int kDigitLo = 0, kDigitHi = 1, kDigitSpan = 2, kDigitNone = 3;
 template <int kMode>
 __device__ __forceinline__ uint32_t digit_m(uint64_t k, const Digit& g) {
-  if constexpr (kMode == kDigitLo) return (static_cast<uint32_t>(k) >> g.msh) & g.mask;
-  if constexpr (kMode == kDigitHi) return (static_cast<uint32_t>(k >> 32) >> g.msh) & g.mask;
-  return digit(k, g);
+  const uint32_t lo = static_cast<uint32_t>(k), hi = static_cast<uint32_t>(k >> 32);
+  if constexpr (kMode == kDigitLo) return (lo >> g.msh) & g.mask;
+  if constexpr (kMode == kDigitHi) return (hi >> g.msh) & g.mask;
+  return ((lo >> g.msh) | (hi << g.hsh)) & g.mask;
 }
 
 struct HistArgs {
@@ -201,7 +196,7 @@ __device__ __forceinline__ void load_tile(TileBuf* b, uint64_t* bar, const uint6
 // Stable rank of one tile held in shared memory (tile order: warp, item,
 // lane): r[j] = number of earlier items of this warp with the same digit;
 // the warp's counter row (zero on entry) ends holding its count per digit.
-template <int kMode>
+template <int kMode, int kModeN>
 __device__ __forceinline__ void rank_in_warps(const TileBuf& tb, uint32_t valid, const Digit& dg, uint16_t* my_wh,
                                               uint32_t (&r)[kItems], const Digit& dgn, uint32_t* hn) {
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
@@ -215,7 +210,8 @@ __device__ __forceinline__ void rank_in_warps(const TileBuf& tb, uint32_t valid,
       const uint32_t idx = wbase + (j0 + g) * 32 + lane;
       const uint64_t key = idx < valid ? tb.k[idx] : 0ull;
       d[g] = digit_m<kMode>(key, dg);
-      if (hn && idx < valid) atomicAdd(&hn[digit(key, dgn)], 1u);
+      if constexpr (kModeN != kDigitNone)
+        if (idx < valid) atomicAdd(&hn[digit_m<kModeN>(key, dgn)], 1u);
       r[j0 + g] = radix::equal_digit_lanes<kBits>(d[g]);
       const uint32_t fi = wbase + (j0 + g) * 32;
       const uint32_t nlive = valid > fi ? min(valid - fi, 32u) : 0u;
@@ -245,7 +241,7 @@ __device__ __forceinline__ void rank_in_warps(const TileBuf& tb, uint32_t valid,
 // and the scan always completes.  Launched cooperatively: the scan CTAs
 // must run alongside every other CTA.  While ranking, the CTA also counts
 // the next pass's digits; the counts reach hist_next when it finishes.
-template <int kMode>
+template <int kMode, int kModeN>
 __global__ void __launch_bounds__(kThreads, 2)
     k_onesweep_pass(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
                     uint32_t* __restrict__ vout, PassArgs a) {
@@ -254,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   uint16_t* wh = reinterpret_cast<uint16_t*>(smem + 2 * sizeof(TileBuf));
   uint32_t* lstart = reinterpret_cast<uint32_t*>(smem + 2 * sizeof(TileBuf) + kWhBytes);
   uint32_t* off = lstart + kBins;
-  uint32_t* hn = a.hist_next ? off + kBins : nullptr;  // next pass's digit counts of this CTA
+  uint32_t* hn = kModeN != kDigitNone ? off + kBins : nullptr;  // next pass's digit counts of this CTA
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t s_tile[2];
   __shared__ uint32_t s_warp[kWarps];
@@ -341,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       // ---- stable rank within each warp
       uint32_t r[kItems];
-      rank_in_warps<kMode>(tb, valid, dg, my_wh, r, a.dgn, hn);
+      rank_in_warps<kMode, kModeN>(tb, valid, dg, my_wh, r, a.dgn, hn);
       if (t == 0 && nxt < ntiles) {
         const uint32_t nf = nxt * kTileKeys, nv = min(kTileKeys, m - nf);
         radix::prefetch_l2(kin + nf, static_cast<uint64_t>(nv) * 8);
@@ -459,7 +455,8 @@ uint32_t pass_grid() {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_grid[dev]) {
-    const void* fn = reinterpret_cast<const void*>(&onesweep::k_onesweep_pass<onesweep::kDigitAny>);
+    const void* fn =
+        reinterpret_cast<const void*>(&onesweep::k_onesweep_pass<onesweep::kDigitLo, onesweep::kDigitNone>);
     int sms = 0, occ = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(onesweep::kSmem)) !=
@@ -475,13 +472,9 @@ uint32_t pass_grid() {
 
 onesweep::Digit make_digit(uint32_t shift, uint32_t mask, bool drop31) {
   onesweep::Digit d{};
-  const uint32_t s = shift + (drop31 ? 1u : 0u);
-  d.lo_shl = drop31 ? 1u : 0u;
-  d.hi_only = s >= 32 ? 1u : 0u;
-  d.sh = s >= 32 ? s - 32 : s;
   d.mask = mask;
-  // one-word digits: bits [0, 31) (or [0, 32) without the drop) are the
-  // low word's; bits from 31 on (32 on) are the high word's
+  // bits [0, 31) (or [0, 32) without the drop) are the low word's; bits
+  // from 31 on (32 on) are the high word's
   const uint32_t width = static_cast<uint32_t>(__builtin_popcount(mask));
   const uint32_t split = drop31 ? 31u : 32u;
   if (shift + width <= split) {
@@ -490,11 +483,24 @@ onesweep::Digit make_digit(uint32_t shift, uint32_t mask, bool drop31) {
   } else if (shift >= split) {
     d.mode = onesweep::kDigitHi;
     d.msh = shift - split;
-  } else {
-    d.mode = onesweep::kDigitAny;
-    d.msh = 0;
+  } else {  // 0 < split - shift < width <= 9: both shifts stay below 32
+    d.mode = onesweep::kDigitSpan;
+    d.msh = shift;
+    d.hsh = split - shift;
   }
   return d;
+}
+
+// The pass kernel for a digit form and the next pass's digit form.
+template <int kMode>
+const void* pass_kernel(uint32_t next) {
+  using namespace onesweep;
+  switch (next) {
+    case kDigitLo: return reinterpret_cast<const void*>(&k_onesweep_pass<kMode, kDigitLo>);
+    case kDigitHi: return reinterpret_cast<const void*>(&k_onesweep_pass<kMode, kDigitHi>);
+    case kDigitSpan: return reinterpret_cast<const void*>(&k_onesweep_pass<kMode, kDigitSpan>);
+    default: return reinterpret_cast<const void*>(&k_onesweep_pass<kMode, kDigitNone>);
+  }
 }
 }  // namespace
 
@@ -581,9 +587,10 @@ cudaError_t launch_onesweep_pass(const SortPlan& plan, uint32_t pass, const uint
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const void* fn = a.dg.mode == kDigitLo   ? reinterpret_cast<const void*>(&k_onesweep_pass<kDigitLo>)
-                   : a.dg.mode == kDigitHi ? reinterpret_cast<const void*>(&k_onesweep_pass<kDigitHi>)
-                                           : reinterpret_cast<const void*>(&k_onesweep_pass<kDigitAny>);
+  const uint32_t next = pass + 1 < plan.passes ? a.dgn.mode : static_cast<uint32_t>(kDigitNone);
+  const void* fn = a.dg.mode == kDigitLo   ? pass_kernel<kDigitLo>(next)
+                   : a.dg.mode == kDigitHi ? pass_kernel<kDigitHi>(next)
+                                           : pass_kernel<kDigitSpan>(next);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmem)) != cudaSuccess)
     return cudaErrorInvalidConfiguration;
   return cudaLaunchKernelExC(&cfg, fn, args);
