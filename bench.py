@@ -664,7 +664,8 @@ def run_large(args, local_rank):
             "frame": {"pairs_per_s": m / (statistics.median(t_frame) * 1e-3),
                       "p50_ms": round(statistics.median(t_frame), 4),
                       "p99_ms": round(float(np.percentile(t_frame, 99)), 4)},
-            "kernels": {k: {"launches": d["launches"] // reps, "avg_ms": round(d["ms"] / max(1, d["launches"]), 5)}
+            "kernels": {k: {"launches": d["launches"] // reps, "avg_ms": round(d["ms"] / max(1, d["launches"]), 5),
+                            "ms_per_frame": round(d["ms"] / reps, 5)}
                         for k, d in kt.items()},
             "sort_pairs": {"pairs_per_s": m / (smean * 1e-3), "ms_mean": round(smean, 4), "passes": passes,
                            "algorithmic_bytes": sbytes,

@@ -108,11 +108,12 @@ struct tdgs_context {
   Buffer scan_status, sort_scratch;
   Buffer os_scratch;  // onesweep sort: histograms, digit starts, tickets, look-back status
   Buffer f_dsort;     // single-launch depth sort: barrier counters, totals, rows (kept zero between launches)
+  Buffer f_dos;       // onesweep depth sort (large N): histograms, digit starts, tickets, look-back status
   // State that kernels keep between launches, to be cleared before its next
   // use after an error was latched on the device (a bounded wait may have
-  // given up mid-launch): the depth sort's buffer, the onesweep header, the
+  // given up mid-launch): the depth sort's buffers, the onesweep header, the
   // radix grid barrier words.
-  bool dsort_dirty = true, os_dirty = false, bar_dirty = false;
+  bool dsort_dirty = true, dos_dirty = true, os_dirty = false, bar_dirty = false;
   // fused-frame / multi-view buffers
   Buffer f_rec3, f_conic;  // projected records and conics of tdgs_sort_frame_3d
   Buffer d_cams;           // cameras of the 3D calls (device)
@@ -203,7 +204,9 @@ tdgs_status ensure(tdgs_context* ctx, Buffer& b, size_t bytes, cudaStream_t s,
 
 uint32_t* err_word(tdgs_context* ctx) { return &ctx->d_status->err; }
 
-void note_device_error(tdgs_context* ctx) { ctx->dsort_dirty = ctx->os_dirty = ctx->bar_dirty = true; }
+void note_device_error(tdgs_context* ctx) {
+  ctx->dsort_dirty = ctx->dos_dirty = ctx->os_dirty = ctx->bar_dirty = true;
+}
 
 // The radix grid barrier words back to zero if an error was latched since
 // their last use.
@@ -536,7 +539,7 @@ void tdgs_context_destroy(tdgs_context* ctx) {
   DeviceGuard g(ctx->device);
   drain_timings(ctx);
   for (cudaEvent_t e : ctx->free_events) cudaEventDestroy(e);
-  Buffer* bufs[] = {&ctx->scan_status, &ctx->sort_scratch, &ctx->os_scratch, &ctx->f_dsort, &ctx->f_counts, &ctx->f_dkey[0],
+  Buffer* bufs[] = {&ctx->scan_status, &ctx->sort_scratch, &ctx->os_scratch, &ctx->f_dsort, &ctx->f_dos, &ctx->f_counts, &ctx->f_dkey[0],
                     &ctx->f_dkey[1],    &ctx->f_dkey[2],     &ctx->f_dval[0],    &ctx->f_dval[1],
                     &ctx->f_dval[2],    &ctx->f_soff,       &ctx->f_sdo,        &ctx->f_rec3,
                     &ctx->f_conic,      &ctx->d_cams,       &ctx->diag,       &ctx->b_keys,       &ctx->b_vals,       &ctx->n_counts,
@@ -771,6 +774,14 @@ tdgs_status ensure_record_buffers(tdgs_context* ctx, cudaStream_t s) {
       ctx->dsort_dirty = false;
     }
   }
+  if (st == TDGS_OK && dp.onesweep) {
+    grown = false;
+    st = ensure(ctx, ctx->f_dos, onesweep_scratch_words(n_all ? n_all : 1) * 4, s, &grown);
+    if (st == TDGS_OK && (grown || ctx->dos_dirty)) {
+      TDGS_CUDA(ctx, cudaMemsetAsync(ctx->f_dos.p, 0, onesweep_header_words() * 4, s));
+      ctx->dos_dirty = false;
+    }
+  }
   return st;
 }
 
@@ -849,6 +860,15 @@ tdgs_status run_front(tdgs_context* ctx, cudaStream_t s, bool early_total = fals
   if (dp.resident) {  // one launch: the sort (pass count from the depth range) and the offsets
     da.key0 = dk[0];
     TDGS_TRACED(ctx, kKDepthSort, n_all, s, launch_depth_sort(dp.grid, da, s));
+  } else if (dp.onesweep) {  // histogram, then the passes the key range needs (result in pair 1)
+    if (n_all) {
+      uint32_t* dos = static_cast<uint32_t*>(ctx->f_dos.p);
+      TDGS_TRACED(ctx, kKDepthSort, n_all, s,
+                  launch_depth_onesweep_hist(dk[0], n_all, ctx->d_range, dos, err_word(ctx), s));
+      for (uint32_t p = 0; p < dpasses; ++p)
+        TDGS_TRACED(ctx, kKDepthSort, n_all, s,
+                    launch_depth_onesweep_pass(p, dk, dv, n_all, ctx->d_range, dos, err_word(ctx), s));
+    }
   } else {
     for (uint32_t p = 0; p < dpasses; ++p) {
       TDGS_TRACED(ctx, kKDepthSort, n_all, s,

@@ -26,6 +26,7 @@
 // and latches TDGS_ERR_TIMEOUT when it runs out; every scatter is checked
 // against the pair count.
 #include <mutex>
+#include <type_traits>
 
 #include "onesweep.cuh"
 
@@ -43,31 +44,66 @@ constexpr uint32_t kScanCtas = scan_ctas<kBins>();
 
 static_assert(kBins == 2 * kThreads, "two digits per thread in the look-back and the digit scan");
 
+template <typename K>
 struct TileBuf {
-  uint64_t k[kTileKeys];
+  K k[kTileKeys];
   uint32_t v[kTileKeys];
 };
 constexpr size_t kWhBytes = static_cast<size_t>(kWarps) * kBins * 2;  // per-warp 16-bit counters
-constexpr size_t kSmem = 2 * sizeof(TileBuf) + kWhBytes + 3 * kBins * 4;
+template <typename K>
+constexpr size_t smem_bytes() {
+  return 2 * sizeof(TileBuf<K>) + kWhBytes + 3 * kBins * 4;
+}
 
-// Digit of one key for one pass: bits [shift, shift + width) of the key,
-// or of (tile bits : depth bits 30..0) when bit 31 is dropped (the keys
-// then have bit 31 clear).  Three forms, chosen on the host (make_digit)
-// and compiled separately: a bit field of the low word, a bit field of the
-// high word, or a field spanning both, (lo >> msh) | (hi << hsh).
+// Digit of one key for one pass.  64-bit keys (tdgs_sort_pairs): bits
+// [shift, shift + width) of the key, or of (tile bits : depth bits 30..0)
+// when bit 31 is dropped (the keys then have bit 31 clear), in three forms
+// chosen on the host (make_digit) and compiled separately: a bit field of
+// the low word, a bit field of the high word, or a field spanning both,
+// (lo >> msh) | (hi << hsh).  32-bit depth keys (the depth sort of
+// Sec. II-A's frame; form kDigitDepth): bits [msh, msh + width) of the key
+// less the smallest visible key lo, culled Gaussians' keys (all ones)
+// becoming cull, one more than the largest; the device derives the pass
+// plan from the key range the count kernel published (depth_digits).
 struct Digit {
-  uint32_t mode;  // kDigitLo, kDigitHi or kDigitSpan
+  uint32_t mode;  // kDigitLo, kDigitHi, kDigitSpan or kDigitDepth
   uint32_t msh;   // right shift of the word holding the field (the low word for a span)
   uint32_t hsh;   // span: left shift of the high word
   uint32_t mask;
+  uint32_t lo, cull;  // depth keys: the compression
 };
-constexpr int kDigitLo = 0, kDigitHi = 1, kDigitSpan = 2, kDigitNone = 3;
+constexpr int kDigitLo = 0, kDigitHi = 1, kDigitSpan = 2, kDigitDepth = 3, kDigitNone = 4;
 template <int kMode>
-__device__ __forceinline__ uint32_t digit_m(uint64_t k, const Digit& g) {
-  const uint32_t lo = static_cast<uint32_t>(k), hi = static_cast<uint32_t>(k >> 32);
-  if constexpr (kMode == kDigitLo) return (lo >> g.msh) & g.mask;
-  if constexpr (kMode == kDigitHi) return (hi >> g.msh) & g.mask;
-  return ((lo >> g.msh) | (hi << g.hsh)) & g.mask;
+using KeyOf = std::conditional_t<kMode == kDigitDepth, uint32_t, uint64_t>;
+template <int kMode, typename K>
+__device__ __forceinline__ uint32_t digit_m(K k, const Digit& g) {
+  if constexpr (kMode == kDigitDepth) {
+    const uint32_t x = static_cast<uint32_t>(k) == 0xffffffffu ? g.cull : static_cast<uint32_t>(k) - g.lo;
+    return (x >> g.msh) & g.mask;
+  } else {
+    const uint32_t lo = static_cast<uint32_t>(k), hi = static_cast<uint32_t>(static_cast<uint64_t>(k) >> 32);
+    if constexpr (kMode == kDigitLo) return (lo >> g.msh) & g.mask;
+    if constexpr (kMode == kDigitHi) return (hi >> g.msh) & g.mask;
+    return ((lo >> g.msh) | (hi << g.hsh)) & g.mask;
+  }
+}
+
+// Pass plan of the depth keys from their range (range[2..3]: the smallest
+// and largest visible key): the compressed keys 0 .. cull need `bits` bits,
+// split evenly over the fewest passes of at most kBits.
+struct DepthDigits {
+  uint32_t lo, cull, passes, width, mask;
+};
+__device__ __forceinline__ DepthDigits depth_digits(const uint32_t* range) {
+  DepthDigits d;
+  d.lo = __ldcg(range + 2);
+  const uint32_t hi = __ldcg(range + 3);
+  d.cull = hi >= d.lo ? hi - d.lo + 1u : 0u;
+  const uint32_t bits = d.cull ? 32u - static_cast<uint32_t>(__clz(d.cull)) : 0u;
+  d.passes = bits ? (bits + kBits - 1) / kBits : 1u;
+  d.width = (bits + d.passes - 1) / d.passes;
+  d.mask = d.width ? (1u << d.width) - 1u : 0u;
+  return d;
 }
 
 struct HistArgs {
@@ -79,6 +115,7 @@ struct HistArgs {
   uint32_t* done;      // block counter, zero on entry, left zero
   uint32_t* tickets;   // [kMaxPasses] tile tickets, cleared here
   uint32_t* status0;   // [ntiles][kBins] look-back status of pass 0, cleared here
+  uint32_t* range;     // depth keys: the key range (range[2..3]); the pass count goes to range[4]
   uint32_t* err;
 };
 
@@ -92,6 +129,12 @@ struct PassArgs {
   uint32_t* status;        // [ntiles][kBins] this pass's status (all zero on entry)
   uint32_t* status_next;   // [ntiles][kBins] the next pass's, cleared here (or null)
   uint32_t* ticket;        // zero on entry
+  // depth keys: the pass number, the key range and the three key and value
+  // buffers (0: input; the last pass that runs writes buffer 1)
+  uint32_t pass;
+  const uint32_t* range;
+  uint32_t* dk[3];
+  uint32_t* dv[3];
   uint32_t* err;
 };
 
@@ -104,7 +147,9 @@ struct PassArgs {
 // into L2 while it counts.  Few blocks (4 per SM) keep the final global
 // atomics on the counters few.
 constexpr int kHistThreads = 512;
-__global__ void __launch_bounds__(kHistThreads) k_onesweep_hist(const uint64_t* __restrict__ keys, HistArgs a) {
+template <int kMode>
+__global__ void __launch_bounds__(kHistThreads) k_onesweep_hist(const KeyOf<kMode>* __restrict__ keys, HistArgs a) {
+  using K = KeyOf<kMode>;
   __shared__ uint32_t h[kBins];
   __shared__ uint32_t s_warp[kHistThreads / 32];
   __shared__ bool s_last;
@@ -125,7 +170,12 @@ __global__ void __launch_bounds__(kHistThreads) k_onesweep_hist(const uint64_t* 
   }
   __syncthreads();
   const uint32_t m = a.m;
-  const uint32_t mask0 = a.dg[0].mask;  // the first digit is bits [0, width) of the key's low word
+  Digit dg0 = a.dg[0];  // 64-bit keys: the first digit is bits [0, width) of the low word
+  if constexpr (kMode == kDigitDepth) {
+    const DepthDigits dd = depth_digits(a.range);
+    dg0 = Digit{kDigitDepth, 0u, 0u, dd.mask, dd.lo, dd.cull};
+    if (blockIdx.x == 0 && t == 0) a.range[4] = dd.passes;  // for the host's diagnostics
+  }
   const bool vec = (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
   constexpr uint32_t kStep = 8 * kHistThreads;  // keys per block and step: 8 consecutive per thread
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kStep;
@@ -134,24 +184,35 @@ __global__ void __launch_bounds__(kHistThreads) k_onesweep_hist(const uint64_t* 
     if (t == 0 && base + stride < m)  // the next step's keys into L2 while this step counts
       radix::prefetch_l2(keys + base + stride, (min(static_cast<uint64_t>(kStep), m - (base + stride))) * 8);
     const uint64_t i0 = base + 8 * t;
-    uint64_t k[8];
+    K k[8];
     if (vec && i0 + 8 <= m) {
+      if constexpr (sizeof(K) == 8) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const uint4 w = __ldcs(reinterpret_cast<const uint4*>(keys + i0) + u);
-        k[2 * u] = (static_cast<uint64_t>(w.y) << 32) | w.x;
-        k[2 * u + 1] = (static_cast<uint64_t>(w.w) << 32) | w.z;
+        for (int u = 0; u < 4; ++u) {
+          const uint4 w = __ldcs(reinterpret_cast<const uint4*>(keys + i0) + u);
+          k[2 * u] = (static_cast<uint64_t>(w.y) << 32) | w.x;
+          k[2 * u + 1] = (static_cast<uint64_t>(w.w) << 32) | w.z;
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const uint4 w = __ldcs(reinterpret_cast<const uint4*>(keys + i0) + u);
+          k[4 * u] = w.x;
+          k[4 * u + 1] = w.y;
+          k[4 * u + 2] = w.z;
+          k[4 * u + 3] = w.w;
+        }
       }
     } else {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) k[j] = i0 + j < m ? keys[i0 + j] : 0ull;
+      for (int j = 0; j < 8; ++j) k[j] = i0 + j < m ? keys[i0 + j] : K(0);
     }
     uint32_t run_d = 0, run_n = 0;  // runs of equal digits: one atomic each
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       if (i0 + j < m) {
-        bad |= (k[j] & a.bad_mask) != 0;
-        const uint32_t d = static_cast<uint32_t>(k[j]) & mask0;
+        if constexpr (kMode != kDigitDepth) bad |= (k[j] & a.bad_mask) != 0;
+        const uint32_t d = digit_m<kMode>(k[j], dg0);
         if (run_n && d != run_d) {
           atomicAdd(&h[run_d], run_n);
           run_n = 0;
@@ -182,9 +243,10 @@ __global__ void __launch_bounds__(kHistThreads) k_onesweep_hist(const uint64_t* 
 
 // One tile's keys and values (first `nbulk` pairs, a multiple of 4) by bulk
 // copies completing on `bar`.
-__device__ __forceinline__ void load_tile(TileBuf* b, uint64_t* bar, const uint64_t* kin, const uint32_t* vin,
+template <typename K>
+__device__ __forceinline__ void load_tile(TileBuf<K>* b, uint64_t* bar, const K* kin, const uint32_t* vin,
                                           uint32_t first, uint32_t nbulk) {
-  const uint32_t kb = nbulk * 8, vb = nbulk * 4;
+  const uint32_t kb = nbulk * static_cast<uint32_t>(sizeof(K)), vb = nbulk * 4;
   mbar_arrive(bar, kb + vb);
   if (nbulk) {
     bulk_g2s(b->k, kin + first, kb, bar);
@@ -197,7 +259,7 @@ __device__ __forceinline__ void load_tile(TileBuf* b, uint64_t* bar, const uint6
 // lane): r[j] = number of earlier items of this warp with the same digit;
 // the warp's counter row (zero on entry) ends holding its count per digit.
 template <int kMode, int kModeN>
-__device__ __forceinline__ void rank_in_warps(const TileBuf& tb, uint32_t valid, const Digit& dg, uint16_t* my_wh,
+__device__ __forceinline__ void rank_in_warps(const TileBuf<KeyOf<kMode>>& tb, uint32_t valid, const Digit& dg, uint16_t* my_wh,
                                               uint32_t (&r)[kItems], const Digit& dgn, uint32_t* hn) {
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t wbase = warp * 32 * kItems;
@@ -208,10 +270,10 @@ __device__ __forceinline__ void rank_in_warps(const TileBuf& tb, uint32_t valid,
 #pragma unroll
     for (int g = 0; g < kGroup; ++g) {
       const uint32_t idx = wbase + (j0 + g) * 32 + lane;
-      const uint64_t key = idx < valid ? tb.k[idx] : 0ull;
+      const KeyOf<kMode> key = idx < valid ? tb.k[idx] : KeyOf<kMode>(0);
       d[g] = digit_m<kMode>(key, dg);
-      if constexpr (kModeN != kDigitNone)
-        if (idx < valid) atomicAdd(&hn[digit_m<kModeN>(key, dgn)], 1u);
+      if constexpr (kModeN != kDigitNone)  // (depth keys: hn is null in the last pass)
+        if (idx < valid && (kMode != kDigitDepth || hn)) atomicAdd(&hn[digit_m<kModeN>(key, dgn)], 1u);
       r[j0 + g] = radix::equal_digit_lanes<kBits>(d[g]);
       const uint32_t fi = wbase + (j0 + g) * 32;
       const uint32_t nlive = valid > fi ? min(valid - fi, 32u) : 0u;
@@ -243,17 +305,42 @@ __device__ __forceinline__ void rank_in_warps(const TileBuf& tb, uint32_t valid,
 // the next pass's digits; the counts reach hist_next when it finishes.
 template <int kMode, int kModeN>
 __global__ void __launch_bounds__(kThreads, 2)
-    k_onesweep_pass(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
-                    uint32_t* __restrict__ vout, PassArgs a) {
+    k_onesweep_pass(const KeyOf<kMode>* __restrict__ kin, const uint32_t* __restrict__ vin,
+                    KeyOf<kMode>* __restrict__ kout, uint32_t* __restrict__ vout, PassArgs a) {
+  using K = KeyOf<kMode>;
   extern __shared__ __align__(128) unsigned char smem[];
-  TileBuf* buf = reinterpret_cast<TileBuf*>(smem);
-  uint16_t* wh = reinterpret_cast<uint16_t*>(smem + 2 * sizeof(TileBuf));
-  uint32_t* lstart = reinterpret_cast<uint32_t*>(smem + 2 * sizeof(TileBuf) + kWhBytes);
+  TileBuf<K>* buf = reinterpret_cast<TileBuf<K>*>(smem);
+  uint16_t* wh = reinterpret_cast<uint16_t*>(smem + 2 * sizeof(TileBuf<K>));
+  uint32_t* lstart = reinterpret_cast<uint32_t*>(smem + 2 * sizeof(TileBuf<K>) + kWhBytes);
   uint32_t* off = lstart + kBins;
-  uint32_t* hn = kModeN != kDigitNone ? off + kBins : nullptr;  // next pass's digit counts of this CTA
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t s_tile[2];
   __shared__ uint32_t s_warp[kWarps];
+
+  Digit dg = a.dg, dgn = a.dgn;
+  uint32_t* hist_next = a.hist_next;
+  uint32_t* status_next = a.status_next;
+  if constexpr (kMode == kDigitDepth) {
+    // The pass plan from the key range: a pass beyond it ends at once on
+    // every CTA (scan CTAs included); the buffers alternate so that the
+    // last pass that runs writes buffer 1.
+    const DepthDigits dd = depth_digits(a.range);
+    if (a.pass >= dd.passes) return;
+    dg = Digit{kDigitDepth, a.pass * dd.width, 0u, dd.mask, dd.lo, dd.cull};
+    dgn = dg;
+    dgn.msh += dd.width;
+    if (a.pass + 1 >= dd.passes) {
+      hist_next = nullptr;
+      status_next = nullptr;
+    }
+    const uint32_t out = ((dd.passes - 1 - a.pass) & 1u) ? 2u : 1u;
+    const uint32_t in = a.pass == 0 ? 0u : (((dd.passes - a.pass) & 1u) ? 2u : 1u);
+    kin = a.dk[in];
+    vin = a.dv[in];
+    kout = a.dk[out];
+    vout = a.dv[out];
+  }
+  uint32_t* hn = kModeN != kDigitNone && hist_next ? off + kBins : nullptr;  // next pass's digit counts of this CTA
 
   const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
   const uint32_t m = a.m, ntiles = a.ntiles;
@@ -261,7 +348,6 @@ __global__ void __launch_bounds__(kThreads, 2)
     scan_tiles<kBins>(a.status, ntiles, blockIdx.x - (gridDim.x - kScanCtas), a.err, reinterpret_cast<uint32_t*>(smem));
     return;
   }
-  const Digit dg = a.dg;
   uint16_t* my_wh = wh + warp * kBins;
   {
     uint4* z = reinterpret_cast<uint4*>(wh);
@@ -314,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     uint32_t nxt = ntiles;
     if (t == 0 && have_cur) nxt = atomicAdd(a.ticket, 1u);
     if (have_cur) {
-      TileBuf& tb = buf[b];
+      TileBuf<K>& tb = buf[b];
       const uint32_t first = cur * kTileKeys;
       valid = min(kTileKeys, m - first);
       const bool arrived = mbar_wait(&mbar[b], (phase >> b) & 1u, a.err);
@@ -337,7 +423,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       // ---- stable rank within each warp
       uint32_t r[kItems];
-      rank_in_warps<kMode, kModeN>(tb, valid, dg, my_wh, r, a.dgn, hn);
+      rank_in_warps<kMode, kModeN>(tb, valid, dg, my_wh, r, dgn, hn);
       if (t == 0 && nxt < ntiles) {
         const uint32_t nf = nxt * kTileKeys, nv = min(kTileKeys, m - nf);
         radix::prefetch_l2(kin + nf, static_cast<uint64_t>(nv) * 8);
@@ -365,7 +451,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       lstart[2 * t + 1] = s0 + c0;
       __syncthreads();
       const uint32_t wbase = warp * 32 * kItems;
-      uint64_t kr[kItems];
+      K kr[kItems];
       uint32_t vr[kItems];
 #pragma unroll
       for (int j = 0; j < kItems; ++j) {
@@ -395,20 +481,20 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (have_prev) {
       uint32_t e0 = 0, e1 = 0;
       if (prev != 0) wait_prefix<kBins>(a.status, prev, t, e0, e1, a.err);
-      if (a.status_next)
-        *reinterpret_cast<uint2*>(a.status_next + static_cast<size_t>(prev) * kBins + 2 * t) = make_uint2(0u, 0u);
+      if (status_next)
+        *reinterpret_cast<uint2*>(status_next + static_cast<size_t>(prev) * kBins + 2 * t) = make_uint2(0u, 0u);
       off[2 * t] = g0 + e0 - ps0;
       off[2 * t + 1] = g1 + e1 - (ps0 + pc0);
     }
     __syncthreads();  // cur is in digit order; off[] of prev is complete
     // ---- coalesced scatter of the previous tile in digit order
     if (have_prev) {
-      const TileBuf& pb = buf[b ^ 1u];
+      const TileBuf<K>& pb = buf[b ^ 1u];
 #pragma unroll
       for (int i = 0; i < kItems; ++i) {
         const uint32_t p = i * kThreads + t;
         if (p < pvalid) {
-          const uint64_t key = pb.k[p];
+          const K key = pb.k[p];
           const uint32_t dst = off[digit_m<kMode>(key, dg)] + p;
           if (dst < m) {
             kout[dst] = key;
@@ -438,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   if (hn) {  // this CTA's counts of the next pass's digits
     __syncthreads();
     for (uint32_t i = t; i < kBins; i += kThreads)
-      if (hn[i]) atomicAdd(a.hist_next + i, hn[i]);
+      if (hn[i]) atomicAdd(hist_next + i, hn[i]);
   }
 }
 
@@ -448,26 +534,96 @@ __global__ void __launch_bounds__(kThreads, 2)
 // ------------------------------------------------------------ host side
 namespace {
 std::mutex g_mu;
-uint32_t g_grid[64] = {};  // resident pass CTAs per device (0: not queried)
+uint32_t g_grid[2][64] = {};  // resident pass CTAs per key width and device (0: not queried)
 
-uint32_t pass_grid() {
+const void* depth_pass_kernel() {
+  return reinterpret_cast<const void*>(&onesweep::k_onesweep_pass<onesweep::kDigitDepth, onesweep::kDigitDepth>);
+}
+size_t pass_smem(bool depth) {
+  return depth ? onesweep::smem_bytes<uint32_t>() : onesweep::smem_bytes<uint64_t>();
+}
+
+// Resident CTAs of the pass kernel (64-bit keys, or the 32-bit depth keys);
+// every form of one key width has the same launch bounds and shared memory.
+uint32_t pass_grid(bool depth) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_grid[dev]) {
+  uint32_t& g = g_grid[depth ? 1 : 0][dev];
+  if (!g) {
     const void* fn =
-        reinterpret_cast<const void*>(&onesweep::k_onesweep_pass<onesweep::kDigitLo, onesweep::kDigitNone>);
+        depth ? depth_pass_kernel()
+              : reinterpret_cast<const void*>(&onesweep::k_onesweep_pass<onesweep::kDigitLo, onesweep::kDigitNone>);
+    const size_t smem = pass_smem(depth);
     int sms = 0, occ = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(onesweep::kSmem)) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
       return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, onesweep::kThreads, onesweep::kSmem) != cudaSuccess ||
-        occ <= 0)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, onesweep::kThreads, smem) != cudaSuccess || occ <= 0)
       return 0;
-    g_grid[dev] = static_cast<uint32_t>(sms * occ);
+    g = static_cast<uint32_t>(sms * occ);
   }
-  return g_grid[dev];
+  return g;
+}
+
+// Scratch layout shared by both key widths: hist | gstart | done, tickets
+// | status rows of two passes.
+void scratch_layout(onesweep::HistArgs& a, uint32_t* scratch) {
+  using namespace onesweep;
+  a.hist = scratch;
+  a.gstart = scratch + kMaxPasses * kBins;
+  a.done = scratch + 2 * kMaxPasses * kBins;
+  a.tickets = a.done + 4;
+  a.status0 = scratch + onesweep_header_words();
+}
+void pass_layout(onesweep::PassArgs& a, uint32_t pass, bool has_next, uint32_t* scratch) {
+  using namespace onesweep;
+  if (has_next) a.hist_next = scratch + (pass + 1) * kBins;
+  if (pass == 0)
+    a.gstart = scratch + kMaxPasses * kBins;
+  else
+    a.hist = scratch + pass * kBins;
+  a.ticket = scratch + 2 * kMaxPasses * kBins + 4 + pass;
+  uint32_t* st = scratch + onesweep_header_words();
+  const size_t rows = static_cast<size_t>(a.ntiles) * kBins;
+  a.status = st + (pass & 1u) * rows;
+  a.status_next = has_next ? st + ((pass + 1) & 1u) * rows : nullptr;
+}
+
+// 32 KB of keys per block and step, 4 blocks per SM
+uint32_t hist_grid(uint32_t m) {
+  int sms = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  uint32_t grid = (m + 8 * onesweep::kHistThreads - 1) / (8 * onesweep::kHistThreads);
+  const uint32_t cap = static_cast<uint32_t>(sms) * 4;
+  if (grid > cap) grid = cap;
+  return grid ? grid : 1;
+}
+
+// One cooperative launch of a pass: CTAs that take tiles while they last,
+// plus the scan CTAs (all resident).
+cudaError_t launch_pass(const void* fn, bool depth, const void* kin, const uint32_t* vin, void* kout, uint32_t* vout,
+                        onesweep::PassArgs& a, cudaStream_t s) {
+  using namespace onesweep;
+  const uint32_t resident = pass_grid(depth);
+  if (resident < 2 * kScanCtas) return cudaErrorInvalidConfiguration;
+  const uint32_t grid = (a.ntiles < resident - kScanCtas ? a.ntiles : resident - kScanCtas) + kScanCtas;
+  void* args[] = {(void*)&kin, (void*)&vin, (void*)&kout, (void*)&vout, (void*)&a};
+  const size_t smem = pass_smem(depth);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
+    return cudaErrorInvalidConfiguration;
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 onesweep::Digit make_digit(uint32_t shift, uint32_t mask, bool drop31) {
@@ -531,21 +687,11 @@ cudaError_t launch_onesweep_hist(const SortPlan& plan, const uint64_t* keys, uin
   a.ntiles = (m + kTileKeys - 1) / kTileKeys;
   a.dg[0] = make_digit(plan.shift[0], plan.mask[0], plan.drop31);
   a.bad_mask = plan.bad_mask;
-  a.hist = scratch;
-  a.gstart = scratch + kMaxPasses * kBins;
-  a.done = scratch + 2 * kMaxPasses * kBins;
-  a.tickets = a.done + 4;
-  a.status0 = scratch + onesweep_header_words();
+  scratch_layout(a, scratch);
   a.err = err;
-  int sms = 0, dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    return cudaErrorInvalidDevice;
-  // 32 KB of keys per block and step, 4 blocks per SM
-  uint32_t grid = (m + 8 * kHistThreads - 1) / (8 * kHistThreads);
-  const uint32_t cap = static_cast<uint32_t>(sms) * 4;
-  if (grid > cap) grid = cap;
-  if (grid == 0) grid = 1;
-  k_onesweep_hist<<<grid, kHistThreads, 0, s>>>(keys, a);
+  const uint32_t grid = hist_grid(m);
+  if (grid == 0) return cudaErrorInvalidDevice;
+  k_onesweep_hist<kDigitLo><<<grid, kHistThreads, 0, s>>>(keys, a);
   return cudaGetLastError();
 }
 
@@ -553,47 +699,55 @@ cudaError_t launch_onesweep_pass(const SortPlan& plan, uint32_t pass, const uint
                                  uint64_t* kout, uint32_t* vout, uint32_t m, uint32_t* scratch, uint32_t* err,
                                  cudaStream_t s) {
   using namespace onesweep;
-  const uint32_t resident = pass_grid();
-  if (resident == 0) return cudaErrorInvalidConfiguration;
   PassArgs a{};
   a.m = m;
   a.ntiles = (m + kTileKeys - 1) / kTileKeys;
   a.dg = make_digit(plan.shift[pass], plan.mask[pass], plan.drop31);
-  if (pass + 1 < plan.passes) {
-    a.dgn = make_digit(plan.shift[pass + 1], plan.mask[pass + 1], plan.drop31);
-    a.hist_next = scratch + (pass + 1) * kBins;
-  }
-  if (pass == 0)
-    a.gstart = scratch + kMaxPasses * kBins;
-  else
-    a.hist = scratch + pass * kBins;
-  a.ticket = scratch + 2 * kMaxPasses * kBins + 4 + pass;
-  uint32_t* st = scratch + onesweep_header_words();
-  const size_t rows = static_cast<size_t>(a.ntiles) * kBins;
-  a.status = st + (pass & 1u) * rows;
-  a.status_next = pass + 1 < plan.passes ? st + ((pass + 1) & 1u) * rows : nullptr;
+  const bool has_next = pass + 1 < plan.passes;
+  if (has_next) a.dgn = make_digit(plan.shift[pass + 1], plan.mask[pass + 1], plan.drop31);
+  pass_layout(a, pass, has_next, scratch);
   a.err = err;
-  // CTAs that take tiles while they last, plus the scan CTAs (all resident)
-  if (resident < 2 * kScanCtas) return cudaErrorInvalidConfiguration;
-  const uint32_t grid = (a.ntiles < resident - kScanCtas ? a.ntiles : resident - kScanCtas) + kScanCtas;
-  void* args[] = {(void*)&kin, (void*)&vin, (void*)&kout, (void*)&vout, (void*)&a};
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = kSmem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  const uint32_t next = pass + 1 < plan.passes ? a.dgn.mode : static_cast<uint32_t>(kDigitNone);
+  const uint32_t next = has_next ? a.dgn.mode : static_cast<uint32_t>(kDigitNone);
   const void* fn = a.dg.mode == kDigitLo   ? pass_kernel<kDigitLo>(next)
                    : a.dg.mode == kDigitHi ? pass_kernel<kDigitHi>(next)
                                            : pass_kernel<kDigitSpan>(next);
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmem)) != cudaSuccess)
-    return cudaErrorInvalidConfiguration;
-  return cudaLaunchKernelExC(&cfg, fn, args);
+  return launch_pass(fn, false, kin, vin, kout, vout, a, s);
+}
+
+cudaError_t launch_depth_onesweep_hist(const uint32_t* keys, uint32_t n, uint32_t* range, uint32_t* scratch,
+                                       uint32_t* err, cudaStream_t s) {
+  using namespace onesweep;
+  HistArgs a{};
+  a.m = n;
+  a.passes = 1;
+  a.ntiles = (n + kTileKeys - 1) / kTileKeys;
+  a.range = range;
+  scratch_layout(a, scratch);
+  a.err = err;
+  const uint32_t grid = hist_grid(n);
+  if (grid == 0) return cudaErrorInvalidDevice;
+  k_onesweep_hist<kDigitDepth><<<grid, kHistThreads, 0, s>>>(keys, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_depth_onesweep_pass(uint32_t pass, uint32_t* const dk[3], uint32_t* const dv[3], uint32_t n,
+                                       const uint32_t* range, uint32_t* scratch, uint32_t* err, cudaStream_t s) {
+  using namespace onesweep;
+  if (pass >= kDepthOnesweepPasses) return cudaErrorInvalidValue;
+  PassArgs a{};
+  a.m = n;
+  a.ntiles = (n + kTileKeys - 1) / kTileKeys;
+  // the device drops the next pass's counts and status when this pass is
+  // the last that the key range needs
+  pass_layout(a, pass, pass + 1 < kDepthOnesweepPasses, scratch);
+  a.pass = pass;
+  a.range = range;
+  for (int i = 0; i < 3; ++i) {
+    a.dk[i] = dk[i];
+    a.dv[i] = dv[i];
+  }
+  a.err = err;
+  return launch_pass(depth_pass_kernel(), true, nullptr, nullptr, nullptr, nullptr, a, s);
 }
 
 }  // namespace tdgs

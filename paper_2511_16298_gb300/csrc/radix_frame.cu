@@ -34,7 +34,7 @@ DepthPlan plan_depth_sort(uint32_t n, int tuned_bits, int ctas_per_sm) {
   DepthPlan p{};
   const uint32_t nn = n ? n : 1;
   const uint32_t g = depth_sort_grid();
-  if (g && nn <= depth_sort_capacity(g)) {
+  if (g && nn <= depth_sort_count_capacity(g)) {
     p.resident = true;
     p.bits = 9;
     p.passes = 4;  // at most; the kernel runs as many as the key range needs
@@ -44,6 +44,15 @@ DepthPlan plan_depth_sort(uint32_t n, int tuned_bits, int ctas_per_sm) {
     return p;
   }
   p.resident = false;
+  if (g && nn < (1u << 30)) {
+    p.onesweep = true;
+    p.bits = 9;
+    p.passes = kDepthOnesweepPasses;  // launches; the device runs as many as the key range needs
+    p.grid = g;
+    p.result = 1;
+    p.scratch_words = 0;  // its scratch is a buffer of its own (onesweep_scratch_words)
+    return p;
+  }
   p.bits = tuned_bits == 11 ? 11 : 8;
   p.passes = p.bits == 11 ? 3u : 4u;
   p.grid = radix::grid_for(depth_kernel(p.bits), nn, ctas_per_sm);

@@ -236,16 +236,21 @@ cudaError_t launch_views_dup(const ViewTable& vt, const uint32_t* sorder, const 
                              uint2* sdo, uint32_t* err, cudaStream_t s);
 
 // Radix passes of the frame path (radix_frame.cu, depth_sort.cu).
-// Depth sort of the N Gaussians: (uint32 depth key, uint32 index).  When
-// the Gaussians fit one 8192-key chunk per resident CTA the whole sort and
-// the scan of the tile counts in depth order run in one cooperative launch
-// (launch_depth_sort) over keys compressed to their range (key - smallest;
-// culled Gaussians one past the largest), with as many 9-bit digits as that
-// range needs (3 for a range below 2^27, 4 at most).  Otherwise one launch
-// per pass over all 32 bits: 8-bit (4 passes) or, if tuned, 11-bit (3
-// passes) digits.
+// Depth sort of the N Gaussians: (uint32 depth key, uint32 index), over
+// keys compressed to their range (key - smallest; culled Gaussians one past
+// the largest) with as many 9-bit digits as that range needs (3 for a range
+// below 2^27, 4 at most).  When the Gaussians fit one 8192-key chunk per
+// resident CTA, the whole sort and the scan of the tile counts in depth
+// order run in one cooperative launch (launch_depth_sort).  Larger N (below
+// 2^30) take the onesweep passes over 32-bit keys (onesweep.cu): a
+// histogram launch and kDepthOnesweepPasses pass launches, each reading the
+// pass plan from the key range (passes beyond it end at once), the result
+// in buffer pair 1; the scan of the counts in depth order follows.
+// Otherwise one launch per pass over all 32 bits: 8-bit (4 passes) or, if
+// tuned, 11-bit (3 passes) digits.
 struct DepthPlan {
   bool resident;          // one launch; keys compressed to their range, passes chosen on the device
+  bool onesweep;          // the onesweep passes over compressed 32-bit keys
   int bits;
   uint32_t passes, grid;  // passes: the most that run; grid 0: the device query failed
   uint32_t result;        // which of the three buffer pairs holds the sorted keys and indices
@@ -389,5 +394,18 @@ cudaError_t launch_onesweep_hist(const SortPlan& plan, const uint64_t* keys, uin
 cudaError_t launch_onesweep_pass(const SortPlan& plan, uint32_t pass, const uint64_t* kin, const uint32_t* vin,
                                  uint64_t* kout, uint32_t* vout, uint32_t m, uint32_t* scratch, uint32_t* err,
                                  cudaStream_t s);
+// The same passes over the depth sort's 32-bit keys (dk[0], dv[0]: keys and
+// indices from the count kernel; range: the key range it published in
+// range[2..3]; the histogram writes the pass count to range[4]).  The pass
+// plan is read on the device: launch the histogram,
+// then passes 0 .. kDepthOnesweepPasses - 1 in order; passes the range does
+// not need end at once, and the last pass that runs writes dk[1], dv[1]
+// (dk[2], dv[2] hold intermediate passes).  Scratch as above for m = n,
+// separate from any other sort's while both may be in use.
+constexpr uint32_t kDepthOnesweepPasses = 4;  // 32 bits in 9-bit digits
+cudaError_t launch_depth_onesweep_hist(const uint32_t* keys, uint32_t n, uint32_t* range, uint32_t* scratch,
+                                       uint32_t* err, cudaStream_t s);
+cudaError_t launch_depth_onesweep_pass(uint32_t pass, uint32_t* const dk[3], uint32_t* const dv[3], uint32_t n,
+                                       const uint32_t* range, uint32_t* scratch, uint32_t* err, cudaStream_t s);
 
 }  // namespace tdgs
