@@ -1,18 +1,18 @@
 // Depth sort of the frame path in one cooperative launch (Sec. II-A,
 // Sorting: a frame's Gaussians ordered by depth before their pairs are
 // emitted), followed by the exclusive scan of their tile counts in that
-// order (the first pair of every Gaussian).  Three forms:
+// order (the first pair of every Gaussian).  Two forms, both with one
+// 8192-key tile per CTA (larger frames take the onesweep passes over the
+// same compressed keys, onesweep.cu):
 //  * k_depth_sort<true>: the tile count step first (records in, keys kept
-//    in registers), then the sort; one 8192-key tile per CTA.
-//  * k_depth_sort<false>: keys and counts from the count kernel; one tile
-//    per CTA.
-//  * k_depth_sort_tiles: the same with 2 to 4 tiles per CTA.
+//    in registers), then the sort.
+//  * k_depth_sort<false>: keys and counts from the count kernel.
 //
 // The N depth keys (raw float bits; all ones for a Gaussian without pairs)
 // are compressed to key - smallest (all ones -> one past the largest) and
 // sorted stably, least significant digit first, with as many digits of at
 // most 9 bits as the compressed range needs.  One CTA of 512 threads per SM
-// owns one chunk and ranks each of its tiles in shared memory in every pass
+// owns one chunk (one tile) and ranks it in shared memory in every pass
 // (radix::rank_keys).
 //
 // A chunk's output base per digit = the keys of smaller digits (all
@@ -765,291 +765,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_depth_sort(DepthSortArgs A) {
   }
 }
 
-// The same sort for chunks of 2 to kMaxTiles tiles of 8192 keys per CTA
-// (keys and counts from the count kernel).  Each pass ranks every tile of
-// the chunk once and keeps each key's position in its tile (16 bits, in
-// shared memory) and the tile's digit counts; publishes the chunk's counts
-// as its row; reads all rows (the digit totals and the chunks before it,
-// so no totals are kept between passes and no extra barrier is needed);
-// then reloads each tile's keys and scatters them from the running base
-// per digit, the next tile's values arriving by bulk copy meanwhile.
-constexpr uint32_t kMaxTiles = 4;
-constexpr size_t kSmemTiles = S::kSmem + 2 * kTileKeys * 4 + kMaxTiles * kTileKeys * 2;
-
-// Sums of bins 8q..8q+7 over all rows g, g + kRowGroups, ... < G of one
-// pass (all: every row; lo: rows below c), waiting (bounded) until each
-// row is written.
-__device__ __forceinline__ void sum_all_rows(const uint32_t* __restrict__ rows, uint32_t G, uint32_t c, uint32_t g,
-                                             uint32_t q, uint32_t lo[8], uint32_t all[8], uint32_t* err) {
-  for (uint32_t r0 = g; r0 < G; r0 += kRowGroups * kRowBatch) {
-    uint4 w[kRowBatch];
-    uint32_t pend = 0;
-#pragma unroll
-    for (uint32_t i = 0; i < kRowBatch; ++i) {
-      const uint32_t r = r0 + i * kRowGroups;
-      w[i] = make_uint4(0x10001u, 0x10001u, 0x10001u, 0x10001u);  // rows past G count zero
-      if (r < G) w[i] = ld_relaxed_v4(rows + static_cast<size_t>(r) * kRowWords + 4 * q);
-      if (!row_ready(w[i])) pend |= 1u << i;
-    }
-    uint32_t spins = 0;
-    while (pend) {
-      if (++spins > kSpinLimit) {
-        latch_error(err, TDGS_ERR_TIMEOUT, kSiteBarrier);
-        break;
-      }
-      __nanosleep(32);
-#pragma unroll
-      for (uint32_t i = 0; i < kRowBatch; ++i) {
-        if (pend & (1u << i)) {
-          w[i] = ld_relaxed_v4(rows + static_cast<size_t>(r0 + i * kRowGroups) * kRowWords + 4 * q);
-          if (row_ready(w[i])) pend &= ~(1u << i);
-        }
-      }
-    }
-#pragma unroll
-    for (uint32_t i = 0; i < kRowBatch; ++i) {
-      const bool below = r0 + i * kRowGroups < c;
-      const uint32_t x[4] = {w[i].x, w[i].y, w[i].z, w[i].w};
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const uint32_t c0 = (x[u] & 0xffffu) - 1u, c1 = (x[u] >> 16) - 1u;
-        all[2 * u] += c0;
-        all[2 * u + 1] += c1;
-        if (below) {
-          lo[2 * u] += c0;
-          lo[2 * u + 1] += c1;
-        }
-      }
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kThreads, 1) k_depth_sort_tiles(DepthSortArgs A) {
-  const uint32_t* __restrict__ key0 = A.key0;
-  uint32_t* __restrict__ k1 = A.k1;
-  uint32_t* __restrict__ v1 = A.v1;
-  uint32_t* __restrict__ k2 = A.k2;
-  uint32_t* __restrict__ v2 = A.v2;
-  uint32_t* __restrict__ counts = A.counts;
-  uint32_t* __restrict__ range = A.range;
-  uint32_t* __restrict__ scratch = A.scratch;
-  uint32_t* __restrict__ err = A.err;
-  const uint32_t n = A.n;
-  extern __shared__ __align__(16) unsigned char smem[];
-  radix::Smem<uint32_t> sm;
-  {
-    unsigned char* p = smem;
-    sm.wh = reinterpret_cast<uint16_t*>(p);
-    p += S::kWhBytes;
-    sm.xk = reinterpret_cast<uint32_t*>(p);
-    p += S::kXkBytes;
-    sm.xv = reinterpret_cast<uint32_t*>(p);
-    p += S::kXvBytes;
-    sm.base = reinterpret_cast<uint32_t*>(p);
-    sm.lstart = sm.base + kBins;
-    sm.off = sm.lstart + kBins;
-  }
-  uint32_t* vst[2] = {reinterpret_cast<uint32_t*>(smem + S::kSmem),
-                      reinterpret_cast<uint32_t*>(smem + S::kSmem) + kTileKeys};  // staged values, two tiles
-  uint16_t* s_pos = reinterpret_cast<uint16_t*>(smem + S::kSmem + 2 * kTileKeys * 4);  // [tile][item] position
-  static_assert(S::kXkBytes >= kRowGroups * kBins * 4 && S::kXvBytes >= kRowGroups * kBins * 4,
-                "row-sum partials fit the exchange buffers");
-  __shared__ uint32_t s_tc[kMaxTiles][kBins];  // this pass's digit counts per tile
-  __shared__ uint2 s_warp2[kWarps];
-  __shared__ unsigned long long s_sum[kWarps + 1];
-  __shared__ unsigned long long s_base;
-  __shared__ __align__(8) uint64_t s_mbar[2];
-  const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5, c = blockIdx.x, G = gridDim.x;
-  const uint32_t Sz = ((n + G - 1) / G + 3) & ~3u;
-  const uint32_t beg = min(c * Sz, n), end = min(beg + Sz, n);
-  uint32_t tiles = (end - beg + kTileKeys - 1) / kTileKeys;
-  bool ok = tiles <= kMaxTiles;  // guaranteed by the host
-  if (!ok) tiles = kMaxTiles;
-  {
-    uint4* z = reinterpret_cast<uint4*>(sm.wh);
-    for (uint32_t i = t; i < S::kWhBytes / 16; i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
-  }
-  uint32_t* csum = scratch + kSumWord;
-  uint32_t* rows = scratch + kRowWord;
-  const uint32_t lo = __ldcg(range + 2), hi = __ldcg(range + 3);
-  const uint32_t cull = hi >= lo ? hi - lo + 1u : 0u;
-  const uint32_t bits = cull ? 32u - static_cast<uint32_t>(__clz(cull)) : 0u;
-  const uint32_t passes = bits ? (bits + kBits - 1) / kBits : 1u;
-  const uint32_t width = (bits + passes - 1) / passes;
-  const uint32_t mask = width ? (1u << width) - 1u : 0u;
-  if (c == 0 && t == 0) {
-    range[4] = passes;
-    scratch[kFinalSlot * kLine] = 0u;
-  }
-  if (c == 0)
-    for (uint32_t i = t; i < G; i += kThreads) csum[i] = 0u;
-  if (t == 0) {
-    osw::mbar_init(&s_mbar[0]);
-    osw::mbar_init(&s_mbar[1]);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  const uint32_t g = t / (kBins / 8), q = t % (kBins / 8);
-  const uint32_t wbase = warp * 32 * kItems;
-  uint32_t par = 0;  // bit b: the phase parity of buffer b's next copy
-  for (uint32_t p = 0; p < passes; ++p) {
-    const bool last = p + 1 == passes;
-    const bool to_one = ((passes - 1 - p) & 1u) == 0;
-    const uint32_t* kin = p == 0 ? key0 : (to_one ? k2 : k1);
-    const uint32_t* vin = to_one ? v2 : v1;
-    uint32_t* kout = to_one ? k1 : k2;
-    uint32_t* vout = to_one ? v1 : v2;
-    const uint32_t* vsrc = p == 0 ? counts : vin;
-    const uint32_t shift = p * width;
-    auto stage = [&](uint32_t ti) {  // thread 0: the bulk copy of tile ti's values
-      const uint32_t tb = beg + ti * kTileKeys, nbulk = min(kTileKeys, end - tb) & ~3u;
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      osw::mbar_arrive(&s_mbar[ti & 1u], nbulk * 4);
-      if (nbulk) osw::bulk_g2s(vst[ti & 1u], vsrc + tb, nbulk * 4, &s_mbar[ti & 1u]);
-    };
-    // ---- rank every tile once: its digit counts and each key's position
-    for (uint32_t ti = 0; ti < tiles; ++ti) {
-      const uint32_t tb = beg + ti * kTileKeys, valid = min(kTileKeys, end - tb);
-      radix::TileRegs<uint32_t, false, kItems> R;
-#pragma unroll
-      for (int j = 0; j < kItems; ++j) {
-        const uint32_t idx = wbase + j * 32 + lane;
-        R.k[j] = idx < valid ? __ldcs(kin + tb + idx) : 0u;
-      }
-      if (p == 0) {
-#pragma unroll
-        for (int j = 0; j < kItems; ++j)
-          if (wbase + j * 32 + lane < valid) R.k[j] = R.k[j] == 0xffffffffu ? cull : R.k[j] - lo;
-      }
-#pragma unroll
-      for (int j = 0; j < kItems; ++j) R.d[j] = (R.k[j] >> shift) & mask;
-      radix::rank_keys<false, S, uint32_t, false, kBits, kItems>(valid, sm, R);
-      const uint32_t cnt = sm.lstart[t];
-      s_tc[ti][t] = cnt;
-      sm.lstart[t] = excl_scan2(cnt, 0u, s_warp2).x;
-      __syncthreads();
-      uint16_t* my_wh = sm.wh + warp * kBins;
-#pragma unroll
-      for (int j = 0; j < kItems; ++j) {
-        const uint32_t idx = wbase + j * 32 + lane;
-        if (idx < valid) s_pos[ti * kTileKeys + idx] = static_cast<uint16_t>(R.r[j] + sm.lstart[R.d[j]] + my_wh[R.d[j]]);
-      }
-      __syncwarp();
-      uint4* z = reinterpret_cast<uint4*>(my_wh);
-      for (uint32_t i = lane; i < kBins / 8; i += 32) z[i] = make_uint4(0, 0, 0, 0);
-      __syncthreads();
-    }
-    if (t == 0 && tiles) stage(0);  // overlaps with the rows below
-    // ---- publish the chunk's counts; totals and the chunks before it
-    uint32_t own = 0;
-    for (uint32_t ti = 0; ti < tiles; ++ti) own += s_tc[ti][t];
-    sm.lstart[t] = own;
-    __syncthreads();
-    if (t < kBins / 8) {
-      const uint32_t* ls = sm.lstart + 8 * t;
-      uint4 w;
-      w.x = (ls[0] + 1u) | ((ls[1] + 1u) << 16);
-      w.y = (ls[2] + 1u) | ((ls[3] + 1u) << 16);
-      w.z = (ls[4] + 1u) | ((ls[5] + 1u) << 16);
-      w.w = (ls[6] + 1u) | ((ls[7] + 1u) << 16);
-      st_relaxed_v4(rows + (static_cast<size_t>(p) * G + c) * kRowWords + 4 * t, w);
-    }
-    {
-      uint32_t acc_lo[8] = {0, 0, 0, 0, 0, 0, 0, 0}, acc_all[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      sum_all_rows(rows + static_cast<size_t>(p) * G * kRowWords, G, c, g, q, acc_lo, acc_all, err);
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        sm.xv[g * kBins + 8 * q + i] = acc_lo[i];
-        sm.xk[g * kBins + 8 * q + i] = acc_all[i];
-      }
-      __syncthreads();
-      uint32_t before = 0, tot = 0;
-#pragma unroll
-      for (uint32_t gg = 0; gg < kRowGroups; ++gg) {
-        before += sm.xv[gg * kBins + t];
-        tot += sm.xk[gg * kBins + t];
-      }
-      sm.base[t] = excl_scan2(tot, 0u, s_warp2).x + before;  // this chunk's first position per digit
-      __syncthreads();
-    }
-    // ---- the tiles, from the running base per digit
-    for (uint32_t ti = 0; ti < tiles; ++ti) {
-      const uint32_t tb = beg + ti * kTileKeys, valid = min(kTileKeys, end - tb);
-      const uint32_t b = ti & 1u;
-      if (t == 0 && ti + 1 < tiles) stage(ti + 1);
-      {
-        const uint32_t cnt = s_tc[ti][t];
-        const uint32_t st = excl_scan2(cnt, 0u, s_warp2).x;
-        const uint32_t bs = sm.base[t];
-        sm.off[t] = bs - st;
-        sm.base[t] = bs + cnt;
-      }
-      uint32_t hk[kItems], pos[kItems];
-#pragma unroll
-      for (int j = 0; j < kItems; ++j) {
-        const uint32_t idx = wbase + j * 32 + lane;
-        uint32_t k = 0u;
-        pos[j] = 0u;
-        if (idx < valid) {
-          k = __ldcs(kin + tb + idx);
-          if (p == 0) k = k == 0xffffffffu ? cull : k - lo;
-          pos[j] = s_pos[ti * kTileKeys + idx];
-        }
-        hk[j] = last ? (k >> shift) & mask : k;
-      }
-      if (!osw::mbar_wait(&s_mbar[b], (par >> b) & 1u, err) && t == 0)
-        (void)osw::mbar_wait(&s_mbar[b], (par >> b) & 1u, err);
-      par ^= 1u << b;
-      __syncthreads();
-      ok &= exchange_scatter(sm, vst[b], hk, pos, valid, tb, valid & ~3u, vsrc, p == 0, last, shift, mask, n, kout,
-                             vout, k1, v1, counts, Sz, G, csum);
-    }
-    arrive_and_wait(scratch + (last ? kFinalSlot : 1 + p) * kLine, G, err);
-  }
-  if (!ok) latch_error(err, TDGS_ERR_CAPACITY, kSiteRadixRange);
-  // ---- the pair offsets, tile by tile from the sum of the chunks before
-  if (warp == 0) {
-    const uint64_t before = chunks_before(csum, c);
-    if (lane == 0) s_base = before;
-  }
-  __syncthreads();
-  uint64_t run = s_base;
-  for (uint32_t ti = 0; ti < tiles; ++ti) {
-    const uint32_t tb = beg + ti * kTileKeys;
-    run = scan_offsets(k1, A.offsets, tb, min(tb + kTileKeys, end), run, s_sum, err);
-  }
-  // ---- reset for the next launch: this chunk's rows; CTA 0 the counters
-  for (uint32_t i = t; i < passes * (kRowWords / 4); i += kThreads) {
-    const uint32_t pp = i / (kRowWords / 4), w = i % (kRowWords / 4);
-    reinterpret_cast<uint4*>(rows + (static_cast<size_t>(pp) * G + c) * kRowWords)[w] = make_uint4(0, 0, 0, 0);
-  }
-  if (c == 0 && t < passes) scratch[(1 + t) * kLine] = 0u;  // slots 1 .. passes (the last is unused)
-}
-
 }  // namespace depth
 
 // ------------------------------------------------------------- host side
 namespace {
-enum class Form { kCount, kOne, kTiles };
+enum class Form { kCount, kOne };
 radix::Kernel depth_kernel(Form f) {
   const void* fn = f == Form::kCount ? reinterpret_cast<const void*>(&depth::k_depth_sort<true>)
-                   : f == Form::kOne ? reinterpret_cast<const void*>(&depth::k_depth_sort<false>)
-                                     : reinterpret_cast<const void*>(&depth::k_depth_sort_tiles);
-  return radix::Kernel{fn, depth::kBits, depth::kThreads, depth::kItems,
-                       f == Form::kTiles ? depth::kSmemTiles : depth::kSmem, 1};
+                                     : reinterpret_cast<const void*>(&depth::k_depth_sort<false>);
+  return radix::Kernel{fn, depth::kBits, depth::kThreads, depth::kItems, depth::kSmem, 1};
 }
 
 cudaError_t launch_depth(Form f, uint32_t grid, const DepthSortArgs& a, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
-  if (grid == 0 || grid > radix::kMaxGrid || a.n > depth_sort_capacity(grid)) return cudaErrorInvalidConfiguration;
-  if (f != Form::kTiles && a.n > depth_sort_count_capacity(grid)) return cudaErrorInvalidConfiguration;
+  if (grid == 0 || grid > radix::kMaxGrid || a.n > depth_sort_count_capacity(grid))
+    return cudaErrorInvalidConfiguration;
   if (f == Form::kCount && a.vt.nv > kMaxViews) return cudaErrorInvalidValue;
   DepthSortArgs args = a;
   void* params[] = {(void*)&args};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(depth::kThreads);
-  cfg.dynamicSmemBytes = f == Form::kTiles ? depth::kSmemTiles : depth::kSmem;
+  cfg.dynamicSmemBytes = depth::kSmem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -1064,7 +801,7 @@ uint32_t depth_sort_grid() {
   // every form: one CTA per SM (the occupancy query also sets their shared
   // memory limit on this device)
   uint32_t g = radix::kMaxGrid;
-  for (Form f : {Form::kCount, Form::kOne, Form::kTiles}) {
+  for (Form f : {Form::kCount, Form::kOne}) {
     const uint32_t r = radix::resident_ctas(depth_kernel(f), 1);
     if (r < g) g = r;
   }
@@ -1077,18 +814,12 @@ uint32_t depth_sort_count_capacity(uint32_t grid) {
   return grid * depth::kTileKeys;
 }
 
-uint32_t depth_sort_capacity(uint32_t grid) {
-  // up to kMaxTiles tiles per CTA; record indices below 2^22
-  const uint64_t c = static_cast<uint64_t>(grid) * depth::kTileKeys * depth::kMaxTiles;
-  return static_cast<uint32_t>(c < (1ull << depth::kValueBits) ? c : (1ull << depth::kValueBits));
-}
-
 size_t depth_sort_scratch_words(uint32_t grid) {
   return depth::kRowWord + static_cast<size_t>(depth::kMaxPasses) * grid * depth::kRowWords;
 }
 
 cudaError_t launch_depth_sort(uint32_t grid, const DepthSortArgs& a, cudaStream_t s) {
-  return launch_depth(a.n <= depth_sort_count_capacity(grid) ? Form::kOne : Form::kTiles, grid, a, s);
+  return launch_depth(Form::kOne, grid, a, s);
 }
 
 cudaError_t launch_count_depth_sort(uint32_t grid, const DepthSortArgs& a, cudaStream_t s) {

@@ -590,12 +590,14 @@ void pass_layout(onesweep::PassArgs& a, uint32_t pass, bool has_next, uint32_t* 
   a.status_next = has_next ? st + ((pass + 1) & 1u) * rows : nullptr;
 }
 
-// 32 KB of keys per block and step, 4 blocks per SM
+// 4096 keys per block and step, at least 4 steps per block (fewer blocks:
+// fewer global atomics on the 512 counters), at most 4 blocks per SM
 uint32_t hist_grid(uint32_t m) {
   int sms = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return 0;
-  uint32_t grid = (m + 8 * onesweep::kHistThreads - 1) / (8 * onesweep::kHistThreads);
+  constexpr uint32_t kPerBlock = 4 * 8 * onesweep::kHistThreads;
+  uint32_t grid = static_cast<uint32_t>((static_cast<uint64_t>(m) + kPerBlock - 1) / kPerBlock);
   const uint32_t cap = static_cast<uint32_t>(sms) * 4;
   if (grid > cap) grid = cap;
   return grid ? grid : 1;

@@ -264,9 +264,8 @@ cudaError_t launch_depth_pass(const DepthPlan& dp, uint32_t pass, const uint32_t
                               uint32_t* kout, uint32_t* vout, uint32_t n, uint32_t* scratch, uint32_t* bar,
                               uint32_t* err, cudaStream_t s);
 // Single-launch depth sort (depth_sort.cu).  Grid: one CTA per SM (0 if
-// the device query failed); it takes n <= depth_sort_capacity(grid) keys
-// (up to 4 tiles of 8192 per CTA, below 2^22), with the count step
-// n <= depth_sort_count_capacity(grid) (one tile per CTA).
+// the device query failed); it takes n <= depth_sort_count_capacity(grid)
+// keys (one tile of 8192 per CTA), with or without the count step.
 // Results: v1 = record indices in depth order, offsets = the exclusive scan
 // of the tile counts in that order (the pair offsets in depth order); k1
 // receives the counts in depth order, (k2, v2) are intermediate.  range:
@@ -298,7 +297,6 @@ struct DepthSortArgs {
   uint32_t* err;
 };
 uint32_t depth_sort_grid();
-uint32_t depth_sort_capacity(uint32_t grid);
 uint32_t depth_sort_count_capacity(uint32_t grid);
 size_t depth_sort_scratch_words(uint32_t grid);
 cudaError_t launch_depth_sort(uint32_t grid, const DepthSortArgs& a, cudaStream_t s);

@@ -368,7 +368,7 @@ def test_depth_sort_alternating_pass_counts(ctx, oracle):
 
 def test_depth_sort_at_capacity(ctx, oracle):
     """N = SMs x 8192 Gaussians, the most the single-launch depth sort takes
-    (every CTA a full chunk), and one more (the per-pass launches)."""
+    (every CTA a full chunk), and one more (the onesweep passes)."""
     cap = torch.cuda.get_device_properties(0).multi_processor_count * 8192
     for n in (cap, cap + 1):
         fr = synth.frame_random(77, n, 1280, 720, max_sigma=6.0)
@@ -377,9 +377,10 @@ def test_depth_sort_at_capacity(ctx, oracle):
 
 
 @pytest.mark.parametrize("mult", [2, 3, 4])
-def test_depth_sort_several_tiles_per_cta(ctx, oracle, mult):
-    """Above SMs x 8192 Gaussians the single launch takes 2 to 4 tiles of
-    8192 per CTA (up to 2^22 Gaussians); ragged last chunks included."""
+def test_depth_sort_onesweep_sizes(ctx, oracle, mult):
+    """Above SMs x 8192 Gaussians the depth sort takes the onesweep passes
+    over the compressed 32-bit keys: 2 to 4 times that N (up to 2^22), each
+    with a ragged last 4096-key tile."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     n = min(mult * sms * 8192 - 5 * mult, 1 << 22)
     fr = synth.frame_random(90 + mult, n, 1920, 1080, max_sigma=4.0)
@@ -387,9 +388,11 @@ def test_depth_sort_several_tiles_per_cta(ctx, oracle, mult):
     assert 1 <= ctx.depth_passes() <= 4
 
 
-def test_depth_sort_several_tiles_alternating_pass_counts(ctx, oracle):
-    """The multi-tile form's counters, totals and rows are reset for every
-    pass count too."""
+def test_depth_sort_onesweep_alternating_pass_counts(ctx, oracle):
+    """The onesweep depth form under 4, 1, 3 and 2 passes in a row: the
+    passes the key range does not need end at once, the result always lands
+    in the same buffers, and the scratch state left by each run serves the
+    next."""
     n = torch.cuda.get_device_properties(0).multi_processor_count * 8192 + 4099
     for i, ((lo, hi), passes) in enumerate([((1e-30, 1e30), 4), ((3.0, 3.0), 1), ((0.5, 80.0), 3),
                                              ((1.0, 1.01), 2)]):
