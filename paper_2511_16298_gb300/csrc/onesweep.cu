@@ -88,6 +88,20 @@ __device__ __forceinline__ uint32_t digit_m(K k, const Digit& g) {
   }
 }
 
+// Shared-memory slot of digit d in the per-digit tables of a pass (the
+// warps' 16-bit counters, the tile-local starts, the output offsets, the
+// next pass's counts).  A digit spanning the two key words is (tile bits :
+// top depth bits), whose low bits take few values, so a warp's digits would
+// crowd a few banks; the slot d ^ ((d >> 6) << 1) spreads them and keeps
+// each digit pair 2t, 2t + 1 in one 32-bit word of the 16-bit counters
+// (word t ^ (t >> 5)).  A bijection on [0, 512): ranks, counts and starts
+// are unchanged.
+template <bool kSwz>
+__device__ __forceinline__ uint32_t slot(uint32_t d) {
+  if constexpr (kSwz) return d ^ ((d >> 6) << 1);
+  return d;
+}
+
 // Pass plan of the depth keys from their range (range[2..3]: the smallest
 // and largest visible key): the compressed keys 0 .. cull need `bits` bits,
 // split evenly over the fewest passes of at most kBits.
@@ -271,9 +285,10 @@ __device__ __forceinline__ void rank_in_warps(const TileBuf<KeyOf<kMode>>& tb, u
     for (int g = 0; g < kGroup; ++g) {
       const uint32_t idx = wbase + (j0 + g) * 32 + lane;
       const KeyOf<kMode> key = idx < valid ? tb.k[idx] : KeyOf<kMode>(0);
-      d[g] = digit_m<kMode>(key, dg);
+      d[g] = slot<kMode == kDigitSpan>(digit_m<kMode>(key, dg));  // equal slots <=> equal digits
       if constexpr (kModeN != kDigitNone)  // (depth keys: hn is null in the last pass)
-        if (idx < valid && (kMode != kDigitDepth || hn)) atomicAdd(&hn[digit_m<kModeN>(key, dgn)], 1u);
+        if (idx < valid && (kMode != kDigitDepth || hn))
+          atomicAdd(&hn[slot<kModeN == kDigitSpan>(digit_m<kModeN>(key, dgn))], 1u);
       r[j0 + g] = radix::equal_digit_lanes<kBits>(d[g]);
       const uint32_t fi = wbase + (j0 + g) * 32;
       const uint32_t nlive = valid > fi ? min(valid - fi, 32u) : 0u;
@@ -308,6 +323,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     k_onesweep_pass(const KeyOf<kMode>* __restrict__ kin, const uint32_t* __restrict__ vin,
                     KeyOf<kMode>* __restrict__ kout, uint32_t* __restrict__ vout, PassArgs a) {
   using K = KeyOf<kMode>;
+  constexpr bool kSwz = kMode == kDigitSpan;  // per-digit tables in swizzled slots
   extern __shared__ __align__(128) unsigned char smem[];
   TileBuf<K>* buf = reinterpret_cast<TileBuf<K>*>(smem);
   uint16_t* wh = reinterpret_cast<uint16_t*>(smem + 2 * sizeof(TileBuf<K>));
@@ -435,9 +451,10 @@ __global__ void __launch_bounds__(kThreads, 2)
         uint32_t* wh32 = reinterpret_cast<uint32_t*>(wh);
         uint32_t run = 0;
 #pragma unroll
+        const uint32_t pw = slot<kSwz>(2 * t) >> 1;  // the word of digits 2t, 2t+1
         for (int w = 0; w < kWarps; ++w) {
-          const uint32_t x = wh32[w * (kBins / 2) + t];
-          wh32[w * (kBins / 2) + t] = run;
+          const uint32_t x = wh32[w * (kBins / 2) + pw];
+          wh32[w * (kBins / 2) + pw] = run;
           run += x;  // halves stay below 2^16: no carry between digits
         }
         c0 = run & 0xffffu;
@@ -447,8 +464,8 @@ __global__ void __launch_bounds__(kThreads, 2)
       st_relaxed_v2(a.status + static_cast<size_t>(cur) * kBins + 2 * t, kFlagA | c0, kFlagA | c1);
       // ---- tile-local digit starts, positions, exchange into digit order
       s0 = cta_excl_scan(c0 + c1, s_warp);
-      lstart[2 * t] = s0;
-      lstart[2 * t + 1] = s0 + c0;
+      lstart[slot<kSwz>(2 * t)] = s0;
+      lstart[slot<kSwz>(2 * t + 1)] = s0 + c0;
       __syncthreads();
       const uint32_t wbase = warp * 32 * kItems;
       K kr[kItems];
@@ -460,7 +477,8 @@ __global__ void __launch_bounds__(kThreads, 2)
           kr[j] = tb.k[idx];
           vr[j] = tb.v[idx];
           const uint32_t dd = digit_m<kMode>(kr[j], dg);
-          r[j] += lstart[dd] + my_wh[dd];
+          const uint32_t sd = slot<kSwz>(dd);
+          r[j] += lstart[sd] + my_wh[sd];
         }
       }
       __syncwarp();
@@ -483,8 +501,8 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (prev != 0) wait_prefix<kBins>(a.status, prev, t, e0, e1, a.err);
       if (status_next)
         *reinterpret_cast<uint2*>(status_next + static_cast<size_t>(prev) * kBins + 2 * t) = make_uint2(0u, 0u);
-      off[2 * t] = g0 + e0 - ps0;
-      off[2 * t + 1] = g1 + e1 - (ps0 + pc0);
+      off[slot<kSwz>(2 * t)] = g0 + e0 - ps0;
+      off[slot<kSwz>(2 * t + 1)] = g1 + e1 - (ps0 + pc0);
     }
     __syncthreads();  // cur is in digit order; off[] of prev is complete
     // ---- coalesced scatter of the previous tile in digit order
@@ -495,7 +513,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const uint32_t p = i * kThreads + t;
         if (p < pvalid) {
           const K key = pb.k[p];
-          const uint32_t dst = off[digit_m<kMode>(key, dg)] + p;
+          const uint32_t dst = off[slot<kSwz>(digit_m<kMode>(key, dg))] + p;
           if (dst < m) {
             kout[dst] = key;
             vout[dst] = pb.v[p];
@@ -524,7 +542,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   if (hn) {  // this CTA's counts of the next pass's digits
     __syncthreads();
     for (uint32_t i = t; i < kBins; i += kThreads)
-      if (hn[i]) atomicAdd(hist_next + i, hn[i]);
+      if (const uint32_t c = hn[slot<kModeN == kDigitSpan>(i)]) atomicAdd(hist_next + i, c);
   }
 }
 
