@@ -287,9 +287,11 @@ __global__ void __launch_bounds__(256)
     for (uint32_t q0 = 0; q0 < nquad; q0 += 32) {
       const uint32_t qi = q0 + lane;
       if (qi < nquad) {
-        // relative position of the quad's first element (may be < 0 in the first quad)
-        const int64_t r0 = static_cast<int64_t>(qi) * 4 - lead;
-        const uint32_t x = r0 < 0 ? 0u : static_cast<uint32_t>(r0);
+        // relative position of the quad's first element, modulo 2^32: the
+        // first quad's lead elements wrap to 2^32 - lead .. 2^32 - 1, at or
+        // above nrel (<= 0xfffffff0), so one unsigned test skips them
+        const uint32_t r0 = qi * 4u - lead;
+        const uint32_t x = qi ? r0 : 0u;
         uint32_t owner = 0;
 #pragma unroll
         for (uint32_t step = 16; step > 0; step >>= 1)
@@ -319,10 +321,9 @@ __global__ void __launch_bounds__(256)
         uint32_t valid = 0;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const int64_t r = r0 + i;
+          const uint32_t ru = r0 + static_cast<uint32_t>(i);
           e[i] = K(0);
-          if (r >= 0 && r < static_cast<int64_t>(nrel)) {
-            const uint32_t ru = static_cast<uint32_t>(r);
+          if (ru < nrel) {
             while (next <= ru) {  // the owner's pairs are done: the next Gaussian with pairs
               ++owner;
               next = s_st[w8][owner + 1];
