@@ -729,7 +729,8 @@ struct Shape {
   uint32_t rbits, tbits;
   bool wide;
   uint32_t npass, w0;
-  uint32_t kbits;  // compiled digit width of the tile passes
+  uint32_t kbits;  // compiled digit width of the tile passes before the last
+  uint32_t klast;  // compiled digit width of the last (expanding) pass, for its own width
 };
 
 Shape shape_of(const tdgs_context* ctx) {
@@ -745,6 +746,7 @@ Shape shape_of(const tdgs_context* ctx) {
   sh.npass = sh.tbits <= dmax ? 1u : (sh.tbits + dmax - 1) / dmax;
   sh.w0 = (sh.tbits + sh.npass - 1) / std::max(1u, sh.npass);
   sh.kbits = stream_kernel_bits(sh.w0);
+  sh.klast = stream_kernel_bits(sh.tbits - (sh.npass - 1) * sh.w0);  // e.g. 13 tile bits: 7 + 6
   return sh;
 }
 
@@ -795,12 +797,12 @@ tdgs_status ensure_pair_buffers(tdgs_context* ctx, uint64_t m, cudaStream_t s) {
   if (st == TDGS_OK) st = ensure(ctx, ctx->f_values, m * 4 + 16, s);
   const uint32_t mm = static_cast<uint32_t>(m ? m : 1);
   const int cps = ctx->tuning.ctas_per_sm;
-  const uint32_t g0 = stream_grid(sh.wide, false, sh.kbits, mm, cps), g1 = stream_grid(sh.wide, true, sh.kbits, mm, cps);
+  const uint32_t g0 = stream_grid(sh.wide, false, sh.kbits, mm, cps), g1 = stream_grid(sh.wide, true, sh.klast, mm, cps);
   if (g0 == 0 || g1 == 0) return fail(ctx, TDGS_ERR_CUDA, "device query for the tile sort failed");
   if (st == TDGS_OK)
     st = ensure(ctx, ctx->sort_scratch,
                 std::max(stream_scratch_words(sh.wide, false, sh.kbits, g0),
-                         stream_scratch_words(sh.wide, true, sh.kbits, g1)) * 4,
+                         stream_scratch_words(sh.wide, true, sh.klast, g1)) * 4,
                 s);
   return st;
 }
@@ -927,8 +929,8 @@ tdgs_status run_back(tdgs_context* ctx, uint32_t m, const uint64_t* m_dev, cudaS
     StreamPass sp{};
     sp.wide = sh.wide;
     sp.expand = last;
-    sp.bits = sh.kbits;
-    sp.grid = stream_grid(sh.wide, last, sh.kbits, m, ctx->tuning.ctas_per_sm);
+    sp.bits = last ? sh.klast : sh.kbits;
+    sp.grid = stream_grid(sh.wide, last, sp.bits, m, ctx->tuning.ctas_per_sm);
     sp.kin = st[p & 1];
     sp.kout = last ? ctx->f_keys.p : st[(p + 1) & 1];
     sp.vout = last ? static_cast<uint32_t*>(ctx->f_values.p) : nullptr;
