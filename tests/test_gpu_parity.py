@@ -400,6 +400,20 @@ def test_depth_sort_onesweep_alternating_pass_counts(ctx, oracle):
         assert ctx.depth_passes() == passes
 
 
+def test_depth_sort_onesweep_all_culled_then_visible(ctx, oracle):
+    """The onesweep depth form when no Gaussian has pairs (an empty key
+    range: one pass over a zero-width digit, M = 0, every range {0, 0}),
+    then an ordinary frame of the same size on the same context."""
+    n = torch.cuda.get_device_properties(0).multi_processor_count * 8192 + 777
+    rng = np.random.default_rng(5)
+    culled = synth.records(rng.uniform(0, 640, n), rng.uniform(0, 360, n), rng.uniform(1.0, 9.0, n),
+                           np.zeros(n, dtype=np.int64))
+    assert _check_frame(ctx, oracle, synth.Frame(640, 360, culled, "all-culled-onesweep")) == 0
+    assert ctx.depth_passes() == 1
+    _check_frame(ctx, oracle, _depth_range_frame(71, 0.5, 80.0, n=n))
+    assert ctx.depth_passes() == 3
+
+
 def test_sort_frame_scene_1m(ctx, oracle):
     m = _check_frame(ctx, oracle, synth.frame_scene(0))
     assert m > 5_000_000
