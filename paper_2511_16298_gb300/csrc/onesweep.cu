@@ -450,8 +450,8 @@ __global__ void __launch_bounds__(kThreads, 2)
       {
         uint32_t* wh32 = reinterpret_cast<uint32_t*>(wh);
         uint32_t run = 0;
-#pragma unroll
         const uint32_t pw = slot<kSwz>(2 * t) >> 1;  // the word of digits 2t, 2t+1
+#pragma unroll
         for (int w = 0; w < kWarps; ++w) {
           const uint32_t x = wh32[w * (kBins / 2) + pw];
           wh32[w * (kBins / 2) + pw] = run;

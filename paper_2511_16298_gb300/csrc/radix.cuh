@@ -374,10 +374,7 @@ template <typename K, int kBins, int kThreads, uint32_t kU = 8>
 __device__ __forceinline__ void chunk_bases(const K* __restrict__ kin, const PassArgs& a,
                                             uint32_t beg, uint32_t end, bool d31, uint32_t* base,
                                             uint32_t* hist, uint32_t* s_warp, const uint32_t* s_vtile) {
-  constexpr int kWarps = kThreads / 32;
-  constexpr int kBpt = (kBins + kThreads - 1) / kThreads;
-  const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
-  const uint32_t G = gridDim.x, c = blockIdx.x;
+  const uint32_t t = threadIdx.x, lane = lane_id(), c = blockIdx.x;
   for (uint32_t b = t; b < kBins; b += kThreads) hist[b] = 0;
   __syncthreads();
   {
