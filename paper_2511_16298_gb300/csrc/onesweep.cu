@@ -1,30 +1,36 @@
 // tdgs_sort_pairs as a onesweep LSD radix sort (the Sorting step of
 // Sec. II-A: instances ordered by tile, then by depth; sorting is 86-89 % of
-// the frame in Table VI).
+// the frame in Table VI), and the same passes over the depth keys of large
+// frames.
 //
-//   k_onesweep_hist  reads every key once and builds the digit histograms of
-//                    all passes at once (shared-memory counters per CTA,
-//                    then global atomics); the last CTA scans them into each
+//   k_onesweep_hist  reads every key once and counts the first pass's
+//                    digits (shared-memory counters per CTA, then global
+//                    atomics); the last CTA scans them into the first
 //                    pass's digit starts.  It also clears the first pass's
-//                    look-back status and the tile tickets.
-//   k_onesweep_pass  one launch per digit.  Persistent CTAs take tiles of
-//                    4096 pairs in ticket order; each tile is copied into
-//                    shared memory by one bulk copy (double buffered: the
-//                    next tile is in flight while this one is ranked),
-//                    ranked stably with one ballot per digit bit, and its
-//                    per-digit counts are published at once.  A decoupled
-//                    look-back over the predecessors' status words -- a
-//                    window of tiles per L2 round trip -- gives the tile's
-//                    global position per digit; the tile is then exchanged
-//                    into digit order in shared memory and written out with
-//                    coalesced stores.  Every key and value is read once and
-//                    written once per pass.
+//                    status words, the later passes' counters and the tile
+//                    tickets.
+//   k_onesweep_pass  one cooperative launch per digit.  Compute CTAs take
+//                    tiles of 4096 pairs in ticket order; a tile arrives in
+//                    shared memory by bulk copies (double buffered: the
+//                    next tile is in flight while this one is ranked), is
+//                    ranked stably with one ballot per digit bit, publishes
+//                    its per-digit counts at once, counts the next pass's
+//                    digits and is exchanged into digit order in place.
+//                    The last CTAs of the grid are scan CTAs that turn the
+//                    published counts into per-tile prefixes; a compute CTA
+//                    takes tile k's prefix one iteration after publishing
+//                    it (while it ranked the next tile) and writes tile k
+//                    out with coalesced stores.  Every key and value is
+//                    read once and written once per pass.
 //
-// Tickets make the look-back deadlock-free without co-residency: a tile
-// only waits on tiles with smaller tickets, and the smallest unfinished
-// ticket is always the one its CTA is working on.  Every wait is bounded
-// and latches TDGS_ERR_TIMEOUT when it runs out; every scatter is checked
-// against the pair count.
+// Key forms: 64-bit keys with the digit a bit field of the low word, of the
+// high word, or spanning both (tdgs_sort_pairs), and 32-bit depth keys
+// compressed to their range, whose pass plan each launch reads from the
+// range on the device.  Tickets keep the waits deadlock-free: a tile only
+// waits on tiles with smaller tickets, and ranking (which publishes the
+// counts) never waits on another CTA.  Every wait is bounded and latches
+// TDGS_ERR_TIMEOUT when it runs out; every scatter is checked against the
+// pair count.
 #include <mutex>
 #include <type_traits>
 
