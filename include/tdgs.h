@@ -136,14 +136,16 @@ tdgs_status tdgs_context_set_sort_variant(tdgs_context* ctx, int variant);
  *   TDGS_TUNE_CTAS_PER_SM      CTAs per SM of the persistent radix grids
  *                              (capped by occupancy)
  *   TDGS_TUNE_DEPTH_DIGIT_BITS digit width of the frame's depth sort when
- *                              it runs as one launch per pass (frames or
- *                              batches above the single-launch sort's
- *                              capacity, one 8192-key tile per resident
- *                              CTA: about 1.25M Gaussians on 152 SMs):
- *                              8 (4 passes, the built-in choice) or 11
- *                              (3 passes).  The single-launch sort below
- *                              that capacity always takes 9-bit digits and
- *                              only the passes the depth range needs. */
+ *                              it runs as one launch per pass over all 32
+ *                              key bits (frames or batches of 2^30
+ *                              Gaussians or more): 8 (4 passes, the
+ *                              built-in choice) or 11 (3 passes).  Below
+ *                              that the depth sort takes 9-bit digits over
+ *                              the keys less the smallest and only the
+ *                              passes their range needs: one launch up to
+ *                              one 8192-key tile per resident CTA (about
+ *                              1.25M Gaussians on 152 SMs), the onesweep
+ *                              passes above. */
 enum {
   TDGS_TUNE_SORT_VARIANT = 0,
   TDGS_TUNE_TILE_DIGIT_BITS = 1,
@@ -173,9 +175,10 @@ uint64_t tdgs_context_launch_count(const tdgs_context* ctx);
 tdgs_status tdgs_context_enable_timing(tdgs_context* ctx, int enable);
 int tdgs_context_kernel_times(tdgs_context* ctx, tdgs_kernel_time* out, int max);
 
-/* Digit passes the last single-launch depth sort of the fused frame ran on
- * this context (the count follows the frame's depth range: 1 to 4), or 0
- * if none has run.  Waits for the work on `stream`. */
+/* Digit passes the last depth sort of the fused frame ran on this context
+ * over keys compressed to their range (the single launch or the onesweep
+ * passes; the count follows the frame's depth range: 1 to 4), or 0 if
+ * none has run.  Waits for the work on `stream`. */
 tdgs_status tdgs_context_depth_passes(tdgs_context* ctx, int* passes, void* stream);
 
 /* ------------------------------------------------------- the five steps --- */

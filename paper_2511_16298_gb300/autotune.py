@@ -26,6 +26,9 @@ import torch
 from . import tdgs
 
 L2_FLUSH = 256 << 20
+# Gaussians from which a frame's depth sort runs one launch per pass over
+# all key bits (the only form the depth digit width knob reaches)
+DEPTH_PER_PASS_MIN = 1 << 30
 
 
 def _bucket(x: int) -> int:
@@ -77,10 +80,14 @@ def tune_views(ctx: tdgs.Context, views: list, reps: int = 3) -> dict:
     """Best (tile_digit_bits, ctas_per_sm, depth_digit_bits) for a batch of
     views [(records, width, height)] (one view = one frame)."""
     flush = torch.empty(L2_FLUSH, dtype=torch.uint8, device=views[0][0].device)
+    n = sum(int(v[0].shape[0]) for v in views)
+    # the depth digit width only reaches the per-pass depth sort (2^30
+    # Gaussians or more); below that the built-in choice stands
+    dbit_choices = (11, 8) if n >= DEPTH_PER_PASS_MIN else (0,)
     trials = []
     for bits in (12, 8, 6):
         for cps in (0, 1, 2, 3):
-            for dbits in (11, 8):
+            for dbits in dbit_choices:
                 knobs = {"tile_digit_bits": bits, "ctas_per_sm": cps, "depth_digit_bits": dbits}
                 ctx.apply_tuning(knobs)
                 ms = _time(lambda: ctx.sort_views(views), reps, flush)
@@ -88,7 +95,6 @@ def tune_views(ctx: tdgs.Context, views: list, reps: int = 3) -> dict:
     ctx.apply_tuning({"tile_digit_bits": 0, "ctas_per_sm": 0, "depth_digit_bits": 0})
     ctx.sync()
     best, ms = min(trials, key=lambda x: x[1])
-    n = sum(int(v[0].shape[0]) for v in views)
     t = sum(tdgs.num_tiles(v[1], v[2]) for v in views)
     return {"best": best, "ms": ms, "trials": [(tt, round(m, 4)) for tt, m in trials],
             "key": f"views:n{_bucket(n)}:t{_bucket(t)}:v{len(views)}"}
