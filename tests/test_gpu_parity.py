@@ -178,6 +178,28 @@ def test_sort_pairs_onesweep(ctx, oracle, m, tile_bits, ties):
     assert np.array_equal(u32(sv), rv)
 
 
+@pytest.mark.parametrize("m,tile_bits,positive", [(70_001, 2, False), (65_537, 3, True), (300_007, 12, True),
+                                                    (123_457, 4, False)])
+def test_sort_pairs_onesweep_spanning_digits(ctx, oracle, m, tile_bits, positive):
+    """Digits that straddle the two key words (7 to 9 bits wide, with and
+    without bit 31 dropped), on keys whose top depth bits take two values
+    as real depths do: the passes whose per-digit tables sit in swizzled
+    slots, and the passes before them, which count their digits."""
+    rng = np.random.default_rng(m + tile_bits)
+    k = rng.integers(0, 1 << (32 + tile_bits), size=m, dtype=np.uint64)
+    top = rng.choice(np.array([7, 8], dtype=np.uint64), size=m)  # bits 27..30
+    k = (k & ~np.uint64(0xF << 27)) | (top << np.uint64(27))
+    if positive:
+        k &= ~np.uint64(1 << 31)
+    v = rng.permutation(m).astype(np.uint32)
+    _, rk, rv = oracle.sort_pairs(k, v)
+    sk, sv = ctx.sort_pairs(torch.from_numpy(k.view(np.int64)).to(DEV), torch.from_numpy(v.view(np.int32)).to(DEV),
+                            tile_bits, T.SORT_DEPTH_POSITIVE if positive else 0)
+    ctx.sync()
+    assert np.array_equal(u64(sk), rk)
+    assert np.array_equal(u32(sv), rv)
+
+
 def test_sort_pairs_onesweep_skewed_and_repeated(ctx, oracle):
     """All keys equal (one digit takes every pair of every tile), one hot tile
     with random depths, then sizes that shrink and grow between calls on the
