@@ -316,6 +316,16 @@ def test_sort_frame_wide_elements(ctx, oracle):
     _check_frame(ctx, oracle, fr)
 
 
+@pytest.mark.parametrize("n,width,height", [(400_000, 1920, 1080), (1_300_000, 3840, 2160)])
+def test_sort_frame_pass_widths(ctx, oracle, n, width, height):
+    """Tile ids of 13 and 15 bits split into passes of 7 + 6 and 8 + 7 bits,
+    each pass on the kernel compiled for its own digit width (8-bit, then
+    6-bit at 1080p).  400k Gaussians at 1080p pack into 32-bit elements;
+    1.3M at 4K (above one depth-sort chunk per CTA: the onesweep depth form)
+    into 64-bit ones."""
+    _check_frame(ctx, oracle, synth.frame_random(31 + width, n, width, height, max_sigma=12.0))
+
+
 def test_sort_frame_repeated_calls(ctx, oracle):
     """Many sorts on one context (the look-back epoch tag wraps every 7
     passes) stay exact."""
