@@ -83,6 +83,47 @@ def test_views_async_and_graph(ctx, oracle):
         check_view(oracle, f, res)
 
 
+def test_views_graph_onesweep_depth(ctx, oracle):
+    """A batch above one depth-sort chunk per CTA (3 x 500k Gaussians: the
+    onesweep depth form, whose pass plan is read on the device) captured
+    in a CUDA graph: replays equal the exact call, and new depths through
+    the same graph match the oracle."""
+    mv = synth.multiview(seed=5, n=500_000, views=3, width=1280, height=720, scale0=0.05)
+    frames = mv.views
+    gs = [T.records_to_tensor(f.gaussians, DEV) for f in frames]
+    views = [(g, f.width, f.height) for g, f in zip(gs, frames)]
+    rng = np.random.default_rng(8)
+    frames2 = []
+    for f in frames:  # same positions and radii, other depths (another depth range)
+        g2 = f.gaussians.copy()
+        g2["depth"] = (g2["depth"] * rng.uniform(0.5, 4.0, size=f.n)).astype(np.float32)
+        frames2.append(synth.Frame(f.width, f.height, g2, f.name + "-redepth"))
+    exact = ctx.sort_views(views, copy=True)
+    cap = sum(r[3] for r in exact) + 1000  # same rectangles: the same pair count
+    ctx.reserve_views(views, cap)
+    ctx.sort_views_async(views)  # the first call on this shape, outside the capture
+    for e, res in zip(exact, ctx.views_results(len(views))):
+        for a, b in zip(e[:3], res[:3]):
+            assert torch.equal(a, b)
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            ctx.sort_views_async(views)
+    torch.cuda.current_stream().wait_stream(side)
+    for _ in range(2):
+        graph.replay()
+        for e, res in zip(exact, ctx.views_results(len(views))):
+            for a, b in zip(e[:3], res[:3]):
+                assert torch.equal(a, b)
+    for g, f2 in zip(gs, frames2):
+        g.copy_(T.records_to_tensor(f2.gaussians, DEV))
+    graph.replay()
+    res = ctx.views_results(len(views))
+    check_view(oracle, frames2[1], res[1])
+
+
 def test_views_capacity_exceeded(ctx):
     frames = [synth.frame_small(0)]
     g = T.records_to_tensor(frames[0].gaussians, DEV)
